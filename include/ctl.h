@@ -1,0 +1,243 @@
+/*
+ * ctl.h -- C-ABI of the GB300 CKKS server path of CryptoTL (arXiv 2205.11935).
+ *
+ * CryptoTL's protocol (Fig. "alg:cryptotl", Sec. 3) has a client encrypt its input,
+ * a server evaluate its frozen layers on the ciphertext ("ClassifyHE"), and the client
+ * decrypt the resulting features.  This library is the server side, on one GPU:
+ * CKKS with RNS limbs, hybrid key switching, the baby-step giant-step diagonal mat-vec
+ * of Eq. (bsgs), the square activation and rescaling (Sec. 3.1).  The client calls
+ * (keygen, encrypt, decrypt) are provided so that a test or a caller can close the loop.
+ *
+ * Conventions for every function:
+ *  - Return value: CTL_OK (0) or a negative CTL_E* code; the message of the last error
+ *    of the calling thread is available from ctl_last_error().  No C++ exception
+ *    crosses this interface.  On error, output handles are left untouched (NULL).
+ *  - Ownership: handles are created by the library and released by the matching
+ *    *_destroy.  Input arrays are owned by the caller and are read (copied) before the
+ *    call returns.  Output arrays are written before the call returns.
+ *  - Pointers: every array argument is a HOST pointer unless its name ends in _dev.
+ *  - Streams: all GPU work of a context runs on its stream (ctl_set_stream); calls that
+ *    return host data synchronise that stream first.  Contexts and keys are immutable
+ *    after creation and may be shared; a ciphertext must not be used by two concurrent
+ *    calls.
+ *  - Layout: a ciphertext at level l (l live data primes q_0..q_{l-1}) is a pair of
+ *    ring elements, stored limb-major as [2][l][N] 64-bit residues.  Exported and
+ *    imported ciphertexts are in coefficient form; on the device they are kept in the
+ *    NTT (evaluation) form.  A batch of B ciphertexts is [B][2][l][N].
+ *  - Parameters: the ring degree N is a power of two in [16, 16384]; prime sizes are
+ *    20..61 bits; every prime is the largest unused prime q < 2^b with q = 1 mod
+ *    max(2N, 32768) (so that N = 8192 and N = 16384 share primes).
+ */
+#ifndef CTL_H
+#define CTL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CTL_OK 0
+#define CTL_EINVAL (-1)   /* invalid argument (sizes, N, primes, NULL handle)        */
+#define CTL_ELEVEL (-2)   /* no level left to rescale / level mismatch              */
+#define CTL_ESCALE (-3)   /* scale mismatch between operands                        */
+#define CTL_EKEY (-4)     /* a needed Galois or relinearisation key is missing      */
+#define CTL_ENOMEM (-5)   /* device or host allocation failed                       */
+#define CTL_ECUDA (-6)    /* a CUDA runtime call failed                              */
+#define CTL_ETIMEOUT (-7) /* a bounded device or host wait expired                   */
+#define CTL_EBUSY (-8)    /* admission refused (memory budget or queue full)        */
+#define CTL_ENOTSUP (-9)  /* unsupported parameter combination                       */
+
+typedef struct ctl_context ctl_context;
+typedef struct ctl_keys ctl_keys;
+typedef struct ctl_ct ctl_ct;
+typedef struct ctl_model ctl_model;
+typedef struct ctl_server ctl_server;
+
+/* Device allocator hooks: alloc(bytes, stream, user) returns device memory ordered on
+ * `stream`; free(ptr, stream, user) releases it.  NULL hooks select the library's
+ * stream-ordered pool (cudaMallocAsync). */
+typedef void* (*ctl_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*ctl_free_fn)(void* ptr, void* stream, void* user);
+
+/* Thread-local message of the last error, or "" if none. */
+const char* ctl_last_error(void);
+/* Library version string. */
+const char* ctl_version(void);
+
+/* Host only (no GPU needed): the primes the library would choose for `n` bit sizes at
+ * ring degree N, written to out[n].  Same rule as ctl_context_create. */
+int ctl_plan_primes(uint32_t N, const uint32_t* bits, uint32_t n, uint64_t* out);
+
+/* ---------------------------------------------------------------------------------
+ * Context: CKKS parameters (Sec. 3.1, "The CKKS HE scheme"; the modulus chain of the
+ * "Multiplicative Depth" paragraph).  q_bits[n_q] is the data chain, q_0 first (the
+ * last prime is the first to be dropped by rescaling); p_bits[n_p] are the special
+ * primes of key switching.  dnum (1..n_q) is the number of key-switching digits at the
+ * top level; each digit holds alpha = ceil(n_q/dnum) consecutive data primes.  scale is
+ * the nominal encoding scale Delta.  seed is reserved for context-level randomness.
+ * Builds device twiddle and base-conversion tables on the current CUDA device.
+ * Errors: CTL_EINVAL (bad N or bit sizes), CTL_ECUDA, CTL_ENOMEM.
+ * ------------------------------------------------------------------------------- */
+int ctl_context_create(ctl_context** out, uint32_t N, const uint32_t* q_bits, uint32_t n_q, const uint32_t* p_bits,
+                       uint32_t n_p, uint32_t dnum, double scale, uint64_t seed);
+void ctl_context_destroy(ctl_context* ctx);
+/* Writes the n_q + n_p primes (data chain then special primes) to moduli (nullable) and
+ * the counts to the other (nullable) outputs. */
+int ctl_context_info(const ctl_context* ctx, uint64_t* moduli, uint32_t* n_q, uint32_t* n_p, uint32_t* alpha);
+/* Makes the context issue its work on `stream` (a cudaStream_t, NULL = library stream). */
+int ctl_set_stream(ctl_context* ctx, void* stream);
+int ctl_set_allocator(ctl_context* ctx, ctl_alloc_fn alloc_fn, ctl_free_fn free_fn, void* user);
+/* Blocks until the context stream is idle. */
+int ctl_synchronize(ctl_context* ctx);
+
+/* ---------------------------------------------------------------------------------
+ * Keys (Fig. alg:cryptotl: the client's key pair; Sec. 3.1 rotations need Galois keys).
+ * Samples the ternary secret, the relinearisation key (s^2 -> s) and one Galois key
+ * (sigma_{5^r}(s) -> s) per distinct rotation r of rotations[n_rot] (r < 0 allowed,
+ * r = 0 mod N/2 needs none), all from SplitMix64 streams of `seed`.  Keys live on the
+ * device.  Errors: CTL_EINVAL, CTL_ENOMEM, CTL_ECUDA.
+ * ------------------------------------------------------------------------------- */
+int ctl_keygen(ctl_context* ctx, const int32_t* rotations, uint32_t n_rot, uint64_t seed, ctl_keys** out);
+void ctl_keys_destroy(ctl_keys* keys);
+/* Exports key `key_id` (0 = relinearisation, odd g = Galois key of X -> X^g) as
+ * [beta][2][n_q+n_p][N] coefficient-form residues into out (cap words).
+ * Errors: CTL_EKEY (no such key), CTL_EINVAL (cap too small). */
+int ctl_keys_export(const ctl_keys* keys, uint64_t key_id, uint64_t* out, size_t cap);
+/* Galois element 5^(r mod N/2) mod 2N of a left rotation by r. */
+uint64_t ctl_galois_element(const ctl_context* ctx, int64_t r);
+
+/* ---------------------------------------------------------------------------------
+ * Client side (Fig. alg:cryptotl: HE.Enc, HE.Dec; Sec. 3.1 "SIMD Encoding").
+ * ctl_encode: slot values x[n] (n <= N/2) -> integer coefficients m[N] at `scale`
+ *   (host FP64 canonical embedding, round half away from zero).
+ * ctl_encrypt: encodes x at the nominal scale and encrypts at the top level with the
+ *   secret key: ct = (-a*s + m + e, a), a and e drawn from streams of `seed`.
+ * ctl_encrypt_coeffs: the same from given integer coefficients m[N].
+ * ctl_decrypt: decrypts and decodes the first n slots into y[n] (synchronises).
+ * ctl_decrypt_coeffs: the centred coefficients of c0 + c1*s as doubles, m[N].
+ * ------------------------------------------------------------------------------- */
+int ctl_encode(ctl_context* ctx, const double* x, size_t n, double scale, int64_t* m);
+int ctl_decode(ctl_context* ctx, const double* m, size_t n, double scale, double* y);
+int ctl_encrypt(ctl_context* ctx, const ctl_keys* keys, const double* x, size_t n, uint64_t seed, ctl_ct** out);
+int ctl_encrypt_coeffs(ctl_context* ctx, const ctl_keys* keys, const int64_t* m, uint64_t seed, ctl_ct** out);
+int ctl_decrypt(ctl_context* ctx, const ctl_keys* keys, const ctl_ct* ct, double* y, size_t n);
+int ctl_decrypt_coeffs(ctl_context* ctx, const ctl_keys* keys, const ctl_ct* ct, double* m);
+
+/* ---------------------------------------------------------------------------------
+ * Ciphertext handles.  ctl_ct_import copies count ciphertexts [count][2][level][N]
+ * (coefficient form) from host memory to the device; ctl_ct_export writes them back
+ * (synchronises).  ctl_ct_import_dev / export_dev do the same from/to device memory
+ * (the caller's pointer, ordered on the context stream).
+ * ------------------------------------------------------------------------------- */
+int ctl_ct_import(ctl_context* ctx, const uint64_t* coeffs, uint32_t count, uint32_t level, double scale,
+                  ctl_ct** out);
+int ctl_ct_export(const ctl_ct* ct, uint64_t* coeffs, size_t cap);
+int ctl_ct_import_dev(ctl_context* ctx, const uint64_t* coeffs_dev, uint32_t count, uint32_t level, double scale,
+                      ctl_ct** out);
+int ctl_ct_export_dev(const ctl_ct* ct, uint64_t* coeffs_dev, size_t cap);
+int ctl_ct_info(const ctl_ct* ct, uint32_t* level, uint32_t* count, double* scale);
+/* Concatenates cts[n] (same level and scale) into one batch; ctl_ct_slice copies
+ * ciphertext i of a batch out. */
+int ctl_ct_concat(ctl_context* ctx, const ctl_ct* const* cts, size_t n, ctl_ct** out);
+int ctl_ct_slice(const ctl_ct* batch, uint32_t i, ctl_ct** out);
+void ctl_ct_destroy(ctl_ct* ct);
+
+/* ---------------------------------------------------------------------------------
+ * Homomorphic operations (Sec. 3.1).  Each accepts a batch (count >= 1) and returns a
+ * new handle; the input is not modified.
+ * ctl_rotate: left rotation of the slots by r (rot_r of Eq. bsgs).  Hybrid key
+ *   switching: ModUp(c1) -> sigma_g -> key product -> ModDown; (sigma_g(c0) + ks0, ks1).
+ *   Errors: CTL_EKEY if the Galois key of r is missing.
+ * ctl_rescale: divides by the last prime with rounding ("rescaling ... is equivalent to
+ *   rounding", Sec. 3.1).  Errors: CTL_ELEVEL at level 1.
+ * ctl_eval_square: HMult(ct, ct) + relinearisation + rescale (the square activation;
+ *   ciphertext products are the costliest operation, Sec. 5.1).  Scale becomes
+ *   scale^2 / q_last.
+ * ctl_eval_dense: y = W x for W (m x n, row-major FP64) by Eq. (bsgs): t = next power of
+ *   two >= max(m, n) (zero padding), t1 = 2^ceil(log2(t)/2), t2 = t/t1; t1+t2-2
+ *   rotations, t plaintext products, depth 1.  The input must hold [x, x] in slots
+ *   [0, 2t); the output holds y in slots [0, m) and zeros elsewhere.  The diagonals are
+ *   encoded at scale q_last * Delta / scale_in, so the output carries Delta again.
+ *   bias (nullable, m values) is added before the rescale.  Needs the Galois keys of
+ *   1..t1-1 and k*t1 (k = 1..t2-1).  Errors: CTL_EINVAL (2t > N/2), CTL_EKEY, CTL_ELEVEL.
+ * ctl_eval_dense_coeffs: the same with the t diagonal plaintexts given as integer
+ *   coefficients pts[t][N] (and bias as coefficients, nullable); the scale bookkeeping
+ *   uses pt_scale.  Lets a caller inject exactly encoded plaintexts.
+ * ctl_replicate: y + rot_{-t}(y): turns y in slots [0, t) into [y, y] (the layout the
+ *   next dense layer needs, Sec. 3.1 "Multiple Predictions").
+ * ------------------------------------------------------------------------------- */
+int ctl_rotate(ctl_context* ctx, const ctl_keys* keys, const ctl_ct* in, int32_t r, ctl_ct** out);
+int ctl_rescale(ctl_context* ctx, const ctl_ct* in, ctl_ct** out);
+int ctl_eval_square(ctl_context* ctx, const ctl_keys* keys, const ctl_ct* in, ctl_ct** out);
+int ctl_eval_dense(ctl_context* ctx, const ctl_keys* keys, const ctl_ct* in, const double* W, uint32_t m, uint32_t n,
+                   const double* bias, ctl_ct** out);
+int ctl_eval_dense_coeffs(ctl_context* ctx, const ctl_keys* keys, const ctl_ct* in, const int64_t* pts, uint32_t t,
+                          const int64_t* bias, double pt_scale, ctl_ct** out);
+int ctl_replicate(ctl_context* ctx, const ctl_keys* keys, const ctl_ct* in, uint32_t t, ctl_ct** out);
+int ctl_add(ctl_context* ctx, const ctl_ct* a, const ctl_ct* b, ctl_ct** out);
+int ctl_mul_plain_coeffs(ctl_context* ctx, const ctl_ct* in, const int64_t* pt, double pt_scale, ctl_ct** out);
+
+/* ---------------------------------------------------------------------------------
+ * Transform access.  ctl_ntt_dev computes, for n_polys polys of `limbs` limbs each
+ * ([n_polys][limbs][N] words, limb l taken modulo prime l of the chain q_0..q_{n_q-1},
+ * p_0..), the negacyclic NTT a_hat[k] = a(psi^(2*bitrev(k)+1)) (psi the smallest
+ * primitive 2N-th root of unity; bit-reversed order) or, with inverse != 0, its inverse.
+ * in_dev and out_dev are device pointers (they may be equal); inputs must be reduced.
+ * Ordered on the context stream; does not synchronise.
+ * Errors: CTL_EINVAL (limbs > n_q + n_p, null pointer).
+ * ------------------------------------------------------------------------------- */
+int ctl_ntt_dev(ctl_context* ctx, const uint64_t* in_dev, uint64_t* out_dev, uint32_t n_polys, uint32_t limbs,
+                int inverse);
+
+/* ---------------------------------------------------------------------------------
+ * Models: the frozen server layers of Fig. alg:cryptotl (M_S), encoded once.
+ * A layer is CTL_LAYER_DENSE (W m x n, optional bias, optional injected coefficients
+ * pt_coeffs[t][N]), CTL_LAYER_SQUARE or CTL_LAYER_REPLICATE (t = rep_t).  The model is
+ * built for ciphertexts entering at in_level with scale in_scale; the diagonals of each
+ * dense layer are encoded at the level and scale that layer will see.
+ * ctl_model_forward runs ClassifyHE on a batch of ciphertexts under one key set.
+ * ctl_model_rotations lists the rotations the model needs (for ctl_keygen).
+ * ------------------------------------------------------------------------------- */
+#define CTL_LAYER_DENSE 1
+#define CTL_LAYER_SQUARE 2
+#define CTL_LAYER_REPLICATE 3
+typedef struct ctl_layer {
+  int32_t kind;
+  uint32_t m, n;              /* dense: output and input dimensions                 */
+  const double* W;            /* dense: m x n row-major (nullable if pt_coeffs)     */
+  const double* bias;         /* dense: m values or NULL                            */
+  const int64_t* pt_coeffs;   /* dense: injected diagonal coefficients [t][N] or NULL */
+  uint32_t rep_t;             /* replicate: shift t                                 */
+} ctl_layer;
+
+int ctl_model_create(ctl_context* ctx, const ctl_layer* layers, uint32_t n_layers, uint32_t in_level, double in_scale,
+                     ctl_model** out);
+void ctl_model_destroy(ctl_model* model);
+/* Writes up to cap distinct rotation amounts to rot and their number to *n_rot. */
+int ctl_model_rotations(const ctl_model* model, int32_t* rot, uint32_t cap, uint32_t* n_rot);
+int ctl_model_forward(ctl_context* ctx, const ctl_model* model, const ctl_keys* keys, const ctl_ct* in, ctl_ct** out);
+/* Output level and scale of the model. */
+int ctl_model_info(const ctl_model* model, uint32_t* out_level, double* out_scale, uint64_t* bytes);
+
+/* ---------------------------------------------------------------------------------
+ * Statistics: kernel launches since the last reset, homomorphic operation counters
+ * (rotations, plaintext products, additions, relinearisations, rescales), and, when
+ * timing is enabled, per-kernel-class device milliseconds and launch counts measured
+ * with CUDA events on the context stream.  Class names: ctl_stats_class_name(i).
+ * ------------------------------------------------------------------------------- */
+int ctl_stats_reset(ctl_context* ctx);
+int ctl_stats_enable_timing(ctl_context* ctx, int enable);
+uint64_t ctl_stats_launches(const ctl_context* ctx);
+int ctl_stats_ops(const ctl_context* ctx, uint64_t* ops5);
+int ctl_stats_kernel_classes(void);
+const char* ctl_stats_class_name(int i);
+/* Collects pending event timings (synchronises) and writes ms[i], launches[i] and the
+ * algorithmic modular multiplications work[i] of each class i. */
+int ctl_stats_kernels(ctl_context* ctx, double* ms, uint64_t* launches, double* work);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CTL_H */

@@ -1,0 +1,1522 @@
+// C-ABI of the ctl library: contexts, keys, ciphertexts and the homomorphic operations
+// of CryptoTL's server step (ClassifyHE, Fig. alg:cryptotl; layers of Sec. 3.1).
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <cmath>
+#include <algorithm>
+#include <memory>
+#include <new>
+#include "ctl_internal.h"
+#include "modarith.cuh"
+
+using namespace ctl;
+
+// =====================================================================================
+// Errors, memory, timing
+// =====================================================================================
+static thread_local std::string g_last_error;
+
+namespace ctl {
+const char* kKernelClassName[KC_COUNT] = {"ntt_fwd", "ntt_inv", "modup_ntt", "key_ip",
+                                          "moddown_ntt", "rescale", "bsgs_inner", "elementwise"};
+
+void set_error(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+int cuda_check(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return CTL_OK;
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? CTL_ENOMEM : CTL_ECUDA;
+}
+void* dev_alloc(ctl_context* c, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  if (c->alloc_fn) {
+    p = c->alloc_fn(bytes, (void*)c->stream, c->alloc_user);
+  } else if (cudaMallocAsync(&p, bytes, c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  return p;
+}
+void dev_free(ctl_context* c, void* p) {
+  if (!p) return;
+  if (c->free_fn) c->free_fn(p, (void*)c->stream, c->alloc_user);
+  else cudaFreeAsync(p, c->stream);
+}
+void timing_begin(ctl_context* c, int, cudaEvent_t* ev) {
+  *ev = nullptr;
+  if (!c->timing.enabled) return;
+  cudaEvent_t e;
+  if (!c->timing.pool.empty()) {
+    e = c->timing.pool.back();
+    c->timing.pool.pop_back();
+  } else {
+    cudaEventCreate(&e);
+  }
+  cudaEventRecord(e, c->stream);
+  *ev = e;
+}
+void timing_end(ctl_context* c, int cls, cudaEvent_t ev, double work) {
+  if (!c->timing.enabled || !ev) return;
+  cudaEvent_t e;
+  if (!c->timing.pool.empty()) {
+    e = c->timing.pool.back();
+    c->timing.pool.pop_back();
+  } else {
+    cudaEventCreate(&e);
+  }
+  cudaEventRecord(e, c->stream);
+  c->timing.pending.push_back({cls, {ev, e}});
+  c->timing.launches[cls]++;
+  c->timing.work[cls] += work;
+}
+}  // namespace ctl
+
+namespace {
+
+// Device buffer released (stream-ordered) at scope exit.
+struct DBuf {
+  ctl_context* c = nullptr;
+  u64* p = nullptr;
+  DBuf() = default;
+  DBuf(ctl_context* cc, size_t words) : c(cc) { p = (u64*)dev_alloc(cc, words * sizeof(u64)); }
+  ~DBuf() {
+    if (p) dev_free(c, p);
+  }
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  u64* release() {
+    u64* r = p;
+    p = nullptr;
+    return r;
+  }
+};
+
+#define CHECK_ARG(cond, msg)      \
+  do {                            \
+    if (!(cond)) {                \
+      set_error("%s", msg);       \
+      return CTL_EINVAL;          \
+    }                             \
+  } while (0)
+#define CHECK_ALLOC(buf)                                 \
+  do {                                                   \
+    if (!(buf).p) {                                      \
+      set_error("device allocation failed");             \
+      return CTL_ENOMEM;                                 \
+    }                                                    \
+  } while (0)
+
+int last_cuda(const char* what) { return cuda_check(cudaGetLastError(), what); }
+
+size_t ct_words(const ctl_context* c, uint32_t lvl, uint32_t count) { return (size_t)count * 2 * lvl * c->N; }
+
+ctl_ct* new_ct(ctl_context* c, uint32_t lvl, uint32_t count, double scale) {
+  ctl_ct* ct = new (std::nothrow) ctl_ct();
+  if (!ct) return nullptr;
+  ct->ctx = c;
+  ct->level = lvl;
+  ct->count = count;
+  ct->scale = scale;
+  ct->bytes = ct_words(c, lvl, count) * sizeof(u64);
+  ct->d = (u64*)dev_alloc(c, ct->bytes);
+  if (!ct->d) {
+    delete ct;
+    return nullptr;
+  }
+  return ct;
+}
+
+// Scale agreement up to FP64 rounding of the bookkeeping.
+bool same_scale(double a, double b) { return std::fabs(a - b) <= 1e-9 * std::max(std::fabs(a), std::fabs(b)); }
+
+}  // namespace
+
+// =====================================================================================
+// Context
+// =====================================================================================
+extern "C" const char* ctl_last_error(void) { return g_last_error.c_str(); }
+extern "C" const char* ctl_version(void) { return "ctl 0.1 (sm_103a)"; }
+
+extern "C" int ctl_plan_primes(uint32_t N, const uint32_t* bits, uint32_t n, uint64_t* out) {
+  if (!bits || !out || n == 0) {
+    set_error("ctl_plan_primes: null argument");
+    return CTL_EINVAL;
+  }
+  std::vector<u64> ps;
+  if (N < 16 || (N & (N - 1)) || !plan_primes(N, std::vector<uint32_t>(bits, bits + n), ps)) {
+    set_error("ctl_plan_primes: invalid N or bit sizes");
+    return CTL_EINVAL;
+  }
+  for (uint32_t i = 0; i < n; i++) out[i] = ps[i];
+  return CTL_OK;
+}
+
+static int build_tables(ctl_context* c) {
+  const uint32_t N = c->N, L = c->L, K = c->K, LK = L + K;
+  const std::vector<u64>& m = c->moduli;
+  // per-prime constants and twiddles
+  std::vector<u64> tw((size_t)LK * N), tws((size_t)LK * N), itw((size_t)LK * N), itws((size_t)LK * N);
+  c->h_primes.resize(LK);
+  for (uint32_t i = 0; i < LK; i++) {
+    const u64 q = m[i];
+    const u64 psi = min_primitive_2n_root(q, N), psi_inv = h_invmod(psi, q);
+    for (uint32_t k = 0; k < N; k++) {
+      const uint32_t e = h_bitrev(k, c->logN);
+      const u64 w = h_powmod(psi, e, q), wi = h_powmod(psi_inv, e, q);
+      tw[(size_t)i * N + k] = w;
+      tws[(size_t)i * N + k] = h_shoup(w, q);
+      itw[(size_t)i * N + k] = wi;
+      itws[(size_t)i * N + k] = h_shoup(wi, q);
+    }
+    DPrime& P = c->h_primes[i];
+    P.q = q;
+    P.qinv = h_neg_inv64(q);
+    P.rmod = h_mont(1, q);
+    P.r2 = h_mulmod(P.rmod, P.rmod, q);
+    P.ninv = h_invmod(N % q, q);
+    P.ninv_sh = h_shoup(P.ninv, q);
+    P.iw1 = h_mulmod(itw[(size_t)i * N + 1], P.ninv, q);
+    P.iw1_sh = h_shoup(P.iw1, q);
+  }
+  // conversion tables, packed into one host vector then copied to the device
+  std::vector<u64> tab;
+  struct Pending {
+    size_t sinv, sinv_sh, sq, cmont;
+    int ns, nt;
+  };
+  std::vector<Pending> modup_p;
+  auto add_conv = [&](const std::vector<uint32_t>& src, const std::vector<uint32_t>& tgt) {
+    Pending pd;
+    pd.ns = (int)src.size();
+    pd.nt = (int)tgt.size();
+    pd.sinv = tab.size();
+    for (uint32_t sj : src) {
+      u64 qs = m[sj], prod = 1 % qs;
+      for (uint32_t so : src)
+        if (so != sj) prod = h_mulmod(prod, m[so] % qs, qs);
+      tab.push_back(h_invmod(prod, qs));
+    }
+    pd.sinv_sh = tab.size();
+    for (int j = 0; j < pd.ns; j++) tab.push_back(h_shoup(tab[pd.sinv + j], m[src[j]]));
+    pd.sq = tab.size();
+    for (uint32_t sj : src) tab.push_back(m[sj]);
+    pd.cmont = tab.size();
+    for (uint32_t sj : src) {
+      for (uint32_t ti : tgt) {
+        const u64 qt = m[ti];
+        u64 prod = 1 % qt;
+        for (uint32_t so : src)
+          if (so != sj) prod = h_mulmod(prod, m[so] % qt, qt);
+        tab.push_back(h_mont(prod, qt));
+      }
+    }
+    return pd;
+  };
+  for (uint32_t lvl = 1; lvl <= L; lvl++) {
+    for (uint32_t d = 0; d < c->beta; d++) {
+      std::vector<uint32_t> src, tgt;
+      for (uint32_t j = d * c->alpha; j < std::min((d + 1) * c->alpha, lvl); j++) src.push_back(j);
+      for (uint32_t i = 0; i < lvl + K; i++) tgt.push_back(prime_of_limb(i, lvl, L));
+      if (src.empty()) src.push_back(0);  // unused digit slot
+      modup_p.push_back(add_conv(src, tgt));
+    }
+  }
+  std::vector<uint32_t> sp, dp;
+  for (uint32_t j = 0; j < K; j++) sp.push_back(L + j);
+  for (uint32_t i = 0; i < L; i++) dp.push_back(i);
+  Pending md = add_conv(sp, dp);
+  const size_t pinv_off = tab.size();
+  for (uint32_t i = 0; i < L; i++) {
+    u64 P = 1;
+    for (uint32_t j = 0; j < K; j++) P = h_mulmod(P, m[L + j] % m[i], m[i]);
+    tab.push_back(h_invmod(P, m[i]));
+  }
+  const size_t pinvsh_off = tab.size();
+  for (uint32_t i = 0; i < L; i++) tab.push_back(h_shoup(tab[pinv_off + i], m[i]));
+  std::vector<size_t> rs_off(L + 1, 0);
+  for (uint32_t lvl = 2; lvl <= L; lvl++) {
+    const u64 ql = m[lvl - 1];
+    rs_off[lvl] = tab.size();
+    for (uint32_t i = 0; i + 1 < lvl; i++) tab.push_back(h_invmod(ql % m[i], m[i]));
+    for (uint32_t i = 0; i + 1 < lvl; i++) tab.push_back(h_shoup(tab[rs_off[lvl] + i], m[i]));
+    for (uint32_t i = 0; i + 1 < lvl; i++) tab.push_back((ql / 2) % m[i]);
+  }
+  // device copies
+  const size_t twb = (size_t)LK * N * sizeof(u64);
+  int rc;
+  if ((rc = cuda_check(cudaMalloc(&c->d_primes, LK * sizeof(DPrime)), "cudaMalloc primes"))) return rc;
+  if ((rc = cuda_check(cudaMalloc(&c->d_tw, 4 * twb), "cudaMalloc twiddles"))) return rc;
+  c->d_tw_sh = c->d_tw + (size_t)LK * N;
+  c->d_itw = c->d_tw_sh + (size_t)LK * N;
+  c->d_itw_sh = c->d_itw + (size_t)LK * N;
+  if ((rc = cuda_check(cudaMalloc(&c->d_tables, tab.size() * sizeof(u64)), "cudaMalloc tables"))) return rc;
+  cudaMemcpy(c->d_primes, c->h_primes.data(), LK * sizeof(DPrime), cudaMemcpyHostToDevice);
+  cudaMemcpy(c->d_tw, tw.data(), twb, cudaMemcpyHostToDevice);
+  cudaMemcpy(c->d_tw_sh, tws.data(), twb, cudaMemcpyHostToDevice);
+  cudaMemcpy(c->d_itw, itw.data(), twb, cudaMemcpyHostToDevice);
+  cudaMemcpy(c->d_itw_sh, itws.data(), twb, cudaMemcpyHostToDevice);
+  cudaMemcpy(c->d_tables, tab.data(), tab.size() * sizeof(u64), cudaMemcpyHostToDevice);
+  auto mk = [&](const Pending& p) {
+    ConvTab t;
+    t.ns = p.ns;
+    t.nt = p.nt;
+    t.sinv = c->d_tables + p.sinv;
+    t.sinv_sh = c->d_tables + p.sinv_sh;
+    t.sq = c->d_tables + p.sq;
+    t.cmont = c->d_tables + p.cmont;
+    return t;
+  };
+  for (auto& p : modup_p) c->modup_tabs.push_back(mk(p));
+  c->moddown.conv = mk(md);
+  c->moddown.pinv = c->d_tables + pinv_off;
+  c->moddown.pinv_sh = c->d_tables + pinvsh_off;
+  c->rescale_tabs.assign(L + 1, RescaleTab{});
+  for (uint32_t lvl = 2; lvl <= L; lvl++) {
+    RescaleTab& R = c->rescale_tabs[lvl];
+    R.inv = c->d_tables + rs_off[lvl];
+    R.inv_sh = R.inv + (lvl - 1);
+    R.hmod = R.inv_sh + (lvl - 1);
+    R.qlast = m[lvl - 1];
+    R.h = m[lvl - 1] / 2;
+  }
+  return cuda_check(cudaGetLastError(), "table upload");
+}
+
+extern "C" int ctl_context_create(ctl_context** out, uint32_t N, const uint32_t* q_bits, uint32_t n_q,
+                                  const uint32_t* p_bits, uint32_t n_p, uint32_t dnum, double scale, uint64_t seed) {
+  if (!out || !q_bits || !p_bits) {
+    set_error("ctl_context_create: null argument");
+    return CTL_EINVAL;
+  }
+  *out = nullptr;
+  if (N < 16 || N > 16384 || (N & (N - 1)) || n_q == 0 || n_p == 0 || n_p > 8 || dnum == 0 || dnum > n_q ||
+      !(scale > 1.0)) {
+    set_error("ctl_context_create: invalid parameters (N=%u n_q=%u n_p=%u dnum=%u)", N, n_q, n_p, dnum);
+    return CTL_EINVAL;
+  }
+  std::unique_ptr<ctl_context> c(new ctl_context());
+  c->N = N;
+  while ((1u << c->logN) < N) c->logN++;
+  c->L = n_q;
+  c->K = n_p;
+  c->alpha = (n_q + dnum - 1) / dnum;
+  c->beta = (n_q + c->alpha - 1) / c->alpha;
+  if (c->alpha > 8 || c->beta > 16) {
+    set_error("ctl_context_create: digit shape alpha=%u beta=%u unsupported", c->alpha, c->beta);
+    return CTL_ENOTSUP;
+  }
+  c->scale = scale;
+  c->seed = seed;
+  std::vector<uint32_t> bits(q_bits, q_bits + n_q);
+  bits.insert(bits.end(), p_bits, p_bits + n_p);
+  if (!plan_primes(N, bits, c->moduli)) {
+    set_error("ctl_context_create: no prime chain for these bit sizes");
+    return CTL_EINVAL;
+  }
+  int rc;
+  if ((rc = cuda_check(cudaGetDevice(&c->device), "cudaGetDevice"))) return rc;
+  cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
+  if ((rc = cuda_check(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking), "stream"))) return rc;
+  c->own_stream = true;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, c->device) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  c->enc.init(N);
+  if ((rc = build_tables(c.get()))) return rc;
+  *out = c.release();
+  return CTL_OK;
+}
+
+extern "C" void ctl_context_destroy(ctl_context* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  for (auto& pe : c->timing.pending) {
+    cudaEventDestroy(pe.second.first);
+    cudaEventDestroy(pe.second.second);
+  }
+  for (auto e : c->timing.pool) cudaEventDestroy(e);
+  cudaFree(c->d_primes);
+  cudaFree(c->d_tw);
+  cudaFree(c->d_tables);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+extern "C" int ctl_context_info(const ctl_context* c, uint64_t* moduli, uint32_t* n_q, uint32_t* n_p,
+                                uint32_t* alpha) {
+  if (!c) {
+    set_error("ctl_context_info: null context");
+    return CTL_EINVAL;
+  }
+  if (moduli)
+    for (size_t i = 0; i < c->moduli.size(); i++) moduli[i] = c->moduli[i];
+  if (n_q) *n_q = c->L;
+  if (n_p) *n_p = c->K;
+  if (alpha) *alpha = c->alpha;
+  return CTL_OK;
+}
+
+extern "C" int ctl_set_stream(ctl_context* c, void* stream) {
+  if (!c) {
+    set_error("ctl_set_stream: null context");
+    return CTL_EINVAL;
+  }
+  if (stream) {
+    c->stream = (cudaStream_t)stream;
+  } else {
+    cudaStream_t s;
+    if (int rc = cuda_check(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "stream")) return rc;
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    c->stream = s;
+    c->own_stream = true;
+    return CTL_OK;
+  }
+  return CTL_OK;
+}
+
+extern "C" int ctl_set_allocator(ctl_context* c, ctl_alloc_fn a, ctl_free_fn f, void* user) {
+  if (!c || (!a) != (!f)) {
+    set_error("ctl_set_allocator: need both hooks or neither");
+    return CTL_EINVAL;
+  }
+  c->alloc_fn = a;
+  c->free_fn = f;
+  c->alloc_user = user;
+  return CTL_OK;
+}
+
+extern "C" int ctl_synchronize(ctl_context* c) {
+  if (!c) return CTL_EINVAL;
+  return cuda_check(cudaStreamSynchronize(c->stream), "synchronize");
+}
+
+extern "C" uint64_t ctl_galois_element(const ctl_context* c, int64_t r) {
+  const int64_t n = c->N / 2;
+  const int64_t rr = ((r % n) + n) % n;
+  return h_powmod(5, (u64)rr, 2ull * c->N);
+}
+
+// =====================================================================================
+// Keys
+// =====================================================================================
+namespace {
+
+// Pointwise product of two plain NTT-form polys over all L+K primes (s * s).
+__global__ void k_pointwise_sq(const u64* __restrict__ a, u64* __restrict__ o, const DPrime* __restrict__ pr,
+                               int logN, size_t total) {
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const DPrime P = pr[idx >> logN];
+    o[idx] = mulmod_plain(a[idx], a[idx], P.q, P.qinv, P.r2);
+  }
+}
+
+int gen_key(ctl_context* c, ctl_keys* k, u64 seed, u64 key_id, const u64* sp_ntt) {
+  const uint32_t N = c->N, L = c->L, LK = c->L + c->K, beta = c->beta;
+  const size_t kw = (size_t)beta * 2 * LK * N;
+  std::vector<u64> host(kw, 0);
+  std::vector<i64> e((size_t)beta * N);
+  for (uint32_t d = 0; d < beta; d++) {
+    SplitMixStream se(seed, stream_id_key_e(key_id, d));
+    draw_cbd21(se, N, &e[(size_t)d * N]);
+    for (uint32_t i = 0; i < LK; i++) {
+      SplitMixStream sa(seed, stream_id_key_a(key_id, d, i));
+      draw_uniform(sa, c->moduli[i], N, &host[(((size_t)d * 2 + 1) * LK + i) * N]);
+    }
+  }
+  DBuf key(c, kw), ed(c, (size_t)beta * N), e_res(c, (size_t)beta * LK * N), pmod(c, LK);
+  if (!key.p || !ed.p || !e_res.p || !pmod.p) {
+    set_error("keygen: device allocation failed");
+    return CTL_ENOMEM;
+  }
+  std::vector<u64> pm(LK, 0);
+  for (uint32_t i = 0; i < L; i++) {
+    u64 P = 1;
+    for (uint32_t j = 0; j < c->K; j++) P = h_mulmod(P, c->moduli[L + j] % c->moduli[i], c->moduli[i]);
+    pm[i] = P;
+  }
+  cudaMemcpyAsync(key.p, host.data(), kw * sizeof(u64), cudaMemcpyHostToDevice, c->stream);
+  cudaMemcpyAsync(ed.p, e.data(), e.size() * sizeof(u64), cudaMemcpyHostToDevice, c->stream);
+  cudaMemcpyAsync(pmod.p, pm.data(), LK * sizeof(u64), cudaMemcpyHostToDevice, c->stream);
+  // a -> NTT (poly 1 of every digit), e -> residues -> NTT
+  launch_ntt_fwd(c, key.p + (size_t)LK * N, (size_t)2 * LK * N, (int)beta, 0, (int)LK, (int)L);
+  launch_from_signed(c, (const i64*)ed.p, e_res.p, (int)beta, (int)LK, (int)L, N, (size_t)LK * N);
+  launch_ntt_fwd(c, e_res.p, (size_t)LK * N, (int)beta, 0, (int)LK, (int)L);
+  launch_keygen_combine(c, key.p, k->d_s, e_res.p, sp_ntt, (int)beta, (int)c->alpha, pmod.p);
+  if (int rc = last_cuda("keygen")) return rc;
+  // keep host vectors alive until the copies are done
+  if (int rc = cuda_check(cudaStreamSynchronize(c->stream), "keygen sync")) return rc;
+  k->evk[key_id] = key.release();
+  k->key_bytes += kw * sizeof(u64);
+  return CTL_OK;
+}
+
+}  // namespace
+
+extern "C" int ctl_keygen(ctl_context* c, const int32_t* rot, uint32_t n_rot, uint64_t seed, ctl_keys** out) {
+  if (!c || !out || (n_rot && !rot)) {
+    set_error("ctl_keygen: null argument");
+    return CTL_EINVAL;
+  }
+  *out = nullptr;
+  const uint32_t N = c->N, LK = c->L + c->K;
+  std::unique_ptr<ctl_keys> k(new ctl_keys());
+  k->ctx = c;
+  k->s.resize(N);
+  SplitMixStream ss(seed, stream_id_secret());
+  draw_ternary(ss, N, k->s.data());
+  DBuf sraw(c, N), sq(c, (size_t)LK * N), sg(c, (size_t)LK * N);
+  k->d_s = (u64*)dev_alloc(c, (size_t)LK * N * sizeof(u64));
+  if (!sraw.p || !sq.p || !sg.p || !k->d_s) {
+    set_error("keygen: device allocation failed");
+    return CTL_ENOMEM;
+  }
+  cudaMemcpyAsync(sraw.p, k->s.data(), N * sizeof(u64), cudaMemcpyHostToDevice, c->stream);
+  launch_from_signed(c, (const i64*)sraw.p, k->d_s, 1, (int)LK, (int)c->L, N, (size_t)LK * N);
+  launch_ntt_fwd(c, k->d_s, (size_t)LK * N, 1, 0, (int)LK, (int)c->L);
+  {
+    size_t total = (size_t)LK * N;
+    k_pointwise_sq<<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(k->d_s, sq.p, c->d_primes, (int)c->logN,
+                                                                           total);
+    c->launch_count++;
+  }
+  int rc = gen_key(c, k.get(), seed, 0, sq.p);
+  if (rc) return rc;
+  for (uint32_t i = 0; i < n_rot; i++) {
+    const u64 g = ctl_galois_element(c, rot[i]);
+    if (g == 1 || k->evk.count(g)) continue;
+    launch_automorph(c, k->d_s, sg.p, 1, (int)LK, (int)c->L, (size_t)LK * N, g);
+    if ((rc = gen_key(c, k.get(), seed, g, sg.p))) {
+      for (auto& kv : k->evk) dev_free(c, kv.second);
+      return rc;
+    }
+  }
+  if ((rc = cuda_check(cudaStreamSynchronize(c->stream), "keygen"))) return rc;
+  *out = k.release();
+  return CTL_OK;
+}
+
+extern "C" void ctl_keys_destroy(ctl_keys* k) {
+  if (!k) return;
+  ctl_context* c = k->ctx;
+  cudaStreamSynchronize(c->stream);
+  for (auto& kv : k->evk) dev_free(c, kv.second);
+  dev_free(c, k->d_s);
+  cudaStreamSynchronize(c->stream);
+  delete k;
+}
+
+extern "C" int ctl_keys_export(const ctl_keys* k, uint64_t key_id, uint64_t* out, size_t cap) {
+  if (!k || !out) {
+    set_error("ctl_keys_export: null argument");
+    return CTL_EINVAL;
+  }
+  ctl_context* c = k->ctx;
+  auto it = k->evk.find(key_id);
+  if (it == k->evk.end()) {
+    set_error("ctl_keys_export: no key %llu", (unsigned long long)key_id);
+    return CTL_EKEY;
+  }
+  const uint32_t N = c->N, LK = c->L + c->K;
+  const size_t kw = (size_t)c->beta * 2 * LK * N;
+  if (cap < kw) {
+    set_error("ctl_keys_export: capacity %zu < %zu", cap, kw);
+    return CTL_EINVAL;
+  }
+  DBuf tmp(c, kw);
+  CHECK_ALLOC(tmp);
+  cudaMemcpyAsync(tmp.p, it->second, kw * sizeof(u64), cudaMemcpyDeviceToDevice, c->stream);
+  launch_to_mont(c, tmp.p, (int)(2 * c->beta), (int)LK, (int)c->L, (size_t)LK * N, false);
+  launch_ntt_inv(c, tmp.p, (size_t)LK * N, (int)(2 * c->beta), 0, (int)LK, (int)c->L);
+  cudaMemcpyAsync(out, tmp.p, kw * sizeof(u64), cudaMemcpyDeviceToHost, c->stream);
+  return cuda_check(cudaStreamSynchronize(c->stream), "key export");
+}
+
+// =====================================================================================
+// Encoding, encryption, decryption
+// =====================================================================================
+extern "C" int ctl_encode(ctl_context* c, const double* x, size_t n, double scale, int64_t* m) {
+  if (!c || !m || (n && !x) || n > c->N / 2 || !(scale > 0)) {
+    set_error("ctl_encode: invalid argument");
+    return CTL_EINVAL;
+  }
+  if (!c->enc.encode(x, n, scale, (i64*)m)) {
+    set_error("ctl_encode: coefficient overflow (scale too large)");
+    return CTL_EINVAL;
+  }
+  return CTL_OK;
+}
+
+extern "C" int ctl_decode(ctl_context* c, const double* m, size_t n, double scale, double* y) {
+  if (!c || !m || !y || n > c->N / 2) {
+    set_error("ctl_decode: invalid argument");
+    return CTL_EINVAL;
+  }
+  c->enc.decode(m, n, scale, y);
+  return CTL_OK;
+}
+
+extern "C" int ctl_encrypt_coeffs(ctl_context* c, const ctl_keys* k, const int64_t* m, uint64_t seed, ctl_ct** out) {
+  if (!c || !k || !m || !out) {
+    set_error("ctl_encrypt_coeffs: null argument");
+    return CTL_EINVAL;
+  }
+  *out = nullptr;
+  const uint32_t N = c->N, L = c->L;
+  std::vector<u64> a((size_t)L * N);
+  for (uint32_t i = 0; i < L; i++) {
+    SplitMixStream sa(seed, stream_id_enc_a(i));
+    draw_uniform(sa, c->moduli[i], N, &a[(size_t)i * N]);
+  }
+  std::vector<i64> me(N);
+  SplitMixStream se(seed, stream_id_enc_e());
+  draw_cbd21(se, N, me.data());
+  for (uint32_t j = 0; j < N; j++) {
+    if (m[j] > (int64_t)4e18 || m[j] < -(int64_t)4e18) {
+      set_error("ctl_encrypt_coeffs: coefficient out of range");
+      return CTL_EINVAL;
+    }
+    me[j] += m[j];
+  }
+  ctl_ct* ct = new_ct(c, L, 1, c->scale);
+  DBuf raw(c, N), mer(c, (size_t)L * N);
+  if (!ct || !raw.p || !mer.p) {
+    if (ct) ctl_ct_destroy(ct);
+    set_error("ctl_encrypt: allocation failed");
+    return CTL_ENOMEM;
+  }
+  cudaMemcpyAsync(ct->d + (size_t)L * N, a.data(), a.size() * sizeof(u64), cudaMemcpyHostToDevice, c->stream);
+  cudaMemcpyAsync(raw.p, me.data(), N * sizeof(u64), cudaMemcpyHostToDevice, c->stream);
+  launch_ntt_fwd(c, ct->d + (size_t)L * N, (size_t)L * N, 1, 0, (int)L, (int)L);
+  launch_from_signed(c, (const i64*)raw.p, mer.p, 1, (int)L, (int)L, N, (size_t)L * N);
+  launch_ntt_fwd(c, mer.p, (size_t)L * N, 1, 0, (int)L, (int)L);
+  launch_encrypt_combine(c, ct->d, k->d_s, mer.p, (int)L);
+  int rc = cuda_check(cudaStreamSynchronize(c->stream), "encrypt");
+  if (rc) {
+    ctl_ct_destroy(ct);
+    return rc;
+  }
+  *out = ct;
+  return CTL_OK;
+}
+
+extern "C" int ctl_encrypt(ctl_context* c, const ctl_keys* k, const double* x, size_t n, uint64_t seed, ctl_ct** out) {
+  if (!c || !k || !out || (n && !x) || n > c->N / 2) {
+    set_error("ctl_encrypt: invalid argument");
+    return CTL_EINVAL;
+  }
+  std::vector<i64> m(c->N);
+  if (!c->enc.encode(x, n, c->scale, m.data())) {
+    set_error("ctl_encrypt: coefficient overflow");
+    return CTL_EINVAL;
+  }
+  return ctl_encrypt_coeffs(c, k, (const int64_t*)m.data(), seed, out);
+}
+
+extern "C" int ctl_decrypt_coeffs(ctl_context* c, const ctl_keys* k, const ctl_ct* ct, double* m) {
+  if (!c || !k || !ct || !m) {
+    set_error("ctl_decrypt_coeffs: null argument");
+    return CTL_EINVAL;
+  }
+  const uint32_t N = c->N, lvl = ct->level;
+  DBuf t(c, (size_t)lvl * N);
+  CHECK_ALLOC(t);
+  launch_decrypt_mul(c, ct->d, k->d_s, t.p, 1, (int)lvl);
+  launch_ntt_inv(c, t.p, (size_t)lvl * N, 1, 0, (int)lvl, (int)lvl);
+  std::vector<u64> h((size_t)lvl * N);
+  cudaMemcpyAsync(h.data(), t.p, h.size() * sizeof(u64), cudaMemcpyDeviceToHost, c->stream);
+  if (int rc = cuda_check(cudaStreamSynchronize(c->stream), "decrypt")) return rc;
+  crt_centred_to_double(h.data(), N, lvl, c->moduli.data(), N, m);
+  return CTL_OK;
+}
+
+extern "C" int ctl_decrypt(ctl_context* c, const ctl_keys* k, const ctl_ct* ct, double* y, size_t n) {
+  if (!c || !k || !ct || !y || n > c->N / 2) {
+    set_error("ctl_decrypt: invalid argument");
+    return CTL_EINVAL;
+  }
+  std::vector<double> m(c->N);
+  if (int rc = ctl_decrypt_coeffs(c, k, ct, m.data())) return rc;
+  c->enc.decode(m.data(), n, ct->scale, y);
+  return CTL_OK;
+}
+
+// =====================================================================================
+// Ciphertext handles
+// =====================================================================================
+static int import_common(ctl_context* c, const uint64_t* src, bool dev, uint32_t count, uint32_t level, double scale,
+                         ctl_ct** out) {
+  if (!c || !src || !out || count == 0 || level == 0 || level > c->L || !(scale > 0)) {
+    set_error("ctl_ct_import: invalid argument");
+    return CTL_EINVAL;
+  }
+  *out = nullptr;
+  ctl_ct* ct = new_ct(c, level, count, scale);
+  if (!ct) {
+    set_error("ctl_ct_import: allocation failed");
+    return CTL_ENOMEM;
+  }
+  cudaMemcpyAsync(ct->d, src, ct->bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
+  launch_ntt_fwd(c, ct->d, (size_t)level * c->N, (int)(2 * count), 0, (int)level, (int)level);
+  if (int rc = last_cuda("import")) {
+    ctl_ct_destroy(ct);
+    return rc;
+  }
+  *out = ct;
+  return CTL_OK;
+}
+extern "C" int ctl_ct_import(ctl_context* c, const uint64_t* coeffs, uint32_t count, uint32_t level, double scale,
+                             ctl_ct** out) {
+  return import_common(c, coeffs, false, count, level, scale, out);
+}
+extern "C" int ctl_ct_import_dev(ctl_context* c, const uint64_t* coeffs, uint32_t count, uint32_t level, double scale,
+                                 ctl_ct** out) {
+  return import_common(c, coeffs, true, count, level, scale, out);
+}
+
+static int export_common(const ctl_ct* ct, uint64_t* dst, size_t cap, bool dev) {
+  if (!ct || !dst) {
+    set_error("ctl_ct_export: null argument");
+    return CTL_EINVAL;
+  }
+  ctl_context* c = ct->ctx;
+  const size_t w = ct_words(c, ct->level, ct->count);
+  if (cap < w) {
+    set_error("ctl_ct_export: capacity %zu < %zu", cap, w);
+    return CTL_EINVAL;
+  }
+  if (dev) {
+    launch_ntt_inv_oop(c, ct->d, (size_t)ct->level * c->N, (u64*)dst, (size_t)ct->level * c->N, (int)(2 * ct->count),
+                       0, (int)ct->level, (int)ct->level);
+    return last_cuda("export");
+  }
+  DBuf t(c, w);
+  CHECK_ALLOC(t);
+  launch_ntt_inv_oop(c, ct->d, (size_t)ct->level * c->N, t.p, (size_t)ct->level * c->N, (int)(2 * ct->count), 0,
+                     (int)ct->level, (int)ct->level);
+  cudaMemcpyAsync(dst, t.p, w * sizeof(u64), cudaMemcpyDeviceToHost, c->stream);
+  return cuda_check(cudaStreamSynchronize(c->stream), "export");
+}
+extern "C" int ctl_ct_export(const ctl_ct* ct, uint64_t* coeffs, size_t cap) { return export_common(ct, coeffs, cap, false); }
+extern "C" int ctl_ct_export_dev(const ctl_ct* ct, uint64_t* coeffs, size_t cap) {
+  return export_common(ct, coeffs, cap, true);
+}
+
+extern "C" int ctl_ct_info(const ctl_ct* ct, uint32_t* level, uint32_t* count, double* scale) {
+  if (!ct) {
+    set_error("ctl_ct_info: null ciphertext");
+    return CTL_EINVAL;
+  }
+  if (level) *level = ct->level;
+  if (count) *count = ct->count;
+  if (scale) *scale = ct->scale;
+  return CTL_OK;
+}
+
+extern "C" int ctl_ct_concat(ctl_context* c, const ctl_ct* const* cts, size_t n, ctl_ct** out) {
+  if (!c || !cts || !out || n == 0) {
+    set_error("ctl_ct_concat: invalid argument");
+    return CTL_EINVAL;
+  }
+  *out = nullptr;
+  uint32_t total = 0;
+  for (size_t i = 0; i < n; i++) {
+    if (!cts[i] || cts[i]->level != cts[0]->level) {
+      set_error("ctl_ct_concat: level mismatch");
+      return CTL_ELEVEL;
+    }
+    if (!same_scale(cts[i]->scale, cts[0]->scale)) {
+      set_error("ctl_ct_concat: scale mismatch");
+      return CTL_ESCALE;
+    }
+    total += cts[i]->count;
+  }
+  ctl_ct* o = new_ct(c, cts[0]->level, total, cts[0]->scale);
+  if (!o) {
+    set_error("ctl_ct_concat: allocation failed");
+    return CTL_ENOMEM;
+  }
+  size_t off = 0;
+  for (size_t i = 0; i < n; i++) {
+    cudaMemcpyAsync((char*)o->d + off, cts[i]->d, cts[i]->bytes, cudaMemcpyDeviceToDevice, c->stream);
+    off += cts[i]->bytes;
+  }
+  *out = o;
+  return last_cuda("concat");
+}
+
+extern "C" int ctl_ct_slice(const ctl_ct* b, uint32_t i, ctl_ct** out) {
+  if (!b || !out || i >= b->count) {
+    set_error("ctl_ct_slice: invalid argument");
+    return CTL_EINVAL;
+  }
+  ctl_context* c = b->ctx;
+  ctl_ct* o = new_ct(c, b->level, 1, b->scale);
+  if (!o) {
+    set_error("ctl_ct_slice: allocation failed");
+    return CTL_ENOMEM;
+  }
+  cudaMemcpyAsync(o->d, (const char*)b->d + (size_t)i * o->bytes, o->bytes, cudaMemcpyDeviceToDevice, c->stream);
+  *out = o;
+  return last_cuda("slice");
+}
+
+extern "C" void ctl_ct_destroy(ctl_ct* ct) {
+  if (!ct) return;
+  dev_free(ct->ctx, ct->d);
+  delete ct;
+}
+
+// =====================================================================================
+// Key switching core (hybrid: ModUp -> [sigma_g] -> key product -> ModDown)
+// =====================================================================================
+namespace {
+
+// Key switch of the polys x_{r,b} (NTT form, level lvl; x_{r,b} = x + r*x_r + b*x_b with
+// x_r either 0 (one input shared by all rotations: hoisting) or nb*x_b) with the key and
+// Galois element of rotation r.  out [nr][nb][2][lvl][N].  The addend (nullable) is
+// added through sigma_g as described at launch_moddown_ntt.
+int keyswitch(ctl_context* c, int nr, int nb, int lvl, const u64* x, size_t x_r, size_t x_b,
+              const std::vector<const u64*>& keys, const std::vector<u64>& gs, const u64* addend, size_t add_r,
+              size_t add_b, size_t add_p, bool add_both, u64* out) {
+  const uint32_t N = c->N;
+  const int nd = (lvl + (int)c->alpha - 1) / (int)c->alpha;
+  const int E = lvl + (int)c->K;
+  const bool hoisted = (x_r == 0);
+  const int n_in = hoisted ? nb : nr * nb;
+  if (nr > CTL_MAX_ROT) {
+    set_error("keyswitch: at most %d rotations per launch", CTL_MAX_ROT);
+    return CTL_EINVAL;
+  }
+  DBuf xc(c, (size_t)n_in * lvl * N), ext(c, (size_t)n_in * nd * E * N), acc(c, (size_t)nr * nb * 2 * E * N);
+  if (!xc.p || !ext.p || !acc.p) {
+    set_error("keyswitch: device allocation failed");
+    return CTL_ENOMEM;
+  }
+  RotList rl;
+  rl.n = nr;
+  for (int r = 0; r < CTL_MAX_ROT; r++) {
+    rl.key[r] = r < nr ? keys[r] : nullptr;
+    rl.g[r] = r < nr ? gs[r] : 1;
+  }
+  // 1. coefficient form of the inputs
+  launch_ntt_inv_oop(c, x, x_b, xc.p, (size_t)lvl * N, n_in, 0, lvl, lvl);
+  // 2. ModUp + NTT of every digit
+  launch_modup_ntt(c, xc.p, (size_t)lvl * N, x, x_b, n_in, lvl, ext.p);
+  // 3. key inner products (automorphism folded into the gather)
+  launch_key_ip(c, ext.p, hoisted ? 0 : (size_t)nb * nd * E * N, nb, lvl, rl, acc.p);
+  // 4. ModDown: special limbs to coefficient form, then conversion + NTT + combine
+  launch_ntt_inv(c, acc.p, (size_t)E * N, nr * nb * 2, lvl, E, lvl);
+  launch_moddown_ntt(c, acc.p, nr, nb, lvl, out, addend, add_r, add_b, add_p, add_both, rl);
+  return last_cuda("keyswitch");
+}
+
+// Rotations of one ciphertext batch by several amounts (hoisted), chunked to bound memory.
+int rotate_many(ctl_context* c, const ctl_keys* k, const u64* in, int nb, int lvl, const std::vector<int64_t>& rots,
+                u64* out /*[nr][nb][2][lvl][N]*/) {
+  const uint32_t N = c->N;
+  const size_t ctw = (size_t)2 * lvl * N;
+  std::vector<const u64*> keys;
+  std::vector<u64> gs;
+  std::vector<int> idx;
+  for (size_t r = 0; r < rots.size(); r++) {
+    const u64 g = ctl_galois_element(c, rots[r]);
+    if (g == 1) {
+      cudaMemcpyAsync(out + r * nb * ctw, in, nb * ctw * sizeof(u64), cudaMemcpyDeviceToDevice, c->stream);
+      continue;
+    }
+    auto it = k->evk.find(g);
+    if (it == k->evk.end()) {
+      set_error("missing Galois key for rotation %lld", (long long)rots[r]);
+      return CTL_EKEY;
+    }
+    keys.push_back(it->second);
+    gs.push_back(g);
+    idx.push_back((int)r);
+  }
+  if (keys.empty()) return last_cuda("rotate");
+  // chunk so that the accumulators stay within ~4 GiB
+  const int E = lvl + (int)c->K;
+  const size_t acc_per_rot = (size_t)nb * 2 * E * N * sizeof(u64);
+  int chunk = (int)std::max<size_t>(1, ((size_t)4 << 30) / std::max<size_t>(acc_per_rot, 1));
+  chunk = std::min(chunk, CTL_MAX_ROT);
+  for (size_t s = 0; s < keys.size();) {
+    // consecutive output slots only (idx contiguous runs)
+    size_t e = s + 1;
+    while (e < keys.size() && (int)(e - s) < chunk && idx[e] == idx[e - 1] + 1) e++;
+    std::vector<const u64*> kk(keys.begin() + s, keys.begin() + e);
+    std::vector<u64> gg(gs.begin() + s, gs.begin() + e);
+    int rc = keyswitch(c, (int)(e - s), nb, lvl, in + (size_t)lvl * N, 0, ctw, kk, gg, in, 0, ctw, 0, false,
+                       out + (size_t)idx[s] * nb * ctw);
+    if (rc) return rc;
+    c->op_rot += (e - s) * nb;
+    s = e;
+  }
+  return CTL_OK;
+}
+
+int rescale_into(ctl_context* c, const u64* in, int nb, int lvl, u64* out) {
+  const uint32_t N = c->N;
+  DBuf r(c, (size_t)nb * 2 * N);
+  CHECK_ALLOC(r);
+  launch_intt_rescale_last(c, in, (size_t)lvl * N, nb * 2, lvl, r.p);
+  launch_rescale_ntt(c, r.p, in, (size_t)lvl * N, out, (size_t)(lvl - 1) * N, nb * 2, lvl);
+  c->op_rescale += nb;
+  return last_cuda("rescale");
+}
+
+}  // namespace
+
+// =====================================================================================
+// Homomorphic operations
+// =====================================================================================
+extern "C" int ctl_rotate(ctl_context* c, const ctl_keys* k, const ctl_ct* in, int32_t r, ctl_ct** out) {
+  if (!c || !k || !in || !out) {
+    set_error("ctl_rotate: null argument");
+    return CTL_EINVAL;
+  }
+  *out = nullptr;
+  ctl_ct* o = new_ct(c, in->level, in->count, in->scale);
+  if (!o) {
+    set_error("ctl_rotate: allocation failed");
+    return CTL_ENOMEM;
+  }
+  int rc = rotate_many(c, k, in->d, (int)in->count, (int)in->level, {r}, o->d);
+  if (rc) {
+    ctl_ct_destroy(o);
+    return rc;
+  }
+  *out = o;
+  return CTL_OK;
+}
+
+extern "C" int ctl_rescale(ctl_context* c, const ctl_ct* in, ctl_ct** out) {
+  if (!c || !in || !out) {
+    set_error("ctl_rescale: null argument");
+    return CTL_EINVAL;
+  }
+  *out = nullptr;
+  if (in->level < 2) {
+    set_error("ctl_rescale: no level left");
+    return CTL_ELEVEL;
+  }
+  ctl_ct* o = new_ct(c, in->level - 1, in->count, in->scale / (double)c->moduli[in->level - 1]);
+  if (!o) {
+    set_error("ctl_rescale: allocation failed");
+    return CTL_ENOMEM;
+  }
+  int rc = rescale_into(c, in->d, (int)in->count, (int)in->level, o->d);
+  if (rc) {
+    ctl_ct_destroy(o);
+    return rc;
+  }
+  *out = o;
+  return CTL_OK;
+}
+
+namespace {
+int square_into(ctl_context* c, const ctl_keys* k, const u64* in, int nb, int lvl, u64* out) {
+  const uint32_t N = c->N;
+  auto it = k->evk.find(0);
+  if (it == k->evk.end()) {
+    set_error("missing relinearisation key");
+    return CTL_EKEY;
+  }
+  const size_t LN = (size_t)lvl * N;
+  DBuf d(c, (size_t)nb * 3 * LN), r(c, (size_t)nb * 2 * LN);
+  if (!d.p || !r.p) {
+    set_error("square: allocation failed");
+    return CTL_ENOMEM;
+  }
+  launch_tensor_square(c, in, d.p, nb, lvl);
+  int rc = keyswitch(c, 1, nb, lvl, d.p + 2 * LN, 0, 3 * LN, {it->second}, {1}, d.p, 0, 3 * LN, LN, true, r.p);
+  if (rc) return rc;
+  c->op_relin += nb;
+  return rescale_into(c, r.p, nb, lvl, out);
+}
+}  // namespace
+
+extern "C" int ctl_eval_square(ctl_context* c, const ctl_keys* k, const ctl_ct* in, ctl_ct** out) {
+  if (!c || !k || !in || !out) {
+    set_error("ctl_eval_square: null argument");
+    return CTL_EINVAL;
+  }
+  *out = nullptr;
+  if (in->level < 2) {
+    set_error("ctl_eval_square: no level left");
+    return CTL_ELEVEL;
+  }
+  const double q = (double)c->moduli[in->level - 1];
+  ctl_ct* o = new_ct(c, in->level - 1, in->count, in->scale * in->scale / q);
+  if (!o) {
+    set_error("ctl_eval_square: allocation failed");
+    return CTL_ENOMEM;
+  }
+  int rc = square_into(c, k, in->d, (int)in->count, (int)in->level, o->d);
+  if (rc) {
+    ctl_ct_destroy(o);
+    return rc;
+  }
+  *out = o;
+  return CTL_OK;
+}
+
+extern "C" int ctl_add(ctl_context* c, const ctl_ct* a, const ctl_ct* b, ctl_ct** out) {
+  if (!c || !a || !b || !out) {
+    set_error("ctl_add: null argument");
+    return CTL_EINVAL;
+  }
+  *out = nullptr;
+  if (a->level != b->level || a->count != b->count) {
+    set_error("ctl_add: shape mismatch");
+    return CTL_ELEVEL;
+  }
+  if (!same_scale(a->scale, b->scale)) {
+    set_error("ctl_add: scale mismatch");
+    return CTL_ESCALE;
+  }
+  ctl_ct* o = new_ct(c, a->level, a->count, a->scale);
+  if (!o) {
+    set_error("ctl_add: allocation failed");
+    return CTL_ENOMEM;
+  }
+  const size_t LN = (size_t)a->level * c->N;
+  launch_add(c, a->d, b->d, o->d, (int)(2 * a->count), (int)a->level, LN, LN, LN);
+  c->op_add += a->count;
+  *out = o;
+  return last_cuda("add");
+}
+
+// =====================================================================================
+// Dense layer (Eq. bsgs) with pre-encoded diagonals
+// =====================================================================================
+struct DenseLayer {
+  uint32_t m = 0, n = 0, t = 0, t1 = 0, t2 = 0, lvl = 0;
+  double pt_scale = 0, in_scale = 0, out_scale = 0;
+  u64* diag = nullptr;   // [t][lvl][N] NTT + Montgomery form
+  u64* bias = nullptr;   // [lvl][N] NTT form (plain residues) or null
+};
+
+namespace {
+
+uint32_t bsgs_t(uint32_t m, uint32_t n) {
+  uint32_t t = 1;
+  while (t < m || t < n) t <<= 1;
+  return t;
+}
+uint32_t bsgs_t1(uint32_t t) {
+  uint32_t lg = 0;
+  while ((1u << lg) < t) lg++;
+  return 1u << ((lg + 1) / 2);
+}
+
+// Upload integer coefficient plaintexts [cnt][N] as NTT-form residues at level lvl.
+int upload_plaintexts(ctl_context* c, const i64* coeffs, uint32_t cnt, uint32_t lvl, bool mont, u64** out) {
+  const uint32_t N = c->N;
+  DBuf raw(c, (size_t)cnt * N);
+  u64* d = (u64*)dev_alloc(c, (size_t)cnt * lvl * N * sizeof(u64));
+  if (!raw.p || !d) {
+    if (d) dev_free(c, d);
+    set_error("plaintext upload: allocation failed");
+    return CTL_ENOMEM;
+  }
+  cudaMemcpyAsync(raw.p, coeffs, (size_t)cnt * N * sizeof(u64), cudaMemcpyHostToDevice, c->stream);
+  launch_from_signed(c, (const i64*)raw.p, d, (int)cnt, (int)lvl, (int)lvl, N, (size_t)lvl * N);
+  launch_ntt_fwd(c, d, (size_t)lvl * N, (int)cnt, 0, (int)lvl, (int)lvl);
+  if (mont) launch_to_mont(c, d, (int)cnt, (int)lvl, (int)lvl, (size_t)lvl * N, true);
+  int rc = cuda_check(cudaStreamSynchronize(c->stream), "plaintext upload");
+  if (rc) {
+    dev_free(c, d);
+    return rc;
+  }
+  *out = d;
+  return CTL_OK;
+}
+
+// Diagonals of W for Eq. (bsgs): diag_i[r] = W[r][(r+i) mod t] (zero padded),
+// diag'_i = rot_{-floor(i/t1)*t1}(diag_i), i.e. diag_i placed at slots [k*t1, k*t1 + t).
+int encode_diagonals(ctl_context* c, const double* W, uint32_t m, uint32_t n, double scale, std::vector<i64>& pts) {
+  const uint32_t t = bsgs_t(m, n), t1 = bsgs_t1(t), ns = c->N / 2;
+  pts.assign((size_t)t * c->N, 0);
+  std::vector<double> v(ns);
+  for (uint32_t i = 0; i < t; i++) {
+    std::fill(v.begin(), v.end(), 0.0);
+    const uint32_t sh = (i / t1) * t1;
+    for (uint32_t r = 0; r < t; r++) {
+      const uint32_t col = (r + i) % t;
+      v[r + sh] = (r < m && col < n) ? W[(size_t)r * n + col] : 0.0;
+    }
+    if (!c->enc.encode(v.data(), ns, scale, &pts[(size_t)i * c->N])) {
+      set_error("dense: diagonal encoding overflow");
+      return CTL_EINVAL;
+    }
+  }
+  return CTL_OK;
+}
+
+int dense_prepare(ctl_context* c, DenseLayer& D, const double* W, const double* bias, const int64_t* pts_in,
+                  const int64_t* bias_in, uint32_t m, uint32_t n, uint32_t t_given, uint32_t lvl, double in_scale,
+                  double pt_scale) {
+  D.m = m;
+  D.n = n;
+  D.t = pts_in ? t_given : bsgs_t(m, n);
+  D.t1 = bsgs_t1(D.t);
+  D.t2 = D.t / D.t1;
+  D.lvl = lvl;
+  D.in_scale = in_scale;
+  if (lvl < 2) {
+    set_error("dense: needs two live primes");
+    return CTL_ELEVEL;
+  }
+  if (2 * D.t > c->N / 2 || D.t == 0 || (D.t & (D.t - 1))) {
+    set_error("dense: t=%u does not fit N/2 slots with the [x, x] layout", D.t);
+    return CTL_EINVAL;
+  }
+  const double ql = (double)c->moduli[lvl - 1];
+  D.pt_scale = pt_scale > 0 ? pt_scale : ql * (c->scale / in_scale);
+  D.out_scale = pt_scale > 0 ? in_scale * pt_scale / ql : c->scale;
+  std::vector<i64> enc;
+  const i64* src = (const i64*)pts_in;
+  if (!src) {
+    if (int rc = encode_diagonals(c, W, m, n, D.pt_scale, enc)) return rc;
+    src = enc.data();
+  }
+  if (int rc = upload_plaintexts(c, src, D.t, lvl, true, &D.diag)) return rc;
+  std::vector<i64> benc;
+  const i64* bsrc = (const i64*)bias_in;
+  if (!bsrc && bias) {
+    std::vector<double> v(c->N / 2, 0.0);
+    for (uint32_t r = 0; r < m; r++) v[r] = bias[r];
+    benc.resize(c->N);
+    if (!c->enc.encode(v.data(), v.size(), in_scale * D.pt_scale, benc.data())) {
+      set_error("dense: bias encoding overflow");
+      return CTL_EINVAL;
+    }
+    bsrc = benc.data();
+  }
+  if (bsrc) {
+    if (int rc = upload_plaintexts(c, bsrc, 1, lvl, false, &D.bias)) return rc;
+  }
+  return CTL_OK;
+}
+
+void dense_release(ctl_context* c, DenseLayer& D) {
+  dev_free(c, D.diag);
+  dev_free(c, D.bias);
+  D.diag = D.bias = nullptr;
+}
+
+// out = rescale( sum_k rot_{k t1}( sum_j diag'_{k t1 + j} o rot_j(in) ) [+ bias] ), batch nb.
+int dense_apply(ctl_context* c, const ctl_keys* k, const DenseLayer& D, const u64* in, int nb, u64* out) {
+  const uint32_t N = c->N, lvl = D.lvl, t1 = D.t1, t2 = D.t2;
+  const size_t ctw = (size_t)2 * lvl * N, bw = ctw * nb;
+  DBuf baby(c, bw * t1), inner(c, bw * t2), acc(c, bw);
+  if (!baby.p || !inner.p || !acc.p) {
+    set_error("dense: allocation failed (batch %d)", nb);
+    return CTL_ENOMEM;
+  }
+  // baby steps rot_j(in), j = 0..t1-1 (hoisted: one ModUp shared by all)
+  std::vector<int64_t> rots;
+  for (uint32_t j = 0; j < t1; j++) rots.push_back(j);
+  if (int rc = rotate_many(c, k, in, nb, (int)lvl, rots, baby.p)) return rc;
+  // inner sums for all giant steps
+  launch_bsgs_inner(c, baby.p, D.diag, (size_t)lvl * N, inner.p, (int)t1, (int)t2, nb, (int)lvl);
+  c->op_ptmul += (uint64_t)D.t * nb;
+  c->op_add += (uint64_t)(D.t - 1) * nb;
+  // giant steps: rot_{k t1}(inner_k) for k >= 1, chunked, each with its own input
+  cudaMemcpyAsync(acc.p, inner.p, bw * sizeof(u64), cudaMemcpyDeviceToDevice, c->stream);
+  if (t2 > 1) {
+    const int E = (int)lvl + (int)c->K;
+    const int nd = ((int)lvl + (int)c->alpha - 1) / (int)c->alpha;
+    const size_t per = (size_t)nb * N * sizeof(u64) * ((size_t)2 * E + (size_t)nd * E + lvl + 2 * lvl);
+    const int chunk = (int)std::min<size_t>(CTL_MAX_ROT, std::max<size_t>(1, ((size_t)6 << 30) / std::max<size_t>(per, 1)));
+    DBuf rot(c, bw * std::min<uint32_t>(t2 - 1, (uint32_t)chunk));
+    CHECK_ALLOC(rot);
+    for (uint32_t k0 = 1; k0 < t2; k0 += chunk) {
+      const uint32_t k1 = std::min<uint32_t>(t2, k0 + chunk);
+      std::vector<const u64*> keys;
+      std::vector<u64> gs;
+      for (uint32_t kk = k0; kk < k1; kk++) {
+        const u64 g = ctl_galois_element(c, (int64_t)kk * t1);
+        auto it = k->evk.find(g);
+        if (it == k->evk.end()) {
+          set_error("dense: missing Galois key for rotation %u", kk * t1);
+          return CTL_EKEY;
+        }
+        keys.push_back(it->second);
+        gs.push_back(g);
+      }
+      const u64* src = inner.p + (size_t)k0 * bw;
+      int rc = keyswitch(c, (int)(k1 - k0), nb, (int)lvl, src + (size_t)lvl * N, bw, ctw, keys, gs, src, bw, ctw, 0,
+                         false, rot.p);
+      if (rc) return rc;
+      c->op_rot += (uint64_t)(k1 - k0) * nb;
+      for (uint32_t kk = k0; kk < k1; kk++)
+        launch_add(c, acc.p, rot.p + (size_t)(kk - k0) * bw, acc.p, nb * 2, (int)lvl, (size_t)lvl * N,
+                   (size_t)lvl * N, (size_t)lvl * N);
+    }
+  }
+  if (D.bias) launch_add_plain(c, acc.p, D.bias, nb, (int)lvl, ctw);
+  return rescale_into(c, acc.p, nb, (int)lvl, out);
+}
+
+}  // namespace
+
+static int dense_common(ctl_context* c, const ctl_keys* k, const ctl_ct* in, const double* W, const double* bias,
+                        const int64_t* pts, const int64_t* bias_c, uint32_t m, uint32_t n, uint32_t t, double pt_scale,
+                        ctl_ct** out) {
+  if (!c || !k || !in || !out) {
+    set_error("dense: null argument");
+    return CTL_EINVAL;
+  }
+  *out = nullptr;
+  DenseLayer D;
+  int rc = dense_prepare(c, D, W, bias, pts, bias_c, m, n, t, in->level, in->scale, pt_scale);
+  if (rc) {
+    dense_release(c, D);
+    return rc;
+  }
+  ctl_ct* o = new_ct(c, in->level - 1, in->count, D.out_scale);
+  if (!o) {
+    dense_release(c, D);
+    set_error("dense: allocation failed");
+    return CTL_ENOMEM;
+  }
+  rc = dense_apply(c, k, D, in->d, (int)in->count, o->d);
+  dense_release(c, D);
+  if (rc) {
+    ctl_ct_destroy(o);
+    return rc;
+  }
+  *out = o;
+  return CTL_OK;
+}
+
+extern "C" int ctl_eval_dense(ctl_context* c, const ctl_keys* k, const ctl_ct* in, const double* W, uint32_t m,
+                              uint32_t n, const double* bias, ctl_ct** out) {
+  if (!W || m == 0 || n == 0) {
+    set_error("ctl_eval_dense: invalid weights");
+    return CTL_EINVAL;
+  }
+  return dense_common(c, k, in, W, bias, nullptr, nullptr, m, n, 0, 0.0, out);
+}
+
+extern "C" int ctl_eval_dense_coeffs(ctl_context* c, const ctl_keys* k, const ctl_ct* in, const int64_t* pts,
+                                     uint32_t t, const int64_t* bias, double pt_scale, ctl_ct** out) {
+  if (!pts || t == 0 || !(pt_scale > 0)) {
+    set_error("ctl_eval_dense_coeffs: invalid plaintexts");
+    return CTL_EINVAL;
+  }
+  return dense_common(c, k, in, nullptr, nullptr, pts, bias, t, t, t, pt_scale, out);
+}
+
+extern "C" int ctl_replicate(ctl_context* c, const ctl_keys* k, const ctl_ct* in, uint32_t t, ctl_ct** out) {
+  if (!c || !k || !in || !out) {
+    set_error("ctl_replicate: null argument");
+    return CTL_EINVAL;
+  }
+  *out = nullptr;
+  ctl_ct* o = new_ct(c, in->level, in->count, in->scale);
+  if (!o) {
+    set_error("ctl_replicate: allocation failed");
+    return CTL_ENOMEM;
+  }
+  int rc = rotate_many(c, k, in->d, (int)in->count, (int)in->level, {-(int64_t)t}, o->d);
+  if (!rc) {
+    const size_t LN = (size_t)in->level * c->N;
+    launch_add(c, o->d, in->d, o->d, (int)(2 * in->count), (int)in->level, LN, LN, LN);
+    c->op_add += in->count;
+    rc = last_cuda("replicate");
+  }
+  if (rc) {
+    ctl_ct_destroy(o);
+    return rc;
+  }
+  *out = o;
+  return CTL_OK;
+}
+
+extern "C" int ctl_mul_plain_coeffs(ctl_context* c, const ctl_ct* in, const int64_t* pt, double pt_scale,
+                                    ctl_ct** out) {
+  if (!c || !in || !pt || !out || !(pt_scale > 0)) {
+    set_error("ctl_mul_plain_coeffs: invalid argument");
+    return CTL_EINVAL;
+  }
+  *out = nullptr;
+  u64* d = nullptr;
+  int rc = upload_plaintexts(c, (const i64*)pt, 1, in->level, true, &d);
+  if (rc) return rc;
+  ctl_ct* o = new_ct(c, in->level, in->count, in->scale * pt_scale);
+  if (!o) {
+    dev_free(c, d);
+    set_error("ctl_mul_plain_coeffs: allocation failed");
+    return CTL_ENOMEM;
+  }
+  const size_t LN = (size_t)in->level * c->N;
+  launch_mul_plain(c, in->d, d, o->d, (int)(2 * in->count), (int)in->level, LN, LN);
+  c->op_ptmul += in->count;
+  dev_free(c, d);
+  *out = o;
+  return last_cuda("mul_plain");
+}
+
+extern "C" int ctl_ntt_dev(ctl_context* c, const uint64_t* in, uint64_t* out, uint32_t n_polys, uint32_t limbs,
+                           int inverse) {
+  if (!c || !in || !out || limbs == 0 || limbs > c->L + c->K || n_polys == 0) {
+    set_error("ctl_ntt_dev: invalid argument");
+    return CTL_EINVAL;
+  }
+  const size_t stride = (size_t)limbs * c->N;
+  // prime of limb l is l: the (lvl = L, L = L) limb map is the identity on the chain
+  if (inverse) {
+    launch_ntt_inv_oop(c, (const u64*)in, stride, (u64*)out, stride, (int)n_polys, 0, (int)limbs, (int)c->L);
+  } else {
+    if (in != out) cudaMemcpyAsync(out, in, n_polys * stride * sizeof(u64), cudaMemcpyDeviceToDevice, c->stream);
+    launch_ntt_fwd(c, (u64*)out, stride, (int)n_polys, 0, (int)limbs, (int)c->L);
+  }
+  return last_cuda("ntt");
+}
+
+// =====================================================================================
+// Models (the frozen server layers M_S)
+// =====================================================================================
+struct LayerPlan {
+  int kind = 0;
+  DenseLayer dense;
+  uint32_t rep_t = 0;
+  uint32_t in_level = 0;
+  double in_scale = 0, out_scale = 0;
+};
+struct ctl_model {
+  ctl_context* ctx = nullptr;
+  std::vector<LayerPlan> layers;
+  uint32_t in_level = 0, out_level = 0;
+  double in_scale = 0, out_scale = 0;
+  std::vector<int32_t> rotations;
+  uint64_t bytes = 0;
+};
+
+extern "C" int ctl_model_create(ctl_context* c, const ctl_layer* layers, uint32_t n_layers, uint32_t in_level,
+                                double in_scale, ctl_model** out) {
+  if (!c || !layers || !out || n_layers == 0 || in_level == 0 || in_level > c->L || !(in_scale > 0)) {
+    set_error("ctl_model_create: invalid argument");
+    return CTL_EINVAL;
+  }
+  *out = nullptr;
+  std::unique_ptr<ctl_model> M(new ctl_model());
+  M->ctx = c;
+  M->in_level = in_level;
+  M->in_scale = in_scale;
+  uint32_t lvl = in_level;
+  double sc = in_scale;
+  std::vector<int32_t> rots;
+  auto fail = [&](int rc) {
+    for (auto& L : M->layers) dense_release(c, L.dense);
+    return rc;
+  };
+  for (uint32_t i = 0; i < n_layers; i++) {
+    const ctl_layer& ly = layers[i];
+    LayerPlan P;
+    P.kind = ly.kind;
+    P.in_level = lvl;
+    P.in_scale = sc;
+    if (ly.kind == CTL_LAYER_DENSE) {
+      if (ly.m == 0 || ly.n == 0 || (!ly.W && !ly.pt_coeffs)) {
+        set_error("ctl_model_create: dense layer %u needs W or coefficients", i);
+        return fail(CTL_EINVAL);
+      }
+      const uint32_t t = bsgs_t(ly.m, ly.n);
+      if (int rc = dense_prepare(c, P.dense, ly.W, ly.bias, ly.pt_coeffs, nullptr, ly.m, ly.n, t, lvl, sc, 0.0)) {
+        M->layers.push_back(P);
+        return fail(rc);
+      }
+      M->bytes += (uint64_t)P.dense.t * lvl * c->N * 8;
+      for (uint32_t j = 1; j < P.dense.t1; j++) rots.push_back((int32_t)j);
+      for (uint32_t k = 1; k < P.dense.t2; k++) rots.push_back((int32_t)(k * P.dense.t1));
+      sc = P.dense.out_scale;
+      lvl--;
+    } else if (ly.kind == CTL_LAYER_SQUARE) {
+      if (lvl < 2) {
+        set_error("ctl_model_create: no level left for square layer %u", i);
+        return fail(CTL_ELEVEL);
+      }
+      sc = sc * sc / (double)c->moduli[lvl - 1];
+      lvl--;
+    } else if (ly.kind == CTL_LAYER_REPLICATE) {
+      if (ly.rep_t == 0 || 2 * ly.rep_t > c->N / 2) {
+        set_error("ctl_model_create: invalid replicate shift");
+        return fail(CTL_EINVAL);
+      }
+      P.rep_t = ly.rep_t;
+      rots.push_back(-(int32_t)ly.rep_t);
+    } else {
+      set_error("ctl_model_create: unknown layer kind %d", ly.kind);
+      return fail(CTL_EINVAL);
+    }
+    P.out_scale = sc;
+    M->layers.push_back(P);
+  }
+  std::sort(rots.begin(), rots.end());
+  rots.erase(std::unique(rots.begin(), rots.end()), rots.end());
+  M->rotations = rots;
+  M->out_level = lvl;
+  M->out_scale = sc;
+  *out = M.release();
+  return CTL_OK;
+}
+
+extern "C" void ctl_model_destroy(ctl_model* M) {
+  if (!M) return;
+  for (auto& L : M->layers) dense_release(M->ctx, L.dense);
+  cudaStreamSynchronize(M->ctx->stream);
+  delete M;
+}
+
+extern "C" int ctl_model_rotations(const ctl_model* M, int32_t* rot, uint32_t cap, uint32_t* n_rot) {
+  if (!M || !n_rot) {
+    set_error("ctl_model_rotations: null argument");
+    return CTL_EINVAL;
+  }
+  *n_rot = (uint32_t)M->rotations.size();
+  if (rot)
+    for (uint32_t i = 0; i < cap && i < M->rotations.size(); i++) rot[i] = M->rotations[i];
+  return CTL_OK;
+}
+
+extern "C" int ctl_model_info(const ctl_model* M, uint32_t* out_level, double* out_scale, uint64_t* bytes) {
+  if (!M) {
+    set_error("ctl_model_info: null model");
+    return CTL_EINVAL;
+  }
+  if (out_level) *out_level = M->out_level;
+  if (out_scale) *out_scale = M->out_scale;
+  if (bytes) *bytes = M->bytes;
+  return CTL_OK;
+}
+
+extern "C" int ctl_model_forward(ctl_context* c, const ctl_model* M, const ctl_keys* k, const ctl_ct* in,
+                                 ctl_ct** out) {
+  if (!c || !M || !k || !in || !out) {
+    set_error("ctl_model_forward: null argument");
+    return CTL_EINVAL;
+  }
+  *out = nullptr;
+  if (in->level != M->in_level) {
+    set_error("ctl_model_forward: input level %u, model expects %u", in->level, M->in_level);
+    return CTL_ELEVEL;
+  }
+  if (!same_scale(in->scale, M->in_scale)) {
+    set_error("ctl_model_forward: input scale mismatch");
+    return CTL_ESCALE;
+  }
+  const int nb = (int)in->count;
+  const uint32_t N = c->N;
+  // ping-pong buffers sized for the input level
+  DBuf a(c, ct_words(c, in->level, in->count)), b(c, ct_words(c, in->level, in->count));
+  if (!a.p || !b.p) {
+    set_error("ctl_model_forward: allocation failed");
+    return CTL_ENOMEM;
+  }
+  const u64* cur = in->d;
+  u64* bufs[2] = {a.p, b.p};
+  int w = 0;
+  uint32_t lvl = in->level;
+  for (const LayerPlan& P : M->layers) {
+    u64* dst = bufs[w];
+    int rc = CTL_OK;
+    if (P.kind == CTL_LAYER_DENSE) {
+      rc = dense_apply(c, k, P.dense, cur, nb, dst);
+      lvl--;
+    } else if (P.kind == CTL_LAYER_SQUARE) {
+      rc = square_into(c, k, cur, nb, (int)lvl, dst);
+      lvl--;
+    } else {
+      rc = rotate_many(c, k, cur, nb, (int)lvl, {-(int64_t)P.rep_t}, dst);
+      if (!rc) {
+        const size_t LN = (size_t)lvl * N;
+        launch_add(c, dst, cur, dst, nb * 2, (int)lvl, LN, LN, LN);
+        c->op_add += nb;
+      }
+    }
+    if (rc) return rc;
+    cur = dst;
+    w ^= 1;
+  }
+  ctl_ct* o = new_ct(c, lvl, in->count, M->out_scale);
+  if (!o) {
+    set_error("ctl_model_forward: allocation failed");
+    return CTL_ENOMEM;
+  }
+  cudaMemcpyAsync(o->d, cur, o->bytes, cudaMemcpyDeviceToDevice, c->stream);
+  if (int rc = last_cuda("model forward")) {
+    ctl_ct_destroy(o);
+    return rc;
+  }
+  *out = o;
+  return CTL_OK;
+}
+
+// =====================================================================================
+// Statistics
+// =====================================================================================
+extern "C" int ctl_stats_reset(ctl_context* c) {
+  if (!c) return CTL_EINVAL;
+  cudaStreamSynchronize(c->stream);
+  for (auto& pe : c->timing.pending) {
+    c->timing.pool.push_back(pe.second.first);
+    c->timing.pool.push_back(pe.second.second);
+  }
+  c->timing.pending.clear();
+  for (int i = 0; i < KC_COUNT; i++) {
+    c->timing.ms[i] = 0;
+    c->timing.launches[i] = 0;
+    c->timing.work[i] = 0;
+  }
+  c->launch_count = 0;
+  c->op_rot = c->op_ptmul = c->op_add = c->op_relin = c->op_rescale = 0;
+  return CTL_OK;
+}
+extern "C" int ctl_stats_enable_timing(ctl_context* c, int enable) {
+  if (!c) return CTL_EINVAL;
+  c->timing.enabled = enable != 0;
+  return CTL_OK;
+}
+extern "C" uint64_t ctl_stats_launches(const ctl_context* c) { return c ? c->launch_count.load() : 0; }
+extern "C" int ctl_stats_ops(const ctl_context* c, uint64_t* o) {
+  if (!c || !o) return CTL_EINVAL;
+  o[0] = c->op_rot;
+  o[1] = c->op_ptmul;
+  o[2] = c->op_add;
+  o[3] = c->op_relin;
+  o[4] = c->op_rescale;
+  return CTL_OK;
+}
+extern "C" int ctl_stats_kernel_classes(void) { return KC_COUNT; }
+extern "C" const char* ctl_stats_class_name(int i) { return (i >= 0 && i < KC_COUNT) ? kKernelClassName[i] : ""; }
+extern "C" int ctl_stats_kernels(ctl_context* c, double* ms, uint64_t* launches, double* work) {
+  if (!c) return CTL_EINVAL;
+  if (int rc = cuda_check(cudaStreamSynchronize(c->stream), "stats")) return rc;
+  for (auto& pe : c->timing.pending) {
+    float t = 0;
+    cudaEventElapsedTime(&t, pe.second.first, pe.second.second);
+    c->timing.ms[pe.first] += t;
+    c->timing.pool.push_back(pe.second.first);
+    c->timing.pool.push_back(pe.second.second);
+  }
+  c->timing.pending.clear();
+  for (int i = 0; i < KC_COUNT; i++) {
+    if (ms) ms[i] = c->timing.ms[i];
+    if (launches) launches[i] = c->timing.launches[i];
+    if (work) work[i] = c->timing.work[i];
+  }
+  return CTL_OK;
+}

@@ -1,0 +1,259 @@
+// Internal declarations of the ctl library (not part of the C-ABI).
+#pragma once
+#include <cstdint>
+#include <cstddef>
+#include <string>
+#include <vector>
+#include <map>
+#include <mutex>
+#include <atomic>
+#include <cuda_runtime.h>
+
+#include "ctl.h"
+
+namespace ctl {
+
+typedef unsigned long long u64;
+typedef long long i64;
+
+// ---------------------------------------------------------------------------------
+// Per-prime constants, device resident.
+// ---------------------------------------------------------------------------------
+struct DPrime {
+  u64 q;        // the prime
+  u64 qinv;     // q^-1 mod 2^64 (Montgomery, positive form)
+  u64 r2;       // 2^128 mod q: mulmod_mont(x, r2) = x * 2^64 mod q
+  u64 rmod;     // 2^64 mod q: mulmod_mont(x, rmod) = x mod q for any 64-bit x
+  u64 ninv, ninv_sh;  // N^-1 mod q and its Shoup companion
+  u64 iw1, iw1_sh;    // (psi^-1)^{bitrev(1)} * N^-1: the folded last inverse twiddle
+};
+
+// Fast base conversion from a set of source primes S to target primes:
+//   y_i = sum_{j in S} [x_j * Shat_j^-1]_{s_j} * (Shat_j mod t_i)  mod t_i.
+struct ConvTab {
+  int ns;               // |S|
+  int nt;               // number of target positions
+  const u64* sinv;      // [ns] Shat_j^-1 mod s_j
+  const u64* sinv_sh;   // [ns] Shoup companions
+  const u64* sq;        // [ns] source primes
+  const u64* cmont;     // [ns][nt] (Shat_j mod t_i) * 2^64 mod t_i
+};
+
+// Rescale constants for dropping the last prime of a level-lvl ciphertext.
+struct RescaleTab {
+  const u64* inv;     // [lvl-1] q_last^-1 mod q_i
+  const u64* inv_sh;  // [lvl-1]
+  const u64* hmod;    // [lvl-1] floor(q_last/2) mod q_i
+  u64 qlast, h;
+};
+
+// Keys and Galois elements of the rotations served by one key-switching launch, passed
+// by value as a kernel parameter (no host-to-device copy on the hot path).
+#define CTL_MAX_ROT 64
+struct RotList {
+  int n;
+  const u64* key[CTL_MAX_ROT];  // device key [beta][2][L+K][N] (Montgomery, NTT form)
+  u64 g[CTL_MAX_ROT];           // Galois element (1 = no automorphism)
+};
+
+// ModDown constants (special primes P -> data primes).
+struct ModDownTab {
+  ConvTab conv;       // S = special primes, targets = data primes 0..L-1
+  const u64* pinv;    // [L] P^-1 mod q_i
+  const u64* pinv_sh; // [L]
+};
+
+// ---------------------------------------------------------------------------------
+// Host-side mathematics (host_math.cpp).
+// ---------------------------------------------------------------------------------
+bool plan_primes(uint32_t N, const std::vector<uint32_t>& bits, std::vector<u64>& out);
+u64 min_primitive_2n_root(u64 q, uint32_t N);
+u64 h_powmod(u64 a, u64 e, u64 q);
+u64 h_mulmod(u64 a, u64 b, u64 q);
+u64 h_invmod(u64 a, u64 q);
+u64 h_shoup(u64 w, u64 q);        // floor(w * 2^64 / q)
+u64 h_mont(u64 x, u64 q);         // x * 2^64 mod q
+u64 h_neg_inv64(u64 q);           // q^-1 mod 2^64
+uint32_t h_bitrev(uint32_t x, uint32_t logn);
+
+// SplitMix64 streams and the samplers of the key/encryption randomness.
+struct SplitMixStream {
+  u64 key, ctr;
+  SplitMixStream(u64 seed, u64 stream);
+  u64 next();
+};
+u64 stream_id_secret();
+u64 stream_id_key_a(u64 key_id, u64 digit, u64 limb);
+u64 stream_id_key_e(u64 key_id, u64 digit);
+u64 stream_id_enc_a(u64 limb);
+u64 stream_id_enc_e();
+void draw_uniform(SplitMixStream& st, u64 q, uint32_t N, u64* out);
+void draw_ternary(SplitMixStream& st, uint32_t N, i64* out);
+void draw_cbd21(SplitMixStream& st, uint32_t N, i64* out);
+
+// FP64 canonical-embedding encoder (radix-2 complex FFT).
+struct Encoder {
+  uint32_t N = 0;
+  std::vector<uint32_t> slot_pos;   // odd-power index (e-1)/2 of slot j, e = 5^j mod 2N
+  std::vector<uint32_t> conj_pos;   // index of the conjugate root -5^j
+  std::vector<double> cs, sn;       // cos/sin(2*pi*k/N)
+  std::vector<double> zc, zs;       // cos/sin(pi*k/N): the twist zeta^k
+  void init(uint32_t n);
+  // m_k = round(scale * (2/N) * Re sum_j z_j zeta^(-5^j k)); returns false on overflow.
+  bool encode(const double* z, size_t nz, double scale, i64* m) const;
+  // z_j = Re( sum_k m_k zeta^(5^j k) ) / scale for j < nz.
+  void decode(const double* m, size_t nz, double scale, double* z) const;
+ private:
+  void fft(std::vector<double>& re, std::vector<double>& im, bool inverse) const;
+};
+
+// Centred CRT of residues over the first lvl primes, returned as double.
+void crt_centred_to_double(const u64* res, size_t stride, uint32_t lvl, const u64* primes, size_t N, double* out);
+
+// ---------------------------------------------------------------------------------
+// Launch statistics (kernel launches and per-class device time).
+// ---------------------------------------------------------------------------------
+enum KernelClass {
+  KC_NTT_FWD = 0, KC_NTT_INV, KC_MODUP, KC_KEYIP, KC_MODDOWN, KC_RESCALE, KC_BSGS, KC_ELEM, KC_COUNT
+};
+extern const char* kKernelClassName[KC_COUNT];
+
+struct Timing {
+  bool enabled = false;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+  std::vector<cudaEvent_t> pool;
+  double ms[KC_COUNT] = {0};
+  uint64_t launches[KC_COUNT] = {0};
+  double work[KC_COUNT] = {0};  // algorithmic units (modmul) attributed to the class
+};
+
+}  // namespace ctl
+
+// ---------------------------------------------------------------------------------
+// Opaque handles of the C-ABI.
+// ---------------------------------------------------------------------------------
+struct ctl_context {
+  uint32_t N = 0, logN = 0, L = 0, K = 0, alpha = 1, beta = 1;
+  double scale = 0;
+  uint64_t seed = 0;
+  std::vector<ctl::u64> moduli;   // L data primes then K special primes
+  int device = 0, sm_count = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  ctl_alloc_fn alloc_fn = nullptr;
+  ctl_free_fn free_fn = nullptr;
+  void* alloc_user = nullptr;
+  // device tables
+  ctl::DPrime* d_primes = nullptr;
+  ctl::u64* d_tw = nullptr;      // [L+K][N] forward twiddles psi^{bitrev(i)}
+  ctl::u64* d_tw_sh = nullptr;
+  ctl::u64* d_itw = nullptr;     // [L+K][N] inverse twiddles (psi^-1)^{bitrev(i)}
+  ctl::u64* d_itw_sh = nullptr;
+  ctl::u64* d_tables = nullptr;  // conversion / rescale constants
+  std::vector<ctl::ConvTab> modup_tabs;      // index (lvl-1)*beta + d
+  std::vector<ctl::RescaleTab> rescale_tabs; // index lvl (valid for lvl >= 2)
+  ctl::ModDownTab moddown;
+  std::vector<ctl::DPrime> h_primes;
+  ctl::Encoder enc;
+  ctl::Timing timing;
+  std::atomic<uint64_t> launch_count{0};
+  uint64_t op_rot = 0, op_ptmul = 0, op_add = 0, op_relin = 0, op_rescale = 0;
+  int ntt_threads_fwd = 0, ntt_threads_inv = 0;  // autotuned block sizes (0: default)
+};
+
+struct ctl_keys {
+  ctl_context* ctx = nullptr;
+  std::vector<ctl::i64> s;               // ternary secret (host)
+  ctl::u64* d_s = nullptr;               // [L+K][N] NTT form, plain residues
+  // key_id -> device key [beta][2][L+K][N], NTT form, Montgomery form
+  std::map<ctl::u64, ctl::u64*> evk;
+  size_t key_bytes = 0;
+};
+
+struct ctl_ct {
+  ctl_context* ctx = nullptr;
+  ctl::u64* d = nullptr;    // [count][2][level][N], NTT form
+  uint32_t level = 0;       // live data primes
+  uint32_t count = 1;       // ciphertexts in this batch
+  double scale = 0;
+  size_t bytes = 0;
+};
+
+namespace ctl {
+
+// ---------------------------------------------------------------------------------
+// Memory and error helpers (ctl_api.cu).
+// ---------------------------------------------------------------------------------
+void* dev_alloc(ctl_context* c, size_t bytes);
+void dev_free(ctl_context* c, void* p);
+void set_error(const char* fmt, ...);
+int cuda_check(cudaError_t e, const char* what);
+void timing_begin(ctl_context* c, int cls, cudaEvent_t* ev);
+void timing_end(ctl_context* c, int cls, cudaEvent_t ev, double work);
+
+inline uint32_t prime_of_limb(uint32_t l, uint32_t lvl, uint32_t L) { return l < lvl ? l : L + (l - lvl); }
+
+// ---------------------------------------------------------------------------------
+// Kernel launchers (ntt.cu, kernels.cu).  All operate on the context stream.
+// Layout conventions: a "poly" is [limbs][N]; polys are spaced by poly_stride words.
+// A limb l of a poly of a level-lvl object maps to prime prime_of_limb(l, lvl, L).
+// ---------------------------------------------------------------------------------
+// In-place forward / inverse NTT of limbs [limb_lo, limb_hi) of n_polys polys.
+void launch_ntt_fwd(ctl_context* c, u64* data, size_t poly_stride, int n_polys, int limb_lo, int limb_hi, int lvl);
+void launch_ntt_inv(ctl_context* c, u64* data, size_t poly_stride, int n_polys, int limb_lo, int limb_hi, int lvl);
+// Inverse NTT of limb lvl-1 of each poly, writing r = [x + floor(q/2)]_q (coefficient form)
+// to r_out[p][N].
+void launch_intt_rescale_last(ctl_context* c, const u64* in, size_t poly_stride, int n_polys, int lvl, u64* r_out);
+// Rescale combine: out[p][i] = (in[p][i] - NTT_i((r - h) mod q_i)) * q_last^-1 for i < lvl-1.
+void launch_rescale_ntt(ctl_context* c, const u64* r, const u64* in, size_t in_stride, u64* out, size_t out_stride,
+                        int n_polys, int lvl);
+// ModUp of c1 (coefficient form src_coef, NTT form src_ntt; polys spaced by src_stride)
+// into ext[b][d][E][N] (NTT form), E = lvl + K, for all live digits d.
+void launch_modup_ntt(ctl_context* c, const u64* src_coef, size_t coef_stride, const u64* src_ntt, size_t src_stride,
+                      int nb, int lvl, u64* ext);
+// Key inner products with automorphism: for rotation r (g[r], key[r]) and batch b:
+//   acc[r][b][t][i][k] = sum_d ext_r[b][d][i][perm_g(k)] * key_r[d][t][prime(i)][k],
+// ext_r = ext + r * ext_r_stride (0 when the ModUp is shared by all rotations).
+void launch_key_ip(ctl_context* c, const u64* ext, size_t ext_r_stride, int nb, int lvl, const RotList& rl, u64* acc);
+// ModDown after the special limbs of acc [nr][nb][2][E][N] were inverse-transformed in
+// place: out[p][i] = (acc[p][i] - NTT_i(conv_i(acc[p][specials]))) * P^-1 (+ addend),
+// out [nr][nb][2][lvl][N].  Addend of output (r, b, t): addend + r*add_r + b*add_b + t*add_p
+// read through sigma_{g_r}; t = 1 gets one only if add_both.
+void launch_moddown_ntt(ctl_context* c, const u64* acc, int nr, int nb, int lvl, u64* out, const u64* addend,
+                        size_t add_r, size_t add_b, size_t add_p, bool add_both, const RotList& rl);
+// Out-of-place inverse NTT.
+void launch_ntt_inv_oop(ctl_context* c, const u64* src, size_t src_stride, u64* dst, size_t dst_stride, int n_polys,
+                        int limb_lo, int limb_hi, int lvl);
+
+// Elementwise (kernels.cu).
+void launch_add(ctl_context* c, const u64* a, const u64* b, u64* out, int n_polys, int lvl, size_t stride_a,
+                size_t stride_b, size_t stride_o);
+void launch_sub(ctl_context* c, const u64* a, const u64* b, u64* out, int n_polys, int lvl, size_t stride_a,
+                size_t stride_b, size_t stride_o);
+// out = ct * pt_mont (pt in Montgomery form, [lvl_pt][N], same for every poly).
+void launch_mul_plain(ctl_context* c, const u64* ct, const u64* pt, u64* out, int n_polys, int lvl,
+                      size_t stride_ct, size_t stride_o);
+// out = ct + pt on poly 0 of each ciphertext.
+void launch_add_plain(ctl_context* c, u64* ct, const u64* pt, int n_ct, int lvl, size_t ct_stride);
+// (a0,a1) -> (a0^2, 2 a0 a1, a1^2) for each of nb ciphertexts; d layout [nb][3][lvl][N].
+void launch_tensor_square(ctl_context* c, const u64* ct, u64* d, int nb, int lvl);
+// Montgomery form conversion of limbs (to: x*R, from: x*R^-1).
+void launch_to_mont(ctl_context* c, u64* data, int n_polys, int limbs, int lvl, size_t stride, bool to);
+// Signed integer polynomial -> residues [limbs][N] with limb prime map (lvl, L).
+void launch_from_signed(ctl_context* c, const i64* src, u64* dst, int n_polys, int limbs, int lvl, size_t src_stride,
+                        size_t dst_stride);
+// Key assembly: b = -a*s + e + gadget_i * s' (NTT form), then Montgomery form of b and a.
+void launch_keygen_combine(ctl_context* c, u64* key, const u64* s_ntt, const u64* e_ntt, const u64* sp_ntt, int beta,
+                           int alpha, const u64* pmod);
+// Encryption: c0 = -a*s + m + e at each limb; inputs NTT form; c1 = a already in place.
+void launch_encrypt_combine(ctl_context* c, u64* ct, const u64* s_ntt, const u64* me_ntt, int lvl);
+// Decryption: out = c0 + c1 * s (NTT form) for nb ciphertexts -> out [nb][lvl][N].
+void launch_decrypt_mul(ctl_context* c, const u64* ct, const u64* s_ntt, u64* out, int nb, int lvl);
+// Automorphism of a whole object in the NTT domain.
+void launch_automorph(ctl_context* c, const u64* in, u64* out, int n_polys, int limbs, int lvl, size_t stride, u64 g);
+// Baby-step giant-step inner sums:
+//   inner[k][b][p][i] = sum_j diag[k*t1+j][i] * baby[j][b][p][i]   (diag in Montgomery form)
+void launch_bsgs_inner(ctl_context* c, const u64* baby, const u64* diag, size_t diag_stride, u64* inner, int t1,
+                       int t2, int nb, int lvl);
+
+}  // namespace ctl

@@ -1,0 +1,418 @@
+// Element-wise kernels of the CKKS server path (NTT domain), the key-switching inner
+// product and the baby-step giant-step inner sums of Eq. (bsgs).
+//
+// All products are exact: Montgomery reduction of 128-bit accumulators against
+// operands stored in Montgomery form (keys, diagonal plaintexts), so a lazy sum of
+// several 64x64-bit products costs one reduction.
+#include "ctl_internal.h"
+#include "modarith.cuh"
+
+namespace ctl {
+
+__device__ __forceinline__ uint32_t brv_k(uint32_t x, int logn) { return __brev(x) >> (32 - logn); }
+__device__ __forceinline__ uint32_t auto_src_k(uint32_t k, u64 g, int logN) {
+  uint32_t e = 2u * brv_k(k, logN) + 1u;
+  uint32_t e2 = (uint32_t)(((u64)e * g) & ((2ull << logN) - 1));
+  return brv_k((e2 - 1u) >> 1, logN);
+}
+
+static const int kThreads = 256;
+
+static int elem_grid(ctl_context* c, size_t total) {
+  size_t g = (total + kThreads - 1) / kThreads;
+  size_t cap = (size_t)c->sm_count * 16;
+  return (int)(g < cap ? g : cap);
+}
+
+#define CTL_LAUNCH(cls, work, grid, ...)  \
+  do {                                    \
+    cudaEvent_t ev__;                     \
+    timing_begin(c, cls, &ev__);          \
+    __VA_ARGS__;                          \
+    c->launch_count++;                    \
+    timing_end(c, cls, ev__, work);       \
+  } while (0)
+
+// ---------------------------------------------------------------------------------
+// add / sub over n_polys polys of lvl limbs (limb i -> prime i).
+// ---------------------------------------------------------------------------------
+template <bool SUB>
+__global__ void k_addsub(const u64* __restrict__ a, const u64* __restrict__ b, u64* __restrict__ o,
+                         const DPrime* __restrict__ pr, int logN, int lvl, size_t total, size_t sa, size_t sb,
+                         size_t so) {
+  const size_t N = (size_t)1 << logN;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t p = idx / (lvl * N), r = idx % (lvl * N);
+    const int i = (int)(r >> logN);
+    const u64 q = pr[i].q;
+    const u64 x = a[p * sa + r], y = b[p * sb + r];
+    o[p * so + r] = SUB ? submod(x, y, q) : addmod(x, y, q);
+  }
+}
+
+void launch_add(ctl_context* c, const u64* a, const u64* b, u64* out, int n_polys, int lvl, size_t sa, size_t sb,
+                size_t so) {
+  size_t total = (size_t)n_polys * lvl * c->N;
+  if (!total) return;
+  int g = elem_grid(c, total);
+  CTL_LAUNCH(KC_ELEM, 0, g, (k_addsub<false><<<g, kThreads, 0, c->stream>>>(a, b, out, c->d_primes, (int)c->logN, lvl,
+                                                                          total, sa, sb, so)));
+}
+void launch_sub(ctl_context* c, const u64* a, const u64* b, u64* out, int n_polys, int lvl, size_t sa, size_t sb,
+                size_t so) {
+  size_t total = (size_t)n_polys * lvl * c->N;
+  if (!total) return;
+  int g = elem_grid(c, total);
+  CTL_LAUNCH(KC_ELEM, 0, g, (k_addsub<true><<<g, kThreads, 0, c->stream>>>(a, b, out, c->d_primes, (int)c->logN, lvl,
+                                                                         total, sa, sb, so)));
+}
+
+// ---------------------------------------------------------------------------------
+// Plaintext product (pt in Montgomery form, NTT domain) and plaintext addition.
+// ---------------------------------------------------------------------------------
+__global__ void k_mul_plain(const u64* __restrict__ ct, const u64* __restrict__ pt, u64* __restrict__ o,
+                            const DPrime* __restrict__ pr, int logN, int lvl, size_t total, size_t sc, size_t so) {
+  const size_t N = (size_t)1 << logN;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t p = idx / (lvl * N), r = idx % (lvl * N);
+    const int i = (int)(r >> logN);
+    o[p * so + r] = mulmod_mont(ct[p * sc + r], pt[r], pr[i].q, pr[i].qinv);
+  }
+}
+void launch_mul_plain(ctl_context* c, const u64* ct, const u64* pt, u64* out, int n_polys, int lvl, size_t sc,
+                      size_t so) {
+  size_t total = (size_t)n_polys * lvl * c->N;
+  if (!total) return;
+  int g = elem_grid(c, total);
+  CTL_LAUNCH(KC_ELEM, (double)total, g,
+             (k_mul_plain<<<g, kThreads, 0, c->stream>>>(ct, pt, out, c->d_primes, (int)c->logN, lvl, total, sc, so)));
+}
+
+__global__ void k_add_plain(u64* ct, const u64* __restrict__ pt, const DPrime* __restrict__ pr, int logN, int lvl,
+                            size_t total, size_t sc) {
+  const size_t N = (size_t)1 << logN;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t b = idx / (lvl * N), r = idx % (lvl * N);
+    const int i = (int)(r >> logN);
+    ct[b * sc + r] = addmod(ct[b * sc + r], pt[r], pr[i].q);
+  }
+}
+void launch_add_plain(ctl_context* c, u64* ct, const u64* pt, int n_ct, int lvl, size_t ct_stride) {
+  size_t total = (size_t)n_ct * lvl * c->N;
+  if (!total) return;
+  int g = elem_grid(c, total);
+  CTL_LAUNCH(KC_ELEM, 0, g,
+             (k_add_plain<<<g, kThreads, 0, c->stream>>>(ct, pt, c->d_primes, (int)c->logN, lvl, total, ct_stride)));
+}
+
+// ---------------------------------------------------------------------------------
+// Tensor of a ciphertext with itself: (c0^2, 2 c0 c1, c1^2).
+// ---------------------------------------------------------------------------------
+__global__ void k_tensor_sq(const u64* __restrict__ ct, u64* __restrict__ d, const DPrime* __restrict__ pr, int logN,
+                            int lvl, size_t total) {
+  const size_t N = (size_t)1 << logN;
+  const size_t LN = (size_t)lvl * N;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t b = idx / LN, r = idx % LN;
+    const int i = (int)(r >> logN);
+    const DPrime P = pr[i];
+    const u64 a0 = ct[b * 2 * LN + r], a1 = ct[b * 2 * LN + LN + r];
+    const u64 a0m = mulmod_mont(a0, P.r2, P.q, P.qinv);  // a0 * R
+    const u64 a1m = mulmod_mont(a1, P.r2, P.q, P.qinv);  // a1 * R
+    const u64 x01 = mulmod_mont(a1, a0m, P.q, P.qinv);
+    d[b * 3 * LN + r] = mulmod_mont(a0, a0m, P.q, P.qinv);
+    d[b * 3 * LN + LN + r] = addmod(x01, x01, P.q);
+    d[b * 3 * LN + 2 * LN + r] = mulmod_mont(a1, a1m, P.q, P.qinv);
+  }
+}
+void launch_tensor_square(ctl_context* c, const u64* ct, u64* d, int nb, int lvl) {
+  size_t total = (size_t)nb * lvl * c->N;
+  if (!total) return;
+  int g = elem_grid(c, total);
+  CTL_LAUNCH(KC_ELEM, 5.0 * total, g,
+             (k_tensor_sq<<<g, kThreads, 0, c->stream>>>(ct, d, c->d_primes, (int)c->logN, lvl, total)));
+}
+
+// ---------------------------------------------------------------------------------
+// Montgomery form conversion and signed-integer import.
+// ---------------------------------------------------------------------------------
+__global__ void k_mont(u64* data, const DPrime* __restrict__ pr, int logN, int limbs, int lvl, int L, size_t total,
+                       size_t stride, bool to) {
+  const size_t N = (size_t)1 << logN;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t p = idx / (limbs * N), r = idx % (limbs * N);
+    const int l = (int)(r >> logN);
+    const int pi = l < lvl ? l : L + (l - lvl);
+    const DPrime P = pr[pi];
+    u64& v = data[p * stride + r];
+    v = to ? mulmod_mont(v, P.r2, P.q, P.qinv) : redc(0, v, P.q, P.qinv);
+  }
+}
+void launch_to_mont(ctl_context* c, u64* data, int n_polys, int limbs, int lvl, size_t stride, bool to) {
+  size_t total = (size_t)n_polys * limbs * c->N;
+  if (!total) return;
+  int g = elem_grid(c, total);
+  CTL_LAUNCH(KC_ELEM, 0, g,
+             (k_mont<<<g, kThreads, 0, c->stream>>>(data, c->d_primes, (int)c->logN, limbs, lvl, (int)c->L, total,
+                                                    stride, to)));
+}
+
+__global__ void k_from_signed(const i64* __restrict__ src, u64* __restrict__ dst, const DPrime* __restrict__ pr,
+                              int logN, int limbs, int lvl, int L, size_t total, size_t ss, size_t ds) {
+  const size_t N = (size_t)1 << logN;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t p = idx / (limbs * N), r = idx % (limbs * N);
+    const int l = (int)(r >> logN);
+    const size_t k = r & (N - 1);
+    const int pi = l < lvl ? l : L + (l - lvl);
+    const DPrime P = pr[pi];
+    const i64 v = src[p * ss + k];
+    const u64 a = v >= 0 ? (u64)v : (u64)(-(v + 1)) + 1ull;
+    const u64 m = mulmod_mont(a, P.rmod, P.q, P.qinv);  // a mod q
+    dst[p * ds + r] = v >= 0 ? m : negmod(m, P.q);
+  }
+}
+void launch_from_signed(ctl_context* c, const i64* src, u64* dst, int n_polys, int limbs, int lvl, size_t ss,
+                        size_t ds) {
+  size_t total = (size_t)n_polys * limbs * c->N;
+  if (!total) return;
+  int g = elem_grid(c, total);
+  CTL_LAUNCH(KC_ELEM, 0, g,
+             (k_from_signed<<<g, kThreads, 0, c->stream>>>(src, dst, c->d_primes, (int)c->logN, limbs, lvl, (int)c->L,
+                                                           total, ss, ds)));
+}
+
+// ---------------------------------------------------------------------------------
+// Key generation: key [beta][2][LK][N] holds a in poly 1 (NTT form) on entry; e_ntt is
+// [beta][LK][N]; sp_ntt [LK][N] is s'; pmod[i] = P mod q_i.  Writes
+//   b = -a*s + e + [i in digit d] * (P mod q_i) * s'   and converts b and a to Montgomery form.
+// ---------------------------------------------------------------------------------
+__global__ void k_keygen(u64* key, const u64* __restrict__ s, const u64* __restrict__ e, const u64* __restrict__ sp,
+                         const u64* __restrict__ pmod, const DPrime* __restrict__ pr, int logN, int LK, int L,
+                         int alpha, size_t total) {
+  const size_t N = (size_t)1 << logN;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t d = idx / (LK * N), r = idx % (LK * N);
+    const int i = (int)(r >> logN);
+    const DPrime P = pr[i];
+    u64* b0 = key + (d * 2) * LK * N + r;
+    u64* b1 = key + (d * 2 + 1) * LK * N + r;
+    const u64 a = *b1;
+    const u64 as = mulmod_plain(a, s[r], P.q, P.qinv, P.r2);
+    u64 v = submod(e[d * LK * N + r], as, P.q);
+    const bool in_digit = (i < L) && (i >= (int)d * alpha) && (i < ((int)d + 1) * alpha);
+    if (in_digit) v = addmod(v, mulmod_plain(pmod[i], sp[r], P.q, P.qinv, P.r2), P.q);
+    *b0 = mulmod_mont(v, P.r2, P.q, P.qinv);
+    *b1 = mulmod_mont(a, P.r2, P.q, P.qinv);
+  }
+}
+void launch_keygen_combine(ctl_context* c, u64* key, const u64* s_ntt, const u64* e_ntt, const u64* sp_ntt, int beta,
+                           int alpha, const u64* pmod) {
+  const int LK = (int)(c->L + c->K);
+  size_t total = (size_t)beta * LK * c->N;
+  int g = elem_grid(c, total);
+  CTL_LAUNCH(KC_ELEM, 0, g,
+             (k_keygen<<<g, kThreads, 0, c->stream>>>(key, s_ntt, e_ntt, sp_ntt, pmod, c->d_primes, (int)c->logN,
+                                                      LK, (int)c->L, alpha, total)));
+}
+
+// ---------------------------------------------------------------------------------
+// Encryption / decryption arithmetic.
+// ---------------------------------------------------------------------------------
+__global__ void k_encrypt(u64* ct, const u64* __restrict__ s, const u64* __restrict__ me,
+                          const DPrime* __restrict__ pr, int logN, int lvl, size_t total) {
+  const size_t N = (size_t)1 << logN;
+  for (size_t r = blockIdx.x * (size_t)blockDim.x + threadIdx.x; r < total; r += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(r >> logN);
+    const DPrime P = pr[i];
+    const u64 a = ct[(size_t)lvl * N + r];
+    ct[r] = submod(me[r], mulmod_plain(a, s[r], P.q, P.qinv, P.r2), P.q);
+  }
+}
+void launch_encrypt_combine(ctl_context* c, u64* ct, const u64* s_ntt, const u64* me_ntt, int lvl) {
+  size_t total = (size_t)lvl * c->N;
+  int g = elem_grid(c, total);
+  CTL_LAUNCH(KC_ELEM, 0, g,
+             (k_encrypt<<<g, kThreads, 0, c->stream>>>(ct, s_ntt, me_ntt, c->d_primes, (int)c->logN, lvl, total)));
+}
+
+__global__ void k_decrypt(const u64* __restrict__ ct, const u64* __restrict__ s, u64* __restrict__ out,
+                          const DPrime* __restrict__ pr, int logN, int lvl, size_t total) {
+  const size_t N = (size_t)1 << logN;
+  const size_t LN = (size_t)lvl * N;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t b = idx / LN, r = idx % LN;
+    const int i = (int)(r >> logN);
+    const DPrime P = pr[i];
+    out[idx] = addmod(ct[b * 2 * LN + r], mulmod_plain(ct[b * 2 * LN + LN + r], s[r], P.q, P.qinv, P.r2), P.q);
+  }
+}
+void launch_decrypt_mul(ctl_context* c, const u64* ct, const u64* s_ntt, u64* out, int nb, int lvl) {
+  size_t total = (size_t)nb * lvl * c->N;
+  int g = elem_grid(c, total);
+  CTL_LAUNCH(KC_ELEM, 0, g,
+             (k_decrypt<<<g, kThreads, 0, c->stream>>>(ct, s_ntt, out, c->d_primes, (int)c->logN, lvl, total)));
+}
+
+// ---------------------------------------------------------------------------------
+// Automorphism sigma_g of whole polys in the NTT domain (a gather).
+// ---------------------------------------------------------------------------------
+__global__ void k_automorph(const u64* __restrict__ in, u64* __restrict__ out, int logN, int limbs, size_t total,
+                            size_t stride, u64 g) {
+  const size_t N = (size_t)1 << logN;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t p = idx / (limbs * N), r = idx % (limbs * N);
+    const size_t l = r >> logN, k = r & (N - 1);
+    out[p * stride + r] = in[p * stride + l * N + auto_src_k((uint32_t)k, g, logN)];
+  }
+}
+void launch_automorph(ctl_context* c, const u64* in, u64* out, int n_polys, int limbs, int, size_t stride, u64 g) {
+  size_t total = (size_t)n_polys * limbs * c->N;
+  int gr = elem_grid(c, total);
+  CTL_LAUNCH(KC_ELEM, 0, gr,
+             (k_automorph<<<gr, kThreads, 0, c->stream>>>(in, out, (int)c->logN, limbs, total, stride, g)));
+}
+
+// ---------------------------------------------------------------------------------
+// Key-switching inner product with the automorphism folded into the gather.
+//   acc[r][b][t][i][k] = sum_{d < nd} ext[b][d][i][src_g(k)] * key_r[d][t][prime(i)][k]
+// Key values are in Montgomery form, so one REDC yields the plain residue.  The 128-bit
+// sum of nd products stays below q * 2^64 when nd * q < 2^64 (REDC precondition); the
+// CHECK variant reduces the high word on the way for larger digit counts.
+// ---------------------------------------------------------------------------------
+template <bool CHECK>
+__global__ void k_key_ip(const u64* __restrict__ ext, size_t ext_r, const RotList rl, u64* __restrict__ acc,
+                         const DPrime* __restrict__ pr, int logN, int nb, int nd, int E, int lvl, int L, int LK) {
+  const size_t N = (size_t)1 << logN;
+  const size_t per_rot = (size_t)nb * E * N;
+  const int r = blockIdx.y;
+  const u64* key = rl.key[r];
+  const u64 g = rl.g[r];
+  const u64* ex = ext + (size_t)r * ext_r;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < per_rot; idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t b = idx / (E * N), rr = idx % (E * N);
+    const int i = (int)(rr >> logN);
+    const uint32_t k = (uint32_t)(rr & (N - 1));
+    const int pi = i < lvl ? i : L + (i - lvl);
+    const DPrime P = pr[pi];
+    const uint32_t ks = g == 1 ? k : auto_src_k(k, g, logN);
+    u64 lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
+    for (int d = 0; d < nd; d++) {
+      const u64 x = ex[((b * nd + d) * E + i) * N + ks];
+      const u64 k0 = key[(((size_t)d * 2) * LK + pi) * N + k];
+      const u64 k1 = key[(((size_t)d * 2 + 1) * LK + pi) * N + k];
+      mac(lo0, hi0, x, k0);
+      mac(lo1, hi1, x, k1);
+      if (CHECK) {
+        if (hi0 >= P.q) hi0 -= P.q;
+        if (hi1 >= P.q) hi1 -= P.q;
+      }
+    }
+    u64* o = acc + (size_t)r * 2 * per_rot + (b * 2) * E * N + rr;
+    o[0] = redc(hi0, lo0, P.q, P.qinv);
+    o[(size_t)E * N] = redc(hi1, lo1, P.q, P.qinv);
+  }
+}
+void launch_key_ip(ctl_context* c, const u64* ext, size_t ext_r, int nb, int lvl, const RotList& rl, u64* acc) {
+  const int nrot = rl.n;
+  const int nd = (lvl + (int)c->alpha - 1) / (int)c->alpha;
+  const int E = lvl + (int)c->K;
+  const int LK = (int)(c->L + c->K);
+  size_t per_rot = (size_t)nb * E * c->N;
+  int g = elem_grid(c, per_rot);
+  dim3 grid(g, nrot);
+  u64 maxq = 0;
+  for (auto q : c->moduli) maxq = q > maxq ? q : maxq;
+  const bool check = (double)nd * (double)maxq >= 1.8e19;
+  double work = 2.0 * nd * per_rot * nrot;
+  if (check)
+    CTL_LAUNCH(KC_KEYIP, work, g,
+               (k_key_ip<true><<<grid, kThreads, 0, c->stream>>>(ext, ext_r, rl, acc, c->d_primes,
+                                                                 (int)c->logN, nb, nd, E, lvl, (int)c->L, LK)));
+  else
+    CTL_LAUNCH(KC_KEYIP, work, g,
+               (k_key_ip<false><<<grid, kThreads, 0, c->stream>>>(ext, ext_r, rl, acc, c->d_primes,
+                                                                  (int)c->logN, nb, nd, E, lvl, (int)c->L, LK)));
+}
+
+// ---------------------------------------------------------------------------------
+// Baby-step giant-step inner sums (Eq. bsgs):
+//   inner[k][b][p][i][c] = sum_{j < t1} diag[k*t1 + j][i][c] * baby[j][b][p][i][c]
+// One thread per (b, p, i, c) keeps its t1 baby-step values in registers and sweeps the
+// t2 giant steps; the diagonal values are shared by every ciphertext of the batch (and
+// both polys), so the grid runs the batch fastest to reuse them from L2.  Groups of at
+// most G products are summed lazily before one Montgomery reduction (G * q < 2^64).
+// ---------------------------------------------------------------------------------
+template <int T1>
+__global__ void __launch_bounds__(256) k_bsgs(const u64* __restrict__ baby, const u64* __restrict__ diag,
+                                              size_t diag_stride, u64* __restrict__ inner,
+                                              const DPrime* __restrict__ pr, int logN, int t1, int t2, int nb,
+                                              int lvl, int group) {
+  const size_t N = (size_t)1 << logN;
+  const size_t LN = (size_t)lvl * N;
+  const size_t bp_count = (size_t)nb * 2;
+  // blockIdx.x enumerates (b, p) fastest, blockIdx.y the coefficient tiles of all limbs
+  const size_t bp = blockIdx.x;
+  const size_t cidx = (size_t)blockIdx.y * blockDim.x + threadIdx.x;  // index in [0, lvl*N)
+  if (bp >= bp_count || cidx >= LN) return;
+  const int i = (int)(cidx >> logN);
+  const DPrime P = pr[i];
+  const size_t bstride = bp_count * LN;  // stride between baby steps j
+  u64 x[T1];
+#pragma unroll
+  for (int j = 0; j < T1; j++) x[j] = (j < t1) ? baby[(size_t)j * bstride + bp * LN + cidx] : 0;
+  for (int k = 0; k < t2; k++) {
+    const u64* dk = diag + (size_t)(k * t1) * diag_stride + cidx;
+    u64 res = 0;
+    u64 lo = 0, hi = 0;
+    int cnt = 0;
+#pragma unroll
+    for (int j = 0; j < T1; j++) {
+      if (j < t1) {
+        mac(lo, hi, x[j], __ldg(dk + (size_t)j * diag_stride));
+        if (++cnt == group) {
+          res = addmod(res, redc(hi, lo, P.q, P.qinv), P.q);
+          lo = hi = 0;
+          cnt = 0;
+        }
+      }
+    }
+    if (cnt) res = addmod(res, redc(hi, lo, P.q, P.qinv), P.q);
+    inner[(size_t)k * bstride + bp * LN + cidx] = res;
+  }
+}
+
+void launch_bsgs_inner(ctl_context* c, const u64* baby, const u64* diag, size_t diag_stride, u64* inner, int t1,
+                       int t2, int nb, int lvl) {
+  u64 maxq = 0;
+  for (int i = 0; i < lvl; i++) maxq = c->moduli[i] > maxq ? c->moduli[i] : maxq;
+  int group = (int)(1.8e19 / (double)maxq);
+  if (group < 1) group = 1;
+  if (group > 64) group = 64;
+  const size_t LN = (size_t)lvl * c->N;
+  dim3 grid((unsigned)(nb * 2), (unsigned)((LN + 255) / 256));
+  double work = (double)t1 * t2 * nb * 2 * LN;
+#define CTL_BSGS_CASE(TT)                                                                                      \
+  case TT:                                                                                                     \
+    CTL_LAUNCH(KC_BSGS, work, grid,                                                                            \
+               (k_bsgs<TT><<<grid, 256, 0, c->stream>>>(baby, diag, diag_stride, inner, c->d_primes,           \
+                                                        (int)c->logN, t1, t2, nb, lvl, group)));               \
+    break;
+  int T1 = 1;
+  while (T1 < t1) T1 <<= 1;
+  switch (T1) {
+    CTL_BSGS_CASE(1)
+    CTL_BSGS_CASE(2)
+    CTL_BSGS_CASE(4)
+    CTL_BSGS_CASE(8)
+    CTL_BSGS_CASE(16)
+    CTL_BSGS_CASE(32)
+    default:
+      CTL_LAUNCH(KC_BSGS, work, grid,
+                 (k_bsgs<64><<<grid, 256, 0, c->stream>>>(baby, diag, diag_stride, inner, c->d_primes, (int)c->logN,
+                                                          t1, t2, nb, lvl, group)));
+  }
+#undef CTL_BSGS_CASE
+}
+
+}  // namespace ctl

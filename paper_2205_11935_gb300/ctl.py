@@ -1,0 +1,397 @@
+"""ctypes binding of the ctl C-ABI (include/ctl.h): argument marshalling only.
+
+Every ``ctl_*`` function of the header is available under the same name on the
+loaded library (``lib()``); the small classes below only convert numpy arrays and
+raise ``CtlError`` on negative return codes.  All homomorphic work runs in the CUDA
+library; nothing here computes on ciphertexts.  If the compiled library is missing the
+import fails loudly (there is no CPU fallback).
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libctl.so")
+
+CTL_LAYER_DENSE, CTL_LAYER_SQUARE, CTL_LAYER_REPLICATE = 1, 2, 3
+ERRORS = {-1: "EINVAL", -2: "ELEVEL", -3: "ESCALE", -4: "EKEY", -5: "ENOMEM", -6: "ECUDA", -7: "ETIMEOUT",
+          -8: "EBUSY", -9: "ENOTSUP"}
+
+
+class CtlError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Layer(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("m", C.c_uint32), ("n", C.c_uint32), ("W", C.POINTER(C.c_double)),
+                ("bias", C.POINTER(C.c_double)), ("pt_coeffs", C.POINTER(C.c_int64)), ("rep_t", C.c_uint32)]
+
+
+_vp = C.c_void_p
+_pp = C.POINTER(C.c_void_p)
+_u64p = C.POINTER(C.c_uint64)
+_i64p = C.POINTER(C.c_int64)
+_u32p = C.POINTER(C.c_uint32)
+_i32p = C.POINTER(C.c_int32)
+_dp = C.POINTER(C.c_double)
+_sz = C.c_size_t
+
+SIGNATURES = {
+    "ctl_last_error": (C.c_char_p, []),
+    "ctl_version": (C.c_char_p, []),
+    "ctl_plan_primes": (C.c_int, [C.c_uint32, _u32p, C.c_uint32, _u64p]),
+    "ctl_context_create": (C.c_int, [_pp, C.c_uint32, _u32p, C.c_uint32, _u32p, C.c_uint32, C.c_uint32, C.c_double,
+                                     C.c_uint64]),
+    "ctl_context_destroy": (None, [_vp]),
+    "ctl_context_info": (C.c_int, [_vp, _u64p, _u32p, _u32p, _u32p]),
+    "ctl_set_stream": (C.c_int, [_vp, _vp]),
+    "ctl_set_allocator": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "ctl_synchronize": (C.c_int, [_vp]),
+    "ctl_keygen": (C.c_int, [_vp, _i32p, C.c_uint32, C.c_uint64, _pp]),
+    "ctl_keys_destroy": (None, [_vp]),
+    "ctl_keys_export": (C.c_int, [_vp, C.c_uint64, _u64p, _sz]),
+    "ctl_galois_element": (C.c_uint64, [_vp, C.c_int64]),
+    "ctl_encode": (C.c_int, [_vp, _dp, _sz, C.c_double, _i64p]),
+    "ctl_decode": (C.c_int, [_vp, _dp, _sz, C.c_double, _dp]),
+    "ctl_encrypt": (C.c_int, [_vp, _vp, _dp, _sz, C.c_uint64, _pp]),
+    "ctl_encrypt_coeffs": (C.c_int, [_vp, _vp, _i64p, C.c_uint64, _pp]),
+    "ctl_decrypt": (C.c_int, [_vp, _vp, _vp, _dp, _sz]),
+    "ctl_decrypt_coeffs": (C.c_int, [_vp, _vp, _vp, _dp]),
+    "ctl_ct_import": (C.c_int, [_vp, _u64p, C.c_uint32, C.c_uint32, C.c_double, _pp]),
+    "ctl_ct_export": (C.c_int, [_vp, _u64p, _sz]),
+    "ctl_ct_import_dev": (C.c_int, [_vp, _vp, C.c_uint32, C.c_uint32, C.c_double, _pp]),
+    "ctl_ct_export_dev": (C.c_int, [_vp, _vp, _sz]),
+    "ctl_ct_info": (C.c_int, [_vp, _u32p, _u32p, _dp]),
+    "ctl_ct_concat": (C.c_int, [_vp, _pp, _sz, _pp]),
+    "ctl_ct_slice": (C.c_int, [_vp, C.c_uint32, _pp]),
+    "ctl_ct_destroy": (None, [_vp]),
+    "ctl_rotate": (C.c_int, [_vp, _vp, _vp, C.c_int32, _pp]),
+    "ctl_rescale": (C.c_int, [_vp, _vp, _pp]),
+    "ctl_eval_square": (C.c_int, [_vp, _vp, _vp, _pp]),
+    "ctl_eval_dense": (C.c_int, [_vp, _vp, _vp, _dp, C.c_uint32, C.c_uint32, _dp, _pp]),
+    "ctl_eval_dense_coeffs": (C.c_int, [_vp, _vp, _vp, _i64p, C.c_uint32, _i64p, C.c_double, _pp]),
+    "ctl_replicate": (C.c_int, [_vp, _vp, _vp, C.c_uint32, _pp]),
+    "ctl_add": (C.c_int, [_vp, _vp, _vp, _pp]),
+    "ctl_mul_plain_coeffs": (C.c_int, [_vp, _vp, _i64p, C.c_double, _pp]),
+    "ctl_ntt_dev": (C.c_int, [_vp, _vp, _vp, C.c_uint32, C.c_uint32, C.c_int]),
+    "ctl_model_create": (C.c_int, [_vp, C.POINTER(Layer), C.c_uint32, C.c_uint32, C.c_double, _pp]),
+    "ctl_model_destroy": (None, [_vp]),
+    "ctl_model_rotations": (C.c_int, [_vp, _i32p, C.c_uint32, _u32p]),
+    "ctl_model_forward": (C.c_int, [_vp, _vp, _vp, _vp, _pp]),
+    "ctl_model_info": (C.c_int, [_vp, _u32p, _dp, _u64p]),
+    "ctl_stats_reset": (C.c_int, [_vp]),
+    "ctl_stats_enable_timing": (C.c_int, [_vp, C.c_int]),
+    "ctl_stats_launches": (C.c_uint64, [_vp]),
+    "ctl_stats_ops": (C.c_int, [_vp, _u64p]),
+    "ctl_stats_kernel_classes": (C.c_int, []),
+    "ctl_stats_class_name": (C.c_char_p, [C.c_int]),
+    "ctl_stats_kernels": (C.c_int, [_vp, _dp, _u64p, _dp]),
+}
+
+_LIB = None
+
+
+def lib():
+    """Load libctl.so (built by ``paper_2205_11935_gb300.build``); raises if absent."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"CUDA library not built: {LIB_PATH} (run paper_2205_11935_gb300/build.py)")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _check(rc):
+    if rc != 0:
+        raise CtlError(rc, lib().ctl_last_error().decode())
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t)
+
+
+def plan_primes(N, bits):
+    b = np.asarray(bits, dtype=np.uint32)
+    out = np.zeros(len(b), dtype=np.uint64)
+    _check(lib().ctl_plan_primes(N, _p(b, _u32p), len(b), _p(out, _u64p)))
+    return [int(x) for x in out]
+
+
+class Context:
+    def __init__(self, N, q_bits, p_bits, dnum=None, scale=2.0 ** 40, seed=0, stream=None):
+        L = lib()
+        qb = np.asarray(q_bits, dtype=np.uint32)
+        pb = np.asarray(p_bits, dtype=np.uint32)
+        dnum = len(qb) if dnum is None else dnum
+        h = C.c_void_p()
+        _check(L.ctl_context_create(C.byref(h), N, _p(qb, _u32p), len(qb), _p(pb, _u32p), len(pb), dnum, scale, seed))
+        self.h = h
+        self.N, self.L, self.K, self.scale = N, len(qb), len(pb), scale
+        mods = np.zeros(self.L + self.K, dtype=np.uint64)
+        a = C.c_uint32()
+        _check(L.ctl_context_info(h, _p(mods, _u64p), None, None, C.byref(a)))
+        self.moduli = [int(x) for x in mods]
+        self.alpha = a.value
+        self.beta = (self.L + self.alpha - 1) // self.alpha
+        if stream is not None:
+            self.set_stream(stream)
+
+    def set_stream(self, stream_ptr):
+        _check(lib().ctl_set_stream(self.h, C.c_void_p(stream_ptr)))
+
+    def synchronize(self):
+        _check(lib().ctl_synchronize(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ctl_context_destroy(self.h)
+            self.h = None
+
+    def galois_element(self, r):
+        return int(lib().ctl_galois_element(self.h, r))
+
+    def keygen(self, rotations=(), seed=3):
+        r = np.asarray(list(rotations), dtype=np.int32)
+        h = C.c_void_p()
+        _check(lib().ctl_keygen(self.h, _p(r, _i32p), len(r), seed, C.byref(h)))
+        return Keys(self, h)
+
+    def encode(self, x, scale=None):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        m = np.zeros(self.N, dtype=np.int64)
+        _check(lib().ctl_encode(self.h, _p(x, _dp), len(x), self.scale if scale is None else scale, _p(m, _i64p)))
+        return m
+
+    def decode(self, m, n, scale=None):
+        m = np.ascontiguousarray(m, dtype=np.float64)
+        y = np.zeros(n, dtype=np.float64)
+        _check(lib().ctl_decode(self.h, _p(m, _dp), n, self.scale if scale is None else scale, _p(y, _dp)))
+        return y
+
+    def encrypt(self, keys, x, seed):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        h = C.c_void_p()
+        _check(lib().ctl_encrypt(self.h, keys.h, _p(x, _dp), len(x), seed, C.byref(h)))
+        return Ciphertext(self, h)
+
+    def encrypt_coeffs(self, keys, m, seed):
+        m = np.ascontiguousarray(m, dtype=np.int64)
+        h = C.c_void_p()
+        _check(lib().ctl_encrypt_coeffs(self.h, keys.h, _p(m, _i64p), seed, C.byref(h)))
+        return Ciphertext(self, h)
+
+    def decrypt(self, keys, ct, n):
+        y = np.zeros(n, dtype=np.float64)
+        _check(lib().ctl_decrypt(self.h, keys.h, ct.h, _p(y, _dp), n))
+        return y
+
+    def decrypt_coeffs(self, keys, ct):
+        m = np.zeros(self.N, dtype=np.float64)
+        _check(lib().ctl_decrypt_coeffs(self.h, keys.h, ct.h, _p(m, _dp)))
+        return m
+
+    def ct_import(self, coeffs, scale):
+        a = np.ascontiguousarray(coeffs, dtype=np.uint64)
+        if a.ndim == 3:
+            a = a[None]
+        count, _, level, _ = a.shape
+        h = C.c_void_p()
+        _check(lib().ctl_ct_import(self.h, _p(a, _u64p), count, level, scale, C.byref(h)))
+        return Ciphertext(self, h)
+
+    def concat(self, cts):
+        arr = (C.c_void_p * len(cts))(*[c.h.value for c in cts])
+        h = C.c_void_p()
+        _check(lib().ctl_ct_concat(self.h, C.cast(arr, _pp), len(cts), C.byref(h)))
+        return Ciphertext(self, h)
+
+    # --- operations -------------------------------------------------------------
+    def _op(self, fn, *args):
+        h = C.c_void_p()
+        _check(fn(*args, C.byref(h)))
+        return Ciphertext(self, h)
+
+    def rotate(self, keys, ct, r):
+        return self._op(lib().ctl_rotate, self.h, keys.h, ct.h, r)
+
+    def rescale(self, ct):
+        return self._op(lib().ctl_rescale, self.h, ct.h)
+
+    def square(self, keys, ct):
+        return self._op(lib().ctl_eval_square, self.h, keys.h, ct.h)
+
+    def dense(self, keys, ct, W, bias=None):
+        W = np.ascontiguousarray(W, dtype=np.float64)
+        m, n = W.shape
+        bp = _p(np.ascontiguousarray(bias, dtype=np.float64), _dp) if bias is not None else None
+        return self._op(lib().ctl_eval_dense, self.h, keys.h, ct.h, _p(W, _dp), m, n, bp)
+
+    def dense_coeffs(self, keys, ct, pts, pt_scale, bias=None):
+        pts = np.ascontiguousarray(pts, dtype=np.int64)
+        bp = _p(np.ascontiguousarray(bias, dtype=np.int64), _i64p) if bias is not None else None
+        return self._op(lib().ctl_eval_dense_coeffs, self.h, keys.h, ct.h, _p(pts, _i64p), pts.shape[0], bp,
+                        pt_scale)
+
+    def replicate(self, keys, ct, t):
+        return self._op(lib().ctl_replicate, self.h, keys.h, ct.h, t)
+
+    def add(self, a, b):
+        return self._op(lib().ctl_add, self.h, a.h, b.h)
+
+    def mul_plain_coeffs(self, ct, pt, pt_scale):
+        pt = np.ascontiguousarray(pt, dtype=np.int64)
+        return self._op(lib().ctl_mul_plain_coeffs, self.h, ct.h, _p(pt, _i64p), pt_scale)
+
+    def ntt_dev(self, in_ptr, out_ptr, n_polys, limbs, inverse=False):
+        _check(lib().ctl_ntt_dev(self.h, C.c_void_p(in_ptr), C.c_void_p(out_ptr), n_polys, limbs, 1 if inverse else 0))
+
+    # --- statistics -------------------------------------------------------------
+    def stats_reset(self):
+        _check(lib().ctl_stats_reset(self.h))
+
+    def stats_enable_timing(self, on=True):
+        _check(lib().ctl_stats_enable_timing(self.h, 1 if on else 0))
+
+    def stats_launches(self):
+        return int(lib().ctl_stats_launches(self.h))
+
+    def stats_ops(self):
+        o = np.zeros(5, dtype=np.uint64)
+        _check(lib().ctl_stats_ops(self.h, _p(o, _u64p)))
+        return dict(zip(["rotations", "ptmul", "add", "relin", "rescale"], [int(x) for x in o]))
+
+    def stats_kernels(self):
+        n = lib().ctl_stats_kernel_classes()
+        ms = np.zeros(n)
+        la = np.zeros(n, dtype=np.uint64)
+        wk = np.zeros(n)
+        _check(lib().ctl_stats_kernels(self.h, _p(ms, _dp), _p(la, _u64p), _p(wk, _dp)))
+        return {lib().ctl_stats_class_name(i).decode(): {"ms": float(ms[i]), "launches": int(la[i]),
+                                                           "modmul": float(wk[i])} for i in range(n)}
+
+
+class Keys:
+    def __init__(self, ctx, h):
+        self.ctx, self.h = ctx, h
+
+    def export(self, key_id):
+        c = self.ctx
+        out = np.zeros((c.beta, 2, c.L + c.K, c.N), dtype=np.uint64)
+        _check(lib().ctl_keys_export(self.h, key_id, _p(out, _u64p), out.size))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ctl_keys_destroy(self.h)
+            self.h = None
+
+
+class Ciphertext:
+    def __init__(self, ctx, h):
+        self.ctx, self.h = ctx, h
+
+    def info(self):
+        lvl, cnt, sc = C.c_uint32(), C.c_uint32(), C.c_double()
+        _check(lib().ctl_ct_info(self.h, C.byref(lvl), C.byref(cnt), C.byref(sc)))
+        return lvl.value, cnt.value, sc.value
+
+    @property
+    def level(self):
+        return self.info()[0]
+
+    @property
+    def count(self):
+        return self.info()[1]
+
+    @property
+    def scale(self):
+        return self.info()[2]
+
+    def export(self):
+        lvl, cnt, _ = self.info()
+        out = np.zeros((cnt, 2, lvl, self.ctx.N), dtype=np.uint64)
+        _check(lib().ctl_ct_export(self.h, _p(out, _u64p), out.size))
+        return out
+
+    def slice(self, i):
+        h = C.c_void_p()
+        _check(lib().ctl_ct_slice(self.h, i, C.byref(h)))
+        return Ciphertext(self.ctx, h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ctl_ct_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Model:
+    """Frozen server layers: list of ("dense", W[, bias][, pt_coeffs]), ("square",), ("replicate", t)."""
+
+    def __init__(self, ctx, layers, in_level=None, in_scale=None):
+        self.ctx = ctx
+        self._keep = []
+        arr = (Layer * len(layers))()
+        for i, ly in enumerate(layers):
+            kind = ly[0]
+            if kind == "dense":
+                W = np.ascontiguousarray(ly[1], dtype=np.float64)
+                self._keep.append(W)
+                arr[i].kind = CTL_LAYER_DENSE
+                arr[i].m, arr[i].n = W.shape
+                arr[i].W = _p(W, _dp)
+                if len(ly) > 2 and ly[2] is not None:
+                    b = np.ascontiguousarray(ly[2], dtype=np.float64)
+                    self._keep.append(b)
+                    arr[i].bias = _p(b, _dp)
+                if len(ly) > 3 and ly[3] is not None:
+                    pc = np.ascontiguousarray(ly[3], dtype=np.int64)
+                    self._keep.append(pc)
+                    arr[i].pt_coeffs = _p(pc, _i64p)
+            elif kind == "square":
+                arr[i].kind = CTL_LAYER_SQUARE
+            elif kind == "replicate":
+                arr[i].kind = CTL_LAYER_REPLICATE
+                arr[i].rep_t = ly[1]
+            else:
+                raise ValueError(kind)
+        h = C.c_void_p()
+        _check(lib().ctl_model_create(ctx.h, arr, len(layers), ctx.L if in_level is None else in_level,
+                                      ctx.scale if in_scale is None else in_scale, C.byref(h)))
+        self.h = h
+        self._keep = []
+
+    def rotations(self):
+        n = C.c_uint32()
+        _check(lib().ctl_model_rotations(self.h, None, 0, C.byref(n)))
+        r = np.zeros(n.value, dtype=np.int32)
+        _check(lib().ctl_model_rotations(self.h, _p(r, _i32p), n.value, C.byref(n)))
+        return [int(x) for x in r]
+
+    def info(self):
+        lvl, sc, by = C.c_uint32(), C.c_double(), C.c_uint64()
+        _check(lib().ctl_model_info(self.h, C.byref(lvl), C.byref(sc), C.byref(by)))
+        return lvl.value, sc.value, by.value
+
+    def forward(self, keys, ct):
+        h = C.c_void_p()
+        _check(lib().ctl_model_forward(self.ctx.h, self.h, keys.h, ct.h, C.byref(h)))
+        return Ciphertext(self.ctx, h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ctl_model_destroy(self.h)
+            self.h = None

@@ -1,0 +1,408 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the CKKS oracle.
+
+Integer outputs (NTT limbs, keys, ciphertexts) must be bit-exact; decoded values must be
+within 1e-4 max-abs of the FP64 plaintext computation (at scale 2^40).  Bit-exact tests
+inject the oracle's integer plaintexts (two FP64 encoders may round a coefficient
+differently), and the GPU's own encoder is checked against the oracle's within one unit.
+"""
+import numpy as np
+import pytest
+
+from oracle import ckks_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU-only machines
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2205_11935_gb300 import ctl  # noqa: E402
+
+TOL = 1e-4
+
+# (N, q_bits, p_bits, dnum): cfg1-like (alpha 1), cfg3-like (alpha 2, two special primes),
+# cfg2-like (60-bit q0)
+PARAMS = {
+    "a1": (64, [50, 40, 40], [60], 3),
+    "a2": (256, [45, 45, 45, 45], [60, 60], 2),
+    "c2": (1024, [60, 40, 40, 40], [60], 4),
+}
+ROTS = [1, 2, 3, 5, 7, -4, -8, 12]
+
+
+class Pair:
+    def __init__(self, name, rots=ROTS, seed=3):
+        N, qb, pb, dnum = PARAMS[name]
+        self.o = O.Oracle(N, qb, pb, dnum=dnum, scale=2.0 ** 40)
+        self.o.keygen(rots, seed=seed)
+        self.g = ctl.Context(N, qb, pb, dnum=dnum, scale=2.0 ** 40)
+        self.k = self.g.keygen(rots, seed=seed)
+        self.N = N
+
+    def fresh(self, seed=11, z=None):
+        rng = np.random.default_rng(seed)
+        if z is None:
+            z = rng.uniform(-1, 1, self.N // 2)
+        m = self.o.encode(z)
+        return z, self.o.encrypt(m, seed)
+
+
+_cache = {}
+
+
+def pair(name):
+    if name not in _cache:
+        _cache[name] = Pair(name)
+    return _cache[name]
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).cuda()
+
+
+def from_dev(t, shape):
+    return t.cpu().numpy().view(np.uint64).reshape(shape)
+
+
+# ----------------------------------------------------------------------------- NTT
+@pytest.mark.parametrize("N", [16, 32, 64, 256, 1024, 4096])
+def test_ntt_matches_definition(N):
+    o = O.Oracle(N, [50, 40, 61], [60])
+    g = ctl.Context(N, [50, 40, 61], [60])
+    rng = np.random.default_rng(N)
+    limbs = 4
+    a = np.stack([rng.integers(0, q, N, dtype=np.uint64) for q in o.moduli[:limbs]])[None]
+    a[0, 0, :3] = 0
+    a[0, 1, :3] = np.uint64(o.moduli[1] - 1)  # edge values
+    x = to_dev(a)
+    y = torch.empty_like(x)
+    torch.cuda.synchronize()
+    g.ntt_dev(x.data_ptr(), y.data_ptr(), 1, limbs)
+    g.synchronize()
+    got = from_dev(y, a.shape)
+    check = range(limbs) if N <= 1024 else [0, 3]
+    for i in check:
+        assert np.array_equal(got[0, i], o.ntt_direct(i, a[0, i])), f"limb {i}"
+    z = torch.empty_like(x)
+    g.ntt_dev(y.data_ptr(), z.data_ptr(), 1, limbs, inverse=True)
+    g.synchronize()
+    assert np.array_equal(from_dev(z, a.shape), a)
+    g.close()
+
+
+def test_ntt_16384_convolution_and_batch():
+    """N = 16384 (the batched workload's ring): NTT-domain product equals the schoolbook
+    negacyclic product; a batch of polys transforms like each alone."""
+    N = 16384
+    o = O.Oracle(N, [45, 45], [60])
+    g = ctl.Context(N, [45, 45], [60])
+    rng = np.random.default_rng(5)
+    q = o.moduli[0]
+    a = rng.integers(0, q, N, dtype=np.uint64)
+    b = rng.integers(0, q, N, dtype=np.uint64)
+    ab = np.zeros((3, 3, N), dtype=np.uint64)  # 3 polys x 3 limbs
+    for p in range(3):
+        for i in range(3):
+            ab[p, i] = rng.integers(0, g.moduli[i], N, dtype=np.uint64)
+    ab[0, 0], ab[1, 0] = a, b
+    x = to_dev(ab)
+    y = torch.empty_like(x)
+    torch.cuda.synchronize()
+    g.ntt_dev(x.data_ptr(), y.data_ptr(), 3, 3)
+    g.synchronize()
+    Y = from_dev(y, ab.shape)
+    prod = np.array([(int(u) * int(v)) % q for u, v in zip(Y[0, 0], Y[1, 0])], dtype=np.uint64)
+    pd = to_dev(prod[None, None])
+    out = torch.empty_like(pd)
+    torch.cuda.synchronize()
+    g.ntt_dev(pd.data_ptr(), out.data_ptr(), 1, 1, inverse=True)
+    g.synchronize()
+    assert np.array_equal(from_dev(out, (N,)), o.polymul(0, a, b))
+    # each poly of the batch alone
+    for p in (1, 2):
+        x1 = to_dev(ab[p:p + 1])
+        y1 = torch.empty_like(x1)
+        torch.cuda.synchronize()
+        g.ntt_dev(x1.data_ptr(), y1.data_ptr(), 1, 3)
+        g.synchronize()
+        assert np.array_equal(from_dev(y1, (1, 3, N))[0], Y[p])
+    g.close()
+
+
+# ----------------------------------------------------------------------------- keys / encryption
+@pytest.mark.parametrize("name", list(PARAMS))
+def test_primes_and_keys_bit_exact(name):
+    P = pair(name)
+    assert P.g.moduli == P.o.moduli
+    for r in (None, 1, -4):
+        kid = 0 if r is None else P.o.galois_element(r)
+        assert np.array_equal(P.k.export(kid), P.o.key_export(kid)), f"key {kid}"
+
+
+@pytest.mark.parametrize("name", list(PARAMS))
+def test_encrypt_decrypt_bit_exact(name):
+    P = pair(name)
+    z, ct_o = P.fresh(21)
+    m = P.o.encode(z)
+    ct = P.g.encrypt_coeffs(P.k, m, 21)
+    assert np.array_equal(ct.export()[0], ct_o)
+    assert np.array_equal(P.g.decrypt_coeffs(P.k, ct), P.o.decrypt(ct_o))
+    assert np.max(np.abs(P.g.decrypt(P.k, ct, P.N // 2) - z)) < TOL
+
+
+@pytest.mark.parametrize("name", list(PARAMS))
+def test_encoder_within_one_unit(name):
+    P = pair(name)
+    rng = np.random.default_rng(22)
+    for scale in (2.0 ** 40, 2.0 ** 50):
+        z = rng.uniform(-1, 1, P.N // 2)
+        d = np.abs(P.g.encode(z, scale) - P.o.encode(z, scale))
+        assert d.max() <= 1
+    z = rng.uniform(-1, 1, P.N // 2)
+    m = P.o.encode(z).astype(np.float64)
+    assert np.max(np.abs(P.g.decode(m, P.N // 2) - P.o.decode(m, P.N // 2))) < 1e-9
+
+
+# ----------------------------------------------------------------------------- operations
+@pytest.mark.parametrize("name", list(PARAMS))
+@pytest.mark.parametrize("r", [1, 3, -4, 12, 0])
+def test_rotate_bit_exact(name, r):
+    P = pair(name)
+    z, ct_o = P.fresh(30)
+    ct = P.g.ct_import(ct_o, 2.0 ** 40)
+    out = P.g.rotate(P.k, ct, r)
+    assert np.array_equal(out.export()[0], P.o.rotate(ct_o, r))
+
+
+@pytest.mark.parametrize("name", list(PARAMS))
+def test_rotate_batch_and_lower_level(name):
+    P = pair(name)
+    cts = [P.fresh(40 + i)[1] for i in range(3)]
+    low = [P.o.rescale(c) for c in cts]
+    b = P.g.ct_import(np.stack(low), 2.0 ** 40 / P.o.moduli[len(P.o.moduli) - P.o.K - 1])
+    out = P.g.rotate(P.k, b, 5).export()
+    for i in range(3):
+        assert np.array_equal(out[i], P.o.rotate(low[i], 5))
+
+
+@pytest.mark.parametrize("name", list(PARAMS))
+def test_rescale_bit_exact(name):
+    P = pair(name)
+    _, ct_o = P.fresh(50)
+    ct = P.g.ct_import(ct_o, 2.0 ** 40)
+    r1 = P.g.rescale(ct)
+    e1 = P.o.rescale(ct_o)
+    assert np.array_equal(r1.export()[0], e1)
+    r2 = P.g.rescale(r1)
+    assert np.array_equal(r2.export()[0], P.o.rescale(e1))
+
+
+@pytest.mark.parametrize("name", list(PARAMS))
+def test_square_bit_exact_and_fp64(name):
+    P = pair(name)
+    z, ct_o = P.fresh(60)
+    ct = P.g.ct_import(ct_o, 2.0 ** 40)
+    sq = P.g.square(P.k, ct)
+    exp = P.o.square(ct_o)
+    assert np.array_equal(sq.export()[0], exp)
+    assert np.max(np.abs(P.g.decrypt(P.k, sq, P.N // 2) - z * z)) < TOL
+
+
+@pytest.mark.parametrize("name", list(PARAMS))
+def test_mul_plain_and_add(name):
+    P = pair(name)
+    z, ct_o = P.fresh(65)
+    pt = P.o.encode(np.linspace(-1, 1, P.N // 2), 2.0 ** 30)
+    ct = P.g.ct_import(ct_o, 2.0 ** 40)
+    assert np.array_equal(P.g.mul_plain_coeffs(ct, pt, 2.0 ** 30).export()[0], P.o.mul_plain(ct_o, pt))
+    assert np.array_equal(P.g.add(ct, ct).export()[0], P.o.add(ct_o, ct_o))
+
+
+def dense_case(P, m, n, seed):
+    rng = np.random.default_rng(seed)
+    t = O.Oracle.bsgs_t(m, n)
+    W = rng.normal(0, 1 / np.sqrt(n), (m, n))
+    x = rng.uniform(-1, 1, n)
+    slots = np.zeros(P.N // 2)
+    slots[:n] = x
+    slots[t:t + n] = x
+    z, ct_o = P.fresh(seed, z=slots)
+    return W, x, t, ct_o
+
+
+@pytest.mark.parametrize("name,m,n", [("a1", 8, 16), ("a1", 5, 12), ("a2", 16, 16), ("c2", 32, 64), ("c2", 3, 1)])
+def test_dense_bit_exact_injected_and_fp64(name, m, n):
+    P = pair(name)
+    t = O.Oracle.bsgs_t(m, n)
+    t1 = O.Oracle.bsgs_t1(t)
+    rots = sorted(set(list(range(1, t1)) + [k * t1 for k in range(1, t // t1)]))
+    o = O.Oracle(P.N, *PARAMS[name][1:3], dnum=PARAMS[name][3], scale=2.0 ** 40)
+    o.keygen(rots, seed=3)
+    g = P.g
+    k = g.keygen(rots, seed=3)
+    W, x, t, ct_o = dense_case(P, m, n, 70 + m)
+    lvl = ct_o.shape[1]
+    sc = o.dense_scale(lvl, o.scale)
+    pts = o.encode_diagonals(W, sc)
+    exp, cnt = o.dense(ct_o, pts)
+    ct = g.ct_import(ct_o, 2.0 ** 40)
+    g.stats_reset()
+    out = g.dense_coeffs(k, ct, pts, sc)
+    ops = g.stats_ops()
+    assert np.array_equal(out.export()[0], exp)
+    assert ops["rotations"] == cnt[0] and ops["ptmul"] == cnt[1] and ops["add"] == cnt[2]
+    # the library's own diagonal encoding: decoded within tolerance of FP64
+    out2 = g.dense(k, ct, W)
+    y = g.decrypt(k, out2, P.N // 2)
+    assert np.max(np.abs(y[:m] - W @ x)) < TOL
+    assert np.max(np.abs(y[m:])) < TOL
+    k.close()
+
+
+@pytest.mark.parametrize("name", list(PARAMS))
+def test_replicate_bit_exact(name):
+    P = pair(name)
+    _, ct_o = P.fresh(80)
+    ct = P.g.ct_import(ct_o, 2.0 ** 40)
+    assert np.array_equal(P.g.replicate(P.k, ct, 8).export()[0], P.o.replicate(ct_o, 8))
+
+
+# ----------------------------------------------------------------------------- networks
+def network_case(N, q_bits, p_bits, dnum, dims, seed=90, sizes_only=False):
+    """dense(d0->d1) -> x^2 -> replicate -> dense(d1->d2) ... with FP64 reference."""
+    rng = np.random.default_rng(seed)
+    Ws = [rng.normal(0, 1 / np.sqrt(dims[i]), (dims[i + 1], dims[i])) for i in range(len(dims) - 1)]
+    x = rng.uniform(-1, 1, dims[0])
+    layers = []
+    ref = x.copy()
+    for i, W in enumerate(Ws):
+        layers.append(("dense", W))
+        ref = W @ ref
+        if i + 1 < len(Ws):
+            layers.append(("square",))
+            ref = ref * ref
+            t_next = O.Oracle.bsgs_t(Ws[i + 1].shape[0], Ws[i + 1].shape[1])
+            layers.append(("replicate", t_next))
+    t0 = O.Oracle.bsgs_t(Ws[0].shape[0], Ws[0].shape[1])
+    slots = np.zeros(N // 2)
+    slots[:dims[0]] = x
+    slots[t0:t0 + dims[0]] = x
+    return layers, slots, ref
+
+
+def oracle_forward(o, ct, layers):
+    sc = o.scale
+    for ly in layers:
+        lvl = ct.shape[1]
+        if ly[0] == "dense":
+            s = o.dense_scale(lvl, sc)
+            ct = o.dense(ct, o.encode_diagonals(ly[1], s))[0]
+            sc = o.scale
+        elif ly[0] == "square":
+            ct = o.square(ct)
+            sc = o.square_scale(lvl, sc)
+        else:
+            ct = o.replicate(ct, ly[1])
+    return ct, sc
+
+
+def inject(o, layers):
+    """Same layers with the oracle's diagonal coefficients attached."""
+    out, sc, lvl = [], o.scale, o.L
+    for ly in layers:
+        if ly[0] == "dense":
+            s = o.dense_scale(lvl, sc)
+            out.append(("dense", ly[1], None, o.encode_diagonals(ly[1], s)))
+            sc = o.scale
+            lvl -= 1
+        elif ly[0] == "square":
+            out.append(ly)
+            sc = o.square_scale(lvl, sc)
+            lvl -= 1
+        else:
+            out.append(ly)
+    return out
+
+
+@pytest.mark.parametrize("N,qb,pb,dnum,dims", [
+    (256, [60, 40, 40, 40], [60], 4, [16, 8, 4]),
+    (512, [45, 45, 45, 45, 45, 45], [60, 60], 3, [32, 16, 16, 8]),
+])
+def test_network_bit_exact_and_fp64(N, qb, pb, dnum, dims):
+    layers, slots, ref = network_case(N, qb, pb, dnum, dims)
+    g = ctl.Context(N, qb, pb, dnum=dnum, scale=2.0 ** 40)
+    o = O.Oracle(N, qb, pb, dnum=dnum, scale=2.0 ** 40)
+    model = ctl.Model(g, inject(o, layers))
+    rots = model.rotations()
+    o.keygen(rots, seed=3)
+    k = g.keygen(rots, seed=3)
+    ct_o = o.encrypt(o.encode(slots), 4)
+    exp, sc = oracle_forward(o, ct_o, layers)
+    out = model.forward(k, g.ct_import(ct_o, 2.0 ** 40))
+    assert np.array_equal(out.export()[0], exp)
+    y = g.decrypt(k, out, len(ref))
+    assert np.max(np.abs(y - ref)) < TOL
+    # the model with the library's own encoding
+    model2 = ctl.Model(g, layers)
+    y2 = g.decrypt(k, model2.forward(k, g.encrypt(k, slots, 4)), len(ref))
+    assert np.max(np.abs(y2 - ref)) < TOL
+
+
+def test_cfg1_full_size_bit_exact():
+    """N = 4096, q {50,40,40} + 60-bit special prime, dense 64->32 then x^2 (single query)."""
+    N, qb, pb = 4096, [50, 40, 40], [60]
+    rng = np.random.default_rng(1)
+    W = rng.normal(0, 1 / 8, (32, 64))
+    x = rng.uniform(-1, 1, 64)
+    slots = np.zeros(N // 2)
+    slots[:64] = x
+    slots[64:128] = x
+    layers = [("dense", W), ("square",)]
+    g = ctl.Context(N, qb, pb, scale=2.0 ** 40)
+    o = O.Oracle(N, qb, pb, scale=2.0 ** 40)
+    model = ctl.Model(g, inject(o, layers))
+    rots = model.rotations()
+    o.keygen(rots, seed=3)
+    k = g.keygen(rots, seed=3)
+    ct_o = o.encrypt(o.encode(slots), 4)
+    exp, _ = oracle_forward(o, ct_o, layers)
+    out = model.forward(k, g.ct_import(ct_o, 2.0 ** 40))
+    assert np.array_equal(out.export()[0], exp)
+    assert np.max(np.abs(g.decrypt(k, out, 32) - (W @ x) ** 2)) < TOL
+
+
+def test_batch_equals_single():
+    N, qb, pb = 1024, [60, 40, 40, 40], [60]
+    layers, slots, ref = network_case(N, qb, pb, 4, [32, 16, 8])
+    g = ctl.Context(N, qb, pb, scale=2.0 ** 40)
+    model = ctl.Model(g, layers)
+    k = g.keygen(model.rotations(), seed=3)
+    rng = np.random.default_rng(7)
+    singles = []
+    for i in range(4):
+        s = slots.copy() if i == 0 else np.concatenate([rng.uniform(-1, 1, 64), np.zeros(N // 2 - 64)])
+        singles.append(g.encrypt(k, s, 100 + i))
+    batch = g.concat(singles)
+    outb = model.forward(k, batch).export()
+    for i, s in enumerate(singles):
+        assert np.array_equal(model.forward(k, s).export()[0], outb[i])
+
+
+def test_error_codes():
+    P = pair("a1")
+    _, ct_o = P.fresh(99)
+    ct = P.g.ct_import(ct_o, 2.0 ** 40)
+    with pytest.raises(ctl.CtlError) as e:
+        P.g.rotate(P.k, ct, 9)  # no key for 9
+    assert e.value.code == -4
+    low = P.g.rescale(P.g.rescale(ct))
+    with pytest.raises(ctl.CtlError) as e:
+        P.g.rescale(low)
+    assert e.value.code == -2
+    other = P.g.ct_import(ct_o, 2.0 ** 39)
+    with pytest.raises(ctl.CtlError) as e:
+        P.g.add(ct, other)
+    assert e.value.code == -3
+    with pytest.raises(ctl.CtlError) as e:
+        ctl.Context(100, [40], [60])
+    assert e.value.code == -1
