@@ -1,0 +1,400 @@
+"""Benchmark: encrypted forwards per second of CryptoTL's server step (ClassifyHE).
+
+Workload (default "batched"): 256 CKKS ciphertexts at N = 16384 (8 x 45-bit data
+primes, 2 x 60-bit special primes, dnum = 4, scale 2^40) under one client's keys,
+through the frozen layers dense 1024->256, x^2, dense 256->256, x^2, dense 256->64
+(Sec. 3.1 layer algorithms; diagonal mat-vec of Eq. (bsgs) with hoisted baby steps).
+Synthetic data: inputs ~U[-1,1], weights ~N(0, 1/fan_in), fixed seeds.
+
+One JSON line on rank 0:
+  value    forwards/s with the input batch resident in HBM (CUDA events on the library's
+           stream, max over ranks);
+  e2e      forwards/s through the C-ABI with host buffers: import (H2D) + forward +
+           export (D2H) of every step inside the timed region;
+  roofline the dominant kernel class against the integer-multiply (IMAD) peak
+           (152 SMs x 64 IMAD/clk x clock), counted in 64-bit Shoup modular
+           multiplications at their measured IMAD cost;
+  cpu_baseline the CKKS oracle on the host cores, on a bounded sample (one rotation,
+           one plaintext product and one rescale at the top level), extrapolated by the
+           forward's operation counts.
+``--impl reference`` times that oracle leg alone on this workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SM_COUNT = 152
+IMAD_PER_CLK_SM = 64          # 32-bit integer multiply-add lanes per SM per clock
+SHOUP_IMAD = 17.4             # IMAD issue slots of one 64-bit Shoup modmul (microbenchmark)
+MAX_SM_MHZ = 2070.0
+
+WORKLOADS = {
+    "batched": dict(N=16384, q=[45] * 8, p=[60, 60], dnum=4, batch=256, dims=[1024, 256, 256, 64],
+                    desc="256 ciphertexts, N=16384, 8x45-bit q + 2x60-bit p, dnum=4, scale 2^40; "
+                         "dense 1024->256, x^2, dense 256->256, x^2, dense 256->64"),
+    "single8192": dict(N=8192, q=[60, 40, 40, 40], p=[60], dnum=4, batch=1, dims=[512, 128, 64],
+                       desc="1 ciphertext, N=8192, q {60,40,40,40} + 60-bit p, scale 2^40; "
+                            "dense 512->128, x^2, dense 128->64"),
+    "single4096": dict(N=4096, q=[50, 40, 40], p=[60], dnum=3, batch=1, dims=[64, 32],
+                       desc="1 ciphertext, N=4096, q {50,40,40} + 60-bit p, scale 2^40; dense 64->32, x^2"),
+}
+
+
+def bsgs_t(m, n):
+    t = 1
+    while t < m or t < n:
+        t <<= 1
+    return t
+
+
+def layers_for(dims, square_last):
+    rng = np.random.default_rng(1)
+    Ws = [rng.normal(0, 1 / np.sqrt(dims[i]), (dims[i + 1], dims[i])) for i in range(len(dims) - 1)]
+    layers = []
+    for i, W in enumerate(Ws):
+        layers.append(("dense", W))
+        if i + 1 < len(Ws):
+            layers.append(("square",))
+            layers.append(("replicate", bsgs_t(*Ws[i + 1].shape)))
+        elif square_last:
+            layers.append(("square",))
+    return layers, Ws
+
+
+def inputs_for(N, dims, B, t0):
+    rng = np.random.default_rng(2)
+    xs = rng.uniform(-1, 1, (B, dims[0]))
+    slots = np.zeros((B, N // 2))
+    slots[:, :dims[0]] = xs
+    slots[:, t0:t0 + dims[0]] = xs
+    return xs, slots
+
+
+def fp64_forward(Ws, x, square_last):
+    h = x
+    for i, W in enumerate(Ws):
+        h = W @ h
+        if i + 1 < len(Ws) or square_last:
+            h = h * h
+    return h
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([s.strip() for s in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        sm = []
+        mx = MAX_SM_MHZ
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            try:
+                sm.append(float(s[0]))
+                mx = float(s[1])
+                for n, v in zip(names, s[4:8]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_sample(wl):
+    """Times the oracle on one rotation, one plaintext product and one rescale at the top
+    level of the workload's ring, and extrapolates a forward by its operation counts.
+    Returns (seconds per forward estimate, description, cores)."""
+    from oracle import ckks_oracle as O
+
+    N, q, p, dnum = wl["N"], wl["q"], wl["p"], wl["dnum"]
+    o = O.Oracle(N, q, p, dnum=dnum, scale=2.0 ** 40)
+    t0 = time.perf_counter()
+    o.keygen([1], seed=3)
+    t_keygen = time.perf_counter() - t0
+    rng = np.random.default_rng(9)
+    L = len(q)
+    ct = np.stack([np.stack([rng.integers(0, m, N, dtype=np.uint64) for m in o.moduli[:L]]) for _ in range(2)])
+    t0 = time.perf_counter()
+    o.rotate(ct, 1)
+    t_rot = time.perf_counter() - t0
+    pt = rng.integers(-2 ** 40, 2 ** 40, N, dtype=np.int64)
+    t0 = time.perf_counter()
+    o.mul_plain(ct, pt)
+    t_pt = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    o.rescale(ct)
+    t_rs = time.perf_counter() - t0
+    # operation counts of the forward, each scaled by its level relative to the top
+    K = len(p)
+    alpha = (L + dnum - 1) // dnum
+    est = 0.0
+    lvl = L
+    dims = wl["dims"]
+
+    def ks_scale(l):
+        nd = (l + alpha - 1) // alpha
+        ndL = (L + alpha - 1) // alpha
+        return (nd * (l + K)) / (ndL * (L + K))
+
+    for i in range(len(dims) - 1):
+        t = bsgs_t(dims[i + 1], dims[i])
+        lg = t.bit_length() - 1
+        t1 = 1 << ((lg + 1) // 2)
+        t2 = t // t1
+        est += (t1 + t2 - 2) * t_rot * ks_scale(lvl) + t * t_pt * lvl / L + t_rs * lvl / L
+        lvl -= 1
+        if i + 1 < len(dims) - 1 or wl is WORKLOADS["single4096"]:
+            # square: 3 products per limb + relinearisation + rescale; then replicate
+            est += 1.5 * t_pt * lvl / L + t_rot * ks_scale(lvl) + t_rs * lvl / L
+            lvl -= 1
+            if i + 1 < len(dims) - 1:
+                est += t_rot * ks_scale(lvl)
+    cores = os.cpu_count()
+    desc = (f"oracle on {cores} host threads: 1 rotation ({t_rot:.2f} s), 1 plaintext product ({t_pt:.2f} s), "
+            f"1 rescale ({t_rs:.2f} s) at N={N}, level {L}, plus one Galois key ({t_keygen:.2f} s); "
+            f"forward extrapolated by operation counts and limb counts")
+    return est, desc, cores, t_rot + t_pt + t_rs + t_keygen
+
+
+def run_reference(args, wl, rank, world):
+    if rank != 0:
+        return
+    times = []
+    desc, cores = "", os.cpu_count()
+    for s in range(args.warmup + args.steps):
+        est, desc, cores, spent = cpu_oracle_sample(wl)
+        if s >= args.warmup:
+            times.append(est)
+        if spent * (args.warmup + args.steps) > 240:  # keep the whole run within minutes
+            break
+    est = statistics.median(times) if times else est
+    value = wl["batch"] / (est * wl["batch"])
+    line = {"impl": "reference", "metric": "encrypted forwards/sec (batched)", "value": value,
+            "unit": "forwards/s", "n_gpus": args.gpus, "steps": len(times), "warmup": args.warmup,
+            "ms_per_step": est * 1e3 * wl["batch"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": wl["desc"], "batch": wl["batch"]},
+            "cpu_baseline": {"value": value, "unit": "forwards/s", "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": "forwards/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batched", choices=list(WORKLOADS))
+    ap.add_argument("--batch", type=int, default=0, help="override the batch size")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    wl = dict(WORKLOADS[args.workload])
+    if args.batch:
+        wl["batch"] = args.batch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, wl, rank, world)
+        return
+
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2205_11935_gb300 import ctl
+
+    N, B = wl["N"], wl["batch"]
+    square_last = args.workload == "single4096"
+    layers, Ws = layers_for(wl["dims"], square_last)
+    t0 = bsgs_t(Ws[0].shape[0], Ws[0].shape[1])
+    stream = torch.cuda.Stream()
+    ctx = ctl.Context(N, wl["q"], wl["p"], dnum=wl["dnum"], scale=2.0 ** 40)
+    ctx.set_stream(stream.cuda_stream)
+    model = ctl.Model(ctx, layers)
+    keys = ctx.keygen(model.rotations(), seed=3)
+    xs, slots = inputs_for(N, wl["dims"], B, t0)
+    cts = [ctx.encrypt(keys, slots[i], 4 + i) for i in range(B)]
+    batch = ctx.concat(cts)
+    for c in cts:
+        c.close()
+    out_level, out_scale, model_bytes = model.info()
+
+    # correctness of the measured configuration: decoded outputs vs FP64 on a sample
+    out = model.forward(keys, batch)
+    check_idx = sorted({0, B // 2, B - 1})
+    max_err = 0.0
+    for i in check_idx:
+        yi = ctx.decrypt(keys, out.slice(i), wl["dims"][-1])
+        max_err = max(max_err, float(np.max(np.abs(yi - fp64_forward(Ws, xs[i], square_last)))))
+    out.close()
+
+    def step():
+        o = model.forward(keys, batch)
+        o.close()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # timed region: device-resident inputs
+    ctx.stats_reset()
+    ctx.stats_enable_timing(True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    for s in range(args.steps):
+        step()
+        ev[s + 1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    step_ms = [ev[s].elapsed_time(ev[s + 1]) for s in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    launches = ctx.stats_launches()
+    kern = ctx.stats_kernels()
+    ops = ctx.stats_ops()
+    ctx.stats_enable_timing(False)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * B * args.steps / (total_ms / 1e3)
+
+    # end to end through host buffers
+    e2e = None
+    if not args.no_e2e:
+        host_in = batch.export()  # coefficient form, as a client would send it
+        pinned_in = torch.from_numpy(host_in.view(np.int64)).pin_memory()
+        h2d = host_in.nbytes
+        out_words = B * 2 * out_level * N
+        pinned_out = torch.empty(out_words, dtype=torch.int64).pin_memory()
+        import ctypes as C
+
+        def e2e_step():
+            h = C.c_void_p()
+            ctl._check(ctl.lib().ctl_ct_import(ctx.h, C.cast(pinned_in.data_ptr(), ctl._u64p), B, len(wl["q"]),
+                                               2.0 ** 40, C.byref(h)))
+            ci = ctl.Ciphertext(ctx, h)
+            co = model.forward(keys, ci)
+            ctl._check(ctl.lib().ctl_ct_export(co.h, C.cast(pinned_out.data_ptr(), ctl._u64p), out_words))
+            ci.close()
+            co.close()
+
+        e2e_step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t_start = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t_start
+        if dist:
+            t = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * B * args.steps / e2e_s, "unit": "forwards/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(out_words * 8)}
+
+    # roofline of the dominant kernel class (integer-multiply bound)
+    mhz = clocks["sm_mhz"] or MAX_SM_MHZ
+    peak_modmul = SM_COUNT * IMAD_PER_CLK_SM * MAX_SM_MHZ * 1e6 / SHOUP_IMAD
+    classes = {k: v for k, v in kern.items() if v["launches"]}
+    dom = max(classes, key=lambda k: classes[k]["ms"])
+    d = classes[dom]
+    achieved = d["modmul"] / (d["ms"] / 1e3) if d["ms"] else 0.0
+    per_class = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
+                     "share": v["ms"] / max(sum(x["ms"] for x in classes.values()), 1e-9),
+                     "gmodmul_s": (v["modmul"] / (v["ms"] / 1e3) / 1e9) if v["ms"] else 0.0,
+                     "frac_of_alu_peak": (v["modmul"] / (v["ms"] / 1e3) / peak_modmul) if v["ms"] else 0.0}
+                 for k, v in classes.items()}
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved / 1e9, "peak": peak_modmul / 1e9,
+                "unit": "Gmodmul/s", "frac": achieved / peak_modmul, "traffic": None,
+                "peak_basis": f"{SM_COUNT} SMs x {IMAD_PER_CLK_SM} IMAD/clk x {MAX_SM_MHZ:.0f} MHz / "
+                              f"{SHOUP_IMAD} IMAD per Shoup modmul (measured)",
+                "avg_launch_ms": d["ms"] / max(d["launches"], 1), "classes": per_class}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        est, desc, cores, _ = cpu_oracle_sample(wl)
+        cpu = {"value": 1.0 / est, "unit": "forwards/s", "cores": cores, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        lat = sorted(step_ms)
+        line = {"metric": "encrypted forwards/sec (batched)", "value": value, "unit": "forwards/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+                "data": "synthetic",
+                "config": {"workload": wl["desc"], "batch_per_gpu": B, "N": N, "parallelism": f"replicas x{world}",
+                           "l2": "inputs larger than L2 (working set of tens of GB per step)",
+                           "max_abs_err_vs_fp64": max_err},
+                "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                               "per": f"batch of {B}"},
+                "ops_per_step": {k: v / args.steps for k, v in ops.items()},
+                "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
+                "gpu_launches": int(launches)}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
