@@ -163,7 +163,8 @@ static int build_tables(ctl_context* c) {
   const uint32_t N = c->N, L = c->L, K = c->K, LK = L + K;
   const std::vector<u64>& m = c->moduli;
   // per-prime constants and twiddles
-  std::vector<u64> tw((size_t)LK * N), tws((size_t)LK * N), itw((size_t)LK * N), itws((size_t)LK * N);
+  // interleaved (w, w') pairs: tw2[(i*N + k)*2 + {0,1}]
+  std::vector<u64> tw2((size_t)LK * N * 2), itw2((size_t)LK * N * 2);
   c->h_primes.resize(LK);
   for (uint32_t i = 0; i < LK; i++) {
     const u64 q = m[i];
@@ -171,10 +172,10 @@ static int build_tables(ctl_context* c) {
     for (uint32_t k = 0; k < N; k++) {
       const uint32_t e = h_bitrev(k, c->logN);
       const u64 w = h_powmod(psi, e, q), wi = h_powmod(psi_inv, e, q);
-      tw[(size_t)i * N + k] = w;
-      tws[(size_t)i * N + k] = h_shoup(w, q);
-      itw[(size_t)i * N + k] = wi;
-      itws[(size_t)i * N + k] = h_shoup(wi, q);
+      tw2[((size_t)i * N + k) * 2] = w;
+      tw2[((size_t)i * N + k) * 2 + 1] = h_shoup(w, q);
+      itw2[((size_t)i * N + k) * 2] = wi;
+      itw2[((size_t)i * N + k) * 2 + 1] = h_shoup(wi, q);
     }
     DPrime& P = c->h_primes[i];
     P.q = q;
@@ -183,8 +184,10 @@ static int build_tables(ctl_context* c) {
     P.r2 = h_mulmod(P.rmod, P.rmod, q);
     P.ninv = h_invmod(N % q, q);
     P.ninv_sh = h_shoup(P.ninv, q);
-    P.iw1 = h_mulmod(itw[(size_t)i * N + 1], P.ninv, q);
+    P.iw1 = h_mulmod(itw2[((size_t)i * N + 1) * 2], P.ninv, q);
     P.iw1_sh = h_shoup(P.iw1, q);
+    const unsigned bits = 64 - __builtin_clzll(q);
+    P.split = bits <= 54 ? (bits + 1) / 2 : 0;
   }
   // conversion tables, packed into one host vector then copied to the device
   std::vector<u64> tab;
@@ -253,16 +256,12 @@ static int build_tables(ctl_context* c) {
   const size_t twb = (size_t)LK * N * sizeof(u64);
   int rc;
   if ((rc = cuda_check(cudaMalloc(&c->d_primes, LK * sizeof(DPrime)), "cudaMalloc primes"))) return rc;
-  if ((rc = cuda_check(cudaMalloc(&c->d_tw, 4 * twb), "cudaMalloc twiddles"))) return rc;
-  c->d_tw_sh = c->d_tw + (size_t)LK * N;
-  c->d_itw = c->d_tw_sh + (size_t)LK * N;
-  c->d_itw_sh = c->d_itw + (size_t)LK * N;
+  if ((rc = cuda_check(cudaMalloc(&c->d_tw2, 4 * twb), "cudaMalloc twiddles"))) return rc;
+  c->d_itw2 = c->d_tw2 + (size_t)LK * N * 2;
   if ((rc = cuda_check(cudaMalloc(&c->d_tables, tab.size() * sizeof(u64)), "cudaMalloc tables"))) return rc;
   cudaMemcpy(c->d_primes, c->h_primes.data(), LK * sizeof(DPrime), cudaMemcpyHostToDevice);
-  cudaMemcpy(c->d_tw, tw.data(), twb, cudaMemcpyHostToDevice);
-  cudaMemcpy(c->d_tw_sh, tws.data(), twb, cudaMemcpyHostToDevice);
-  cudaMemcpy(c->d_itw, itw.data(), twb, cudaMemcpyHostToDevice);
-  cudaMemcpy(c->d_itw_sh, itws.data(), twb, cudaMemcpyHostToDevice);
+  cudaMemcpy(c->d_tw2, tw2.data(), 2 * twb, cudaMemcpyHostToDevice);
+  cudaMemcpy(c->d_itw2, itw2.data(), 2 * twb, cudaMemcpyHostToDevice);
   cudaMemcpy(c->d_tables, tab.data(), tab.size() * sizeof(u64), cudaMemcpyHostToDevice);
   auto mk = [&](const Pending& p) {
     ConvTab t;
@@ -346,7 +345,7 @@ extern "C" void ctl_context_destroy(ctl_context* c) {
   }
   for (auto e : c->timing.pool) cudaEventDestroy(e);
   cudaFree(c->d_primes);
-  cudaFree(c->d_tw);
+  cudaFree(c->d_tw2);
   cudaFree(c->d_tables);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -1091,6 +1090,7 @@ int dense_prepare(ctl_context* c, DenseLayer& D, const double* W, const double* 
     src = enc.data();
   }
   if (int rc = upload_plaintexts(c, src, D.t, lvl, true, &D.diag)) return rc;
+  launch_split_limbs(c, D.diag, (int)D.t, (int)lvl);
   std::vector<i64> benc;
   const i64* bsrc = (const i64*)bias_in;
   if (!bsrc && bias) {

@@ -26,6 +26,7 @@ struct DPrime {
   u64 rmod;     // 2^64 mod q: mulmod_mont(x, rmod) = x mod q for any 64-bit x
   u64 ninv, ninv_sh;  // N^-1 mod q and its Shoup companion
   u64 iw1, iw1_sh;    // (psi^-1)^{bitrev(1)} * N^-1: the folded last inverse twiddle
+  u64 split;          // w = ceil(bits(q)/2) when q < 2^54 (operands split into w-bit halves), else 0
 };
 
 // Fast base conversion from a set of source primes S to target primes:
@@ -145,10 +146,8 @@ struct ctl_context {
   void* alloc_user = nullptr;
   // device tables
   ctl::DPrime* d_primes = nullptr;
-  ctl::u64* d_tw = nullptr;      // [L+K][N] forward twiddles psi^{bitrev(i)}
-  ctl::u64* d_tw_sh = nullptr;
-  ctl::u64* d_itw = nullptr;     // [L+K][N] inverse twiddles (psi^-1)^{bitrev(i)}
-  ctl::u64* d_itw_sh = nullptr;
+  ctl::u64* d_tw2 = nullptr;     // [L+K][N][2] forward twiddles (psi^{bitrev(i)}, Shoup companion)
+  ctl::u64* d_itw2 = nullptr;    // [L+K][N][2] inverse twiddles ((psi^-1)^{bitrev(i)}, Shoup companion)
   ctl::u64* d_tables = nullptr;  // conversion / rescale constants
   std::vector<ctl::ConvTab> modup_tabs;      // index (lvl-1)*beta + d
   std::vector<ctl::RescaleTab> rescale_tabs; // index lvl (valid for lvl >= 2)
@@ -255,5 +254,8 @@ void launch_automorph(ctl_context* c, const u64* in, u64* out, int n_polys, int 
 //   inner[k][b][p][i] = sum_j diag[k*t1+j][i] * baby[j][b][p][i]   (diag in Montgomery form)
 void launch_bsgs_inner(ctl_context* c, const u64* baby, const u64* diag, size_t diag_stride, u64* inner, int t1,
                        int t2, int nb, int lvl);
+// Re-pack Montgomery-form plaintext limbs [cnt][lvl][N] for the split product: on limbs
+// whose prime has split width w > 0, v -> (v >> w) << 32 | (v & (2^w - 1)).
+void launch_split_limbs(ctl_context* c, u64* data, int cnt, int lvl);
 
 }  // namespace ctl

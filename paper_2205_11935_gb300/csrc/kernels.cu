@@ -280,37 +280,96 @@ void launch_automorph(ctl_context* c, const u64* in, u64* out, int n_polys, int 
 // sum of nd products stays below q * 2^64 when nd * q < 2^64 (REDC precondition); the
 // CHECK variant reduces the high word on the way for larger digit counts.
 // ---------------------------------------------------------------------------------
-template <bool CHECK>
-__global__ void k_key_ip(const u64* __restrict__ ext, size_t ext_r, const RotList rl, u64* __restrict__ acc,
-                         const DPrime* __restrict__ pr, int logN, int nb, int nd, int E, int lvl, int L, int LK) {
+// One thread per (limb i, coefficient k) of rotation r = blockIdx.y keeps the 2*nd key
+// values in registers and sweeps the batch, so each key value leaves HBM once per
+// launch.  The automorphism gather stays inside an aligned 32-element block for the 32
+// consecutive k of a warp (bit-reversed order), so it touches as many sectors as a
+// coalesced load.  On limbs with a split width w the products use w-bit halves
+// (4 32x32->64 multiply-adds, no carries); otherwise 64x64->128 products with the high
+// word kept below q.
+__device__ __forceinline__ u64 split_of(u64 v, int w, u64 mask) { return ((v >> w) << 32) | (v & mask); }
+__device__ __forceinline__ void smac(u64& a00, u64& a01, u64& a11, uint32_t x0, uint32_t x1, u64 k) {
+  const uint32_t k0 = (uint32_t)k, k1 = (uint32_t)(k >> 32);
+  a00 += (u64)x0 * k0;
+  a01 += (u64)x0 * k1;
+  a01 += (u64)x1 * k0;
+  a11 += (u64)x1 * k1;
+}
+__device__ __forceinline__ u64 split_redc(u64 a00, u64 a01, u64 a11, int w, u64 q, u64 qinv) {
+  u64 lo = a00, hi = 0;
+  const u64 t_lo = a01 << w, t_hi = a01 >> (64 - w);
+  lo += t_lo;
+  hi += t_hi + (lo < t_lo);
+  const u64 u_lo = a11 << (2 * w), u_hi = a11 >> (64 - 2 * w);
+  lo += u_lo;
+  hi += u_hi + (lo < u_lo);
+  return redc(hi, lo, q, qinv);
+}
+
+template <int ND>
+__global__ void __launch_bounds__(256) k_key_ip(const u64* __restrict__ ext, size_t ext_r,
+                                                const __grid_constant__ RotList rl, u64* __restrict__ acc,
+                                                const DPrime* __restrict__ pr, int logN, int nb, int nd, int E,
+                                                int lvl, int L, int LK) {
   const size_t N = (size_t)1 << logN;
-  const size_t per_rot = (size_t)nb * E * N;
+  const size_t EN = (size_t)E << logN;
+  const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (idx >= EN) return;
   const int r = blockIdx.y;
+  const int i = (int)(idx >> logN);
+  const uint32_t k = (uint32_t)(idx & (N - 1));
+  const int pi = i < lvl ? i : L + (i - lvl);
+  const DPrime P = pr[pi];
+  const int w = (int)P.split;
+  const u64 mask = w ? (1ull << w) - 1 : 0;
   const u64* key = rl.key[r];
   const u64 g = rl.g[r];
-  const u64* ex = ext + (size_t)r * ext_r;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < per_rot; idx += (size_t)gridDim.x * blockDim.x) {
-    const size_t b = idx / (E * N), rr = idx % (E * N);
-    const int i = (int)(rr >> logN);
-    const uint32_t k = (uint32_t)(rr & (N - 1));
-    const int pi = i < lvl ? i : L + (i - lvl);
-    const DPrime P = pr[pi];
-    const uint32_t ks = g == 1 ? k : auto_src_k(k, g, logN);
-    u64 lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
-    for (int d = 0; d < nd; d++) {
-      const u64 x = ex[((b * nd + d) * E + i) * N + ks];
-      const u64 k0 = key[(((size_t)d * 2) * LK + pi) * N + k];
-      const u64 k1 = key[(((size_t)d * 2 + 1) * LK + pi) * N + k];
-      mac(lo0, hi0, x, k0);
-      mac(lo1, hi1, x, k1);
-      if (CHECK) {
-        if (hi0 >= P.q) hi0 -= P.q;
-        if (hi1 >= P.q) hi1 -= P.q;
-      }
+  const uint32_t ks = g == 1 ? k : auto_src_k(k, g, logN);
+  u64 k0[ND], k1[ND];
+#pragma unroll
+  for (int d = 0; d < ND; d++) {
+    k0[d] = d < nd ? key[(((size_t)d * 2) * LK + pi) * N + k] : 0;
+    k1[d] = d < nd ? key[(((size_t)d * 2 + 1) * LK + pi) * N + k] : 0;
+    if (w) {
+      k0[d] = split_of(k0[d], w, mask);
+      k1[d] = split_of(k1[d], w, mask);
     }
-    u64* o = acc + (size_t)r * 2 * per_rot + (b * 2) * E * N + rr;
-    o[0] = redc(hi0, lo0, P.q, P.qinv);
-    o[(size_t)E * N] = redc(hi1, lo1, P.q, P.qinv);
+  }
+  const u64* ex = ext + (size_t)r * ext_r + ((size_t)i << logN) + ks;
+  u64* o = acc + (size_t)r * 2 * nb * EN + idx;
+  for (int b = 0; b < nb; b++) {
+    const u64* eb = ex + (size_t)b * nd * EN;
+    u64 r0, r1;
+    if (w) {
+      u64 a00 = 0, a01 = 0, a11 = 0, c00 = 0, c01 = 0, c11 = 0;
+#pragma unroll
+      for (int d = 0; d < ND; d++) {
+        if (d < nd) {
+          const u64 x = eb[(size_t)d * EN];
+          const uint32_t x0 = (uint32_t)(x & mask), x1 = (uint32_t)(x >> w);
+          smac(a00, a01, a11, x0, x1, k0[d]);
+          smac(c00, c01, c11, x0, x1, k1[d]);
+        }
+      }
+      r0 = split_redc(a00, a01, a11, w, P.q, P.qinv);
+      r1 = split_redc(c00, c01, c11, w, P.q, P.qinv);
+    } else {
+      u64 lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
+#pragma unroll
+      for (int d = 0; d < ND; d++) {
+        if (d < nd) {
+          const u64 x = eb[(size_t)d * EN];
+          mac(lo0, hi0, x, k0[d]);
+          mac(lo1, hi1, x, k1[d]);
+          if (hi0 >= P.q) hi0 -= P.q;
+          if (hi1 >= P.q) hi1 -= P.q;
+        }
+      }
+      r0 = redc(hi0, lo0, P.q, P.qinv);
+      r1 = redc(hi1, lo1, P.q, P.qinv);
+    }
+    o[(size_t)b * 2 * EN] = r0;
+    o[(size_t)b * 2 * EN + EN] = r1;
   }
 }
 void launch_key_ip(ctl_context* c, const u64* ext, size_t ext_r, int nb, int lvl, const RotList& rl, u64* acc) {
@@ -318,85 +377,132 @@ void launch_key_ip(ctl_context* c, const u64* ext, size_t ext_r, int nb, int lvl
   const int nd = (lvl + (int)c->alpha - 1) / (int)c->alpha;
   const int E = lvl + (int)c->K;
   const int LK = (int)(c->L + c->K);
-  size_t per_rot = (size_t)nb * E * c->N;
-  int g = elem_grid(c, per_rot);
-  dim3 grid(g, nrot);
-  u64 maxq = 0;
-  for (auto q : c->moduli) maxq = q > maxq ? q : maxq;
-  const bool check = (double)nd * (double)maxq >= 1.8e19;
-  double work = 2.0 * nd * per_rot * nrot;
-  if (check)
-    CTL_LAUNCH(KC_KEYIP, work, g,
-               (k_key_ip<true><<<grid, kThreads, 0, c->stream>>>(ext, ext_r, rl, acc, c->d_primes,
-                                                                 (int)c->logN, nb, nd, E, lvl, (int)c->L, LK)));
-  else
-    CTL_LAUNCH(KC_KEYIP, work, g,
-               (k_key_ip<false><<<grid, kThreads, 0, c->stream>>>(ext, ext_r, rl, acc, c->d_primes,
-                                                                  (int)c->logN, nb, nd, E, lvl, (int)c->L, LK)));
+  const size_t EN = (size_t)E * c->N;
+  dim3 grid((unsigned)((EN + 255) / 256), (unsigned)nrot);
+  double work = 2.0 * nd * EN * nb * nrot;
+#define CTL_KEYIP_CASE(NDV)                                                                                    \
+  CTL_LAUNCH(KC_KEYIP, work, grid,                                                                             \
+             (k_key_ip<NDV><<<grid, 256, 0, c->stream>>>(ext, ext_r, rl, acc, c->d_primes, (int)c->logN, nb, nd, \
+                                                         E, lvl, (int)c->L, LK)))
+  if (nd <= 1) CTL_KEYIP_CASE(1);
+  else if (nd <= 2) CTL_KEYIP_CASE(2);
+  else if (nd <= 4) CTL_KEYIP_CASE(4);
+  else if (nd <= 8) CTL_KEYIP_CASE(8);
+  else CTL_KEYIP_CASE(16);
+#undef CTL_KEYIP_CASE
 }
 
 // ---------------------------------------------------------------------------------
 // Baby-step giant-step inner sums (Eq. bsgs):
 //   inner[k][b][p][i][c] = sum_{j < t1} diag[k*t1 + j][i][c] * baby[j][b][p][i][c]
-// One thread per (b, p, i, c) keeps its t1 baby-step values in registers and sweeps the
-// t2 giant steps; the diagonal values are shared by every ciphertext of the batch (and
-// both polys), so the grid runs the batch fastest to reuse them from L2.  Groups of at
-// most G products are summed lazily before one Montgomery reduction (G * q < 2^64).
+// A block covers 32 coefficients of one limb for 8 (ciphertext, poly) pairs (one warp
+// each).  For every giant step k the block stages the t1 x 32 diagonal values in shared
+// memory once for its 8 warps (and the grid runs the pairs fastest so other blocks find
+// the same tile in L2); each thread keeps its t1 baby-step values in registers.
+// Products are exact: on limbs with a split width w (q < 2^54) both operands are cut
+// into w-bit halves and the t1 products go into three 64-bit sums with plain 32x32->64
+// multiply-adds (no carries: 2*t1*2^(2w) < 2^64), combined once into a 128-bit value;
+// otherwise full 64x64->128 products are summed.  One Montgomery reduction per output
+// (diagonals are in Montgomery form; t1 * q < 2^64 keeps the REDC precondition).
 // ---------------------------------------------------------------------------------
+__global__ void k_split(u64* data, const DPrime* __restrict__ pr, int logN, int lvl, size_t total) {
+  const size_t N = (size_t)1 << logN;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)((idx >> logN) % lvl);
+    const int w = (int)pr[i].split;
+    if (!w) continue;
+    const u64 v = data[idx];
+    data[idx] = ((v >> w) << 32) | (v & ((1ull << w) - 1));
+  }
+  (void)N;
+}
+void launch_split_limbs(ctl_context* c, u64* data, int cnt, int lvl) {
+  size_t total = (size_t)cnt * lvl * c->N;
+  int g = elem_grid(c, total);
+  CTL_LAUNCH(KC_ELEM, 0, g, (k_split<<<g, kThreads, 0, c->stream>>>(data, c->d_primes, (int)c->logN, lvl, total)));
+}
+
 template <int T1>
 __global__ void __launch_bounds__(256) k_bsgs(const u64* __restrict__ baby, const u64* __restrict__ diag,
                                               size_t diag_stride, u64* __restrict__ inner,
                                               const DPrime* __restrict__ pr, int logN, int t1, int t2, int nb,
-                                              int lvl, int group) {
-  const size_t N = (size_t)1 << logN;
-  const size_t LN = (size_t)lvl * N;
-  const size_t bp_count = (size_t)nb * 2;
-  // blockIdx.x enumerates (b, p) fastest, blockIdx.y the coefficient tiles of all limbs
-  const size_t bp = blockIdx.x;
-  const size_t cidx = (size_t)blockIdx.y * blockDim.x + threadIdx.x;  // index in [0, lvl*N)
-  if (bp >= bp_count || cidx >= LN) return;
-  const int i = (int)(cidx >> logN);
+                                              int lvl) {
+  __shared__ u64 Ds[T1][32];
+  const size_t LN = (size_t)lvl << logN;
+  const int bp_count = nb * 2;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int bp = blockIdx.x * 8 + warp;
+  const size_t c0 = (size_t)blockIdx.y * 32;  // first coefficient index in [0, lvl*N)
+  const size_t cidx = c0 + lane;
+  const int i = (int)(c0 >> logN);
   const DPrime P = pr[i];
-  const size_t bstride = bp_count * LN;  // stride between baby steps j
+  const int w = (int)P.split;
+  const bool active = bp < bp_count;
+  const size_t bstride = (size_t)bp_count * LN;  // stride between baby steps j
   u64 x[T1];
 #pragma unroll
-  for (int j = 0; j < T1; j++) x[j] = (j < t1) ? baby[(size_t)j * bstride + bp * LN + cidx] : 0;
-  for (int k = 0; k < t2; k++) {
-    const u64* dk = diag + (size_t)(k * t1) * diag_stride + cidx;
-    u64 res = 0;
-    u64 lo = 0, hi = 0;
-    int cnt = 0;
+  for (int j = 0; j < T1; j++)
+    x[j] = (active && j < t1) ? baby[(size_t)j * bstride + (size_t)bp * LN + cidx] : 0;
+  if (w) {
+    const u64 mask = (1ull << w) - 1;
 #pragma unroll
-    for (int j = 0; j < T1; j++) {
-      if (j < t1) {
-        mac(lo, hi, x[j], __ldg(dk + (size_t)j * diag_stride));
-        if (++cnt == group) {
-          res = addmod(res, redc(hi, lo, P.q, P.qinv), P.q);
-          lo = hi = 0;
-          cnt = 0;
+    for (int j = 0; j < T1; j++) x[j] = ((x[j] >> w) << 32) | (x[j] & mask);
+  }
+  for (int k = 0; k < t2; k++) {
+    // stage diag[k*t1 + j][c0 .. c0+32) for j < t1
+    const u64* dk = diag + (size_t)(k * t1) * diag_stride + c0;
+    for (int e = threadIdx.x; e < t1 * 32; e += blockDim.x) Ds[e >> 5][e & 31] = __ldg(dk + (size_t)(e >> 5) * diag_stride + (e & 31));
+    __syncthreads();
+    u64 res = 0;
+    if (w) {
+      u64 a00 = 0, a01 = 0, a11 = 0;
+#pragma unroll
+      for (int j = 0; j < T1; j++) {
+        if (j < t1) {
+          const u64 d = Ds[j][lane];
+          const uint32_t d0 = (uint32_t)d, d1 = (uint32_t)(d >> 32);
+          const uint32_t x0 = (uint32_t)x[j], x1 = (uint32_t)(x[j] >> 32);
+          a00 += (u64)x0 * d0;
+          a01 += (u64)x0 * d1;
+          a01 += (u64)x1 * d0;
+          a11 += (u64)x1 * d1;
         }
       }
+      // S = a11 * 2^(2w) + a01 * 2^w + a00 as a 128-bit (hi, lo)
+      u64 lo = a00, hi = 0;
+      const u64 t_lo = a01 << w, t_hi = a01 >> (64 - w);
+      lo += t_lo;
+      hi += t_hi + (lo < t_lo);
+      const u64 u_lo = a11 << (2 * w), u_hi = a11 >> (64 - 2 * w);
+      lo += u_lo;
+      hi += u_hi + (lo < u_lo);
+      res = redc(hi, lo, P.q, P.qinv);
+    } else {
+      u64 lo = 0, hi = 0;
+#pragma unroll
+      for (int j = 0; j < T1; j++) {
+        if (j < t1) {
+          mac(lo, hi, x[j], Ds[j][lane]);
+          if (hi >= P.q) hi -= P.q;
+        }
+      }
+      res = redc(hi, lo, P.q, P.qinv);
     }
-    if (cnt) res = addmod(res, redc(hi, lo, P.q, P.qinv), P.q);
-    inner[(size_t)k * bstride + bp * LN + cidx] = res;
+    if (active) inner[(size_t)k * bstride + (size_t)bp * LN + cidx] = res;
+    __syncthreads();
   }
 }
 
 void launch_bsgs_inner(ctl_context* c, const u64* baby, const u64* diag, size_t diag_stride, u64* inner, int t1,
                        int t2, int nb, int lvl) {
-  u64 maxq = 0;
-  for (int i = 0; i < lvl; i++) maxq = c->moduli[i] > maxq ? c->moduli[i] : maxq;
-  int group = (int)(1.8e19 / (double)maxq);
-  if (group < 1) group = 1;
-  if (group > 64) group = 64;
   const size_t LN = (size_t)lvl * c->N;
-  dim3 grid((unsigned)(nb * 2), (unsigned)((LN + 255) / 256));
+  dim3 grid((unsigned)((nb * 2 + 7) / 8), (unsigned)(LN / 32));
   double work = (double)t1 * t2 * nb * 2 * LN;
 #define CTL_BSGS_CASE(TT)                                                                                      \
   case TT:                                                                                                     \
     CTL_LAUNCH(KC_BSGS, work, grid,                                                                            \
                (k_bsgs<TT><<<grid, 256, 0, c->stream>>>(baby, diag, diag_stride, inner, c->d_primes,           \
-                                                        (int)c->logN, t1, t2, nb, lvl, group)));               \
+                                                        (int)c->logN, t1, t2, nb, lvl)));                      \
     break;
   int T1 = 1;
   while (T1 < t1) T1 <<= 1;
@@ -408,9 +514,7 @@ void launch_bsgs_inner(ctl_context* c, const u64* baby, const u64* diag, size_t 
     CTL_BSGS_CASE(16)
     CTL_BSGS_CASE(32)
     default:
-      CTL_LAUNCH(KC_BSGS, work, grid,
-                 (k_bsgs<64><<<grid, 256, 0, c->stream>>>(baby, diag, diag_stride, inner, c->d_primes, (int)c->logN,
-                                                          t1, t2, nb, lvl, group)));
+      CTL_BSGS_CASE(64)
   }
 #undef CTL_BSGS_CASE
 }

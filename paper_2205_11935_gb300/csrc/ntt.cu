@@ -3,20 +3,24 @@
 //
 // Definition (the NTT form of a in Z_q[X]/(X^N+1)):  a_hat[k] = a(psi^(2*bitrev(k)+1)),
 // psi the smallest primitive 2N-th root of unity mod q; outputs in bit-reversed order.
-// Forward: Cooley-Tukey butterflies with the psi powers merged (twiddle table
-// tw[i] = psi^bitrev(i)); inverse: Gentleman-Sande butterflies with (psi^-1)^bitrev(i)
-// and N^-1 folded into the last stage.  Values stay lazily reduced (Harvey): forward
-// butterflies keep [0, 4q), inverse [0, 2q); q < 2^62.
+// Forward: Cooley-Tukey butterflies with the psi powers merged (twiddle of stage m,
+// group i: psi^bitrev(m+i)); inverse: Gentleman-Sande butterflies with
+// (psi^-1)^bitrev(m+i) and N^-1 folded into the last stage.  Values stay lazily reduced
+// (Harvey): forward butterflies keep [0, 4q), inverse [0, 2q); q < 2^62.  Twiddles are
+// stored as interleaved (w, floor(w * 2^64 / q)) pairs and read with one 16-byte load.
 //
-// GPU mapping: one CTA owns one limb (N <= 16384 words, 128 KiB) in shared memory,
-// padded by one word every 16 to spread the strided accesses over the banks.  Stages
-// are grouped into passes of up to four (radix-16 sub-transforms held in registers);
-// each pass is one shared-memory round trip.  CTAs loop over the limbs of a batch.
+// GPU mapping.  For N in {4096, 8192, 16384} one CTA of N/32 threads owns a limb and
+// each thread keeps 32 elements in registers through three passes of 5, 5 and
+// log2(N)-10 stages; two shared-memory transposes (padded by one word in 16) connect
+// them.  The forward transform reads its input straight from global memory into
+// registers (thread t takes elements t + k*N/32: coalesced), the inverse writes its
+// output the same way.  Stage indices are compile-time, so only the block index of a
+// sub-transform is computed at run time.  Other N use a generic shared-memory kernel.
 //
 // CKKS (Sec. 3.1 of CryptoTL) needs these transforms around every key switch
 // (rotations, relinearisation) and every rescale; the functors below fuse the fast base
-// conversions of ModUp/ModDown and the rescale arithmetic into the load/store phases so
-// that each converted limb makes one trip through HBM.
+// conversions of ModUp/ModDown and the rescale arithmetic into the element loads and
+// stores, so each converted limb makes one trip through HBM.
 #include "ctl_internal.h"
 #include "modarith.cuh"
 
@@ -34,159 +38,165 @@ __device__ __forceinline__ uint32_t auto_src(uint32_t k, u64 g, int logN) {
   return brv_dev((e2 - 1u) >> 1, logN);
 }
 
-template <int LOGR>
-__device__ __forceinline__ void fwd_pass(u64* s, int logN, int s0, const u64* __restrict__ tw,
-                                         const u64* __restrict__ tws, u64 q) {
-  constexpr int R = 1 << LOGR;
-  const int nsub = 1 << (logN - LOGR);
-  const int log_tl = logN - s0 - LOGR;
+__device__ __forceinline__ void ct_bfly(u64& x, u64& y, const ulonglong2 w, u64 q) {
   const u64 q2 = 2 * q;
-  for (int p = threadIdx.x; p < nsub; p += blockDim.x) {
-    const int b = p >> log_tl;
-    const int o = p & ((1 << log_tl) - 1);
-    const int base = (b << (logN - s0)) + o;
-    u64 x[R];
-#pragma unroll
-    for (int k = 0; k < R; k++) x[k] = s[pidx(base + (k << log_tl))];
-#pragma unroll
-    for (int u = 0; u < LOGR; u++) {
-      const int h = R >> (u + 1);
-#pragma unroll
-      for (int k = 0; k < R; k++) {
-        if (k & h) continue;
-        const int widx = (1 << (s0 + u)) + (b << u) + (k >> (LOGR - u));
-        const u64 w = __ldg(tw + widx), wsh = __ldg(tws + widx);
-        u64 X = x[k];
-        if (X >= q2) X -= q2;
-        const u64 T = shoup_lazy(x[k + h], w, wsh, q);
-        x[k] = X + T;
-        x[k + h] = X - T + q2;
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < R; k++) s[pidx(base + (k << log_tl))] = x[k];
-  }
+  u64 X = x;
+  if (X >= q2) X -= q2;
+  const u64 T = shoup_lazy(y, w.x, w.y, q);
+  x = X + T;
+  y = X - T + q2;
+}
+__device__ __forceinline__ void gs_bfly(u64& x, u64& y, const ulonglong2 w, u64 q) {
+  const u64 q2 = 2 * q;
+  const u64 U = x, V = y;
+  u64 S = U + V;
+  if (S >= q2) S -= q2;
+  x = S;
+  y = shoup_lazy(U - V + q2, w.x, w.y, q);
 }
 
-template <int LOGR>
-__device__ __forceinline__ void inv_pass(u64* s, int logN, int s_lo, const u64* __restrict__ tw,
-                                         const u64* __restrict__ tws, u64 q, const DPrime& P) {
+// LOGR stages of a radix-2^LOGR sub-transform held in registers x[0..2^LOGR), for the
+// stages S0..S0+LOGR-1 and block index b at stage S0.
+template <int S0, int LOGR>
+__device__ __forceinline__ void fwd_regs(u64* x, int b, const ulonglong2* __restrict__ tw, u64 q) {
   constexpr int R = 1 << LOGR;
-  const int nsub = 1 << (logN - LOGR);
-  const int log_tl = logN - s_lo - LOGR;
-  const u64 q2 = 2 * q;
-  for (int p = threadIdx.x; p < nsub; p += blockDim.x) {
-    const int b = p >> log_tl;
-    const int o = p & ((1 << log_tl) - 1);
-    const int base = (b << (logN - s_lo)) + o;
-    u64 x[R];
 #pragma unroll
-    for (int k = 0; k < R; k++) x[k] = s[pidx(base + (k << log_tl))];
+  for (int u = 0; u < LOGR; u++) {
+    const int h = R >> (u + 1);
+    const ulonglong2* tu = tw + (1 << (S0 + u)) + (b << u);
 #pragma unroll
-    for (int u = LOGR - 1; u >= 0; u--) {
-      const int h = R >> (u + 1);
-      const bool last = (s_lo + u) == 0;
+    for (int k = 0; k < R; k++) {
+      if (k & h) continue;
+      ct_bfly(x[k], x[k + h], __ldg(tu + (k >> (LOGR - u))), q);
+    }
+  }
+}
+template <int S0, int LOGR>
+__device__ __forceinline__ void inv_regs(u64* x, int b, const ulonglong2* __restrict__ tw, u64 q, const DPrime& P) {
+  constexpr int R = 1 << LOGR;
 #pragma unroll
-      for (int k = 0; k < R; k++) {
-        if (k & h) continue;
+  for (int u = LOGR - 1; u >= 0; u--) {
+    const int h = R >> (u + 1);
+    const ulonglong2* tu = tw + (1 << (S0 + u)) + (b << u);
+#pragma unroll
+    for (int k = 0; k < R; k++) {
+      if (k & h) continue;
+      if (S0 + u == 0) {  // last stage: fold N^-1
         const u64 U = x[k], V = x[k + h];
-        if (last) {
-          x[k] = shoup_lazy(U + V, P.ninv, P.ninv_sh, q);
-          x[k + h] = shoup_lazy(U - V + q2, P.iw1, P.iw1_sh, q);
-        } else {
-          const int widx = (1 << (s_lo + u)) + (b << u) + (k >> (LOGR - u));
-          const u64 w = __ldg(tw + widx), wsh = __ldg(tws + widx);
-          u64 S = U + V;
-          if (S >= q2) S -= q2;
-          x[k] = S;
-          x[k + h] = shoup_lazy(U - V + q2, w, wsh, q);
-        }
+        x[k] = shoup_lazy(U + V, P.ninv, P.ninv_sh, q);
+        x[k + h] = shoup_lazy(U - V + 2 * q, P.iw1, P.iw1_sh, q);
+      } else {
+        gs_bfly(x[k], x[k + h], __ldg(tu + (k >> (LOGR - u))), q);
       }
     }
-#pragma unroll
-    for (int k = 0; k < R; k++) s[pidx(base + (k << log_tl))] = x[k];
-  }
-}
-
-// Pass plan: ceil(logN/4) passes, the first ones one stage larger when uneven.
-__device__ __forceinline__ int pass_bits(int logN, int i) {
-  const int np = (logN + 3) / 4;
-  const int base = logN / np, extra = logN % np;
-  return base + (i < extra ? 1 : 0);
-}
-
-__device__ __forceinline__ void ntt_fwd_core(u64* s, int logN, const u64* tw, const u64* tws, u64 q) {
-  const int np = (logN + 3) / 4;
-  int s0 = 0;
-  for (int i = 0; i < np; i++) {
-    const int r = pass_bits(logN, i);
-    switch (r) {
-      case 4: fwd_pass<4>(s, logN, s0, tw, tws, q); break;
-      case 3: fwd_pass<3>(s, logN, s0, tw, tws, q); break;
-      case 2: fwd_pass<2>(s, logN, s0, tw, tws, q); break;
-      default: fwd_pass<1>(s, logN, s0, tw, tws, q); break;
-    }
-    __syncthreads();
-    s0 += r;
-  }
-}
-
-__device__ __forceinline__ void ntt_inv_core(u64* s, int logN, const u64* tw, const u64* tws, u64 q, const DPrime& P) {
-  const int np = (logN + 3) / 4;
-  int top = logN;
-  for (int i = 0; i < np; i++) {
-    const int r = pass_bits(logN, i);
-    const int s_lo = top - r;
-    switch (r) {
-      case 4: inv_pass<4>(s, logN, s_lo, tw, tws, q, P); break;
-      case 3: inv_pass<3>(s, logN, s_lo, tw, tws, q, P); break;
-      case 2: inv_pass<2>(s, logN, s_lo, tw, tws, q, P); break;
-      default: inv_pass<1>(s, logN, s_lo, tw, tws, q, P); break;
-    }
-    __syncthreads();
-    top = s_lo;
   }
 }
 
 // ---------------------------------------------------------------------------------
-// Load / store functors.  load() fills s[pidx(k)], k < N, and returns true, or handles
-// the item itself and returns false (uniformly for the block).
+// Element functors.  A functor is a constant kernel parameter (__grid_constant__, so
+// its tables are read in place); its per-item state lives in a small State struct.
+// begin(st, p, l, pi, ...) binds item (poly p, limb l, prime pi) and returns false if
+// the item is complete already (the same answer for the whole block); get(st, j)
+// yields input element j (reduced, < q); put(st, j, v) consumes output element j given
+// lazily reduced (< 4q).
 // ---------------------------------------------------------------------------------
 struct ProLoad {
+  static constexpr bool kStage = false;
   const u64* src;
   size_t poly_stride;
-  __device__ bool load(u64* s, int p, int l, int, const DPrime*, int N) const {
-    const u64* g = src + (size_t)p * poly_stride + (size_t)l * N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) s[pidx(k)] = g[k];
+  struct State {
+    const u64* g;
+  };
+  __device__ bool begin(State& st, int p, int l, int, const DPrime*, int logN) const {
+    st.g = src + (size_t)p * poly_stride + ((size_t)l << logN);
     return true;
+  }
+  __device__ u64 get(const State& st, int j) const { return st.g[j]; }
+  template <int T, int C>
+  __device__ void getc(const State& st, int t0, u64* x) const {
+#pragma unroll
+    for (int k = 0; k < C; k++) x[k] = st.g[t0 + T * k];
   }
 };
 
 struct EpiStore {
   u64* dst;
   size_t poly_stride;
-  __device__ void store(const u64* s, int p, int l, int pi, const DPrime* pr, int N) const {
-    const u64 q = pr[pi].q;
-    u64* g = dst + (size_t)p * poly_stride + (size_t)l * N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) g[k] = reduce4(s[pidx(k)], q);
+  struct State {
+    u64* o;
+    u64 q;
+  };
+  __device__ void begin(State& st, int p, int l, int pi, const DPrime* pr, int logN) const {
+    st.o = dst + (size_t)p * poly_stride + ((size_t)l << logN);
+    st.q = pr[pi].q;
+  }
+  __device__ void put(const State& st, int j, u64 v) const { st.o[j] = reduce4(v, st.q); }
+  template <int T, int C>
+  __device__ void putc(const State& st, int t0, const u64* x) const {
+#pragma unroll
+    for (int k = 0; k < C; k++) st.o[t0 + T * k] = reduce4(x[k], st.q);
   }
 };
 
-// Fast base conversion of one coefficient: y = sum_j [x_j * Shat_j^-1]_{s_j} * Shat_j
-// mod t (the constant Shat_j mod t held in Montgomery form), exact residue in [0, t).
-__device__ __forceinline__ u64 conv_coef(const ConvTab& T, int tpos, const u64* const* srcs, int k, u64 t,
-                                         u64 tinv) {
-  u64 lo = 0, hi = 0;
-  for (int j = 0; j < T.ns; j++) {
-    const u64 sj = __ldg(T.sq + j);
-    const u64 v = shoup(srcs[j][k], __ldg(T.sinv + j), __ldg(T.sinv_sh + j), sj);
-    mac(lo, hi, v, __ldg(T.cmont + (size_t)j * T.nt + tpos));
+// Fast base conversion of one element: y = sum_j [x_j * Shat_j^-1]_{s_j} * (Shat_j mod t)
+// mod t over the ns <= NS source limbs, the constants Shat_j mod t in Montgomery form;
+// exact residue in [0, t).
+template <int NS>
+struct ConvState {
+  int ns;
+  const u64* srcs[NS];
+  u64 sinv[NS], sinv_sh[NS], sq[NS], cm[NS];
+  u64 t, tinv;
+  __device__ void bind(const ConvTab& T, int tpos, const u64* base, size_t limb0, int logN, u64 tq, u64 ti) {
+    ns = T.ns;
+#pragma unroll
+    for (int j = 0; j < NS; j++) {
+      const int jj = j < ns ? j : 0;
+      srcs[j] = base + ((limb0 + jj) << logN);
+      sinv[j] = __ldg(T.sinv + jj);
+      sinv_sh[j] = __ldg(T.sinv_sh + jj);
+      sq[j] = __ldg(T.sq + jj);
+      cm[j] = __ldg(T.cmont + (size_t)jj * T.nt + tpos);
+    }
+    t = tq;
+    tinv = ti;
   }
-  return redc(hi, lo, t, tinv);
-}
+  __device__ u64 eval(int k) const {
+    u64 lo = 0, hi = 0;
+#pragma unroll
+    for (int j = 0; j < NS; j++)
+      if (j < ns) mac(lo, hi, shoup(srcs[j][k], sinv[j], sinv_sh[j], sq[j]), cm[j]);
+    return redc(hi, lo, t, tinv);
+  }
+  // C elements t0 + T*k of one thread: every source load is issued before any arithmetic
+  // so that the loads overlap.
+  template <int T, int C>
+  __device__ void evalc(int t0, u64* x) const {
+    if constexpr (NS <= 2) {
+      u64 v[NS][C];
+#pragma unroll
+      for (int j = 0; j < NS; j++)
+#pragma unroll
+        for (int k = 0; k < C; k++) v[j][k] = (j < ns) ? srcs[j][t0 + T * k] : 0;
+#pragma unroll
+      for (int k = 0; k < C; k++) {
+        u64 lo = 0, hi = 0;
+#pragma unroll
+        for (int j = 0; j < NS; j++)
+          if (j < ns) mac(lo, hi, shoup(v[j][k], sinv[j], sinv_sh[j], sq[j]), cm[j]);
+        x[k] = redc(hi, lo, t, tinv);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < C; k++) x[k] = eval(t0 + T * k);
+    }
+  }
+};
 
 #define CTL_MAX_DIGITS 16
+template <int NS>
 struct ProModUp {
+  static constexpr bool kStage = true;
   const u64* coef;   // c1 coefficient form, input b's limbs at coef + b*coef_stride
   size_t coef_stride;
   const u64* ntt;    // c1 NTT form, input b's limbs at ntt + b*stride
@@ -194,35 +204,43 @@ struct ProModUp {
   u64* ext;          // [nb][nd][E][N]
   int nd, E, lvl, alpha;
   ConvTab tabs[CTL_MAX_DIGITS];
-  __device__ bool load(u64* s, int p, int l, int pi, const DPrime* pr, int N) const {
+  typedef ConvState<NS> State;
+  __device__ bool begin(State& st, int p, int l, int pi, const DPrime* pr, int logN) const {
     const int b = p / nd, d = p % nd;
     const int d0 = d * alpha, d1 = min(d0 + alpha, lvl);
+    const int N = 1 << logN;
     if (l >= d0 && l < d1) {  // the digit's own primes: y = x mod q_l, already in NTT form
-      const u64* g = ntt + (size_t)b * stride + (size_t)l * N;
-      u64* o = ext + ((size_t)p * E + l) * N;
+      const u64* g = ntt + (size_t)b * stride + ((size_t)l << logN);
+      u64* o = ext + (((size_t)p * E + l) << logN);
       for (int k = threadIdx.x; k < N; k += blockDim.x) o[k] = g[k];
       return false;
     }
-    const u64* srcs[8];
-    const ConvTab& T = tabs[d];
-    for (int j = 0; j < T.ns; j++) srcs[j] = coef + (size_t)b * coef_stride + (size_t)(d0 + j) * N;
-    const u64 t = pr[pi].q, tinv = pr[pi].qinv;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) s[pidx(k)] = conv_coef(T, l, srcs, k, t, tinv);
+    st.bind(tabs[d], l, coef + (size_t)b * coef_stride, (size_t)d0, logN, pr[pi].q, pr[pi].qinv);
     return true;
+  }
+  __device__ u64 get(const State& st, int j) const { return st.eval(j); }
+  template <int T, int C>
+  __device__ void getc(const State& st, int t0, u64* x) const {
+    st.template evalc<T, C>(t0, x);
   }
 };
 
+template <int NS>
 struct ProModDown {
+  static constexpr bool kStage = true;
   const u64* acc;    // [np][E][N], special limbs (positions lvl..lvl+K-1) in coefficient form
   size_t acc_stride;
   int lvl;
   ConvTab tab;       // sources: special primes; target position = data limb index
-  __device__ bool load(u64* s, int p, int l, int pi, const DPrime* pr, int N) const {
-    const u64* srcs[8];
-    for (int j = 0; j < tab.ns; j++) srcs[j] = acc + (size_t)p * acc_stride + (size_t)(lvl + j) * N;
-    const u64 t = pr[pi].q, tinv = pr[pi].qinv;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) s[pidx(k)] = conv_coef(tab, l, srcs, k, t, tinv);
+  typedef ConvState<NS> State;
+  __device__ bool begin(State& st, int p, int l, int pi, const DPrime* pr, int logN) const {
+    st.bind(tab, l, acc + (size_t)p * acc_stride, (size_t)lvl, logN, pr[pi].q, pr[pi].qinv);
     return true;
+  }
+  __device__ u64 get(const State& st, int j) const { return st.eval(j); }
+  template <int T, int C>
+  __device__ void getc(const State& st, int t0, u64* x) const {
+    st.template evalc<T, C>(t0, x);
   }
 };
 
@@ -238,27 +256,50 @@ struct EpiModDown {
   const u64* addend;
   size_t add_r, add_b, add_p;
   int add_both;
-  u64 g[CTL_MAX_ROT];
   int nb;
-  int logN;
-  __device__ void store(const u64* s, int p, int l, int pi, const DPrime* pr, int N) const {
-    const u64 q = pr[pi].q;
-    const u64 pv = __ldg(pinv + l), pvs = __ldg(pinv_sh + l);
-    const u64* a = acc + (size_t)p * acc_stride + (size_t)l * N;
-    u64* o = out + (size_t)p * out_stride + (size_t)l * N;
-    const u64* ad = nullptr;
-    u64 g = 1;
+  u64 g[CTL_MAX_ROT];
+  struct State {
+    const u64* a;
+    u64* o;
+    const u64* ad;
+    u64 gg, q, pv, pvs;
+    int lg;
+  };
+  __device__ void begin(State& st, int p, int l, int pi, const DPrime* pr, int logN) const {
+    st.q = pr[pi].q;
+    st.pv = __ldg(pinv + l);
+    st.pvs = __ldg(pinv_sh + l);
+    st.a = acc + (size_t)p * acc_stride + ((size_t)l << logN);
+    st.o = out + (size_t)p * out_stride + ((size_t)l << logN);
+    st.ad = nullptr;
+    st.gg = 1;
+    st.lg = logN;
     const int t = p & 1;
     if (addend && (t == 0 || add_both)) {
       const int rb = p >> 1, r = rb / nb, b = rb % nb;
-      ad = addend + (size_t)r * add_r + (size_t)b * add_b + (size_t)t * add_p + (size_t)l * N;
-      g = this->g[r];
+      st.ad = addend + (size_t)r * add_r + (size_t)b * add_b + (size_t)t * add_p + ((size_t)l << logN);
+      st.gg = g[r];
     }
-    for (int k = threadIdx.x; k < N; k += blockDim.x) {
-      const u64 x = reduce4(s[pidx(k)], q);
-      u64 v = shoup(submod(a[k], x, q), pv, pvs, q);
-      if (ad) v = addmod(v, ad[g == 1 ? k : auto_src(k, g, logN)], q);
-      o[k] = v;
+  }
+  __device__ void put(const State& st, int j, u64 v) const {
+    u64 r = shoup(submod(st.a[j], reduce4(v, st.q), st.q), st.pv, st.pvs, st.q);
+    if (st.ad) r = addmod(r, st.ad[st.gg == 1 ? (uint32_t)j : auto_src((uint32_t)j, st.gg, st.lg)], st.q);
+    st.o[j] = r;
+  }
+  // C elements t0 + T*k of one thread, all loads issued first.
+  template <int T, int C>
+  __device__ void putc(const State& st, int t0, const u64* x) const {
+    u64 a[C], ad[C];
+#pragma unroll
+    for (int k = 0; k < C; k++) {
+      const int j = t0 + T * k;
+      a[k] = st.a[j];
+      ad[k] = st.ad ? st.ad[st.gg == 1 ? (uint32_t)j : auto_src((uint32_t)j, st.gg, st.lg)] : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < C; k++) {
+      const u64 r = shoup(submod(a[k], reduce4(x[k], st.q), st.q), st.pv, st.pvs, st.q);
+      st.o[t0 + T * k] = addmod(r, ad[k], st.q);
     }
   }
 };
@@ -266,24 +307,50 @@ struct EpiModDown {
 struct EpiRescaleLast {   // inverse NTT of the last limb -> r = [x + h]_q_last
   u64* r_out;
   u64 h;
-  __device__ void store(const u64* s, int p, int, int pi, const DPrime* pr, int N) const {
-    const u64 q = pr[pi].q;
-    u64* o = r_out + (size_t)p * N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) o[k] = addmod(reduce4(s[pidx(k)], q), h, q);
+  struct State {
+    u64* o;
+    u64 q;
+  };
+  __device__ void begin(State& st, int p, int, int pi, const DPrime* pr, int logN) const {
+    st.o = r_out + ((size_t)p << logN);
+    st.q = pr[pi].q;
+  }
+  __device__ void put(const State& st, int j, u64 v) const { st.o[j] = addmod(reduce4(v, st.q), h, st.q); }
+  template <int T, int C>
+  __device__ void putc(const State& st, int t0, const u64* x) const {
+#pragma unroll
+    for (int k = 0; k < C; k++) put(st, t0 + T * k, x[k]);
   }
 };
 
 struct ProRescale {       // (r - h) mod q_i in coefficient form
+  static constexpr bool kStage = true;
   const u64* r;
   u64 h;
-  __device__ bool load(u64* s, int p, int, int pi, const DPrime* pr, int N) const {
-    const u64 q = pr[pi].q, qinv = pr[pi].qinv, rm = pr[pi].rmod;
-    const u64* g = r + (size_t)p * N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) {
-      const u64 v = g[k];
-      s[pidx(k)] = v >= h ? mulmod_mont(v - h, rm, q, qinv) : negmod(mulmod_mont(h - v, rm, q, qinv), q);
-    }
+  struct State {
+    const u64* g;
+    u64 q, qinv, rm;
+  };
+  __device__ bool begin(State& st, int p, int, int pi, const DPrime* pr, int logN) const {
+    st.g = r + ((size_t)p << logN);
+    st.q = pr[pi].q;
+    st.qinv = pr[pi].qinv;
+    st.rm = pr[pi].rmod;
     return true;
+  }
+  __device__ u64 get(const State& st, int j) const {
+    const u64 v = st.g[j];
+    return v >= h ? mulmod_mont(v - h, st.rm, st.q, st.qinv) : negmod(mulmod_mont(h - v, st.rm, st.q, st.qinv), st.q);
+  }
+  template <int T, int C>
+  __device__ void getc(const State& st, int t0, u64* x) const {
+    u64 v[C];
+#pragma unroll
+    for (int k = 0; k < C; k++) v[k] = st.g[t0 + T * k];
+#pragma unroll
+    for (int k = 0; k < C; k++)
+      x[k] = v[k] >= h ? mulmod_mont(v[k] - h, st.rm, st.q, st.qinv)
+                       : negmod(mulmod_mont(h - v[k], st.rm, st.q, st.qinv), st.q);
   }
 };
 
@@ -294,112 +361,376 @@ struct EpiRescale {       // out_i = (in_i - x) * q_last^-1
   size_t out_stride;
   const u64* inv;
   const u64* inv_sh;
-  __device__ void store(const u64* s, int p, int l, int pi, const DPrime* pr, int N) const {
-    const u64 q = pr[pi].q;
-    const u64 w = __ldg(inv + l), ws = __ldg(inv_sh + l);
-    const u64* a = in + (size_t)p * in_stride + (size_t)l * N;
-    u64* o = out + (size_t)p * out_stride + (size_t)l * N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) o[k] = shoup(submod(a[k], reduce4(s[pidx(k)], q), q), w, ws, q);
+  struct State {
+    const u64* a;
+    u64* o;
+    u64 q, w, ws;
+  };
+  __device__ void begin(State& st, int p, int l, int pi, const DPrime* pr, int logN) const {
+    st.q = pr[pi].q;
+    st.w = __ldg(inv + l);
+    st.ws = __ldg(inv_sh + l);
+    st.a = in + (size_t)p * in_stride + ((size_t)l << logN);
+    st.o = out + (size_t)p * out_stride + ((size_t)l << logN);
+  }
+  __device__ void put(const State& st, int j, u64 v) const {
+    st.o[j] = shoup(submod(st.a[j], reduce4(v, st.q), st.q), st.w, st.ws, st.q);
+  }
+  template <int T, int C>
+  __device__ void putc(const State& st, int t0, const u64* x) const {
+    u64 a[C];
+#pragma unroll
+    for (int k = 0; k < C; k++) a[k] = st.a[t0 + T * k];
+#pragma unroll
+    for (int k = 0; k < C; k++) st.o[t0 + T * k] = shoup(submod(a[k], reduce4(x[k], st.q), st.q), st.w, st.ws, st.q);
   }
 };
 
 // ---------------------------------------------------------------------------------
-// Kernels.
+// Register-resident kernels, N = 2^LOGN in {4096, 8192, 16384}: N/32 threads.
 // ---------------------------------------------------------------------------------
+template <int LOGN, class Pro, class Epi>
+__global__ void __launch_bounds__((1 << LOGN) / 32, 16384 / (1 << LOGN))
+k_nttf_reg(const __grid_constant__ Pro pro, const __grid_constant__ Epi epi, const DPrime* __restrict__ primes,
+                                                               const ulonglong2* __restrict__ tw, int n_items, int lr,
+                                                               int limb_lo, int lvl, int L) {
+  constexpr int N = 1 << LOGN, T = N / 32, RC = LOGN - 10, R = 1 << RC;
+  extern __shared__ u64 smem[];
+  const int t = threadIdx.x;
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const int p = item / lr, l = limb_lo + item % lr;
+    const int pi = l < lvl ? l : L + (l - lvl);
+    typename Pro::State ps;
+    if (!pro.begin(ps, p, l, pi, primes, LOGN)) continue;
+    typename Epi::State es;
+    epi.begin(es, p, l, pi, primes, LOGN);
+    const u64 q = primes[pi].q;
+    const ulonglong2* W = tw + ((size_t)pi << LOGN);
+    u64 x[32];
+    if constexpr (Pro::kStage) {
+      // arithmetic-heavy prologue: each thread parks its own 32 inputs in shared memory
+      // first (no barrier needed), so several loads are in flight while x[] is not live
+#pragma unroll 4
+      for (int k = 0; k < 32; k++) smem[pidx(t + T * k)] = pro.get(ps, t + T * k);
+#pragma unroll
+      for (int k = 0; k < 32; k++) x[k] = smem[pidx(t + T * k)];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 32; k++) x[k] = pro.get(ps, t + T * k);
+    }
+    // stages 0..4: sub-transform on elements t + T*k, block index 0
+    fwd_regs<0, 5>(x, 0, W, q);
+#pragma unroll
+    for (int k = 0; k < 32; k++) smem[pidx(t + T * k)] = x[k];
+    __syncthreads();
+    {  // stages 5..9
+      const int b = t >> RC, o = t & (R - 1);
+      const int base = (b << (LOGN - 5)) + o;
+#pragma unroll
+      for (int k = 0; k < 32; k++) x[k] = smem[pidx(base + (k << RC))];
+      fwd_regs<5, 5>(x, b, W, q);
+#pragma unroll
+      for (int k = 0; k < 32; k++) smem[pidx(base + (k << RC))] = x[k];
+    }
+    __syncthreads();
+    // stages 10..LOGN-1: 32/R contiguous sub-transforms of R elements per thread
+#pragma unroll
+    for (int i = 0; i < 32 / R; i++) {
+      const int b = t + T * i;
+#pragma unroll
+      for (int k = 0; k < R; k++) x[i * R + k] = smem[pidx(b * R + k)];
+    }
+#pragma unroll
+    for (int i = 0; i < 32 / R; i++) fwd_regs<10, RC>(x + i * R, t + T * i, W, q);
+#pragma unroll
+    for (int i = 0; i < 32 / R; i++) {
+      const int b = t + T * i;
+#pragma unroll
+      for (int k = 0; k < R; k++) smem[pidx(b * R + k)] = x[i * R + k];
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < 32; k++) epi.put(es, t + T * k, smem[pidx(t + T * k)]);
+    __syncthreads();
+  }
+}
+
+template <int LOGN, class Pro, class Epi>
+__global__ void __launch_bounds__((1 << LOGN) / 32, 16384 / (1 << LOGN))
+k_ntti_reg(const __grid_constant__ Pro pro, const __grid_constant__ Epi epi, const DPrime* __restrict__ primes,
+                                                               const ulonglong2* __restrict__ tw, int n_items, int lr,
+                                                               int limb_lo, int lvl, int L) {
+  constexpr int N = 1 << LOGN, T = N / 32, RC = LOGN - 10, R = 1 << RC;
+  extern __shared__ u64 smem[];
+  const int t = threadIdx.x;
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const int p = item / lr, l = limb_lo + item % lr;
+    const int pi = l < lvl ? l : L + (l - lvl);
+    typename Pro::State ps;
+    if (!pro.begin(ps, p, l, pi, primes, LOGN)) continue;
+    typename Epi::State es;
+    epi.begin(es, p, l, pi, primes, LOGN);
+    const DPrime P = primes[pi];
+    const u64 q = P.q;
+    const ulonglong2* W = tw + ((size_t)pi << LOGN);
+    u64 x[32];
+#pragma unroll 8
+    for (int k = 0; k < 32; k++) smem[pidx(t + T * k)] = pro.get(ps, t + T * k);
+    __syncthreads();
+    // stages LOGN-1..10 on contiguous sub-transforms
+#pragma unroll
+    for (int i = 0; i < 32 / R; i++) {
+      const int b = t + T * i;
+#pragma unroll
+      for (int k = 0; k < R; k++) x[i * R + k] = smem[pidx(b * R + k)];
+    }
+#pragma unroll
+    for (int i = 0; i < 32 / R; i++) inv_regs<10, RC>(x + i * R, t + T * i, W, q, P);
+#pragma unroll
+    for (int i = 0; i < 32 / R; i++) {
+      const int b = t + T * i;
+#pragma unroll
+      for (int k = 0; k < R; k++) smem[pidx(b * R + k)] = x[i * R + k];
+    }
+    __syncthreads();
+    {  // stages 9..5
+      const int b = t >> RC, o = t & (R - 1);
+      const int base = (b << (LOGN - 5)) + o;
+#pragma unroll
+      for (int k = 0; k < 32; k++) x[k] = smem[pidx(base + (k << RC))];
+      inv_regs<5, 5>(x, b, W, q, P);
+#pragma unroll
+      for (int k = 0; k < 32; k++) smem[pidx(base + (k << RC))] = x[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 32; k++) x[k] = smem[pidx(t + T * k)];
+    // stages 4..0 (N^-1 folded into stage 0), outputs straight to global
+    inv_regs<0, 5>(x, 0, W, q, P);
+#pragma unroll
+    for (int k = 0; k < 32; k++) epi.put(es, t + T * k, x[k]);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Generic shared-memory kernels (any N = 2^logN, 16 <= N <= 16384).
+// ---------------------------------------------------------------------------------
+template <int LOGR>
+__device__ __forceinline__ void fwd_pass(u64* s, int logN, int s0, const ulonglong2* __restrict__ tw, u64 q) {
+  constexpr int R = 1 << LOGR;
+  const int nsub = 1 << (logN - LOGR);
+  const int log_tl = logN - s0 - LOGR;
+  for (int p = threadIdx.x; p < nsub; p += blockDim.x) {
+    const int b = p >> log_tl;
+    const int o = p & ((1 << log_tl) - 1);
+    const int base = (b << (logN - s0)) + o;
+    u64 x[R];
+#pragma unroll
+    for (int k = 0; k < R; k++) x[k] = s[pidx(base + (k << log_tl))];
+#pragma unroll
+    for (int u = 0; u < LOGR; u++) {
+      const int h = R >> (u + 1);
+#pragma unroll
+      for (int k = 0; k < R; k++) {
+        if (k & h) continue;
+        ct_bfly(x[k], x[k + h], __ldg(tw + (1 << (s0 + u)) + (b << u) + (k >> (LOGR - u))), q);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < R; k++) s[pidx(base + (k << log_tl))] = x[k];
+  }
+}
+
+template <int LOGR>
+__device__ __forceinline__ void inv_pass(u64* s, int logN, int s_lo, const ulonglong2* __restrict__ tw, u64 q,
+                                         const DPrime& P) {
+  constexpr int R = 1 << LOGR;
+  const int nsub = 1 << (logN - LOGR);
+  const int log_tl = logN - s_lo - LOGR;
+  for (int p = threadIdx.x; p < nsub; p += blockDim.x) {
+    const int b = p >> log_tl;
+    const int o = p & ((1 << log_tl) - 1);
+    const int base = (b << (logN - s_lo)) + o;
+    u64 x[R];
+#pragma unroll
+    for (int k = 0; k < R; k++) x[k] = s[pidx(base + (k << log_tl))];
+#pragma unroll
+    for (int u = LOGR - 1; u >= 0; u--) {
+      const int h = R >> (u + 1);
+      const bool last = (s_lo + u) == 0;
+#pragma unroll
+      for (int k = 0; k < R; k++) {
+        if (k & h) continue;
+        if (last) {
+          const u64 U = x[k], V = x[k + h];
+          x[k] = shoup_lazy(U + V, P.ninv, P.ninv_sh, q);
+          x[k + h] = shoup_lazy(U - V + 2 * q, P.iw1, P.iw1_sh, q);
+        } else {
+          gs_bfly(x[k], x[k + h], __ldg(tw + (1 << (s_lo + u)) + (b << u) + (k >> (LOGR - u))), q);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < R; k++) s[pidx(base + (k << log_tl))] = x[k];
+  }
+}
+
+// Pass plan: ceil(logN/4) passes, the first ones one stage larger when uneven.
+__device__ __forceinline__ int pass_bits(int logN, int i) {
+  const int np = (logN + 3) / 4;
+  const int base = logN / np, extra = logN % np;
+  return base + (i < extra ? 1 : 0);
+}
+
 template <class Pro, class Epi>
-__global__ void __launch_bounds__(512) k_ntt_fwd(Pro pro, Epi epi, const DPrime* __restrict__ primes,
-                                                 const u64* __restrict__ tw, const u64* __restrict__ tws, int logN,
-                                                 int n_items, int lr, int limb_lo, int lvl, int L) {
+__global__ void __launch_bounds__(512) k_nttf_gen(const __grid_constant__ Pro pro, const __grid_constant__ Epi epi,
+                                                  const DPrime* __restrict__ primes,
+                                                  const ulonglong2* __restrict__ tw, int logN, int n_items, int lr,
+                                                  int limb_lo, int lvl, int L) {
   extern __shared__ u64 smem[];
   const int N = 1 << logN;
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
     const int p = item / lr, l = limb_lo + item % lr;
     const int pi = l < lvl ? l : L + (l - lvl);
-    if (!pro.load(smem, p, l, pi, primes, N)) continue;
+    typename Pro::State ps;
+    if (!pro.begin(ps, p, l, pi, primes, logN)) continue;
+    typename Epi::State es;
+    epi.begin(es, p, l, pi, primes, logN);
+    for (int k = threadIdx.x; k < N; k += blockDim.x) smem[pidx(k)] = pro.get(ps, k);
     __syncthreads();
-    ntt_fwd_core(smem, logN, tw + (size_t)pi * N, tws + (size_t)pi * N, primes[pi].q);
-    epi.store(smem, p, l, pi, primes, N);
+    const ulonglong2* W = tw + ((size_t)pi << logN);
+    const u64 q = primes[pi].q;
+    const int np = (logN + 3) / 4;
+    int s0 = 0;
+    for (int i = 0; i < np; i++) {
+      const int r = pass_bits(logN, i);
+      switch (r) {
+        case 4: fwd_pass<4>(smem, logN, s0, W, q); break;
+        case 3: fwd_pass<3>(smem, logN, s0, W, q); break;
+        case 2: fwd_pass<2>(smem, logN, s0, W, q); break;
+        default: fwd_pass<1>(smem, logN, s0, W, q); break;
+      }
+      __syncthreads();
+      s0 += r;
+    }
+    for (int k = threadIdx.x; k < N; k += blockDim.x) epi.put(es, k, smem[pidx(k)]);
     __syncthreads();
   }
 }
 
 template <class Pro, class Epi>
-__global__ void __launch_bounds__(512) k_ntt_inv(Pro pro, Epi epi, const DPrime* __restrict__ primes,
-                                                 const u64* __restrict__ tw, const u64* __restrict__ tws, int logN,
-                                                 int n_items, int lr, int limb_lo, int lvl, int L) {
+__global__ void __launch_bounds__(512) k_ntti_gen(const __grid_constant__ Pro pro, const __grid_constant__ Epi epi,
+                                                  const DPrime* __restrict__ primes,
+                                                  const ulonglong2* __restrict__ tw, int logN, int n_items, int lr,
+                                                  int limb_lo, int lvl, int L) {
   extern __shared__ u64 smem[];
   const int N = 1 << logN;
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
     const int p = item / lr, l = limb_lo + item % lr;
     const int pi = l < lvl ? l : L + (l - lvl);
-    if (!pro.load(smem, p, l, pi, primes, N)) continue;
+    typename Pro::State ps;
+    if (!pro.begin(ps, p, l, pi, primes, logN)) continue;
+    typename Epi::State es;
+    epi.begin(es, p, l, pi, primes, logN);
+    for (int k = threadIdx.x; k < N; k += blockDim.x) smem[pidx(k)] = pro.get(ps, k);
     __syncthreads();
     const DPrime P = primes[pi];
-    ntt_inv_core(smem, logN, tw + (size_t)pi * N, tws + (size_t)pi * N, P.q, P);
-    epi.store(smem, p, l, pi, primes, N);
+    const ulonglong2* W = tw + ((size_t)pi << logN);
+    const int np = (logN + 3) / 4;
+    int top = logN;
+    for (int i = 0; i < np; i++) {
+      const int r = pass_bits(logN, i);
+      const int s_lo = top - r;
+      switch (r) {
+        case 4: inv_pass<4>(smem, logN, s_lo, W, P.q, P); break;
+        case 3: inv_pass<3>(smem, logN, s_lo, W, P.q, P); break;
+        case 2: inv_pass<2>(smem, logN, s_lo, W, P.q, P); break;
+        default: inv_pass<1>(smem, logN, s_lo, W, P.q, P); break;
+      }
+      __syncthreads();
+      top = s_lo;
+    }
+    for (int k = threadIdx.x; k < N; k += blockDim.x) epi.put(es, k, smem[pidx(k)]);
     __syncthreads();
   }
 }
 
-static int ntt_threads(int N) {
-  int t = N / 16;
-  if (t < 32) t = 32;
-  if (t > 512) t = 512;
-  return t;
-}
+// ---------------------------------------------------------------------------------
+// Launch helpers.
+// ---------------------------------------------------------------------------------
 static size_t ntt_smem(int N) { return (size_t)(N + N / 16) * sizeof(u64); }
 
 template <class K>
 static int grid_for(ctl_context* c, K kern, int threads, size_t smem, int items) {
-  static thread_local std::map<std::pair<const void*, size_t>, int> cache;
-  auto key = std::make_pair((const void*)kern, smem);
-  auto it = cache.find(key);
+  static std::map<std::pair<const void*, size_t>, int> cache;
+  static std::mutex mu;
   int per_sm;
-  if (it == cache.end()) {
-    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
-    if (per_sm < 1) per_sm = 1;
-    cache[key] = per_sm;
-  } else {
-    per_sm = it->second;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_pair((const void*)kern, smem);
+    auto it = cache.find(key);
+    if (it == cache.end()) {
+      if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      per_sm = 1;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+      if (per_sm < 1) per_sm = 1;
+      cache[key] = per_sm;
+    } else {
+      per_sm = it->second;
+    }
   }
   int g = c->sm_count * per_sm;
   return items < g ? items : g;
 }
 
-template <class Pro, class Epi>
-static void run_fwd(ctl_context* c, int cls, const Pro& pro, const Epi& epi, int n_polys, int limb_lo, int limb_hi,
-                    int lvl, double work_per_limb) {
-  const int lr = limb_hi - limb_lo;
-  const int items = n_polys * lr;
-  if (items <= 0) return;
-  const int N = (int)c->N, th = ntt_threads(N);
-  const size_t sm = ntt_smem(N);
-  auto kern = k_ntt_fwd<Pro, Epi>;
-  const int grid = grid_for(c, kern, th, sm, items);
-  cudaEvent_t ev;
-  timing_begin(c, cls, &ev);
-  kern<<<grid, th, sm, c->stream>>>(pro, epi, c->d_primes, c->d_tw, c->d_tw_sh, (int)c->logN, items, lr, limb_lo, lvl,
-                                    (int)c->L);
-  c->launch_count++;
-  timing_end(c, cls, ev, work_per_limb * items);
+template <bool INV, int LOGN, class Pro, class Epi>
+static void launch_reg(ctl_context* c, const Pro& pro, const Epi& epi, int items, int lr, int limb_lo, int lvl) {
+  const int th = (1 << LOGN) / 32;
+  const size_t sm = ntt_smem(1 << LOGN);
+  const ulonglong2* tw = (const ulonglong2*)(INV ? c->d_itw2 : c->d_tw2);
+  if constexpr (INV) {
+    auto kern = k_ntti_reg<LOGN, Pro, Epi>;
+    const int grid = grid_for(c, kern, th, sm, items);
+    kern<<<grid, th, sm, c->stream>>>(pro, epi, c->d_primes, tw, items, lr, limb_lo, lvl, (int)c->L);
+  } else {
+    auto kern = k_nttf_reg<LOGN, Pro, Epi>;
+    const int grid = grid_for(c, kern, th, sm, items);
+    kern<<<grid, th, sm, c->stream>>>(pro, epi, c->d_primes, tw, items, lr, limb_lo, lvl, (int)c->L);
+  }
 }
 
-template <class Pro, class Epi>
-static void run_inv(ctl_context* c, int cls, const Pro& pro, const Epi& epi, int n_polys, int limb_lo, int limb_hi,
+template <bool INV, class Pro, class Epi>
+static void run_ntt(ctl_context* c, int cls, const Pro& pro, const Epi& epi, int n_polys, int limb_lo, int limb_hi,
                     int lvl, double work_per_limb) {
   const int lr = limb_hi - limb_lo;
   const int items = n_polys * lr;
   if (items <= 0) return;
-  const int N = (int)c->N, th = ntt_threads(N);
-  const size_t sm = ntt_smem(N);
-  auto kern = k_ntt_inv<Pro, Epi>;
-  const int grid = grid_for(c, kern, th, sm, items);
   cudaEvent_t ev;
   timing_begin(c, cls, &ev);
-  kern<<<grid, th, sm, c->stream>>>(pro, epi, c->d_primes, c->d_itw, c->d_itw_sh, (int)c->logN, items, lr, limb_lo,
-                                    lvl, (int)c->L);
+  switch (c->logN) {
+    case 12: launch_reg<INV, 12>(c, pro, epi, items, lr, limb_lo, lvl); break;
+    case 13: launch_reg<INV, 13>(c, pro, epi, items, lr, limb_lo, lvl); break;
+    case 14: launch_reg<INV, 14>(c, pro, epi, items, lr, limb_lo, lvl); break;
+    default: {
+      const int N = (int)c->N;
+      int th = N / 16;
+      th = th < 32 ? 32 : (th > 512 ? 512 : th);
+      const size_t sm = ntt_smem(N);
+      const ulonglong2* tw = (const ulonglong2*)(INV ? c->d_itw2 : c->d_tw2);
+      if constexpr (INV) {
+        auto kern = k_ntti_gen<Pro, Epi>;
+        const int grid = grid_for(c, kern, th, sm, items);
+        kern<<<grid, th, sm, c->stream>>>(pro, epi, c->d_primes, tw, (int)c->logN, items, lr, limb_lo, lvl,
+                                          (int)c->L);
+      } else {
+        auto kern = k_nttf_gen<Pro, Epi>;
+        const int grid = grid_for(c, kern, th, sm, items);
+        kern<<<grid, th, sm, c->stream>>>(pro, epi, c->d_primes, tw, (int)c->logN, items, lr, limb_lo, lvl,
+                                          (int)c->L);
+      }
+    }
+  }
   c->launch_count++;
   timing_end(c, cls, ev, work_per_limb * items);
 }
@@ -407,35 +738,43 @@ static void run_inv(ctl_context* c, int cls, const Pro& pro, const Epi& epi, int
 static double butterflies(const ctl_context* c) { return 0.5 * c->N * c->logN; }
 
 void launch_ntt_fwd(ctl_context* c, u64* data, size_t poly_stride, int n_polys, int limb_lo, int limb_hi, int lvl) {
-  run_fwd(c, KC_NTT_FWD, ProLoad{data, poly_stride}, EpiStore{data, poly_stride}, n_polys, limb_lo, limb_hi, lvl,
-          butterflies(c));
+  run_ntt<false>(c, KC_NTT_FWD, ProLoad{data, poly_stride}, EpiStore{data, poly_stride}, n_polys,
+                 limb_lo, limb_hi, lvl, butterflies(c));
 }
 
 void launch_ntt_inv(ctl_context* c, u64* data, size_t poly_stride, int n_polys, int limb_lo, int limb_hi, int lvl) {
-  run_inv(c, KC_NTT_INV, ProLoad{data, poly_stride}, EpiStore{data, poly_stride}, n_polys, limb_lo, limb_hi, lvl,
-          butterflies(c));
+  run_ntt<true>(c, KC_NTT_INV, ProLoad{data, poly_stride}, EpiStore{data, poly_stride}, n_polys,
+                limb_lo, limb_hi, lvl, butterflies(c));
+}
+
+void launch_ntt_inv_oop(ctl_context* c, const u64* src, size_t src_stride, u64* dst, size_t dst_stride, int n_polys,
+                        int limb_lo, int limb_hi, int lvl) {
+  // limb l of poly p: read at src + p*src_stride + l*N, written at dst + p*dst_stride + l*N
+  run_ntt<true>(c, KC_NTT_INV, ProLoad{src, src_stride}, EpiStore{dst, dst_stride}, n_polys,
+                limb_lo, limb_hi, lvl, butterflies(c));
 }
 
 void launch_intt_rescale_last(ctl_context* c, const u64* in, size_t poly_stride, int n_polys, int lvl, u64* r_out) {
   const RescaleTab& R = c->rescale_tabs[lvl];
-  // limb lvl-1 of poly p is read at in + p*poly_stride + (lvl-1)*N; the store functor
-  // writes r_out[p].
-  run_inv(c, KC_RESCALE, ProLoad{in, poly_stride}, EpiRescaleLast{r_out, R.h}, n_polys, lvl - 1, lvl, lvl,
-          butterflies(c));
+  // limb lvl-1 of poly p is read at in + p*poly_stride + (lvl-1)*N; r_out[p] is written.
+  run_ntt<true>(c, KC_RESCALE, ProLoad{in, poly_stride}, EpiRescaleLast{r_out, R.h}, n_polys,
+                lvl - 1, lvl, lvl, butterflies(c));
 }
 
 void launch_rescale_ntt(ctl_context* c, const u64* r, const u64* in, size_t in_stride, u64* out, size_t out_stride,
                         int n_polys, int lvl) {
   const RescaleTab& R = c->rescale_tabs[lvl];
-  run_fwd(c, KC_RESCALE, ProRescale{r, R.h}, EpiRescale{in, in_stride, out, out_stride, R.inv, R.inv_sh}, n_polys, 0,
-          lvl - 1, lvl, butterflies(c) + 2.0 * c->N);
+  ProRescale pro{r, R.h};
+  EpiRescale epi{in, in_stride, out, out_stride, R.inv, R.inv_sh};
+  run_ntt<false>(c, KC_RESCALE, pro, epi, n_polys, 0, lvl - 1, lvl, butterflies(c) + 2.0 * c->N);
 }
 
-void launch_modup_ntt(ctl_context* c, const u64* src_coef, size_t coef_stride, const u64* src_ntt, size_t src_stride,
-                      int nb, int lvl, u64* ext) {
+template <int NS>
+static void modup_ns(ctl_context* c, const u64* src_coef, size_t coef_stride, const u64* src_ntt, size_t src_stride,
+                     int nb, int lvl, u64* ext) {
   const int nd = (lvl + (int)c->alpha - 1) / (int)c->alpha;
   const int E = lvl + (int)c->K;
-  ProModUp pro;
+  ProModUp<NS> pro;
   pro.coef = src_coef;
   pro.coef_stride = coef_stride;
   pro.ntt = src_ntt;
@@ -445,15 +784,32 @@ void launch_modup_ntt(ctl_context* c, const u64* src_coef, size_t coef_stride, c
   pro.E = E;
   pro.lvl = lvl;
   pro.alpha = (int)c->alpha;
-  for (int d = 0; d < nd && d < CTL_MAX_DIGITS; d++) pro.tabs[d] = c->modup_tabs[(size_t)(lvl - 1) * c->beta + d];
-  run_fwd(c, KC_MODUP, pro, EpiStore{ext, (size_t)E * c->N}, nb * nd, 0, E, lvl,
-          butterflies(c) + (double)c->alpha * 2.0 * c->N);
+  for (int d = 0; d < CTL_MAX_DIGITS; d++)
+    pro.tabs[d] = d < nd ? c->modup_tabs[(size_t)(lvl - 1) * c->beta + d] : ConvTab{};
+  run_ntt<false>(c, KC_MODUP, pro, EpiStore{ext, (size_t)E * c->N}, nb * nd, 0, E, lvl,
+                 butterflies(c) + (double)c->alpha * 2.0 * c->N);
 }
 
-void launch_moddown_ntt(ctl_context* c, const u64* acc, int nr, int nb, int lvl, u64* out, const u64* addend,
-                        size_t add_r, size_t add_b, size_t add_p, bool add_both, const RotList& rl) {
+void launch_modup_ntt(ctl_context* c, const u64* src_coef, size_t coef_stride, const u64* src_ntt, size_t src_stride,
+                      int nb, int lvl, u64* ext) {
+  switch (c->alpha) {
+    case 1: modup_ns<1>(c, src_coef, coef_stride, src_ntt, src_stride, nb, lvl, ext); break;
+    case 2: modup_ns<2>(c, src_coef, coef_stride, src_ntt, src_stride, nb, lvl, ext); break;
+    case 3:
+    case 4: modup_ns<4>(c, src_coef, coef_stride, src_ntt, src_stride, nb, lvl, ext); break;
+    default: modup_ns<8>(c, src_coef, coef_stride, src_ntt, src_stride, nb, lvl, ext); break;
+  }
+}
+
+template <int NS>
+static void moddown_ns(ctl_context* c, const u64* acc, int nr, int nb, int lvl, u64* out, const u64* addend,
+                       size_t add_r, size_t add_b, size_t add_p, bool add_both, const RotList& rl) {
   const int E = lvl + (int)c->K;
-  ProModDown pro{acc, (size_t)E * c->N, lvl, c->moddown.conv};
+  ProModDown<NS> pro;
+  pro.acc = acc;
+  pro.acc_stride = (size_t)E * c->N;
+  pro.lvl = lvl;
+  pro.tab = c->moddown.conv;
   EpiModDown epi;
   epi.acc = acc;
   epi.acc_stride = (size_t)E * c->N;
@@ -466,17 +822,20 @@ void launch_moddown_ntt(ctl_context* c, const u64* acc, int nr, int nb, int lvl,
   epi.add_b = add_b;
   epi.add_p = add_p;
   epi.add_both = add_both ? 1 : 0;
-  for (int r = 0; r < CTL_MAX_ROT; r++) epi.g[r] = r < rl.n ? rl.g[r] : 1;
   epi.nb = nb;
-  epi.logN = (int)c->logN;
-  run_fwd(c, KC_MODDOWN, pro, epi, nr * nb * 2, 0, lvl, lvl, butterflies(c) + (double)(c->K * 2 + 1) * c->N);
+  for (int r = 0; r < CTL_MAX_ROT; r++) epi.g[r] = r < rl.n ? rl.g[r] : 1;
+  run_ntt<false>(c, KC_MODDOWN, pro, epi, nr * nb * 2, 0, lvl, lvl, butterflies(c) + (double)(c->K * 2 + 1) * c->N);
 }
 
-void launch_ntt_inv_oop(ctl_context* c, const u64* src, size_t src_stride, u64* dst, size_t dst_stride, int n_polys,
-                        int limb_lo, int limb_hi, int lvl) {
-  // limb l of poly p: read at src + p*src_stride + l*N, written at dst + p*dst_stride + l*N
-  run_inv(c, KC_NTT_INV, ProLoad{src, src_stride}, EpiStore{dst, dst_stride}, n_polys, limb_lo, limb_hi, lvl,
-          butterflies(c));
+void launch_moddown_ntt(ctl_context* c, const u64* acc, int nr, int nb, int lvl, u64* out, const u64* addend,
+                        size_t add_r, size_t add_b, size_t add_p, bool add_both, const RotList& rl) {
+  switch (c->K) {
+    case 1: moddown_ns<1>(c, acc, nr, nb, lvl, out, addend, add_r, add_b, add_p, add_both, rl); break;
+    case 2: moddown_ns<2>(c, acc, nr, nb, lvl, out, addend, add_r, add_b, add_p, add_both, rl); break;
+    case 3:
+    case 4: moddown_ns<4>(c, acc, nr, nb, lvl, out, addend, add_r, add_b, add_p, add_both, rl); break;
+    default: moddown_ns<8>(c, acc, nr, nb, lvl, out, addend, add_r, add_b, add_p, add_both, rl); break;
+  }
 }
 
 }  // namespace ctl
