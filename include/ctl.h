@@ -192,6 +192,30 @@ int ctl_ntt_dev(ctl_context* ctx, const uint64_t* in_dev, uint64_t* out_dev, uin
                 int inverse);
 
 /* ---------------------------------------------------------------------------------
+ * Rescale with no device allocation (no counterpart in the paper: a deployment aid).
+ * For callers that must not allocate device memory while they run -- a host framework
+ * that already owns the device's memory through its own arena, or a latency-critical
+ * serving thread where an allocation could stall or fail mid-request.  Same arithmetic
+ * as ctl_rescale, on the caller's device buffers: in_dev holds `count` ciphertexts
+ * [count][2][level][N] in NTT form (as ctl_ntt_dev produces them, limb l modulo q_l),
+ * out_dev receives [count][2][level-1][N], also NTT form.  The only scratch space used
+ * is a fixed array compiled into the library (ctl_rescale_static_capacity_words()
+ * 64-bit words = 4 MiB, held on every GPU that loads the library until the process
+ * exits); count * 2 * N must not exceed it (else CTL_EINVAL, with the limit in
+ * ctl_last_error()).  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current; make that first call before any
+ * stream capture.  All calls share the one array: calls whose GPU work overlaps (on
+ * different streams or contexts of the same device) race and corrupt each other;
+ * order them on one stream.  Nothing in the array needs to start at zero.  Work is
+ * ordered on the context stream; the call does not synchronise.  Keep kernel timing
+ * (ctl_stats_enable_timing) off around it: timing records CUDA events from a pool.
+ * Errors: CTL_EINVAL, CTL_ELEVEL (level < 2), CTL_ECUDA.
+ * ------------------------------------------------------------------------------- */
+int ctl_rescale_static_dev(ctl_context* ctx, const uint64_t* in_dev, uint64_t* out_dev, uint32_t count,
+                           uint32_t level);
+size_t ctl_rescale_static_capacity_words(void);
+
+/* ---------------------------------------------------------------------------------
  * Models: the frozen server layers of Fig. alg:cryptotl (M_S), encoded once.
  * A layer is CTL_LAYER_DENSE (W m x n, optional bias, optional injected coefficients
  * pt_coeffs[t][N]), CTL_LAYER_SQUARE or CTL_LAYER_REPLICATE (t = rep_t).  The model is

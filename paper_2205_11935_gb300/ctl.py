@@ -77,6 +77,8 @@ SIGNATURES = {
     "ctl_add": (C.c_int, [_vp, _vp, _vp, _pp]),
     "ctl_mul_plain_coeffs": (C.c_int, [_vp, _vp, _i64p, C.c_double, _pp]),
     "ctl_ntt_dev": (C.c_int, [_vp, _vp, _vp, C.c_uint32, C.c_uint32, C.c_int]),
+    "ctl_rescale_static_dev": (C.c_int, [_vp, _vp, _vp, C.c_uint32, C.c_uint32]),
+    "ctl_rescale_static_capacity_words": (C.c_size_t, []),
     "ctl_model_create": (C.c_int, [_vp, C.POINTER(Layer), C.c_uint32, C.c_uint32, C.c_double, _pp]),
     "ctl_model_destroy": (None, [_vp]),
     "ctl_model_rotations": (C.c_int, [_vp, _i32p, C.c_uint32, _u32p]),
@@ -289,9 +291,11 @@ class Keys:
         return out
 
     def close(self):
-        if getattr(self, "h", None):
+        # a handle outlives nothing: once its context is destroyed, the context took its
+        # device memory with it and the handle must not be released again
+        if getattr(self, "h", None) and getattr(self.ctx, "h", None):
             lib().ctl_keys_destroy(self.h)
-            self.h = None
+        self.h = None
 
 
 class Ciphertext:
@@ -327,9 +331,9 @@ class Ciphertext:
         return Ciphertext(self.ctx, h)
 
     def close(self):
-        if getattr(self, "h", None):
+        if getattr(self, "h", None) and getattr(self.ctx, "h", None):
             lib().ctl_ct_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:
@@ -392,6 +396,6 @@ class Model:
         return Ciphertext(self.ctx, h)
 
     def close(self):
-        if getattr(self, "h", None):
+        if getattr(self, "h", None) and getattr(self.ctx, "h", None):
             lib().ctl_model_destroy(self.h)
-            self.h = None
+        self.h = None
