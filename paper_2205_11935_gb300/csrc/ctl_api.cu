@@ -271,6 +271,7 @@ static int build_tables(ctl_context* c) {
     t.sinv_sh = c->d_tables + p.sinv_sh;
     t.sq = c->d_tables + p.sq;
     t.cmont = c->d_tables + p.cmont;
+    t.premul = 1;  // the inverse NTT before every conversion folds in Shat_j^-1
     return t;
   };
   for (auto& p : modup_p) c->modup_tabs.push_back(mk(p));
@@ -286,6 +287,44 @@ static int build_tables(ctl_context* c) {
     R.qlast = m[lvl - 1];
     R.h = m[lvl - 1] / 2;
   }
+  // Inverse-NTT last-stage constants with a conversion factor folded in:
+  //   ModDown: factor Phat_j^-1 mod p_j on special prime j;
+  //   ModUp at level lvl: factor Qhat_i^-1 mod q_i for data prime i of its (live) digit.
+  auto fold = [&](uint32_t pi, u64 f) {
+    const DPrime& P = c->h_primes[pi];
+    const u64 q = P.q;
+    InvScale s;
+    s.ninv = h_mulmod(f % q, P.ninv, q);
+    s.ninv_sh = h_shoup(s.ninv, q);
+    s.iw1 = h_mulmod(f % q, P.iw1, q);
+    s.iw1_sh = h_shoup(s.iw1, q);
+    return s;
+  };
+  std::vector<InvScale> mds(LK), mu((size_t)L * LK);
+  for (uint32_t pi = 0; pi < LK; pi++) mds[pi] = fold(pi, 1);
+  for (uint32_t j = 0; j < K; j++) {
+    const u64 pj = m[L + j];
+    u64 prod = 1;
+    for (uint32_t o = 0; o < K; o++)
+      if (o != j) prod = h_mulmod(prod, m[L + o] % pj, pj);
+    mds[L + j] = fold(L + j, h_invmod(prod, pj));
+  }
+  for (uint32_t lvl = 1; lvl <= L; lvl++) {
+    InvScale* row = &mu[(size_t)(lvl - 1) * LK];
+    for (uint32_t pi = 0; pi < LK; pi++) row[pi] = fold(pi, 1);
+    for (uint32_t i = 0; i < lvl; i++) {
+      const uint32_t d0 = (i / c->alpha) * c->alpha, d1 = std::min(d0 + c->alpha, lvl);
+      u64 prod = 1;
+      for (uint32_t o = d0; o < d1; o++)
+        if (o != i) prod = h_mulmod(prod, m[o] % m[i], m[i]);
+      row[i] = fold(i, h_invmod(prod, m[i]));
+    }
+  }
+  if ((rc = cuda_check(cudaMalloc(&c->d_md_scale, (mds.size() + mu.size()) * sizeof(InvScale)), "cudaMalloc scale")))
+    return rc;
+  c->d_mu_scale = c->d_md_scale + mds.size();
+  cudaMemcpy(c->d_md_scale, mds.data(), mds.size() * sizeof(InvScale), cudaMemcpyHostToDevice);
+  cudaMemcpy(c->d_mu_scale, mu.data(), mu.size() * sizeof(InvScale), cudaMemcpyHostToDevice);
   return cuda_check(cudaGetLastError(), "table upload");
 }
 
@@ -347,6 +386,7 @@ extern "C" void ctl_context_destroy(ctl_context* c) {
   cudaFree(c->d_primes);
   cudaFree(c->d_tw2);
   cudaFree(c->d_tables);
+  cudaFree(c->d_md_scale);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -808,13 +848,16 @@ int keyswitch(ctl_context* c, int nr, int nb, int lvl, const u64* x, size_t x_r,
     rl.g[r] = r < nr ? gs[r] : 1;
   }
   // 1. coefficient form of the inputs
-  launch_ntt_inv_oop(c, x, x_b, xc.p, (size_t)lvl * N, n_in, 0, lvl, lvl);
+  // (the digit factors Qhat_i^-1 of the ModUp conversion are folded into this transform)
+  launch_ntt_inv_oop(c, x, x_b, xc.p, (size_t)lvl * N, n_in, 0, lvl, lvl,
+                     c->d_mu_scale + (size_t)(lvl - 1) * (c->L + c->K));
   // 2. ModUp + NTT of every digit
   launch_modup_ntt(c, xc.p, (size_t)lvl * N, x, x_b, n_in, lvl, ext.p);
   // 3. key inner products (automorphism folded into the gather)
   launch_key_ip(c, ext.p, hoisted ? 0 : (size_t)nb * nd * E * N, nb, lvl, rl, acc.p);
   // 4. ModDown: special limbs to coefficient form, then conversion + NTT + combine
-  launch_ntt_inv(c, acc.p, (size_t)E * N, nr * nb * 2, lvl, E, lvl);
+  // (the factors Phat_j^-1 of the ModDown conversion are folded into this transform)
+  launch_ntt_inv_oop(c, acc.p, (size_t)E * N, acc.p, (size_t)E * N, nr * nb * 2, lvl, E, lvl, c->d_md_scale);
   launch_moddown_ntt(c, acc.p, nr, nb, lvl, out, addend, add_r, add_b, add_p, add_both, rl);
   return last_cuda("keyswitch");
 }

@@ -34,6 +34,7 @@ struct DPrime {
 struct ConvTab {
   int ns;               // |S|
   int nt;               // number of target positions
+  int premul;           // 1: the source limbs already carry the factor Shat_j^-1 mod s_j
   const u64* sinv;      // [ns] Shat_j^-1 mod s_j
   const u64* sinv_sh;   // [ns] Shoup companions
   const u64* sq;        // [ns] source primes
@@ -55,6 +56,13 @@ struct RotList {
   int n;
   const u64* key[CTL_MAX_ROT];  // device key [beta][2][L+K][N] (Montgomery, NTT form)
   u64 g[CTL_MAX_ROT];           // Galois element (1 = no automorphism)
+};
+
+// Last-stage constants of an inverse NTT that also multiplies its output by a per-prime
+// factor c (c * N^-1 and c * (psi^-1)^bitrev(1) * N^-1 with Shoup companions): folding
+// the factor Shat_j^-1 of a base conversion into the transform that precedes it.
+struct InvScale {
+  u64 ninv, ninv_sh, iw1, iw1_sh;
 };
 
 // ModDown constants (special primes P -> data primes).
@@ -152,6 +160,8 @@ struct ctl_context {
   std::vector<ctl::ConvTab> modup_tabs;      // index (lvl-1)*beta + d
   std::vector<ctl::RescaleTab> rescale_tabs; // index lvl (valid for lvl >= 2)
   ctl::ModDownTab moddown;
+  ctl::InvScale* d_md_scale = nullptr;  // [L+K]: factor Phat_j^-1 on the special primes
+  ctl::InvScale* d_mu_scale = nullptr;  // [L][L+K]: level lvl's factor Qhat_i^-1 on data prime i
   std::vector<ctl::DPrime> h_primes;
   ctl::Encoder enc;
   ctl::Timing timing;
@@ -220,9 +230,10 @@ void launch_key_ip(ctl_context* c, const u64* ext, size_t ext_r_stride, int nb, 
 // read through sigma_{g_r}; t = 1 gets one only if add_both.
 void launch_moddown_ntt(ctl_context* c, const u64* acc, int nr, int nb, int lvl, u64* out, const u64* addend,
                         size_t add_r, size_t add_b, size_t add_p, bool add_both, const RotList& rl);
-// Out-of-place inverse NTT.
+// Out-of-place inverse NTT; with scl, limb output of prime pi is also multiplied by the
+// factor folded into scl[pi].
 void launch_ntt_inv_oop(ctl_context* c, const u64* src, size_t src_stride, u64* dst, size_t dst_stride, int n_polys,
-                        int limb_lo, int limb_hi, int lvl);
+                        int limb_lo, int limb_hi, int lvl, const InvScale* scl = nullptr);
 
 // Elementwise (kernels.cu).
 void launch_add(ctl_context* c, const u64* a, const u64* b, u64* out, int n_polys, int lvl, size_t stride_a,

@@ -143,12 +143,13 @@ struct EpiStore {
 // exact residue in [0, t).
 template <int NS>
 struct ConvState {
-  int ns;
+  int ns, premul;
   const u64* srcs[NS];
   u64 sinv[NS], sinv_sh[NS], sq[NS], cm[NS];
   u64 t, tinv;
   __device__ void bind(const ConvTab& T, int tpos, const u64* base, size_t limb0, int logN, u64 tq, u64 ti) {
     ns = T.ns;
+    premul = T.premul;
 #pragma unroll
     for (int j = 0; j < NS; j++) {
       const int jj = j < ns ? j : 0;
@@ -165,7 +166,7 @@ struct ConvState {
     u64 lo = 0, hi = 0;
 #pragma unroll
     for (int j = 0; j < NS; j++)
-      if (j < ns) mac(lo, hi, shoup(srcs[j][k], sinv[j], sinv_sh[j], sq[j]), cm[j]);
+      if (j < ns) mac(lo, hi, premul ? srcs[j][k] : shoup(srcs[j][k], sinv[j], sinv_sh[j], sq[j]), cm[j]);
     return redc(hi, lo, t, tinv);
   }
   // C elements t0 + T*k of one thread: every source load is issued before any arithmetic
@@ -183,7 +184,7 @@ struct ConvState {
         u64 lo = 0, hi = 0;
 #pragma unroll
         for (int j = 0; j < NS; j++)
-          if (j < ns) mac(lo, hi, shoup(v[j][k], sinv[j], sinv_sh[j], sq[j]), cm[j]);
+          if (j < ns) mac(lo, hi, premul ? v[j][k] : shoup(v[j][k], sinv[j], sinv_sh[j], sq[j]), cm[j]);
         x[k] = redc(hi, lo, t, tinv);
       }
     } else {
@@ -459,7 +460,7 @@ template <int LOGN, class Pro, class Epi>
 __global__ void __launch_bounds__((1 << LOGN) / 32, 16384 / (1 << LOGN))
 k_ntti_reg(const __grid_constant__ Pro pro, const __grid_constant__ Epi epi, const DPrime* __restrict__ primes,
                                                                const ulonglong2* __restrict__ tw, int n_items, int lr,
-                                                               int limb_lo, int lvl, int L) {
+                                                               int limb_lo, int lvl, int L, const InvScale* __restrict__ scl) {
   constexpr int N = 1 << LOGN, T = N / 32, RC = LOGN - 10, R = 1 << RC;
   extern __shared__ u64 smem[];
   const int t = threadIdx.x;
@@ -470,7 +471,14 @@ k_ntti_reg(const __grid_constant__ Pro pro, const __grid_constant__ Epi epi, con
     if (!pro.begin(ps, p, l, pi, primes, LOGN)) continue;
     typename Epi::State es;
     epi.begin(es, p, l, pi, primes, LOGN);
-    const DPrime P = primes[pi];
+    DPrime P = primes[pi];
+    if (scl) {  // output also multiplied by the factor folded into scl[pi]
+      const InvScale f = scl[pi];
+      P.ninv = f.ninv;
+      P.ninv_sh = f.ninv_sh;
+      P.iw1 = f.iw1;
+      P.iw1_sh = f.iw1_sh;
+    }
     const u64 q = P.q;
     const ulonglong2* W = tw + ((size_t)pi << LOGN);
     u64 x[32];
@@ -623,7 +631,7 @@ template <class Pro, class Epi>
 __global__ void __launch_bounds__(512) k_ntti_gen(const __grid_constant__ Pro pro, const __grid_constant__ Epi epi,
                                                   const DPrime* __restrict__ primes,
                                                   const ulonglong2* __restrict__ tw, int logN, int n_items, int lr,
-                                                  int limb_lo, int lvl, int L) {
+                                                  int limb_lo, int lvl, int L, const InvScale* __restrict__ scl) {
   extern __shared__ u64 smem[];
   const int N = 1 << logN;
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
@@ -635,7 +643,14 @@ __global__ void __launch_bounds__(512) k_ntti_gen(const __grid_constant__ Pro pr
     epi.begin(es, p, l, pi, primes, logN);
     for (int k = threadIdx.x; k < N; k += blockDim.x) smem[pidx(k)] = pro.get(ps, k);
     __syncthreads();
-    const DPrime P = primes[pi];
+    DPrime P = primes[pi];
+    if (scl) {  // output also multiplied by the factor folded into scl[pi]
+      const InvScale f = scl[pi];
+      P.ninv = f.ninv;
+      P.ninv_sh = f.ninv_sh;
+      P.iw1 = f.iw1;
+      P.iw1_sh = f.iw1_sh;
+    }
     const ulonglong2* W = tw + ((size_t)pi << logN);
     const int np = (logN + 3) / 4;
     int top = logN;
@@ -685,14 +700,15 @@ static int grid_for(ctl_context* c, K kern, int threads, size_t smem, int items)
 }
 
 template <bool INV, int LOGN, class Pro, class Epi>
-static void launch_reg(ctl_context* c, const Pro& pro, const Epi& epi, int items, int lr, int limb_lo, int lvl) {
+static void launch_reg(ctl_context* c, const Pro& pro, const Epi& epi, int items, int lr, int limb_lo, int lvl,
+                       const InvScale* scl) {
   const int th = (1 << LOGN) / 32;
   const size_t sm = ntt_smem(1 << LOGN);
   const ulonglong2* tw = (const ulonglong2*)(INV ? c->d_itw2 : c->d_tw2);
   if constexpr (INV) {
     auto kern = k_ntti_reg<LOGN, Pro, Epi>;
     const int grid = grid_for(c, kern, th, sm, items);
-    kern<<<grid, th, sm, c->stream>>>(pro, epi, c->d_primes, tw, items, lr, limb_lo, lvl, (int)c->L);
+    kern<<<grid, th, sm, c->stream>>>(pro, epi, c->d_primes, tw, items, lr, limb_lo, lvl, (int)c->L, scl);
   } else {
     auto kern = k_nttf_reg<LOGN, Pro, Epi>;
     const int grid = grid_for(c, kern, th, sm, items);
@@ -702,16 +718,16 @@ static void launch_reg(ctl_context* c, const Pro& pro, const Epi& epi, int items
 
 template <bool INV, class Pro, class Epi>
 static void run_ntt(ctl_context* c, int cls, const Pro& pro, const Epi& epi, int n_polys, int limb_lo, int limb_hi,
-                    int lvl, double work_per_limb) {
+                    int lvl, double work_per_limb, const InvScale* scl = nullptr) {
   const int lr = limb_hi - limb_lo;
   const int items = n_polys * lr;
   if (items <= 0) return;
   cudaEvent_t ev;
   timing_begin(c, cls, &ev);
   switch (c->logN) {
-    case 12: launch_reg<INV, 12>(c, pro, epi, items, lr, limb_lo, lvl); break;
-    case 13: launch_reg<INV, 13>(c, pro, epi, items, lr, limb_lo, lvl); break;
-    case 14: launch_reg<INV, 14>(c, pro, epi, items, lr, limb_lo, lvl); break;
+    case 12: launch_reg<INV, 12>(c, pro, epi, items, lr, limb_lo, lvl, scl); break;
+    case 13: launch_reg<INV, 13>(c, pro, epi, items, lr, limb_lo, lvl, scl); break;
+    case 14: launch_reg<INV, 14>(c, pro, epi, items, lr, limb_lo, lvl, scl); break;
     default: {
       const int N = (int)c->N;
       int th = N / 16;
@@ -722,7 +738,7 @@ static void run_ntt(ctl_context* c, int cls, const Pro& pro, const Epi& epi, int
         auto kern = k_ntti_gen<Pro, Epi>;
         const int grid = grid_for(c, kern, th, sm, items);
         kern<<<grid, th, sm, c->stream>>>(pro, epi, c->d_primes, tw, (int)c->logN, items, lr, limb_lo, lvl,
-                                          (int)c->L);
+                                          (int)c->L, scl);
       } else {
         auto kern = k_nttf_gen<Pro, Epi>;
         const int grid = grid_for(c, kern, th, sm, items);
@@ -748,10 +764,10 @@ void launch_ntt_inv(ctl_context* c, u64* data, size_t poly_stride, int n_polys, 
 }
 
 void launch_ntt_inv_oop(ctl_context* c, const u64* src, size_t src_stride, u64* dst, size_t dst_stride, int n_polys,
-                        int limb_lo, int limb_hi, int lvl) {
+                        int limb_lo, int limb_hi, int lvl, const InvScale* scl) {
   // limb l of poly p: read at src + p*src_stride + l*N, written at dst + p*dst_stride + l*N
-  run_ntt<true>(c, KC_NTT_INV, ProLoad{src, src_stride}, EpiStore{dst, dst_stride}, n_polys,
-                limb_lo, limb_hi, lvl, butterflies(c));
+  run_ntt<true>(c, KC_NTT_INV, ProLoad{src, src_stride}, EpiStore{dst, dst_stride}, n_polys, limb_lo, limb_hi, lvl,
+                butterflies(c), scl);
 }
 
 void launch_intt_rescale_last(ctl_context* c, const u64* in, size_t poly_stride, int n_polys, int lvl, u64* r_out) {
