@@ -38,6 +38,13 @@ __device__ __forceinline__ uint32_t auto_src(uint32_t k, u64 g, int logN) {
   return brv_dev((e2 - 1u) >> 1, logN);
 }
 
+// Asynchronous bulk prefetch of a contiguous global range into L2 (one instruction, no
+// registers); the range is 16-byte aligned and a multiple of 16 bytes (whole limbs).
+__device__ __forceinline__ void l2_prefetch(const void* p, uint32_t bytes) {
+  const unsigned long long g = (unsigned long long)__cvta_generic_to_global(p);
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(g), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ void ct_bfly(u64& x, u64& y, const ulonglong2 w, u64 q) {
   const u64 q2 = 2 * q;
   u64 X = x;
@@ -112,6 +119,9 @@ struct ProLoad {
     return true;
   }
   __device__ u64 get(const State& st, int j) const { return st.g[j]; }
+  __device__ void prefetch_src(int p, int l, int, int logN) const {
+    l2_prefetch(src + (size_t)p * poly_stride + ((size_t)l << logN), 8u << logN);
+  }
   template <int T, int C>
   __device__ void getc(const State& st, int t0, u64* x) const {
 #pragma unroll
@@ -131,6 +141,7 @@ struct EpiStore {
     st.q = pr[pi].q;
   }
   __device__ void put(const State& st, int j, u64 v) const { st.o[j] = reduce4(v, st.q); }
+  __device__ void prefetch(const State&, int) const {}
   template <int T, int C>
   __device__ void putc(const State& st, int t0, const u64* x) const {
 #pragma unroll
@@ -219,6 +230,15 @@ struct ProModUp {
     st.bind(tabs[d], l, coef + (size_t)b * coef_stride, (size_t)d0, logN, pr[pi].q, pr[pi].qinv);
     return true;
   }
+  __device__ void prefetch_src(int p, int l, int, int logN) const {
+    const int b = p / nd, d = p % nd;
+    const int d0 = d * alpha, d1 = min(d0 + alpha, lvl);
+    if (l >= d0 && l < d1) {
+      l2_prefetch(ntt + (size_t)b * stride + ((size_t)l << logN), 8u << logN);
+    } else {
+      for (int j = d0; j < d1; j++) l2_prefetch(coef + (size_t)b * coef_stride + ((size_t)j << logN), 8u << logN);
+    }
+  }
   __device__ u64 get(const State& st, int j) const { return st.eval(j); }
   template <int T, int C>
   __device__ void getc(const State& st, int t0, u64* x) const {
@@ -237,6 +257,9 @@ struct ProModDown {
   __device__ bool begin(State& st, int p, int l, int pi, const DPrime* pr, int logN) const {
     st.bind(tab, l, acc + (size_t)p * acc_stride, (size_t)lvl, logN, pr[pi].q, pr[pi].qinv);
     return true;
+  }
+  __device__ void prefetch_src(int p, int, int, int logN) const {
+    for (int j = 0; j < tab.ns; j++) l2_prefetch(acc + (size_t)p * acc_stride + ((size_t)(lvl + j) << logN), 8u << logN);
   }
   __device__ u64 get(const State& st, int j) const { return st.eval(j); }
   template <int T, int C>
@@ -282,6 +305,10 @@ struct EpiModDown {
       st.gg = g[r];
     }
   }
+  __device__ void prefetch(const State& st, int logN) const {
+    l2_prefetch(st.a, 8u << logN);
+    if (st.ad) l2_prefetch(st.ad, 8u << logN);
+  }
   __device__ void put(const State& st, int j, u64 v) const {
     u64 r = shoup(submod(st.a[j], reduce4(v, st.q), st.q), st.pv, st.pvs, st.q);
     if (st.ad) r = addmod(r, st.ad[st.gg == 1 ? (uint32_t)j : auto_src((uint32_t)j, st.gg, st.lg)], st.q);
@@ -317,6 +344,7 @@ struct EpiRescaleLast {   // inverse NTT of the last limb -> r = [x + h]_q_last
     st.q = pr[pi].q;
   }
   __device__ void put(const State& st, int j, u64 v) const { st.o[j] = addmod(reduce4(v, st.q), h, st.q); }
+  __device__ void prefetch(const State&, int) const {}
   template <int T, int C>
   __device__ void putc(const State& st, int t0, const u64* x) const {
 #pragma unroll
@@ -339,6 +367,7 @@ struct ProRescale {       // (r - h) mod q_i in coefficient form
     st.rm = pr[pi].rmod;
     return true;
   }
+  __device__ void prefetch_src(int p, int, int, int logN) const { l2_prefetch(r + ((size_t)p << logN), 8u << logN); }
   __device__ u64 get(const State& st, int j) const {
     const u64 v = st.g[j];
     return v >= h ? mulmod_mont(v - h, st.rm, st.q, st.qinv) : negmod(mulmod_mont(h - v, st.rm, st.q, st.qinv), st.q);
@@ -377,6 +406,7 @@ struct EpiRescale {       // out_i = (in_i - x) * q_last^-1
   __device__ void put(const State& st, int j, u64 v) const {
     st.o[j] = shoup(submod(st.a[j], reduce4(v, st.q), st.q), st.w, st.ws, st.q);
   }
+  __device__ void prefetch(const State& st, int logN) const { l2_prefetch(st.a, 8u << logN); }
   template <int T, int C>
   __device__ void putc(const State& st, int t0, const u64* x) const {
     u64 a[C];
@@ -405,6 +435,14 @@ k_nttf_reg(const __grid_constant__ Pro pro, const __grid_constant__ Epi epi, con
     if (!pro.begin(ps, p, l, pi, primes, LOGN)) continue;
     typename Epi::State es;
     epi.begin(es, p, l, pi, primes, LOGN);
+    if (threadIdx.x == 0) {  // L2 prefetch: this item's epilogue reads, the next item's sources
+      epi.prefetch(es, LOGN);
+      const int nx = item + gridDim.x;
+      if (nx < n_items) {
+        const int p2 = nx / lr, l2 = limb_lo + nx % lr;
+        pro.prefetch_src(p2, l2, l2 < lvl ? l2 : L + (l2 - lvl), LOGN);
+      }
+    }
     const u64 q = primes[pi].q;
     const ulonglong2* W = tw + ((size_t)pi << LOGN);
     u64 x[32];
@@ -471,6 +509,14 @@ k_ntti_reg(const __grid_constant__ Pro pro, const __grid_constant__ Epi epi, con
     if (!pro.begin(ps, p, l, pi, primes, LOGN)) continue;
     typename Epi::State es;
     epi.begin(es, p, l, pi, primes, LOGN);
+    if (threadIdx.x == 0) {  // L2 prefetch: this item's epilogue reads, the next item's sources
+      epi.prefetch(es, LOGN);
+      const int nx = item + gridDim.x;
+      if (nx < n_items) {
+        const int p2 = nx / lr, l2 = limb_lo + nx % lr;
+        pro.prefetch_src(p2, l2, l2 < lvl ? l2 : L + (l2 - lvl), LOGN);
+      }
+    }
     DPrime P = primes[pi];
     if (scl) {  // output also multiplied by the factor folded into scl[pi]
       const InvScale f = scl[pi];
