@@ -242,8 +242,56 @@ void ctl_model_destroy(ctl_model* model);
 /* Writes up to cap distinct rotation amounts to rot and their number to *n_rot. */
 int ctl_model_rotations(const ctl_model* model, int32_t* rot, uint32_t cap, uint32_t* n_rot);
 int ctl_model_forward(ctl_context* ctx, const ctl_model* model, const ctl_keys* keys, const ctl_ct* in, ctl_ct** out);
+/* The same forward, bit for bit, replayed from a CUDA graph.  The first call for a given
+ * (ctx, keys, batch size) runs the forward once eagerly, then captures the whole layer
+ * sequence (kernels, stream-ordered temporary allocations, copies) into a graph with
+ * fixed staging buffers; later calls copy the input into the staging buffer, replay the
+ * graph and copy the result out, with one launch instead of several hundred.  Calls
+ * for the same (ctx, model) must not overlap.  Needs the library's own allocator
+ * (CTL_ENOTSUP after ctl_set_allocator).  Graph memory is released by
+ * ctl_model_destroy. */
+int ctl_model_forward_graph(ctl_context* ctx, const ctl_model* model, const ctl_keys* keys, const ctl_ct* in,
+                            ctl_ct** out);
 /* Output level and scale of the model. */
 int ctl_model_info(const ctl_model* model, uint32_t* out_level, double* out_scale, uint64_t* bytes);
+
+/* ---------------------------------------------------------------------------------
+ * Context clones: same parameters and device tables, own stream.  Keys and models made
+ * with the original may be used with a clone, so one parameter set can run on several
+ * streams at once.  Destroy clones (ctl_context_destroy) before the original.
+ * ------------------------------------------------------------------------------- */
+int ctl_context_clone(const ctl_context* ctx, ctl_context** out);
+
+/* ---------------------------------------------------------------------------------
+ * Serving (Fig. alg:cryptotl: each client query is one ClassifyHE call).  A server has
+ * lanes (context + model, added before start) and clients (key set bound to a lane, kept
+ * resident).  ctl_server_submit copies one ciphertext (coefficient form, [2][L][N] at
+ * the lane's top level) and returns a request id, or CTL_EBUSY when max_queue requests
+ * wait.  n_workers threads, each with its own stream per lane, repeatedly take the oldest
+ * request, batch it with up to max_batch-1 other queued requests of the same client,
+ * admit the batch when its device-memory estimate fits under mem_budget_bytes (a batch
+ * of one always runs when nothing else is in flight), and run import -> forward ->
+ * export.  So requests arriving while others run are admitted as memory frees up, and
+ * different clients' batches overlap on the device.  ctl_server_poll returns CTL_OK
+ * with the result ([2][out_level][N]) and the request's latency (submit to completion),
+ * CTL_EBUSY while pending, or the negative code the request failed with (the server keeps
+ * serving).  ctl_server_wait blocks up to timeout_ms (then CTL_ETIMEOUT).
+ * ctl_server_stats: counts6 = submitted, completed, rejected, failed, batches, batched
+ * ciphertexts; latency percentiles in ms over completed requests.
+ * ------------------------------------------------------------------------------- */
+int ctl_server_create(ctl_server** out, uint64_t mem_budget_bytes, uint32_t n_workers, uint32_t max_batch,
+                      uint32_t max_queue);
+int ctl_server_add_lane(ctl_server* srv, ctl_context* ctx, const ctl_model* model, uint32_t* lane);
+int ctl_server_add_client(ctl_server* srv, uint32_t lane, const ctl_keys* keys, uint32_t* client);
+int ctl_server_io_words(const ctl_server* srv, uint32_t client, size_t* in_words, size_t* out_words);
+int ctl_server_start(ctl_server* srv);
+int ctl_server_submit(ctl_server* srv, uint32_t client, const uint64_t* ct_coeffs, uint64_t* request);
+int ctl_server_poll(ctl_server* srv, uint64_t request, uint64_t* out, size_t cap, double* latency_ms);
+int ctl_server_wait(ctl_server* srv, uint64_t request, uint32_t timeout_ms, uint64_t* out, size_t cap,
+                    double* latency_ms);
+int ctl_server_stats(ctl_server* srv, uint64_t* counts6, double* p50_ms, double* p99_ms);
+/* Stops the workers (queued requests are dropped) and releases the server. */
+void ctl_server_destroy(ctl_server* srv);
 
 /* ---------------------------------------------------------------------------------
  * Statistics: kernel launches since the last reset, homomorphic operation counters

@@ -6,6 +6,8 @@
 #include <cmath>
 #include <algorithm>
 #include <memory>
+#include <tuple>
+#include <mutex>
 #include <new>
 #include "ctl_internal.h"
 #include "modarith.cuh"
@@ -383,12 +385,56 @@ extern "C" void ctl_context_destroy(ctl_context* c) {
     cudaEventDestroy(pe.second.second);
   }
   for (auto e : c->timing.pool) cudaEventDestroy(e);
-  cudaFree(c->d_primes);
-  cudaFree(c->d_tw2);
-  cudaFree(c->d_tables);
-  cudaFree(c->d_md_scale);
+  if (!c->parent) {  // clones share the parent's tables
+    cudaFree(c->d_primes);
+    cudaFree(c->d_tw2);
+    cudaFree(c->d_tables);
+    cudaFree(c->d_md_scale);
+  }
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
+}
+
+// A context with the same parameters and device tables as `c` and its own stream, so
+// that work for one parameter set can run on several streams at once.  Keys and models
+// made with `c` may be used with the clone.  Destroy clones before `c`.
+extern "C" int ctl_context_clone(const ctl_context* c, ctl_context** out) {
+  if (!c || !out) {
+    set_error("ctl_context_clone: null argument");
+    return CTL_EINVAL;
+  }
+  *out = nullptr;
+  std::unique_ptr<ctl_context> k(new ctl_context());
+  k->N = c->N;
+  k->logN = c->logN;
+  k->L = c->L;
+  k->K = c->K;
+  k->alpha = c->alpha;
+  k->beta = c->beta;
+  k->scale = c->scale;
+  k->seed = c->seed;
+  k->moduli = c->moduli;
+  k->device = c->device;
+  k->sm_count = c->sm_count;
+  k->alloc_fn = c->alloc_fn;
+  k->free_fn = c->free_fn;
+  k->alloc_user = c->alloc_user;
+  k->d_primes = c->d_primes;
+  k->d_tw2 = c->d_tw2;
+  k->d_itw2 = c->d_itw2;
+  k->d_tables = c->d_tables;
+  k->modup_tabs = c->modup_tabs;
+  k->rescale_tabs = c->rescale_tabs;
+  k->moddown = c->moddown;
+  k->d_md_scale = c->d_md_scale;
+  k->d_mu_scale = c->d_mu_scale;
+  k->h_primes = c->h_primes;
+  k->enc = c->enc;
+  k->parent = c->parent ? c->parent : c;
+  if (int rc = cuda_check(cudaStreamCreateWithFlags(&k->stream, cudaStreamNonBlocking), "stream")) return rc;
+  k->own_stream = true;
+  *out = k.release();
+  return CTL_OK;
 }
 
 extern "C" int ctl_context_info(const ctl_context* c, uint64_t* moduli, uint32_t* n_q, uint32_t* n_p,
@@ -1339,6 +1385,15 @@ struct LayerPlan {
   uint32_t in_level = 0;
   double in_scale = 0, out_scale = 0;
 };
+// A captured forward: the whole layer sequence of a model for one (context, keys, batch
+// size), reading a fixed staging input and writing a fixed staging output.
+struct GraphEntry {
+  cudaGraphExec_t exec = nullptr;
+  ctl::u64* in_buf = nullptr;
+  ctl::u64* out_buf = nullptr;
+  uint64_t kernels = 0;
+  uint64_t ops[5] = {0, 0, 0, 0, 0};
+};
 struct ctl_model {
   ctl_context* ctx = nullptr;
   std::vector<LayerPlan> layers;
@@ -1346,6 +1401,8 @@ struct ctl_model {
   double in_scale = 0, out_scale = 0;
   std::vector<int32_t> rotations;
   uint64_t bytes = 0;
+  std::mutex graph_mu;
+  std::map<std::tuple<const ctl_context*, const ctl_keys*, uint32_t>, GraphEntry> graphs;
 };
 
 extern "C" int ctl_model_create(ctl_context* c, const ctl_layer* layers, uint32_t n_layers, uint32_t in_level,
@@ -1419,6 +1476,14 @@ extern "C" int ctl_model_create(ctl_context* c, const ctl_layer* layers, uint32_
 
 extern "C" void ctl_model_destroy(ctl_model* M) {
   if (!M) return;
+  for (auto& kv : M->graphs) {
+    ctl_context* gc = const_cast<ctl_context*>(std::get<0>(kv.first));
+    cudaStreamSynchronize(gc->stream);
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    dev_free(gc, kv.second.in_buf);
+    dev_free(gc, kv.second.out_buf);
+    cudaStreamSynchronize(gc->stream);
+  }
   for (auto& L : M->layers) dense_release(M->ctx, L.dense);
   cudaStreamSynchronize(M->ctx->stream);
   delete M;
@@ -1446,33 +1511,19 @@ extern "C" int ctl_model_info(const ctl_model* M, uint32_t* out_level, double* o
   return CTL_OK;
 }
 
-extern "C" int ctl_model_forward(ctl_context* c, const ctl_model* M, const ctl_keys* k, const ctl_ct* in,
-                                 ctl_ct** out) {
-  if (!c || !M || !k || !in || !out) {
-    set_error("ctl_model_forward: null argument");
-    return CTL_EINVAL;
-  }
-  *out = nullptr;
-  if (in->level != M->in_level) {
-    set_error("ctl_model_forward: input level %u, model expects %u", in->level, M->in_level);
-    return CTL_ELEVEL;
-  }
-  if (!same_scale(in->scale, M->in_scale)) {
-    set_error("ctl_model_forward: input scale mismatch");
-    return CTL_ESCALE;
-  }
-  const int nb = (int)in->count;
+// Runs the layers of M on nb ciphertexts at `in` (level M->in_level), writing the
+// output ciphertexts to `out` (level M->out_level).
+static int model_run(ctl_context* c, const ctl_model* M, const ctl_keys* k, const u64* in, int nb, u64* out) {
   const uint32_t N = c->N;
-  // ping-pong buffers sized for the input level
-  DBuf a(c, ct_words(c, in->level, in->count)), b(c, ct_words(c, in->level, in->count));
+  DBuf a(c, ct_words(c, M->in_level, nb)), b(c, ct_words(c, M->in_level, nb));
   if (!a.p || !b.p) {
     set_error("ctl_model_forward: allocation failed");
     return CTL_ENOMEM;
   }
-  const u64* cur = in->d;
+  const u64* cur = in;
   u64* bufs[2] = {a.p, b.p};
   int w = 0;
-  uint32_t lvl = in->level;
+  uint32_t lvl = M->in_level;
   for (const LayerPlan& P : M->layers) {
     u64* dst = bufs[w];
     int rc = CTL_OK;
@@ -1494,16 +1545,132 @@ extern "C" int ctl_model_forward(ctl_context* c, const ctl_model* M, const ctl_k
     cur = dst;
     w ^= 1;
   }
-  ctl_ct* o = new_ct(c, lvl, in->count, M->out_scale);
+  cudaMemcpyAsync(out, cur, ct_words(c, lvl, nb) * sizeof(u64), cudaMemcpyDeviceToDevice, c->stream);
+  return last_cuda("model forward");
+}
+
+static int forward_check(ctl_context* c, const ctl_model* M, const ctl_keys* k, const ctl_ct* in, ctl_ct** out) {
+  if (!c || !M || !k || !in || !out) {
+    set_error("ctl_model_forward: null argument");
+    return CTL_EINVAL;
+  }
+  *out = nullptr;
+  if (in->level != M->in_level) {
+    set_error("ctl_model_forward: input level %u, model expects %u", in->level, M->in_level);
+    return CTL_ELEVEL;
+  }
+  if (!same_scale(in->scale, M->in_scale)) {
+    set_error("ctl_model_forward: input scale mismatch");
+    return CTL_ESCALE;
+  }
+  if (c->N != M->ctx->N || c->moduli != M->ctx->moduli) {
+    set_error("ctl_model_forward: context parameters differ from the model's");
+    return CTL_EINVAL;
+  }
+  return CTL_OK;
+}
+
+extern "C" int ctl_model_forward(ctl_context* c, const ctl_model* M, const ctl_keys* k, const ctl_ct* in,
+                                 ctl_ct** out) {
+  if (int rc = forward_check(c, M, k, in, out)) return rc;
+  ctl_ct* o = new_ct(c, M->out_level, in->count, M->out_scale);
   if (!o) {
     set_error("ctl_model_forward: allocation failed");
     return CTL_ENOMEM;
   }
-  cudaMemcpyAsync(o->d, cur, o->bytes, cudaMemcpyDeviceToDevice, c->stream);
-  if (int rc = last_cuda("model forward")) {
+  int rc = model_run(c, M, k, in->d, (int)in->count, o->d);
+  if (rc) {
     ctl_ct_destroy(o);
     return rc;
   }
+  *out = o;
+  return CTL_OK;
+}
+
+// Same result as ctl_model_forward, replaying a CUDA graph of the whole forward that is
+// captured on the first call for this (context, keys, batch size).
+extern "C" int ctl_model_forward_graph(ctl_context* c, const ctl_model* M, const ctl_keys* k, const ctl_ct* in,
+                                       ctl_ct** out) {
+  if (int rc = forward_check(c, M, k, in, out)) return rc;
+  if (c->alloc_fn) {
+    set_error("ctl_model_forward_graph: graphs need the library's stream-ordered pool");
+    return CTL_ENOTSUP;
+  }
+  ctl_model* Mm = const_cast<ctl_model*>(M);
+  std::lock_guard<std::mutex> lk(Mm->graph_mu);
+  const uint32_t nb = in->count;
+  auto key = std::make_tuple((const ctl_context*)c, k, nb);
+  auto it = Mm->graphs.find(key);
+  if (it == Mm->graphs.end()) {
+    GraphEntry G;
+    G.in_buf = (u64*)dev_alloc(c, ct_words(c, M->in_level, nb) * sizeof(u64));
+    G.out_buf = (u64*)dev_alloc(c, ct_words(c, M->out_level, nb) * sizeof(u64));
+    if (!G.in_buf || !G.out_buf) {
+      dev_free(c, G.in_buf);
+      dev_free(c, G.out_buf);
+      set_error("ctl_model_forward_graph: allocation failed");
+      return CTL_ENOMEM;
+    }
+    cudaMemsetAsync(G.in_buf, 0, ct_words(c, M->in_level, nb) * sizeof(u64), c->stream);
+    // one eager run settles every launch configuration before capture
+    int rc = model_run(c, M, k, G.in_buf, (int)nb, G.out_buf);
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(c->stream), "graph warm-up");
+    if (rc) {
+      dev_free(c, G.in_buf);
+      dev_free(c, G.out_buf);
+      return rc;
+    }
+    const bool timing = c->timing.enabled;
+    c->timing.enabled = false;
+    const uint64_t l0 = c->launch_count.load();
+    const uint64_t o0[5] = {c->op_rot, c->op_ptmul, c->op_add, c->op_relin, c->op_rescale};
+    cudaGraph_t graph = nullptr;
+    rc = cuda_check(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    if (!rc) {
+      const int rr = model_run(c, M, k, G.in_buf, (int)nb, G.out_buf);
+      const int re = cuda_check(cudaStreamEndCapture(c->stream, &graph), "end capture");
+      rc = rr ? rr : re;
+    }
+    if (!rc) rc = cuda_check(cudaGraphInstantiate(&G.exec, graph, 0), "graph instantiate");
+    if (graph) cudaGraphDestroy(graph);
+    c->timing.enabled = timing;
+    G.kernels = c->launch_count.load() - l0;
+    const uint64_t o1[5] = {c->op_rot, c->op_ptmul, c->op_add, c->op_relin, c->op_rescale};
+    for (int i = 0; i < 5; i++) G.ops[i] = o1[i] - o0[i];
+    c->launch_count = l0;
+    c->op_rot = o0[0];
+    c->op_ptmul = o0[1];
+    c->op_add = o0[2];
+    c->op_relin = o0[3];
+    c->op_rescale = o0[4];
+    if (rc) {
+      cudaGetLastError();
+      dev_free(c, G.in_buf);
+      dev_free(c, G.out_buf);
+      return rc;
+    }
+    it = Mm->graphs.emplace(key, G).first;
+  }
+  GraphEntry& G = it->second;
+  ctl_ct* o = new_ct(c, M->out_level, nb, M->out_scale);
+  if (!o) {
+    set_error("ctl_model_forward_graph: allocation failed");
+    return CTL_ENOMEM;
+  }
+  cudaMemcpyAsync(G.in_buf, in->d, in->bytes, cudaMemcpyDeviceToDevice, c->stream);
+  int rc = cuda_check(cudaGraphLaunch(G.exec, c->stream), "graph launch");
+  cudaMemcpyAsync(o->d, G.out_buf, o->bytes, cudaMemcpyDeviceToDevice, c->stream);
+  if (!rc) rc = last_cuda("graph forward");
+  if (rc) {
+    ctl_ct_destroy(o);
+    return rc;
+  }
+  c->launch_count += G.kernels;
+  c->op_rot += G.ops[0];
+  c->op_ptmul += G.ops[1];
+  c->op_add += G.ops[2];
+  c->op_relin += G.ops[3];
+  c->op_rescale += G.ops[4];
   *out = o;
   return CTL_OK;
 }

@@ -83,7 +83,19 @@ SIGNATURES = {
     "ctl_model_destroy": (None, [_vp]),
     "ctl_model_rotations": (C.c_int, [_vp, _i32p, C.c_uint32, _u32p]),
     "ctl_model_forward": (C.c_int, [_vp, _vp, _vp, _vp, _pp]),
+    "ctl_model_forward_graph": (C.c_int, [_vp, _vp, _vp, _vp, _pp]),
     "ctl_model_info": (C.c_int, [_vp, _u32p, _dp, _u64p]),
+    "ctl_context_clone": (C.c_int, [_vp, _pp]),
+    "ctl_server_create": (C.c_int, [_pp, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32]),
+    "ctl_server_add_lane": (C.c_int, [_vp, _vp, _vp, _u32p]),
+    "ctl_server_add_client": (C.c_int, [_vp, C.c_uint32, _vp, _u32p]),
+    "ctl_server_io_words": (C.c_int, [_vp, C.c_uint32, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
+    "ctl_server_start": (C.c_int, [_vp]),
+    "ctl_server_submit": (C.c_int, [_vp, C.c_uint32, _u64p, _u64p]),
+    "ctl_server_poll": (C.c_int, [_vp, C.c_uint64, _u64p, _sz, _dp]),
+    "ctl_server_wait": (C.c_int, [_vp, C.c_uint64, C.c_uint32, _u64p, _sz, _dp]),
+    "ctl_server_stats": (C.c_int, [_vp, _u64p, _dp, _dp]),
+    "ctl_server_destroy": (None, [_vp]),
     "ctl_stats_reset": (C.c_int, [_vp]),
     "ctl_stats_enable_timing": (C.c_int, [_vp, C.c_int]),
     "ctl_stats_launches": (C.c_uint64, [_vp]),
@@ -390,12 +402,84 @@ class Model:
         _check(lib().ctl_model_info(self.h, C.byref(lvl), C.byref(sc), C.byref(by)))
         return lvl.value, sc.value, by.value
 
-    def forward(self, keys, ct):
+    def forward(self, keys, ct, graph=False, ctx=None):
+        ctx = self.ctx if ctx is None else ctx
         h = C.c_void_p()
-        _check(lib().ctl_model_forward(self.ctx.h, self.h, keys.h, ct.h, C.byref(h)))
-        return Ciphertext(self.ctx, h)
+        fn = lib().ctl_model_forward_graph if graph else lib().ctl_model_forward
+        _check(fn(ctx.h, self.h, keys.h, ct.h, C.byref(h)))
+        return Ciphertext(ctx, h)
 
     def close(self):
         if getattr(self, "h", None) and getattr(self.ctx, "h", None):
             lib().ctl_model_destroy(self.h)
         self.h = None
+
+
+class Server:
+    """Continuous-batching request loop (ctl_server_*): lanes = (context, model), clients = keys."""
+
+    def __init__(self, mem_budget_bytes, n_workers=4, max_batch=64, max_queue=4096):
+        h = C.c_void_p()
+        _check(lib().ctl_server_create(C.byref(h), int(mem_budget_bytes), n_workers, max_batch, max_queue))
+        self.h = h
+        self._keep = []
+
+    def add_lane(self, ctx, model):
+        lane = C.c_uint32()
+        _check(lib().ctl_server_add_lane(self.h, ctx.h, model.h, C.byref(lane)))
+        self._keep += [ctx, model]
+        return lane.value
+
+    def add_client(self, lane, keys):
+        cl = C.c_uint32()
+        _check(lib().ctl_server_add_client(self.h, lane, keys.h, C.byref(cl)))
+        self._keep.append(keys)
+        return cl.value
+
+    def io_words(self, client):
+        i, o = C.c_size_t(), C.c_size_t()
+        _check(lib().ctl_server_io_words(self.h, client, C.byref(i), C.byref(o)))
+        return i.value, o.value
+
+    def start(self):
+        _check(lib().ctl_server_start(self.h))
+
+    def submit(self, client, coeffs):
+        """Returns a request id, or None if the queue is full (CTL_EBUSY)."""
+        a = np.ascontiguousarray(coeffs, dtype=np.uint64)
+        rid = C.c_uint64()
+        rc = lib().ctl_server_submit(self.h, client, _p(a, _u64p), C.byref(rid))
+        if rc == -8:
+            return None
+        _check(rc)
+        return rid.value
+
+    def wait(self, rid, out_words, timeout_ms=600000):
+        out = np.zeros(out_words, dtype=np.uint64)
+        lat = C.c_double()
+        _check(lib().ctl_server_wait(self.h, rid, timeout_ms, _p(out, _u64p), out.size, C.byref(lat)))
+        return out, lat.value
+
+    def poll(self, rid, out_words):
+        """(result, latency_ms) when done, None while pending; raises on failure."""
+        out = np.zeros(out_words, dtype=np.uint64)
+        lat = C.c_double()
+        rc = lib().ctl_server_poll(self.h, rid, _p(out, _u64p), out.size, C.byref(lat))
+        if rc == -8:
+            return None
+        _check(rc)
+        return out, lat.value
+
+    def stats(self):
+        c6 = np.zeros(6, dtype=np.uint64)
+        p50, p99 = C.c_double(), C.c_double()
+        _check(lib().ctl_server_stats(self.h, _p(c6, _u64p), C.byref(p50), C.byref(p99)))
+        names = ["submitted", "completed", "rejected", "failed", "batches", "batched_cts"]
+        d = dict(zip(names, [int(x) for x in c6]))
+        d.update(p50_ms=p50.value, p99_ms=p99.value)
+        return d
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ctl_server_destroy(self.h)
+            self.h = None
