@@ -219,17 +219,191 @@ def run_reference(args, wl, rank, world):
     print(json.dumps(line), flush=True)
 
 
+SHAPES = {  # the three query shapes of the serving mix (configurations 1-3)
+    "cfg1": dict(N=4096, q=[50, 40, 40], p=[60], dnum=3, dims=[64, 32], square_last=True),
+    "cfg2": dict(N=8192, q=[60, 40, 40, 40], p=[60], dnum=4, dims=[512, 128, 64], square_last=False),
+    "cfg3": dict(N=16384, q=[45] * 8, p=[60, 60], dnum=4, dims=[1024, 256, 256, 64], square_last=False),
+}
+
+
+def _slots(N, n_in, t0, x):
+    s = np.zeros(N // 2)
+    s[:n_in] = x
+    s[t0:t0 + n_in] = x
+    return s
+
+
+def run_serving(args, ctl):
+    """Configuration 5: Poisson arrivals from 64 clients, each with its own keys resident
+    in HBM and a query shape drawn uniformly from configurations 1-3; continuous batching
+    with memory admission; p50/p99 latency (submit to result on the host) and throughput
+    per arrival rate."""
+    rng = np.random.default_rng(5)
+    lanes = {}
+    srv = ctl.Server(mem_budget_bytes=int(args.mem_budget_gb * 2 ** 30), n_workers=args.workers,
+                     max_batch=args.max_batch, max_queue=100000)
+    for name, sh in SHAPES.items():
+        layers, Ws = layers_for(sh["dims"], sh["square_last"])
+        ctx = ctl.Context(sh["N"], sh["q"], sh["p"], dnum=sh["dnum"], scale=2.0 ** 40)
+        model = ctl.Model(ctx, layers)
+        lanes[name] = (ctx, model, srv.add_lane(ctx, model), bsgs_t(Ws[0].shape[0], Ws[0].shape[1]))
+    clients = []
+    for c in range(args.clients):
+        name = list(SHAPES)[rng.integers(3)]
+        ctx, model, lane, t0 = lanes[name]
+        keys = ctx.keygen(model.rotations(), seed=1000 + c)
+        cid = srv.add_client(lane, keys)
+        pool = []
+        for i in range(4):  # a few distinct ciphertexts per client, resubmitted
+            x = rng.uniform(-1, 1, SHAPES[name]["dims"][0])
+            pool.append(ctx.encrypt(keys, _slots(ctx.N, len(x), t0, x), 4 + 100 * c + i).export()[0])
+        clients.append((cid, name, pool, srv.io_words(cid)[1]))
+    srv.start()
+    points = []
+    for lam in args.rates:
+        before = srv.stats()
+        t_end = time.perf_counter() + args.seconds
+        t_next = time.perf_counter()
+        ids = []
+        while True:
+            t_next += rng.exponential(1.0 / lam)
+            if t_next > t_end:
+                break
+            d = t_next - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            cid, name, pool, ow = clients[rng.integers(len(clients))]
+            rid = srv.submit(cid, pool[rng.integers(len(pool))])
+            if rid is not None:
+                ids.append((rid, ow))
+        t0 = time.perf_counter()
+        lats = []
+        for rid, ow in ids:
+            _, lat = srv.wait(rid, ow, timeout_ms=600000)
+            lats.append(lat)
+        wall = (t_end - (t_end - args.seconds)) + (time.perf_counter() - t0)
+        after = srv.stats()
+        lats.sort()
+        points.append({"rate_req_s": lam, "completed": len(lats),
+                       "throughput_fwd_s": len(lats) / wall if wall > 0 else 0.0,
+                       "p50_ms": float(np.percentile(lats, 50)) if lats else None,
+                       "p99_ms": float(np.percentile(lats, 99)) if lats else None,
+                       "rejected": after["rejected"] - before["rejected"],
+                       "batches": after["batches"] - before["batches"]})
+    srv.close()
+    return points
+
+
+def run_uneven(args, ctl):
+    """Configuration 4: 1024 queries with N in {8192, 16384}, depth 2..6 and input
+    dimension in {128, 256, 512, 1024}, uniformly.  Chain q0 = 60 bits plus d primes of
+    40 bits; one 60-bit special prime at N = 8192, two (alpha = 2) at N = 16384.  Network:
+    alternating dense (in -> 128, 128 -> 128, the last -> 64) and x^2, d levels in all.
+    Grouped execution (queries of one shape batched, groups overlapped by the server's
+    workers) against one launch sequence per ciphertext."""
+    rng = np.random.default_rng(4)
+    shapes = {}
+    for Nn in (8192, 16384):
+        for d in range(2, 7):
+            q = [60] + [40] * d
+            p = [60] if Nn == 8192 else [60, 60]
+            dnum = len(q) if Nn == 8192 else (len(q) + 1) // 2
+            ctx = ctl.Context(Nn, q, p, dnum=dnum, scale=2.0 ** 40)
+            shapes[(Nn, d)] = {"ctx": ctx, "models": {}}
+    queries = [((int(rng.choice([8192, 16384])), int(rng.integers(2, 7))), int(rng.choice([128, 256, 512, 1024])))
+               for _ in range(args.queries)]
+    srv = ctl.Server(mem_budget_bytes=int(args.mem_budget_gb * 2 ** 30), n_workers=args.workers,
+                     max_batch=args.max_batch, max_queue=100000)
+    clients = {}
+    for (key, dim) in sorted(set(queries)):
+        Nn, d = key
+        sh = shapes[key]
+        ctx = sh["ctx"]
+        w = np.random.default_rng(dim + d)
+        layers, dims_now, ops = [], dim, 0
+        while ops < d:
+            out = 64 if ops + 2 >= d else 128
+            if ops > 0:
+                layers.append(("replicate", bsgs_t(out, dims_now)))
+            layers.append(("dense", w.normal(0, 1 / np.sqrt(dims_now), (out, dims_now))))
+            dims_now, ops = out, ops + 1
+            if ops < d:
+                layers.append(("square",))
+                ops += 1
+        model = ctl.Model(ctx, layers)
+        sh["models"][dim] = model
+        sh["rots"] = sh.get("rots", set()) | set(model.rotations())  # one key set per context
+    for key, sh in shapes.items():
+        sh["keys"] = sh["ctx"].keygen(sorted(sh.get("rots", set())), seed=77)
+    cts = []
+    for i, (key, dim) in enumerate(queries):
+        sh = shapes[key]
+        ctx = sh["ctx"]
+        t0 = bsgs_t(128 if key[1] > 2 else 64, dim)
+        x = rng.uniform(-1, 1, dim)
+        cts.append(ctx.encrypt(sh["keys"], _slots(ctx.N, dim, t0, x), 9000 + i))
+    lanes = {}
+    for key, sh in shapes.items():
+        for dim, model in sh["models"].items():
+            lane = srv.add_lane(sh["ctx"], model)
+            lanes[(key, dim)] = srv.add_client(lane, sh["keys"])
+    srv.start()
+    coeffs = [ct.export()[0] for ct in cts]
+    # grouped: submit everything, the server batches per shape and overlaps groups
+    t0 = time.perf_counter()
+    ids = [(srv.submit(lanes[q], coeffs[i]), srv.io_words(lanes[q])[1]) for i, q in enumerate(queries)]
+    for rid, ow in ids:
+        srv.wait(rid, ow, timeout_ms=600000)
+    grouped = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    # one forward per ciphertext, in submission order
+    import torch
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i, (key, dim) in enumerate(queries):
+        sh = shapes[key]
+        o = sh["models"][dim].forward(sh["keys"], cts[i])
+        o.close()
+    for sh in shapes.values():
+        sh["ctx"].synchronize()
+    single = time.perf_counter() - t0
+    return {"queries": len(queries), "shapes": len(set(queries)), "grouped_fwd_s": len(queries) / grouped,
+            "per_ct_fwd_s": len(queries) / single, "speedup": single / grouped, "server_batches": st["batches"]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="batched", choices=list(WORKLOADS))
+    ap.add_argument("--workload", default="batched", choices=list(WORKLOADS) + ["serving", "uneven"])
     ap.add_argument("--batch", type=int, default=0, help="override the batch size")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--graph", type=int, default=-1, help="1: replay a CUDA graph of the forward (default: single-query workloads)")
+    ap.add_argument("--rates", type=float, nargs="+", default=[50, 100, 200, 500, 1000, 2000])
+    ap.add_argument("--seconds", type=float, default=5.0, help="serving: load duration per arrival rate")
+    ap.add_argument("--clients", type=int, default=64)
+    ap.add_argument("--workers", type=int, default=4)
+    ap.add_argument("--max-batch", type=int, default=64)
+    ap.add_argument("--mem-budget-gb", type=float, default=160.0)
+    ap.add_argument("--queries", type=int, default=1024)
     args = ap.parse_args()
+    if args.workload in ("serving", "uneven"):
+        import torch
+
+        import __graft_entry__
+
+        __graft_entry__.build()
+        from paper_2205_11935_gb300 import ctl
+
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        res = run_serving(args, ctl) if args.workload == "serving" else run_uneven(args, ctl)
+        print(json.dumps({"workload": args.workload, "result": res}), flush=True)
+        return
     wl = dict(WORKLOADS[args.workload])
     if args.batch:
         wl["batch"] = args.batch
@@ -280,8 +454,10 @@ def main():
         max_err = max(max_err, float(np.max(np.abs(yi - fp64_forward(Ws, xs[i], square_last)))))
     out.close()
 
+    use_graph = (args.graph == 1) or (args.graph == -1 and B == 1)
+
     def step():
-        o = model.forward(keys, batch)
+        o = model.forward(keys, batch, graph=use_graph)
         o.close()
 
     for _ in range(args.warmup):
@@ -310,6 +486,16 @@ def main():
     launches = ctx.stats_launches()
     kern = ctx.stats_kernels()
     ops = ctx.stats_ops()
+    timing_source = "CUDA events around every launch of the timed steps"
+    if use_graph:
+        # a replayed graph records no per-launch events: take the per-class times from
+        # the same number of eager forwards (the same kernels) right after the timed region
+        ctx.stats_reset()
+        for _ in range(args.steps):
+            o = model.forward(keys, batch)
+            o.close()
+        kern = ctx.stats_kernels()
+        timing_source = "CUDA events around every launch of eager forwards run after the graph-timed steps"
     ctx.stats_enable_timing(False)
     if dist:
         t = torch.tensor([total_ms], device="cuda")
@@ -332,7 +518,7 @@ def main():
             ctl._check(ctl.lib().ctl_ct_import(ctx.h, C.cast(pinned_in.data_ptr(), ctl._u64p), B, len(wl["q"]),
                                                2.0 ** 40, C.byref(h)))
             ci = ctl.Ciphertext(ctx, h)
-            co = model.forward(keys, ci)
+            co = model.forward(keys, ci, graph=use_graph)
             ctl._check(ctl.lib().ctl_ct_export(co.h, C.cast(pinned_out.data_ptr(), ctl._u64p), out_words))
             ci.close()
             co.close()
@@ -369,7 +555,8 @@ def main():
                 "unit": "Gmodmul/s", "frac": achieved / peak_modmul, "traffic": None,
                 "peak_basis": f"{SM_COUNT} SMs x {IMAD_PER_CLK_SM} IMAD/clk x {MAX_SM_MHZ:.0f} MHz / "
                               f"{SHOUP_IMAD} IMAD per Shoup modmul (measured)",
-                "avg_launch_ms": d["ms"] / max(d["launches"], 1), "classes": per_class}
+                "avg_launch_ms": d["ms"] / max(d["launches"], 1), "classes": per_class,
+                "timing": timing_source}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -383,6 +570,7 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
                 "data": "synthetic",
                 "config": {"workload": wl["desc"], "batch_per_gpu": B, "N": N, "parallelism": f"replicas x{world}",
+                           "cuda_graph": bool(use_graph),
                            "l2": "inputs larger than L2 (working set of tens of GB per step)",
                            "max_abs_err_vs_fp64": max_err},
                 "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
