@@ -670,18 +670,17 @@ int orc_moddown(const orc_ctx* c, const u64* ext, uint32_t lvl, u64* out) {
   return 0;
 }
 
-// Hybrid key switching of a coefficient-form polynomial x at level lvl with key key_id:
-// for every live digit d, ext_d = ModUp_d(x); if g != 1 each ext_d is first mapped by
-// sigma_g; then acc_t = sum_d ext_d * evk_d[t] over the live data primes and the special
-// primes, and the result is (ModDown(acc_0), ModDown(acc_1)).  Key limbs of primes that
-// are no longer live are not used.
-int orc_keyswitch(const orc_ctx* c, const orc_keys* k, u64 key_id, const u64* x, uint32_t lvl, u64 g, u64* out) {
+// The key product of hybrid key switching, kept in the extended basis (before ModDown):
+// acc[t] = sum_d sigma_g(ModUp_d(x)) * evk_d[t], [2][lvl+K][N].
+static int ks_ext(const orc_ctx* c, const orc_keys* k, u64 key_id, const u64* x, uint32_t lvl, u64 g,
+                  std::vector<u64>& acc0, std::vector<u64>& acc1) {
   auto it = k->evk.find(key_id);
   if (it == k->evk.end()) return -2;
   uint32_t N = c->N, K = c->K, L = c->L, LK = L + K, E = lvl + K;
   uint32_t nd = (lvl + c->alpha - 1) / c->alpha;
   std::vector<u64> ext((size_t)E * N), tmp(N), prod(N);
-  std::vector<u64> acc0((size_t)E * N, 0), acc1((size_t)E * N, 0);
+  acc0.assign((size_t)E * N, 0);
+  acc1.assign((size_t)E * N, 0);
   for (uint32_t d = 0; d < nd; d++) {
     orc_modup(c, x, lvl, d, ext.data(), nullptr);
     for (uint32_t i = 0; i < E; i++) {
@@ -697,8 +696,20 @@ int orc_keyswitch(const orc_ctx* c, const orc_keys* k, u64 key_id, const u64* x,
       for (uint32_t j = 0; j < N; j++) acc1[(size_t)i * N + j] = addmod(acc1[(size_t)i * N + j], prod[j], q);
     }
   }
+  return 0;
+}
+
+// Hybrid key switching of a coefficient-form polynomial x at level lvl with key key_id:
+// for every live digit d, ext_d = ModUp_d(x); if g != 1 each ext_d is first mapped by
+// sigma_g; then acc_t = sum_d ext_d * evk_d[t] over the live data primes and the special
+// primes, and the result is (ModDown(acc_0), ModDown(acc_1)).  Key limbs of primes that
+// are no longer live are not used.
+int orc_keyswitch(const orc_ctx* c, const orc_keys* k, u64 key_id, const u64* x, uint32_t lvl, u64 g, u64* out) {
+  std::vector<u64> acc0, acc1;
+  int rc = ks_ext(c, k, key_id, x, lvl, g, acc0, acc1);
+  if (rc) return rc;
   orc_moddown(c, acc0.data(), lvl, out);
-  orc_moddown(c, acc1.data(), lvl, out + (size_t)lvl * N);
+  orc_moddown(c, acc1.data(), lvl, out + (size_t)lvl * c->N);
   return 0;
 }
 
@@ -783,12 +794,14 @@ int orc_encode_diagonals(const orc_ctx* c, const double* W, uint32_t m, uint32_t
   return 0;
 }
 
-// Dense layer by Eq. (bsgs) on an input laid out as [x, x] over 2t slots:
+// Dense layer by Eq. (bsgs) on an input laid out as [x, x] over 2t slots, as a plain
+// composition of whole rotations:
 //   out = sum_k rot_{k t1}( sum_j diag'_{k t1 + j} o rot_j(ct) ),
 // inner sums in increasing j, outer in increasing k, then an optional plaintext bias
 // (added to c0) and a rescale.  counters[0..2] receive the rotations, plaintext
-// products and additions performed (t1+t2-2, t, t-1).
-int orc_dense(const orc_ctx* c, const orc_keys* k, const u64* ct, uint32_t lvl, const i64* pts, uint32_t t,
+// products and additions performed (t1+t2-2, t, t-1).  Decodes to the same values as
+// orc_dense within the noise; kept as the textbook form that orc_dense is pinned to.
+int orc_dense_composed(const orc_ctx* c, const orc_keys* k, const u64* ct, uint32_t lvl, const i64* pts, uint32_t t,
               const i64* bias, u64* out, u64* counters) {
   uint32_t N = c->N, t1 = orc_bsgs_t1(t), t2 = t / t1;
   size_t csz = (size_t)2 * lvl * N;
@@ -808,6 +821,92 @@ int orc_dense(const orc_ctx* c, const orc_keys* k, const u64* ct, uint32_t lvl, 
     if (kk) { int rc = orc_rotate(c, k, inner.data(), lvl, (int64_t)kk * t1, rot.data()); if (rc) return rc; nrot++; inner = rot; }
     if (kk == 0) acc = inner; else { orc_add(c, acc.data(), inner.data(), lvl, acc.data()); nadd++; }
   }
+  if (bias) orc_add_plain(c, acc.data(), lvl, bias, acc.data());
+  if (counters) { counters[0] = nrot; counters[1] = nmul; counters[2] = nadd; }
+  return orc_rescale(c, acc.data(), lvl, out);
+}
+
+// Dense layer by Eq. (bsgs) with every ModDown of the baby and giant steps postponed
+// (the rotations are key switches in the extended basis Q*P; the paper fixes the
+// linear algebra and the hoisting of the baby steps, not where the division by P
+// happens).  With E = lvl + K limbs (data primes, then special primes) and P the
+// special modulus:
+//   B_0 = (P*c0, P*c1) (zero on the special limbs),
+//   B_j = (P*sigma_j(c0) + a_0, a_1), (a_0, a_1) = key product of c1 for rot_j, j >= 1,
+//   I_k = sum_j diag'_{k t1 + j} o B_j over all E limbs (diagonals reduced mod every prime),
+//   S   = I_0 + sum_{k >= 1} ( sigma_{k t1}(I_k.0) + b_0, b_1 ),
+//         (b_0, b_1) = key product of ModDown(I_k.1) for rot_{k t1},
+//   out = rescale( (ModDown(S.0), ModDown(S.1)) [+ bias on c0] ).
+// The sums run in increasing j and k.  counters as for orc_dense_composed.
+int orc_dense(const orc_ctx* c, const orc_keys* k, const u64* ct, uint32_t lvl, const i64* pts, uint32_t t,
+              const i64* bias, u64* out, u64* counters) {
+  uint32_t N = c->N, K = c->K, L = c->L, E = lvl + K, t1 = orc_bsgs_t1(t), t2 = t / t1;
+  auto prime = [&](uint32_t i) { return c->mods[i < lvl ? i : L + (i - lvl)]; };
+  const size_t ew = (size_t)E * N;  // one polynomial in the extended basis
+  std::vector<u64> B((size_t)t1 * 2 * ew, 0), S(2 * ew), Ik(2 * ew), pr(N), prod(N), tmp(N), c1d((size_t)lvl * N);
+  std::vector<u64> a0, a1;
+  u64 nrot = 0, nmul = 0, nadd = 0;
+  std::vector<u64> Pq(lvl);
+  for (uint32_t i = 0; i < lvl; i++) Pq[i] = big_mod_u64(c->P, c->mods[i]);
+  // baby steps in the extended basis
+  for (uint32_t j = 0; j < t1; j++) {
+    u64* Bj = &B[(size_t)j * 2 * ew];
+    u64 g = gal_elt(c, j);
+    if (g != 1) {
+      int rc = ks_ext(c, k, g, ct + (size_t)lvl * N, lvl, g, a0, a1);
+      if (rc) return rc;
+      std::copy(a0.begin(), a0.end(), Bj);
+      std::copy(a1.begin(), a1.end(), Bj + ew);
+      nrot++;
+    }
+    for (uint32_t i = 0; i < lvl; i++) {
+      u64 q = c->mods[i];
+      for (uint32_t p = 0; p < 2; p++) {
+        const u64* src = ct + ((size_t)p * lvl + i) * N;
+        if (g != 1 && p == 0) { automorphism(src, tmp.data(), N, g, q); src = tmp.data(); }
+        if (g != 1 && p == 1) continue;  // the key product carries the whole c1 part
+        u64* d = Bj + (size_t)p * ew + (size_t)i * N;
+        for (uint32_t x = 0; x < N; x++) d[x] = addmod(d[x], mulmod(src[x], Pq[i], q), q);
+      }
+    }
+  }
+  // inner sums and giant steps
+  for (uint32_t kk = 0; kk < t2; kk++) {
+    std::fill(Ik.begin(), Ik.end(), 0);
+    for (uint32_t j = 0; j < t1; j++) {
+      const i64* pt = pts + (size_t)(kk * t1 + j) * N;
+      for (uint32_t i = 0; i < E; i++) {
+        u64 q = prime(i);
+        for (uint32_t x = 0; x < N; x++) pr[x] = from_signed(pt[x], q);
+        for (uint32_t p = 0; p < 2; p++) {
+          negacyclic_mul(&B[(size_t)j * 2 * ew + (size_t)p * ew + (size_t)i * N], pr.data(), prod.data(), N, q);
+          u64* d = &Ik[(size_t)p * ew + (size_t)i * N];
+          for (uint32_t x = 0; x < N; x++) d[x] = addmod(d[x], prod[x], q);
+        }
+      }
+      nmul++;
+      if (j) nadd++;
+    }
+    if (kk == 0) { S = Ik; continue; }
+    u64 g = gal_elt(c, (int64_t)kk * t1);
+    orc_moddown(c, &Ik[ew], lvl, c1d.data());
+    int rc = ks_ext(c, k, g, c1d.data(), lvl, g, a0, a1);
+    if (rc) return rc;
+    nrot++;
+    nadd++;
+    for (uint32_t i = 0; i < E; i++) {
+      u64 q = prime(i);
+      automorphism(&Ik[(size_t)i * N], tmp.data(), N, g, q);
+      for (uint32_t x = 0; x < N; x++) {
+        size_t o = (size_t)i * N + x;
+        S[o] = addmod(S[o], addmod(tmp[x], a0[o], q), q);
+        S[ew + o] = addmod(S[ew + o], a1[o], q);
+      }
+    }
+  }
+  std::vector<u64> acc((size_t)2 * lvl * N);
+  orc_moddown(c, S.data(), lvl, acc.data());
+  orc_moddown(c, S.data() + ew, lvl, acc.data() + (size_t)lvl * N);
   if (bias) orc_add_plain(c, acc.data(), lvl, bias, acc.data());
   if (counters) { counters[0] = nrot; counters[1] = nmul; counters[2] = nadd; }
   return orc_rescale(c, acc.data(), lvl, out);

@@ -63,6 +63,7 @@ def _lib():
             "orc_bsgs_t1": (C.c_uint32, [C.c_uint32]),
             "orc_encode_diagonals": (C.c_int, [vp, _dp, C.c_uint32, C.c_uint32, C.c_double, _i64p]),
             "orc_dense": (C.c_int, [vp, vp, _u64p, C.c_uint32, _i64p, C.c_uint32, _i64p, _u64p, _u64p]),
+            "orc_dense_composed": (C.c_int, [vp, vp, _u64p, C.c_uint32, _i64p, C.c_uint32, _i64p, _u64p, _u64p]),
             "orc_replicate": (C.c_int, [vp, vp, _u64p, C.c_uint32, C.c_uint32, _u64p]),
         }
         for name, (res, args) in sig.items():
@@ -287,13 +288,16 @@ class Oracle:
         _chk(self.lib.orc_encode_diagonals(self.h, _p(W, _dp), m, n, scale, _p(out, _i64p)), "encode_diagonals")
         return out
 
-    def dense(self, ct, pts, bias=None):
+    def dense(self, ct, pts, bias=None, composed=False):
+        """Dense layer by Eq. (bsgs); composed=True takes the plain composition of whole
+        rotations instead of the lazy-ModDown form (same decoded values within noise)."""
         ct = _u64(ct); pts = _i64(pts); lvl = ct.shape[1]
         out = np.zeros((2, lvl - 1, self.N), dtype=np.uint64)
         cnt = np.zeros(3, dtype=np.uint64)
         bp = _p(_i64(bias), _i64p) if bias is not None else None
-        _chk(self.lib.orc_dense(self.h, self.keys, _p(ct, _u64p), lvl, _p(pts, _i64p), pts.shape[0], bp,
-                                _p(out, _u64p), _p(cnt, _u64p)), "dense")
+        fn = self.lib.orc_dense_composed if composed else self.lib.orc_dense
+        _chk(fn(self.h, self.keys, _p(ct, _u64p), lvl, _p(pts, _i64p), pts.shape[0], bp,
+                _p(out, _u64p), _p(cnt, _u64p)), "dense")
         return out, [int(x) for x in cnt]
 
     def replicate(self, ct, t):

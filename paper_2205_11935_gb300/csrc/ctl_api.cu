@@ -246,6 +246,14 @@ static int build_tables(ctl_context* c) {
   }
   const size_t pinvsh_off = tab.size();
   for (uint32_t i = 0; i < L; i++) tab.push_back(h_shoup(tab[pinv_off + i], m[i]));
+  const size_t pmod_off = tab.size();
+  for (uint32_t i = 0; i < L; i++) {
+    u64 P = 1;
+    for (uint32_t j = 0; j < K; j++) P = h_mulmod(P, m[L + j] % m[i], m[i]);
+    tab.push_back(P);
+  }
+  const size_t pmodsh_off = tab.size();
+  for (uint32_t i = 0; i < L; i++) tab.push_back(h_shoup(tab[pmod_off + i], m[i]));
   std::vector<size_t> rs_off(L + 1, 0);
   for (uint32_t lvl = 2; lvl <= L; lvl++) {
     const u64 ql = m[lvl - 1];
@@ -280,6 +288,8 @@ static int build_tables(ctl_context* c) {
   c->moddown.conv = mk(md);
   c->moddown.pinv = c->d_tables + pinv_off;
   c->moddown.pinv_sh = c->d_tables + pinvsh_off;
+  c->moddown.pmod = c->d_tables + pmod_off;
+  c->moddown.pmod_sh = c->d_tables + pmodsh_off;
   c->rescale_tabs.assign(L + 1, RescaleTab{});
   for (uint32_t lvl = 2; lvl <= L; lvl++) {
     RescaleTab& R = c->rescale_tabs[lvl];
@@ -1090,7 +1100,7 @@ extern "C" int ctl_add(ctl_context* c, const ctl_ct* a, const ctl_ct* b, ctl_ct*
 struct DenseLayer {
   uint32_t m = 0, n = 0, t = 0, t1 = 0, t2 = 0, lvl = 0;
   double pt_scale = 0, in_scale = 0, out_scale = 0;
-  u64* diag = nullptr;   // [t][lvl][N] NTT + Montgomery form
+  u64* diag = nullptr;   // [t][lvl+K][N] NTT + Montgomery form (split), extended basis
   u64* bias = nullptr;   // [lvl][N] NTT form (plain residues) or null
 };
 
@@ -1107,20 +1117,22 @@ uint32_t bsgs_t1(uint32_t t) {
   return 1u << ((lg + 1) / 2);
 }
 
-// Upload integer coefficient plaintexts [cnt][N] as NTT-form residues at level lvl.
-int upload_plaintexts(ctl_context* c, const i64* coeffs, uint32_t cnt, uint32_t lvl, bool mont, u64** out) {
+// Upload integer coefficient plaintexts [cnt][N] as NTT-form residues over `limbs`
+// limbs of level lvl (limbs = lvl + K: the extended basis, special primes last).
+int upload_plaintexts(ctl_context* c, const i64* coeffs, uint32_t cnt, uint32_t lvl, uint32_t limbs, bool mont,
+                      u64** out) {
   const uint32_t N = c->N;
   DBuf raw(c, (size_t)cnt * N);
-  u64* d = (u64*)dev_alloc(c, (size_t)cnt * lvl * N * sizeof(u64));
+  u64* d = (u64*)dev_alloc(c, (size_t)cnt * limbs * N * sizeof(u64));
   if (!raw.p || !d) {
     if (d) dev_free(c, d);
     set_error("plaintext upload: allocation failed");
     return CTL_ENOMEM;
   }
   cudaMemcpyAsync(raw.p, coeffs, (size_t)cnt * N * sizeof(u64), cudaMemcpyHostToDevice, c->stream);
-  launch_from_signed(c, (const i64*)raw.p, d, (int)cnt, (int)lvl, (int)lvl, N, (size_t)lvl * N);
-  launch_ntt_fwd(c, d, (size_t)lvl * N, (int)cnt, 0, (int)lvl, (int)lvl);
-  if (mont) launch_to_mont(c, d, (int)cnt, (int)lvl, (int)lvl, (size_t)lvl * N, true);
+  launch_from_signed(c, (const i64*)raw.p, d, (int)cnt, (int)limbs, (int)lvl, N, (size_t)limbs * N);
+  launch_ntt_fwd(c, d, (size_t)limbs * N, (int)cnt, 0, (int)limbs, (int)lvl);
+  if (mont) launch_to_mont(c, d, (int)cnt, (int)limbs, (int)lvl, (size_t)limbs * N, true);
   int rc = cuda_check(cudaStreamSynchronize(c->stream), "plaintext upload");
   if (rc) {
     dev_free(c, d);
@@ -1178,8 +1190,9 @@ int dense_prepare(ctl_context* c, DenseLayer& D, const double* W, const double* 
     if (int rc = encode_diagonals(c, W, m, n, D.pt_scale, enc)) return rc;
     src = enc.data();
   }
-  if (int rc = upload_plaintexts(c, src, D.t, lvl, true, &D.diag)) return rc;
-  launch_split_limbs(c, D.diag, (int)D.t, (int)lvl);
+  const uint32_t E = lvl + c->K;
+  if (int rc = upload_plaintexts(c, src, D.t, lvl, E, true, &D.diag)) return rc;
+  launch_split_limbs(c, D.diag, (int)D.t, (int)E, (int)lvl);
   std::vector<i64> benc;
   const i64* bsrc = (const i64*)bias_in;
   if (!bsrc && bias) {
@@ -1193,7 +1206,7 @@ int dense_prepare(ctl_context* c, DenseLayer& D, const double* W, const double* 
     bsrc = benc.data();
   }
   if (bsrc) {
-    if (int rc = upload_plaintexts(c, bsrc, 1, lvl, false, &D.bias)) return rc;
+    if (int rc = upload_plaintexts(c, bsrc, 1, lvl, lvl, false, &D.bias)) return rc;
   }
   return CTL_OK;
 }
@@ -1204,56 +1217,99 @@ void dense_release(ctl_context* c, DenseLayer& D) {
   D.diag = D.bias = nullptr;
 }
 
-// out = rescale( sum_k rot_{k t1}( sum_j diag'_{k t1 + j} o rot_j(in) ) [+ bias] ), batch nb.
+// Galois keys of the rotations r0, r0 + step, ... (n of them) as a RotList.
+int rot_list(ctl_context* c, const ctl_keys* k, int64_t r0, int64_t step, int n, RotList& rl) {
+  if (n > CTL_MAX_ROT) {
+    set_error("at most %d rotations per launch", CTL_MAX_ROT);
+    return CTL_EINVAL;
+  }
+  rl.n = n;
+  for (int r = 0; r < CTL_MAX_ROT; r++) {
+    rl.key[r] = nullptr;
+    rl.g[r] = 1;
+  }
+  for (int r = 0; r < n; r++) {
+    const int64_t amt = r0 + step * r;
+    const u64 g = ctl_galois_element(c, amt);
+    auto it = k->evk.find(g);
+    if (it == k->evk.end()) {
+      set_error("dense: missing Galois key for rotation %lld", (long long)amt);
+      return CTL_EKEY;
+    }
+    rl.key[r] = it->second;
+    rl.g[r] = g;
+  }
+  return CTL_OK;
+}
+
+// Dense layer by Eq. (bsgs) with every ModDown postponed (E = lvl + K limbs):
+//   baby[0] = P * in, baby[j] = (P * sigma_j(c0) + ip_j.0, ip_j.1)   (one shared ModUp of c1),
+//   inner[k] = sum_j diag'_{k t1 + j} o baby[j]                        (all E limbs),
+//   S = inner[0] + sum_{k >= 1} (sigma_{k t1}(inner[k].0) + ip'_k.0, ip'_k.1),
+//       ip'_k = key product of ModDown(inner[k].1) for rot_{k t1},
+//   out = rescale( ModDown(S) [+ bias] ),  batch nb.
 int dense_apply(ctl_context* c, const ctl_keys* k, const DenseLayer& D, const u64* in, int nb, u64* out) {
   const uint32_t N = c->N, lvl = D.lvl, t1 = D.t1, t2 = D.t2;
-  const size_t ctw = (size_t)2 * lvl * N, bw = ctw * nb;
-  DBuf baby(c, bw * t1), inner(c, bw * t2), acc(c, bw);
-  if (!baby.p || !inner.p || !acc.p) {
+  const int E = (int)lvl + (int)c->K;
+  const int nd = ((int)lvl + (int)c->alpha - 1) / (int)c->alpha;
+  const size_t EN = (size_t)E * N, LN = (size_t)lvl * N, ctw = 2 * LN, xw = 2 * EN * nb;
+  const InvScale* mu = c->d_mu_scale + (size_t)(lvl - 1) * (c->L + c->K);
+  DBuf baby(c, xw * t1), inner(c, xw * t2);
+  if (!baby.p || !inner.p) {
     set_error("dense: allocation failed (batch %d)", nb);
     return CTL_ENOMEM;
   }
-  // baby steps rot_j(in), j = 0..t1-1 (hoisted: one ModUp shared by all)
-  std::vector<int64_t> rots;
-  for (uint32_t j = 0; j < t1; j++) rots.push_back(j);
-  if (int rc = rotate_many(c, k, in, nb, (int)lvl, rots, baby.p)) return rc;
+  // baby steps in the extended basis
+  launch_scale_to_ext(c, in, baby.p, nb, (int)lvl);
+  if (t1 > 1) {
+    DBuf xc(c, (size_t)nb * LN), ext(c, (size_t)nb * nd * EN);
+    CHECK_ALLOC(xc);
+    CHECK_ALLOC(ext);
+    launch_ntt_inv_oop(c, in + LN, ctw, xc.p, LN, nb, 0, (int)lvl, (int)lvl, mu);
+    launch_modup_ntt(c, xc.p, LN, in + LN, ctw, nb, (int)lvl, ext.p);
+    for (uint32_t j0 = 1; j0 < t1; j0 += CTL_MAX_ROT) {
+      const int n = (int)std::min<uint32_t>(t1 - j0, CTL_MAX_ROT);
+      RotList rl;
+      if (int rc = rot_list(c, k, j0, 1, n, rl)) return rc;
+      launch_key_ip(c, ext.p, 0, nb, (int)lvl, rl, baby.p + (size_t)j0 * xw, in, ctw);
+    }
+    c->op_rot += (uint64_t)(t1 - 1) * nb;
+  }
   // inner sums for all giant steps
-  launch_bsgs_inner(c, baby.p, D.diag, (size_t)lvl * N, inner.p, (int)t1, (int)t2, nb, (int)lvl);
+  launch_bsgs_inner(c, baby.p, D.diag, EN, inner.p, (int)t1, (int)t2, nb, E, (int)lvl);
   c->op_ptmul += (uint64_t)D.t * nb;
   c->op_add += (uint64_t)(D.t - 1) * nb;
-  // giant steps: rot_{k t1}(inner_k) for k >= 1, chunked, each with its own input
-  cudaMemcpyAsync(acc.p, inner.p, bw * sizeof(u64), cudaMemcpyDeviceToDevice, c->stream);
+  dev_free(c, baby.release());
+  // giant steps accumulated into S = inner[0], chunked by rotations
   if (t2 > 1) {
-    const int E = (int)lvl + (int)c->K;
-    const int nd = ((int)lvl + (int)c->alpha - 1) / (int)c->alpha;
-    const size_t per = (size_t)nb * N * sizeof(u64) * ((size_t)2 * E + (size_t)nd * E + lvl + 2 * lvl);
-    const int chunk = (int)std::min<size_t>(CTL_MAX_ROT, std::max<size_t>(1, ((size_t)6 << 30) / std::max<size_t>(per, 1)));
-    DBuf rot(c, bw * std::min<uint32_t>(t2 - 1, (uint32_t)chunk));
-    CHECK_ALLOC(rot);
+    const size_t per = (size_t)nb * N * sizeof(u64) * (2 * (size_t)lvl + (size_t)nd * E);
+    const int chunk = (int)std::min<size_t>(
+        std::min<size_t>(CTL_MAX_ROT, t2 - 1), std::max<size_t>(1, ((size_t)6 << 30) / std::max<size_t>(per, 1)));
+    DBuf x1(c, (size_t)chunk * nb * LN), xc(c, (size_t)chunk * nb * LN), ext(c, (size_t)chunk * nb * nd * EN);
+    if (!x1.p || !xc.p || !ext.p) {
+      set_error("dense: allocation failed (batch %d)", nb);
+      return CTL_ENOMEM;
+    }
     for (uint32_t k0 = 1; k0 < t2; k0 += chunk) {
-      const uint32_t k1 = std::min<uint32_t>(t2, k0 + chunk);
-      std::vector<const u64*> keys;
-      std::vector<u64> gs;
-      for (uint32_t kk = k0; kk < k1; kk++) {
-        const u64 g = ctl_galois_element(c, (int64_t)kk * t1);
-        auto it = k->evk.find(g);
-        if (it == k->evk.end()) {
-          set_error("dense: missing Galois key for rotation %u", kk * t1);
-          return CTL_EKEY;
-        }
-        keys.push_back(it->second);
-        gs.push_back(g);
-      }
-      const u64* src = inner.p + (size_t)k0 * bw;
-      int rc = keyswitch(c, (int)(k1 - k0), nb, (int)lvl, src + (size_t)lvl * N, bw, ctw, keys, gs, src, bw, ctw, 0,
-                         false, rot.p);
-      if (rc) return rc;
-      c->op_rot += (uint64_t)(k1 - k0) * nb;
-      for (uint32_t kk = k0; kk < k1; kk++)
-        launch_add(c, acc.p, rot.p + (size_t)(kk - k0) * bw, acc.p, nb * 2, (int)lvl, (size_t)lvl * N,
-                   (size_t)lvl * N, (size_t)lvl * N);
+      const int nr = (int)std::min<uint32_t>(t2 - k0, (uint32_t)chunk);
+      RotList rl;
+      if (int rc = rot_list(c, k, (int64_t)k0 * t1, t1, nr, rl)) return rc;
+      u64* Ik = inner.p + (size_t)k0 * xw;
+      // ModDown of the c1 parts (special limbs to coefficient form in place first)
+      launch_ntt_inv_oop(c, Ik + EN, 2 * EN, Ik + EN, 2 * EN, nr * nb, (int)lvl, E, (int)lvl, c->d_md_scale);
+      launch_moddown_polys(c, Ik + EN, 2 * EN, nr * nb, (int)lvl, x1.p, LN);
+      // key products of the rotations, kept in the extended basis and summed into S
+      launch_ntt_inv_oop(c, x1.p, LN, xc.p, LN, nr * nb, 0, (int)lvl, (int)lvl, mu);
+      launch_modup_ntt(c, xc.p, LN, x1.p, LN, nr * nb, (int)lvl, ext.p);
+      launch_key_ip_acc(c, ext.p, (size_t)nb * nd * EN, nb, (int)lvl, rl, Ik, xw, 2 * EN, inner.p, 2 * EN);
+      c->op_rot += (uint64_t)nr * nb;
     }
   }
+  // one ModDown of both polys of S, then bias and rescale
+  DBuf acc(c, (size_t)nb * ctw);
+  CHECK_ALLOC(acc);
+  launch_ntt_inv_oop(c, inner.p, EN, inner.p, EN, 2 * nb, (int)lvl, E, (int)lvl, c->d_md_scale);
+  launch_moddown_polys(c, inner.p, EN, 2 * nb, (int)lvl, acc.p, LN);
   if (D.bias) launch_add_plain(c, acc.p, D.bias, nb, (int)lvl, ctw);
   return rescale_into(c, acc.p, nb, (int)lvl, out);
 }
@@ -1342,7 +1398,7 @@ extern "C" int ctl_mul_plain_coeffs(ctl_context* c, const ctl_ct* in, const int6
   }
   *out = nullptr;
   u64* d = nullptr;
-  int rc = upload_plaintexts(c, (const i64*)pt, 1, in->level, true, &d);
+  int rc = upload_plaintexts(c, (const i64*)pt, 1, in->level, in->level, true, &d);
   if (rc) return rc;
   ctl_ct* o = new_ct(c, in->level, in->count, in->scale * pt_scale);
   if (!o) {

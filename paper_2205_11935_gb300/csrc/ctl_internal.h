@@ -70,6 +70,8 @@ struct ModDownTab {
   ConvTab conv;       // S = special primes, targets = data primes 0..L-1
   const u64* pinv;    // [L] P^-1 mod q_i
   const u64* pinv_sh; // [L]
+  const u64* pmod;    // [L] P mod q_i
+  const u64* pmod_sh; // [L]
 };
 
 // ---------------------------------------------------------------------------------
@@ -224,13 +226,30 @@ void launch_modup_ntt(ctl_context* c, const u64* src_coef, size_t coef_stride, c
 // Key inner products with automorphism: for rotation r (g[r], key[r]) and batch b:
 //   acc[r][b][t][i][k] = sum_d ext_r[b][d][i][perm_g(k)] * key_r[d][t][prime(i)][k],
 // ext_r = ext + r * ext_r_stride (0 when the ModUp is shared by all rotations).
-void launch_key_ip(ctl_context* c, const u64* ext, size_t ext_r_stride, int nb, int lvl, const RotList& rl, u64* acc);
+// With add_c0 set, output poly t = 0 on the data limbs also gets (P mod q_i) * sigma_g(c0)
+// with c0 of input b at add_c0 + b*add_b (NTT form, level lvl): the baby step of a
+// rotation kept in the extended basis.
+void launch_key_ip(ctl_context* c, const u64* ext, size_t ext_r_stride, int nb, int lvl, const RotList& rl, u64* acc,
+                   const u64* add_c0 = nullptr, size_t add_b = 0);
+// Key inner products of nr = rl.n rotations summed into S in the extended basis:
+//   S[b][0] += sum_r ( ip_r[b][0] + sigma_{g_r}(add[r][b]) ),  S[b][1] += sum_r ip_r[b][1],
+// ext_r = ext + r*ext_r_stride ([nb][nd][E][N] each), add[r][b] = add + r*add_r + b*add_b
+// ([E][N]), S[b] = S + b*s_b ([2][E][N]).
+void launch_key_ip_acc(ctl_context* c, const u64* ext, size_t ext_r_stride, int nb, int lvl, const RotList& rl,
+                       const u64* add, size_t add_r, size_t add_b, u64* S, size_t s_b);
+// Extended-basis image of a batch: out[b][t] ([E][N]) = P * in[b][t] on the data limbs,
+// 0 on the special limbs; in [nb][2][lvl][N].
+void launch_scale_to_ext(ctl_context* c, const u64* in, u64* out, int nb, int lvl);
 // ModDown after the special limbs of acc [nr][nb][2][E][N] were inverse-transformed in
 // place: out[p][i] = (acc[p][i] - NTT_i(conv_i(acc[p][specials]))) * P^-1 (+ addend),
 // out [nr][nb][2][lvl][N].  Addend of output (r, b, t): addend + r*add_r + b*add_b + t*add_p
 // read through sigma_{g_r}; t = 1 gets one only if add_both.
 void launch_moddown_ntt(ctl_context* c, const u64* acc, int nr, int nb, int lvl, u64* out, const u64* addend,
                         size_t add_r, size_t add_b, size_t add_p, bool add_both, const RotList& rl);
+// ModDown of n_polys extended polys spaced by acc_stride (special limbs already
+// inverse-transformed in place, as above) into out + p*out_stride ([lvl][N]), no addend.
+void launch_moddown_polys(ctl_context* c, const u64* acc, size_t acc_stride, int n_polys, int lvl, u64* out,
+                          size_t out_stride);
 // Out-of-place inverse NTT; with scl, limb output of prime pi is also multiplied by the
 // factor folded into scl[pi].
 void launch_ntt_inv_oop(ctl_context* c, const u64* src, size_t src_stride, u64* dst, size_t dst_stride, int n_polys,
@@ -262,12 +281,13 @@ void launch_encrypt_combine(ctl_context* c, u64* ct, const u64* s_ntt, const u64
 void launch_decrypt_mul(ctl_context* c, const u64* ct, const u64* s_ntt, u64* out, int nb, int lvl);
 // Automorphism of a whole object in the NTT domain.
 void launch_automorph(ctl_context* c, const u64* in, u64* out, int n_polys, int limbs, int lvl, size_t stride, u64 g);
-// Baby-step giant-step inner sums:
+// Baby-step giant-step inner sums over polys of `limbs` limbs (prime map (lvl, L)):
 //   inner[k][b][p][i] = sum_j diag[k*t1+j][i] * baby[j][b][p][i]   (diag in Montgomery form)
 void launch_bsgs_inner(ctl_context* c, const u64* baby, const u64* diag, size_t diag_stride, u64* inner, int t1,
-                       int t2, int nb, int lvl);
-// Re-pack Montgomery-form plaintext limbs [cnt][lvl][N] for the split product: on limbs
-// whose prime has split width w > 0, v -> (v >> w) << 32 | (v & (2^w - 1)).
-void launch_split_limbs(ctl_context* c, u64* data, int cnt, int lvl);
+                       int t2, int nb, int limbs, int lvl);
+// Re-pack Montgomery-form plaintext limbs [cnt][limbs][N] (prime map (lvl, L)) for the
+// split product: on limbs whose prime has split width w > 0,
+// v -> (v >> w) << 32 | (v & (2^w - 1)).
+void launch_split_limbs(ctl_context* c, u64* data, int cnt, int limbs, int lvl);
 
 }  // namespace ctl

@@ -4,6 +4,8 @@
 // All products are exact: Montgomery reduction of 128-bit accumulators against
 // operands stored in Montgomery form (keys, diagonal plaintexts), so a lazy sum of
 // several 64x64-bit products costs one reduction.
+#include <algorithm>
+
 #include "ctl_internal.h"
 #include "modarith.cuh"
 
@@ -306,40 +308,26 @@ __device__ __forceinline__ u64 split_redc(u64 a00, u64 a01, u64 a11, int w, u64 
   return redc(hi, lo, q, qinv);
 }
 
+// Key values of one (limb, coefficient) for the nd digits of one rotation, split into
+// w-bit halves where the limb's prime has a split width.
 template <int ND>
-__global__ void __launch_bounds__(256) k_key_ip(const u64* __restrict__ ext, size_t ext_r,
-                                                const __grid_constant__ RotList rl, u64* __restrict__ acc,
-                                                const DPrime* __restrict__ pr, int logN, int nb, int nd, int E,
-                                                int lvl, int L, int LK) {
-  const size_t N = (size_t)1 << logN;
-  const size_t EN = (size_t)E << logN;
-  const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (idx >= EN) return;
-  const int r = blockIdx.y;
-  const int i = (int)(idx >> logN);
-  const uint32_t k = (uint32_t)(idx & (N - 1));
-  const int pi = i < lvl ? i : L + (i - lvl);
-  const DPrime P = pr[pi];
-  const int w = (int)P.split;
-  const u64 mask = w ? (1ull << w) - 1 : 0;
-  const u64* key = rl.key[r];
-  const u64 g = rl.g[r];
-  const uint32_t ks = g == 1 ? k : auto_src_k(k, g, logN);
+struct KeyRegs {
   u64 k0[ND], k1[ND];
+  __device__ __forceinline__ void load(const u64* key, int nd, int pi, int LK, size_t N, uint32_t k, int w,
+                                       u64 mask) {
 #pragma unroll
-  for (int d = 0; d < ND; d++) {
-    k0[d] = d < nd ? key[(((size_t)d * 2) * LK + pi) * N + k] : 0;
-    k1[d] = d < nd ? key[(((size_t)d * 2 + 1) * LK + pi) * N + k] : 0;
-    if (w) {
-      k0[d] = split_of(k0[d], w, mask);
-      k1[d] = split_of(k1[d], w, mask);
+    for (int d = 0; d < ND; d++) {
+      k0[d] = d < nd ? key[(((size_t)d * 2) * LK + pi) * N + k] : 0;
+      k1[d] = d < nd ? key[(((size_t)d * 2 + 1) * LK + pi) * N + k] : 0;
+      if (w) {
+        k0[d] = split_of(k0[d], w, mask);
+        k1[d] = split_of(k1[d], w, mask);
+      }
     }
   }
-  const u64* ex = ext + (size_t)r * ext_r + ((size_t)i << logN) + ks;
-  u64* o = acc + (size_t)r * 2 * nb * EN + idx;
-  for (int b = 0; b < nb; b++) {
-    const u64* eb = ex + (size_t)b * nd * EN;
-    u64 r0, r1;
+  // (r0, r1) = sum_d eb[d*EN] * (k0[d], k1[d]) mod q, plain residues.
+  __device__ __forceinline__ void ip(const u64* eb, size_t EN, int nd, int w, u64 mask, const DPrime& P, u64& r0,
+                                     u64& r1) const {
     if (w) {
       u64 a00 = 0, a01 = 0, a11 = 0, c00 = 0, c01 = 0, c11 = 0;
 #pragma unroll
@@ -368,11 +356,47 @@ __global__ void __launch_bounds__(256) k_key_ip(const u64* __restrict__ ext, siz
       r0 = redc(hi0, lo0, P.q, P.qinv);
       r1 = redc(hi1, lo1, P.q, P.qinv);
     }
+  }
+};
+
+template <int ND>
+__global__ void __launch_bounds__(256) k_key_ip(const u64* __restrict__ ext, size_t ext_r,
+                                                const __grid_constant__ RotList rl, u64* __restrict__ acc,
+                                                const u64* __restrict__ add_c0, size_t add_b,
+                                                const u64* __restrict__ pmod, const u64* __restrict__ pmod_sh,
+                                                const DPrime* __restrict__ pr, int logN, int nb, int nd, int E,
+                                                int lvl, int L, int LK) {
+  const size_t N = (size_t)1 << logN;
+  const size_t EN = (size_t)E << logN;
+  const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (idx >= EN) return;
+  const int r = blockIdx.y;
+  const int i = (int)(idx >> logN);
+  const uint32_t k = (uint32_t)(idx & (N - 1));
+  const int pi = i < lvl ? i : L + (i - lvl);
+  const DPrime P = pr[pi];
+  const int w = (int)P.split;
+  const u64 mask = w ? (1ull << w) - 1 : 0;
+  const u64 g = rl.g[r];
+  const uint32_t ks = g == 1 ? k : auto_src_k(k, g, logN);
+  KeyRegs<ND> kr;
+  kr.load(rl.key[r], nd, pi, LK, N, k, w, mask);
+  // baby step in the extended basis: + (P mod q_i) * sigma_g(c0) on the data limbs
+  const bool with_c0 = add_c0 != nullptr && i < lvl;
+  const u64 pm = with_c0 ? __ldg(pmod + i) : 0, pms = with_c0 ? __ldg(pmod_sh + i) : 0;
+  const u64* c0 = with_c0 ? add_c0 + ((size_t)i << logN) + ks : nullptr;
+  const u64* ex = ext + (size_t)r * ext_r + ((size_t)i << logN) + ks;
+  u64* o = acc + (size_t)r * 2 * nb * EN + idx;
+  for (int b = 0; b < nb; b++) {
+    u64 r0, r1;
+    kr.ip(ex + (size_t)b * nd * EN, EN, nd, w, mask, P, r0, r1);
+    if (with_c0) r0 = addmod(r0, shoup(c0[(size_t)b * add_b], pm, pms, P.q), P.q);
     o[(size_t)b * 2 * EN] = r0;
     o[(size_t)b * 2 * EN + EN] = r1;
   }
 }
-void launch_key_ip(ctl_context* c, const u64* ext, size_t ext_r, int nb, int lvl, const RotList& rl, u64* acc) {
+void launch_key_ip(ctl_context* c, const u64* ext, size_t ext_r, int nb, int lvl, const RotList& rl, u64* acc,
+                   const u64* add_c0, size_t add_b) {
   const int nrot = rl.n;
   const int nd = (lvl + (int)c->alpha - 1) / (int)c->alpha;
   const int E = lvl + (int)c->K;
@@ -380,16 +404,104 @@ void launch_key_ip(ctl_context* c, const u64* ext, size_t ext_r, int nb, int lvl
   const size_t EN = (size_t)E * c->N;
   dim3 grid((unsigned)((EN + 255) / 256), (unsigned)nrot);
   double work = 2.0 * nd * EN * nb * nrot;
+  const u64* pm = c->moddown.pmod;
+  const u64* pms = c->moddown.pmod_sh;
 #define CTL_KEYIP_CASE(NDV)                                                                                    \
   CTL_LAUNCH(KC_KEYIP, work, grid,                                                                             \
-             (k_key_ip<NDV><<<grid, 256, 0, c->stream>>>(ext, ext_r, rl, acc, c->d_primes, (int)c->logN, nb, nd, \
-                                                         E, lvl, (int)c->L, LK)))
+             (k_key_ip<NDV><<<grid, 256, 0, c->stream>>>(ext, ext_r, rl, acc, add_c0, add_b, pm, pms,           \
+                                                         c->d_primes, (int)c->logN, nb, nd, E, lvl, (int)c->L, \
+                                                         LK)))
   if (nd <= 1) CTL_KEYIP_CASE(1);
   else if (nd <= 2) CTL_KEYIP_CASE(2);
   else if (nd <= 4) CTL_KEYIP_CASE(4);
   else if (nd <= 8) CTL_KEYIP_CASE(8);
   else CTL_KEYIP_CASE(16);
 #undef CTL_KEYIP_CASE
+}
+
+// Giant steps in the extended basis: one thread per (limb i, coefficient k) sweeps the
+// rotations r (their key values in registers, one rotation at a time) and, for each,
+// the ciphertexts b of its block's share of the batch, adding the key product and the
+// rotated poly-0 term into the running sum S.  Every element of S has one owner thread,
+// so no two threads update it.
+template <int ND>
+__global__ void __launch_bounds__(256) k_key_ip_acc(const u64* __restrict__ ext, size_t ext_r,
+                                                    const __grid_constant__ RotList rl, const u64* __restrict__ add,
+                                                    size_t add_r, size_t add_b, u64* __restrict__ S, size_t s_b,
+                                                    const DPrime* __restrict__ pr, int logN, int nb, int b_per,
+                                                    int nd, int E, int lvl, int L, int LK) {
+  const size_t N = (size_t)1 << logN;
+  const size_t EN = (size_t)E << logN;
+  const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (idx >= EN) return;
+  const int b0 = blockIdx.y * b_per, b1 = min(nb, b0 + b_per);
+  const int i = (int)(idx >> logN);
+  const uint32_t k = (uint32_t)(idx & (N - 1));
+  const int pi = i < lvl ? i : L + (i - lvl);
+  const DPrime P = pr[pi];
+  const int w = (int)P.split;
+  const u64 mask = w ? (1ull << w) - 1 : 0;
+  for (int r = 0; r < rl.n; r++) {
+    const u64 g = rl.g[r];
+    const uint32_t ks = g == 1 ? k : auto_src_k(k, g, logN);
+    KeyRegs<ND> kr;
+    kr.load(rl.key[r], nd, pi, LK, N, k, w, mask);
+    const u64* ex = ext + (size_t)r * ext_r + ((size_t)i << logN) + ks;
+    const u64* ad = add + (size_t)r * add_r + ((size_t)i << logN) + ks;
+    for (int b = b0; b < b1; b++) {
+      u64 r0, r1;
+      kr.ip(ex + (size_t)b * nd * EN, EN, nd, w, mask, P, r0, r1);
+      u64* sb = S + (size_t)b * s_b + idx;
+      sb[0] = addmod(sb[0], addmod(r0, ad[(size_t)b * add_b], P.q), P.q);
+      sb[EN] = addmod(sb[EN], r1, P.q);
+    }
+  }
+}
+void launch_key_ip_acc(ctl_context* c, const u64* ext, size_t ext_r, int nb, int lvl, const RotList& rl,
+                       const u64* add, size_t add_r, size_t add_b, u64* S, size_t s_b) {
+  const int nd = (lvl + (int)c->alpha - 1) / (int)c->alpha;
+  const int E = lvl + (int)c->K;
+  const int LK = (int)(c->L + c->K);
+  const size_t EN = (size_t)E * c->N;
+  const unsigned gx = (unsigned)((EN + 255) / 256);
+  // split the batch over blockIdx.y until the grid covers the SMs several times over
+  const int want = (int)((8u * (unsigned)c->sm_count + gx - 1) / gx);
+  const int splits = std::max(1, std::min(nb, want));
+  const int b_per = (nb + splits - 1) / splits;
+  dim3 grid(gx, (unsigned)((nb + b_per - 1) / b_per));
+  double work = 2.0 * nd * EN * nb * rl.n;
+#define CTL_KEYIPA_CASE(NDV)                                                                                     \
+  CTL_LAUNCH(KC_KEYIP, work, grid,                                                                               \
+             (k_key_ip_acc<NDV><<<grid, 256, 0, c->stream>>>(ext, ext_r, rl, add, add_r, add_b, S, s_b,           \
+                                                             c->d_primes, (int)c->logN, nb, b_per, nd, E, lvl,    \
+                                                             (int)c->L, LK)))
+  if (nd <= 1) CTL_KEYIPA_CASE(1);
+  else if (nd <= 2) CTL_KEYIPA_CASE(2);
+  else if (nd <= 4) CTL_KEYIPA_CASE(4);
+  else if (nd <= 8) CTL_KEYIPA_CASE(8);
+  else CTL_KEYIPA_CASE(16);
+#undef CTL_KEYIPA_CASE
+}
+
+// Extended-basis image P * x of a batch: data limbs times (P mod q_i), special limbs 0.
+__global__ void k_scale_ext(const u64* __restrict__ in, u64* __restrict__ out, const u64* __restrict__ pmod,
+                            const u64* __restrict__ pmod_sh, const DPrime* __restrict__ pr, int logN, int lvl, int E,
+                            size_t total) {
+  const size_t EN = (size_t)E << logN, LN = (size_t)lvl << logN;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t p = idx / EN, r = idx % EN;
+    const int i = (int)(r >> logN);
+    out[idx] = i < lvl ? shoup(in[p * LN + r], __ldg(pmod + i), __ldg(pmod_sh + i), pr[i].q) : 0;
+  }
+}
+void launch_scale_to_ext(ctl_context* c, const u64* in, u64* out, int nb, int lvl) {
+  const int E = lvl + (int)c->K;
+  size_t total = (size_t)nb * 2 * E * c->N;
+  if (!total) return;
+  int g = elem_grid(c, total);
+  CTL_LAUNCH(KC_ELEM, 0, g,
+             (k_scale_ext<<<g, kThreads, 0, c->stream>>>(in, out, c->moddown.pmod, c->moddown.pmod_sh, c->d_primes,
+                                                         (int)c->logN, lvl, E, total)));
 }
 
 // ---------------------------------------------------------------------------------
@@ -405,37 +517,37 @@ void launch_key_ip(ctl_context* c, const u64* ext, size_t ext_r, int nb, int lvl
 // otherwise full 64x64->128 products are summed.  One Montgomery reduction per output
 // (diagonals are in Montgomery form; t1 * q < 2^64 keeps the REDC precondition).
 // ---------------------------------------------------------------------------------
-__global__ void k_split(u64* data, const DPrime* __restrict__ pr, int logN, int lvl, size_t total) {
-  const size_t N = (size_t)1 << logN;
+__global__ void k_split(u64* data, const DPrime* __restrict__ pr, int logN, int limbs, int lvl, int L,
+                        size_t total) {
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)((idx >> logN) % lvl);
-    const int w = (int)pr[i].split;
+    const int i = (int)((idx >> logN) % limbs);
+    const int w = (int)pr[i < lvl ? i : L + (i - lvl)].split;
     if (!w) continue;
     const u64 v = data[idx];
     data[idx] = ((v >> w) << 32) | (v & ((1ull << w) - 1));
   }
-  (void)N;
 }
-void launch_split_limbs(ctl_context* c, u64* data, int cnt, int lvl) {
-  size_t total = (size_t)cnt * lvl * c->N;
+void launch_split_limbs(ctl_context* c, u64* data, int cnt, int limbs, int lvl) {
+  size_t total = (size_t)cnt * limbs * c->N;
   int g = elem_grid(c, total);
-  CTL_LAUNCH(KC_ELEM, 0, g, (k_split<<<g, kThreads, 0, c->stream>>>(data, c->d_primes, (int)c->logN, lvl, total)));
+  CTL_LAUNCH(KC_ELEM, 0, g,
+             (k_split<<<g, kThreads, 0, c->stream>>>(data, c->d_primes, (int)c->logN, limbs, lvl, (int)c->L, total)));
 }
 
 template <int T1>
 __global__ void __launch_bounds__(256) k_bsgs(const u64* __restrict__ baby, const u64* __restrict__ diag,
                                               size_t diag_stride, u64* __restrict__ inner,
                                               const DPrime* __restrict__ pr, int logN, int t1, int t2, int nb,
-                                              int lvl) {
+                                              int limbs, int lvl, int L) {
   __shared__ u64 Ds[T1][32];
-  const size_t LN = (size_t)lvl << logN;
+  const size_t LN = (size_t)limbs << logN;
   const int bp_count = nb * 2;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int bp = blockIdx.x * 8 + warp;
   const size_t c0 = (size_t)blockIdx.y * 32;  // first coefficient index in [0, lvl*N)
   const size_t cidx = c0 + lane;
   const int i = (int)(c0 >> logN);
-  const DPrime P = pr[i];
+  const DPrime P = pr[i < lvl ? i : L + (i - lvl)];
   const int w = (int)P.split;
   const bool active = bp < bp_count;
   const size_t bstride = (size_t)bp_count * LN;  // stride between baby steps j
@@ -494,15 +606,15 @@ __global__ void __launch_bounds__(256) k_bsgs(const u64* __restrict__ baby, cons
 }
 
 void launch_bsgs_inner(ctl_context* c, const u64* baby, const u64* diag, size_t diag_stride, u64* inner, int t1,
-                       int t2, int nb, int lvl) {
-  const size_t LN = (size_t)lvl * c->N;
+                       int t2, int nb, int limbs, int lvl) {
+  const size_t LN = (size_t)limbs * c->N;
   dim3 grid((unsigned)((nb * 2 + 7) / 8), (unsigned)(LN / 32));
   double work = (double)t1 * t2 * nb * 2 * LN;
 #define CTL_BSGS_CASE(TT)                                                                                      \
   case TT:                                                                                                     \
     CTL_LAUNCH(KC_BSGS, work, grid,                                                                            \
                (k_bsgs<TT><<<grid, 256, 0, c->stream>>>(baby, diag, diag_stride, inner, c->d_primes,           \
-                                                        (int)c->logN, t1, t2, nb, lvl)));                      \
+                                                        (int)c->logN, t1, t2, nb, limbs, lvl, (int)c->L)));    \
     break;
   int T1 = 1;
   while (T1 < t1) T1 <<= 1;

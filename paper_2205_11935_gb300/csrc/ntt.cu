@@ -864,19 +864,19 @@ void launch_modup_ntt(ctl_context* c, const u64* src_coef, size_t coef_stride, c
 }
 
 template <int NS>
-static void moddown_ns(ctl_context* c, const u64* acc, int nr, int nb, int lvl, u64* out, const u64* addend,
-                       size_t add_r, size_t add_b, size_t add_p, bool add_both, const RotList& rl) {
-  const int E = lvl + (int)c->K;
+static void moddown_ns(ctl_context* c, const u64* acc, size_t acc_stride, int n_polys, int lvl, u64* out,
+                       size_t out_stride, const u64* addend, size_t add_r, size_t add_b, size_t add_p, bool add_both,
+                       int nb, const RotList* rl) {
   ProModDown<NS> pro;
   pro.acc = acc;
-  pro.acc_stride = (size_t)E * c->N;
+  pro.acc_stride = acc_stride;
   pro.lvl = lvl;
   pro.tab = c->moddown.conv;
   EpiModDown epi;
   epi.acc = acc;
-  epi.acc_stride = (size_t)E * c->N;
+  epi.acc_stride = acc_stride;
   epi.out = out;
-  epi.out_stride = (size_t)lvl * c->N;
+  epi.out_stride = out_stride;
   epi.pinv = c->moddown.pinv;
   epi.pinv_sh = c->moddown.pinv_sh;
   epi.addend = addend;
@@ -885,19 +885,32 @@ static void moddown_ns(ctl_context* c, const u64* acc, int nr, int nb, int lvl, 
   epi.add_p = add_p;
   epi.add_both = add_both ? 1 : 0;
   epi.nb = nb;
-  for (int r = 0; r < CTL_MAX_ROT; r++) epi.g[r] = r < rl.n ? rl.g[r] : 1;
-  run_ntt<false>(c, KC_MODDOWN, pro, epi, nr * nb * 2, 0, lvl, lvl, butterflies(c) + (double)(c->K * 2 + 1) * c->N);
+  for (int r = 0; r < CTL_MAX_ROT; r++) epi.g[r] = (rl && r < rl->n) ? rl->g[r] : 1;
+  run_ntt<false>(c, KC_MODDOWN, pro, epi, n_polys, 0, lvl, lvl, butterflies(c) + (double)(c->K * 2 + 1) * c->N);
+}
+
+template <class... A>
+static void moddown_dispatch(ctl_context* c, A... a) {
+  switch (c->K) {
+    case 1: moddown_ns<1>(c, a...); break;
+    case 2: moddown_ns<2>(c, a...); break;
+    case 3:
+    case 4: moddown_ns<4>(c, a...); break;
+    default: moddown_ns<8>(c, a...); break;
+  }
 }
 
 void launch_moddown_ntt(ctl_context* c, const u64* acc, int nr, int nb, int lvl, u64* out, const u64* addend,
                         size_t add_r, size_t add_b, size_t add_p, bool add_both, const RotList& rl) {
-  switch (c->K) {
-    case 1: moddown_ns<1>(c, acc, nr, nb, lvl, out, addend, add_r, add_b, add_p, add_both, rl); break;
-    case 2: moddown_ns<2>(c, acc, nr, nb, lvl, out, addend, add_r, add_b, add_p, add_both, rl); break;
-    case 3:
-    case 4: moddown_ns<4>(c, acc, nr, nb, lvl, out, addend, add_r, add_b, add_p, add_both, rl); break;
-    default: moddown_ns<8>(c, acc, nr, nb, lvl, out, addend, add_r, add_b, add_p, add_both, rl); break;
-  }
+  const size_t EN = (size_t)(lvl + (int)c->K) * c->N;
+  moddown_dispatch(c, acc, EN, nr * nb * 2, lvl, out, (size_t)lvl * c->N, addend, add_r, add_b, add_p, add_both, nb,
+                   &rl);
+}
+
+void launch_moddown_polys(ctl_context* c, const u64* acc, size_t acc_stride, int n_polys, int lvl, u64* out,
+                          size_t out_stride) {
+  moddown_dispatch(c, acc, acc_stride, n_polys, lvl, out, out_stride, (const u64*)nullptr, (size_t)0, (size_t)0,
+                   (size_t)0, false, 1, (const RotList*)nullptr);
 }
 
 }  // namespace ctl

@@ -366,8 +366,9 @@ def test_square_matches_fp64():
     assert np.max(np.abs(o.decode(o.decrypt(sq), o.N // 2, sc) - z * z)) < 1e-6
 
 
+@pytest.mark.parametrize("composed", [False, True])
 @pytest.mark.parametrize("m,n", [(8, 16), (16, 16), (5, 12)])
-def test_dense_bsgs_matches_fp64_and_op_counts(m, n):
+def test_dense_bsgs_matches_fp64_and_op_counts(m, n, composed):
     N = 128
     t = O.Oracle.bsgs_t(m, n)
     t1 = O.Oracle.bsgs_t1(t)
@@ -383,7 +384,7 @@ def test_dense_bsgs_matches_fp64_and_op_counts(m, n):
     ct = o.encrypt(o.encode(slots), 13)
     lvl = 3
     pts = o.encode_diagonals(W, o.dense_scale(lvl, o.scale))
-    out, cnt = o.dense(ct, pts)
+    out, cnt = o.dense(ct, pts, composed=composed)
     # Sec. 3.1: t1 + t2 - 2 rotations, t plaintext products, t - 1 additions
     assert cnt == [t1 + t2 - 2, t, t - 1]
     y = o.decode(o.decrypt(out), N // 2)
@@ -412,6 +413,39 @@ def test_dense_equals_direct_diagonal_method():
     pts = o.encode_diagonals(W, sc)
     bsgs = o.decode(o.decrypt(o.dense(ct, pts)[0]), N // 2)
     assert np.max(np.abs(direct - bsgs)) < 1e-6
+
+
+@pytest.mark.parametrize("m,n,pb", [(16, 16, [60]), (32, 32, [50, 50]), (4, 8, [60])])
+def test_dense_lazy_moddown_equals_composed_rotations(m, n, pb):
+    """The lazy-ModDown form and the plain composition of whole rotations encrypt the
+    same layer output: decoded values agree far inside the noise bound, and with only
+    the j = 0, k = 0 diagonal non-zero (no rotation at all) both reduce to
+    rescale(diag o ct) exactly (ModDown(P * x) = x)."""
+    N = 128
+    t = O.Oracle.bsgs_t(m, n)
+    t1 = O.Oracle.bsgs_t1(t)
+    rots = list(range(1, t1)) + [k * t1 for k in range(1, t // t1)]
+    o = O.Oracle(N, [60, 40, 40, 40], pb, scale=2.0 ** 40)
+    o.keygen(rots, seed=3)
+    rng = np.random.default_rng(m + 7 * n)
+    W = rng.normal(0, 1 / np.sqrt(n), (m, n))
+    x = rng.uniform(-1, 1, n)
+    slots = np.zeros(N // 2); slots[:n] = x; slots[t:t + n] = x
+    ct = o.encrypt(o.encode(slots), 21)
+    pts = o.encode_diagonals(W, o.dense_scale(4, o.scale))
+    lazy, c1 = o.dense(ct, pts)
+    comp, c2 = o.dense(ct, pts, composed=True)
+    assert c1 == c2
+    y1 = o.decode(o.decrypt(lazy), N // 2)
+    y2 = o.decode(o.decrypt(comp), N // 2)
+    assert np.max(np.abs(y1 - y2)) < 1e-7
+    assert np.max(np.abs(y1[:m] - W @ x)) < 1e-6
+    # only diagonal 0 non-zero: no key switch takes part in the result
+    pz = np.zeros_like(pts); pz[0] = pts[0]
+    a, _ = o.dense(ct, pz)
+    b, _ = o.dense(ct, pz, composed=True)
+    assert np.array_equal(a, b)
+    assert np.array_equal(a, o.rescale(o.mul_plain(ct, pts[0])))
 
 
 def test_replicate():
