@@ -56,6 +56,7 @@ struct RotList {
   int n;
   const u64* key[CTL_MAX_ROT];  // device key [beta][2][L+K][N] (Montgomery, NTT form)
   u64 g[CTL_MAX_ROT];           // Galois element (1 = no automorphism)
+  u64 ginv[CTL_MAX_ROT];        // g^-1 mod 2N (filled by the key-product launcher)
 };
 
 // Last-stage constants of an inverse NTT that also multiplies its output by a per-prime

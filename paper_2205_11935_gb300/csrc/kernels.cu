@@ -368,17 +368,23 @@ __global__ void __launch_bounds__(256) k_key_ip(const u64* __restrict__ ext, siz
                                                 int lvl, int L, int LK) {
   const size_t N = (size_t)1 << logN;
   const size_t EN = (size_t)E << logN;
-  const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  // src_major (one ModUp shared by all rotations): the rotations run fastest over the
+  // grid and a thread owns a SOURCE element s, writing destination k = sigma_g^-1(s), so
+  // consecutive blocks read the same digits (from L2).  Otherwise a thread owns a
+  // destination element k and gathers its source s = sigma_g(k).
+  const bool src_major = ext_r == 0;
+  const int r = src_major ? blockIdx.x : blockIdx.y;
+  const size_t idx = (src_major ? blockIdx.y : blockIdx.x) * (size_t)blockDim.x + threadIdx.x;
   if (idx >= EN) return;
-  const int r = blockIdx.y;
   const int i = (int)(idx >> logN);
-  const uint32_t k = (uint32_t)(idx & (N - 1));
+  const uint32_t e = (uint32_t)(idx & (N - 1));
   const int pi = i < lvl ? i : L + (i - lvl);
   const DPrime P = pr[pi];
   const int w = (int)P.split;
   const u64 mask = w ? (1ull << w) - 1 : 0;
   const u64 g = rl.g[r];
-  const uint32_t ks = g == 1 ? k : auto_src_k(k, g, logN);
+  const uint32_t k = (g == 1 || !src_major) ? e : auto_src_k(e, rl.ginv[r], logN);
+  const uint32_t ks = (g == 1 || src_major) ? e : auto_src_k(e, g, logN);
   KeyRegs<ND> kr;
   kr.load(rl.key[r], nd, pi, LK, N, k, w, mask);
   // baby step in the extended basis: + (P mod q_i) * sigma_g(c0) on the data limbs
@@ -386,7 +392,7 @@ __global__ void __launch_bounds__(256) k_key_ip(const u64* __restrict__ ext, siz
   const u64 pm = with_c0 ? __ldg(pmod + i) : 0, pms = with_c0 ? __ldg(pmod_sh + i) : 0;
   const u64* c0 = with_c0 ? add_c0 + ((size_t)i << logN) + ks : nullptr;
   const u64* ex = ext + (size_t)r * ext_r + ((size_t)i << logN) + ks;
-  u64* o = acc + (size_t)r * 2 * nb * EN + idx;
+  u64* o = acc + (size_t)r * 2 * nb * EN + ((size_t)i << logN) + k;
   for (int b = 0; b < nb; b++) {
     u64 r0, r1;
     kr.ip(ex + (size_t)b * nd * EN, EN, nd, w, mask, P, r0, r1);
@@ -395,14 +401,24 @@ __global__ void __launch_bounds__(256) k_key_ip(const u64* __restrict__ ext, siz
     o[(size_t)b * 2 * EN + EN] = r1;
   }
 }
-void launch_key_ip(ctl_context* c, const u64* ext, size_t ext_r, int nb, int lvl, const RotList& rl, u64* acc,
+// g^-1 mod 2N for odd g (2N a power of two): Newton iteration on the 2-adic inverse.
+static u64 inv_mod_2n(u64 g, u64 two_n) {
+  u64 x = g;  // correct to 3 bits for odd g
+  for (int it = 0; it < 6; it++) x *= 2 - g * x;
+  return x & (two_n - 1);
+}
+
+void launch_key_ip(ctl_context* c, const u64* ext, size_t ext_r, int nb, int lvl, const RotList& rl_in, u64* acc,
                    const u64* add_c0, size_t add_b) {
+  RotList rl = rl_in;
+  for (int r = 0; r < rl.n; r++) rl.ginv[r] = inv_mod_2n(rl.g[r], 2ull * c->N);
   const int nrot = rl.n;
   const int nd = (lvl + (int)c->alpha - 1) / (int)c->alpha;
   const int E = lvl + (int)c->K;
   const int LK = (int)(c->L + c->K);
   const size_t EN = (size_t)E * c->N;
-  dim3 grid((unsigned)((EN + 255) / 256), (unsigned)nrot);
+  const unsigned eblocks = (unsigned)((EN + 255) / 256);
+  dim3 grid = ext_r == 0 ? dim3((unsigned)nrot, eblocks) : dim3(eblocks, (unsigned)nrot);
   double work = 2.0 * nd * EN * nb * nrot;
   const u64* pm = c->moddown.pmod;
   const u64* pms = c->moddown.pmod_sh;
@@ -534,23 +550,42 @@ void launch_split_limbs(ctl_context* c, u64* data, int cnt, int limbs, int lvl) 
              (k_split<<<g, kThreads, 0, c->stream>>>(data, c->d_primes, (int)c->logN, limbs, lvl, (int)c->L, total)));
 }
 
+// 16-byte global -> shared copy that completes asynchronously (L2 only), and its group
+// fences: the next giant step's diagonal tile is in flight while the current one is used.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 template <int T1>
 __global__ void __launch_bounds__(256) k_bsgs(const u64* __restrict__ baby, const u64* __restrict__ diag,
                                               size_t diag_stride, u64* __restrict__ inner,
                                               const DPrime* __restrict__ pr, int logN, int t1, int t2, int nb,
                                               int limbs, int lvl, int L) {
-  __shared__ u64 Ds[T1][32];
+  __shared__ __align__(16) u64 Ds[2][T1][32];
   const size_t LN = (size_t)limbs << logN;
   const int bp_count = nb * 2;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int bp = blockIdx.x * 8 + warp;
-  const size_t c0 = (size_t)blockIdx.y * 32;  // first coefficient index in [0, lvl*N)
+  const size_t c0 = (size_t)blockIdx.y * 32;  // first coefficient index in [0, limbs*N)
   const size_t cidx = c0 + lane;
   const int i = (int)(c0 >> logN);
   const DPrime P = pr[i < lvl ? i : L + (i - lvl)];
   const int w = (int)P.split;
   const bool active = bp < bp_count;
   const size_t bstride = (size_t)bp_count * LN;  // stride between baby steps j
+  // diag[k*t1 + j][c0 .. c0+32) for j < t1 -> Ds[buf]: t1 rows of 16 16-byte pieces
+  auto stage = [&](int k, int buf) {
+    const u64* dk = diag + (size_t)(k * t1) * diag_stride + c0;
+    for (int e = threadIdx.x; e < t1 * 16; e += blockDim.x) {
+      const int row = e >> 4, col = (e & 15) * 2;
+      cp_async16(&Ds[buf][row][col], dk + (size_t)row * diag_stride + col);
+    }
+    cp_async_commit();
+  };
+  stage(0, 0);
   u64 x[T1];
 #pragma unroll
   for (int j = 0; j < T1; j++)
@@ -561,28 +596,31 @@ __global__ void __launch_bounds__(256) k_bsgs(const u64* __restrict__ baby, cons
     for (int j = 0; j < T1; j++) x[j] = ((x[j] >> w) << 32) | (x[j] & mask);
   }
   for (int k = 0; k < t2; k++) {
-    // stage diag[k*t1 + j][c0 .. c0+32) for j < t1
-    const u64* dk = diag + (size_t)(k * t1) * diag_stride + c0;
-    for (int e = threadIdx.x; e < t1 * 32; e += blockDim.x) Ds[e >> 5][e & 31] = __ldg(dk + (size_t)(e >> 5) * diag_stride + (e & 31));
-    __syncthreads();
+    cp_async_wait_all();  // tile k has landed (the only group in flight)
+    __syncthreads();      // ... for every thread, and every warp is done with tile k-1
+    if (k + 1 < t2) stage(k + 1, (k + 1) & 1);
+    const u64(*D)[32] = Ds[k & 1];
     u64 res = 0;
     if (w) {
-      u64 a00 = 0, a01 = 0, a11 = 0;
+      // two accumulators for the middle term keep the dependent chains short
+      u64 a00 = 0, a01 = 0, a10 = 0, a11 = 0;
 #pragma unroll
       for (int j = 0; j < T1; j++) {
         if (j < t1) {
-          const u64 d = Ds[j][lane];
+          const u64 d = D[j][lane];
           const uint32_t d0 = (uint32_t)d, d1 = (uint32_t)(d >> 32);
           const uint32_t x0 = (uint32_t)x[j], x1 = (uint32_t)(x[j] >> 32);
           a00 += (u64)x0 * d0;
           a01 += (u64)x0 * d1;
-          a01 += (u64)x1 * d0;
+          a10 += (u64)x1 * d0;
           a11 += (u64)x1 * d1;
         }
       }
-      // S = a11 * 2^(2w) + a01 * 2^w + a00 as a 128-bit (hi, lo)
+      // S = a11 * 2^(2w) + (a01 + a10) * 2^w + a00 as a 128-bit (hi, lo); a01 + a10 < 2^64
+      // because each is below t1 * 2^(2w) and 2 * t1 * 2^(2w) < 2^64
+      const u64 m = a01 + a10;
       u64 lo = a00, hi = 0;
-      const u64 t_lo = a01 << w, t_hi = a01 >> (64 - w);
+      const u64 t_lo = m << w, t_hi = m >> (64 - w);
       lo += t_lo;
       hi += t_hi + (lo < t_lo);
       const u64 u_lo = a11 << (2 * w), u_hi = a11 >> (64 - 2 * w);
@@ -594,14 +632,13 @@ __global__ void __launch_bounds__(256) k_bsgs(const u64* __restrict__ baby, cons
 #pragma unroll
       for (int j = 0; j < T1; j++) {
         if (j < t1) {
-          mac(lo, hi, x[j], Ds[j][lane]);
+          mac(lo, hi, x[j], D[j][lane]);
           if (hi >= P.q) hi -= P.q;
         }
       }
       res = redc(hi, lo, P.q, P.qinv);
     }
     if (active) inner[(size_t)k * bstride + (size_t)bp * LN + cidx] = res;
-    __syncthreads();
   }
 }
 
