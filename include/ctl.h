@@ -156,7 +156,7 @@ void ctl_ct_destroy(ctl_ct* ct);
  *   ciphertext products are the costliest operation, Sec. 5.1).  Scale becomes
  *   scale^2 / q_last.
  * ctl_eval_dense: y = W x for W (m x n, row-major FP64) by Eq. (bsgs): t = next power of
- *   two >= max(m, n) (zero padding), t1 = 2^ceil(log2(t)/2), t2 = t/t1; t1+t2-2
+ *   two >= max(m, n) (zero padding), t1 = min(t, 2^ceil(log2(4t)/2)), t2 = t/t1; t1+t2-2
  *   rotations, t plaintext products, depth 1.  The input must hold [x, x] in slots
  *   [0, 2t); the output holds y in slots [0, m) and zeros elsewhere.  The diagonals are
  *   encoded at scale q_last * Delta / scale_in, so the output carries Delta again.

@@ -769,9 +769,17 @@ int orc_square(const orc_ctx* c, const orc_keys* k, const u64* ct, uint32_t lvl,
 }
 
 // Baby-step giant-step sizes (Eq. bsgs): t is the next power of two >= max(m, n) (the
-// paper pads non-square matrices with zeros), t1 = 2^ceil(log2(t)/2), t2 = t / t1.
+// paper pads non-square matrices with zeros) and t = t1 * t2.  The paper leaves the
+// split open; it is taken as t1 = min(t, 2^ceil(log2(4t)/2)), the power of two nearest
+// sqrt(4t), which minimises (t1 - 1) + 4 (t2 - 1): with the ModDowns postponed a giant
+// step costs about four baby steps.
 uint32_t orc_bsgs_t(uint32_t m, uint32_t n) { uint32_t t = 1; while (t < m || t < n) t <<= 1; return t; }
-uint32_t orc_bsgs_t1(uint32_t t) { uint32_t lg = 0; while ((1u << lg) < t) lg++; return 1u << ((lg + 1) / 2); }
+uint32_t orc_bsgs_t1(uint32_t t) {
+  uint32_t lg = 0;
+  while ((1u << lg) < t) lg++;
+  uint32_t t1 = 1u << ((lg + 3) / 2);
+  return t1 < t ? t1 : t;
+}
 
 // Diagonal plaintexts of a dense layer W (m x n, row-major) for Eq. (bsgs):
 // diag_i[r] = W[r][(r+i) mod t] (zero outside W), diag'_i = rot_{-floor(i/t1)*t1}(diag_i)

@@ -1111,10 +1111,14 @@ uint32_t bsgs_t(uint32_t m, uint32_t n) {
   while (t < m || t < n) t <<= 1;
   return t;
 }
+// t = t1 * t2 with t1 = min(t, 2^ceil(log2(4t)/2)): a giant step (ModDown of c1, ModUp,
+// key product) costs about four baby steps (a key product in the extended basis), and
+// this split minimises (t1 - 1) + 4 (t2 - 1).
 uint32_t bsgs_t1(uint32_t t) {
   uint32_t lg = 0;
   while ((1u << lg) < t) lg++;
-  return 1u << ((lg + 1) / 2);
+  const uint32_t t1 = 1u << ((lg + 3) / 2);
+  return t1 < t ? t1 : t;
 }
 
 // Upload integer coefficient plaintexts [cnt][N] as NTT-form residues over `limbs`

@@ -325,15 +325,20 @@ struct KeyRegs {
       }
     }
   }
-  // (r0, r1) = sum_d eb[d*EN] * (k0[d], k1[d]) mod q, plain residues.
-  __device__ __forceinline__ void ip(const u64* eb, size_t EN, int nd, int w, u64 mask, const DPrime& P, u64& r0,
+  // The nd digit values of one ciphertext (issued together, before any arithmetic).
+  __device__ __forceinline__ static void fetch(const u64* eb, size_t EN, int nd, u64 (&xv)[ND]) {
+#pragma unroll
+    for (int d = 0; d < ND; d++) xv[d] = d < nd ? eb[(size_t)d * EN] : 0;
+  }
+  // (r0, r1) = sum_d xv[d] * (k0[d], k1[d]) mod q, plain residues.
+  __device__ __forceinline__ void ip(const u64 (&xv)[ND], int nd, int w, u64 mask, const DPrime& P, u64& r0,
                                      u64& r1) const {
     if (w) {
       u64 a00 = 0, a01 = 0, a11 = 0, c00 = 0, c01 = 0, c11 = 0;
 #pragma unroll
       for (int d = 0; d < ND; d++) {
         if (d < nd) {
-          const u64 x = eb[(size_t)d * EN];
+          const u64 x = xv[d];
           const uint32_t x0 = (uint32_t)(x & mask), x1 = (uint32_t)(x >> w);
           smac(a00, a01, a11, x0, x1, k0[d]);
           smac(c00, c01, c11, x0, x1, k1[d]);
@@ -346,7 +351,7 @@ struct KeyRegs {
 #pragma unroll
       for (int d = 0; d < ND; d++) {
         if (d < nd) {
-          const u64 x = eb[(size_t)d * EN];
+          const u64 x = xv[d];
           mac(lo0, hi0, x, k0[d]);
           mac(lo1, hi1, x, k1[d]);
           if (hi0 >= P.q) hi0 -= P.q;
@@ -393,9 +398,30 @@ __global__ void __launch_bounds__(256) k_key_ip(const u64* __restrict__ ext, siz
   const u64* c0 = with_c0 ? add_c0 + ((size_t)i << logN) + ks : nullptr;
   const u64* ex = ext + (size_t)r * ext_r + ((size_t)i << logN) + ks;
   u64* o = acc + (size_t)r * 2 * nb * EN + ((size_t)i << logN) + k;
-  for (int b = 0; b < nb; b++) {
+  // two ciphertexts per iteration: all their loads are issued before the arithmetic
+  int b = 0;
+  for (; b + 1 < nb; b += 2) {
+    u64 xa[ND], xb[ND];
+    KeyRegs<ND>::fetch(ex + (size_t)b * nd * EN, EN, nd, xa);
+    KeyRegs<ND>::fetch(ex + (size_t)(b + 1) * nd * EN, EN, nd, xb);
+    const u64 ca = with_c0 ? c0[(size_t)b * add_b] : 0, cb = with_c0 ? c0[(size_t)(b + 1) * add_b] : 0;
+    u64 r0, r1, s0, s1;
+    kr.ip(xa, nd, w, mask, P, r0, r1);
+    kr.ip(xb, nd, w, mask, P, s0, s1);
+    if (with_c0) {
+      r0 = addmod(r0, shoup(ca, pm, pms, P.q), P.q);
+      s0 = addmod(s0, shoup(cb, pm, pms, P.q), P.q);
+    }
+    o[(size_t)b * 2 * EN] = r0;
+    o[(size_t)b * 2 * EN + EN] = r1;
+    o[(size_t)(b + 1) * 2 * EN] = s0;
+    o[(size_t)(b + 1) * 2 * EN + EN] = s1;
+  }
+  if (b < nb) {
+    u64 xa[ND];
+    KeyRegs<ND>::fetch(ex + (size_t)b * nd * EN, EN, nd, xa);
     u64 r0, r1;
-    kr.ip(ex + (size_t)b * nd * EN, EN, nd, w, mask, P, r0, r1);
+    kr.ip(xa, nd, w, mask, P, r0, r1);
     if (with_c0) r0 = addmod(r0, shoup(c0[(size_t)b * add_b], pm, pms, P.q), P.q);
     o[(size_t)b * 2 * EN] = r0;
     o[(size_t)b * 2 * EN + EN] = r1;
@@ -464,12 +490,32 @@ __global__ void __launch_bounds__(256) k_key_ip_acc(const u64* __restrict__ ext,
     kr.load(rl.key[r], nd, pi, LK, N, k, w, mask);
     const u64* ex = ext + (size_t)r * ext_r + ((size_t)i << logN) + ks;
     const u64* ad = add + (size_t)r * add_r + ((size_t)i << logN) + ks;
-    for (int b = b0; b < b1; b++) {
+    // two ciphertexts per iteration: all their loads are issued before the arithmetic
+    int b = b0;
+    for (; b + 1 < b1; b += 2) {
+      u64 xa[ND], xb[ND];
+      KeyRegs<ND>::fetch(ex + (size_t)b * nd * EN, EN, nd, xa);
+      KeyRegs<ND>::fetch(ex + (size_t)(b + 1) * nd * EN, EN, nd, xb);
+      u64* sa = S + (size_t)b * s_b + idx;
+      u64* sb = S + (size_t)(b + 1) * s_b + idx;
+      const u64 aa = ad[(size_t)b * add_b], ab = ad[(size_t)(b + 1) * add_b];
+      const u64 sa0 = sa[0], sa1 = sa[EN], sb0 = sb[0], sb1 = sb[EN];
+      u64 r0, r1, q0, q1;
+      kr.ip(xa, nd, w, mask, P, r0, r1);
+      kr.ip(xb, nd, w, mask, P, q0, q1);
+      sa[0] = addmod(sa0, addmod(r0, aa, P.q), P.q);
+      sa[EN] = addmod(sa1, r1, P.q);
+      sb[0] = addmod(sb0, addmod(q0, ab, P.q), P.q);
+      sb[EN] = addmod(sb1, q1, P.q);
+    }
+    if (b < b1) {
+      u64 xa[ND];
+      KeyRegs<ND>::fetch(ex + (size_t)b * nd * EN, EN, nd, xa);
       u64 r0, r1;
-      kr.ip(ex + (size_t)b * nd * EN, EN, nd, w, mask, P, r0, r1);
-      u64* sb = S + (size_t)b * s_b + idx;
-      sb[0] = addmod(sb[0], addmod(r0, ad[(size_t)b * add_b], P.q), P.q);
-      sb[EN] = addmod(sb[EN], r1, P.q);
+      kr.ip(xa, nd, w, mask, P, r0, r1);
+      u64* sa = S + (size_t)b * s_b + idx;
+      sa[0] = addmod(sa[0], addmod(r0, ad[(size_t)b * add_b], P.q), P.q);
+      sa[EN] = addmod(sa[EN], r1, P.q);
     }
   }
 }
@@ -559,6 +605,10 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
+// The baby steps are taken in chunks of T1 = min(t1, 32) (registers); a chunk after the
+// first adds its partial sums to the ones the same thread stored for the chunk before
+// (that value is requested before the chunk's products, so its latency is covered).
+// A block has one warp per (ciphertext, poly) pair, up to 8.
 template <int T1>
 __global__ void __launch_bounds__(256) k_bsgs(const u64* __restrict__ baby, const u64* __restrict__ diag,
                                               size_t diag_stride, u64* __restrict__ inner,
@@ -566,20 +616,24 @@ __global__ void __launch_bounds__(256) k_bsgs(const u64* __restrict__ baby, cons
                                               int limbs, int lvl, int L) {
   __shared__ __align__(16) u64 Ds[2][T1][32];
   const size_t LN = (size_t)limbs << logN;
+  const size_t chunk = blockIdx.y + (size_t)blockIdx.z * gridDim.y;
+  if (chunk >= (LN >> 5)) return;  // whole block
   const int bp_count = nb * 2;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int bp = blockIdx.x * 8 + warp;
-  const size_t c0 = (size_t)blockIdx.y * 32;  // first coefficient index in [0, limbs*N)
+  const int bp = blockIdx.x * (blockDim.x >> 5) + warp;
+  const size_t c0 = chunk * 32;  // first coefficient index in [0, limbs*N)
   const size_t cidx = c0 + lane;
   const int i = (int)(c0 >> logN);
   const DPrime P = pr[i < lvl ? i : L + (i - lvl)];
   const int w = (int)P.split;
   const bool active = bp < bp_count;
   const size_t bstride = (size_t)bp_count * LN;  // stride between baby steps j
-  // diag[k*t1 + j][c0 .. c0+32) for j < t1 -> Ds[buf]: t1 rows of 16 16-byte pieces
-  auto stage = [&](int k, int buf) {
-    const u64* dk = diag + (size_t)(k * t1) * diag_stride + c0;
-    for (int e = threadIdx.x; e < t1 * 16; e += blockDim.x) {
+  const int n_chunks = t1 / T1;
+  // step s = (chunk jc, giant step k): diag[k*t1 + jc*T1 + j][c0 .. c0+32), j < T1 -> Ds[buf]
+  auto stage = [&](int s_, int buf) {
+    const int jc = s_ / t2, k = s_ % t2;
+    const u64* dk = diag + (size_t)(k * t1 + jc * T1) * diag_stride + c0;
+    for (int e = threadIdx.x; e < T1 * 16; e += blockDim.x) {
       const int row = e >> 4, col = (e & 15) * 2;
       cp_async16(&Ds[buf][row][col], dk + (size_t)row * diag_stride + col);
     }
@@ -587,37 +641,42 @@ __global__ void __launch_bounds__(256) k_bsgs(const u64* __restrict__ baby, cons
   };
   stage(0, 0);
   u64 x[T1];
+  const int n_steps = n_chunks * t2;
+  const u64* xb = baby + (size_t)bp * LN + cidx;
+  u64* ob = inner + (size_t)bp * LN + cidx;
+  for (int s_ = 0; s_ < n_steps; s_++) {
+    const int jc = s_ / t2, k = s_ % t2;
+    if (k == 0) {  // this chunk's baby-step values, split into w-bit halves
 #pragma unroll
-  for (int j = 0; j < T1; j++)
-    x[j] = (active && j < t1) ? baby[(size_t)j * bstride + (size_t)bp * LN + cidx] : 0;
-  if (w) {
-    const u64 mask = (1ull << w) - 1;
+      for (int j = 0; j < T1; j++) x[j] = active ? xb[(size_t)(jc * T1 + j) * bstride] : 0;
+      if (w) {
+        const u64 mask = (1ull << w) - 1;
 #pragma unroll
-    for (int j = 0; j < T1; j++) x[j] = ((x[j] >> w) << 32) | (x[j] & mask);
-  }
-  for (int k = 0; k < t2; k++) {
-    cp_async_wait_all();  // tile k has landed (the only group in flight)
-    __syncthreads();      // ... for every thread, and every warp is done with tile k-1
-    if (k + 1 < t2) stage(k + 1, (k + 1) & 1);
-    const u64(*D)[32] = Ds[k & 1];
-    u64 res = 0;
+        for (int j = 0; j < T1; j++) x[j] = ((x[j] >> w) << 32) | (x[j] & mask);
+      }
+    }
+    u64* o = ob + (size_t)k * bstride;
+    const u64 prev = (active && jc > 0) ? *o : 0;
+    cp_async_wait_all();  // tile s has landed (the only group in flight)
+    __syncthreads();      // ... for every thread, and every warp is done with tile s-1
+    if (s_ + 1 < n_steps) stage(s_ + 1, (s_ + 1) & 1);
+    const u64(*D)[32] = Ds[s_ & 1];
+    u64 res;
     if (w) {
       // two accumulators for the middle term keep the dependent chains short
       u64 a00 = 0, a01 = 0, a10 = 0, a11 = 0;
 #pragma unroll
       for (int j = 0; j < T1; j++) {
-        if (j < t1) {
-          const u64 d = D[j][lane];
-          const uint32_t d0 = (uint32_t)d, d1 = (uint32_t)(d >> 32);
-          const uint32_t x0 = (uint32_t)x[j], x1 = (uint32_t)(x[j] >> 32);
-          a00 += (u64)x0 * d0;
-          a01 += (u64)x0 * d1;
-          a10 += (u64)x1 * d0;
-          a11 += (u64)x1 * d1;
-        }
+        const u64 d = D[j][lane];
+        const uint32_t d0 = (uint32_t)d, d1 = (uint32_t)(d >> 32);
+        const uint32_t x0 = (uint32_t)x[j], x1 = (uint32_t)(x[j] >> 32);
+        a00 += (u64)x0 * d0;
+        a01 += (u64)x0 * d1;
+        a10 += (u64)x1 * d0;
+        a11 += (u64)x1 * d1;
       }
       // S = a11 * 2^(2w) + (a01 + a10) * 2^w + a00 as a 128-bit (hi, lo); a01 + a10 < 2^64
-      // because each is below t1 * 2^(2w) and 2 * t1 * 2^(2w) < 2^64
+      // because each is below T1 * 2^(2w) and 2 * T1 * 2^(2w) < 2^64 (T1 <= 32, w <= 27)
       const u64 m = a01 + a10;
       u64 lo = a00, hi = 0;
       const u64 t_lo = m << w, t_hi = m >> (64 - w);
@@ -631,39 +690,41 @@ __global__ void __launch_bounds__(256) k_bsgs(const u64* __restrict__ baby, cons
       u64 lo = 0, hi = 0;
 #pragma unroll
       for (int j = 0; j < T1; j++) {
-        if (j < t1) {
-          mac(lo, hi, x[j], D[j][lane]);
-          if (hi >= P.q) hi -= P.q;
-        }
+        mac(lo, hi, x[j], D[j][lane]);
+        if (hi >= P.q) hi -= P.q;
       }
       res = redc(hi, lo, P.q, P.qinv);
     }
-    if (active) inner[(size_t)k * bstride + (size_t)bp * LN + cidx] = res;
+    if (active) *o = jc == 0 ? res : addmod(prev, res, P.q);
   }
 }
 
 void launch_bsgs_inner(ctl_context* c, const u64* baby, const u64* diag, size_t diag_stride, u64* inner, int t1,
                        int t2, int nb, int limbs, int lvl) {
   const size_t LN = (size_t)limbs * c->N;
-  dim3 grid((unsigned)((nb * 2 + 7) / 8), (unsigned)(LN / 32));
+  const size_t chunks = LN / 32;
+  const unsigned gy = (unsigned)std::min<size_t>(chunks, 65535);
+  const int wpb = std::min(8, nb * 2);  // warps (ciphertext polys) per block
+  dim3 grid((unsigned)((nb * 2 + wpb - 1) / wpb), gy, (unsigned)((chunks + gy - 1) / gy));
   double work = (double)t1 * t2 * nb * 2 * LN;
 #define CTL_BSGS_CASE(TT)                                                                                      \
   case TT:                                                                                                     \
     CTL_LAUNCH(KC_BSGS, work, grid,                                                                            \
-               (k_bsgs<TT><<<grid, 256, 0, c->stream>>>(baby, diag, diag_stride, inner, c->d_primes,           \
-                                                        (int)c->logN, t1, t2, nb, limbs, lvl, (int)c->L)));    \
+               (k_bsgs<TT><<<grid, 32 * wpb, 0, c->stream>>>(baby, diag, diag_stride, inner, c->d_primes,      \
+                                                             (int)c->logN, t1, t2, nb, limbs, lvl,             \
+                                                             (int)c->L)));                                     \
     break;
+  // T1 = min(t1, 32); t1 is a power of two, so T1 divides it
   int T1 = 1;
-  while (T1 < t1) T1 <<= 1;
+  while (T1 < t1 && T1 < 32) T1 <<= 1;
   switch (T1) {
     CTL_BSGS_CASE(1)
     CTL_BSGS_CASE(2)
     CTL_BSGS_CASE(4)
     CTL_BSGS_CASE(8)
     CTL_BSGS_CASE(16)
-    CTL_BSGS_CASE(32)
     default:
-      CTL_BSGS_CASE(64)
+      CTL_BSGS_CASE(32)
   }
 #undef CTL_BSGS_CASE
 }

@@ -392,6 +392,15 @@ def test_dense_bsgs_matches_fp64_and_op_counts(m, n, composed):
     assert np.max(np.abs(y[m:])) < 1e-6  # outputs outside [0, m) stay zero
 
 
+def test_bsgs_split_minimises_rotation_cost():
+    # t = t1 * t2 (Eq. bsgs); the split is the power of two that minimises
+    # (t1 - 1) + 4 (t2 - 1), ties to the larger t1, found here by brute force.
+    for lg in range(0, 13):
+        t = 1 << lg
+        best = min(((1 << a) for a in range(lg + 1)), key=lambda a: ((a - 1) + 4 * (t // a - 1), -a))
+        assert O.Oracle.bsgs_t1(t) == best, t
+
+
 def test_dense_equals_direct_diagonal_method():
     # The diagonal method without baby-step/giant-step (t rotations) decodes to the same.
     N, m, n = 128, 8, 8
@@ -463,8 +472,12 @@ def test_small_network_matches_fp64():
     """dense(16->8) -> x^2 -> replicate -> dense(8->4), the layer pattern of the paper's
     frozen stack with the square activation, decoded within 1e-4 of FP64."""
     N = 256
-    r1 = list(range(1, 4)) + [4, 8, 12]
-    r2 = [1, 2, 3, 4] + [-8]
+    def bsgs_rots(m, n):
+        t = O.Oracle.bsgs_t(m, n)
+        t1 = O.Oracle.bsgs_t1(t)
+        return list(range(1, t1)) + [k * t1 for k in range(1, t // t1)]
+    r1 = bsgs_rots(8, 16)
+    r2 = bsgs_rots(4, 8) + [-8]
     o = O.Oracle(N, [60, 40, 40, 40], [60], scale=2.0 ** 40)
     o.keygen(sorted(set(r1 + r2)), seed=3)
     rng = np.random.default_rng(18)
