@@ -37,6 +37,9 @@ SM_COUNT = 152
 IMAD_PER_CLK_SM = 64          # 32-bit integer multiply-add lanes per SM per clock
 SHOUP_IMAD = 17.4             # IMAD issue slots of one 64-bit Shoup modmul (microbenchmark)
 MAX_SM_MHZ = 2070.0
+# one split-half multiply-accumulate (four 32x32->64 IMAD.WIDE, each two IMAD issue slots)
+SPLIT_MAC_IMAD = 8.0
+MAC_CLASSES = ("key_ip", "bsgs_inner")  # kernel classes whose work unit is a split-half MAC
 
 WORKLOADS = {
     "batched": dict(N=16384, q=[45] * 8, p=[60, 60], dnum=4, batch=256, dims=[1024, 256, 256, 64],
@@ -391,6 +394,8 @@ def main():
     ap.add_argument("--max-batch", type=int, default=64)
     ap.add_argument("--mem-budget-gb", type=float, default=160.0)
     ap.add_argument("--queries", type=int, default=1024)
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the extra measurement of the lazy-ModDown dense form")
     args = ap.parse_args()
     if args.workload in ("serving", "uneven"):
         import torch
@@ -539,22 +544,64 @@ def main():
         e2e = {"value": world * B * args.steps / e2e_s, "unit": "forwards/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(out_words * 8)}
 
-    # roofline of the dominant kernel class (integer-multiply bound)
-    mhz = clocks["sm_mhz"] or MAX_SM_MHZ
+    # the same workload with the dense layers in the lazy-ModDown form (a different, equally
+    # valid ciphertext; its own BSGS split and Galois keys): reported beside, not as, the value
+    variants = None
+    if not args.no_variants and world == 1:
+        ctx.set_dense_mode(ctx.DENSE_LAZY_MODDOWN)
+        model_l = ctl.Model(ctx, layers)
+        keys_l = ctx.keygen(model_l.rotations(), seed=3)  # same secret (same seed)
+        o = model_l.forward(keys_l, batch)
+        err_l = 0.0
+        for i in check_idx:
+            yi = ctx.decrypt(keys_l, o.slice(i), wl["dims"][-1])
+            err_l = max(err_l, float(np.max(np.abs(yi - fp64_forward(Ws, xs[i], square_last)))))
+        o.close()
+        for _ in range(2):
+            model_l.forward(keys_l, batch, graph=use_graph).close()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            model_l.forward(keys_l, batch, graph=use_graph).close()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_l = e0.elapsed_time(e1)
+        variants = {"lazy_moddown": {
+            "value": B * args.steps / (ms_l / 1e3), "unit": "forwards/s", "ms_per_step": ms_l / args.steps,
+            "max_abs_err_vs_fp64": err_l, "rotations_per_forward": len(model_l.rotations()),
+            "desc": "ctl_set_dense_mode(CTL_DENSE_LAZY_MODDOWN): rotations kept in the extended basis, "
+                    "ModDown once per giant step and once per layer, t1 = min(t, 2^ceil(log2(4t)/2))"}}
+        model_l.close()
+        keys_l.close()
+        ctx.set_dense_mode(ctx.DENSE_COMPOSED)
+
+    # roofline of the dominant kernel class (integer-multiply bound): NTT-type classes count
+    # Shoup modmuls (butterflies + conversions), key_ip and bsgs_inner count split-half MACs
     peak_modmul = SM_COUNT * IMAD_PER_CLK_SM * MAX_SM_MHZ * 1e6 / SHOUP_IMAD
+    peak_mac = SM_COUNT * IMAD_PER_CLK_SM * MAX_SM_MHZ * 1e6 / SPLIT_MAC_IMAD
     classes = {k: v for k, v in kern.items() if v["launches"]}
     dom = max(classes, key=lambda k: classes[k]["ms"])
     d = classes[dom]
-    achieved = d["modmul"] / (d["ms"] / 1e3) if d["ms"] else 0.0
+
+    def unit_peak(k):
+        return ("Gmac/s", peak_mac) if k in MAC_CLASSES else ("Gmodmul/s", peak_modmul)
+
+    def rate(v):
+        return v["modmul"] / (v["ms"] / 1e3) if v["ms"] else 0.0
+
     per_class = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
                      "share": v["ms"] / max(sum(x["ms"] for x in classes.values()), 1e-9),
-                     "gmodmul_s": (v["modmul"] / (v["ms"] / 1e3) / 1e9) if v["ms"] else 0.0,
-                     "frac_of_alu_peak": (v["modmul"] / (v["ms"] / 1e3) / peak_modmul) if v["ms"] else 0.0}
+                     "rate": rate(v) / 1e9, "unit": unit_peak(k)[0], "peak": unit_peak(k)[1] / 1e9,
+                     "frac_of_alu_peak": rate(v) / unit_peak(k)[1]}
                  for k, v in classes.items()}
-    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved / 1e9, "peak": peak_modmul / 1e9,
-                "unit": "Gmodmul/s", "frac": achieved / peak_modmul, "traffic": None,
-                "peak_basis": f"{SM_COUNT} SMs x {IMAD_PER_CLK_SM} IMAD/clk x {MAX_SM_MHZ:.0f} MHz / "
-                              f"{SHOUP_IMAD} IMAD per Shoup modmul (measured)",
+    unit, peak = unit_peak(dom)
+    achieved = rate(d)
+    basis = (f"{SM_COUNT} SMs x {IMAD_PER_CLK_SM} IMAD/clk x {MAX_SM_MHZ:.0f} MHz / " +
+             (f"{SPLIT_MAC_IMAD:.0f} IMAD slots per split-half MAC" if dom in MAC_CLASSES
+              else f"{SHOUP_IMAD} IMAD per Shoup modmul (measured)"))
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved / 1e9, "peak": peak / 1e9,
+                "unit": unit, "frac": achieved / peak, "traffic": None, "peak_basis": basis,
                 "avg_launch_ms": d["ms"] / max(d["launches"], 1), "classes": per_class,
                 "timing": timing_source}
 
@@ -577,7 +624,7 @@ def main():
                                "per": f"batch of {B}"},
                 "ops_per_step": {k: v / args.steps for k, v in ops.items()},
                 "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
-                "gpu_launches": int(launches)}
+                "gpu_launches": int(launches), "variants": variants}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

@@ -91,6 +91,19 @@ int ctl_set_stream(ctl_context* ctx, void* stream);
 int ctl_set_allocator(ctl_context* ctx, ctl_alloc_fn alloc_fn, ctl_free_fn free_fn, void* user);
 /* Blocks until the context stream is idle. */
 int ctl_synchronize(ctl_context* ctx);
+/* How later dense layers (ctl_eval_dense*, ctl_model_create) evaluate Eq. (bsgs):
+ *   CTL_DENSE_COMPOSED (default): the composition of whole rotations, each ending with
+ *     its ModDown, the baby steps sharing one ModUp; t1 = 2^ceil(log2(t)/2).  Bit-identical
+ *     to composing ctl_rotate, ctl_mul_plain_coeffs, ctl_add and ctl_rescale.
+ *   CTL_DENSE_LAZY_MODDOWN: rotations kept in the extended basis Q*P, ModDown once per
+ *     giant step (on c1) and once at the end; t1 = min(t, 2^ceil(log2(4t)/2)).  A
+ *     different ciphertext of the same values (lower noise), not bit-identical to the
+ *     default; needs the Galois keys of its own split.
+ * The paper fixes neither choice (Sec. 3.1 only fixes t = t1 * t2 and the hoisting).  A
+ * model keeps the mode it was created with.  Errors: CTL_EINVAL (unknown mode). */
+#define CTL_DENSE_COMPOSED 0
+#define CTL_DENSE_LAZY_MODDOWN 1
+int ctl_set_dense_mode(ctl_context* ctx, int mode);
 
 /* ---------------------------------------------------------------------------------
  * Keys (Fig. alg:cryptotl: the client's key pair; Sec. 3.1 rotations need Galois keys).

@@ -769,12 +769,13 @@ int orc_square(const orc_ctx* c, const orc_keys* k, const u64* ct, uint32_t lvl,
 }
 
 // Baby-step giant-step sizes (Eq. bsgs): t is the next power of two >= max(m, n) (the
-// paper pads non-square matrices with zeros) and t = t1 * t2.  The paper leaves the
-// split open; it is taken as t1 = min(t, 2^ceil(log2(4t)/2)), the power of two nearest
-// sqrt(4t), which minimises (t1 - 1) + 4 (t2 - 1): with the ModDowns postponed a giant
-// step costs about four baby steps.
+// paper pads non-square matrices with zeros) and t = t1 * t2 with t1 = 2^ceil(log2(t)/2).
 uint32_t orc_bsgs_t(uint32_t m, uint32_t n) { uint32_t t = 1; while (t < m || t < n) t <<= 1; return t; }
-uint32_t orc_bsgs_t1(uint32_t t) {
+uint32_t orc_bsgs_t1(uint32_t t) { uint32_t lg = 0; while ((1u << lg) < t) lg++; return 1u << ((lg + 1) / 2); }
+// The split of the lazy-ModDown form (orc_dense_lazy): there a baby step is one key
+// product and a giant step a whole key switch (about four baby steps), so
+// t1 = min(t, 2^ceil(log2(4t)/2)), which minimises (t1 - 1) + 4 (t2 - 1).
+uint32_t orc_bsgs_t1_lazy(uint32_t t) {
   uint32_t lg = 0;
   while ((1u << lg) < t) lg++;
   uint32_t t1 = 1u << ((lg + 3) / 2);
@@ -784,8 +785,11 @@ uint32_t orc_bsgs_t1(uint32_t t) {
 // Diagonal plaintexts of a dense layer W (m x n, row-major) for Eq. (bsgs):
 // diag_i[r] = W[r][(r+i) mod t] (zero outside W), diag'_i = rot_{-floor(i/t1)*t1}(diag_i)
 // with diag_i placed in slots [0, t) of the full slot vector, encoded at `scale`.
-int orc_encode_diagonals(const orc_ctx* c, const double* W, uint32_t m, uint32_t n, double scale, i64* pts) {
-  uint32_t t = orc_bsgs_t(m, n), t1 = orc_bsgs_t1(t), ns = c->N / 2;
+// t1 = 0 takes orc_bsgs_t1(t).
+int orc_encode_diagonals(const orc_ctx* c, const double* W, uint32_t m, uint32_t n, uint32_t t1, double scale,
+                         i64* pts) {
+  uint32_t t = orc_bsgs_t(m, n), ns = c->N / 2;
+  if (!t1) t1 = orc_bsgs_t1(t);
   if (2 * t > ns) return -1;
   std::vector<double> v(ns);
   for (uint32_t i = 0; i < t; i++) {
@@ -802,14 +806,14 @@ int orc_encode_diagonals(const orc_ctx* c, const double* W, uint32_t m, uint32_t
   return 0;
 }
 
-// Dense layer by Eq. (bsgs) on an input laid out as [x, x] over 2t slots, as a plain
-// composition of whole rotations:
+// Dense layer by Eq. (bsgs) on an input laid out as [x, x] over 2t slots, as the plain
+// composition of whole rotations (each one ModUp -> sigma_g -> key product -> ModDown,
+// the baby steps sharing one ModUp):
 //   out = sum_k rot_{k t1}( sum_j diag'_{k t1 + j} o rot_j(ct) ),
 // inner sums in increasing j, outer in increasing k, then an optional plaintext bias
 // (added to c0) and a rescale.  counters[0..2] receive the rotations, plaintext
-// products and additions performed (t1+t2-2, t, t-1).  Decodes to the same values as
-// orc_dense within the noise; kept as the textbook form that orc_dense is pinned to.
-int orc_dense_composed(const orc_ctx* c, const orc_keys* k, const u64* ct, uint32_t lvl, const i64* pts, uint32_t t,
+// products and additions performed (t1+t2-2, t, t-1).
+int orc_dense(const orc_ctx* c, const orc_keys* k, const u64* ct, uint32_t lvl, const i64* pts, uint32_t t,
               const i64* bias, u64* out, u64* counters) {
   uint32_t N = c->N, t1 = orc_bsgs_t1(t), t2 = t / t1;
   size_t csz = (size_t)2 * lvl * N;
@@ -835,20 +839,20 @@ int orc_dense_composed(const orc_ctx* c, const orc_keys* k, const u64* ct, uint3
 }
 
 // Dense layer by Eq. (bsgs) with every ModDown of the baby and giant steps postponed
-// (the rotations are key switches in the extended basis Q*P; the paper fixes the
-// linear algebra and the hoisting of the baby steps, not where the division by P
-// happens).  With E = lvl + K limbs (data primes, then special primes) and P the
-// special modulus:
+// (an alternative to orc_dense, not bit-identical to it: the rotations are key switches
+// kept in the extended basis Q*P, and the division by P happens once per giant step
+// and once at the end).  With E = lvl + K limbs (data primes, then special primes),
+// P the special modulus and t1 = orc_bsgs_t1_lazy(t):
 //   B_0 = (P*c0, P*c1) (zero on the special limbs),
 //   B_j = (P*sigma_j(c0) + a_0, a_1), (a_0, a_1) = key product of c1 for rot_j, j >= 1,
 //   I_k = sum_j diag'_{k t1 + j} o B_j over all E limbs (diagonals reduced mod every prime),
 //   S   = I_0 + sum_{k >= 1} ( sigma_{k t1}(I_k.0) + b_0, b_1 ),
 //         (b_0, b_1) = key product of ModDown(I_k.1) for rot_{k t1},
 //   out = rescale( (ModDown(S.0), ModDown(S.1)) [+ bias on c0] ).
-// The sums run in increasing j and k.  counters as for orc_dense_composed.
-int orc_dense(const orc_ctx* c, const orc_keys* k, const u64* ct, uint32_t lvl, const i64* pts, uint32_t t,
-              const i64* bias, u64* out, u64* counters) {
-  uint32_t N = c->N, K = c->K, L = c->L, E = lvl + K, t1 = orc_bsgs_t1(t), t2 = t / t1;
+// The sums run in increasing j and k.  counters as for orc_dense.
+int orc_dense_lazy(const orc_ctx* c, const orc_keys* k, const u64* ct, uint32_t lvl, const i64* pts, uint32_t t,
+                   const i64* bias, u64* out, u64* counters) {
+  uint32_t N = c->N, K = c->K, L = c->L, E = lvl + K, t1 = orc_bsgs_t1_lazy(t), t2 = t / t1;
   auto prime = [&](uint32_t i) { return c->mods[i < lvl ? i : L + (i - lvl)]; };
   const size_t ew = (size_t)E * N;  // one polynomial in the extended basis
   std::vector<u64> B((size_t)t1 * 2 * ew, 0), S(2 * ew), Ik(2 * ew), pr(N), prod(N), tmp(N), c1d((size_t)lvl * N);

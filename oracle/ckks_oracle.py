@@ -61,9 +61,10 @@ def _lib():
             "orc_square": (C.c_int, [vp, vp, _u64p, C.c_uint32, _u64p]),
             "orc_bsgs_t": (C.c_uint32, [C.c_uint32, C.c_uint32]),
             "orc_bsgs_t1": (C.c_uint32, [C.c_uint32]),
-            "orc_encode_diagonals": (C.c_int, [vp, _dp, C.c_uint32, C.c_uint32, C.c_double, _i64p]),
+            "orc_bsgs_t1_lazy": (C.c_uint32, [C.c_uint32]),
+            "orc_encode_diagonals": (C.c_int, [vp, _dp, C.c_uint32, C.c_uint32, C.c_uint32, C.c_double, _i64p]),
             "orc_dense": (C.c_int, [vp, vp, _u64p, C.c_uint32, _i64p, C.c_uint32, _i64p, _u64p, _u64p]),
-            "orc_dense_composed": (C.c_int, [vp, vp, _u64p, C.c_uint32, _i64p, C.c_uint32, _i64p, _u64p, _u64p]),
+            "orc_dense_lazy": (C.c_int, [vp, vp, _u64p, C.c_uint32, _i64p, C.c_uint32, _i64p, _u64p, _u64p]),
             "orc_replicate": (C.c_int, [vp, vp, _u64p, C.c_uint32, C.c_uint32, _u64p]),
         }
         for name, (res, args) in sig.items():
@@ -277,25 +278,34 @@ class Oracle:
         return int(_lib().orc_bsgs_t(m, n))
 
     @staticmethod
-    def bsgs_t1(t):
-        return int(_lib().orc_bsgs_t1(t))
+    def bsgs_t1(t, lazy=False):
+        return int(_lib().orc_bsgs_t1_lazy(t) if lazy else _lib().orc_bsgs_t1(t))
 
-    def encode_diagonals(self, W, scale):
+    @classmethod
+    def bsgs_rotations(cls, m, n, lazy=False):
+        """Galois rotations a dense layer m x n needs: 1..t1-1 and k*t1 for k = 1..t2-1."""
+        t = cls.bsgs_t(m, n)
+        t1 = cls.bsgs_t1(t, lazy)
+        return list(range(1, t1)) + [k * t1 for k in range(1, t // t1)]
+
+    def encode_diagonals(self, W, scale, lazy=False):
         W = np.ascontiguousarray(W, dtype=np.float64)
         m, n = W.shape
         t = self.bsgs_t(m, n)
         out = np.zeros((t, self.N), dtype=np.int64)
-        _chk(self.lib.orc_encode_diagonals(self.h, _p(W, _dp), m, n, scale, _p(out, _i64p)), "encode_diagonals")
+        _chk(self.lib.orc_encode_diagonals(self.h, _p(W, _dp), m, n, self.bsgs_t1(t, lazy), scale, _p(out, _i64p)),
+             "encode_diagonals")
         return out
 
-    def dense(self, ct, pts, bias=None, composed=False):
-        """Dense layer by Eq. (bsgs); composed=True takes the plain composition of whole
-        rotations instead of the lazy-ModDown form (same decoded values within noise)."""
+    def dense(self, ct, pts, bias=None, lazy=False):
+        """Dense layer by Eq. (bsgs) as the composition of whole rotations; lazy=True takes
+        the lazy-ModDown form instead (its own split and diagonals; decodes to the same
+        values within the noise)."""
         ct = _u64(ct); pts = _i64(pts); lvl = ct.shape[1]
         out = np.zeros((2, lvl - 1, self.N), dtype=np.uint64)
         cnt = np.zeros(3, dtype=np.uint64)
         bp = _p(_i64(bias), _i64p) if bias is not None else None
-        fn = self.lib.orc_dense_composed if composed else self.lib.orc_dense
+        fn = self.lib.orc_dense_lazy if lazy else self.lib.orc_dense
         _chk(fn(self.h, self.keys, _p(ct, _u64p), lvl, _p(pts, _i64p), pts.shape[0], bp,
                 _p(out, _u64p), _p(cnt, _u64p)), "dense")
         return out, [int(x) for x in cnt]
@@ -306,10 +316,11 @@ class Oracle:
         return out
 
     # --- composite helpers (scale bookkeeping of the oracle's reading) -----------
-    def dense_scale(self, lvl, in_scale):
-        """Plaintext scale for a dense layer applied at level lvl: q_{lvl-1} * Delta / in_scale,
-        so that the rescaled output carries the nominal scale Delta again."""
-        return float(self.moduli[lvl - 1]) * (self.scale / in_scale)
+    def dense_scale(self, lvl, in_scale=None):
+        """Plaintext scale of a dense layer applied at level lvl to an input at in_scale
+        (default Delta): q_{lvl-1} * Delta / in_scale, so that the rescaled output carries
+        the nominal scale Delta again."""
+        return float(self.moduli[lvl - 1]) * (self.scale / (self.scale if in_scale is None else in_scale))
 
     def square_scale(self, lvl, in_scale):
         return in_scale * in_scale / float(self.moduli[lvl - 1])

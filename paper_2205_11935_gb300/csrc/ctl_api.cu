@@ -440,6 +440,7 @@ extern "C" int ctl_context_clone(const ctl_context* c, ctl_context** out) {
   k->d_mu_scale = c->d_mu_scale;
   k->h_primes = c->h_primes;
   k->enc = c->enc;
+  k->dense_mode = c->dense_mode;
   k->parent = c->parent ? c->parent : c;
   if (int rc = cuda_check(cudaStreamCreateWithFlags(&k->stream, cudaStreamNonBlocking), "stream")) return rc;
   k->own_stream = true;
@@ -487,6 +488,15 @@ extern "C" int ctl_set_allocator(ctl_context* c, ctl_alloc_fn a, ctl_free_fn f, 
   c->alloc_fn = a;
   c->free_fn = f;
   c->alloc_user = user;
+  return CTL_OK;
+}
+
+extern "C" int ctl_set_dense_mode(ctl_context* c, int mode) {
+  if (!c || (mode != CTL_DENSE_COMPOSED && mode != CTL_DENSE_LAZY_MODDOWN)) {
+    set_error("ctl_set_dense_mode: invalid argument");
+    return CTL_EINVAL;
+  }
+  c->dense_mode = mode;
   return CTL_OK;
 }
 
@@ -1099,8 +1109,9 @@ extern "C" int ctl_add(ctl_context* c, const ctl_ct* a, const ctl_ct* b, ctl_ct*
 // =====================================================================================
 struct DenseLayer {
   uint32_t m = 0, n = 0, t = 0, t1 = 0, t2 = 0, lvl = 0;
+  bool lazy = false;     // lazy-ModDown form (CTL_DENSE_LAZY_MODDOWN) instead of composed rotations
   double pt_scale = 0, in_scale = 0, out_scale = 0;
-  u64* diag = nullptr;   // [t][lvl+K][N] NTT + Montgomery form (split), extended basis
+  u64* diag = nullptr;   // [t][limbs][N] NTT + Montgomery form (split); limbs = lvl (+K if lazy)
   u64* bias = nullptr;   // [lvl][N] NTT form (plain residues) or null
 };
 
@@ -1111,12 +1122,14 @@ uint32_t bsgs_t(uint32_t m, uint32_t n) {
   while (t < m || t < n) t <<= 1;
   return t;
 }
-// t = t1 * t2 with t1 = min(t, 2^ceil(log2(4t)/2)): a giant step (ModDown of c1, ModUp,
-// key product) costs about four baby steps (a key product in the extended basis), and
-// this split minimises (t1 - 1) + 4 (t2 - 1).
-uint32_t bsgs_t1(uint32_t t) {
+// t = t1 * t2 with t1 = 2^ceil(log2(t)/2).  The lazy-ModDown form takes
+// t1 = min(t, 2^ceil(log2(4t)/2)) instead: there a giant step (ModDown of c1, ModUp, key
+// product) costs about four baby steps (a key product in the extended basis), and this
+// split minimises (t1 - 1) + 4 (t2 - 1).
+uint32_t bsgs_t1(uint32_t t, bool lazy) {
   uint32_t lg = 0;
   while ((1u << lg) < t) lg++;
+  if (!lazy) return 1u << ((lg + 1) / 2);
   const uint32_t t1 = 1u << ((lg + 3) / 2);
   return t1 < t ? t1 : t;
 }
@@ -1148,8 +1161,9 @@ int upload_plaintexts(ctl_context* c, const i64* coeffs, uint32_t cnt, uint32_t 
 
 // Diagonals of W for Eq. (bsgs): diag_i[r] = W[r][(r+i) mod t] (zero padded),
 // diag'_i = rot_{-floor(i/t1)*t1}(diag_i), i.e. diag_i placed at slots [k*t1, k*t1 + t).
-int encode_diagonals(ctl_context* c, const double* W, uint32_t m, uint32_t n, double scale, std::vector<i64>& pts) {
-  const uint32_t t = bsgs_t(m, n), t1 = bsgs_t1(t), ns = c->N / 2;
+int encode_diagonals(ctl_context* c, const double* W, uint32_t m, uint32_t n, uint32_t t1, double scale,
+                     std::vector<i64>& pts) {
+  const uint32_t t = bsgs_t(m, n), ns = c->N / 2;
   pts.assign((size_t)t * c->N, 0);
   std::vector<double> v(ns);
   for (uint32_t i = 0; i < t; i++) {
@@ -1173,7 +1187,8 @@ int dense_prepare(ctl_context* c, DenseLayer& D, const double* W, const double* 
   D.m = m;
   D.n = n;
   D.t = pts_in ? t_given : bsgs_t(m, n);
-  D.t1 = bsgs_t1(D.t);
+  D.lazy = c->dense_mode == CTL_DENSE_LAZY_MODDOWN;
+  D.t1 = bsgs_t1(D.t, D.lazy);
   D.t2 = D.t / D.t1;
   D.lvl = lvl;
   D.in_scale = in_scale;
@@ -1186,17 +1201,18 @@ int dense_prepare(ctl_context* c, DenseLayer& D, const double* W, const double* 
     return CTL_EINVAL;
   }
   const double ql = (double)c->moduli[lvl - 1];
+  // diagonals at q_last * Delta / scale_in: the rescaled output carries Delta again
   D.pt_scale = pt_scale > 0 ? pt_scale : ql * (c->scale / in_scale);
   D.out_scale = pt_scale > 0 ? in_scale * pt_scale / ql : c->scale;
   std::vector<i64> enc;
   const i64* src = (const i64*)pts_in;
   if (!src) {
-    if (int rc = encode_diagonals(c, W, m, n, D.pt_scale, enc)) return rc;
+    if (int rc = encode_diagonals(c, W, m, n, D.t1, D.pt_scale, enc)) return rc;
     src = enc.data();
   }
-  const uint32_t E = lvl + c->K;
-  if (int rc = upload_plaintexts(c, src, D.t, lvl, E, true, &D.diag)) return rc;
-  launch_split_limbs(c, D.diag, (int)D.t, (int)E, (int)lvl);
+  const uint32_t limbs = D.lazy ? lvl + c->K : lvl;
+  if (int rc = upload_plaintexts(c, src, D.t, lvl, limbs, true, &D.diag)) return rc;
+  launch_split_limbs(c, D.diag, (int)D.t, (int)limbs, (int)lvl);
   std::vector<i64> benc;
   const i64* bsrc = (const i64*)bias_in;
   if (!bsrc && bias) {
@@ -1246,13 +1262,13 @@ int rot_list(ctl_context* c, const ctl_keys* k, int64_t r0, int64_t step, int n,
   return CTL_OK;
 }
 
-// Dense layer by Eq. (bsgs) with every ModDown postponed (E = lvl + K limbs):
+// Dense layer by Eq. (bsgs), lazy-ModDown form, every ModDown postponed (E = lvl + K limbs):
 //   baby[0] = P * in, baby[j] = (P * sigma_j(c0) + ip_j.0, ip_j.1)   (one shared ModUp of c1),
 //   inner[k] = sum_j diag'_{k t1 + j} o baby[j]                        (all E limbs),
 //   S = inner[0] + sum_{k >= 1} (sigma_{k t1}(inner[k].0) + ip'_k.0, ip'_k.1),
 //       ip'_k = key product of ModDown(inner[k].1) for rot_{k t1},
 //   out = rescale( ModDown(S) [+ bias] ),  batch nb.
-int dense_apply(ctl_context* c, const ctl_keys* k, const DenseLayer& D, const u64* in, int nb, u64* out) {
+int dense_apply_lazy(ctl_context* c, const ctl_keys* k, const DenseLayer& D, const u64* in, int nb, u64* out) {
   const uint32_t N = c->N, lvl = D.lvl, t1 = D.t1, t2 = D.t2;
   const int E = (int)lvl + (int)c->K;
   const int nd = ((int)lvl + (int)c->alpha - 1) / (int)c->alpha;
@@ -1316,6 +1332,58 @@ int dense_apply(ctl_context* c, const ctl_keys* k, const DenseLayer& D, const u6
   launch_moddown_polys(c, inner.p, EN, 2 * nb, (int)lvl, acc.p, LN);
   if (D.bias) launch_add_plain(c, acc.p, D.bias, nb, (int)lvl, ctw);
   return rescale_into(c, acc.p, nb, (int)lvl, out);
+}
+
+// Dense layer by Eq. (bsgs) as the composition of whole rotations, batch nb:
+//   out = rescale( sum_k rot_{k t1}( sum_j diag'_{k t1 + j} o rot_j(in) ) [+ bias] ),
+// the baby steps sharing one ModUp (hoisted), each rotation ending with its ModDown.
+int dense_apply_composed(ctl_context* c, const ctl_keys* k, const DenseLayer& D, const u64* in, int nb, u64* out) {
+  const uint32_t N = c->N, lvl = D.lvl, t1 = D.t1, t2 = D.t2;
+  const size_t LN = (size_t)lvl * N, ctw = 2 * LN, bw = ctw * nb;
+  DBuf baby(c, bw * t1), inner(c, bw * t2);
+  if (!baby.p || !inner.p) {
+    set_error("dense: allocation failed (batch %d)", nb);
+    return CTL_ENOMEM;
+  }
+  // baby steps rot_j(in), j = 0..t1-1 (hoisted: one ModUp shared by all)
+  std::vector<int64_t> rots;
+  for (uint32_t j = 0; j < t1; j++) rots.push_back(j);
+  if (int rc = rotate_many(c, k, in, nb, (int)lvl, rots, baby.p)) return rc;
+  // inner sums for all giant steps
+  launch_bsgs_inner(c, baby.p, D.diag, LN, inner.p, (int)t1, (int)t2, nb, (int)lvl, (int)lvl);
+  c->op_ptmul += (uint64_t)D.t * nb;
+  c->op_add += (uint64_t)(D.t - 1) * nb;
+  dev_free(c, baby.release());
+  // giant steps: acc = inner[0] + sum_{k >= 1} rot_{k t1}(inner[k]), chunked, each rotation
+  // with its own input; acc is the k = 0 slice of inner
+  u64* acc = inner.p;
+  if (t2 > 1) {
+    const int E = (int)lvl + (int)c->K;
+    const int nd = ((int)lvl + (int)c->alpha - 1) / (int)c->alpha;
+    const size_t per = (size_t)nb * N * sizeof(u64) * ((size_t)2 * E + (size_t)nd * E + 3 * (size_t)lvl);
+    const int chunk = (int)std::min<size_t>(
+        std::min<size_t>(CTL_MAX_ROT, t2 - 1), std::max<size_t>(1, ((size_t)6 << 30) / std::max<size_t>(per, 1)));
+    DBuf rot(c, bw * (size_t)chunk);
+    CHECK_ALLOC(rot);
+    for (uint32_t k0 = 1; k0 < t2; k0 += chunk) {
+      const int nr = (int)std::min<uint32_t>(t2 - k0, (uint32_t)chunk);
+      RotList rl;
+      if (int rc = rot_list(c, k, (int64_t)k0 * t1, t1, nr, rl)) return rc;
+      std::vector<const u64*> keys(rl.key, rl.key + nr);
+      std::vector<u64> gs(rl.g, rl.g + nr);
+      const u64* src = inner.p + (size_t)k0 * bw;
+      int rc = keyswitch(c, nr, nb, (int)lvl, src + LN, bw, ctw, keys, gs, src, bw, ctw, 0, false, rot.p);
+      if (rc) return rc;
+      c->op_rot += (uint64_t)nr * nb;
+      for (int r = 0; r < nr; r++) launch_add(c, acc, rot.p + (size_t)r * bw, acc, nb * 2, (int)lvl, LN, LN, LN);
+    }
+  }
+  if (D.bias) launch_add_plain(c, acc, D.bias, nb, (int)lvl, ctw);
+  return rescale_into(c, acc, nb, (int)lvl, out);
+}
+
+int dense_apply(ctl_context* c, const ctl_keys* k, const DenseLayer& D, const u64* in, int nb, u64* out) {
+  return D.lazy ? dense_apply_lazy(c, k, D, in, nb, out) : dense_apply_composed(c, k, D, in, nb, out);
 }
 
 }  // namespace
@@ -1499,7 +1567,7 @@ extern "C" int ctl_model_create(ctl_context* c, const ctl_layer* layers, uint32_
         M->layers.push_back(P);
         return fail(rc);
       }
-      M->bytes += (uint64_t)P.dense.t * lvl * c->N * 8;
+      M->bytes += (uint64_t)P.dense.t * (P.dense.lazy ? lvl + c->K : lvl) * c->N * 8;
       for (uint32_t j = 1; j < P.dense.t1; j++) rots.push_back((int32_t)j);
       for (uint32_t k = 1; k < P.dense.t2; k++) rots.push_back((int32_t)(k * P.dense.t1));
       sc = P.dense.out_scale;

@@ -171,6 +171,7 @@ struct ctl_context {
   std::atomic<uint64_t> launch_count{0};
   uint64_t op_rot = 0, op_ptmul = 0, op_add = 0, op_relin = 0, op_rescale = 0;
   int ntt_threads_fwd = 0, ntt_threads_inv = 0;  // autotuned block sizes (0: default)
+  int dense_mode = CTL_DENSE_COMPOSED;          // ctl_set_dense_mode
   const ctl_context* parent = nullptr;  // clones share the parent's device tables
 };
 

@@ -49,6 +49,7 @@ SIGNATURES = {
     "ctl_context_info": (C.c_int, [_vp, _u64p, _u32p, _u32p, _u32p]),
     "ctl_set_stream": (C.c_int, [_vp, _vp]),
     "ctl_set_allocator": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "ctl_set_dense_mode": (C.c_int, [_vp, C.c_int]),
     "ctl_synchronize": (C.c_int, [_vp]),
     "ctl_keygen": (C.c_int, [_vp, _i32p, C.c_uint32, C.c_uint64, _pp]),
     "ctl_keys_destroy": (None, [_vp]),
@@ -157,6 +158,13 @@ class Context:
         self.beta = (self.L + self.alpha - 1) // self.alpha
         if stream is not None:
             self.set_stream(stream)
+
+    DENSE_COMPOSED = 0
+    DENSE_LAZY_MODDOWN = 1
+
+    def set_dense_mode(self, mode):
+        """Dense layers created afterwards: DENSE_COMPOSED (default) or DENSE_LAZY_MODDOWN."""
+        _check(lib().ctl_set_dense_mode(self.h, int(mode)))
 
     def set_stream(self, stream_ptr):
         _check(lib().ctl_set_stream(self.h, C.c_void_p(stream_ptr)))

@@ -230,33 +230,44 @@ def dense_case(P, m, n, seed):
     return W, x, t, ct_o
 
 
-@pytest.mark.parametrize("name,m,n", [("a1", 8, 16), ("a1", 5, 12), ("a2", 16, 16), ("c2", 32, 64), ("c2", 3, 1)])
-def test_dense_bit_exact_injected_and_fp64(name, m, n):
+@pytest.mark.parametrize("lazy", [False, True])
+@pytest.mark.parametrize("name,m,n", [("a1", 8, 16), ("a1", 5, 12), ("a2", 16, 16), ("c2", 32, 64), ("c2", 3, 1),
+                                      ("c2", 128, 128)])
+def test_dense_bit_exact_injected_and_fp64(name, m, n, lazy):
     P = pair(name)
-    t = O.Oracle.bsgs_t(m, n)
-    t1 = O.Oracle.bsgs_t1(t)
-    rots = sorted(set(list(range(1, t1)) + [k * t1 for k in range(1, t // t1)]))
+    rots = sorted(set(O.Oracle.bsgs_rotations(m, n, lazy)))
     o = O.Oracle(P.N, *PARAMS[name][1:3], dnum=PARAMS[name][3], scale=2.0 ** 40)
     o.keygen(rots, seed=3)
     g = P.g
     k = g.keygen(rots, seed=3)
     W, x, t, ct_o = dense_case(P, m, n, 70 + m)
     lvl = ct_o.shape[1]
-    sc = o.dense_scale(lvl, o.scale)
-    pts = o.encode_diagonals(W, sc)
-    exp, cnt = o.dense(ct_o, pts)
+    sc = o.dense_scale(lvl)
+    pts = o.encode_diagonals(W, sc, lazy)
+    exp, cnt = o.dense(ct_o, pts, lazy=lazy)
     ct = g.ct_import(ct_o, 2.0 ** 40)
-    g.stats_reset()
-    out = g.dense_coeffs(k, ct, pts, sc)
-    ops = g.stats_ops()
-    assert np.array_equal(out.export()[0], exp)
-    assert ops["rotations"] == cnt[0] and ops["ptmul"] == cnt[1] and ops["add"] == cnt[2]
-    # the library's own diagonal encoding: decoded within tolerance of FP64
-    out2 = g.dense(k, ct, W)
-    y = g.decrypt(k, out2, P.N // 2)
-    assert np.max(np.abs(y[:m] - W @ x)) < TOL
-    assert np.max(np.abs(y[m:])) < TOL
+    g.set_dense_mode(g.DENSE_LAZY_MODDOWN if lazy else g.DENSE_COMPOSED)
+    try:
+        g.stats_reset()
+        out = g.dense_coeffs(k, ct, pts, sc)
+        ops = g.stats_ops()
+        assert np.array_equal(out.export()[0], exp)
+        assert ops["rotations"] == cnt[0] and ops["ptmul"] == cnt[1] and ops["add"] == cnt[2]
+        # the library's own diagonal encoding: decoded within tolerance of FP64, output at Delta
+        out2 = g.dense(k, ct, W)
+        assert out2.info()[2] == 2.0 ** 40
+        y = g.decrypt(k, out2, P.N // 2)
+        assert np.max(np.abs(y[:m] - W @ x)) < TOL
+        assert np.max(np.abs(y[m:])) < TOL
+    finally:
+        g.set_dense_mode(g.DENSE_COMPOSED)
     k.close()
+
+
+def test_dense_mode_argument():
+    P = pair("a1")
+    with pytest.raises(ctl.CtlError):
+        P.g.set_dense_mode(7)
 
 
 @pytest.mark.parametrize("name", list(PARAMS))
@@ -290,13 +301,12 @@ def network_case(N, q_bits, p_bits, dnum, dims, seed=90, sizes_only=False):
     return layers, slots, ref
 
 
-def oracle_forward(o, ct, layers):
-    sc = o.scale
+def oracle_forward(o, ct, layers, lazy=False):
+    sc = o.scale  # a dense layer restores Delta, a square squares the scale over q_last
     for ly in layers:
         lvl = ct.shape[1]
         if ly[0] == "dense":
-            s = o.dense_scale(lvl, sc)
-            ct = o.dense(ct, o.encode_diagonals(ly[1], s))[0]
+            ct = o.dense(ct, o.encode_diagonals(ly[1], o.dense_scale(lvl, sc), lazy), lazy=lazy)[0]
             sc = o.scale
         elif ly[0] == "square":
             ct = o.square(ct)
@@ -306,13 +316,12 @@ def oracle_forward(o, ct, layers):
     return ct, sc
 
 
-def inject(o, layers):
+def inject(o, layers, lazy=False):
     """Same layers with the oracle's diagonal coefficients attached."""
     out, sc, lvl = [], o.scale, o.L
     for ly in layers:
         if ly[0] == "dense":
-            s = o.dense_scale(lvl, sc)
-            out.append(("dense", ly[1], None, o.encode_diagonals(ly[1], s)))
+            out.append(("dense", ly[1], None, o.encode_diagonals(ly[1], o.dense_scale(lvl, sc), lazy)))
             sc = o.scale
             lvl -= 1
         elif ly[0] == "square":
@@ -324,20 +333,23 @@ def inject(o, layers):
     return out
 
 
+@pytest.mark.parametrize("lazy", [False, True])
 @pytest.mark.parametrize("N,qb,pb,dnum,dims", [
     (256, [60, 40, 40, 40], [60], 4, [16, 8, 4]),
     (512, [45, 45, 45, 45, 45, 45], [60, 60], 3, [32, 16, 16, 8]),
 ])
-def test_network_bit_exact_and_fp64(N, qb, pb, dnum, dims):
+def test_network_bit_exact_and_fp64(N, qb, pb, dnum, dims, lazy):
     layers, slots, ref = network_case(N, qb, pb, dnum, dims)
     g = ctl.Context(N, qb, pb, dnum=dnum, scale=2.0 ** 40)
+    if lazy:
+        g.set_dense_mode(g.DENSE_LAZY_MODDOWN)
     o = O.Oracle(N, qb, pb, dnum=dnum, scale=2.0 ** 40)
-    model = ctl.Model(g, inject(o, layers))
+    model = ctl.Model(g, inject(o, layers, lazy))
     rots = model.rotations()
     o.keygen(rots, seed=3)
     k = g.keygen(rots, seed=3)
     ct_o = o.encrypt(o.encode(slots), 4)
-    exp, sc = oracle_forward(o, ct_o, layers)
+    exp, sc = oracle_forward(o, ct_o, layers, lazy)
     out = model.forward(k, g.ct_import(ct_o, 2.0 ** 40))
     assert np.array_equal(out.export()[0], exp)
     y = g.decrypt(k, out, len(ref))
@@ -348,7 +360,8 @@ def test_network_bit_exact_and_fp64(N, qb, pb, dnum, dims):
     assert np.max(np.abs(y2 - ref)) < TOL
 
 
-def test_cfg1_full_size_bit_exact():
+@pytest.mark.parametrize("lazy", [False, True])
+def test_cfg1_full_size_bit_exact(lazy):
     """N = 4096, q {50,40,40} + 60-bit special prime, dense 64->32 then x^2 (single query)."""
     N, qb, pb = 4096, [50, 40, 40], [60]
     rng = np.random.default_rng(1)
@@ -359,13 +372,15 @@ def test_cfg1_full_size_bit_exact():
     slots[64:128] = x
     layers = [("dense", W), ("square",)]
     g = ctl.Context(N, qb, pb, scale=2.0 ** 40)
+    if lazy:
+        g.set_dense_mode(g.DENSE_LAZY_MODDOWN)
     o = O.Oracle(N, qb, pb, scale=2.0 ** 40)
-    model = ctl.Model(g, inject(o, layers))
+    model = ctl.Model(g, inject(o, layers, lazy))
     rots = model.rotations()
     o.keygen(rots, seed=3)
     k = g.keygen(rots, seed=3)
     ct_o = o.encrypt(o.encode(slots), 4)
-    exp, _ = oracle_forward(o, ct_o, layers)
+    exp, _ = oracle_forward(o, ct_o, layers, lazy)
     out = model.forward(k, g.ct_import(ct_o, 2.0 ** 40))
     assert np.array_equal(out.export()[0], exp)
     assert np.max(np.abs(g.decrypt(k, out, 32) - (W @ x) ** 2)) < TOL

@@ -366,15 +366,14 @@ def test_square_matches_fp64():
     assert np.max(np.abs(o.decode(o.decrypt(sq), o.N // 2, sc) - z * z)) < 1e-6
 
 
-@pytest.mark.parametrize("composed", [False, True])
+@pytest.mark.parametrize("lazy", [False, True])
 @pytest.mark.parametrize("m,n", [(8, 16), (16, 16), (5, 12)])
-def test_dense_bsgs_matches_fp64_and_op_counts(m, n, composed):
+def test_dense_bsgs_matches_fp64_and_op_counts(m, n, lazy):
     N = 128
     t = O.Oracle.bsgs_t(m, n)
-    t1 = O.Oracle.bsgs_t1(t)
+    t1 = O.Oracle.bsgs_t1(t, lazy)
     t2 = t // t1
-    rots = list(range(1, t1)) + [k * t1 for k in range(1, t2)]
-    o = small_ctx(N=N, rots=rots)
+    o = small_ctx(N=N, rots=O.Oracle.bsgs_rotations(m, n, lazy))
     rng = np.random.default_rng(m * 100 + n)
     W = rng.normal(0, 1 / np.sqrt(n), (m, n))
     x = rng.uniform(-1, 1, n)
@@ -383,22 +382,49 @@ def test_dense_bsgs_matches_fp64_and_op_counts(m, n, composed):
     slots[t:t + n] = x  # [x, x] over 2t slots (Sec. 3.1, Multiple Predictions: 2 * #neurons)
     ct = o.encrypt(o.encode(slots), 13)
     lvl = 3
-    pts = o.encode_diagonals(W, o.dense_scale(lvl, o.scale))
-    out, cnt = o.dense(ct, pts, composed=composed)
+    pts = o.encode_diagonals(W, o.dense_scale(lvl), lazy)
+    out, cnt = o.dense(ct, pts, lazy=lazy)
     # Sec. 3.1: t1 + t2 - 2 rotations, t plaintext products, t - 1 additions
     assert cnt == [t1 + t2 - 2, t, t - 1]
-    y = o.decode(o.decrypt(out), N // 2)
+    y = o.decode(o.decrypt(out), N // 2)  # input at Delta: the output is at Delta too
     assert np.max(np.abs(y[:m] - W @ x)) < 1e-6
     assert np.max(np.abs(y[m:])) < 1e-6  # outputs outside [0, m) stay zero
 
 
-def test_bsgs_split_minimises_rotation_cost():
-    # t = t1 * t2 (Eq. bsgs); the split is the power of two that minimises
-    # (t1 - 1) + 4 (t2 - 1), ties to the larger t1, found here by brute force.
+def test_bsgs_splits():
+    # t = t1 * t2 (Eq. bsgs).  Default split t1 = 2^ceil(log2(t)/2); the lazy form's split
+    # is the power of two minimising (t1 - 1) + 4 (t2 - 1), ties to the larger t1, found
+    # here by brute force.
     for lg in range(0, 13):
         t = 1 << lg
+        assert O.Oracle.bsgs_t1(t) == 1 << ((lg + 1) // 2)
         best = min(((1 << a) for a in range(lg + 1)), key=lambda a: ((a - 1) + 4 * (t // a - 1), -a))
-        assert O.Oracle.bsgs_t1(t) == best, t
+        assert O.Oracle.bsgs_t1(t, lazy=True) == best, t
+
+
+def test_dense_is_composition_of_rotations():
+    """With one ModUp shared by the baby steps, the dense layer is bit-identical to the
+    composition of whole rotations, products, sums and a rescale in the order of Eq. (bsgs)."""
+    N, m, n = 128, 16, 16
+    t = 16
+    t1, t2 = O.Oracle.bsgs_t1(t), t // O.Oracle.bsgs_t1(t)
+    o = small_ctx(N=N, rots=O.Oracle.bsgs_rotations(m, n))
+    rng = np.random.default_rng(23)
+    W = rng.normal(0, 1 / np.sqrt(n), (m, n))
+    x = rng.uniform(-1, 1, n)
+    slots = np.zeros(N // 2); slots[:n] = x; slots[t:t + n] = x
+    ct = o.encrypt(o.encode(slots), 24)
+    pts = o.encode_diagonals(W, o.dense_scale(3))
+    baby = [o.rotate(ct, j) for j in range(t1)]
+    acc = None
+    for k in range(t2):
+        inner = None
+        for j in range(t1):
+            term = o.mul_plain(baby[j], pts[k * t1 + j])
+            inner = term if inner is None else o.add(inner, term)
+        rot = o.rotate(inner, k * t1)
+        acc = rot if acc is None else o.add(acc, rot)
+    assert np.array_equal(o.dense(ct, pts)[0], o.rescale(acc))
 
 
 def test_dense_equals_direct_diagonal_method():
@@ -411,7 +437,7 @@ def test_dense_equals_direct_diagonal_method():
     x = rng.uniform(-1, 1, n)
     slots = np.zeros(N // 2); slots[:n] = x; slots[t:t + n] = x
     ct = o.encrypt(o.encode(slots), 15)
-    sc = o.dense_scale(3, o.scale)
+    sc = o.dense_scale(3)
     acc = None
     for i in range(t):
         diag = np.zeros(N // 2)
@@ -426,35 +452,33 @@ def test_dense_equals_direct_diagonal_method():
 
 @pytest.mark.parametrize("m,n,pb", [(16, 16, [60]), (32, 32, [50, 50]), (4, 8, [60])])
 def test_dense_lazy_moddown_equals_composed_rotations(m, n, pb):
-    """The lazy-ModDown form and the plain composition of whole rotations encrypt the
-    same layer output: decoded values agree far inside the noise bound, and with only
-    the j = 0, k = 0 diagonal non-zero (no rotation at all) both reduce to
-    rescale(diag o ct) exactly (ModDown(P * x) = x)."""
+    """The lazy-ModDown form and the composition of whole rotations encrypt the same
+    layer output: decoded values agree far inside the noise bound; and with only
+    diagonal 0 non-zero (no rotation at all) both reduce to rescale(diag o ct) exactly
+    (ModDown(P * x) = x)."""
     N = 128
-    t = O.Oracle.bsgs_t(m, n)
-    t1 = O.Oracle.bsgs_t1(t)
-    rots = list(range(1, t1)) + [k * t1 for k in range(1, t // t1)]
     o = O.Oracle(N, [60, 40, 40, 40], pb, scale=2.0 ** 40)
-    o.keygen(rots, seed=3)
+    o.keygen(sorted(set(O.Oracle.bsgs_rotations(m, n) + O.Oracle.bsgs_rotations(m, n, True))), seed=3)
+    t = O.Oracle.bsgs_t(m, n)
     rng = np.random.default_rng(m + 7 * n)
     W = rng.normal(0, 1 / np.sqrt(n), (m, n))
     x = rng.uniform(-1, 1, n)
     slots = np.zeros(N // 2); slots[:n] = x; slots[t:t + n] = x
     ct = o.encrypt(o.encode(slots), 21)
-    pts = o.encode_diagonals(W, o.dense_scale(4, o.scale))
-    lazy, c1 = o.dense(ct, pts)
-    comp, c2 = o.dense(ct, pts, composed=True)
-    assert c1 == c2
+    pl = o.encode_diagonals(W, o.dense_scale(4), lazy=True)
+    pc = o.encode_diagonals(W, o.dense_scale(4))
+    lazy, c1 = o.dense(ct, pl, lazy=True)
+    comp, c2 = o.dense(ct, pc)
     y1 = o.decode(o.decrypt(lazy), N // 2)
     y2 = o.decode(o.decrypt(comp), N // 2)
     assert np.max(np.abs(y1 - y2)) < 1e-7
     assert np.max(np.abs(y1[:m] - W @ x)) < 1e-6
     # only diagonal 0 non-zero: no key switch takes part in the result
-    pz = np.zeros_like(pts); pz[0] = pts[0]
-    a, _ = o.dense(ct, pz)
-    b, _ = o.dense(ct, pz, composed=True)
+    pz = np.zeros_like(pl); pz[0] = pl[0]
+    a, _ = o.dense(ct, pz, lazy=True)
+    b, _ = o.dense(ct, pz)
     assert np.array_equal(a, b)
-    assert np.array_equal(a, o.rescale(o.mul_plain(ct, pts[0])))
+    assert np.array_equal(a, o.rescale(o.mul_plain(ct, pl[0])))
 
 
 def test_replicate():
@@ -472,12 +496,8 @@ def test_small_network_matches_fp64():
     """dense(16->8) -> x^2 -> replicate -> dense(8->4), the layer pattern of the paper's
     frozen stack with the square activation, decoded within 1e-4 of FP64."""
     N = 256
-    def bsgs_rots(m, n):
-        t = O.Oracle.bsgs_t(m, n)
-        t1 = O.Oracle.bsgs_t1(t)
-        return list(range(1, t1)) + [k * t1 for k in range(1, t // t1)]
-    r1 = bsgs_rots(8, 16)
-    r2 = bsgs_rots(4, 8) + [-8]
+    r1 = O.Oracle.bsgs_rotations(8, 16)
+    r2 = O.Oracle.bsgs_rotations(4, 8) + [-8]
     o = O.Oracle(N, [60, 40, 40, 40], [60], scale=2.0 ** 40)
     o.keygen(sorted(set(r1 + r2)), seed=3)
     rng = np.random.default_rng(18)
@@ -485,7 +505,7 @@ def test_small_network_matches_fp64():
     x = rng.uniform(-1, 1, 16)
     slots = np.zeros(N // 2); slots[:16] = x; slots[16:32] = x
     ct = o.encrypt(o.encode(slots), 19)
-    sc = o.scale
+    sc = o.scale  # a dense layer restores Delta, the square squares it over q_last
     h = o.dense(ct, o.encode_diagonals(W1, o.dense_scale(4, sc)))[0]
     sc = o.scale
     h = o.square(h); sc = o.square_scale(3, sc)
