@@ -394,6 +394,8 @@ def main():
     ap.add_argument("--max-batch", type=int, default=64)
     ap.add_argument("--mem-budget-gb", type=float, default=160.0)
     ap.add_argument("--queries", type=int, default=1024)
+    ap.add_argument("--ntt-shape", default="auto", choices=["auto", "r32", "r16"],
+                    help="register NTT shape (default: the context's autotuned choice)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the extra measurement of the lazy-ModDown dense form")
     args = ap.parse_args()
@@ -441,6 +443,11 @@ def main():
     stream = torch.cuda.Stream()
     ctx = ctl.Context(N, wl["q"], wl["p"], dnum=wl["dnum"], scale=2.0 ** 40)
     ctx.set_stream(stream.cuda_stream)
+    if args.ntt_shape != "auto":
+        sh = ctx.NTT_R16 if args.ntt_shape == "r16" else ctx.NTT_R32
+        ctx.set_ntt_shape(sh, sh)
+    shape_names = {ctx.NTT_R32: "r32", ctx.NTT_R16: "r16"}
+    ntt_shape = dict(zip(("fwd", "inv"), (shape_names.get(v, str(v)) for v in ctx.ntt_shape())))
     model = ctl.Model(ctx, layers)
     keys = ctx.keygen(model.rotations(), seed=3)
     xs, slots = inputs_for(N, wl["dims"], B, t0)
@@ -617,7 +624,7 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
                 "data": "synthetic",
                 "config": {"workload": wl["desc"], "batch_per_gpu": B, "N": N, "parallelism": f"replicas x{world}",
-                           "cuda_graph": bool(use_graph),
+                           "cuda_graph": bool(use_graph), "ntt_shape": ntt_shape,
                            "l2": "inputs larger than L2 (working set of tens of GB per step)",
                            "max_abs_err_vs_fp64": max_err},
                 "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),

@@ -101,6 +101,21 @@ int ctl_synchronize(ctl_context* ctx);
  *     default; needs the Galois keys of its own split.
  * The paper fixes neither choice (Sec. 3.1 only fixes t = t1 * t2 and the hoisting).  A
  * model keeps the mode it was created with.  Errors: CTL_EINVAL (unknown mode). */
+/* Register-resident NTT shapes for N = 4096 .. 16384 (other N use one shared-memory
+ * kernel): R32 = N/32 threads with 32 elements each in three passes (5 + 5 + log2N-10
+ * stages); R16 = N/16 threads with 16 elements each in 4-stage passes (twice the warps
+ * per SM, one more shared-memory transpose).  Both compute the same exact transform.
+ * ctl_set_ntt_shape sets the forward and inverse shapes of a context (CTL_NTT_SHAPE_AUTO
+ * keeps the current one); ctl_autotune_ntt times both shapes on scratch limbs of the
+ * context (plain forward and inverse transforms over batch_limbs limbs) and keeps the
+ * faster per direction, writing the choices to the nullable outputs.  Contexts run the
+ * autotuner once at creation.  Errors: CTL_EINVAL, CTL_ENOMEM, CTL_ECUDA. */
+#define CTL_NTT_SHAPE_AUTO (-1)
+#define CTL_NTT_SHAPE_R32 0
+#define CTL_NTT_SHAPE_R16 1
+int ctl_set_ntt_shape(ctl_context* ctx, int fwd_shape, int inv_shape);
+int ctl_get_ntt_shape(const ctl_context* ctx, int* fwd_shape, int* inv_shape);
+int ctl_autotune_ntt(ctl_context* ctx, uint32_t batch_limbs, int* fwd_shape, int* inv_shape);
 #define CTL_DENSE_COMPOSED 0
 #define CTL_DENSE_LAZY_MODDOWN 1
 int ctl_set_dense_mode(ctl_context* ctx, int mode);

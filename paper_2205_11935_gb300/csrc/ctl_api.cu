@@ -383,6 +383,7 @@ extern "C" int ctl_context_create(ctl_context** out, uint32_t N, const uint32_t*
   }
   c->enc.init(N);
   if ((rc = build_tables(c.get()))) return rc;
+  if ((rc = ctl_autotune_ntt(c.get(), 0, nullptr, nullptr)) && rc != CTL_ENOMEM) return rc;
   *out = c.release();
   return CTL_OK;
 }
@@ -441,6 +442,8 @@ extern "C" int ctl_context_clone(const ctl_context* c, ctl_context** out) {
   k->h_primes = c->h_primes;
   k->enc = c->enc;
   k->dense_mode = c->dense_mode;
+  k->ntt_shape_fwd = c->ntt_shape_fwd;
+  k->ntt_shape_inv = c->ntt_shape_inv;
   k->parent = c->parent ? c->parent : c;
   if (int rc = cuda_check(cudaStreamCreateWithFlags(&k->stream, cudaStreamNonBlocking), "stream")) return rc;
   k->own_stream = true;
@@ -498,6 +501,86 @@ extern "C" int ctl_set_dense_mode(ctl_context* c, int mode) {
   }
   c->dense_mode = mode;
   return CTL_OK;
+}
+
+extern "C" int ctl_set_ntt_shape(ctl_context* c, int fwd_shape, int inv_shape) {
+  auto ok = [](int v) { return v == CTL_NTT_SHAPE_AUTO || v == CTL_NTT_SHAPE_R32 || v == CTL_NTT_SHAPE_R16; };
+  if (!c || !ok(fwd_shape) || !ok(inv_shape)) {
+    set_error("ctl_set_ntt_shape: invalid argument");
+    return CTL_EINVAL;
+  }
+  if (fwd_shape != CTL_NTT_SHAPE_AUTO) c->ntt_shape_fwd = fwd_shape;
+  if (inv_shape != CTL_NTT_SHAPE_AUTO) c->ntt_shape_inv = inv_shape;
+  return CTL_OK;
+}
+
+extern "C" int ctl_get_ntt_shape(const ctl_context* c, int* fwd_shape, int* inv_shape) {
+  if (!c) {
+    set_error("ctl_get_ntt_shape: null context");
+    return CTL_EINVAL;
+  }
+  if (fwd_shape) *fwd_shape = c->ntt_shape_fwd;
+  if (inv_shape) *inv_shape = c->ntt_shape_inv;
+  return CTL_OK;
+}
+
+// Times plain forward and inverse transforms of both register shapes on zero-filled
+// scratch limbs (a valid residue for every prime) and keeps the faster shape per
+// direction.  The launches are not counted in the context's statistics.
+extern "C" int ctl_autotune_ntt(ctl_context* c, uint32_t batch_limbs, int* fwd_shape, int* inv_shape) {
+  if (!c) {
+    set_error("ctl_autotune_ntt: null context");
+    return CTL_EINVAL;
+  }
+  auto report = [&]() {
+    if (fwd_shape) *fwd_shape = c->ntt_shape_fwd;
+    if (inv_shape) *inv_shape = c->ntt_shape_inv;
+    return CTL_OK;
+  };
+  if (c->logN < 12 || c->logN > 14) return report();  // one kernel shape only
+  const uint32_t LK = c->L + c->K;
+  if (batch_limbs == 0) batch_limbs = 8u * (uint32_t)c->sm_count;
+  const int n_polys = (int)std::max<uint32_t>(1, batch_limbs / LK);
+  DBuf buf(c, (size_t)n_polys * LK * c->N);
+  if (!buf.p) {
+    set_error("ctl_autotune_ntt: scratch allocation failed");
+    return CTL_ENOMEM;
+  }
+  cudaMemsetAsync(buf.p, 0, (size_t)n_polys * LK * c->N * sizeof(u64), c->stream);
+  const uint64_t launches0 = c->launch_count.load();
+  const bool timing0 = c->timing.enabled;
+  c->timing.enabled = false;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  auto time_it = [&](bool inv, int shape) {
+    (inv ? c->ntt_shape_inv : c->ntt_shape_fwd) = shape;
+    auto run = [&]() {
+      if (inv)
+        launch_ntt_inv(c, buf.p, (size_t)LK * c->N, n_polys, 0, (int)LK, (int)c->L);
+      else
+        launch_ntt_fwd(c, buf.p, (size_t)LK * c->N, n_polys, 0, (int)LK, (int)c->L);
+    };
+    run();  // warm-up (and occupancy query)
+    cudaEventRecord(e0, c->stream);
+    for (int r = 0; r < 3; r++) run();
+    cudaEventRecord(e1, c->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms;
+  };
+  for (int inv = 0; inv < 2; inv++) {
+    const float t32 = time_it(inv, CTL_NTT_SHAPE_R32);
+    const float t16 = time_it(inv, CTL_NTT_SHAPE_R16);
+    (inv ? c->ntt_shape_inv : c->ntt_shape_fwd) = t16 < t32 ? CTL_NTT_SHAPE_R16 : CTL_NTT_SHAPE_R32;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->timing.enabled = timing0;
+  c->launch_count = launches0;
+  if (int rc = last_cuda("ctl_autotune_ntt")) return rc;
+  return report();
 }
 
 extern "C" int ctl_synchronize(ctl_context* c) {

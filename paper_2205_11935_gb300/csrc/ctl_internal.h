@@ -170,7 +170,7 @@ struct ctl_context {
   ctl::Timing timing;
   std::atomic<uint64_t> launch_count{0};
   uint64_t op_rot = 0, op_ptmul = 0, op_add = 0, op_relin = 0, op_rescale = 0;
-  int ntt_threads_fwd = 0, ntt_threads_inv = 0;  // autotuned block sizes (0: default)
+  int ntt_shape_fwd = CTL_NTT_SHAPE_R32, ntt_shape_inv = CTL_NTT_SHAPE_R32;  // ctl_set_ntt_shape / autotune
   int dense_mode = CTL_DENSE_COMPOSED;          // ctl_set_dense_mode
   const ctl_context* parent = nullptr;  // clones share the parent's device tables
 };

@@ -718,6 +718,171 @@ __global__ void __launch_bounds__(512) k_ntti_gen(const __grid_constant__ Pro pr
 }
 
 // ---------------------------------------------------------------------------------
+// Register-resident kernels with 16 elements per thread (N/16 threads, 4-stage passes):
+// half the registers per thread of the kernels above, so twice as many warps resident
+// per SM to cover memory latency, at the price of one more shared-memory transpose.
+// ---------------------------------------------------------------------------------
+// Pass of stages [S0, S0 + LOGR) on sub-transforms of 2^LOGR elements, 16 / 2^LOGR per
+// thread: sub-transform u = t + T*i is block b = u / D (block index at stage S0), offset
+// o = u % D, elements b * (N >> S0) + o + k * D with D = N >> (S0 + LOGR).
+template <int LOGN, int S0, int LOGR>
+struct Pass16 {
+  static constexpr int N = 1 << LOGN, T = N / 16, R = 1 << LOGR, NS = 16 / R, D = N >> (S0 + LOGR);
+  __device__ __forceinline__ static int blk(int t, int i) { return (t + T * i) / D; }
+  __device__ __forceinline__ static int pos(int t, int i, int k) {
+    const int u = t + T * i;
+    return (u / D) * (N >> S0) + (u % D) + k * D;
+  }
+  __device__ __forceinline__ static void load(u64* x, const u64* smem, int t) {
+#pragma unroll
+    for (int i = 0; i < NS; i++)
+#pragma unroll
+      for (int k = 0; k < R; k++) x[i * R + k] = smem[pidx(pos(t, i, k))];
+  }
+  __device__ __forceinline__ static void store(const u64* x, u64* smem, int t) {
+#pragma unroll
+    for (int i = 0; i < NS; i++)
+#pragma unroll
+      for (int k = 0; k < R; k++) smem[pidx(pos(t, i, k))] = x[i * R + k];
+  }
+  __device__ __forceinline__ static void fwd(u64* x, int t, const ulonglong2* W, u64 q) {
+#pragma unroll
+    for (int i = 0; i < NS; i++) fwd_regs<S0, LOGR>(x + i * R, blk(t, i), W, q);
+  }
+  __device__ __forceinline__ static void inv(u64* x, int t, const ulonglong2* W, u64 q, const DPrime& P) {
+#pragma unroll
+    for (int i = 0; i < NS; i++) inv_regs<S0, LOGR>(x + i * R, blk(t, i), W, q, P);
+  }
+};
+
+template <int LOGN, class Pro, class Epi>
+__global__ void __launch_bounds__((1 << LOGN) / 16, 16384 / (1 << LOGN))
+k_nttf_r16(const __grid_constant__ Pro pro, const __grid_constant__ Epi epi, const DPrime* __restrict__ primes,
+           const ulonglong2* __restrict__ tw, int n_items, int lr, int limb_lo, int lvl, int L) {
+  static_assert(LOGN >= 12 && LOGN <= 14, "16-element kernels cover N = 4096 .. 16384");
+  constexpr int N = 1 << LOGN, T = N / 16, R3 = LOGN - 12;
+  typedef Pass16<LOGN, 0, 4> P0;
+  typedef Pass16<LOGN, 4, 4> P1;
+  typedef Pass16<LOGN, 8, 4> P2;
+  typedef Pass16<LOGN, 12, (R3 > 0 ? R3 : 1)> P3;
+  extern __shared__ u64 smem[];
+  const int t = threadIdx.x;
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const int p = item / lr, l = limb_lo + item % lr;
+    const int pi = l < lvl ? l : L + (l - lvl);
+    typename Pro::State ps;
+    if (!pro.begin(ps, p, l, pi, primes, LOGN)) continue;
+    typename Epi::State es;
+    epi.begin(es, p, l, pi, primes, LOGN);
+    if (threadIdx.x == 0) {  // L2 prefetch: this item's epilogue reads, the next item's sources
+      epi.prefetch(es, LOGN);
+      const int nx = item + gridDim.x;
+      if (nx < n_items) {
+        const int p2 = nx / lr, l2 = limb_lo + nx % lr;
+        pro.prefetch_src(p2, l2, l2 < lvl ? l2 : L + (l2 - lvl), LOGN);
+      }
+    }
+    const u64 q = primes[pi].q;
+    const ulonglong2* W = tw + ((size_t)pi << LOGN);
+    u64 x[16];
+    if constexpr (Pro::kStage) {
+#pragma unroll 4
+      for (int k = 0; k < 16; k++) smem[pidx(t + T * k)] = pro.get(ps, t + T * k);
+#pragma unroll
+      for (int k = 0; k < 16; k++) x[k] = smem[pidx(t + T * k)];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 16; k++) x[k] = pro.get(ps, t + T * k);
+    }
+    P0::fwd(x, t, W, q);
+    P0::store(x, smem, t);
+    __syncthreads();
+    P1::load(x, smem, t);
+    P1::fwd(x, t, W, q);
+    P1::store(x, smem, t);
+    __syncthreads();
+    P2::load(x, smem, t);
+    P2::fwd(x, t, W, q);
+    P2::store(x, smem, t);
+    if constexpr (R3 > 0) {
+      __syncthreads();
+      P3::load(x, smem, t);
+      P3::fwd(x, t, W, q);
+      P3::store(x, smem, t);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < 16; k++) epi.put(es, t + T * k, smem[pidx(t + T * k)]);
+    __syncthreads();
+  }
+}
+
+template <int LOGN, class Pro, class Epi>
+__global__ void __launch_bounds__((1 << LOGN) / 16, 16384 / (1 << LOGN))
+k_ntti_r16(const __grid_constant__ Pro pro, const __grid_constant__ Epi epi, const DPrime* __restrict__ primes,
+           const ulonglong2* __restrict__ tw, int n_items, int lr, int limb_lo, int lvl, int L,
+           const InvScale* __restrict__ scl) {
+  static_assert(LOGN >= 12 && LOGN <= 14, "16-element kernels cover N = 4096 .. 16384");
+  constexpr int N = 1 << LOGN, T = N / 16, R3 = LOGN - 12;
+  typedef Pass16<LOGN, 0, 4> P0;
+  typedef Pass16<LOGN, 4, 4> P1;
+  typedef Pass16<LOGN, 8, 4> P2;
+  typedef Pass16<LOGN, 12, (R3 > 0 ? R3 : 1)> P3;
+  extern __shared__ u64 smem[];
+  const int t = threadIdx.x;
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const int p = item / lr, l = limb_lo + item % lr;
+    const int pi = l < lvl ? l : L + (l - lvl);
+    typename Pro::State ps;
+    if (!pro.begin(ps, p, l, pi, primes, LOGN)) continue;
+    typename Epi::State es;
+    epi.begin(es, p, l, pi, primes, LOGN);
+    if (threadIdx.x == 0) {
+      epi.prefetch(es, LOGN);
+      const int nx = item + gridDim.x;
+      if (nx < n_items) {
+        const int p2 = nx / lr, l2 = limb_lo + nx % lr;
+        pro.prefetch_src(p2, l2, l2 < lvl ? l2 : L + (l2 - lvl), LOGN);
+      }
+    }
+    DPrime P = primes[pi];
+    if (scl) {  // output also multiplied by the factor folded into scl[pi]
+      const InvScale f = scl[pi];
+      P.ninv = f.ninv;
+      P.ninv_sh = f.ninv_sh;
+      P.iw1 = f.iw1;
+      P.iw1_sh = f.iw1_sh;
+    }
+    const u64 q = P.q;
+    const ulonglong2* W = tw + ((size_t)pi << LOGN);
+    u64 x[16];
+#pragma unroll 8
+    for (int k = 0; k < 16; k++) smem[pidx(t + T * k)] = pro.get(ps, t + T * k);
+    __syncthreads();
+    if constexpr (R3 > 0) {
+      P3::load(x, smem, t);
+      P3::inv(x, t, W, q, P);
+      P3::store(x, smem, t);
+      __syncthreads();
+    }
+    P2::load(x, smem, t);
+    P2::inv(x, t, W, q, P);
+    P2::store(x, smem, t);
+    __syncthreads();
+    P1::load(x, smem, t);
+    P1::inv(x, t, W, q, P);
+    P1::store(x, smem, t);
+    __syncthreads();
+    P0::load(x, smem, t);
+    // stages 3..0 (N^-1 folded into stage 0), outputs straight to global
+    P0::inv(x, t, W, q, P);
+#pragma unroll
+    for (int k = 0; k < 16; k++) epi.put(es, t + T * k, x[k]);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------
 // Launch helpers.
 // ---------------------------------------------------------------------------------
 static size_t ntt_smem(int N) { return (size_t)(N + N / 16) * sizeof(u64); }
@@ -748,9 +913,22 @@ static int grid_for(ctl_context* c, K kern, int threads, size_t smem, int items)
 template <bool INV, int LOGN, class Pro, class Epi>
 static void launch_reg(ctl_context* c, const Pro& pro, const Epi& epi, int items, int lr, int limb_lo, int lvl,
                        const InvScale* scl) {
-  const int th = (1 << LOGN) / 32;
   const size_t sm = ntt_smem(1 << LOGN);
   const ulonglong2* tw = (const ulonglong2*)(INV ? c->d_itw2 : c->d_tw2);
+  if ((INV ? c->ntt_shape_inv : c->ntt_shape_fwd) == CTL_NTT_SHAPE_R16) {
+    const int th = (1 << LOGN) / 16;
+    if constexpr (INV) {
+      auto kern = k_ntti_r16<LOGN, Pro, Epi>;
+      const int grid = grid_for(c, kern, th, sm, items);
+      kern<<<grid, th, sm, c->stream>>>(pro, epi, c->d_primes, tw, items, lr, limb_lo, lvl, (int)c->L, scl);
+    } else {
+      auto kern = k_nttf_r16<LOGN, Pro, Epi>;
+      const int grid = grid_for(c, kern, th, sm, items);
+      kern<<<grid, th, sm, c->stream>>>(pro, epi, c->d_primes, tw, items, lr, limb_lo, lvl, (int)c->L);
+    }
+    return;
+  }
+  const int th = (1 << LOGN) / 32;
   if constexpr (INV) {
     auto kern = k_ntti_reg<LOGN, Pro, Epi>;
     const int grid = grid_for(c, kern, th, sm, items);

@@ -50,6 +50,9 @@ SIGNATURES = {
     "ctl_set_stream": (C.c_int, [_vp, _vp]),
     "ctl_set_allocator": (C.c_int, [_vp, _vp, _vp, _vp]),
     "ctl_set_dense_mode": (C.c_int, [_vp, C.c_int]),
+    "ctl_set_ntt_shape": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "ctl_get_ntt_shape": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "ctl_autotune_ntt": (C.c_int, [_vp, C.c_uint32, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "ctl_synchronize": (C.c_int, [_vp]),
     "ctl_keygen": (C.c_int, [_vp, _i32p, C.c_uint32, C.c_uint64, _pp]),
     "ctl_keys_destroy": (None, [_vp]),
@@ -165,6 +168,24 @@ class Context:
     def set_dense_mode(self, mode):
         """Dense layers created afterwards: DENSE_COMPOSED (default) or DENSE_LAZY_MODDOWN."""
         _check(lib().ctl_set_dense_mode(self.h, int(mode)))
+
+    NTT_R32 = 0
+    NTT_R16 = 1
+
+    def set_ntt_shape(self, fwd=-1, inv=-1):
+        """Register NTT shapes (NTT_R32 / NTT_R16; -1 keeps the current one)."""
+        _check(lib().ctl_set_ntt_shape(self.h, int(fwd), int(inv)))
+
+    def ntt_shape(self):
+        f, i = C.c_int(), C.c_int()
+        _check(lib().ctl_get_ntt_shape(self.h, C.byref(f), C.byref(i)))
+        return f.value, i.value
+
+    def autotune_ntt(self, batch_limbs=0):
+        """Re-times both NTT shapes and keeps the faster per direction; returns (fwd, inv)."""
+        f, i = C.c_int(), C.c_int()
+        _check(lib().ctl_autotune_ntt(self.h, batch_limbs, C.byref(f), C.byref(i)))
+        return f.value, i.value
 
     def set_stream(self, stream_ptr):
         _check(lib().ctl_set_stream(self.h, C.c_void_p(stream_ptr)))
