@@ -733,17 +733,36 @@ struct Pass16 {
     const int u = t + T * i;
     return (u / D) * (N >> S0) + (u % D) + k * D;
   }
+  // pidx(pos(t, i, k)) = pidx(pos(t, i, 0)) + k * DP whenever D is a multiple of 16 or a
+  // sub-transform stays inside one 16-element group (R * D <= 16): then one address per
+  // sub-transform and compile-time offsets suffice.
+  static constexpr bool AFFINE = (D % 16 == 0) || (R * D <= 16);
+  static constexpr int DP = (D % 16 == 0) ? D + D / 16 : D;
   __device__ __forceinline__ static void load(u64* x, const u64* smem, int t) {
 #pragma unroll
-    for (int i = 0; i < NS; i++)
+    for (int i = 0; i < NS; i++) {
+      if constexpr (AFFINE) {
+        const u64* s = smem + pidx(pos(t, i, 0));
 #pragma unroll
-      for (int k = 0; k < R; k++) x[i * R + k] = smem[pidx(pos(t, i, k))];
+        for (int k = 0; k < R; k++) x[i * R + k] = s[k * DP];
+      } else {
+#pragma unroll
+        for (int k = 0; k < R; k++) x[i * R + k] = smem[pidx(pos(t, i, k))];
+      }
+    }
   }
   __device__ __forceinline__ static void store(const u64* x, u64* smem, int t) {
 #pragma unroll
-    for (int i = 0; i < NS; i++)
+    for (int i = 0; i < NS; i++) {
+      if constexpr (AFFINE) {
+        u64* s = smem + pidx(pos(t, i, 0));
 #pragma unroll
-      for (int k = 0; k < R; k++) smem[pidx(pos(t, i, k))] = x[i * R + k];
+        for (int k = 0; k < R; k++) s[k * DP] = x[i * R + k];
+      } else {
+#pragma unroll
+        for (int k = 0; k < R; k++) smem[pidx(pos(t, i, k))] = x[i * R + k];
+      }
+    }
   }
   __device__ __forceinline__ static void fwd(u64* x, int t, const ulonglong2* W, u64 q) {
 #pragma unroll
