@@ -973,9 +973,11 @@ namespace {
 // x_r either 0 (one input shared by all rotations: hoisting) or nb*x_b) with the key and
 // Galois element of rotation r.  out [nr][nb][2][lvl][N].  The addend (nullable) is
 // added through sigma_g as described at launch_moddown_ntt.
+// With accum, the nr results are summed into out [nb][2][lvl][N] (out += each result,
+// one ModDown launch per rotation so that no two items of a launch share an output).
 int keyswitch(ctl_context* c, int nr, int nb, int lvl, const u64* x, size_t x_r, size_t x_b,
               const std::vector<const u64*>& keys, const std::vector<u64>& gs, const u64* addend, size_t add_r,
-              size_t add_b, size_t add_p, bool add_both, u64* out) {
+              size_t add_b, size_t add_p, bool add_both, u64* out, bool accum = false) {
   const uint32_t N = c->N;
   const int nd = (lvl + (int)c->alpha - 1) / (int)c->alpha;
   const int E = lvl + (int)c->K;
@@ -1007,7 +1009,18 @@ int keyswitch(ctl_context* c, int nr, int nb, int lvl, const u64* x, size_t x_r,
   // 4. ModDown: special limbs to coefficient form, then conversion + NTT + combine
   // (the factors Phat_j^-1 of the ModDown conversion are folded into this transform)
   launch_ntt_inv_oop(c, acc.p, (size_t)E * N, acc.p, (size_t)E * N, nr * nb * 2, lvl, E, lvl, c->d_md_scale);
-  launch_moddown_ntt(c, acc.p, nr, nb, lvl, out, addend, add_r, add_b, add_p, add_both, rl);
+  if (!accum) {
+    launch_moddown_ntt(c, acc.p, nr, nb, lvl, out, addend, add_r, add_b, add_p, add_both, rl);
+  } else {
+    for (int r = 0; r < nr; r++) {
+      RotList one;
+      one.n = 1;
+      one.key[0] = rl.key[r];
+      one.g[0] = rl.g[r];
+      launch_moddown_ntt(c, acc.p + (size_t)r * nb * 2 * E * N, 1, nb, lvl, out,
+                         addend ? addend + (size_t)r * add_r : nullptr, 0, add_b, add_p, add_both, one, true);
+    }
+  }
   return last_cuda("keyswitch");
 }
 
@@ -1443,11 +1456,9 @@ int dense_apply_composed(ctl_context* c, const ctl_keys* k, const DenseLayer& D,
   if (t2 > 1) {
     const int E = (int)lvl + (int)c->K;
     const int nd = ((int)lvl + (int)c->alpha - 1) / (int)c->alpha;
-    const size_t per = (size_t)nb * N * sizeof(u64) * ((size_t)2 * E + (size_t)nd * E + 3 * (size_t)lvl);
+    const size_t per = (size_t)nb * N * sizeof(u64) * ((size_t)2 * E + (size_t)nd * E + (size_t)lvl);
     const int chunk = (int)std::min<size_t>(
         std::min<size_t>(CTL_MAX_ROT, t2 - 1), std::max<size_t>(1, ((size_t)6 << 30) / std::max<size_t>(per, 1)));
-    DBuf rot(c, bw * (size_t)chunk);
-    CHECK_ALLOC(rot);
     for (uint32_t k0 = 1; k0 < t2; k0 += chunk) {
       const int nr = (int)std::min<uint32_t>(t2 - k0, (uint32_t)chunk);
       RotList rl;
@@ -1455,10 +1466,10 @@ int dense_apply_composed(ctl_context* c, const ctl_keys* k, const DenseLayer& D,
       std::vector<const u64*> keys(rl.key, rl.key + nr);
       std::vector<u64> gs(rl.g, rl.g + nr);
       const u64* src = inner.p + (size_t)k0 * bw;
-      int rc = keyswitch(c, nr, nb, (int)lvl, src + LN, bw, ctw, keys, gs, src, bw, ctw, 0, false, rot.p);
+      // each rotation's ModDown adds its result (and sigma_g of its c0) straight into acc
+      int rc = keyswitch(c, nr, nb, (int)lvl, src + LN, bw, ctw, keys, gs, src, bw, ctw, 0, false, acc, true);
       if (rc) return rc;
       c->op_rot += (uint64_t)nr * nb;
-      for (int r = 0; r < nr; r++) launch_add(c, acc, rot.p + (size_t)r * bw, acc, nb * 2, (int)lvl, LN, LN, LN);
     }
   }
   if (D.bias) launch_add_plain(c, acc, D.bias, nb, (int)lvl, ctw);

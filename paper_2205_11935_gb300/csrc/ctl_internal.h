@@ -245,9 +245,11 @@ void launch_scale_to_ext(ctl_context* c, const u64* in, u64* out, int nb, int lv
 // ModDown after the special limbs of acc [nr][nb][2][E][N] were inverse-transformed in
 // place: out[p][i] = (acc[p][i] - NTT_i(conv_i(acc[p][specials]))) * P^-1 (+ addend),
 // out [nr][nb][2][lvl][N].  Addend of output (r, b, t): addend + r*add_r + b*add_b + t*add_p
-// read through sigma_{g_r}; t = 1 gets one only if add_both.
+// read through sigma_{g_r}; t = 1 gets one only if add_both.  With accum (nr = 1 only),
+// out += result instead of out = result.
 void launch_moddown_ntt(ctl_context* c, const u64* acc, int nr, int nb, int lvl, u64* out, const u64* addend,
-                        size_t add_r, size_t add_b, size_t add_p, bool add_both, const RotList& rl);
+                        size_t add_r, size_t add_b, size_t add_p, bool add_both, const RotList& rl,
+                        bool accum = false);
 // ModDown of n_polys extended polys spaced by acc_stride (special limbs already
 // inverse-transformed in place, as above) into out + p*out_stride ([lvl][N]), no addend.
 void launch_moddown_polys(ctl_context* c, const u64* acc, size_t acc_stride, int n_polys, int lvl, u64* out,

@@ -281,6 +281,7 @@ struct EpiModDown {
   size_t add_r, add_b, add_p;
   int add_both;
   int nb;
+  int accum;  // 1: out += result (each output element is written by one item of the launch)
   u64 g[CTL_MAX_ROT];
   struct State {
     const u64* a;
@@ -308,26 +309,29 @@ struct EpiModDown {
   __device__ void prefetch(const State& st, int logN) const {
     l2_prefetch(st.a, 8u << logN);
     if (st.ad) l2_prefetch(st.ad, 8u << logN);
+    if (accum) l2_prefetch(st.o, 8u << logN);
   }
   __device__ void put(const State& st, int j, u64 v) const {
     u64 r = shoup(submod(st.a[j], reduce4(v, st.q), st.q), st.pv, st.pvs, st.q);
     if (st.ad) r = addmod(r, st.ad[st.gg == 1 ? (uint32_t)j : auto_src((uint32_t)j, st.gg, st.lg)], st.q);
+    if (accum) r = addmod(r, st.o[j], st.q);
     st.o[j] = r;
   }
   // C elements t0 + T*k of one thread, all loads issued first.
   template <int T, int C>
   __device__ void putc(const State& st, int t0, const u64* x) const {
-    u64 a[C], ad[C];
+    u64 a[C], ad[C], ac[C];
 #pragma unroll
     for (int k = 0; k < C; k++) {
       const int j = t0 + T * k;
       a[k] = st.a[j];
       ad[k] = st.ad ? st.ad[st.gg == 1 ? (uint32_t)j : auto_src((uint32_t)j, st.gg, st.lg)] : 0;
+      ac[k] = accum ? st.o[j] : 0;
     }
 #pragma unroll
     for (int k = 0; k < C; k++) {
       const u64 r = shoup(submod(a[k], reduce4(x[k], st.q), st.q), st.pv, st.pvs, st.q);
-      st.o[t0 + T * k] = addmod(r, ad[k], st.q);
+      st.o[t0 + T * k] = addmod(addmod(r, ad[k], st.q), ac[k], st.q);
     }
   }
 };
@@ -1063,7 +1067,7 @@ void launch_modup_ntt(ctl_context* c, const u64* src_coef, size_t coef_stride, c
 template <int NS>
 static void moddown_ns(ctl_context* c, const u64* acc, size_t acc_stride, int n_polys, int lvl, u64* out,
                        size_t out_stride, const u64* addend, size_t add_r, size_t add_b, size_t add_p, bool add_both,
-                       int nb, const RotList* rl) {
+                       int nb, const RotList* rl, bool accum) {
   ProModDown<NS> pro;
   pro.acc = acc;
   pro.acc_stride = acc_stride;
@@ -1082,6 +1086,7 @@ static void moddown_ns(ctl_context* c, const u64* acc, size_t acc_stride, int n_
   epi.add_p = add_p;
   epi.add_both = add_both ? 1 : 0;
   epi.nb = nb;
+  epi.accum = accum ? 1 : 0;
   for (int r = 0; r < CTL_MAX_ROT; r++) epi.g[r] = (rl && r < rl->n) ? rl->g[r] : 1;
   run_ntt<false>(c, KC_MODDOWN, pro, epi, n_polys, 0, lvl, lvl, butterflies(c) + (double)(c->K * 2 + 1) * c->N);
 }
@@ -1098,16 +1103,16 @@ static void moddown_dispatch(ctl_context* c, A... a) {
 }
 
 void launch_moddown_ntt(ctl_context* c, const u64* acc, int nr, int nb, int lvl, u64* out, const u64* addend,
-                        size_t add_r, size_t add_b, size_t add_p, bool add_both, const RotList& rl) {
+                        size_t add_r, size_t add_b, size_t add_p, bool add_both, const RotList& rl, bool accum) {
   const size_t EN = (size_t)(lvl + (int)c->K) * c->N;
   moddown_dispatch(c, acc, EN, nr * nb * 2, lvl, out, (size_t)lvl * c->N, addend, add_r, add_b, add_p, add_both, nb,
-                   &rl);
+                   &rl, accum);
 }
 
 void launch_moddown_polys(ctl_context* c, const u64* acc, size_t acc_stride, int n_polys, int lvl, u64* out,
                           size_t out_stride) {
   moddown_dispatch(c, acc, acc_stride, n_polys, lvl, out, out_stride, (const u64*)nullptr, (size_t)0, (size_t)0,
-                   (size_t)0, false, 1, (const RotList*)nullptr);
+                   (size_t)0, false, 1, (const RotList*)nullptr, false);
 }
 
 }  // namespace ctl
