@@ -40,6 +40,10 @@ MAX_SM_MHZ = 2070.0
 # one split-half multiply-accumulate (four 32x32->64 IMAD.WIDE, each two IMAD issue slots)
 SPLIT_MAC_IMAD = 8.0
 MAC_CLASSES = ("key_ip", "bsgs_inner")  # kernel classes whose work unit is a split-half MAC
+# DRAM bytes (read + write) per limb item of the fused NTT kernels, from one ncu capture of
+# the same kernels at batch 16 (profiles/ncu_full_modup_moddown_bsgs_keyip_n16384_b16.md);
+# traffic grows with the items, so a launch's traffic is this times its items.
+TRAFFIC_PER_ITEM = {"moddown_ntt": 2846e6 / 7936, "modup_ntt": 4275e6 / 19840}
 
 WORKLOADS = {
     "batched": dict(N=16384, q=[45] * 8, p=[60, 60], dnum=4, batch=256, dims=[1024, 256, 256, 64],
@@ -604,11 +608,18 @@ def main():
                  for k, v in classes.items()}
     unit, peak = unit_peak(dom)
     achieved = rate(d)
+    traffic = None
+    if dom in TRAFFIC_PER_ITEM and N == 16384:
+        K, alpha = len(wl["p"]), -(-len(wl["q"]) // wl["dnum"])
+        per_item = 0.5 * N * 14 + (2 * K + 1) * N if dom == "moddown_ntt" else 0.5 * N * 14 + alpha * 2 * N
+        traffic = TRAFFIC_PER_ITEM[dom] * (d["modmul"] / max(d["launches"], 1)) / per_item
     basis = (f"{SM_COUNT} SMs x {IMAD_PER_CLK_SM} IMAD/clk x {MAX_SM_MHZ:.0f} MHz / " +
              (f"{SPLIT_MAC_IMAD:.0f} IMAD slots per split-half MAC" if dom in MAC_CLASSES
               else f"{SHOUP_IMAD} IMAD per Shoup modmul (measured)"))
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved / 1e9, "peak": peak / 1e9,
-                "unit": unit, "frac": achieved / peak, "traffic": None, "peak_basis": basis,
+                "unit": unit, "frac": achieved / peak, "traffic": traffic, "peak_basis": basis,
+                "traffic_basis": ("ncu dram bytes per limb item of this kernel at batch 16, times the items of "
+                                  "an average launch" if traffic is not None else None),
                 "avg_launch_ms": d["ms"] / max(d["launches"], 1), "classes": per_class,
                 "timing": timing_source}
 

@@ -222,7 +222,8 @@ void launch_intt_rescale_last(ctl_context* c, const u64* in, size_t poly_stride,
 void launch_rescale_ntt(ctl_context* c, const u64* r, const u64* in, size_t in_stride, u64* out, size_t out_stride,
                         int n_polys, int lvl);
 // ModUp of c1 (coefficient form src_coef, NTT form src_ntt; polys spaced by src_stride)
-// into ext[b][d][E][N] (NTT form), E = lvl + K, for all live digits d.
+// into ext[b][d][E][N] (NTT form), E = lvl + K, for all live digits d.  Limbs whose prime
+// has a split width w are stored split, (v >> w) << 32 | (v & (2^w - 1)), for the key product.
 void launch_modup_ntt(ctl_context* c, const u64* src_coef, size_t coef_stride, const u64* src_ntt, size_t src_stride,
                       int nb, int lvl, u64* ext);
 // Key inner products with automorphism: for rotation r (g[r], key[r]) and batch b:

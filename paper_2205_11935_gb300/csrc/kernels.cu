@@ -286,17 +286,10 @@ void launch_automorph(ctl_context* c, const u64* in, u64* out, int n_polys, int 
 // values in registers and sweeps the batch, so each key value leaves HBM once per
 // launch.  The automorphism gather stays inside an aligned 32-element block for the 32
 // consecutive k of a warp (bit-reversed order), so it touches as many sectors as a
-// coalesced load.  On limbs with a split width w the products use w-bit halves
-// (4 32x32->64 multiply-adds, no carries); otherwise 64x64->128 products with the high
-// word kept below q.
+// coalesced load.  On limbs with a split width w the products use w-bit halves (the
+// ModUp stores its digits split; three 32x32->64 multiply-adds per product, no carries);
+// otherwise 64x64->128 products with the high word kept below q.
 __device__ __forceinline__ u64 split_of(u64 v, int w, u64 mask) { return ((v >> w) << 32) | (v & mask); }
-__device__ __forceinline__ void smac(u64& a00, u64& a01, u64& a11, uint32_t x0, uint32_t x1, u64 k) {
-  const uint32_t k0 = (uint32_t)k, k1 = (uint32_t)(k >> 32);
-  a00 += (u64)x0 * k0;
-  a01 += (u64)x0 * k1;
-  a01 += (u64)x1 * k0;
-  a11 += (u64)x1 * k1;
-}
 __device__ __forceinline__ u64 split_redc(u64 a00, u64 a01, u64 a11, int w, u64 q, u64 qinv) {
   u64 lo = a00, hi = 0;
   const u64 t_lo = a01 << w, t_hi = a01 >> (64 - w);
@@ -313,6 +306,7 @@ __device__ __forceinline__ u64 split_redc(u64 a00, u64 a01, u64 a11, int w, u64 
 template <int ND>
 struct KeyRegs {
   u64 k0[ND], k1[ND];
+  uint32_t s0[ND], s1[ND];  // split key halves summed (Karatsuba middle operands)
   __device__ __forceinline__ void load(const u64* key, int nd, int pi, int LK, size_t N, uint32_t k, int w,
                                        u64 mask) {
 #pragma unroll
@@ -322,6 +316,8 @@ struct KeyRegs {
       if (w) {
         k0[d] = split_of(k0[d], w, mask);
         k1[d] = split_of(k1[d], w, mask);
+        s0[d] = (uint32_t)k0[d] + (uint32_t)(k0[d] >> 32);
+        s1[d] = (uint32_t)k1[d] + (uint32_t)(k1[d] >> 32);
       }
     }
   }
@@ -330,22 +326,29 @@ struct KeyRegs {
 #pragma unroll
     for (int d = 0; d < ND; d++) xv[d] = d < nd ? eb[(size_t)d * EN] : 0;
   }
-  // (r0, r1) = sum_d xv[d] * (k0[d], k1[d]) mod q, plain residues.
+  // (r0, r1) = sum_d xv[d] * (k0[d], k1[d]) mod q, plain residues.  On split limbs the
+  // digit values arrive split and each product takes three 32x32->64 multiply-adds
+  // (Karatsuba: the middle term is (x0 + x1)(k0 + k1) - x0 k0 - x1 k1; every sum stays
+  // below nd * 2^(2w+2) <= 2^60 for nd <= 16, w <= 27).
   __device__ __forceinline__ void ip(const u64 (&xv)[ND], int nd, int w, u64 mask, const DPrime& P, u64& r0,
                                      u64& r1) const {
+    (void)mask;
     if (w) {
-      u64 a00 = 0, a01 = 0, a11 = 0, c00 = 0, c01 = 0, c11 = 0;
+      u64 a00 = 0, am = 0, a11 = 0, c00 = 0, cm = 0, c11 = 0;
 #pragma unroll
       for (int d = 0; d < ND; d++) {
         if (d < nd) {
-          const u64 x = xv[d];
-          const uint32_t x0 = (uint32_t)(x & mask), x1 = (uint32_t)(x >> w);
-          smac(a00, a01, a11, x0, x1, k0[d]);
-          smac(c00, c01, c11, x0, x1, k1[d]);
+          const uint32_t x0 = (uint32_t)xv[d], x1 = (uint32_t)(xv[d] >> 32), xs = x0 + x1;
+          a00 += (u64)x0 * (uint32_t)k0[d];
+          a11 += (u64)x1 * (uint32_t)(k0[d] >> 32);
+          am += (u64)xs * s0[d];
+          c00 += (u64)x0 * (uint32_t)k1[d];
+          c11 += (u64)x1 * (uint32_t)(k1[d] >> 32);
+          cm += (u64)xs * s1[d];
         }
       }
-      r0 = split_redc(a00, a01, a11, w, P.q, P.qinv);
-      r1 = split_redc(c00, c01, c11, w, P.q, P.qinv);
+      r0 = split_redc(a00, am - a00 - a11, a11, w, P.q, P.qinv);
+      r1 = split_redc(c00, cm - c00 - c11, c11, w, P.q, P.qinv);
     } else {
       u64 lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
 #pragma unroll

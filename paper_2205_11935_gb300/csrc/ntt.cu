@@ -149,6 +149,30 @@ struct EpiStore {
   }
 };
 
+// Store of ModUp digits for the key product: on limbs whose prime has a split width w,
+// the residue v is stored as (v >> w) << 32 | (v & (2^w - 1)), the operand form of the
+// split-half multiply-adds, so the key product does not split it once per rotation.
+struct EpiStoreSplit {
+  u64* dst;
+  size_t poly_stride;
+  struct State {
+    u64* o;
+    u64 q, mask;
+    int w;
+  };
+  __device__ void begin(State& st, int p, int l, int pi, const DPrime* pr, int logN) const {
+    st.o = dst + (size_t)p * poly_stride + ((size_t)l << logN);
+    st.q = pr[pi].q;
+    st.w = (int)pr[pi].split;
+    st.mask = st.w ? (1ull << st.w) - 1 : ~0ull;
+  }
+  __device__ void put(const State& st, int j, u64 v) const {
+    const u64 r = reduce4(v, st.q);
+    st.o[j] = st.w ? ((r >> st.w) << 32) | (r & st.mask) : r;
+  }
+  __device__ void prefetch(const State&, int) const {}
+};
+
 // Fast base conversion of one element: y = sum_j [x_j * Shat_j^-1]_{s_j} * (Shat_j mod t)
 // mod t over the ns <= NS source limbs, the constants Shat_j mod t in Montgomery form;
 // exact residue in [0, t).
@@ -224,7 +248,12 @@ struct ProModUp {
     if (l >= d0 && l < d1) {  // the digit's own primes: y = x mod q_l, already in NTT form
       const u64* g = ntt + (size_t)b * stride + ((size_t)l << logN);
       u64* o = ext + (((size_t)p * E + l) << logN);
-      for (int k = threadIdx.x; k < N; k += blockDim.x) o[k] = g[k];
+      const int w = (int)pr[pi].split;  // stored split, as EpiStoreSplit does
+      const u64 mask = w ? (1ull << w) - 1 : ~0ull;
+      for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        const u64 v = g[k];
+        o[k] = w ? ((v >> w) << 32) | (v & mask) : v;
+      }
       return false;
     }
     st.bind(tabs[d], l, coef + (size_t)b * coef_stride, (size_t)d0, logN, pr[pi].q, pr[pi].qinv);
@@ -1049,7 +1078,7 @@ static void modup_ns(ctl_context* c, const u64* src_coef, size_t coef_stride, co
   pro.alpha = (int)c->alpha;
   for (int d = 0; d < CTL_MAX_DIGITS; d++)
     pro.tabs[d] = d < nd ? c->modup_tabs[(size_t)(lvl - 1) * c->beta + d] : ConvTab{};
-  run_ntt<false>(c, KC_MODUP, pro, EpiStore{ext, (size_t)E * c->N}, nb * nd, 0, E, lvl,
+  run_ntt<false>(c, KC_MODUP, pro, EpiStoreSplit{ext, (size_t)E * c->N}, nb * nd, 0, E, lvl,
                  butterflies(c) + (double)c->alpha * 2.0 * c->N);
 }
 
