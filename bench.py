@@ -400,6 +400,7 @@ def main():
     ap.add_argument("--queries", type=int, default=1024)
     ap.add_argument("--ntt-shape", default="auto", choices=["auto", "r32", "r16"],
                     help="register NTT shape (default: the context's autotuned choice)")
+    ap.add_argument("--bsgs-shape", default="", help="chunk,karatsuba for the BSGS kernel (default: library's)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the extra measurement of the lazy-ModDown dense form")
     args = ap.parse_args()
@@ -450,6 +451,8 @@ def main():
     if args.ntt_shape != "auto":
         sh = ctx.NTT_R16 if args.ntt_shape == "r16" else ctx.NTT_R32
         ctx.set_ntt_shape(sh, sh)
+    if args.bsgs_shape:
+        ctx.set_bsgs_shape(*[int(v) for v in args.bsgs_shape.split(",")])
     shape_names = {ctx.NTT_R32: "r32", ctx.NTT_R16: "r16"}
     ntt_shape = dict(zip(("fwd", "inv"), (shape_names.get(v, str(v)) for v in ctx.ntt_shape())))
     model = ctl.Model(ctx, layers)

@@ -116,6 +116,11 @@ int ctl_synchronize(ctl_context* ctx);
 int ctl_set_ntt_shape(ctl_context* ctx, int fwd_shape, int inv_shape);
 int ctl_get_ntt_shape(const ctl_context* ctx, int* fwd_shape, int* inv_shape);
 int ctl_autotune_ntt(ctl_context* ctx, uint32_t batch_limbs, int* fwd_shape, int* inv_shape);
+/* Shape of the baby-step giant-step inner-sum kernel: baby-step values held per thread
+ * (chunk 16 or 32; larger t1 is summed in chunks) and the split products with four or
+ * three (karatsuba = 1) 32x32->64 multiply-adds.  Results are identical for every
+ * shape.  Errors: CTL_EINVAL. */
+int ctl_set_bsgs_shape(ctl_context* ctx, int chunk, int karatsuba);
 #define CTL_DENSE_COMPOSED 0
 #define CTL_DENSE_LAZY_MODDOWN 1
 int ctl_set_dense_mode(ctl_context* ctx, int mode);

@@ -444,6 +444,8 @@ extern "C" int ctl_context_clone(const ctl_context* c, ctl_context** out) {
   k->dense_mode = c->dense_mode;
   k->ntt_shape_fwd = c->ntt_shape_fwd;
   k->ntt_shape_inv = c->ntt_shape_inv;
+  k->bsgs_chunk = c->bsgs_chunk;
+  k->bsgs_karatsuba = c->bsgs_karatsuba;
   k->parent = c->parent ? c->parent : c;
   if (int rc = cuda_check(cudaStreamCreateWithFlags(&k->stream, cudaStreamNonBlocking), "stream")) return rc;
   k->own_stream = true;
@@ -511,6 +513,16 @@ extern "C" int ctl_set_ntt_shape(ctl_context* c, int fwd_shape, int inv_shape) {
   }
   if (fwd_shape != CTL_NTT_SHAPE_AUTO) c->ntt_shape_fwd = fwd_shape;
   if (inv_shape != CTL_NTT_SHAPE_AUTO) c->ntt_shape_inv = inv_shape;
+  return CTL_OK;
+}
+
+extern "C" int ctl_set_bsgs_shape(ctl_context* c, int chunk, int karatsuba) {
+  if (!c || (chunk != 16 && chunk != 32) || (karatsuba != 0 && karatsuba != 1)) {
+    set_error("ctl_set_bsgs_shape: invalid argument");
+    return CTL_EINVAL;
+  }
+  c->bsgs_chunk = chunk;
+  c->bsgs_karatsuba = karatsuba;
   return CTL_OK;
 }
 

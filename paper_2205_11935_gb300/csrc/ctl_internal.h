@@ -172,6 +172,7 @@ struct ctl_context {
   uint64_t op_rot = 0, op_ptmul = 0, op_add = 0, op_relin = 0, op_rescale = 0;
   int ntt_shape_fwd = CTL_NTT_SHAPE_R32, ntt_shape_inv = CTL_NTT_SHAPE_R32;  // ctl_set_ntt_shape / autotune
   int dense_mode = CTL_DENSE_COMPOSED;          // ctl_set_dense_mode
+  int bsgs_chunk = 32, bsgs_karatsuba = 1;      // ctl_set_bsgs_shape (measured fastest)
   const ctl_context* parent = nullptr;  // clones share the parent's device tables
 };
 

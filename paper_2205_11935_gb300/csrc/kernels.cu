@@ -612,7 +612,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // first adds its partial sums to the ones the same thread stored for the chunk before
 // (that value is requested before the chunk's products, so its latency is covered).
 // A block has one warp per (ciphertext, poly) pair, up to 8.
-template <int T1>
+template <int T1, bool KARA>
 __global__ void __launch_bounds__(256) k_bsgs(const u64* __restrict__ baby, const u64* __restrict__ diag,
                                               size_t diag_stride, u64* __restrict__ inner,
                                               const DPrime* __restrict__ pr, int logN, int t1, int t2, int nb,
@@ -666,21 +666,38 @@ __global__ void __launch_bounds__(256) k_bsgs(const u64* __restrict__ baby, cons
     const u64(*D)[32] = Ds[s_ & 1];
     u64 res;
     if (w) {
-      // two accumulators for the middle term keep the dependent chains short
-      u64 a00 = 0, a01 = 0, a10 = 0, a11 = 0;
+      u64 a00 = 0, a11 = 0, m;
+      if constexpr (KARA) {
+        // three multiply-adds per product: middle term (x0 + x1)(d0 + d1) - x0 d0 - x1 d1;
+        // am < T1 * 2^(2w+2) <= 2^61
+        u64 am = 0;
 #pragma unroll
-      for (int j = 0; j < T1; j++) {
-        const u64 d = D[j][lane];
-        const uint32_t d0 = (uint32_t)d, d1 = (uint32_t)(d >> 32);
-        const uint32_t x0 = (uint32_t)x[j], x1 = (uint32_t)(x[j] >> 32);
-        a00 += (u64)x0 * d0;
-        a01 += (u64)x0 * d1;
-        a10 += (u64)x1 * d0;
-        a11 += (u64)x1 * d1;
+        for (int j = 0; j < T1; j++) {
+          const u64 d = D[j][lane];
+          const uint32_t d0 = (uint32_t)d, d1 = (uint32_t)(d >> 32);
+          const uint32_t x0 = (uint32_t)x[j], x1 = (uint32_t)(x[j] >> 32);
+          a00 += (u64)x0 * d0;
+          a11 += (u64)x1 * d1;
+          am += (u64)(x0 + x1) * (d0 + d1);
+        }
+        m = am - a00 - a11;
+      } else {
+        // two accumulators for the middle term keep the dependent chains short
+        u64 a01 = 0, a10 = 0;
+#pragma unroll
+        for (int j = 0; j < T1; j++) {
+          const u64 d = D[j][lane];
+          const uint32_t d0 = (uint32_t)d, d1 = (uint32_t)(d >> 32);
+          const uint32_t x0 = (uint32_t)x[j], x1 = (uint32_t)(x[j] >> 32);
+          a00 += (u64)x0 * d0;
+          a01 += (u64)x0 * d1;
+          a10 += (u64)x1 * d0;
+          a11 += (u64)x1 * d1;
+        }
+        m = a01 + a10;
       }
-      // S = a11 * 2^(2w) + (a01 + a10) * 2^w + a00 as a 128-bit (hi, lo); a01 + a10 < 2^64
-      // because each is below T1 * 2^(2w) and 2 * T1 * 2^(2w) < 2^64 (T1 <= 32, w <= 27)
-      const u64 m = a01 + a10;
+      // S = a11 * 2^(2w) + m * 2^w + a00 as a 128-bit (hi, lo); m < 2^64 because it is
+      // below 2 * T1 * 2^(2w) (T1 <= 32, w <= 27)
       u64 lo = a00, hi = 0;
       const u64 t_lo = m << w, t_hi = m >> (64 - w);
       lo += t_lo;
@@ -710,16 +727,24 @@ void launch_bsgs_inner(ctl_context* c, const u64* baby, const u64* diag, size_t 
   const int wpb = std::min(8, nb * 2);  // warps (ciphertext polys) per block
   dim3 grid((unsigned)((nb * 2 + wpb - 1) / wpb), gy, (unsigned)((chunks + gy - 1) / gy));
   double work = (double)t1 * t2 * nb * 2 * LN;
+  const bool kara = c->bsgs_karatsuba != 0;
 #define CTL_BSGS_CASE(TT)                                                                                      \
   case TT:                                                                                                     \
-    CTL_LAUNCH(KC_BSGS, work, grid,                                                                            \
-               (k_bsgs<TT><<<grid, 32 * wpb, 0, c->stream>>>(baby, diag, diag_stride, inner, c->d_primes,      \
-                                                             (int)c->logN, t1, t2, nb, limbs, lvl,             \
-                                                             (int)c->L)));                                     \
+    if (kara)                                                                                                  \
+      CTL_LAUNCH(KC_BSGS, work, grid,                                                                          \
+                 (k_bsgs<TT, true><<<grid, 32 * wpb, 0, c->stream>>>(baby, diag, diag_stride, inner,           \
+                                                                     c->d_primes, (int)c->logN, t1, t2, nb,   \
+                                                                     limbs, lvl, (int)c->L)));                \
+    else                                                                                                       \
+      CTL_LAUNCH(KC_BSGS, work, grid,                                                                          \
+                 (k_bsgs<TT, false><<<grid, 32 * wpb, 0, c->stream>>>(baby, diag, diag_stride, inner,          \
+                                                                      c->d_primes, (int)c->logN, t1, t2, nb,  \
+                                                                      limbs, lvl, (int)c->L)));               \
     break;
-  // T1 = min(t1, 32); t1 is a power of two, so T1 divides it
+  // T1 = min(t1, chunk cap); t1 and the cap are powers of two, so T1 divides t1
+  const int cap = c->bsgs_chunk == 16 ? 16 : 32;
   int T1 = 1;
-  while (T1 < t1 && T1 < 32) T1 <<= 1;
+  while (T1 < t1 && T1 < cap) T1 <<= 1;
   switch (T1) {
     CTL_BSGS_CASE(1)
     CTL_BSGS_CASE(2)

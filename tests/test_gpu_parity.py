@@ -449,3 +449,29 @@ def test_ntt_shapes_agree_on_a_16384_network(lazy):
         y = g.decrypt(k, out.slice(0), len(ref))
         assert np.max(np.abs(y - ref)) < TOL
     assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("chunk,kara", [(32, 0), (32, 1), (16, 0), (16, 1)])
+def test_bsgs_shapes_bit_exact(chunk, kara):
+    """Every shape of the inner-sum kernel (baby steps held per thread, three or four
+    multiply-adds per split product) gives the oracle's dense layer, with t1 = 64 > chunk."""
+    P = pair("c2")
+    m = n = 256  # t = 256: t1 = 16 (default split) and 32 (lazy split)
+    for lazy in (False, True):
+        rots = sorted(set(O.Oracle.bsgs_rotations(m, n, lazy)))
+        o = O.Oracle(P.N, *PARAMS["c2"][1:3], dnum=PARAMS["c2"][3], scale=2.0 ** 40)
+        o.keygen(rots, seed=3)
+        k = P.g.keygen(rots, seed=3)
+        W, x, t, ct_o = dense_case(P, m, n, 91)
+        sc = o.dense_scale(ct_o.shape[1])
+        pts = o.encode_diagonals(W, sc, lazy)
+        exp, _ = o.dense(ct_o, pts, lazy=lazy)
+        P.g.set_bsgs_shape(chunk, kara)
+        P.g.set_dense_mode(P.g.DENSE_LAZY_MODDOWN if lazy else P.g.DENSE_COMPOSED)
+        try:
+            out = P.g.dense_coeffs(k, P.g.ct_import(ct_o, 2.0 ** 40), pts, sc)
+            assert np.array_equal(out.export()[0], exp)
+        finally:
+            P.g.set_bsgs_shape(32, 1)
+            P.g.set_dense_mode(P.g.DENSE_COMPOSED)
+        k.close()
