@@ -78,8 +78,13 @@ __device__ __forceinline__ void fwd_regs(u64* x, int b, const ulonglong2* __rest
     }
   }
 }
-template <int S0, int LOGR>
-__device__ __forceinline__ void inv_regs(u64* x, int b, const ulonglong2* __restrict__ tw, u64 q, const DPrime& P) {
+// The last-stage constants of an inverse transform (N^-1 and the folded last twiddle).
+struct InvLast {
+  u64 ninv, ninv_sh, iw1, iw1_sh;
+};
+
+template <int S0, int LOGR, class PL>
+__device__ __forceinline__ void inv_regs(u64* x, int b, const ulonglong2* __restrict__ tw, u64 q, const PL& P) {
   constexpr int R = 1 << LOGR;
 #pragma unroll
   for (int u = LOGR - 1; u >= 0; u--) {
@@ -766,42 +771,32 @@ struct Pass16 {
     const int u = t + T * i;
     return (u / D) * (N >> S0) + (u % D) + k * D;
   }
-  // pidx(pos(t, i, k)) = pidx(pos(t, i, 0)) + k * DP whenever D is a multiple of 16 or a
-  // sub-transform stays inside one 16-element group (R * D <= 16): then one address per
-  // sub-transform and compile-time offsets suffice.
-  static constexpr bool AFFINE = (D % 16 == 0) || (R * D <= 16);
-  static constexpr int DP = (D % 16 == 0) ? D + D / 16 : D;
+  // pidx(pos(t, i, k)) = pidx(pos(t, i, 0)) + OFF(k) with OFF(k) = k*D + (k*D >> 4): the
+  // first element of a sub-transform is o (mod D*R) with o < D, and D*R is a multiple of
+  // 16 or the whole sub-transform stays inside one 16-element group.  So a sub-transform
+  // needs one address register and compile-time offsets.
+  __device__ __forceinline__ static constexpr int OFF(int k) { return k * D + ((k * D) >> 4); }
   __device__ __forceinline__ static void load(u64* x, const u64* smem, int t) {
 #pragma unroll
     for (int i = 0; i < NS; i++) {
-      if constexpr (AFFINE) {
-        const u64* s = smem + pidx(pos(t, i, 0));
+      const u64* s = smem + pidx(pos(t, i, 0));
 #pragma unroll
-        for (int k = 0; k < R; k++) x[i * R + k] = s[k * DP];
-      } else {
-#pragma unroll
-        for (int k = 0; k < R; k++) x[i * R + k] = smem[pidx(pos(t, i, k))];
-      }
+      for (int k = 0; k < R; k++) x[i * R + k] = s[OFF(k)];
     }
   }
   __device__ __forceinline__ static void store(const u64* x, u64* smem, int t) {
 #pragma unroll
     for (int i = 0; i < NS; i++) {
-      if constexpr (AFFINE) {
-        u64* s = smem + pidx(pos(t, i, 0));
+      u64* s = smem + pidx(pos(t, i, 0));
 #pragma unroll
-        for (int k = 0; k < R; k++) s[k * DP] = x[i * R + k];
-      } else {
-#pragma unroll
-        for (int k = 0; k < R; k++) smem[pidx(pos(t, i, k))] = x[i * R + k];
-      }
+      for (int k = 0; k < R; k++) s[OFF(k)] = x[i * R + k];
     }
   }
   __device__ __forceinline__ static void fwd(u64* x, int t, const ulonglong2* W, u64 q) {
 #pragma unroll
     for (int i = 0; i < NS; i++) fwd_regs<S0, LOGR>(x + i * R, blk(t, i), W, q);
   }
-  __device__ __forceinline__ static void inv(u64* x, int t, const ulonglong2* W, u64 q, const DPrime& P) {
+  __device__ __forceinline__ static void inv(u64* x, int t, const ulonglong2* W, u64 q, const InvLast& P) {
 #pragma unroll
     for (int i = 0; i < NS; i++) inv_regs<S0, LOGR>(x + i * R, blk(t, i), W, q, P);
   }
@@ -897,15 +892,14 @@ k_ntti_r16(const __grid_constant__ Pro pro, const __grid_constant__ Epi epi, con
         pro.prefetch_src(p2, l2, l2 < lvl ? l2 : L + (l2 - lvl), LOGN);
       }
     }
-    DPrime P = primes[pi];
+    const u64 q = primes[pi].q;
+    InvLast P;
     if (scl) {  // output also multiplied by the factor folded into scl[pi]
       const InvScale f = scl[pi];
-      P.ninv = f.ninv;
-      P.ninv_sh = f.ninv_sh;
-      P.iw1 = f.iw1;
-      P.iw1_sh = f.iw1_sh;
+      P = InvLast{f.ninv, f.ninv_sh, f.iw1, f.iw1_sh};
+    } else {
+      P = InvLast{primes[pi].ninv, primes[pi].ninv_sh, primes[pi].iw1, primes[pi].iw1_sh};
     }
-    const u64 q = P.q;
     const ulonglong2* W = tw + ((size_t)pi << LOGN);
     u64 x[16];
 #pragma unroll 8
