@@ -202,11 +202,16 @@ struct ConvState {
     t = tq;
     tinv = ti;
   }
+  // The source limbs are read-only in the launch (non-coherent loads, free to be issued
+  // ahead of the kernel's shared-memory stores).
   __device__ u64 eval(int k) const {
     u64 lo = 0, hi = 0;
 #pragma unroll
     for (int j = 0; j < NS; j++)
-      if (j < ns) mac(lo, hi, premul ? srcs[j][k] : shoup(srcs[j][k], sinv[j], sinv_sh[j], sq[j]), cm[j]);
+      if (j < ns) {
+        const u64 v = __ldg(srcs[j] + k);
+        mac(lo, hi, premul ? v : shoup(v, sinv[j], sinv_sh[j], sq[j]), cm[j]);
+      }
     return redc(hi, lo, t, tinv);
   }
   // C elements t0 + T*k of one thread: every source load is issued before any arithmetic
@@ -345,9 +350,11 @@ struct EpiModDown {
     if (st.ad) l2_prefetch(st.ad, 8u << logN);
     if (accum) l2_prefetch(st.o, 8u << logN);
   }
+  // acc and the addend are read-only in this launch (non-coherent loads), so the loads of
+  // several elements can be issued ahead of the stores of earlier ones
   __device__ void put(const State& st, int j, u64 v) const {
-    u64 r = shoup(submod(st.a[j], reduce4(v, st.q), st.q), st.pv, st.pvs, st.q);
-    if (st.ad) r = addmod(r, st.ad[st.gg == 1 ? (uint32_t)j : auto_src((uint32_t)j, st.gg, st.lg)], st.q);
+    u64 r = shoup(submod(__ldg(st.a + j), reduce4(v, st.q), st.q), st.pv, st.pvs, st.q);
+    if (st.ad) r = addmod(r, __ldg(st.ad + (st.gg == 1 ? (uint32_t)j : auto_src((uint32_t)j, st.gg, st.lg))), st.q);
     if (accum) r = addmod(r, st.o[j], st.q);
     st.o[j] = r;
   }

@@ -475,3 +475,52 @@ def test_bsgs_shapes_bit_exact(chunk, kara):
             P.g.set_bsgs_shape(32, 1)
             P.g.set_dense_mode(P.g.DENSE_COMPOSED)
         k.close()
+
+
+def _fp64_forward(Ws, x, square_last):
+    h = x
+    for i, W in enumerate(Ws):
+        h = W @ h
+        if i + 1 < len(Ws) or square_last:
+            h = h * h
+    return h
+
+
+@pytest.mark.parametrize("name,N,qb,pb,dnum,dims,B", [
+    ("cfg2", 8192, [60, 40, 40, 40], [60], 4, [512, 128, 64], 2),
+    ("cfg3", 16384, [45] * 8, [60, 60], 4, [1024, 256, 256, 64], 8),
+])
+def test_full_size_networks_properties(name, N, qb, pb, dnum, dims, B):
+    """The single-query (N = 8192) and batched (N = 16384) networks at their full sizes,
+    in the launch configuration bench.py times: every decoded output within 1e-4 of the
+    FP64 network, each ciphertext of the batch bit-identical to its forward alone, the
+    CUDA-graph replay bit-identical to the eager forward, and two runs identical."""
+    rng = np.random.default_rng(1)
+    Ws = [rng.normal(0, 1 / np.sqrt(dims[i]), (dims[i + 1], dims[i])) for i in range(len(dims) - 1)]
+    layers = []
+    for i, W in enumerate(Ws):
+        layers.append(("dense", W))
+        if i + 1 < len(Ws):
+            layers += [("square",), ("replicate", O.Oracle.bsgs_t(*Ws[i + 1].shape))]
+    t0 = O.Oracle.bsgs_t(*Ws[0].shape)
+    g = ctl.Context(N, qb, pb, dnum=dnum, scale=2.0 ** 40)
+    model = ctl.Model(g, layers)
+    k = g.keygen(model.rotations(), seed=3)
+    xs, cts = [], []
+    for i in range(B):
+        x = rng.uniform(-1, 1, dims[0])
+        s = np.zeros(N // 2)
+        s[:dims[0]] = x
+        s[t0:t0 + dims[0]] = x
+        xs.append(x)
+        cts.append(g.encrypt(k, s, 4 + i))
+    batch = g.concat(cts)
+    out = model.forward(k, batch)
+    got = out.export()
+    for i in range(B):
+        y = g.decrypt(k, out.slice(i), dims[-1])
+        assert np.max(np.abs(y - _fp64_forward(Ws, xs[i], False))) < TOL
+    for i in (0, B - 1):
+        assert np.array_equal(model.forward(k, cts[i]).export()[0], got[i])
+    assert np.array_equal(model.forward(k, batch, graph=True).export(), got)
+    assert np.array_equal(model.forward(k, batch).export(), got)
