@@ -190,11 +190,12 @@ static int build_tables(ctl_context* c) {
     P.iw1_sh = h_shoup(P.iw1, q);
     const unsigned bits = 64 - __builtin_clzll(q);
     P.split = bits <= 54 ? (bits + 1) / 2 : 0;
+    P.bar = q > (1ull << 32) ? (u64)((((unsigned __int128)1) << 64) / q) : 0;
   }
   // conversion tables, packed into one host vector then copied to the device
   std::vector<u64> tab;
   struct Pending {
-    size_t sinv, sinv_sh, sq, cmont;
+    size_t c, c_sh;
     int ns, nt;
   };
   std::vector<Pending> modup_p;
@@ -202,27 +203,19 @@ static int build_tables(ctl_context* c) {
     Pending pd;
     pd.ns = (int)src.size();
     pd.nt = (int)tgt.size();
-    pd.sinv = tab.size();
-    for (uint32_t sj : src) {
-      u64 qs = m[sj], prod = 1 % qs;
-      for (uint32_t so : src)
-        if (so != sj) prod = h_mulmod(prod, m[so] % qs, qs);
-      tab.push_back(h_invmod(prod, qs));
-    }
-    pd.sinv_sh = tab.size();
-    for (int j = 0; j < pd.ns; j++) tab.push_back(h_shoup(tab[pd.sinv + j], m[src[j]]));
-    pd.sq = tab.size();
-    for (uint32_t sj : src) tab.push_back(m[sj]);
-    pd.cmont = tab.size();
+    pd.c = tab.size();
     for (uint32_t sj : src) {
       for (uint32_t ti : tgt) {
         const u64 qt = m[ti];
         u64 prod = 1 % qt;
         for (uint32_t so : src)
           if (so != sj) prod = h_mulmod(prod, m[so] % qt, qt);
-        tab.push_back(h_mont(prod, qt));
+        tab.push_back(prod);
       }
     }
+    pd.c_sh = tab.size();
+    for (int j = 0; j < pd.ns; j++)
+      for (int i = 0; i < pd.nt; i++) tab.push_back(h_shoup(tab[pd.c + (size_t)j * pd.nt + i], m[tgt[i]]));
     return pd;
   };
   for (uint32_t lvl = 1; lvl <= L; lvl++) {
@@ -277,11 +270,8 @@ static int build_tables(ctl_context* c) {
     ConvTab t;
     t.ns = p.ns;
     t.nt = p.nt;
-    t.sinv = c->d_tables + p.sinv;
-    t.sinv_sh = c->d_tables + p.sinv_sh;
-    t.sq = c->d_tables + p.sq;
-    t.cmont = c->d_tables + p.cmont;
-    t.premul = 1;  // the inverse NTT before every conversion folds in Shat_j^-1
+    t.c = c->d_tables + p.c;
+    t.c_sh = c->d_tables + p.c_sh;
     return t;
   };
   for (auto& p : modup_p) c->modup_tabs.push_back(mk(p));

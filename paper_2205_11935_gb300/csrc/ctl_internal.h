@@ -27,18 +27,19 @@ struct DPrime {
   u64 ninv, ninv_sh;  // N^-1 mod q and its Shoup companion
   u64 iw1, iw1_sh;    // (psi^-1)^{bitrev(1)} * N^-1: the folded last inverse twiddle
   u64 split;          // w = ceil(bits(q)/2) when q < 2^54 (operands split into w-bit halves), else 0
+  u64 bar;            // floor(2^64 / q) when 2^32 < q (reduce_wide), else 0
 };
 
 // Fast base conversion from a set of source primes S to target primes:
 //   y_i = sum_{j in S} [x_j * Shat_j^-1]_{s_j} * (Shat_j mod t_i)  mod t_i.
+// The source limbs arrive with the factor Shat_j^-1 already applied (it is folded into the
+// inverse NTT that precedes every conversion), so a conversion is a sum of products with
+// the constants Shat_j mod t_i, taken in Shoup form.
 struct ConvTab {
   int ns;               // |S|
   int nt;               // number of target positions
-  int premul;           // 1: the source limbs already carry the factor Shat_j^-1 mod s_j
-  const u64* sinv;      // [ns] Shat_j^-1 mod s_j
-  const u64* sinv_sh;   // [ns] Shoup companions
-  const u64* sq;        // [ns] source primes
-  const u64* cmont;     // [ns][nt] (Shat_j mod t_i) * 2^64 mod t_i
+  const u64* c;         // [ns][nt] Shat_j mod t_i
+  const u64* c_sh;      // [ns][nt] floor(c * 2^64 / t_i)
 };
 
 // Rescale constants for dropping the last prime of a level-lvl ciphertext.

@@ -6,7 +6,8 @@
 // Forward: Cooley-Tukey butterflies with the psi powers merged (twiddle of stage m,
 // group i: psi^bitrev(m+i)); inverse: Gentleman-Sande butterflies with
 // (psi^-1)^bitrev(m+i) and N^-1 folded into the last stage.  Values stay lazily reduced
-// (Harvey): forward butterflies keep [0, 4q), inverse [0, 2q); q < 2^62.  Twiddles are
+// (Harvey): forward butterflies keep [0, 4q), inverse [0, 2q); q < 2^62 (primes below
+// 2^56 take a path with fewer reductions, described at ct_bfly).  Twiddles are
 // stored as interleaved (w, floor(w * 2^64 / q)) pairs and read with one 16-byte load.
 //
 // GPU mapping.  For N in {4096, 8192, 16384} one CTA of N/32 threads owns a limb and
@@ -45,14 +46,29 @@ __device__ __forceinline__ void l2_prefetch(const void* p, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(g), "r"(bytes) : "memory");
 }
 
+// Harvey butterflies.  Forward: X is brought below 2q, outputs stay below 4q.  With
+// SMALL (2^32 < q < 2^56) X is left as it is and the twiddle product is shoup_small
+// (below 4q): each stage adds less than 4q to the bound, so an input below q leaves the
+// 14 stages of N = 16384 below 57q, and the store reduces once.
+template <bool SMALL = false>
 __device__ __forceinline__ void ct_bfly(u64& x, u64& y, const ulonglong2 w, u64 q) {
-  const u64 q2 = 2 * q;
   u64 X = x;
-  if (X >= q2) X -= q2;
-  const u64 T = shoup_lazy(y, w.x, w.y, q);
-  x = X + T;
-  y = X - T + q2;
+  if constexpr (!SMALL) {
+    const u64 q2 = 2 * q;
+    if (X >= q2) X -= q2;
+    const u64 T = shoup_lazy(y, w.x, w.y, q);
+    x = X + T;
+    y = X - T + q2;
+  } else {
+    // keeps the butterflies in program order: left free, the scheduler interleaves enough
+    // of them to run out of registers
+    asm volatile("" : "+l"(X));
+    const u64 T = shoup_small(y, w.x, w.y, q);
+    x = X + T;
+    y = X - T + 4 * q;
+  }
 }
+// Inverse: inputs below 2q, outputs below 2q (the sum reduced once).
 __device__ __forceinline__ void gs_bfly(u64& x, u64& y, const ulonglong2 w, u64 q) {
   const u64 q2 = 2 * q;
   const u64 U = x, V = y;
@@ -61,10 +77,18 @@ __device__ __forceinline__ void gs_bfly(u64& x, u64& y, const ulonglong2 w, u64 
   x = S;
   y = shoup_lazy(U - V + q2, w.x, w.y, q);
 }
+// Inverse without reduction of the sum (q * 2^logN < 2^63): V is below the multiple
+// C >= 2q of q that bounds this stage's inputs, the sum below 2C (the next stage's
+// bound), the difference path below 4q after its shoup_small product.
+__device__ __forceinline__ void gs_bfly_s(u64& x, u64& y, const ulonglong2 w, u64 q, u64 C) {
+  const u64 U = x, V = y;
+  x = U + V;
+  y = shoup_small(U - V + C, w.x, w.y, q);
+}
 
 // LOGR stages of a radix-2^LOGR sub-transform held in registers x[0..2^LOGR), for the
 // stages S0..S0+LOGR-1 and block index b at stage S0.
-template <int S0, int LOGR>
+template <int S0, int LOGR, bool SMALL = false>
 __device__ __forceinline__ void fwd_regs(u64* x, int b, const ulonglong2* __restrict__ tw, u64 q) {
   constexpr int R = 1 << LOGR;
 #pragma unroll
@@ -74,7 +98,7 @@ __device__ __forceinline__ void fwd_regs(u64* x, int b, const ulonglong2* __rest
 #pragma unroll
     for (int k = 0; k < R; k++) {
       if (k & h) continue;
-      ct_bfly(x[k], x[k + h], __ldg(tu + (k >> (LOGR - u))), q);
+      ct_bfly<SMALL>(x[k], x[k + h], __ldg(tu + (k >> (LOGR - u))), q);
     }
   }
 }
@@ -83,20 +107,32 @@ struct InvLast {
   u64 ninv, ninv_sh, iw1, iw1_sh;
 };
 
-template <int S0, int LOGR, class PL>
+// Inverse stages S0+LOGR-1 .. S0.  With SMALL (q * 2^LOGN < 2^63) the inputs of stage s
+// are below C_s = q * 2^(LOGN - s) (2q at the first stage, doubling per stage) and no sum
+// is reduced; the last stage's two products bring both outputs below 4q (below 2q on the
+// general path).
+template <int S0, int LOGR, class PL, bool SMALL = false, int LOGN = 0>
 __device__ __forceinline__ void inv_regs(u64* x, int b, const ulonglong2* __restrict__ tw, u64 q, const PL& P) {
   constexpr int R = 1 << LOGR;
 #pragma unroll
   for (int u = LOGR - 1; u >= 0; u--) {
     const int h = R >> (u + 1);
     const ulonglong2* tu = tw + (1 << (S0 + u)) + (b << u);
+    const u64 C = SMALL ? q << (LOGN - (S0 + u)) : 2 * q;
 #pragma unroll
     for (int k = 0; k < R; k++) {
       if (k & h) continue;
       if (S0 + u == 0) {  // last stage: fold N^-1
         const u64 U = x[k], V = x[k + h];
-        x[k] = shoup_lazy(U + V, P.ninv, P.ninv_sh, q);
-        x[k + h] = shoup_lazy(U - V + 2 * q, P.iw1, P.iw1_sh, q);
+        if constexpr (SMALL) {
+          x[k] = shoup_small(U + V, P.ninv, P.ninv_sh, q);
+          x[k + h] = shoup_small(U - V + C, P.iw1, P.iw1_sh, q);
+        } else {
+          x[k] = shoup_lazy(U + V, P.ninv, P.ninv_sh, q);
+          x[k + h] = shoup_lazy(U - V + C, P.iw1, P.iw1_sh, q);
+        }
+      } else if constexpr (SMALL) {
+        gs_bfly_s(x[k], x[k + h], __ldg(tu + (k >> (LOGR - u))), q, C);
       } else {
         gs_bfly(x[k], x[k + h], __ldg(tu + (k >> (LOGR - u))), q);
       }
@@ -104,16 +140,23 @@ __device__ __forceinline__ void inv_regs(u64* x, int b, const ulonglong2* __rest
   }
 }
 
+// Which path a limb's transform takes (the same answer for every thread of a block).
+__device__ __forceinline__ bool fwd_small(const DPrime& P) { return P.bar != 0 && P.q < (1ull << 56); }
+__device__ __forceinline__ bool inv_small(u64 q, int logN) { return q < (1ull << (63 - logN)); }
+
 // ---------------------------------------------------------------------------------
 // Element functors.  A functor is a constant kernel parameter (__grid_constant__, so
 // its tables are read in place); its per-item state lives in a small State struct.
 // begin(st, p, l, pi, ...) binds item (poly p, limb l, prime pi) and returns false if
 // the item is complete already (the same answer for the whole block); get(st, j)
-// yields input element j (reduced, < q); put(st, j, v) consumes output element j given
-// lazily reduced (< 4q).
+// yields input element j (reduced, < q); put<SMALL>(st, j, v) consumes output element j
+// given lazily reduced: below 4q, or below 64q with SMALL (the forward transform's
+// small-prime path, q < 2^56).
 // ---------------------------------------------------------------------------------
 struct ProLoad {
-  static constexpr bool kStage = false;
+  // inputs parked in shared memory first as well: with all loads of a thread in flight
+  // in registers, the forward transform runs out of registers
+  static constexpr bool kStage = true;
   const u64* src;
   size_t poly_stride;
   struct State {
@@ -127,31 +170,30 @@ struct ProLoad {
   __device__ void prefetch_src(int p, int l, int, int logN) const {
     l2_prefetch(src + (size_t)p * poly_stride + ((size_t)l << logN), 8u << logN);
   }
-  template <int T, int C>
-  __device__ void getc(const State& st, int t0, u64* x) const {
-#pragma unroll
-    for (int k = 0; k < C; k++) x[k] = st.g[t0 + T * k];
-  }
 };
+
+// Full reduction of an output element: below 4q, or below 64q on the small-prime path.
+template <bool SMALL>
+__device__ __forceinline__ u64 reduce_out(u64 v, u64 q, u64 bar) {
+  if constexpr (SMALL) return reduce_wide(v, q, bar);
+  else return reduce4(v, q);
+}
 
 struct EpiStore {
   u64* dst;
   size_t poly_stride;
   struct State {
     u64* o;
-    u64 q;
+    u64 q, bar;
   };
   __device__ void begin(State& st, int p, int l, int pi, const DPrime* pr, int logN) const {
     st.o = dst + (size_t)p * poly_stride + ((size_t)l << logN);
     st.q = pr[pi].q;
+    st.bar = pr[pi].bar;
   }
-  __device__ void put(const State& st, int j, u64 v) const { st.o[j] = reduce4(v, st.q); }
+  template <bool SMALL = false>
+  __device__ void put(const State& st, int j, u64 v) const { st.o[j] = reduce_out<SMALL>(v, st.q, st.bar); }
   __device__ void prefetch(const State&, int) const {}
-  template <int T, int C>
-  __device__ void putc(const State& st, int t0, const u64* x) const {
-#pragma unroll
-    for (int k = 0; k < C; k++) st.o[t0 + T * k] = reduce4(x[k], st.q);
-  }
 };
 
 // Store of ModUp digits for the key product: on limbs whose prime has a split width w,
@@ -162,80 +204,56 @@ struct EpiStoreSplit {
   size_t poly_stride;
   struct State {
     u64* o;
-    u64 q, mask;
+    u64 q, mask, bar;
     int w;
   };
   __device__ void begin(State& st, int p, int l, int pi, const DPrime* pr, int logN) const {
     st.o = dst + (size_t)p * poly_stride + ((size_t)l << logN);
     st.q = pr[pi].q;
+    st.bar = pr[pi].bar;
     st.w = (int)pr[pi].split;
     st.mask = st.w ? (1ull << st.w) - 1 : ~0ull;
   }
+  template <bool SMALL = false>
   __device__ void put(const State& st, int j, u64 v) const {
-    const u64 r = reduce4(v, st.q);
+    const u64 r = reduce_out<SMALL>(v, st.q, st.bar);
     st.o[j] = st.w ? ((r >> st.w) << 32) | (r & st.mask) : r;
   }
   __device__ void prefetch(const State&, int) const {}
 };
 
-// Fast base conversion of one element: y = sum_j [x_j * Shat_j^-1]_{s_j} * (Shat_j mod t)
-// mod t over the ns <= NS source limbs, the constants Shat_j mod t in Montgomery form;
-// exact residue in [0, t).
+// Fast base conversion of one element: y = sum_j v_j * (Shat_j mod t) mod t over the
+// ns <= NS source limbs, v_j = [x_j * Shat_j^-1]_{s_j} as stored by the inverse NTT that
+// precedes the conversion; exact residue in [0, t).  Each product is a shoup_small (below
+// 4t, for any source value) and the running sum stays below 4t (t < 2^61).
 template <int NS>
 struct ConvState {
-  int ns, premul;
+  int ns;
   const u64* srcs[NS];
-  u64 sinv[NS], sinv_sh[NS], sq[NS], cm[NS];
-  u64 t, tinv;
-  __device__ void bind(const ConvTab& T, int tpos, const u64* base, size_t limb0, int logN, u64 tq, u64 ti) {
+  u64 c[NS], c_sh[NS];
+  u64 t;
+  __device__ void bind(const ConvTab& T, int tpos, const u64* base, size_t limb0, int logN, u64 tq) {
     ns = T.ns;
-    premul = T.premul;
 #pragma unroll
     for (int j = 0; j < NS; j++) {
       const int jj = j < ns ? j : 0;
       srcs[j] = base + ((limb0 + jj) << logN);
-      sinv[j] = __ldg(T.sinv + jj);
-      sinv_sh[j] = __ldg(T.sinv_sh + jj);
-      sq[j] = __ldg(T.sq + jj);
-      cm[j] = __ldg(T.cmont + (size_t)jj * T.nt + tpos);
+      c[j] = __ldg(T.c + (size_t)jj * T.nt + tpos);
+      c_sh[j] = __ldg(T.c_sh + (size_t)jj * T.nt + tpos);
     }
     t = tq;
-    tinv = ti;
   }
   // The source limbs are read-only in the launch (non-coherent loads, free to be issued
   // ahead of the kernel's shared-memory stores).
   __device__ u64 eval(int k) const {
-    u64 lo = 0, hi = 0;
+    u64 s = 0;
 #pragma unroll
     for (int j = 0; j < NS; j++)
       if (j < ns) {
-        const u64 v = __ldg(srcs[j] + k);
-        mac(lo, hi, premul ? v : shoup(v, sinv[j], sinv_sh[j], sq[j]), cm[j]);
+        s += shoup_small(__ldg(srcs[j] + k), c[j], c_sh[j], t);
+        if (s >= 4 * t) s -= 4 * t;
       }
-    return redc(hi, lo, t, tinv);
-  }
-  // C elements t0 + T*k of one thread: every source load is issued before any arithmetic
-  // so that the loads overlap.
-  template <int T, int C>
-  __device__ void evalc(int t0, u64* x) const {
-    if constexpr (NS <= 2) {
-      u64 v[NS][C];
-#pragma unroll
-      for (int j = 0; j < NS; j++)
-#pragma unroll
-        for (int k = 0; k < C; k++) v[j][k] = (j < ns) ? srcs[j][t0 + T * k] : 0;
-#pragma unroll
-      for (int k = 0; k < C; k++) {
-        u64 lo = 0, hi = 0;
-#pragma unroll
-        for (int j = 0; j < NS; j++)
-          if (j < ns) mac(lo, hi, premul ? v[j][k] : shoup(v[j][k], sinv[j], sinv_sh[j], sq[j]), cm[j]);
-        x[k] = redc(hi, lo, t, tinv);
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < C; k++) x[k] = eval(t0 + T * k);
-    }
+    return reduce4(s, t);
   }
 };
 
@@ -266,7 +284,7 @@ struct ProModUp {
       }
       return false;
     }
-    st.bind(tabs[d], l, coef + (size_t)b * coef_stride, (size_t)d0, logN, pr[pi].q, pr[pi].qinv);
+    st.bind(tabs[d], l, coef + (size_t)b * coef_stride, (size_t)d0, logN, pr[pi].q);
     return true;
   }
   __device__ void prefetch_src(int p, int l, int, int logN) const {
@@ -279,10 +297,6 @@ struct ProModUp {
     }
   }
   __device__ u64 get(const State& st, int j) const { return st.eval(j); }
-  template <int T, int C>
-  __device__ void getc(const State& st, int t0, u64* x) const {
-    st.template evalc<T, C>(t0, x);
-  }
 };
 
 template <int NS>
@@ -294,17 +308,13 @@ struct ProModDown {
   ConvTab tab;       // sources: special primes; target position = data limb index
   typedef ConvState<NS> State;
   __device__ bool begin(State& st, int p, int l, int pi, const DPrime* pr, int logN) const {
-    st.bind(tab, l, acc + (size_t)p * acc_stride, (size_t)lvl, logN, pr[pi].q, pr[pi].qinv);
+    st.bind(tab, l, acc + (size_t)p * acc_stride, (size_t)lvl, logN, pr[pi].q);
     return true;
   }
   __device__ void prefetch_src(int p, int, int, int logN) const {
     for (int j = 0; j < tab.ns; j++) l2_prefetch(acc + (size_t)p * acc_stride + ((size_t)(lvl + j) << logN), 8u << logN);
   }
   __device__ u64 get(const State& st, int j) const { return st.eval(j); }
-  template <int T, int C>
-  __device__ void getc(const State& st, int t0, u64* x) const {
-    st.template evalc<T, C>(t0, x);
-  }
 };
 
 struct EpiModDown {
@@ -351,29 +361,15 @@ struct EpiModDown {
     if (accum) l2_prefetch(st.o, 8u << logN);
   }
   // acc and the addend are read-only in this launch (non-coherent loads), so the loads of
-  // several elements can be issued ahead of the stores of earlier ones
+  // several elements can be issued ahead of the stores of earlier ones.  (acc - v) P^-1:
+  // the Shoup product takes acc + c*q - v for the bound c*q of v (4q, or 64q with SMALL).
+  template <bool SMALL = false>
   __device__ void put(const State& st, int j, u64 v) const {
-    u64 r = shoup(submod(__ldg(st.a + j), reduce4(v, st.q), st.q), st.pv, st.pvs, st.q);
+    const u64 cq = SMALL ? 64 * st.q : 4 * st.q;
+    u64 r = shoup(__ldg(st.a + j) + cq - v, st.pv, st.pvs, st.q);
     if (st.ad) r = addmod(r, __ldg(st.ad + (st.gg == 1 ? (uint32_t)j : auto_src((uint32_t)j, st.gg, st.lg))), st.q);
     if (accum) r = addmod(r, st.o[j], st.q);
     st.o[j] = r;
-  }
-  // C elements t0 + T*k of one thread, all loads issued first.
-  template <int T, int C>
-  __device__ void putc(const State& st, int t0, const u64* x) const {
-    u64 a[C], ad[C], ac[C];
-#pragma unroll
-    for (int k = 0; k < C; k++) {
-      const int j = t0 + T * k;
-      a[k] = st.a[j];
-      ad[k] = st.ad ? st.ad[st.gg == 1 ? (uint32_t)j : auto_src((uint32_t)j, st.gg, st.lg)] : 0;
-      ac[k] = accum ? st.o[j] : 0;
-    }
-#pragma unroll
-    for (int k = 0; k < C; k++) {
-      const u64 r = shoup(submod(a[k], reduce4(x[k], st.q), st.q), st.pv, st.pvs, st.q);
-      st.o[t0 + T * k] = addmod(addmod(r, ad[k], st.q), ac[k], st.q);
-    }
   }
 };
 
@@ -390,11 +386,6 @@ struct EpiRescaleLast {   // inverse NTT of the last limb -> r = [x + h]_q_last
   }
   __device__ void put(const State& st, int j, u64 v) const { st.o[j] = addmod(reduce4(v, st.q), h, st.q); }
   __device__ void prefetch(const State&, int) const {}
-  template <int T, int C>
-  __device__ void putc(const State& st, int t0, const u64* x) const {
-#pragma unroll
-    for (int k = 0; k < C; k++) put(st, t0 + T * k, x[k]);
-  }
 };
 
 struct ProRescale {       // (r - h) mod q_i in coefficient form
@@ -417,16 +408,6 @@ struct ProRescale {       // (r - h) mod q_i in coefficient form
     const u64 v = st.g[j];
     return v >= h ? mulmod_mont(v - h, st.rm, st.q, st.qinv) : negmod(mulmod_mont(h - v, st.rm, st.q, st.qinv), st.q);
   }
-  template <int T, int C>
-  __device__ void getc(const State& st, int t0, u64* x) const {
-    u64 v[C];
-#pragma unroll
-    for (int k = 0; k < C; k++) v[k] = st.g[t0 + T * k];
-#pragma unroll
-    for (int k = 0; k < C; k++)
-      x[k] = v[k] >= h ? mulmod_mont(v[k] - h, st.rm, st.q, st.qinv)
-                       : negmod(mulmod_mont(h - v[k], st.rm, st.q, st.qinv), st.q);
-  }
 };
 
 struct EpiRescale {       // out_i = (in_i - x) * q_last^-1
@@ -448,29 +429,67 @@ struct EpiRescale {       // out_i = (in_i - x) * q_last^-1
     st.a = in + (size_t)p * in_stride + ((size_t)l << logN);
     st.o = out + (size_t)p * out_stride + ((size_t)l << logN);
   }
+  // (in - v) q_last^-1 through one Shoup product of in + c*q - v (c*q the bound of v)
+  template <bool SMALL = false>
   __device__ void put(const State& st, int j, u64 v) const {
-    st.o[j] = shoup(submod(st.a[j], reduce4(v, st.q), st.q), st.w, st.ws, st.q);
+    const u64 cq = SMALL ? 64 * st.q : 4 * st.q;
+    st.o[j] = shoup(st.a[j] + cq - v, st.w, st.ws, st.q);
   }
   __device__ void prefetch(const State& st, int logN) const { l2_prefetch(st.a, 8u << logN); }
-  template <int T, int C>
-  __device__ void putc(const State& st, int t0, const u64* x) const {
-    u64 a[C];
-#pragma unroll
-    for (int k = 0; k < C; k++) a[k] = st.a[t0 + T * k];
-#pragma unroll
-    for (int k = 0; k < C; k++) st.o[t0 + T * k] = shoup(submod(a[k], reduce4(x[k], st.q), st.q), st.w, st.ws, st.q);
-  }
 };
 
 // ---------------------------------------------------------------------------------
 // Register-resident kernels, N = 2^LOGN in {4096, 8192, 16384}: N/32 threads.
+// Each limb's transform takes the small-prime path (no reductions inside the stages,
+// one at the store) or the general one; the branch is the same for the whole block.
 // ---------------------------------------------------------------------------------
+// Forward stages and the epilogue of one item, inputs x[k] = element t + T*k.
+template <int LOGN, bool SMALL, class Epi>
+__device__ __forceinline__ void fwd32_body(u64* x, u64* smem, int t, const ulonglong2* __restrict__ W, u64 q,
+                                           const Epi& epi, int p, int l, int pi, const DPrime* __restrict__ primes) {
+  constexpr int N = 1 << LOGN, T = N / 32, RC = LOGN - 10, R = 1 << RC;
+  // stages 0..4: sub-transform on elements t + T*k, block index 0
+  fwd_regs<0, 5, SMALL>(x, 0, W, q);
+#pragma unroll
+  for (int k = 0; k < 32; k++) smem[pidx(t + T * k)] = x[k];
+  __syncthreads();
+  {  // stages 5..9
+    const int b = t >> RC, o = t & (R - 1);
+    const int base = (b << (LOGN - 5)) + o;
+#pragma unroll
+    for (int k = 0; k < 32; k++) x[k] = smem[pidx(base + (k << RC))];
+    fwd_regs<5, 5, SMALL>(x, b, W, q);
+#pragma unroll
+    for (int k = 0; k < 32; k++) smem[pidx(base + (k << RC))] = x[k];
+  }
+  __syncthreads();
+  // stages 10..LOGN-1: 32/R contiguous sub-transforms of R elements per thread
+#pragma unroll
+  for (int i = 0; i < 32 / R; i++) {
+    const int b = t + T * i;
+#pragma unroll
+    for (int k = 0; k < R; k++) x[i * R + k] = smem[pidx(b * R + k)];
+  }
+#pragma unroll
+  for (int i = 0; i < 32 / R; i++) fwd_regs<10, RC, SMALL>(x + i * R, t + T * i, W, q);
+#pragma unroll
+  for (int i = 0; i < 32 / R; i++) {
+    const int b = t + T * i;
+#pragma unroll
+    for (int k = 0; k < R; k++) smem[pidx(b * R + k)] = x[i * R + k];
+  }
+  __syncthreads();
+  typename Epi::State es;
+  epi.begin(es, p, l, pi, primes, LOGN);
+#pragma unroll 8
+  for (int k = 0; k < 32; k++) epi.template put<SMALL>(es, t + T * k, smem[pidx(t + T * k)]);
+}
+
 template <int LOGN, class Pro, class Epi>
 __global__ void __launch_bounds__((1 << LOGN) / 32, 16384 / (1 << LOGN))
 k_nttf_reg(const __grid_constant__ Pro pro, const __grid_constant__ Epi epi, const DPrime* __restrict__ primes,
-                                                               const ulonglong2* __restrict__ tw, int n_items, int lr,
-                                                               int limb_lo, int lvl, int L) {
-  constexpr int N = 1 << LOGN, T = N / 32, RC = LOGN - 10, R = 1 << RC;
+           const ulonglong2* __restrict__ tw, int n_items, int lr, int limb_lo, int lvl, int L) {
+  constexpr int N = 1 << LOGN, T = N / 32;
   extern __shared__ u64 smem[];
   const int t = threadIdx.x;
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
@@ -478,9 +497,9 @@ k_nttf_reg(const __grid_constant__ Pro pro, const __grid_constant__ Epi epi, con
     const int pi = l < lvl ? l : L + (l - lvl);
     typename Pro::State ps;
     if (!pro.begin(ps, p, l, pi, primes, LOGN)) continue;
-    typename Epi::State es;
-    epi.begin(es, p, l, pi, primes, LOGN);
     if (threadIdx.x == 0) {  // L2 prefetch: this item's epilogue reads, the next item's sources
+      typename Epi::State es;  // bound again after the transform (not live through it)
+      epi.begin(es, p, l, pi, primes, LOGN);
       epi.prefetch(es, LOGN);
       const int nx = item + gridDim.x;
       if (nx < n_items) {
@@ -488,7 +507,8 @@ k_nttf_reg(const __grid_constant__ Pro pro, const __grid_constant__ Epi epi, con
         pro.prefetch_src(p2, l2, l2 < lvl ? l2 : L + (l2 - lvl), LOGN);
       }
     }
-    const u64 q = primes[pi].q;
+    const DPrime& P = primes[pi];
+    const u64 q = P.q;
     const ulonglong2* W = tw + ((size_t)pi << LOGN);
     u64 x[32];
     if constexpr (Pro::kStage) {
@@ -502,49 +522,63 @@ k_nttf_reg(const __grid_constant__ Pro pro, const __grid_constant__ Epi epi, con
 #pragma unroll
       for (int k = 0; k < 32; k++) x[k] = pro.get(ps, t + T * k);
     }
-    // stages 0..4: sub-transform on elements t + T*k, block index 0
-    fwd_regs<0, 5>(x, 0, W, q);
-#pragma unroll
-    for (int k = 0; k < 32; k++) smem[pidx(t + T * k)] = x[k];
-    __syncthreads();
-    {  // stages 5..9
-      const int b = t >> RC, o = t & (R - 1);
-      const int base = (b << (LOGN - 5)) + o;
-#pragma unroll
-      for (int k = 0; k < 32; k++) x[k] = smem[pidx(base + (k << RC))];
-      fwd_regs<5, 5>(x, b, W, q);
-#pragma unroll
-      for (int k = 0; k < 32; k++) smem[pidx(base + (k << RC))] = x[k];
-    }
-    __syncthreads();
-    // stages 10..LOGN-1: 32/R contiguous sub-transforms of R elements per thread
-#pragma unroll
-    for (int i = 0; i < 32 / R; i++) {
-      const int b = t + T * i;
-#pragma unroll
-      for (int k = 0; k < R; k++) x[i * R + k] = smem[pidx(b * R + k)];
-    }
-#pragma unroll
-    for (int i = 0; i < 32 / R; i++) fwd_regs<10, RC>(x + i * R, t + T * i, W, q);
-#pragma unroll
-    for (int i = 0; i < 32 / R; i++) {
-      const int b = t + T * i;
-#pragma unroll
-      for (int k = 0; k < R; k++) smem[pidx(b * R + k)] = x[i * R + k];
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int k = 0; k < 32; k++) epi.put(es, t + T * k, smem[pidx(t + T * k)]);
+    if (fwd_small(P))
+      fwd32_body<LOGN, true>(x, smem, t, W, q, epi, p, l, pi, primes);
+    else
+      fwd32_body<LOGN, false>(x, smem, t, W, q, epi, p, l, pi, primes);
     __syncthreads();
   }
+}
+
+// Inverse stages of one item from shared memory (its inputs stored there), outputs to
+// the epilogue (below 4q).
+template <int LOGN, bool SMALL, class Epi>
+__device__ __forceinline__ void inv32_body(u64* x, u64* smem, int t, const ulonglong2* __restrict__ W, u64 q,
+                                           const DPrime& P, const Epi& epi, int p, int l, int pi,
+                                           const DPrime* __restrict__ primes) {
+  constexpr int N = 1 << LOGN, T = N / 32, RC = LOGN - 10, R = 1 << RC;
+  // stages LOGN-1..10 on contiguous sub-transforms
+#pragma unroll
+  for (int i = 0; i < 32 / R; i++) {
+    const int b = t + T * i;
+#pragma unroll
+    for (int k = 0; k < R; k++) x[i * R + k] = smem[pidx(b * R + k)];
+  }
+#pragma unroll
+  for (int i = 0; i < 32 / R; i++) inv_regs<10, RC, DPrime, SMALL, LOGN>(x + i * R, t + T * i, W, q, P);
+#pragma unroll
+  for (int i = 0; i < 32 / R; i++) {
+    const int b = t + T * i;
+#pragma unroll
+    for (int k = 0; k < R; k++) smem[pidx(b * R + k)] = x[i * R + k];
+  }
+  __syncthreads();
+  {  // stages 9..5
+    const int b = t >> RC, o = t & (R - 1);
+    const int base = (b << (LOGN - 5)) + o;
+#pragma unroll
+    for (int k = 0; k < 32; k++) x[k] = smem[pidx(base + (k << RC))];
+    inv_regs<5, 5, DPrime, SMALL, LOGN>(x, b, W, q, P);
+#pragma unroll
+    for (int k = 0; k < 32; k++) smem[pidx(base + (k << RC))] = x[k];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 32; k++) x[k] = smem[pidx(t + T * k)];
+  // stages 4..0 (N^-1 folded into stage 0), outputs straight to global
+  inv_regs<0, 5, DPrime, SMALL, LOGN>(x, 0, W, q, P);
+  typename Epi::State es;
+  epi.begin(es, p, l, pi, primes, LOGN);
+#pragma unroll
+  for (int k = 0; k < 32; k++) epi.put(es, t + T * k, x[k]);
 }
 
 template <int LOGN, class Pro, class Epi>
 __global__ void __launch_bounds__((1 << LOGN) / 32, 16384 / (1 << LOGN))
 k_ntti_reg(const __grid_constant__ Pro pro, const __grid_constant__ Epi epi, const DPrime* __restrict__ primes,
-                                                               const ulonglong2* __restrict__ tw, int n_items, int lr,
-                                                               int limb_lo, int lvl, int L, const InvScale* __restrict__ scl) {
-  constexpr int N = 1 << LOGN, T = N / 32, RC = LOGN - 10, R = 1 << RC;
+           const ulonglong2* __restrict__ tw, int n_items, int lr, int limb_lo, int lvl, int L,
+           const InvScale* __restrict__ scl) {
+  constexpr int N = 1 << LOGN, T = N / 32;
   extern __shared__ u64 smem[];
   const int t = threadIdx.x;
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
@@ -552,9 +586,9 @@ k_ntti_reg(const __grid_constant__ Pro pro, const __grid_constant__ Epi epi, con
     const int pi = l < lvl ? l : L + (l - lvl);
     typename Pro::State ps;
     if (!pro.begin(ps, p, l, pi, primes, LOGN)) continue;
-    typename Epi::State es;
-    epi.begin(es, p, l, pi, primes, LOGN);
     if (threadIdx.x == 0) {  // L2 prefetch: this item's epilogue reads, the next item's sources
+      typename Epi::State es;  // bound again after the transform (not live through it)
+      epi.begin(es, p, l, pi, primes, LOGN);
       epi.prefetch(es, LOGN);
       const int nx = item + gridDim.x;
       if (nx < n_items) {
@@ -576,38 +610,10 @@ k_ntti_reg(const __grid_constant__ Pro pro, const __grid_constant__ Epi epi, con
 #pragma unroll 8
     for (int k = 0; k < 32; k++) smem[pidx(t + T * k)] = pro.get(ps, t + T * k);
     __syncthreads();
-    // stages LOGN-1..10 on contiguous sub-transforms
-#pragma unroll
-    for (int i = 0; i < 32 / R; i++) {
-      const int b = t + T * i;
-#pragma unroll
-      for (int k = 0; k < R; k++) x[i * R + k] = smem[pidx(b * R + k)];
-    }
-#pragma unroll
-    for (int i = 0; i < 32 / R; i++) inv_regs<10, RC>(x + i * R, t + T * i, W, q, P);
-#pragma unroll
-    for (int i = 0; i < 32 / R; i++) {
-      const int b = t + T * i;
-#pragma unroll
-      for (int k = 0; k < R; k++) smem[pidx(b * R + k)] = x[i * R + k];
-    }
-    __syncthreads();
-    {  // stages 9..5
-      const int b = t >> RC, o = t & (R - 1);
-      const int base = (b << (LOGN - 5)) + o;
-#pragma unroll
-      for (int k = 0; k < 32; k++) x[k] = smem[pidx(base + (k << RC))];
-      inv_regs<5, 5>(x, b, W, q, P);
-#pragma unroll
-      for (int k = 0; k < 32; k++) smem[pidx(base + (k << RC))] = x[k];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < 32; k++) x[k] = smem[pidx(t + T * k)];
-    // stages 4..0 (N^-1 folded into stage 0), outputs straight to global
-    inv_regs<0, 5>(x, 0, W, q, P);
-#pragma unroll
-    for (int k = 0; k < 32; k++) epi.put(es, t + T * k, x[k]);
+    if (inv_small(q, LOGN))
+      inv32_body<LOGN, true>(x, smem, t, W, q, P, epi, p, l, pi, primes);
+    else
+      inv32_body<LOGN, false>(x, smem, t, W, q, P, epi, p, l, pi, primes);
     __syncthreads();
   }
 }
@@ -799,26 +805,56 @@ struct Pass16 {
       for (int k = 0; k < R; k++) s[OFF(k)] = x[i * R + k];
     }
   }
+  template <bool SMALL>
   __device__ __forceinline__ static void fwd(u64* x, int t, const ulonglong2* W, u64 q) {
 #pragma unroll
-    for (int i = 0; i < NS; i++) fwd_regs<S0, LOGR>(x + i * R, blk(t, i), W, q);
+    for (int i = 0; i < NS; i++) fwd_regs<S0, LOGR, SMALL>(x + i * R, blk(t, i), W, q);
   }
+  template <bool SMALL>
   __device__ __forceinline__ static void inv(u64* x, int t, const ulonglong2* W, u64 q, const InvLast& P) {
 #pragma unroll
-    for (int i = 0; i < NS; i++) inv_regs<S0, LOGR>(x + i * R, blk(t, i), W, q, P);
+    for (int i = 0; i < NS; i++) inv_regs<S0, LOGR, InvLast, SMALL, LOGN>(x + i * R, blk(t, i), W, q, P);
   }
 };
+
+// Forward passes and the epilogue of one item (16 elements per thread).
+template <int LOGN, bool SMALL, class Epi>
+__device__ __forceinline__ void fwd16_body(u64* x, u64* smem, int t, const ulonglong2* __restrict__ W, u64 q,
+                                           const Epi& epi, int p, int l, int pi, const DPrime* __restrict__ primes) {
+  constexpr int N = 1 << LOGN, T = N / 16, R3 = LOGN - 12;
+  typedef Pass16<LOGN, 0, 4> P0;
+  typedef Pass16<LOGN, 4, 4> P1;
+  typedef Pass16<LOGN, 8, 4> P2;
+  typedef Pass16<LOGN, 12, (R3 > 0 ? R3 : 1)> P3;
+  P0::template fwd<SMALL>(x, t, W, q);
+  P0::store(x, smem, t);
+  __syncthreads();
+  P1::load(x, smem, t);
+  P1::template fwd<SMALL>(x, t, W, q);
+  P1::store(x, smem, t);
+  __syncthreads();
+  P2::load(x, smem, t);
+  P2::template fwd<SMALL>(x, t, W, q);
+  P2::store(x, smem, t);
+  if constexpr (R3 > 0) {
+    __syncthreads();
+    P3::load(x, smem, t);
+    P3::template fwd<SMALL>(x, t, W, q);
+    P3::store(x, smem, t);
+  }
+  __syncthreads();
+  typename Epi::State es;
+  epi.begin(es, p, l, pi, primes, LOGN);
+#pragma unroll 8
+  for (int k = 0; k < 16; k++) epi.template put<SMALL>(es, t + T * k, smem[pidx(t + T * k)]);
+}
 
 template <int LOGN, class Pro, class Epi>
 __global__ void __launch_bounds__((1 << LOGN) / 16, 16384 / (1 << LOGN))
 k_nttf_r16(const __grid_constant__ Pro pro, const __grid_constant__ Epi epi, const DPrime* __restrict__ primes,
            const ulonglong2* __restrict__ tw, int n_items, int lr, int limb_lo, int lvl, int L) {
   static_assert(LOGN >= 12 && LOGN <= 14, "16-element kernels cover N = 4096 .. 16384");
-  constexpr int N = 1 << LOGN, T = N / 16, R3 = LOGN - 12;
-  typedef Pass16<LOGN, 0, 4> P0;
-  typedef Pass16<LOGN, 4, 4> P1;
-  typedef Pass16<LOGN, 8, 4> P2;
-  typedef Pass16<LOGN, 12, (R3 > 0 ? R3 : 1)> P3;
+  constexpr int N = 1 << LOGN, T = N / 16;
   extern __shared__ u64 smem[];
   const int t = threadIdx.x;
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
@@ -826,9 +862,9 @@ k_nttf_r16(const __grid_constant__ Pro pro, const __grid_constant__ Epi epi, con
     const int pi = l < lvl ? l : L + (l - lvl);
     typename Pro::State ps;
     if (!pro.begin(ps, p, l, pi, primes, LOGN)) continue;
-    typename Epi::State es;
-    epi.begin(es, p, l, pi, primes, LOGN);
     if (threadIdx.x == 0) {  // L2 prefetch: this item's epilogue reads, the next item's sources
+      typename Epi::State es;  // bound again after the transform (not live through it)
+      epi.begin(es, p, l, pi, primes, LOGN);
       epi.prefetch(es, LOGN);
       const int nx = item + gridDim.x;
       if (nx < n_items) {
@@ -836,11 +872,12 @@ k_nttf_r16(const __grid_constant__ Pro pro, const __grid_constant__ Epi epi, con
         pro.prefetch_src(p2, l2, l2 < lvl ? l2 : L + (l2 - lvl), LOGN);
       }
     }
-    const u64 q = primes[pi].q;
+    const DPrime& P = primes[pi];
+    const u64 q = P.q;
     const ulonglong2* W = tw + ((size_t)pi << LOGN);
     u64 x[16];
     if constexpr (Pro::kStage) {
-#pragma unroll 4
+#pragma unroll 2
       for (int k = 0; k < 16; k++) smem[pidx(t + T * k)] = pro.get(ps, t + T * k);
 #pragma unroll
       for (int k = 0; k < 16; k++) x[k] = smem[pidx(t + T * k)];
@@ -848,27 +885,45 @@ k_nttf_r16(const __grid_constant__ Pro pro, const __grid_constant__ Epi epi, con
 #pragma unroll
       for (int k = 0; k < 16; k++) x[k] = pro.get(ps, t + T * k);
     }
-    P0::fwd(x, t, W, q);
-    P0::store(x, smem, t);
-    __syncthreads();
-    P1::load(x, smem, t);
-    P1::fwd(x, t, W, q);
-    P1::store(x, smem, t);
-    __syncthreads();
-    P2::load(x, smem, t);
-    P2::fwd(x, t, W, q);
-    P2::store(x, smem, t);
-    if constexpr (R3 > 0) {
-      __syncthreads();
-      P3::load(x, smem, t);
-      P3::fwd(x, t, W, q);
-      P3::store(x, smem, t);
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int k = 0; k < 16; k++) epi.put(es, t + T * k, smem[pidx(t + T * k)]);
+    if (fwd_small(P))
+      fwd16_body<LOGN, true>(x, smem, t, W, q, epi, p, l, pi, primes);
+    else
+      fwd16_body<LOGN, false>(x, smem, t, W, q, epi, p, l, pi, primes);
     __syncthreads();
   }
+}
+
+// Inverse passes of one item from shared memory, outputs (below 4q) to the epilogue.
+template <int LOGN, bool SMALL, class Epi>
+__device__ __forceinline__ void inv16_body(u64* x, u64* smem, int t, const ulonglong2* __restrict__ W, u64 q,
+                                           const InvLast& P, const Epi& epi, int p, int l, int pi,
+                                           const DPrime* __restrict__ primes) {
+  constexpr int N = 1 << LOGN, T = N / 16, R3 = LOGN - 12;
+  typedef Pass16<LOGN, 0, 4> P0;
+  typedef Pass16<LOGN, 4, 4> P1;
+  typedef Pass16<LOGN, 8, 4> P2;
+  typedef Pass16<LOGN, 12, (R3 > 0 ? R3 : 1)> P3;
+  if constexpr (R3 > 0) {
+    P3::load(x, smem, t);
+    P3::template inv<SMALL>(x, t, W, q, P);
+    P3::store(x, smem, t);
+    __syncthreads();
+  }
+  P2::load(x, smem, t);
+  P2::template inv<SMALL>(x, t, W, q, P);
+  P2::store(x, smem, t);
+  __syncthreads();
+  P1::load(x, smem, t);
+  P1::template inv<SMALL>(x, t, W, q, P);
+  P1::store(x, smem, t);
+  __syncthreads();
+  P0::load(x, smem, t);
+  // stages 3..0 (N^-1 folded into stage 0), outputs straight to global
+  P0::template inv<SMALL>(x, t, W, q, P);
+  typename Epi::State es;
+  epi.begin(es, p, l, pi, primes, LOGN);
+#pragma unroll
+  for (int k = 0; k < 16; k++) epi.put(es, t + T * k, x[k]);
 }
 
 template <int LOGN, class Pro, class Epi>
@@ -877,11 +932,7 @@ k_ntti_r16(const __grid_constant__ Pro pro, const __grid_constant__ Epi epi, con
            const ulonglong2* __restrict__ tw, int n_items, int lr, int limb_lo, int lvl, int L,
            const InvScale* __restrict__ scl) {
   static_assert(LOGN >= 12 && LOGN <= 14, "16-element kernels cover N = 4096 .. 16384");
-  constexpr int N = 1 << LOGN, T = N / 16, R3 = LOGN - 12;
-  typedef Pass16<LOGN, 0, 4> P0;
-  typedef Pass16<LOGN, 4, 4> P1;
-  typedef Pass16<LOGN, 8, 4> P2;
-  typedef Pass16<LOGN, 12, (R3 > 0 ? R3 : 1)> P3;
+  constexpr int N = 1 << LOGN, T = N / 16;
   extern __shared__ u64 smem[];
   const int t = threadIdx.x;
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
@@ -889,9 +940,9 @@ k_ntti_r16(const __grid_constant__ Pro pro, const __grid_constant__ Epi epi, con
     const int pi = l < lvl ? l : L + (l - lvl);
     typename Pro::State ps;
     if (!pro.begin(ps, p, l, pi, primes, LOGN)) continue;
-    typename Epi::State es;
-    epi.begin(es, p, l, pi, primes, LOGN);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0) {  // L2 prefetch: this item's epilogue reads, the next item's sources
+      typename Epi::State es;  // bound again after the transform (not live through it)
+      epi.begin(es, p, l, pi, primes, LOGN);
       epi.prefetch(es, LOGN);
       const int nx = item + gridDim.x;
       if (nx < n_items) {
@@ -912,25 +963,10 @@ k_ntti_r16(const __grid_constant__ Pro pro, const __grid_constant__ Epi epi, con
 #pragma unroll 8
     for (int k = 0; k < 16; k++) smem[pidx(t + T * k)] = pro.get(ps, t + T * k);
     __syncthreads();
-    if constexpr (R3 > 0) {
-      P3::load(x, smem, t);
-      P3::inv(x, t, W, q, P);
-      P3::store(x, smem, t);
-      __syncthreads();
-    }
-    P2::load(x, smem, t);
-    P2::inv(x, t, W, q, P);
-    P2::store(x, smem, t);
-    __syncthreads();
-    P1::load(x, smem, t);
-    P1::inv(x, t, W, q, P);
-    P1::store(x, smem, t);
-    __syncthreads();
-    P0::load(x, smem, t);
-    // stages 3..0 (N^-1 folded into stage 0), outputs straight to global
-    P0::inv(x, t, W, q, P);
-#pragma unroll
-    for (int k = 0; k < 16; k++) epi.put(es, t + T * k, x[k]);
+    if (inv_small(q, LOGN))
+      inv16_body<LOGN, true>(x, smem, t, W, q, P, epi, p, l, pi, primes);
+    else
+      inv16_body<LOGN, false>(x, smem, t, W, q, P, epi, p, l, pi, primes);
     __syncthreads();
   }
 }
