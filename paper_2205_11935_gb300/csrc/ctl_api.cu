@@ -189,7 +189,7 @@ static int build_tables(ctl_context* c) {
     P.iw1 = h_mulmod(itw2[((size_t)i * N + 1) * 2], P.ninv, q);
     P.iw1_sh = h_shoup(P.iw1, q);
     const unsigned bits = 64 - __builtin_clzll(q);
-    P.split = bits <= 54 ? (bits + 1) / 2 : 0;
+    P.split = bits <= 54 ? kSplitW : 0;
     P.bar = q > (1ull << 32) ? (u64)((((unsigned __int128)1) << 64) / q) : 0;
   }
   // conversion tables, packed into one host vector then copied to the device
@@ -1210,6 +1210,7 @@ struct DenseLayer {
   bool lazy = false;     // lazy-ModDown form (CTL_DENSE_LAZY_MODDOWN) instead of composed rotations
   double pt_scale = 0, in_scale = 0, out_scale = 0;
   u64* diag = nullptr;   // [t][limbs][N] NTT + Montgomery form (split); limbs = lvl (+K if lazy)
+  u64* wino = nullptr;   // [t2][limbs][N] diagonal pair terms of the Winograd inner sums
   u64* bias = nullptr;   // [lvl][N] NTT form (plain residues) or null
 };
 
@@ -1311,6 +1312,15 @@ int dense_prepare(ctl_context* c, DenseLayer& D, const double* W, const double* 
   const uint32_t limbs = D.lazy ? lvl + c->K : lvl;
   if (int rc = upload_plaintexts(c, src, D.t, lvl, limbs, true, &D.diag)) return rc;
   launch_split_limbs(c, D.diag, (int)D.t, (int)limbs, (int)lvl);
+  {
+    DBuf w(c, (size_t)D.t2 * limbs * c->N);
+    if (!w.p) {
+      set_error("dense: allocation failed (diagonal pair terms)");
+      return CTL_ENOMEM;
+    }
+    launch_bsgs_wino_diag(c, D.diag, (size_t)limbs * c->N, w.p, (int)D.t1, (int)D.t2, (int)limbs, (int)lvl);
+    D.wino = w.release();
+  }
   std::vector<i64> benc;
   const i64* bsrc = (const i64*)bias_in;
   if (!bsrc && bias) {
@@ -1331,8 +1341,9 @@ int dense_prepare(ctl_context* c, DenseLayer& D, const double* W, const double* 
 
 void dense_release(ctl_context* c, DenseLayer& D) {
   dev_free(c, D.diag);
+  dev_free(c, D.wino);
   dev_free(c, D.bias);
-  D.diag = D.bias = nullptr;
+  D.diag = D.wino = D.bias = nullptr;
 }
 
 // Galois keys of the rotations r0, r0 + step, ... (n of them) as a RotList.
@@ -1394,7 +1405,7 @@ int dense_apply_lazy(ctl_context* c, const ctl_keys* k, const DenseLayer& D, con
     c->op_rot += (uint64_t)(t1 - 1) * nb;
   }
   // inner sums for all giant steps
-  launch_bsgs_inner(c, baby.p, D.diag, EN, inner.p, (int)t1, (int)t2, nb, E, (int)lvl);
+  launch_bsgs_inner(c, baby.p, D.diag, EN, D.wino, inner.p, (int)t1, (int)t2, nb, E, (int)lvl);
   c->op_ptmul += (uint64_t)D.t * nb;
   c->op_add += (uint64_t)(D.t - 1) * nb;
   dev_free(c, baby.release());
@@ -1448,7 +1459,7 @@ int dense_apply_composed(ctl_context* c, const ctl_keys* k, const DenseLayer& D,
   for (uint32_t j = 0; j < t1; j++) rots.push_back(j);
   if (int rc = rotate_many(c, k, in, nb, (int)lvl, rots, baby.p)) return rc;
   // inner sums for all giant steps
-  launch_bsgs_inner(c, baby.p, D.diag, LN, inner.p, (int)t1, (int)t2, nb, (int)lvl, (int)lvl);
+  launch_bsgs_inner(c, baby.p, D.diag, LN, D.wino, inner.p, (int)t1, (int)t2, nb, (int)lvl, (int)lvl);
   c->op_ptmul += (uint64_t)D.t * nb;
   c->op_add += (uint64_t)(D.t - 1) * nb;
   dev_free(c, baby.release());
@@ -1663,7 +1674,7 @@ extern "C" int ctl_model_create(ctl_context* c, const ctl_layer* layers, uint32_
         M->layers.push_back(P);
         return fail(rc);
       }
-      M->bytes += (uint64_t)P.dense.t * (P.dense.lazy ? lvl + c->K : lvl) * c->N * 8;
+      M->bytes += (uint64_t)(P.dense.t + P.dense.t2) * (P.dense.lazy ? lvl + c->K : lvl) * c->N * 8;
       for (uint32_t j = 1; j < P.dense.t1; j++) rots.push_back((int32_t)j);
       for (uint32_t k = 1; k < P.dense.t2; k++) rots.push_back((int32_t)(k * P.dense.t1));
       sc = P.dense.out_scale;

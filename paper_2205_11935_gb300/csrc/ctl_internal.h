@@ -26,9 +26,16 @@ struct DPrime {
   u64 rmod;     // 2^64 mod q: mulmod_mont(x, rmod) = x mod q for any 64-bit x
   u64 ninv, ninv_sh;  // N^-1 mod q and its Shoup companion
   u64 iw1, iw1_sh;    // (psi^-1)^{bitrev(1)} * N^-1: the folded last inverse twiddle
-  u64 split;          // w = ceil(bits(q)/2) when q < 2^54 (operands split into w-bit halves), else 0
+  u64 split;          // kSplitW when q < 2^54 (operands split into kSplitW-bit halves), else 0
   u64 bar;            // floor(2^64 / q) when 2^32 < q (reduce_wide), else 0
 };
+
+// Split form of a residue v < 2^54 for the split-half products of the key product and the
+// baby-step giant-step sums: (v >> kSplitW) << 32 | (v & (2^kSplitW - 1)).  One width for
+// every such prime keeps the shifts compile-time constants; the halves stay below 2^27, so
+// a product of two halves is below 2^54 and a Karatsuba middle term below 2^56, leaving
+// room for sums of up to 32 terms in 64 bits.
+constexpr int kSplitW = 27;
 
 // Fast base conversion from a set of source primes S to target primes:
 //   y_i = sum_{j in S} [x_j * Shat_j^-1]_{s_j} * (Shat_j mod t_i)  mod t_i.
@@ -290,8 +297,12 @@ void launch_decrypt_mul(ctl_context* c, const u64* ct, const u64* s_ntt, u64* ou
 void launch_automorph(ctl_context* c, const u64* in, u64* out, int n_polys, int limbs, int lvl, size_t stride, u64 g);
 // Baby-step giant-step inner sums over polys of `limbs` limbs (prime map (lvl, L)):
 //   inner[k][b][p][i] = sum_j diag[k*t1+j][i] * baby[j][b][p][i]   (diag in Montgomery form)
-void launch_bsgs_inner(ctl_context* c, const u64* baby, const u64* diag, size_t diag_stride, u64* inner, int t1,
-                       int t2, int nb, int limbs, int lvl);
+// wino: the diagonal pair terms of launch_bsgs_wino_diag ([t2][limbs][N]) for the
+// Winograd form of the Karatsuba shape (t1 >= 2).
+void launch_bsgs_inner(ctl_context* c, const u64* baby, const u64* diag, size_t diag_stride, const u64* wino,
+                       u64* inner, int t1, int t2, int nb, int limbs, int lvl);
+void launch_bsgs_wino_diag(ctl_context* c, const u64* diag, size_t diag_stride, u64* wino, int t1, int t2, int limbs,
+                           int lvl);
 // Re-pack Montgomery-form plaintext limbs [cnt][limbs][N] (prime map (lvl, L)) for the
 // split product: on limbs whose prime has split width w > 0,
 // v -> (v >> w) << 32 | (v & (2^w - 1)).

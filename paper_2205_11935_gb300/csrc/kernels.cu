@@ -286,36 +286,78 @@ void launch_automorph(ctl_context* c, const u64* in, u64* out, int n_polys, int 
 // values in registers and sweeps the batch, so each key value leaves HBM once per
 // launch.  The automorphism gather stays inside an aligned 32-element block for the 32
 // consecutive k of a warp (bit-reversed order), so it touches as many sectors as a
-// coalesced load.  On limbs with a split width w the products use w-bit halves (the
-// ModUp stores its digits split; three 32x32->64 multiply-adds per product, no carries);
-// otherwise 64x64->128 products with the high word kept below q.
-__device__ __forceinline__ u64 split_of(u64 v, int w, u64 mask) { return ((v >> w) << 32) | (v & mask); }
-__device__ __forceinline__ u64 split_redc(u64 a00, u64 a01, u64 a11, int w, u64 q, u64 qinv) {
+// coalesced load.  On limbs whose prime is below 2^54 the products use kSplitW-bit halves
+// (the ModUp stores its digits split; three 32x32->64 multiply-adds per product, no
+// carries); otherwise 64x64->128 products with the high word kept below q.
+__device__ __forceinline__ u64 split_of(u64 v) { return ((v >> kSplitW) << 32) | (v & ((1ull << kSplitW) - 1)); }
+// REDC of S = a00 + a01 * 2^W + a11 * 2^(2W) (W = kSplitW), a 128-bit value below q * 2^64.
+__device__ __forceinline__ u64 split_redc(u64 a00, u64 a01, u64 a11, u64 q, u64 qinv) {
+  constexpr int W = kSplitW;
   u64 lo = a00, hi = 0;
-  const u64 t_lo = a01 << w, t_hi = a01 >> (64 - w);
+  const u64 t_lo = a01 << W, t_hi = a01 >> (64 - W);
   lo += t_lo;
   hi += t_hi + (lo < t_lo);
-  const u64 u_lo = a11 << (2 * w), u_hi = a11 >> (64 - 2 * w);
+  const u64 u_lo = a11 << (2 * W), u_hi = a11 >> (64 - 2 * W);
   lo += u_lo;
   hi += u_hi + (lo < u_lo);
   return redc(hi, lo, q, qinv);
 }
 
-// Key values of one (limb, coefficient) for the nd digits of one rotation, split into
-// w-bit halves where the limb's prime has a split width.
+// Karatsuba multiply-adds of a split operand x = x1 * 2^32 + x0 with two split constants
+// (k0 = k01:k00 and k1 = k11:k10, middle operands ks0 = k00 + k01, ks1 = k10 + k11):
+//   a00 += x0 k00, a11 += x1 k01, am += (x0 + x1) ks0, and the same into c* for k1.
+// Six 32x32->64 multiply-adds and one add, written out so that no other instruction
+// enters the product chain.
+__device__ __forceinline__ void kara_mac2(u64& a00, u64& a11, u64& am, u64& c00, u64& c11, u64& cm, u64 x,
+                                          uint32_t k00, uint32_t k01, uint32_t ks0, uint32_t k10, uint32_t k11,
+                                          uint32_t ks1) {
+  asm("{\n\t"
+      ".reg .u32 x0, x1, xs;\n\t"
+      "mov.b64 {x0, x1}, %6;\n\t"
+      "add.u32 xs, x0, x1;\n\t"
+      "mad.wide.u32 %0, x0, %7, %0;\n\t"
+      "mad.wide.u32 %1, x1, %8, %1;\n\t"
+      "mad.wide.u32 %2, xs, %9, %2;\n\t"
+      "mad.wide.u32 %3, x0, %10, %3;\n\t"
+      "mad.wide.u32 %4, x1, %11, %4;\n\t"
+      "mad.wide.u32 %5, xs, %12, %5;\n\t"
+      "}"
+      : "+l"(a00), "+l"(a11), "+l"(am), "+l"(c00), "+l"(c11), "+l"(cm)
+      : "l"(x), "r"(k00), "r"(k01), "r"(ks0), "r"(k10), "r"(k11), "r"(ks1));
+}
+
+// Karatsuba multiply-add of two split operands x = x1:x0 and d = d1:d0 (32-bit halves):
+//   a00 += x0 d0, a11 += x1 d1, am += (x0 + x1)(d0 + d1).
+__device__ __forceinline__ void kara_mac1(u64& a00, u64& a11, u64& am, u64 x, u64 d) {
+  asm("{\n\t"
+      ".reg .u32 x0, x1, xs, d0, d1, ds;\n\t"
+      "mov.b64 {x0, x1}, %3;\n\t"
+      "mov.b64 {d0, d1}, %4;\n\t"
+      "add.u32 xs, x0, x1;\n\t"
+      "add.u32 ds, d0, d1;\n\t"
+      "mad.wide.u32 %0, x0, d0, %0;\n\t"
+      "mad.wide.u32 %1, x1, d1, %1;\n\t"
+      "mad.wide.u32 %2, xs, ds, %2;\n\t"
+      "}"
+      : "+l"(a00), "+l"(a11), "+l"(am)
+      : "l"(x), "l"(d));
+}
+
+// Key values of one (limb, coefficient) for the nd digits of one rotation, in split form
+// where the limb's prime is below 2^54 (sp).  ND is the digit count, or an upper bound
+// of it (nd <= ND) for the largest counts.
 template <int ND>
 struct KeyRegs {
   u64 k0[ND], k1[ND];
   uint32_t s0[ND], s1[ND];  // split key halves summed (Karatsuba middle operands)
-  __device__ __forceinline__ void load(const u64* key, int nd, int pi, int LK, size_t N, uint32_t k, int w,
-                                       u64 mask) {
+  __device__ __forceinline__ void load(const u64* key, int nd, int pi, int LK, size_t N, uint32_t k, bool sp) {
 #pragma unroll
     for (int d = 0; d < ND; d++) {
       k0[d] = d < nd ? key[(((size_t)d * 2) * LK + pi) * N + k] : 0;
       k1[d] = d < nd ? key[(((size_t)d * 2 + 1) * LK + pi) * N + k] : 0;
-      if (w) {
-        k0[d] = split_of(k0[d], w, mask);
-        k1[d] = split_of(k1[d], w, mask);
+      if (sp) {
+        k0[d] = split_of(k0[d]);
+        k1[d] = split_of(k1[d]);
         s0[d] = (uint32_t)k0[d] + (uint32_t)(k0[d] >> 32);
         s1[d] = (uint32_t)k1[d] + (uint32_t)(k1[d] >> 32);
       }
@@ -329,26 +371,19 @@ struct KeyRegs {
   // (r0, r1) = sum_d xv[d] * (k0[d], k1[d]) mod q, plain residues.  On split limbs the
   // digit values arrive split and each product takes three 32x32->64 multiply-adds
   // (Karatsuba: the middle term is (x0 + x1)(k0 + k1) - x0 k0 - x1 k1; every sum stays
-  // below nd * 2^(2w+2) <= 2^60 for nd <= 16, w <= 27).
-  __device__ __forceinline__ void ip(const u64 (&xv)[ND], int nd, int w, u64 mask, const DPrime& P, u64& r0,
+  // below nd * 2^(2W+2) <= 2^60 for nd <= 16, W = 27).
+  __device__ __forceinline__ void ip(const u64 (&xv)[ND], int nd, bool sp, const DPrime& P, u64& r0,
                                      u64& r1) const {
-    (void)mask;
-    if (w) {
+    if (sp) {
       u64 a00 = 0, am = 0, a11 = 0, c00 = 0, cm = 0, c11 = 0;
 #pragma unroll
       for (int d = 0; d < ND; d++) {
-        if (d < nd) {
-          const uint32_t x0 = (uint32_t)xv[d], x1 = (uint32_t)(xv[d] >> 32), xs = x0 + x1;
-          a00 += (u64)x0 * (uint32_t)k0[d];
-          a11 += (u64)x1 * (uint32_t)(k0[d] >> 32);
-          am += (u64)xs * s0[d];
-          c00 += (u64)x0 * (uint32_t)k1[d];
-          c11 += (u64)x1 * (uint32_t)(k1[d] >> 32);
-          cm += (u64)xs * s1[d];
-        }
+        if (d < nd)
+          kara_mac2(a00, a11, am, c00, c11, cm, xv[d], (uint32_t)k0[d], (uint32_t)(k0[d] >> 32), s0[d],
+                    (uint32_t)k1[d], (uint32_t)(k1[d] >> 32), s1[d]);
       }
-      r0 = split_redc(a00, am - a00 - a11, a11, w, P.q, P.qinv);
-      r1 = split_redc(c00, cm - c00 - c11, c11, w, P.q, P.qinv);
+      r0 = split_redc(a00, am - a00 - a11, a11, P.q, P.qinv);
+      r1 = split_redc(c00, cm - c00 - c11, c11, P.q, P.qinv);
     } else {
       u64 lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
 #pragma unroll
@@ -367,13 +402,15 @@ struct KeyRegs {
   }
 };
 
-template <int ND>
+// ND: the digit count when EXACT, else an upper bound of the run-time count nd_arg.
+template <int ND, bool EXACT>
 __global__ void __launch_bounds__(256) k_key_ip(const u64* __restrict__ ext, size_t ext_r,
                                                 const __grid_constant__ RotList rl, u64* __restrict__ acc,
                                                 const u64* __restrict__ add_c0, size_t add_b,
                                                 const u64* __restrict__ pmod, const u64* __restrict__ pmod_sh,
-                                                const DPrime* __restrict__ pr, int logN, int nb, int nd, int E,
+                                                const DPrime* __restrict__ pr, int logN, int nb, int nd_arg, int E,
                                                 int lvl, int L, int LK) {
+  const int nd = EXACT ? ND : nd_arg;
   const size_t N = (size_t)1 << logN;
   const size_t EN = (size_t)E << logN;
   // src_major (one ModUp shared by all rotations): the rotations run fastest over the
@@ -388,46 +425,55 @@ __global__ void __launch_bounds__(256) k_key_ip(const u64* __restrict__ ext, siz
   const uint32_t e = (uint32_t)(idx & (N - 1));
   const int pi = i < lvl ? i : L + (i - lvl);
   const DPrime P = pr[pi];
-  const int w = (int)P.split;
-  const u64 mask = w ? (1ull << w) - 1 : 0;
+  const bool sp = P.split != 0;
   const u64 g = rl.g[r];
   const uint32_t k = (g == 1 || !src_major) ? e : auto_src_k(e, rl.ginv[r], logN);
   const uint32_t ks = (g == 1 || src_major) ? e : auto_src_k(e, g, logN);
   KeyRegs<ND> kr;
-  kr.load(rl.key[r], nd, pi, LK, N, k, w, mask);
+  kr.load(rl.key[r], nd, pi, LK, N, k, sp);
   // baby step in the extended basis: + (P mod q_i) * sigma_g(c0) on the data limbs
   const bool with_c0 = add_c0 != nullptr && i < lvl;
   const u64 pm = with_c0 ? __ldg(pmod + i) : 0, pms = with_c0 ? __ldg(pmod_sh + i) : 0;
   const u64* c0 = with_c0 ? add_c0 + ((size_t)i << logN) + ks : nullptr;
+  // running pointers (ciphertext b: digits at ex + d*EN, outputs at o and o + EN): the
+  // loop advances them by constant strides instead of recomputing 64-bit offsets
   const u64* ex = ext + (size_t)r * ext_r + ((size_t)i << logN) + ks;
   u64* o = acc + (size_t)r * 2 * nb * EN + ((size_t)i << logN) + k;
+  const size_t xstep = (size_t)nd * EN, ostep = 2 * EN;
   // two ciphertexts per iteration: all their loads are issued before the arithmetic
   int b = 0;
   for (; b + 1 < nb; b += 2) {
     u64 xa[ND], xb[ND];
-    KeyRegs<ND>::fetch(ex + (size_t)b * nd * EN, EN, nd, xa);
-    KeyRegs<ND>::fetch(ex + (size_t)(b + 1) * nd * EN, EN, nd, xb);
-    const u64 ca = with_c0 ? c0[(size_t)b * add_b] : 0, cb = with_c0 ? c0[(size_t)(b + 1) * add_b] : 0;
+    KeyRegs<ND>::fetch(ex, EN, nd, xa);
+    KeyRegs<ND>::fetch(ex + xstep, EN, nd, xb);
+    ex += 2 * xstep;
+    u64 ca = 0, cb = 0;
+    if (with_c0) {
+      ca = c0[0];
+      cb = c0[add_b];
+      c0 += 2 * add_b;
+    }
     u64 r0, r1, s0, s1;
-    kr.ip(xa, nd, w, mask, P, r0, r1);
-    kr.ip(xb, nd, w, mask, P, s0, s1);
+    kr.ip(xa, nd, sp, P, r0, r1);
+    kr.ip(xb, nd, sp, P, s0, s1);
     if (with_c0) {
       r0 = addmod(r0, shoup(ca, pm, pms, P.q), P.q);
       s0 = addmod(s0, shoup(cb, pm, pms, P.q), P.q);
     }
-    o[(size_t)b * 2 * EN] = r0;
-    o[(size_t)b * 2 * EN + EN] = r1;
-    o[(size_t)(b + 1) * 2 * EN] = s0;
-    o[(size_t)(b + 1) * 2 * EN + EN] = s1;
+    o[0] = r0;
+    o[EN] = r1;
+    o[ostep] = s0;
+    o[ostep + EN] = s1;
+    o += 2 * ostep;
   }
   if (b < nb) {
     u64 xa[ND];
-    KeyRegs<ND>::fetch(ex + (size_t)b * nd * EN, EN, nd, xa);
+    KeyRegs<ND>::fetch(ex, EN, nd, xa);
     u64 r0, r1;
-    kr.ip(xa, nd, w, mask, P, r0, r1);
-    if (with_c0) r0 = addmod(r0, shoup(c0[(size_t)b * add_b], pm, pms, P.q), P.q);
-    o[(size_t)b * 2 * EN] = r0;
-    o[(size_t)b * 2 * EN + EN] = r1;
+    kr.ip(xa, nd, sp, P, r0, r1);
+    if (with_c0) r0 = addmod(r0, shoup(c0[0], pm, pms, P.q), P.q);
+    o[0] = r0;
+    o[EN] = r1;
   }
 }
 // g^-1 mod 2N for odd g (2N a power of two): Newton iteration on the 2-adic inverse.
@@ -451,16 +497,20 @@ void launch_key_ip(ctl_context* c, const u64* ext, size_t ext_r, int nb, int lvl
   double work = 2.0 * nd * EN * nb * nrot;
   const u64* pm = c->moddown.pmod;
   const u64* pms = c->moddown.pmod_sh;
-#define CTL_KEYIP_CASE(NDV)                                                                                    \
+#define CTL_KEYIP_CASE(NDV, EX)                                                                                \
   CTL_LAUNCH(KC_KEYIP, work, grid,                                                                             \
-             (k_key_ip<NDV><<<grid, 256, 0, c->stream>>>(ext, ext_r, rl, acc, add_c0, add_b, pm, pms,           \
-                                                         c->d_primes, (int)c->logN, nb, nd, E, lvl, (int)c->L, \
-                                                         LK)))
-  if (nd <= 1) CTL_KEYIP_CASE(1);
-  else if (nd <= 2) CTL_KEYIP_CASE(2);
-  else if (nd <= 4) CTL_KEYIP_CASE(4);
-  else if (nd <= 8) CTL_KEYIP_CASE(8);
-  else CTL_KEYIP_CASE(16);
+             (k_key_ip<NDV, EX><<<grid, 256, 0, c->stream>>>(ext, ext_r, rl, acc, add_c0, add_b, pm, pms,       \
+                                                             c->d_primes, (int)c->logN, nb, nd, E, lvl,        \
+                                                             (int)c->L, LK)))
+  switch (nd) {
+    case 1: CTL_KEYIP_CASE(1, true); break;
+    case 2: CTL_KEYIP_CASE(2, true); break;
+    case 3: CTL_KEYIP_CASE(3, true); break;
+    case 4: CTL_KEYIP_CASE(4, true); break;
+    default:
+      if (nd <= 8) CTL_KEYIP_CASE(8, false);
+      else CTL_KEYIP_CASE(16, false);
+  }
 #undef CTL_KEYIP_CASE
 }
 
@@ -484,13 +534,12 @@ __global__ void __launch_bounds__(256) k_key_ip_acc(const u64* __restrict__ ext,
   const uint32_t k = (uint32_t)(idx & (N - 1));
   const int pi = i < lvl ? i : L + (i - lvl);
   const DPrime P = pr[pi];
-  const int w = (int)P.split;
-  const u64 mask = w ? (1ull << w) - 1 : 0;
+  const bool sp = P.split != 0;
   for (int r = 0; r < rl.n; r++) {
     const u64 g = rl.g[r];
     const uint32_t ks = g == 1 ? k : auto_src_k(k, g, logN);
     KeyRegs<ND> kr;
-    kr.load(rl.key[r], nd, pi, LK, N, k, w, mask);
+    kr.load(rl.key[r], nd, pi, LK, N, k, sp);
     const u64* ex = ext + (size_t)r * ext_r + ((size_t)i << logN) + ks;
     const u64* ad = add + (size_t)r * add_r + ((size_t)i << logN) + ks;
     // two ciphertexts per iteration: all their loads are issued before the arithmetic
@@ -504,8 +553,8 @@ __global__ void __launch_bounds__(256) k_key_ip_acc(const u64* __restrict__ ext,
       const u64 aa = ad[(size_t)b * add_b], ab = ad[(size_t)(b + 1) * add_b];
       const u64 sa0 = sa[0], sa1 = sa[EN], sb0 = sb[0], sb1 = sb[EN];
       u64 r0, r1, q0, q1;
-      kr.ip(xa, nd, w, mask, P, r0, r1);
-      kr.ip(xb, nd, w, mask, P, q0, q1);
+      kr.ip(xa, nd, sp, P, r0, r1);
+      kr.ip(xb, nd, sp, P, q0, q1);
       sa[0] = addmod(sa0, addmod(r0, aa, P.q), P.q);
       sa[EN] = addmod(sa1, r1, P.q);
       sb[0] = addmod(sb0, addmod(q0, ab, P.q), P.q);
@@ -515,7 +564,7 @@ __global__ void __launch_bounds__(256) k_key_ip_acc(const u64* __restrict__ ext,
       u64 xa[ND];
       KeyRegs<ND>::fetch(ex + (size_t)b * nd * EN, EN, nd, xa);
       u64 r0, r1;
-      kr.ip(xa, nd, w, mask, P, r0, r1);
+      kr.ip(xa, nd, sp, P, r0, r1);
       u64* sa = S + (size_t)b * s_b + idx;
       sa[0] = addmod(sa[0], addmod(r0, ad[(size_t)b * add_b], P.q), P.q);
       sa[EN] = addmod(sa[EN], r1, P.q);
@@ -576,9 +625,9 @@ void launch_scale_to_ext(ctl_context* c, const u64* in, u64* out, int nb, int lv
 // each).  For every giant step k the block stages the t1 x 32 diagonal values in shared
 // memory once for its 8 warps (and the grid runs the pairs fastest so other blocks find
 // the same tile in L2); each thread keeps its t1 baby-step values in registers.
-// Products are exact: on limbs with a split width w (q < 2^54) both operands are cut
-// into w-bit halves and the t1 products go into three 64-bit sums with plain 32x32->64
-// multiply-adds (no carries: 2*t1*2^(2w) < 2^64), combined once into a 128-bit value;
+// Products are exact: on limbs whose prime is below 2^54 both operands are in split form
+// (kSplitW-bit halves) and the t1 products go into three 64-bit sums with plain
+// 32x32->64 multiply-adds (no carries: t1 * 2^56 < 2^64), combined once into a 128-bit value;
 // otherwise full 64x64->128 products are summed.  One Montgomery reduction per output
 // (diagonals are in Montgomery form; t1 * q < 2^64 keeps the REDC precondition).
 // ---------------------------------------------------------------------------------
@@ -586,10 +635,8 @@ __global__ void k_split(u64* data, const DPrime* __restrict__ pr, int logN, int 
                         size_t total) {
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)((idx >> logN) % limbs);
-    const int w = (int)pr[i < lvl ? i : L + (i - lvl)].split;
-    if (!w) continue;
-    const u64 v = data[idx];
-    data[idx] = ((v >> w) << 32) | (v & ((1ull << w) - 1));
+    if (!pr[i < lvl ? i : L + (i - lvl)].split) continue;
+    data[idx] = split_of(data[idx]);
   }
 }
 void launch_split_limbs(ctl_context* c, u64* data, int cnt, int limbs, int lvl) {
@@ -614,9 +661,9 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // A block has one warp per (ciphertext, poly) pair, up to 8.
 template <int T1, bool KARA>
 __global__ void __launch_bounds__(256) k_bsgs(const u64* __restrict__ baby, const u64* __restrict__ diag,
-                                              size_t diag_stride, u64* __restrict__ inner,
-                                              const DPrime* __restrict__ pr, int logN, int t1, int t2, int nb,
-                                              int limbs, int lvl, int L) {
+                                              size_t diag_stride, const u64* __restrict__ wino,
+                                              u64* __restrict__ inner, const DPrime* __restrict__ pr, int logN,
+                                              int t1, int t2, int nb, int limbs, int lvl, int L) {
   __shared__ __align__(16) u64 Ds[2][T1][32];
   const size_t LN = (size_t)limbs << logN;
   const size_t chunk = blockIdx.y + (size_t)blockIdx.z * gridDim.y;
@@ -628,7 +675,7 @@ __global__ void __launch_bounds__(256) k_bsgs(const u64* __restrict__ baby, cons
   const size_t cidx = c0 + lane;
   const int i = (int)(c0 >> logN);
   const DPrime P = pr[i < lvl ? i : L + (i - lvl)];
-  const int w = (int)P.split;
+  const bool sp = P.split != 0;
   const bool active = bp < bp_count;
   const size_t bstride = (size_t)bp_count * LN;  // stride between baby steps j
   const int n_chunks = t1 / T1;
@@ -644,42 +691,54 @@ __global__ void __launch_bounds__(256) k_bsgs(const u64* __restrict__ baby, cons
   };
   stage(0, 0);
   u64 x[T1];
+  u64 Y = 0;  // Winograd form: REDC(sum_i x_{2i} x_{2i+1}) of this chunk
+  constexpr bool kWino = KARA && T1 >= 2;
   const int n_steps = n_chunks * t2;
   const u64* xb = baby + (size_t)bp * LN + cidx;
   u64* ob = inner + (size_t)bp * LN + cidx;
   for (int s_ = 0; s_ < n_steps; s_++) {
     const int jc = s_ / t2, k = s_ % t2;
-    if (k == 0) {  // this chunk's baby-step values, split into w-bit halves
+    if (k == 0) {  // this chunk's baby-step values, in split form
 #pragma unroll
       for (int j = 0; j < T1; j++) x[j] = active ? xb[(size_t)(jc * T1 + j) * bstride] : 0;
-      if (w) {
-        const u64 mask = (1ull << w) - 1;
+      if (sp) {
 #pragma unroll
-        for (int j = 0; j < T1; j++) x[j] = ((x[j] >> w) << 32) | (x[j] & mask);
+        for (int j = 0; j < T1; j++) x[j] = split_of(x[j]);
+        if constexpr (kWino) {
+          u64 y00 = 0, y11 = 0, ym = 0;
+#pragma unroll
+          for (int j = 0; j < T1; j += 2) kara_mac1(y00, y11, ym, x[j], x[j + 1]);
+          Y = split_redc(y00, ym - y00 - y11, y11, P.q, P.qinv);
+        }
       }
     }
     u64* o = ob + (size_t)k * bstride;
     const u64 prev = (active && jc > 0) ? *o : 0;
+    // Winograd form: the diagonal pair term of giant step k (subtracted once, in chunk 0)
+    const u64 ek = (kWino && sp && active && jc == 0) ? __ldg(wino + (size_t)k * LN + cidx) : 0;
     cp_async_wait_all();  // tile s has landed (the only group in flight)
     __syncthreads();      // ... for every thread, and every warp is done with tile s-1
     if (s_ + 1 < n_steps) stage(s_ + 1, (s_ + 1) & 1);
     const u64(*D)[32] = Ds[s_ & 1];
     u64 res;
-    if (w) {
+    if (sp) {
       u64 a00 = 0, a11 = 0, m;
-      if constexpr (KARA) {
-        // three multiply-adds per product: middle term (x0 + x1)(d0 + d1) - x0 d0 - x1 d1;
-        // am < T1 * 2^(2w+2) <= 2^61
+      if constexpr (kWino) {
+        // Winograd's inner product: sum_j x_j d_j = sum_i (x_{2i} + d_{2i+1})(x_{2i+1} + d_{2i})
+        // - sum_i x_{2i} x_{2i+1} - sum_i d_{2i} d_{2i+1}: T1/2 products, each a Karatsuba
+        // product of split sums (halves below 2^28, so the packed 64-bit add carries
+        // nothing across halves); am < (T1/2) * 2^58 <= 2^62, and the 128-bit total
+        // sum (x + d)(x' + d') < 16 (2q)^2 stays below q * 2^64 (REDC precondition)
         u64 am = 0;
 #pragma unroll
-        for (int j = 0; j < T1; j++) {
-          const u64 d = D[j][lane];
-          const uint32_t d0 = (uint32_t)d, d1 = (uint32_t)(d >> 32);
-          const uint32_t x0 = (uint32_t)x[j], x1 = (uint32_t)(x[j] >> 32);
-          a00 += (u64)x0 * d0;
-          a11 += (u64)x1 * d1;
-          am += (u64)(x0 + x1) * (d0 + d1);
-        }
+        for (int j = 0; j < T1; j += 2) kara_mac1(a00, a11, am, x[j] + D[j + 1][lane], x[j + 1] + D[j][lane]);
+        m = am - a00 - a11;
+      } else if constexpr (KARA) {
+        // three multiply-adds per product: middle term (x0 + x1)(d0 + d1) - x0 d0 - x1 d1;
+        // am < T1 * 2^56 <= 2^61
+        u64 am = 0;
+#pragma unroll
+        for (int j = 0; j < T1; j++) kara_mac1(a00, a11, am, x[j], D[j][lane]);
         m = am - a00 - a11;
       } else {
         // two accumulators for the middle term keep the dependent chains short
@@ -696,16 +755,9 @@ __global__ void __launch_bounds__(256) k_bsgs(const u64* __restrict__ baby, cons
         }
         m = a01 + a10;
       }
-      // S = a11 * 2^(2w) + m * 2^w + a00 as a 128-bit (hi, lo); m < 2^64 because it is
-      // below 2 * T1 * 2^(2w) (T1 <= 32, w <= 27)
-      u64 lo = a00, hi = 0;
-      const u64 t_lo = m << w, t_hi = m >> (64 - w);
-      lo += t_lo;
-      hi += t_hi + (lo < t_lo);
-      const u64 u_lo = a11 << (2 * w), u_hi = a11 >> (64 - 2 * w);
-      lo += u_lo;
-      hi += u_hi + (lo < u_lo);
-      res = redc(hi, lo, P.q, P.qinv);
+      // S = a11 * 2^(2W) + m * 2^W + a00 (W = kSplitW); m < 2^62
+      res = split_redc(a00, m, a11, P.q, P.qinv);
+      if constexpr (kWino) res = submod(submod(res, Y, P.q), ek, P.q);
     } else {
       u64 lo = 0, hi = 0;
 #pragma unroll
@@ -719,8 +771,43 @@ __global__ void __launch_bounds__(256) k_bsgs(const u64* __restrict__ baby, cons
   }
 }
 
-void launch_bsgs_inner(ctl_context* c, const u64* baby, const u64* diag, size_t diag_stride, u64* inner, int t1,
-                       int t2, int nb, int limbs, int lvl) {
+// Diagonal pair terms of Winograd's inner product, once per dense layer:
+//   wino[k][i][c] = REDC( sum_{j even, j + 1 < t1} diag[k t1 + j][i][c] * diag[k t1 + j + 1][i][c] )
+// (the diagonals are in Montgomery form, so this is the plain sum of d_j d_{j+1} times
+// 2^64 mod q; the accumulated high word is kept below q by subtracting q * 2^64).
+__global__ void k_wino_diag(const u64* __restrict__ diag, size_t diag_stride, u64* __restrict__ wino,
+                            const DPrime* __restrict__ pr, int logN, int t1, int limbs, int lvl, int L,
+                            size_t total) {
+  const size_t LN = (size_t)limbs << logN;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t k = idx / LN, r = idx % LN;
+    const int i = (int)(r >> logN);
+    const DPrime P = pr[i < lvl ? i : L + (i - lvl)];
+    const u64 mask = (1ull << kSplitW) - 1;
+    u64 lo = 0, hi = 0;
+    for (int j = 0; j + 1 < t1; j += 2) {
+      u64 a = diag[(k * t1 + j) * diag_stride + r], b = diag[(k * t1 + j + 1) * diag_stride + r];
+      if (P.split) {  // stored split: back to the plain residue
+        a = ((a >> 32) << kSplitW) | (a & mask);
+        b = ((b >> 32) << kSplitW) | (b & mask);
+      }
+      mac(lo, hi, a, b);
+      if (hi >= P.q) hi -= P.q;
+    }
+    wino[idx] = redc(hi, lo, P.q, P.qinv);
+  }
+}
+void launch_bsgs_wino_diag(ctl_context* c, const u64* diag, size_t diag_stride, u64* wino, int t1, int t2, int limbs,
+                           int lvl) {
+  const size_t total = (size_t)t2 * limbs * c->N;
+  const int g = elem_grid(c, total);
+  CTL_LAUNCH(KC_ELEM, 0, g,
+             (k_wino_diag<<<g, kThreads, 0, c->stream>>>(diag, diag_stride, wino, c->d_primes, (int)c->logN, t1,
+                                                          limbs, lvl, (int)c->L, total)));
+}
+
+void launch_bsgs_inner(ctl_context* c, const u64* baby, const u64* diag, size_t diag_stride, const u64* wino,
+                       u64* inner, int t1, int t2, int nb, int limbs, int lvl) {
   const size_t LN = (size_t)limbs * c->N;
   const size_t chunks = LN / 32;
   const unsigned gy = (unsigned)std::min<size_t>(chunks, 65535);
@@ -732,13 +819,13 @@ void launch_bsgs_inner(ctl_context* c, const u64* baby, const u64* diag, size_t 
   case TT:                                                                                                     \
     if (kara)                                                                                                  \
       CTL_LAUNCH(KC_BSGS, work, grid,                                                                          \
-                 (k_bsgs<TT, true><<<grid, 32 * wpb, 0, c->stream>>>(baby, diag, diag_stride, inner,           \
-                                                                     c->d_primes, (int)c->logN, t1, t2, nb,   \
+                 (k_bsgs<TT, true><<<grid, 32 * wpb, 0, c->stream>>>(baby, diag, diag_stride, wino,      \
+                                                                     inner, c->d_primes, (int)c->logN, t1, t2, nb,   \
                                                                      limbs, lvl, (int)c->L)));                \
     else                                                                                                       \
       CTL_LAUNCH(KC_BSGS, work, grid,                                                                          \
-                 (k_bsgs<TT, false><<<grid, 32 * wpb, 0, c->stream>>>(baby, diag, diag_stride, inner,          \
-                                                                      c->d_primes, (int)c->logN, t1, t2, nb,  \
+                 (k_bsgs<TT, false><<<grid, 32 * wpb, 0, c->stream>>>(baby, diag, diag_stride, wino,    \
+                                                                      inner, c->d_primes, (int)c->logN, t1, t2, nb,  \
                                                                       limbs, lvl, (int)c->L)));               \
     break;
   // T1 = min(t1, chunk cap); t1 and the cap are powers of two, so T1 divides t1

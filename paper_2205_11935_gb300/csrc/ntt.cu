@@ -196,28 +196,27 @@ struct EpiStore {
   __device__ void prefetch(const State&, int) const {}
 };
 
-// Store of ModUp digits for the key product: on limbs whose prime has a split width w,
-// the residue v is stored as (v >> w) << 32 | (v & (2^w - 1)), the operand form of the
-// split-half multiply-adds, so the key product does not split it once per rotation.
+// Store of ModUp digits for the key product: on limbs whose prime is below 2^54 the
+// residue is stored in split form (kSplitW-bit halves in the two words), the operand form
+// of the split-half multiply-adds, so the key product does not split it once per rotation.
 struct EpiStoreSplit {
   u64* dst;
   size_t poly_stride;
   struct State {
     u64* o;
-    u64 q, mask, bar;
-    int w;
+    u64 q, bar;
+    bool sp;
   };
   __device__ void begin(State& st, int p, int l, int pi, const DPrime* pr, int logN) const {
     st.o = dst + (size_t)p * poly_stride + ((size_t)l << logN);
     st.q = pr[pi].q;
     st.bar = pr[pi].bar;
-    st.w = (int)pr[pi].split;
-    st.mask = st.w ? (1ull << st.w) - 1 : ~0ull;
+    st.sp = pr[pi].split != 0;
   }
   template <bool SMALL = false>
   __device__ void put(const State& st, int j, u64 v) const {
     const u64 r = reduce_out<SMALL>(v, st.q, st.bar);
-    st.o[j] = st.w ? ((r >> st.w) << 32) | (r & st.mask) : r;
+    st.o[j] = st.sp ? ((r >> kSplitW) << 32) | (r & ((1ull << kSplitW) - 1)) : r;
   }
   __device__ void prefetch(const State&, int) const {}
 };
@@ -276,11 +275,10 @@ struct ProModUp {
     if (l >= d0 && l < d1) {  // the digit's own primes: y = x mod q_l, already in NTT form
       const u64* g = ntt + (size_t)b * stride + ((size_t)l << logN);
       u64* o = ext + (((size_t)p * E + l) << logN);
-      const int w = (int)pr[pi].split;  // stored split, as EpiStoreSplit does
-      const u64 mask = w ? (1ull << w) - 1 : ~0ull;
+      const bool sp = pr[pi].split != 0;  // stored split, as EpiStoreSplit does
       for (int k = threadIdx.x; k < N; k += blockDim.x) {
         const u64 v = g[k];
-        o[k] = w ? ((v >> w) << 32) | (v & mask) : v;
+        o[k] = sp ? ((v >> kSplitW) << 32) | (v & ((1ull << kSplitW) - 1)) : v;
       }
       return false;
     }
