@@ -39,6 +39,21 @@ __device__ __forceinline__ uint32_t auto_src(uint32_t k, u64 g, int logN) {
   return brv_dev((e2 - 1u) >> 1, logN);
 }
 
+// The same index with 32-bit arithmetic, for g < 2N <= 2^17 (e * g < 2^32).
+__device__ __forceinline__ uint32_t auto_src32(uint32_t k, uint32_t g, int logN) {
+  const uint32_t e = 2u * brv_dev(k, logN) + 1u;
+  return brv_dev((((e * g) & ((2u << logN) - 1)) - 1u) >> 1, logN);
+}
+
+// Load of an element that this thread alone reads and then overwrites: no memory clobber,
+// so the compiler may issue it ahead of stores to other elements (it cannot prove on its
+// own that those stores do not alias it).
+__device__ __forceinline__ u64 ld_own(const u64* p) {
+  u64 v;
+  asm("ld.global.u64 %0, [%1];" : "=l"(v) : "l"(p));
+  return v;
+}
+
 // Asynchronous bulk prefetch of a contiguous global range into L2 (one instruction, no
 // registers); the range is 16-byte aligned and a multiple of 16 bytes (whole limbs).
 __device__ __forceinline__ void l2_prefetch(const void* p, uint32_t bytes) {
@@ -167,6 +182,11 @@ struct ProLoad {
     return true;
   }
   __device__ u64 get(const State& st, int j) const { return st.g[j]; }
+  template <int G>
+  __device__ void getg(const State& st, int k0, int stride, u64 (&y)[G]) const {
+#pragma unroll
+    for (int g = 0; g < G; g++) y[g] = st.g[k0 + g * stride];
+  }
   __device__ void prefetch_src(int p, int l, int, int logN) const {
     l2_prefetch(src + (size_t)p * poly_stride + ((size_t)l << logN), 8u << logN);
   }
@@ -193,6 +213,11 @@ struct EpiStore {
   }
   template <bool SMALL = false>
   __device__ void put(const State& st, int j, u64 v) const { st.o[j] = reduce_out<SMALL>(v, st.q, st.bar); }
+  template <bool SMALL, int G>
+  __device__ void putg(const State& st, int j0, int stride, const u64 (&v)[G]) const {
+#pragma unroll
+    for (int g = 0; g < G; g++) put<SMALL>(st, j0 + g * stride, v[g]);
+  }
   __device__ void prefetch(const State&, int) const {}
 };
 
@@ -217,6 +242,11 @@ struct EpiStoreSplit {
   __device__ void put(const State& st, int j, u64 v) const {
     const u64 r = reduce_out<SMALL>(v, st.q, st.bar);
     st.o[j] = st.sp ? ((r >> kSplitW) << 32) | (r & ((1ull << kSplitW) - 1)) : r;
+  }
+  template <bool SMALL, int G>
+  __device__ void putg(const State& st, int j0, int stride, const u64 (&v)[G]) const {
+#pragma unroll
+    for (int g = 0; g < G; g++) put<SMALL>(st, j0 + g * stride, v[g]);
   }
   __device__ void prefetch(const State&, int) const {}
 };
@@ -253,6 +283,26 @@ struct ConvState {
         if (s >= 4 * t) s -= 4 * t;
       }
     return reduce4(s, t);
+  }
+  // G elements k0 + g*stride: all G * ns source loads are issued before any product.
+  template <int G>
+  __device__ void evalg(int k0, int stride, u64 (&y)[G]) const {
+    u64 v[NS][G];
+#pragma unroll
+    for (int j = 0; j < NS; j++)
+#pragma unroll
+      for (int g = 0; g < G; g++) v[j][g] = j < ns ? __ldg(srcs[j] + k0 + g * stride) : 0;
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+      u64 s = 0;
+#pragma unroll
+      for (int j = 0; j < NS; j++)
+        if (j < ns) {
+          s += shoup_small(v[j][g], c[j], c_sh[j], t);
+          if (s >= 4 * t) s -= 4 * t;
+        }
+      y[g] = reduce4(s, t);
+    }
   }
 };
 
@@ -295,6 +345,10 @@ struct ProModUp {
     }
   }
   __device__ u64 get(const State& st, int j) const { return st.eval(j); }
+  template <int G>
+  __device__ void getg(const State& st, int k0, int stride, u64 (&y)[G]) const {
+    st.template evalg<G>(k0, stride, y);
+  }
 };
 
 template <int NS>
@@ -313,6 +367,10 @@ struct ProModDown {
     for (int j = 0; j < tab.ns; j++) l2_prefetch(acc + (size_t)p * acc_stride + ((size_t)(lvl + j) << logN), 8u << logN);
   }
   __device__ u64 get(const State& st, int j) const { return st.eval(j); }
+  template <int G>
+  __device__ void getg(const State& st, int k0, int stride, u64 (&y)[G]) const {
+    st.template evalg<G>(k0, stride, y);
+  }
 };
 
 struct EpiModDown {
@@ -358,16 +416,28 @@ struct EpiModDown {
     if (st.ad) l2_prefetch(st.ad, 8u << logN);
     if (accum) l2_prefetch(st.o, 8u << logN);
   }
-  // acc and the addend are read-only in this launch (non-coherent loads), so the loads of
-  // several elements can be issued ahead of the stores of earlier ones.  (acc - v) P^-1:
-  // the Shoup product takes acc + c*q - v for the bound c*q of v (4q, or 64q with SMALL).
-  template <bool SMALL = false>
-  __device__ void put(const State& st, int j, u64 v) const {
+  // (acc - v) P^-1: the Shoup product takes acc + c*q - v for the bound c*q of v (4q, or
+  // 64q with SMALL).  G elements j0 + g*stride at a time: every load of the group (acc
+  // and the addend read-only in the launch, the running sum read by its owner only) is
+  // issued before the first store, so the group's loads are in flight together.
+  template <bool SMALL, int G>
+  __device__ void putg(const State& st, int j0, int stride, const u64 (&v)[G]) const {
     const u64 cq = SMALL ? 64 * st.q : 4 * st.q;
-    u64 r = shoup(__ldg(st.a + j) + cq - v, st.pv, st.pvs, st.q);
-    if (st.ad) r = addmod(r, __ldg(st.ad + (st.gg == 1 ? (uint32_t)j : auto_src((uint32_t)j, st.gg, st.lg))), st.q);
-    if (accum) r = addmod(r, st.o[j], st.q);
-    st.o[j] = r;
+    u64 a[G], ad[G], ac[G];
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+      const uint32_t j = (uint32_t)(j0 + g * stride);
+      a[g] = __ldg(st.a + j);
+      ad[g] = st.ad ? __ldg(st.ad + (st.gg == 1 ? j : auto_src32(j, (uint32_t)st.gg, st.lg))) : 0;
+      ac[g] = accum ? ld_own(st.o + j) : 0;
+    }
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+      u64 r = shoup_small(a[g] + cq - v[g], st.pv, st.pvs, st.q);  // below 4q
+      r = reduce4(r, st.q);
+      r = addmod(addmod(r, ad[g], st.q), ac[g], st.q);
+      st.o[j0 + g * stride] = r;
+    }
   }
 };
 
@@ -406,6 +476,16 @@ struct ProRescale {       // (r - h) mod q_i in coefficient form
     const u64 v = st.g[j];
     return v >= h ? mulmod_mont(v - h, st.rm, st.q, st.qinv) : negmod(mulmod_mont(h - v, st.rm, st.q, st.qinv), st.q);
   }
+  template <int G>
+  __device__ void getg(const State& st, int k0, int stride, u64 (&y)[G]) const {
+    u64 v[G];
+#pragma unroll
+    for (int g = 0; g < G; g++) v[g] = st.g[k0 + g * stride];
+#pragma unroll
+    for (int g = 0; g < G; g++)
+      y[g] = v[g] >= h ? mulmod_mont(v[g] - h, st.rm, st.q, st.qinv)
+                       : negmod(mulmod_mont(h - v[g], st.rm, st.q, st.qinv), st.q);
+  }
 };
 
 struct EpiRescale {       // out_i = (in_i - x) * q_last^-1
@@ -427,11 +507,16 @@ struct EpiRescale {       // out_i = (in_i - x) * q_last^-1
     st.a = in + (size_t)p * in_stride + ((size_t)l << logN);
     st.o = out + (size_t)p * out_stride + ((size_t)l << logN);
   }
-  // (in - v) q_last^-1 through one Shoup product of in + c*q - v (c*q the bound of v)
-  template <bool SMALL = false>
-  __device__ void put(const State& st, int j, u64 v) const {
+  // (in - v) q_last^-1 through one Shoup product of in + c*q - v (c*q the bound of v); the
+  // input is read-only in the launch, so a group's loads go ahead of its stores
+  template <bool SMALL, int G>
+  __device__ void putg(const State& st, int j0, int stride, const u64 (&v)[G]) const {
     const u64 cq = SMALL ? 64 * st.q : 4 * st.q;
-    st.o[j] = shoup(st.a[j] + cq - v, st.w, st.ws, st.q);
+    u64 a[G];
+#pragma unroll
+    for (int g = 0; g < G; g++) a[g] = __ldg(st.a + j0 + g * stride);
+#pragma unroll
+    for (int g = 0; g < G; g++) st.o[j0 + g * stride] = reduce4(shoup_small(a[g] + cq - v[g], st.w, st.ws, st.q), st.q);
   }
   __device__ void prefetch(const State& st, int logN) const { l2_prefetch(st.a, 8u << logN); }
 };
@@ -479,8 +564,13 @@ __device__ __forceinline__ void fwd32_body(u64* x, u64* smem, int t, const ulong
   __syncthreads();
   typename Epi::State es;
   epi.begin(es, p, l, pi, primes, LOGN);
-#pragma unroll 8
-  for (int k = 0; k < 32; k++) epi.template put<SMALL>(es, t + T * k, smem[pidx(t + T * k)]);
+#pragma unroll 2
+  for (int k0 = 0; k0 < 32; k0 += 4) {
+    u64 v[4];
+#pragma unroll
+    for (int g = 0; g < 4; g++) v[g] = smem[pidx(t + T * (k0 + g))];
+    epi.template putg<SMALL, 4>(es, t + T * k0, T, v);
+  }
 }
 
 template <int LOGN, class Pro, class Epi>
@@ -717,7 +807,10 @@ __global__ void __launch_bounds__(512) k_nttf_gen(const __grid_constant__ Pro pr
       __syncthreads();
       s0 += r;
     }
-    for (int k = threadIdx.x; k < N; k += blockDim.x) epi.put(es, k, smem[pidx(k)]);
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+      const u64 v[1] = {smem[pidx(k)]};
+      epi.template putg<false, 1>(es, k, 0, v);
+    }
     __syncthreads();
   }
 }
@@ -843,8 +936,13 @@ __device__ __forceinline__ void fwd16_body(u64* x, u64* smem, int t, const ulong
   __syncthreads();
   typename Epi::State es;
   epi.begin(es, p, l, pi, primes, LOGN);
-#pragma unroll 8
-  for (int k = 0; k < 16; k++) epi.template put<SMALL>(es, t + T * k, smem[pidx(t + T * k)]);
+#pragma unroll 2
+  for (int k0 = 0; k0 < 16; k0 += 4) {
+    u64 v[4];
+#pragma unroll
+    for (int g = 0; g < 4; g++) v[g] = smem[pidx(t + T * (k0 + g))];
+    epi.template putg<SMALL, 4>(es, t + T * k0, T, v);
+  }
 }
 
 template <int LOGN, class Pro, class Epi>
@@ -875,8 +973,14 @@ k_nttf_r16(const __grid_constant__ Pro pro, const __grid_constant__ Epi epi, con
     const ulonglong2* W = tw + ((size_t)pi << LOGN);
     u64 x[16];
     if constexpr (Pro::kStage) {
-#pragma unroll 2
-      for (int k = 0; k < 16; k++) smem[pidx(t + T * k)] = pro.get(ps, t + T * k);
+      // groups of four elements, every source load of a group in flight together
+#pragma unroll 1
+      for (int k0 = 0; k0 < 16; k0 += 4) {
+        u64 y[4];
+        pro.template getg<4>(ps, t + T * k0, T, y);
+#pragma unroll
+        for (int g = 0; g < 4; g++) smem[pidx(t + T * (k0 + g))] = y[g];
+      }
 #pragma unroll
       for (int k = 0; k < 16; k++) x[k] = smem[pidx(t + T * k)];
     } else {
