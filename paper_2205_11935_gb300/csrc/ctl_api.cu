@@ -975,11 +975,18 @@ namespace {
 // x_r either 0 (one input shared by all rotations: hoisting) or nb*x_b) with the key and
 // Galois element of rotation r.  out [nr][nb][2][lvl][N].  The addend (nullable) is
 // added through sigma_g as described at launch_moddown_ntt.
-// With accum, the nr results are summed into out [nb][2][lvl][N] (out += each result,
-// one ModDown launch per rotation so that no two items of a launch share an output).
+// With giant (the giant steps of a dense layer), the nr results are not formed: their
+// sum is accumulated as the three partial sums of launch_giant_accum (giant->first: the
+// first chunk), and launch_giant_moddown later adds it into the layer's output.
+struct GiantSums {
+  u64* D = nullptr;
+  u64* C = nullptr;
+  u64* A = nullptr;
+  bool first = true;
+};
 int keyswitch(ctl_context* c, int nr, int nb, int lvl, const u64* x, size_t x_r, size_t x_b,
               const std::vector<const u64*>& keys, const std::vector<u64>& gs, const u64* addend, size_t add_r,
-              size_t add_b, size_t add_p, bool add_both, u64* out, bool accum = false) {
+              size_t add_b, size_t add_p, bool add_both, u64* out, const GiantSums* giant = nullptr) {
   const uint32_t N = c->N;
   const int nd = (lvl + (int)c->alpha - 1) / (int)c->alpha;
   const int E = lvl + (int)c->K;
@@ -1011,17 +1018,13 @@ int keyswitch(ctl_context* c, int nr, int nb, int lvl, const u64* x, size_t x_r,
   // 4. ModDown: special limbs to coefficient form, then conversion + NTT + combine
   // (the factors Phat_j^-1 of the ModDown conversion are folded into this transform)
   launch_ntt_inv_oop(c, acc.p, (size_t)E * N, acc.p, (size_t)E * N, nr * nb * 2, lvl, E, lvl, c->d_md_scale);
-  if (!accum) {
+  if (!giant) {
     launch_moddown_ntt(c, acc.p, nr, nb, lvl, out, addend, add_r, add_b, add_p, add_both, rl);
   } else {
-    for (int r = 0; r < nr; r++) {
-      RotList one;
-      one.n = 1;
-      one.key[0] = rl.key[r];
-      one.g[0] = rl.g[r];
-      launch_moddown_ntt(c, acc.p + (size_t)r * nb * 2 * E * N, 1, nb, lvl, out,
-                         addend ? addend + (size_t)r * add_r : nullptr, 0, add_b, add_p, add_both, one, true);
-    }
+    // sums of the nr ModDowns: data limbs and conversions summed over the rotations
+    // (no transform per rotation); the addend (poly 0 only) is summed through sigma_g
+    launch_giant_accum(c, acc.p, nr, nb, lvl, rl, addend, add_r, add_b, giant->D, giant->C, giant->A,
+                       giant->first);
   }
   return last_cuda("keyswitch");
 }
@@ -1464,14 +1467,27 @@ int dense_apply_composed(ctl_context* c, const ctl_keys* k, const DenseLayer& D,
   c->op_add += (uint64_t)(D.t - 1) * nb;
   dev_free(c, baby.release());
   // giant steps: acc = inner[0] + sum_{k >= 1} rot_{k t1}(inner[k]), chunked, each rotation
-  // with its own input; acc is the k = 0 slice of inner
+  // with its own input; acc is the k = 0 slice of inner.  Each rotation is a whole key
+  // switch (its own ModUp, key product and ModDown), but the sum of their ModDowns takes
+  // one transform per output limb: the data limbs and the conversions of the rotations
+  // are summed first (exact, the transform being linear), then transformed once.  The
+  // rotations go in chunks whose key-switching temporaries stay within 16 GiB.
   u64* acc = inner.p;
   if (t2 > 1) {
     const int E = (int)lvl + (int)c->K;
     const int nd = ((int)lvl + (int)c->alpha - 1) / (int)c->alpha;
     const size_t per = (size_t)nb * N * sizeof(u64) * ((size_t)2 * E + (size_t)nd * E + (size_t)lvl);
     const int chunk = (int)std::min<size_t>(
-        std::min<size_t>(CTL_MAX_ROT, t2 - 1), std::max<size_t>(1, ((size_t)6 << 30) / std::max<size_t>(per, 1)));
+        std::min<size_t>(CTL_MAX_ROT, t2 - 1), std::max<size_t>(1, ((size_t)16 << 30) / std::max<size_t>(per, 1)));
+    DBuf gD(c, bw), gC(c, bw), gA(c, bw / 2);
+    if (!gD.p || !gC.p || !gA.p) {
+      set_error("dense: allocation failed (giant-step sums, batch %d)", nb);
+      return CTL_ENOMEM;
+    }
+    GiantSums gs_sums;
+    gs_sums.D = gD.p;
+    gs_sums.C = gC.p;
+    gs_sums.A = gA.p;
     for (uint32_t k0 = 1; k0 < t2; k0 += chunk) {
       const int nr = (int)std::min<uint32_t>(t2 - k0, (uint32_t)chunk);
       RotList rl;
@@ -1479,11 +1495,12 @@ int dense_apply_composed(ctl_context* c, const ctl_keys* k, const DenseLayer& D,
       std::vector<const u64*> keys(rl.key, rl.key + nr);
       std::vector<u64> gs(rl.g, rl.g + nr);
       const u64* src = inner.p + (size_t)k0 * bw;
-      // each rotation's ModDown adds its result (and sigma_g of its c0) straight into acc
-      int rc = keyswitch(c, nr, nb, (int)lvl, src + LN, bw, ctw, keys, gs, src, bw, ctw, 0, false, acc, true);
+      gs_sums.first = (k0 == 1);
+      int rc = keyswitch(c, nr, nb, (int)lvl, src + LN, bw, ctw, keys, gs, src, bw, ctw, 0, false, acc, &gs_sums);
       if (rc) return rc;
       c->op_rot += (uint64_t)nr * nb;
     }
+    launch_giant_moddown(c, gD.p, gC.p, gA.p, nb, (int)lvl, acc);
   }
   if (D.bias) launch_add_plain(c, acc, D.bias, nb, (int)lvl, ctw);
   return rescale_into(c, acc, nb, (int)lvl, out);

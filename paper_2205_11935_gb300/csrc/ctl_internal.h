@@ -260,6 +260,19 @@ void launch_scale_to_ext(ctl_context* c, const u64* in, u64* out, int nb, int lv
 void launch_moddown_ntt(ctl_context* c, const u64* acc, int nr, int nb, int lvl, u64* out, const u64* addend,
                         size_t add_r, size_t add_b, size_t add_p, bool add_both, const RotList& rl,
                         bool accum = false);
+// Sum of the ModDowns of nr key-switching results (the giant steps of a dense layer),
+// without one NTT per result: the ModDown of acc_r is (acc_r - NTT(conv_r)) * P^-1 on the
+// data limbs, with conv_r the base conversion of its special limbs, and the NTT is
+// linear, so the sum over r needs sum_r acc_r (NTT form) and sum_r conv_r (coefficient
+// form) only.  Accumulates over the nr results of acc [nr][nb][2][E][N] (special limbs
+// inverse-transformed in place, conversion factors folded in):
+//   D[b][t][l] += sum_r acc_r[b][t][l],  C[b][t][l] += sum_r conv_r[b][t][l],
+//   A[b][l] += sum_r sigma_{g_r}(addend_r[b])[l] (addend of rotation r at addend + r*add_r
+//   + b*add_b), all [nb][2 or 1][lvl][N]; first: D, C, A are set instead of added to.
+void launch_giant_accum(ctl_context* c, const u64* acc, int nr, int nb, int lvl, const RotList& rl,
+                        const u64* addend, size_t add_r, size_t add_b, u64* D, u64* C, u64* A, bool first);
+// out[b][t] += (D[b][t] - NTT(C[b][t])) * P^-1 + (t == 0 ? A[b] : 0) for the sums above.
+void launch_giant_moddown(ctl_context* c, const u64* D, const u64* C, const u64* A, int nb, int lvl, u64* out);
 // ModDown of n_polys extended polys spaced by acc_stride (special limbs already
 // inverse-transformed in place, as above) into out + p*out_stride ([lvl][N]), no addend.
 void launch_moddown_polys(ctl_context* c, const u64* acc, size_t acc_stride, int n_polys, int lvl, u64* out,
