@@ -185,7 +185,7 @@ def cpu_oracle_sample(wl):
     for i in range(len(dims) - 1):
         t = bsgs_t(dims[i + 1], dims[i])
         lg = t.bit_length() - 1
-        t1 = min(t, 1 << ((lg + 3) // 2))
+        t1 = 1 << ((lg + 1) // 2)  # the default (composed-rotation) split, 2^ceil(log2(t)/2)
         t2 = t // t1
         est += (t1 + t2 - 2) * t_rot * ks_scale(lvl) + t * t_pt * lvl / L + t_rs * lvl / L
         lvl -= 1

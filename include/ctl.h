@@ -121,6 +121,13 @@ int ctl_autotune_ntt(ctl_context* ctx, uint32_t batch_limbs, int* fwd_shape, int
  * three (karatsuba = 1) 32x32->64 multiply-adds.  Results are identical for every
  * shape.  Errors: CTL_EINVAL. */
 int ctl_set_bsgs_shape(ctl_context* ctx, int chunk, int karatsuba);
+/* Device-memory cap (bytes) of the key-switching temporaries of one launch group: the
+ * rotations of a dense layer's baby and giant steps are key-switched in chunks whose
+ * temporaries (coefficient-form inputs, ModUp digits, key-product results) stay within
+ * it, at least one rotation per chunk.  Default 16 GiB.  Results are identical for every
+ * cap (giant-step sums are carried across chunks).  Errors: CTL_EINVAL (null context or
+ * zero bytes). */
+int ctl_set_keyswitch_budget(ctl_context* ctx, uint64_t bytes);
 #define CTL_DENSE_COMPOSED 0
 #define CTL_DENSE_LAZY_MODDOWN 1
 int ctl_set_dense_mode(ctl_context* ctx, int mode);

@@ -436,6 +436,7 @@ extern "C" int ctl_context_clone(const ctl_context* c, ctl_context** out) {
   k->ntt_shape_inv = c->ntt_shape_inv;
   k->bsgs_chunk = c->bsgs_chunk;
   k->bsgs_karatsuba = c->bsgs_karatsuba;
+  k->ks_budget = c->ks_budget;
   k->parent = c->parent ? c->parent : c;
   if (int rc = cuda_check(cudaStreamCreateWithFlags(&k->stream, cudaStreamNonBlocking), "stream")) return rc;
   k->own_stream = true;
@@ -513,6 +514,15 @@ extern "C" int ctl_set_bsgs_shape(ctl_context* c, int chunk, int karatsuba) {
   }
   c->bsgs_chunk = chunk;
   c->bsgs_karatsuba = karatsuba;
+  return CTL_OK;
+}
+
+extern "C" int ctl_set_keyswitch_budget(ctl_context* c, uint64_t bytes) {
+  if (!c || bytes == 0) {
+    set_error("ctl_set_keyswitch_budget: invalid argument");
+    return CTL_EINVAL;
+  }
+  c->ks_budget = bytes;
   return CTL_OK;
 }
 
@@ -1053,10 +1063,10 @@ int rotate_many(ctl_context* c, const ctl_keys* k, const u64* in, int nb, int lv
     idx.push_back((int)r);
   }
   if (keys.empty()) return last_cuda("rotate");
-  // chunk so that the accumulators stay within ~4 GiB
+  // chunk so that the accumulators stay within the key-switching budget
   const int E = lvl + (int)c->K;
   const size_t acc_per_rot = (size_t)nb * 2 * E * N * sizeof(u64);
-  int chunk = (int)std::max<size_t>(1, ((size_t)4 << 30) / std::max<size_t>(acc_per_rot, 1));
+  int chunk = (int)std::max<size_t>(1, (size_t)c->ks_budget / std::max<size_t>(acc_per_rot, 1));
   chunk = std::min(chunk, CTL_MAX_ROT);
   for (size_t s = 0; s < keys.size();) {
     // consecutive output slots only (idx contiguous runs)
@@ -1416,7 +1426,7 @@ int dense_apply_lazy(ctl_context* c, const ctl_keys* k, const DenseLayer& D, con
   if (t2 > 1) {
     const size_t per = (size_t)nb * N * sizeof(u64) * (2 * (size_t)lvl + (size_t)nd * E);
     const int chunk = (int)std::min<size_t>(
-        std::min<size_t>(CTL_MAX_ROT, t2 - 1), std::max<size_t>(1, ((size_t)6 << 30) / std::max<size_t>(per, 1)));
+        std::min<size_t>(CTL_MAX_ROT, t2 - 1), std::max<size_t>(1, (size_t)c->ks_budget / std::max<size_t>(per, 1)));
     DBuf x1(c, (size_t)chunk * nb * LN), xc(c, (size_t)chunk * nb * LN), ext(c, (size_t)chunk * nb * nd * EN);
     if (!x1.p || !xc.p || !ext.p) {
       set_error("dense: allocation failed (batch %d)", nb);
@@ -1471,14 +1481,14 @@ int dense_apply_composed(ctl_context* c, const ctl_keys* k, const DenseLayer& D,
   // switch (its own ModUp, key product and ModDown), but the sum of their ModDowns takes
   // one transform per output limb: the data limbs and the conversions of the rotations
   // are summed first (exact, the transform being linear), then transformed once.  The
-  // rotations go in chunks whose key-switching temporaries stay within 16 GiB.
+  // rotations go in chunks whose key-switching temporaries stay within the budget.
   u64* acc = inner.p;
   if (t2 > 1) {
     const int E = (int)lvl + (int)c->K;
     const int nd = ((int)lvl + (int)c->alpha - 1) / (int)c->alpha;
     const size_t per = (size_t)nb * N * sizeof(u64) * ((size_t)2 * E + (size_t)nd * E + (size_t)lvl);
     const int chunk = (int)std::min<size_t>(
-        std::min<size_t>(CTL_MAX_ROT, t2 - 1), std::max<size_t>(1, ((size_t)16 << 30) / std::max<size_t>(per, 1)));
+        std::min<size_t>(CTL_MAX_ROT, t2 - 1), std::max<size_t>(1, (size_t)c->ks_budget / std::max<size_t>(per, 1)));
     DBuf gD(c, bw), gC(c, bw), gA(c, bw / 2);
     if (!gD.p || !gC.p || !gA.p) {
       set_error("dense: allocation failed (giant-step sums, batch %d)", nb);

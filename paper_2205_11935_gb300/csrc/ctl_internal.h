@@ -181,6 +181,7 @@ struct ctl_context {
   int ntt_shape_fwd = CTL_NTT_SHAPE_R32, ntt_shape_inv = CTL_NTT_SHAPE_R32;  // ctl_set_ntt_shape / autotune
   int dense_mode = CTL_DENSE_COMPOSED;          // ctl_set_dense_mode
   int bsgs_chunk = 32, bsgs_karatsuba = 1;      // ctl_set_bsgs_shape (measured fastest)
+  uint64_t ks_budget = 16ull << 30;              // ctl_set_keyswitch_budget
   const ctl_context* parent = nullptr;  // clones share the parent's device tables
 };
 

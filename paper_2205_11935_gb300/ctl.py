@@ -53,6 +53,7 @@ SIGNATURES = {
     "ctl_set_ntt_shape": (C.c_int, [_vp, C.c_int, C.c_int]),
     "ctl_get_ntt_shape": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "ctl_set_bsgs_shape": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "ctl_set_keyswitch_budget": (C.c_int, [_vp, C.c_uint64]),
     "ctl_autotune_ntt": (C.c_int, [_vp, C.c_uint32, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "ctl_synchronize": (C.c_int, [_vp]),
     "ctl_keygen": (C.c_int, [_vp, _i32p, C.c_uint32, C.c_uint64, _pp]),
@@ -179,6 +180,9 @@ class Context:
 
     def set_bsgs_shape(self, chunk=32, karatsuba=1):
         _check(lib().ctl_set_bsgs_shape(self.h, int(chunk), int(karatsuba)))
+
+    def set_keyswitch_budget(self, nbytes):
+        _check(lib().ctl_set_keyswitch_budget(self.h, int(nbytes)))
 
     def ntt_shape(self):
         f, i = C.c_int(), C.c_int()

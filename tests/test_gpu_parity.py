@@ -477,6 +477,39 @@ def test_bsgs_shapes_bit_exact(chunk, kara):
         k.close()
 
 
+@pytest.mark.parametrize("lazy", [False, True])
+def test_keyswitch_chunks_bit_exact(lazy):
+    """A key-switching budget of one byte forces one rotation per chunk: the baby steps
+    and the giant-step sums (carried across chunks) give the oracle's dense layer, the
+    same bits as the default single chunk, for a batch of two ciphertexts."""
+    P = pair("c2")
+    m = n = 256  # t = 256: 15 giant-step rotations in the default split
+    rots = sorted(set(O.Oracle.bsgs_rotations(m, n, lazy)))
+    o = O.Oracle(P.N, *PARAMS["c2"][1:3], dnum=PARAMS["c2"][3], scale=2.0 ** 40)
+    o.keygen(rots, seed=3)
+    k = P.g.keygen(rots, seed=3)
+    W, x, t, ct_o = dense_case(P, m, n, 93)
+    _, ct_o2 = P.fresh(94, z=None)
+    sc = o.dense_scale(ct_o.shape[1])
+    pts = o.encode_diagonals(W, sc, lazy)
+    exp = [o.dense(c, pts, lazy=lazy)[0] for c in (ct_o, ct_o2)]
+    P.g.set_dense_mode(P.g.DENSE_LAZY_MODDOWN if lazy else P.g.DENSE_COMPOSED)
+    try:
+        outs = []
+        for budget in (1 << 34, 1):
+            P.g.set_keyswitch_budget(budget)
+            batch = P.g.concat([P.g.ct_import(ct_o, 2.0 ** 40), P.g.ct_import(ct_o2, 2.0 ** 40)])
+            outs.append(P.g.dense_coeffs(k, batch, pts, sc).export())
+        for got in outs:
+            assert np.array_equal(got[0], exp[0]) and np.array_equal(got[1], exp[1])
+    finally:
+        P.g.set_keyswitch_budget(16 << 30)
+        P.g.set_dense_mode(P.g.DENSE_COMPOSED)
+    k.close()
+    with pytest.raises(ctl.CtlError):
+        P.g.set_keyswitch_budget(0)
+
+
 def _fp64_forward(Ws, x, square_last):
     h = x
     for i, W in enumerate(Ws):
