@@ -932,4 +932,194 @@ int orc_replicate(const orc_ctx* c, const orc_keys* k, const u64* ct, uint32_t l
   return orc_add(c, ct, r.data(), lvl, out);
 }
 
+// ---------------------------------------------------------------------------------
+// The other layers of the paper's frozen network (Sec. 3.1: "1D Convolutions",
+// "Average Pool", "ReLU") and the ciphertext operations they are composed of.
+// ---------------------------------------------------------------------------------
+
+// Tensor product of two ciphertexts at the same level: (a0*b0, a0*b1 + a1*b0, a1*b1),
+// [3][lvl][N], each a negacyclic schoolbook product per prime.
+int orc_tensor(const orc_ctx* c, const u64* a, const u64* b, uint32_t lvl, u64* d) {
+  uint32_t N = c->N;
+  std::vector<u64> t(N), u(N);
+  for (uint32_t i = 0; i < lvl; i++) {
+    u64 q = c->mods[i];
+    const u64* a0 = a + (size_t)i * N;
+    const u64* a1 = a + ((size_t)lvl + i) * N;
+    const u64* b0 = b + (size_t)i * N;
+    const u64* b1 = b + ((size_t)lvl + i) * N;
+    negacyclic_mul(a0, b0, d + (size_t)i * N, N, q);
+    negacyclic_mul(a0, b1, t.data(), N, q);
+    negacyclic_mul(a1, b0, u.data(), N, q);
+    for (uint32_t j = 0; j < N; j++) d[((size_t)lvl + i) * N + j] = addmod(t[j], u[j], q);
+    negacyclic_mul(a1, b1, d + ((size_t)2 * lvl + i) * N, N, q);
+  }
+  return 0;
+}
+
+// Ciphertext-ciphertext product (HMult): tensor, relinearise with the s^2 -> s key,
+// rescale.  The output scale is scale_a * scale_b / q_{lvl-1}.
+int orc_mul(const orc_ctx* c, const orc_keys* k, const u64* a, const u64* b, uint32_t lvl, u64* out) {
+  if (lvl < 2) return -1;
+  std::vector<u64> d((size_t)3 * lvl * c->N), r((size_t)2 * lvl * c->N);
+  orc_tensor(c, a, b, lvl, d.data());
+  int rc = orc_relin(c, k, d.data(), lvl, r.data());
+  if (rc) return rc;
+  return orc_rescale(c, r.data(), lvl, out);
+}
+
+// Product with an integer constant C: (C*c0, C*c1) mod every prime.  The constant
+// polynomial C decodes to the value C/scale in every slot.
+int orc_mul_const(const orc_ctx* c, const u64* ct, uint32_t lvl, i64 C, u64* out) {
+  uint32_t N = c->N;
+  for (uint32_t p = 0; p < 2; p++)
+    for (uint32_t i = 0; i < lvl; i++) {
+      u64 q = c->mods[i], cq = from_signed(C, q);
+      for (uint32_t j = 0; j < N; j++) {
+        size_t o = ((size_t)p * lvl + i) * N + j;
+        out[o] = mulmod(ct[o], cq, q);
+      }
+    }
+  return 0;
+}
+
+// Sum with an integer constant C in every slot: C is added to the constant coefficient
+// of c0 (the plaintext (C, 0, ..., 0)).
+int orc_add_const(const orc_ctx* c, const u64* ct, uint32_t lvl, i64 C, u64* out) {
+  uint32_t N = c->N;
+  memcpy(out, ct, sizeof(u64) * 2 * lvl * N);
+  for (uint32_t i = 0; i < lvl; i++) out[(size_t)i * N] = addmod(ct[(size_t)i * N], from_signed(C, c->mods[i]), c->mods[i]);
+  return 0;
+}
+
+// Level drop: keeps the first `to` limbs of both polynomials, i.e. reduces the
+// ciphertext modulo Q_to with no division (the scale is unchanged).
+int orc_drop_level(const orc_ctx* c, const u64* ct, uint32_t lvl, uint32_t to, u64* out) {
+  uint32_t N = c->N;
+  if (to == 0 || to > lvl) return -1;
+  for (uint32_t p = 0; p < 2; p++)
+    memcpy(out + (size_t)p * to * N, ct + (size_t)p * lvl * N, sizeof(u64) * to * N);
+  return 0;
+}
+
+// Integer constants of the degree-3 polynomial evaluation below, from the FP64 scale
+// bookkeeping (q_a = q_{lvl-1}, q_b = q_{lvl-2}, S = in_scale):
+//   S2 = S*S/q_a,  Sw = S2*S/q_b,
+//   C3 = round(a3*q_a), C2 = round(a2*S), C1 = round(a1*((Sw*q_a)/S)), C0 = round(a0*Sw),
+// rounding half away from zero.  consts[4] = {C0, C1, C2, C3}; *out_scale = Sw.
+int orc_poly3_consts(const orc_ctx* c, uint32_t lvl, double in_scale, const double* a, i64* consts,
+                     double* out_scale) {
+  if (lvl < 3 || lvl > c->L) return -1;
+  double qa = (double)c->mods[lvl - 1], qb = (double)c->mods[lvl - 2];
+  double S2 = in_scale * in_scale / qa;
+  double Sw = S2 * in_scale / qb;
+  consts[3] = (i64)llround(a[3] * qa);
+  consts[2] = (i64)llround(a[2] * in_scale);
+  consts[1] = (i64)llround(a[1] * (Sw * qa / in_scale));
+  consts[0] = (i64)llround(a[0] * Sw);
+  if (out_scale) *out_scale = Sw;
+  return 0;
+}
+
+// Degree-3 polynomial a3 z^3 + a2 z^2 + a1 z + a0 at multiplicative depth 2 (Sec. 3.1,
+// "ReLU": the paper's ReLU approximation is such a polynomial).  Reading (the paper
+// fixes only the polynomial): with z at level lvl and scale S, constants as in
+// orc_poly3_consts,
+//   z2 = square(z)                                (level lvl-1, scale S2)
+//   v  = rescale(C3 * z) + C2                     (level lvl-1, scale S)
+//   w  = HMult(z2, v) (tensor, relin, rescale)    (level lvl-2, scale Sw)
+//   l  = drop_{lvl-2}(rescale(C1 * z))            (level lvl-2, scale Sw)
+//   out = (w + l) + C0                            (level lvl-2, scale Sw)
+// so that out decodes to z^2 (a3 z + a2) + a1 z + a0.
+int orc_poly3(const orc_ctx* c, const orc_keys* k, const u64* ct, uint32_t lvl, double in_scale, const double* a,
+              u64* out, double* out_scale) {
+  i64 C[4];
+  int rc = orc_poly3_consts(c, lvl, in_scale, a, C, out_scale);
+  if (rc) return rc;
+  uint32_t N = c->N;
+  size_t w1 = (size_t)2 * (lvl - 1) * N, w2 = (size_t)2 * (lvl - 2) * N;
+  std::vector<u64> z2(w1), t((size_t)2 * lvl * N), v(w1), w(w2), l1(w1), l(w2);
+  if ((rc = orc_square(c, k, ct, lvl, z2.data()))) return rc;
+  orc_mul_const(c, ct, lvl, C[3], t.data());
+  orc_rescale(c, t.data(), lvl, v.data());
+  orc_add_const(c, v.data(), lvl - 1, C[2], v.data());
+  if ((rc = orc_mul(c, k, z2.data(), v.data(), lvl - 1, w.data()))) return rc;
+  orc_mul_const(c, ct, lvl, C[1], t.data());
+  orc_rescale(c, t.data(), lvl, l1.data());
+  orc_drop_level(c, l1.data(), lvl - 1, lvl - 2, l.data());
+  orc_add(c, w.data(), l.data(), lvl - 2, out);
+  return orc_add_const(c, out, lvl - 2, C[0], out);
+}
+
+// Average pooling with stride 1 and size f (Sec. 3.1 "Average Pool"): the sum of
+// rot_{-i}(x) over i = 0..f-1 (the printed bound "i = 0..f" disagrees with the stated
+// f-1 rotations; read as f terms), in increasing i, times the constant
+// Cf = round(q_{lvl-1}/f) (the value 1/f at scale q_{lvl-1}), then rescale; the output
+// keeps the input scale.  counters[0..2]: rotations, constant products, additions.
+int orc_avgpool(const orc_ctx* c, const orc_keys* k, const u64* ct, uint32_t lvl, uint32_t f, u64* out,
+                u64* counters) {
+  if (lvl < 2 || f == 0) return -1;
+  uint32_t N = c->N;
+  size_t w = (size_t)2 * lvl * N;
+  std::vector<u64> s(ct, ct + w), r(w);
+  u64 nrot = 0, nadd = 0;
+  for (uint32_t i = 1; i < f; i++) {
+    int rc = orc_rotate(c, k, ct, lvl, -(int64_t)i, r.data());
+    if (rc) return rc;
+    nrot++;
+    orc_add(c, s.data(), r.data(), lvl, s.data());
+    nadd++;
+  }
+  i64 Cf = (i64)llround((double)c->mods[lvl - 1] / (double)f);
+  orc_mul_const(c, s.data(), lvl, Cf, s.data());
+  if (counters) { counters[0] = nrot; counters[1] = 1; counters[2] = nadd; }
+  return orc_rescale(c, s.data(), lvl, out);
+}
+
+// Plaintexts of the packed single-input single-output 1D convolution (Sec. 3.1 "1D
+// Convolutions", after GAZELLE): filter w[f], input of length n held as [x, x] at block
+// stride t (slots [0, n) and [t, t+n)).  pt_i has w[i] in the slots s < 2t with
+// (s mod t) < n and 0 elsewhere, encoded at `scale`.
+int orc_encode_conv(const orc_ctx* c, const double* w, uint32_t f, uint32_t n, uint32_t t, double scale, i64* pts) {
+  uint32_t ns = c->N / 2;
+  if (f == 0 || n == 0 || n > t || 2 * t > ns) return -1;
+  std::vector<double> v(ns);
+  for (uint32_t i = 0; i < f; i++) {
+    for (uint32_t s = 0; s < ns; s++) v[s] = (s < 2 * t && (s % t) < n) ? w[i] : 0.0;
+    int rc = orc_encode(c, v.data(), ns, scale, pts + (size_t)i * c->N);
+    if (rc) return rc;
+  }
+  return 0;
+}
+
+// 1D convolution with "same" zero padding: out = sum_{i=0}^{f-1} pt_i o rot_{i-h}(x),
+// h = floor((f-1)/2), in increasing i (rot_0 = x), then an optional plaintext bias (on
+// c0) and a rescale.  Slot s of the output holds sum_i w[i] x[s+i-h].  counters[0..2]:
+// rotations (f-1), plaintext products (f), additions (f-1).
+int orc_conv1d(const orc_ctx* c, const orc_keys* k, const u64* ct, uint32_t lvl, const i64* pts, uint32_t f,
+               const i64* bias, u64* out, u64* counters) {
+  if (lvl < 2 || f == 0) return -1;
+  uint32_t N = c->N;
+  int64_t h = (int64_t)(f - 1) / 2;
+  size_t w = (size_t)2 * lvl * N;
+  std::vector<u64> acc(w), r(w), prod(w);
+  u64 nrot = 0, nmul = 0, nadd = 0;
+  for (uint32_t i = 0; i < f; i++) {
+    int64_t o = (int64_t)i - h;
+    const u64* src = ct;
+    if (o != 0) {
+      int rc = orc_rotate(c, k, ct, lvl, o, r.data());
+      if (rc) return rc;
+      nrot++;
+      src = r.data();
+    }
+    orc_mul_plain(c, src, lvl, pts + (size_t)i * N, prod.data());
+    nmul++;
+    if (i == 0) acc = prod; else { orc_add(c, acc.data(), prod.data(), lvl, acc.data()); nadd++; }
+  }
+  if (bias) orc_add_plain(c, acc.data(), lvl, bias, acc.data());
+  if (counters) { counters[0] = nrot; counters[1] = nmul; counters[2] = nadd; }
+  return orc_rescale(c, acc.data(), lvl, out);
+}
+
 }  // extern "C"

@@ -66,6 +66,16 @@ def _lib():
             "orc_dense": (C.c_int, [vp, vp, _u64p, C.c_uint32, _i64p, C.c_uint32, _i64p, _u64p, _u64p]),
             "orc_dense_lazy": (C.c_int, [vp, vp, _u64p, C.c_uint32, _i64p, C.c_uint32, _i64p, _u64p, _u64p]),
             "orc_replicate": (C.c_int, [vp, vp, _u64p, C.c_uint32, C.c_uint32, _u64p]),
+            "orc_tensor": (C.c_int, [vp, _u64p, _u64p, C.c_uint32, _u64p]),
+            "orc_mul": (C.c_int, [vp, vp, _u64p, _u64p, C.c_uint32, _u64p]),
+            "orc_mul_const": (C.c_int, [vp, _u64p, C.c_uint32, C.c_int64, _u64p]),
+            "orc_add_const": (C.c_int, [vp, _u64p, C.c_uint32, C.c_int64, _u64p]),
+            "orc_drop_level": (C.c_int, [vp, _u64p, C.c_uint32, C.c_uint32, _u64p]),
+            "orc_poly3_consts": (C.c_int, [vp, C.c_uint32, C.c_double, _dp, _i64p, _dp]),
+            "orc_poly3": (C.c_int, [vp, vp, _u64p, C.c_uint32, C.c_double, _dp, _u64p, _dp]),
+            "orc_avgpool": (C.c_int, [vp, vp, _u64p, C.c_uint32, C.c_uint32, _u64p, _u64p]),
+            "orc_encode_conv": (C.c_int, [vp, _dp, C.c_uint32, C.c_uint32, C.c_uint32, C.c_double, _i64p]),
+            "orc_conv1d": (C.c_int, [vp, vp, _u64p, C.c_uint32, _i64p, C.c_uint32, _i64p, _u64p, _u64p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -314,6 +324,76 @@ class Oracle:
         ct = _u64(ct); out = np.zeros_like(ct)
         _chk(self.lib.orc_replicate(self.h, self.keys, _p(ct, _u64p), ct.shape[1], t, _p(out, _u64p)), "replicate")
         return out
+
+    # --- the other layers of the paper's frozen network (Sec. 3.1) ---------------
+    def tensor(self, a, b):
+        a = _u64(a); b = _u64(b); lvl = a.shape[1]
+        out = np.zeros((3, lvl, self.N), dtype=np.uint64)
+        _chk(self.lib.orc_tensor(self.h, _p(a, _u64p), _p(b, _u64p), lvl, _p(out, _u64p)), "tensor")
+        return out
+
+    def mul(self, a, b):
+        """HMult of two ciphertexts at the same level: tensor, relinearise, rescale."""
+        a = _u64(a); b = _u64(b); lvl = a.shape[1]
+        out = np.zeros((2, lvl - 1, self.N), dtype=np.uint64)
+        _chk(self.lib.orc_mul(self.h, self.keys, _p(a, _u64p), _p(b, _u64p), lvl, _p(out, _u64p)), "mul")
+        return out
+
+    def mul_const(self, ct, c):
+        ct = _u64(ct); out = np.zeros_like(ct)
+        _chk(self.lib.orc_mul_const(self.h, _p(ct, _u64p), ct.shape[1], int(c), _p(out, _u64p)), "mul_const")
+        return out
+
+    def add_const(self, ct, c):
+        ct = _u64(ct); out = np.zeros_like(ct)
+        _chk(self.lib.orc_add_const(self.h, _p(ct, _u64p), ct.shape[1], int(c), _p(out, _u64p)), "add_const")
+        return out
+
+    def drop_level(self, ct, to):
+        ct = _u64(ct); out = np.zeros((2, to, self.N), dtype=np.uint64)
+        _chk(self.lib.orc_drop_level(self.h, _p(ct, _u64p), ct.shape[1], to, _p(out, _u64p)), "drop_level")
+        return out
+
+    def poly3_consts(self, lvl, in_scale, a):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        C = np.zeros(4, dtype=np.int64)
+        out_scale = np.zeros(1)
+        _chk(self.lib.orc_poly3_consts(self.h, lvl, in_scale, _p(a, _dp), _p(C, _i64p), _p(out_scale, _dp)),
+             "poly3_consts")
+        return [int(x) for x in C], float(out_scale[0])
+
+    def poly3(self, ct, in_scale, a):
+        """a[3] z^3 + a[2] z^2 + a[1] z + a[0] at depth 2; returns (ct, out_scale)."""
+        ct = _u64(ct); lvl = ct.shape[1]
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        out = np.zeros((2, lvl - 2, self.N), dtype=np.uint64)
+        sc = np.zeros(1)
+        _chk(self.lib.orc_poly3(self.h, self.keys, _p(ct, _u64p), lvl, in_scale, _p(a, _dp), _p(out, _u64p),
+                                _p(sc, _dp)), "poly3")
+        return out, float(sc[0])
+
+    def avgpool(self, ct, f):
+        ct = _u64(ct); lvl = ct.shape[1]
+        out = np.zeros((2, lvl - 1, self.N), dtype=np.uint64)
+        cnt = np.zeros(3, dtype=np.uint64)
+        _chk(self.lib.orc_avgpool(self.h, self.keys, _p(ct, _u64p), lvl, f, _p(out, _u64p), _p(cnt, _u64p)),
+             "avgpool")
+        return out, [int(x) for x in cnt]
+
+    def encode_conv(self, w, n, t, scale):
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        out = np.zeros((len(w), self.N), dtype=np.int64)
+        _chk(self.lib.orc_encode_conv(self.h, _p(w, _dp), len(w), n, t, scale, _p(out, _i64p)), "encode_conv")
+        return out
+
+    def conv1d(self, ct, pts, bias=None):
+        ct = _u64(ct); pts = _i64(pts); lvl = ct.shape[1]
+        out = np.zeros((2, lvl - 1, self.N), dtype=np.uint64)
+        cnt = np.zeros(3, dtype=np.uint64)
+        bp = _p(_i64(bias), _i64p) if bias is not None else None
+        _chk(self.lib.orc_conv1d(self.h, self.keys, _p(ct, _u64p), lvl, _p(pts, _i64p), pts.shape[0], bp,
+                                 _p(out, _u64p), _p(cnt, _u64p)), "conv1d")
+        return out, [int(x) for x in cnt]
 
     # --- composite helpers (scale bookkeeping of the oracle's reading) -----------
     def dense_scale(self, lvl, in_scale=None):
