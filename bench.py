@@ -43,7 +43,7 @@ MAC_CLASSES = ("key_ip", "bsgs_inner")  # kernel classes whose work unit is a sp
 # DRAM bytes (read + write) per limb item of the fused NTT kernels, from one ncu capture of
 # the same kernels at batch 16 (profiles/ncu_full_modup_moddown_bsgs_keyip_n16384_b16.md);
 # traffic grows with the items, so a launch's traffic is this times its items.
-TRAFFIC_PER_ITEM = {"moddown_ntt": 2846e6 / 7936, "modup_ntt": 4275e6 / 19840}
+TRAFFIC_PER_ITEM = {"moddown_ntt": 2909.2e6 / 7936, "modup_ntt": 4160.1e6 / 19840}
 
 WORKLOADS = {
     "batched": dict(N=16384, q=[45] * 8, p=[60, 60], dnum=4, batch=256, dims=[1024, 256, 256, 64],
