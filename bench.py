@@ -54,7 +54,20 @@ WORKLOADS = {
                             "dense 512->128, x^2, dense 128->64"),
     "single4096": dict(N=4096, q=[50, 40, 40], p=[60], dnum=3, batch=1, dims=[64, 32],
                        desc="1 ciphertext, N=4096, q {50,40,40} + 60-bit p, scale 2^40; dense 64->32, x^2"),
+    # the paper's own frozen network (Sec. 4.1) at its parameter sets (Tab. 1)
+    "paper_p1": dict(N=8192, q=[34] + [25] * 6, p=[34], dnum=7, batch=1, dims=[768, 768, 766], net="paper",
+                     scale=2.0 ** 25,
+                     desc="CryptoTL_p1: N=8192, q {34, 6x25} + 34-bit p (218 bits), scale 2^25; conv1d f=9 on 768 "
+                          "inputs, dense 768->768, ReLU approx (deg 3), avgpool 3, dense ->766; 1 ciphertext"),
+    "paper_p2": dict(N=16384, q=[60] + [50] * 6, p=[60], dnum=7, batch=1, dims=[768, 768, 766], net="paper",
+                     scale=2.0 ** 50,
+                     desc="CryptoTL_p2: N=16384, q {60, 6x50} + 60-bit p (420 bits), scale 2^50; conv1d f=9 on 768 "
+                          "inputs, dense 768->768, ReLU approx (deg 3), avgpool 3, dense ->766; 1 ciphertext"),
 }
+# t_S of one forward on one notebook CPU thread with SEAL + AVX-512 (Tab. 1), for context
+PAPER_T_S = {"paper_p1": 1.08, "paper_p2": 2.56}
+# ReLU approximation of Sec. 3.1 (a3 z^3 + a2 z^2 + a1 z + a0), as a0..a3
+RELU_APPROX = [0.49383, 0.59259, 0.092593, -0.0061728]
 
 
 def bsgs_t(m, n):
@@ -78,12 +91,43 @@ def layers_for(dims, square_last):
     return layers, Ws
 
 
-def inputs_for(N, dims, B, t0):
+def paper_layers_for(n, f=9, pool=3):
+    """The paper's frozen network (Sec. 4.1) on n inputs held as [x, x] at block stride t:
+    conv1d(f) -> dense n->n -> replicate -> ReLU approx -> avgpool(pool) -> dense to
+    n-pool+1 outputs.  Synthetic weights: filter ~N(0, 1/f), dense ~N(0, 1/fan_in).  The
+    valid pooled value k sits in slot k+pool-1, so the last matrix is applied with its
+    columns moved right by pool-1."""
+    rng = np.random.default_rng(1)
+    t = bsgs_t(n, n)
+    w = rng.normal(0, 1 / np.sqrt(f), f)
+    W1 = rng.normal(0, 1 / np.sqrt(n), (n, n))
+    W2 = rng.normal(0, 1 / np.sqrt(n - pool + 1), (n - pool + 1, n - pool + 1))
+    W2s = np.zeros((n - pool + 1, n))
+    W2s[:, pool - 1:] = W2
+    layers = [("conv1d", w, n, t), ("dense", W1), ("replicate", t), ("poly3", RELU_APPROX), ("avgpool", pool),
+              ("dense", W2s)]
+    return layers, (w, W1, W2, pool)
+
+
+def paper_fp64(weights, x):
+    w, W1, W2, pool = weights
+    h = np.correlate(x, w, "same")
+    z = W1 @ h
+    a = RELU_APPROX
+    r = ((a[3] * z + a[2]) * z + a[1]) * z + a[0]
+    p = np.array([np.mean(r[k:k + pool]) for k in range(len(r) - pool + 1)])
+    return W2 @ p
+
+
+def inputs_for(N, dims, B, t0, windows=1):
+    """B ciphertexts of `windows` inputs each, input j of a ciphertext as [x, x] at block
+    stride t0 in slots [2 t0 j, 2 t0 (j+1)); returns xs [B][windows][n] and the slots."""
     rng = np.random.default_rng(2)
-    xs = rng.uniform(-1, 1, (B, dims[0]))
+    xs = rng.uniform(-1, 1, (B, windows, dims[0]))
     slots = np.zeros((B, N // 2))
-    slots[:, :dims[0]] = xs
-    slots[:, t0:t0 + dims[0]] = xs
+    for j in range(windows):
+        slots[:, 2 * t0 * j:2 * t0 * j + dims[0]] = xs[:, j]
+        slots[:, 2 * t0 * j + t0:2 * t0 * j + t0 + dims[0]] = xs[:, j]
     return xs, slots
 
 
@@ -146,6 +190,42 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def op_plan(wl):
+    """(key switches, plaintext products, rescales, level) per step of the forward, in the
+    oracle's terms: a key switch is a rotation or a relinearisation, a ciphertext product's
+    tensor counts as 1.5 (square) or 2 (two operands) plaintext products."""
+    L = len(wl["q"])
+    plan, lvl = [], L
+
+    def split(t):
+        lg = t.bit_length() - 1
+        t1 = 1 << ((lg + 1) // 2)  # the default (composed-rotation) split, 2^ceil(log2(t)/2)
+        return t1, t // t1
+
+    if wl.get("net") == "paper":
+        n, t = wl["dims"][0], bsgs_t(wl["dims"][0], wl["dims"][0])
+        t1, t2 = split(t)
+        plan.append((8, 9, 1, lvl)); lvl -= 1                     # conv1d f=9
+        plan.append((t1 + t2 - 2, t, 1, lvl)); lvl -= 1           # dense
+        plan.append((1, 0, 0, lvl))                               # replicate
+        plan.append((1, 1.5, 3, lvl)); plan.append((1, 2, 1, lvl - 1)); lvl -= 2  # ReLU approx
+        plan.append((2, 0, 1, lvl)); lvl -= 1                     # avgpool 3
+        plan.append((t1 + t2 - 2, t, 1, lvl))                     # dense
+        return plan
+    dims = wl["dims"]
+    for i in range(len(dims) - 1):
+        t = bsgs_t(dims[i + 1], dims[i])
+        t1, t2 = split(t)
+        plan.append((t1 + t2 - 2, t, 1, lvl))
+        lvl -= 1
+        if i + 1 < len(dims) - 1 or wl is WORKLOADS["single4096"]:
+            plan.append((1, 1.5, 1, lvl))  # square: 3 products, relinearisation, rescale
+            lvl -= 1
+            if i + 1 < len(dims) - 1:
+                plan.append((1, 0, 0, lvl))  # replicate
+    return plan
+
+
 def cpu_oracle_sample(wl):
     """Times the oracle on one rotation, one plaintext product and one rescale at the top
     level of the workload's ring, and extrapolates a forward by its operation counts.
@@ -153,7 +233,7 @@ def cpu_oracle_sample(wl):
     from oracle import ckks_oracle as O
 
     N, q, p, dnum = wl["N"], wl["q"], wl["p"], wl["dnum"]
-    o = O.Oracle(N, q, p, dnum=dnum, scale=2.0 ** 40)
+    o = O.Oracle(N, q, p, dnum=dnum, scale=wl.get("scale", 2.0 ** 40))
     t0 = time.perf_counter()
     o.keygen([1], seed=3)
     t_keygen = time.perf_counter() - t0
@@ -163,7 +243,7 @@ def cpu_oracle_sample(wl):
     t0 = time.perf_counter()
     o.rotate(ct, 1)
     t_rot = time.perf_counter() - t0
-    pt = rng.integers(-2 ** 40, 2 ** 40, N, dtype=np.int64)
+    pt = rng.integers(-2 ** 20, 2 ** 20, N, dtype=np.int64)
     t0 = time.perf_counter()
     o.mul_plain(ct, pt)
     t_pt = time.perf_counter() - t0
@@ -173,28 +253,13 @@ def cpu_oracle_sample(wl):
     # operation counts of the forward, each scaled by its level relative to the top
     K = len(p)
     alpha = (L + dnum - 1) // dnum
-    est = 0.0
-    lvl = L
-    dims = wl["dims"]
 
     def ks_scale(l):
         nd = (l + alpha - 1) // alpha
         ndL = (L + alpha - 1) // alpha
         return (nd * (l + K)) / (ndL * (L + K))
 
-    for i in range(len(dims) - 1):
-        t = bsgs_t(dims[i + 1], dims[i])
-        lg = t.bit_length() - 1
-        t1 = 1 << ((lg + 1) // 2)  # the default (composed-rotation) split, 2^ceil(log2(t)/2)
-        t2 = t // t1
-        est += (t1 + t2 - 2) * t_rot * ks_scale(lvl) + t * t_pt * lvl / L + t_rs * lvl / L
-        lvl -= 1
-        if i + 1 < len(dims) - 1 or wl is WORKLOADS["single4096"]:
-            # square: 3 products per limb + relinearisation + rescale; then replicate
-            est += 1.5 * t_pt * lvl / L + t_rot * ks_scale(lvl) + t_rs * lvl / L
-            lvl -= 1
-            if i + 1 < len(dims) - 1:
-                est += t_rot * ks_scale(lvl)
+    est = sum(ks * t_rot * ks_scale(lv) + npt * t_pt * lv / L + nrs * t_rs * lv / L for ks, npt, nrs, lv in op_plan(wl))
     cores = os.cpu_count()
     desc = (f"oracle on {cores} host threads: 1 rotation ({t_rot:.2f} s), 1 plaintext product ({t_pt:.2f} s), "
             f"1 rescale ({t_rs:.2f} s) at N={N}, level {L}, plus one Galois key ({t_keygen:.2f} s); "
@@ -442,12 +507,27 @@ def main():
     from paper_2205_11935_gb300 import ctl
 
     N, B = wl["N"], wl["batch"]
+    scale = wl.get("scale", 2.0 ** 40)
     square_last = args.workload == "single4096"
-    layers, Ws = layers_for(wl["dims"], square_last)
-    t0 = bsgs_t(Ws[0].shape[0], Ws[0].shape[1])
+    if wl.get("net") == "paper":
+        layers, pw = paper_layers_for(wl["dims"][0])
+        t0 = bsgs_t(wl["dims"][0], wl["dims"][0])
+
+        def reference(x):
+            return paper_fp64(pw, x)
+    else:
+        layers, Ws = layers_for(wl["dims"], square_last)
+        t0 = bsgs_t(Ws[0].shape[0], Ws[0].shape[1])
+
+        def reference(x):
+            return fp64_forward(Ws, x, square_last)
     stream = torch.cuda.Stream()
-    ctx = ctl.Context(N, wl["q"], wl["p"], dnum=wl["dnum"], scale=2.0 ** 40)
+    ctx = ctl.Context(N, wl["q"], wl["p"], dnum=wl["dnum"], scale=scale)
     ctx.set_stream(stream.cuda_stream)
+    # Sec. 3.1 "Multiple Predictions": the paper's network packs p = floor(#slots / 2t)
+    # inputs per ciphertext (one window of 2t slots each)
+    windows = (N // 2) // (2 * t0) if wl.get("net") == "paper" else 1
+    ctx.set_windows(windows)
     if args.ntt_shape != "auto":
         sh = ctx.NTT_R16 if args.ntt_shape == "r16" else ctx.NTT_R32
         ctx.set_ntt_shape(sh, sh)
@@ -457,7 +537,7 @@ def main():
     ntt_shape = dict(zip(("fwd", "inv"), (shape_names.get(v, str(v)) for v in ctx.ntt_shape())))
     model = ctl.Model(ctx, layers)
     keys = ctx.keygen(model.rotations(), seed=3)
-    xs, slots = inputs_for(N, wl["dims"], B, t0)
+    xs, slots = inputs_for(N, wl["dims"], B, t0, windows)
     cts = [ctx.encrypt(keys, slots[i], 4 + i) for i in range(B)]
     batch = ctx.concat(cts)
     for c in cts:
@@ -468,9 +548,11 @@ def main():
     out = model.forward(keys, batch)
     check_idx = sorted({0, B // 2, B - 1})
     max_err = 0.0
+    m_out = wl["dims"][-1]
     for i in check_idx:
-        yi = ctx.decrypt(keys, out.slice(i), wl["dims"][-1])
-        max_err = max(max_err, float(np.max(np.abs(yi - fp64_forward(Ws, xs[i], square_last)))))
+        yi = ctx.decrypt(keys, out.slice(i), 2 * t0 * (windows - 1) + m_out)
+        for j in range(windows):
+            max_err = max(max_err, float(np.max(np.abs(yi[2 * t0 * j:2 * t0 * j + m_out] - reference(xs[i, j])))))
     out.close()
 
     use_graph = (args.graph == 1) or (args.graph == -1 and B == 1)
@@ -535,7 +617,7 @@ def main():
         def e2e_step():
             h = C.c_void_p()
             ctl._check(ctl.lib().ctl_ct_import(ctx.h, C.cast(pinned_in.data_ptr(), ctl._u64p), B, len(wl["q"]),
-                                               2.0 ** 40, C.byref(h)))
+                                               scale, C.byref(h)))
             ci = ctl.Ciphertext(ctx, h)
             co = model.forward(keys, ci, graph=use_graph)
             ctl._check(ctl.lib().ctl_ct_export(co.h, C.cast(pinned_out.data_ptr(), ctl._u64p), out_words))
@@ -568,8 +650,9 @@ def main():
         o = model_l.forward(keys_l, batch)
         err_l = 0.0
         for i in check_idx:
-            yi = ctx.decrypt(keys_l, o.slice(i), wl["dims"][-1])
-            err_l = max(err_l, float(np.max(np.abs(yi - fp64_forward(Ws, xs[i], square_last)))))
+            yi = ctx.decrypt(keys_l, o.slice(i), 2 * t0 * (windows - 1) + m_out)
+            for j in range(windows):
+                err_l = max(err_l, float(np.max(np.abs(yi[2 * t0 * j:2 * t0 * j + m_out] - reference(xs[i, j])))))
         o.close()
         for _ in range(2):
             model_l.forward(keys_l, batch, graph=use_graph).close()
@@ -612,7 +695,7 @@ def main():
     unit, peak = unit_peak(dom)
     achieved = rate(d)
     traffic = None
-    if dom in TRAFFIC_PER_ITEM and N == 16384:
+    if dom in TRAFFIC_PER_ITEM and args.workload == "batched":
         K, alpha = len(wl["p"]), -(-len(wl["q"]) // wl["dnum"])
         per_item = 0.5 * N * 14 + (2 * K + 1) * N if dom == "moddown_ntt" else 0.5 * N * 14 + alpha * 2 * N
         traffic = TRAFFIC_PER_ITEM[dom] * (d["modmul"] / max(d["launches"], 1)) / per_item
@@ -646,6 +729,14 @@ def main():
                 "ops_per_step": {k: v / args.steps for k, v in ops.items()},
                 "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
                 "gpu_launches": int(launches), "variants": variants}
+        if args.workload in PAPER_T_S:
+            ts, pp = PAPER_T_S[args.workload], {"paper_p1": 2, "paper_p2": 5}[args.workload]
+            line["predictions_per_ciphertext"] = windows
+            line["predictions_per_s"] = value * windows
+            line["paper_context"] = {
+                "t_S_s": ts, "predictions_per_forward": pp, "predictions_per_s": pp / ts,
+                "note": "Tab. 1: SEAL 4.0 + HEXL (AVX-512) on one i7-1165G7 thread; context only (other "
+                        "hardware; the paper packs 768-wide windows, here windows of 2t = 2048 slots)"}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

@@ -128,6 +128,16 @@ int ctl_set_bsgs_shape(ctl_context* ctx, int chunk, int karatsuba);
  * cap (giant-step sums are carried across chunks).  Errors: CTL_EINVAL (null context or
  * zero bytes). */
 int ctl_set_keyswitch_budget(ctl_context* ctx, uint64_t bytes);
+/* Prediction windows (Sec. 3.1 "Multiple Predictions": p = floor(#slots / (2 #neurons))
+ * inputs share one ciphertext).  Dense and conv1d layers created afterwards (and the
+ * direct ctl_eval_dense / ctl_eval_conv1d calls) encode their plaintexts for p windows:
+ * the pattern of slots [0, 2t) is repeated in every window [2t w, 2t (w+1)), w < p, so
+ * each window of 2t slots is evaluated as an independent input ([x_w, x_w] at block
+ * stride t inside its window) and its output sits at the start of the window.  The
+ * rotations and the other layers are unchanged.  Default 1.  A layer whose 2 t p exceeds
+ * N/2 fails with CTL_EINVAL.  Injected coefficient plaintexts are used as given.
+ * Errors: CTL_EINVAL (p = 0 or p > N/4). */
+int ctl_set_windows(ctl_context* ctx, uint32_t p);
 #define CTL_DENSE_COMPOSED 0
 #define CTL_DENSE_LAZY_MODDOWN 1
 int ctl_set_dense_mode(ctl_context* ctx, int mode);
@@ -220,6 +230,56 @@ int ctl_add(ctl_context* ctx, const ctl_ct* a, const ctl_ct* b, ctl_ct** out);
 int ctl_mul_plain_coeffs(ctl_context* ctx, const ctl_ct* in, const int64_t* pt, double pt_scale, ctl_ct** out);
 
 /* ---------------------------------------------------------------------------------
+ * The other layers of the paper's frozen server network (Sec. 3.1 "1D Convolutions",
+ * "Average Pool", "ReLU"; Sec. 4.1: Conv1D f = 9 -> Dense 768 + approximated ReLU ->
+ * AveragePooling 3 -> Dense 766) and the operations they are built from.  Batches as
+ * above; the input is not modified; on error *out is NULL.
+ * ctl_eval_mul: HMult of two ciphertexts (same level and count): tensor product,
+ *   relinearisation (s^2 -> s key), rescale.  Scale becomes scale_a * scale_b / q_last.
+ *   ctl_eval_mul(a, a) equals ctl_eval_square(a) bit for bit.  Errors: CTL_ELEVEL
+ *   (shapes differ or level < 2), CTL_EKEY.
+ * ctl_mul_const: (C*c0, C*c1) for the integer constant C (the slot value C / c_scale in
+ *   every slot); scale becomes scale * c_scale; no rescale.
+ * ctl_add_const: adds the integer constant C to every slot (the plaintext (C, 0, .., 0)
+ *   on c0); the slot value C / scale.  Scale unchanged.
+ * ctl_drop_level: keeps the first `level` primes (reduction modulo Q_level, no division;
+ *   scale unchanged).  Errors: CTL_ELEVEL (level 0 or above the input's).
+ * ctl_eval_poly3: a[3] z^3 + a[2] z^2 + a[1] z + a[0] (a = a0..a3; the paper's ReLU
+ *   approximation is such a polynomial) at multiplicative depth 2.  With q_a, q_b the
+ *   last two primes and S the input scale: S2 = S*S/q_a, Sw = S2*S/q_b, integer
+ *   constants C3 = round(a3 q_a), C2 = round(a2 S), C1 = round(a1 (Sw q_a)/S),
+ *   C0 = round(a0 Sw) (half away from zero), and
+ *     out = HMult(square(z), rescale(C3 z) + C2) + drop(rescale(C1 z)) + C0,
+ *   level - 2, scale Sw.  Errors: CTL_ELEVEL (level < 3), CTL_EINVAL (a constant above
+ *   2^63), CTL_EKEY.
+ * ctl_eval_avgpool: stride-1 average pool of size f, (1/f) sum_{i=0}^{f-1} rot_{-i}(x):
+ *   f-1 rotations (one shared ModUp), the sum times round(q_last / f), rescale.  Output
+ *   slot s holds the mean of input slots s-f+1..s; scale unchanged.  Needs the Galois
+ *   keys of -1..-(f-1).  Errors: CTL_ELEVEL, CTL_EINVAL (f = 0 or f > N/2), CTL_EKEY.
+ * ctl_eval_conv1d: packed single-input single-output convolution with filter w[f] and
+ *   "same" zero padding on an input of length n held as [x, x] at block stride t (slots
+ *   [0, n) and [t, t+n), zeros elsewhere; n + (f-1)/2 <= t keeps the padding):
+ *   out = sum_{i<f} pt_i o rot_{i-h}(x) (+ bias), h = (f-1)/2, then rescale, with pt_i
+ *   holding w[i] in the slots s < 2t with (s mod t) < n, encoded at q_last * Delta / scale
+ *   (the output carries Delta).  Output slot s < n holds sum_i w[i] x[s+i-h], repeated at
+ *   t + s.  f plaintext products, f-1 rotations (hoisted), depth 1.  bias (nullable) has
+ *   n values.  Needs the Galois keys of i-h, i != h.  Errors: CTL_EINVAL (shape),
+ *   CTL_ELEVEL, CTL_EKEY.
+ * ctl_eval_conv1d_coeffs: the same with the f plaintexts given as integer coefficients
+ *   pts[f][N] (and bias as coefficients, nullable) at pt_scale.
+ * ------------------------------------------------------------------------------- */
+int ctl_eval_mul(ctl_context* ctx, const ctl_keys* keys, const ctl_ct* a, const ctl_ct* b, ctl_ct** out);
+int ctl_mul_const(ctl_context* ctx, const ctl_ct* in, int64_t c, double c_scale, ctl_ct** out);
+int ctl_add_const(ctl_context* ctx, const ctl_ct* in, int64_t c, ctl_ct** out);
+int ctl_drop_level(ctl_context* ctx, const ctl_ct* in, uint32_t level, ctl_ct** out);
+int ctl_eval_poly3(ctl_context* ctx, const ctl_keys* keys, const ctl_ct* in, const double* a, ctl_ct** out);
+int ctl_eval_avgpool(ctl_context* ctx, const ctl_keys* keys, const ctl_ct* in, uint32_t f, ctl_ct** out);
+int ctl_eval_conv1d(ctl_context* ctx, const ctl_keys* keys, const ctl_ct* in, const double* w, uint32_t f, uint32_t n,
+                    uint32_t t, const double* bias, ctl_ct** out);
+int ctl_eval_conv1d_coeffs(ctl_context* ctx, const ctl_keys* keys, const ctl_ct* in, const int64_t* pts, uint32_t f,
+                           const int64_t* bias, double pt_scale, ctl_ct** out);
+
+/* ---------------------------------------------------------------------------------
  * Transform access.  ctl_ntt_dev computes, for n_polys polys of `limbs` limbs each
  * ([n_polys][limbs][N] words, limb l taken modulo prime l of the chain q_0..q_{n_q-1},
  * p_0..), the negacyclic NTT a_hat[k] = a(psi^(2*bitrev(k)+1)) (psi the smallest
@@ -258,7 +318,11 @@ size_t ctl_rescale_static_capacity_words(void);
 /* ---------------------------------------------------------------------------------
  * Models: the frozen server layers of Fig. alg:cryptotl (M_S), encoded once.
  * A layer is CTL_LAYER_DENSE (W m x n, optional bias, optional injected coefficients
- * pt_coeffs[t][N]), CTL_LAYER_SQUARE or CTL_LAYER_REPLICATE (t = rep_t).  The model is
+ * pt_coeffs[t][N]), CTL_LAYER_SQUARE, CTL_LAYER_REPLICATE (t = rep_t),
+ * CTL_LAYER_CONV1D (filter W[m], f = m, input length n, block stride t = rep_t, optional
+ * bias[n], optional injected pt_coeffs[f][N]; as ctl_eval_conv1d), CTL_LAYER_POLY3 (W =
+ * the four coefficients a0..a3; as ctl_eval_poly3, two levels) or CTL_LAYER_AVGPOOL
+ * (size f = m; as ctl_eval_avgpool).  The model is
  * built for ciphertexts entering at in_level with scale in_scale; the diagonals of each
  * dense layer are encoded at the level and scale that layer will see.
  * ctl_model_forward runs ClassifyHE on a batch of ciphertexts under one key set.
@@ -267,10 +331,14 @@ size_t ctl_rescale_static_capacity_words(void);
 #define CTL_LAYER_DENSE 1
 #define CTL_LAYER_SQUARE 2
 #define CTL_LAYER_REPLICATE 3
+#define CTL_LAYER_CONV1D 4
+#define CTL_LAYER_POLY3 5
+#define CTL_LAYER_AVGPOOL 6
 typedef struct ctl_layer {
   int32_t kind;
   uint32_t m, n;              /* dense: output and input dimensions                 */
-  const double* W;            /* dense: m x n row-major (nullable if pt_coeffs)     */
+  const double* W;            /* dense: m x n row-major (nullable if pt_coeffs);
+                                 conv1d: filter[m]; poly3: a0..a3                  */
   const double* bias;         /* dense: m values or NULL                            */
   const int64_t* pt_coeffs;   /* dense: injected diagonal coefficients [t][N] or NULL */
   uint32_t rep_t;             /* replicate: shift t                                 */

@@ -785,25 +785,32 @@ uint32_t orc_bsgs_t1_lazy(uint32_t t) {
 // Diagonal plaintexts of a dense layer W (m x n, row-major) for Eq. (bsgs):
 // diag_i[r] = W[r][(r+i) mod t] (zero outside W), diag'_i = rot_{-floor(i/t1)*t1}(diag_i)
 // with diag_i placed in slots [0, t) of the full slot vector, encoded at `scale`.
-// t1 = 0 takes orc_bsgs_t1(t).
-int orc_encode_diagonals(const orc_ctx* c, const double* W, uint32_t m, uint32_t n, uint32_t t1, double scale,
-                         i64* pts) {
+// t1 = 0 takes orc_bsgs_t1(t).  With `windows` = p > 1 (Sec. 3.1 "Multiple
+// Predictions": p inputs per ciphertext, each in its own window of 2t slots), the
+// pattern of slots [0, 2t) is repeated at slots [2t w, 2t (w+1)) for w < p.
+int orc_encode_diagonals_w(const orc_ctx* c, const double* W, uint32_t m, uint32_t n, uint32_t t1, double scale,
+                           uint32_t windows, i64* pts) {
   uint32_t t = orc_bsgs_t(m, n), ns = c->N / 2;
   if (!t1) t1 = orc_bsgs_t1(t);
-  if (2 * t > ns) return -1;
+  if (windows == 0 || 2 * t * windows > ns) return -1;
   std::vector<double> v(ns);
   for (uint32_t i = 0; i < t; i++) {
     std::fill(v.begin(), v.end(), 0.0);
     uint32_t sh = (i / t1) * t1;
-    for (uint32_t r = 0; r < t; r++) {
-      uint32_t col = (r + i) % t;
-      double w = (r < m && col < n) ? W[(size_t)r * n + col] : 0.0;
-      v[r + sh] = w;
-    }
+    for (uint32_t w = 0; w < windows; w++)
+      for (uint32_t r = 0; r < t; r++) {
+        uint32_t col = (r + i) % t;
+        double x = (r < m && col < n) ? W[(size_t)r * n + col] : 0.0;
+        v[2 * t * w + r + sh] = x;
+      }
     int rc = orc_encode(c, v.data(), ns, scale, pts + (size_t)i * c->N);
     if (rc) return rc;
   }
   return 0;
+}
+int orc_encode_diagonals(const orc_ctx* c, const double* W, uint32_t m, uint32_t n, uint32_t t1, double scale,
+                         i64* pts) {
+  return orc_encode_diagonals_w(c, W, m, n, t1, scale, 1, pts);
 }
 
 // Dense layer by Eq. (bsgs) on an input laid out as [x, x] over 2t slots, as the plain
@@ -1079,17 +1086,22 @@ int orc_avgpool(const orc_ctx* c, const orc_keys* k, const u64* ct, uint32_t lvl
 // Plaintexts of the packed single-input single-output 1D convolution (Sec. 3.1 "1D
 // Convolutions", after GAZELLE): filter w[f], input of length n held as [x, x] at block
 // stride t (slots [0, n) and [t, t+n)).  pt_i has w[i] in the slots s < 2t with
-// (s mod t) < n and 0 elsewhere, encoded at `scale`.
-int orc_encode_conv(const orc_ctx* c, const double* w, uint32_t f, uint32_t n, uint32_t t, double scale, i64* pts) {
+// (s mod t) < n and 0 elsewhere, encoded at `scale`; with `windows` = p > 1 the pattern
+// repeats in each window of 2t slots (s < 2t p).
+int orc_encode_conv_w(const orc_ctx* c, const double* w, uint32_t f, uint32_t n, uint32_t t, double scale,
+                      uint32_t windows, i64* pts) {
   uint32_t ns = c->N / 2;
-  if (f == 0 || n == 0 || n > t || 2 * t > ns) return -1;
+  if (f == 0 || n == 0 || n > t || windows == 0 || 2 * t * windows > ns) return -1;
   std::vector<double> v(ns);
   for (uint32_t i = 0; i < f; i++) {
-    for (uint32_t s = 0; s < ns; s++) v[s] = (s < 2 * t && (s % t) < n) ? w[i] : 0.0;
+    for (uint32_t s = 0; s < ns; s++) v[s] = (s < 2 * t * windows && (s % t) < n) ? w[i] : 0.0;
     int rc = orc_encode(c, v.data(), ns, scale, pts + (size_t)i * c->N);
     if (rc) return rc;
   }
   return 0;
+}
+int orc_encode_conv(const orc_ctx* c, const double* w, uint32_t f, uint32_t n, uint32_t t, double scale, i64* pts) {
+  return orc_encode_conv_w(c, w, f, n, t, scale, 1, pts);
 }
 
 // 1D convolution with "same" zero padding: out = sum_{i=0}^{f-1} pt_i o rot_{i-h}(x),

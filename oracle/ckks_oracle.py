@@ -63,6 +63,10 @@ def _lib():
             "orc_bsgs_t1": (C.c_uint32, [C.c_uint32]),
             "orc_bsgs_t1_lazy": (C.c_uint32, [C.c_uint32]),
             "orc_encode_diagonals": (C.c_int, [vp, _dp, C.c_uint32, C.c_uint32, C.c_uint32, C.c_double, _i64p]),
+            "orc_encode_diagonals_w": (C.c_int, [vp, _dp, C.c_uint32, C.c_uint32, C.c_uint32, C.c_double,
+                                                 C.c_uint32, _i64p]),
+            "orc_encode_conv_w": (C.c_int, [vp, _dp, C.c_uint32, C.c_uint32, C.c_uint32, C.c_double, C.c_uint32,
+                                            _i64p]),
             "orc_dense": (C.c_int, [vp, vp, _u64p, C.c_uint32, _i64p, C.c_uint32, _i64p, _u64p, _u64p]),
             "orc_dense_lazy": (C.c_int, [vp, vp, _u64p, C.c_uint32, _i64p, C.c_uint32, _i64p, _u64p, _u64p]),
             "orc_replicate": (C.c_int, [vp, vp, _u64p, C.c_uint32, C.c_uint32, _u64p]),
@@ -298,13 +302,15 @@ class Oracle:
         t1 = cls.bsgs_t1(t, lazy)
         return list(range(1, t1)) + [k * t1 for k in range(1, t // t1)]
 
-    def encode_diagonals(self, W, scale, lazy=False):
+    def encode_diagonals(self, W, scale, lazy=False, windows=1):
+        """Diagonal plaintexts of Eq. (bsgs); windows = p repeats them in p windows of 2t
+        slots (Sec. 3.1, Multiple Predictions)."""
         W = np.ascontiguousarray(W, dtype=np.float64)
         m, n = W.shape
         t = self.bsgs_t(m, n)
         out = np.zeros((t, self.N), dtype=np.int64)
-        _chk(self.lib.orc_encode_diagonals(self.h, _p(W, _dp), m, n, self.bsgs_t1(t, lazy), scale, _p(out, _i64p)),
-             "encode_diagonals")
+        _chk(self.lib.orc_encode_diagonals_w(self.h, _p(W, _dp), m, n, self.bsgs_t1(t, lazy), scale, windows,
+                                             _p(out, _i64p)), "encode_diagonals")
         return out
 
     def dense(self, ct, pts, bias=None, lazy=False):
@@ -380,10 +386,11 @@ class Oracle:
              "avgpool")
         return out, [int(x) for x in cnt]
 
-    def encode_conv(self, w, n, t, scale):
+    def encode_conv(self, w, n, t, scale, windows=1):
         w = np.ascontiguousarray(w, dtype=np.float64)
         out = np.zeros((len(w), self.N), dtype=np.int64)
-        _chk(self.lib.orc_encode_conv(self.h, _p(w, _dp), len(w), n, t, scale, _p(out, _i64p)), "encode_conv")
+        _chk(self.lib.orc_encode_conv_w(self.h, _p(w, _dp), len(w), n, t, scale, windows, _p(out, _i64p)),
+             "encode_conv")
         return out
 
     def conv1d(self, ct, pts, bias=None):

@@ -437,6 +437,7 @@ extern "C" int ctl_context_clone(const ctl_context* c, ctl_context** out) {
   k->bsgs_chunk = c->bsgs_chunk;
   k->bsgs_karatsuba = c->bsgs_karatsuba;
   k->ks_budget = c->ks_budget;
+  k->windows = c->windows;
   k->parent = c->parent ? c->parent : c;
   if (int rc = cuda_check(cudaStreamCreateWithFlags(&k->stream, cudaStreamNonBlocking), "stream")) return rc;
   k->own_stream = true;
@@ -514,6 +515,15 @@ extern "C" int ctl_set_bsgs_shape(ctl_context* c, int chunk, int karatsuba) {
   }
   c->bsgs_chunk = chunk;
   c->bsgs_karatsuba = karatsuba;
+  return CTL_OK;
+}
+
+extern "C" int ctl_set_windows(ctl_context* c, uint32_t p) {
+  if (!c || p == 0 || p > c->N / 4) {
+    set_error("ctl_set_windows: p must be in [1, N/4]");
+    return CTL_EINVAL;
+  }
+  c->windows = p;
   return CTL_OK;
 }
 
@@ -1273,6 +1283,8 @@ int upload_plaintexts(ctl_context* c, const i64* coeffs, uint32_t cnt, uint32_t 
 
 // Diagonals of W for Eq. (bsgs): diag_i[r] = W[r][(r+i) mod t] (zero padded),
 // diag'_i = rot_{-floor(i/t1)*t1}(diag_i), i.e. diag_i placed at slots [k*t1, k*t1 + t).
+// With c->windows = p > 1 (Sec. 3.1 "Multiple Predictions") the pattern of slots [0, 2t)
+// repeats in every window [2t w, 2t (w+1)), w < p.
 int encode_diagonals(ctl_context* c, const double* W, uint32_t m, uint32_t n, uint32_t t1, double scale,
                      std::vector<i64>& pts) {
   const uint32_t t = bsgs_t(m, n), ns = c->N / 2;
@@ -1281,10 +1293,11 @@ int encode_diagonals(ctl_context* c, const double* W, uint32_t m, uint32_t n, ui
   for (uint32_t i = 0; i < t; i++) {
     std::fill(v.begin(), v.end(), 0.0);
     const uint32_t sh = (i / t1) * t1;
-    for (uint32_t r = 0; r < t; r++) {
-      const uint32_t col = (r + i) % t;
-      v[r + sh] = (r < m && col < n) ? W[(size_t)r * n + col] : 0.0;
-    }
+    for (uint32_t w = 0; w < c->windows; w++)
+      for (uint32_t r = 0; r < t; r++) {
+        const uint32_t col = (r + i) % t;
+        v[2 * t * w + r + sh] = (r < m && col < n) ? W[(size_t)r * n + col] : 0.0;
+      }
     if (!c->enc.encode(v.data(), ns, scale, &pts[(size_t)i * c->N])) {
       set_error("dense: diagonal encoding overflow");
       return CTL_EINVAL;
@@ -1308,8 +1321,8 @@ int dense_prepare(ctl_context* c, DenseLayer& D, const double* W, const double* 
     set_error("dense: needs two live primes");
     return CTL_ELEVEL;
   }
-  if (2 * D.t > c->N / 2 || D.t == 0 || (D.t & (D.t - 1))) {
-    set_error("dense: t=%u does not fit N/2 slots with the [x, x] layout", D.t);
+  if (2 * D.t * c->windows > c->N / 2 || D.t == 0 || (D.t & (D.t - 1))) {
+    set_error("dense: t=%u does not fit N/2 slots with the [x, x] layout in %u windows", D.t, c->windows);
     return CTL_EINVAL;
   }
   const double ql = (double)c->moduli[lvl - 1];
@@ -1338,7 +1351,8 @@ int dense_prepare(ctl_context* c, DenseLayer& D, const double* W, const double* 
   const i64* bsrc = (const i64*)bias_in;
   if (!bsrc && bias) {
     std::vector<double> v(c->N / 2, 0.0);
-    for (uint32_t r = 0; r < m; r++) v[r] = bias[r];
+    for (uint32_t w = 0; w < c->windows; w++)
+      for (uint32_t r = 0; r < m; r++) v[2 * D.t * w + r] = bias[r];
     benc.resize(c->N);
     if (!c->enc.encode(v.data(), v.size(), in_scale * D.pt_scale, benc.data())) {
       set_error("dense: bias encoding overflow");
@@ -1620,6 +1634,422 @@ extern "C" int ctl_mul_plain_coeffs(ctl_context* c, const ctl_ct* in, const int6
   return last_cuda("mul_plain");
 }
 
+// =====================================================================================
+// The other layers of the paper's frozen network (Sec. 3.1): the ciphertext product,
+// constant products and sums, level drop, the degree-3 ReLU approximation, average
+// pooling and the packed 1D convolution.
+// =====================================================================================
+namespace {
+inline u64 h_from_signed(i64 v, u64 q) {
+  const u64 a = (u64)(v < 0 ? -(v + 1) : v) % q;  // |v| or |v|-1 without overflow
+  if (v >= 0) return a;
+  const u64 m = (a + 1) % q;  // |v| mod q
+  return m ? q - m : 0;
+}
+
+// Per-limb constants for launch_affine / launch_sum_scale over the first lvl primes.
+int limb_consts(ctl_context* c, int lvl, bool has_m, i64 mul, i64 add, LimbConsts& K) {
+  if (lvl > kMaxConstLimbs) {
+    set_error("level %d above the %d limbs of constant-operand kernels", lvl, kMaxConstLimbs);
+    return CTL_ENOTSUP;
+  }
+  for (int i = 0; i < kMaxConstLimbs; i++) K.m[i] = K.a[i] = 0;
+  for (int i = 0; i < lvl; i++) {
+    const u64 q = c->moduli[i];
+    K.m[i] = has_m ? h_mont(h_from_signed(mul, q), q) : 0;
+    K.a[i] = h_from_signed(add, q);
+  }
+  return CTL_OK;
+}
+
+// round(v), half away from zero, if it fits a 64-bit integer.
+bool to_i64(double v, i64* out) {
+  if (!(std::fabs(v) < 9.0e18)) return false;
+  *out = (i64)std::llround(v);
+  return true;
+}
+
+// HMult of two batches at level lvl: tensor, relinearisation, rescale.
+int mul_into(ctl_context* c, const ctl_keys* k, const u64* a, const u64* b, int nb, int lvl, u64* out) {
+  const uint32_t N = c->N;
+  auto it = k->evk.find(0);
+  if (it == k->evk.end()) {
+    set_error("missing relinearisation key");
+    return CTL_EKEY;
+  }
+  const size_t LN = (size_t)lvl * N;
+  DBuf d(c, (size_t)nb * 3 * LN), r(c, (size_t)nb * 2 * LN);
+  if (!d.p || !r.p) {
+    set_error("mul: allocation failed");
+    return CTL_ENOMEM;
+  }
+  launch_tensor2(c, a, b, d.p, nb, lvl);
+  int rc = keyswitch(c, 1, nb, lvl, d.p + 2 * LN, 0, 3 * LN, {it->second}, {1}, d.p, 0, 3 * LN, LN, true, r.p);
+  if (rc) return rc;
+  c->op_relin += nb;
+  return rescale_into(c, r.p, nb, lvl, out);
+}
+
+// Constants of the degree-3 polynomial at level lvl (q_a = q_{lvl-1}, q_b = q_{lvl-2}):
+// S2 = S*S/q_a, Sw = S2*S/q_b, C3 = round(a3*q_a), C2 = round(a2*S),
+// C1 = round(a1*((Sw*q_a)/S)), C0 = round(a0*Sw), rounding half away from zero.
+int poly3_consts(ctl_context* c, int lvl, double S, const double* a, i64 C[4], double* Sw_out) {
+  if (lvl < 3) {
+    set_error("poly3: needs three live primes (depth 2)");
+    return CTL_ELEVEL;
+  }
+  const double qa = (double)c->moduli[lvl - 1], qb = (double)c->moduli[lvl - 2];
+  const double S2 = S * S / qa;
+  const double Sw = S2 * S / qb;
+  if (!to_i64(a[3] * qa, &C[3]) || !to_i64(a[2] * S, &C[2]) || !to_i64(a[1] * (Sw * qa / S), &C[1]) ||
+      !to_i64(a[0] * Sw, &C[0])) {
+    set_error("poly3: a coefficient does not fit a 64-bit constant at this scale");
+    return CTL_EINVAL;
+  }
+  *Sw_out = Sw;
+  return CTL_OK;
+}
+
+// a3 z^3 + a2 z^2 + a1 z + a0 at depth 2:
+//   z2 = square(z); v = rescale(C3 z) + C2; w = HMult(z2, v); l = drop(rescale(C1 z));
+//   out = w + l + C0 (level lvl-2, scale Sw).
+int poly3_into(ctl_context* c, const ctl_keys* k, const u64* in, int nb, int lvl, double S, const double* a, u64* out,
+               double* out_scale) {
+  const uint32_t N = c->N;
+  i64 C[4];
+  double Sw;
+  if (int rc = poly3_consts(c, lvl, S, a, C, &Sw)) return rc;
+  LimbConsts K3, K2, K1, K0;
+  if (int rc = limb_consts(c, lvl, true, C[3], 0, K3)) return rc;
+  limb_consts(c, lvl, false, 0, C[2], K2);
+  limb_consts(c, lvl, true, C[1], 0, K1);
+  limb_consts(c, lvl, false, 0, C[0], K0);
+  const size_t L0 = (size_t)lvl * N, L1 = (size_t)(lvl - 1) * N, L2 = (size_t)(lvl - 2) * N;
+  DBuf z2(c, (size_t)nb * 2 * L1), t(c, (size_t)nb * 2 * L0), v(c, (size_t)nb * 2 * L1), w(c, (size_t)nb * 2 * L2);
+  if (!z2.p || !t.p || !v.p || !w.p) {
+    set_error("poly3: allocation failed");
+    return CTL_ENOMEM;
+  }
+  int rc = square_into(c, k, in, nb, lvl, z2.p);
+  if (rc) return rc;
+  launch_affine(c, in, L0, nullptr, 0, t.p, L0, K3, true, 2 * nb, lvl);
+  if ((rc = rescale_into(c, t.p, nb, lvl, v.p))) return rc;
+  launch_affine(c, v.p, L1, nullptr, 0, v.p, L1, K2, false, 2 * nb, lvl - 1);
+  if ((rc = mul_into(c, k, z2.p, v.p, nb, lvl - 1, w.p))) return rc;
+  launch_affine(c, in, L0, nullptr, 0, t.p, L0, K1, true, 2 * nb, lvl);
+  if ((rc = rescale_into(c, t.p, nb, lvl, v.p))) return rc;  // l at level lvl-1, read on lvl-2 limbs
+  launch_affine(c, w.p, L2, v.p, L1, out, L2, K0, false, 2 * nb, lvl - 2);
+  c->op_ptmul += 2 * nb;
+  c->op_add += 2 * nb;
+  *out_scale = Sw;
+  return last_cuda("poly3");
+}
+
+// Average pool of size f: (sum_{i<f} rot_{-i}(x)) * round(q_{lvl-1}/f), rescaled.
+int avgpool_into(ctl_context* c, const ctl_keys* k, const u64* in, int nb, int lvl, uint32_t f, u64* out) {
+  if (lvl < 2 || f == 0 || f > (uint32_t)c->N / 2) {
+    set_error("avgpool: invalid size or no level left");
+    return f == 0 || f > (uint32_t)c->N / 2 ? CTL_EINVAL : CTL_ELEVEL;
+  }
+  const size_t cw = ct_words(c, lvl, nb);
+  i64 Cf;
+  to_i64((double)c->moduli[lvl - 1] / (double)f, &Cf);
+  LimbConsts K;
+  if (int rc = limb_consts(c, lvl, true, Cf, 0, K)) return rc;
+  DBuf rots(c, (size_t)(f > 1 ? f - 1 : 1) * cw), s(c, cw);
+  if (!rots.p || !s.p) {
+    set_error("avgpool: allocation failed");
+    return CTL_ENOMEM;
+  }
+  std::vector<int64_t> r;
+  for (uint32_t i = 1; i < f; i++) r.push_back(-(int64_t)i);
+  if (!r.empty())
+    if (int rc = rotate_many(c, k, in, nb, lvl, r, rots.p)) return rc;
+  launch_sum_scale(c, in, rots.p, (int)f - 1, s.p, K, nb, lvl);
+  c->op_add += (f - 1) * nb;
+  c->op_ptmul += nb;
+  return rescale_into(c, s.p, nb, lvl, out);
+}
+}  // namespace
+
+// Packed single-input single-output 1D convolution layer (Sec. 3.1 "1D Convolutions").
+struct ConvLayer {
+  uint32_t f = 0, n = 0, t = 0, lvl = 0;
+  double pt_scale = 0, in_scale = 0, out_scale = 0;
+  u64* pts = nullptr;   // [f][lvl][N], NTT + Montgomery form
+  u64* bias = nullptr;  // [lvl][N], NTT form, or null
+};
+
+namespace {
+// Plaintexts of the convolution: pt_i has w[i] in the slots s < 2t with (s mod t) < n.
+int conv_prepare(ctl_context* c, ConvLayer& V, const double* w, const double* bias, const int64_t* pts_in,
+                 const int64_t* bias_in, uint32_t f, uint32_t n, uint32_t t, uint32_t lvl, double in_scale,
+                 double pt_scale) {
+  V.f = f;
+  V.n = n;
+  V.t = t;
+  V.lvl = lvl;
+  V.in_scale = in_scale;
+  if (lvl < 2) {
+    set_error("conv1d: needs two live primes");
+    return CTL_ELEVEL;
+  }
+  if (f == 0 || f > (uint32_t)c->N / 2 || (!pts_in && (n == 0 || n > t || 2 * t * c->windows > c->N / 2))) {
+    set_error("conv1d: invalid shape (f=%u n=%u t=%u)", f, n, t);
+    return CTL_EINVAL;
+  }
+  const double ql = (double)c->moduli[lvl - 1];
+  V.pt_scale = pt_scale > 0 ? pt_scale : ql * (c->scale / in_scale);
+  V.out_scale = pt_scale > 0 ? in_scale * pt_scale / ql : c->scale;
+  std::vector<i64> enc;
+  const i64* src = (const i64*)pts_in;
+  if (!src) {
+    const uint32_t ns = c->N / 2;
+    enc.assign((size_t)f * c->N, 0);
+    std::vector<double> v(ns);
+    for (uint32_t i = 0; i < f; i++) {
+      for (uint32_t s = 0; s < ns; s++) v[s] = (s < 2 * t * c->windows && (s % t) < n) ? w[i] : 0.0;
+      if (!c->enc.encode(v.data(), ns, V.pt_scale, &enc[(size_t)i * c->N])) {
+        set_error("conv1d: plaintext encoding overflow");
+        return CTL_EINVAL;
+      }
+    }
+    src = enc.data();
+  }
+  if (int rc = upload_plaintexts(c, src, f, lvl, lvl, true, &V.pts)) return rc;
+  std::vector<i64> benc;
+  const i64* bsrc = (const i64*)bias_in;
+  if (!bsrc && bias) {
+    std::vector<double> v(c->N / 2, 0.0);
+    for (uint32_t w = 0; w < c->windows; w++)
+      for (uint32_t s = 0; s < n; s++) v[2 * t * w + s] = v[2 * t * w + t + s] = bias[s];
+    benc.resize(c->N);
+    if (!c->enc.encode(v.data(), v.size(), in_scale * V.pt_scale, benc.data())) {
+      set_error("conv1d: bias encoding overflow");
+      return CTL_EINVAL;
+    }
+    bsrc = benc.data();
+  }
+  if (bsrc)
+    if (int rc = upload_plaintexts(c, bsrc, 1, lvl, lvl, false, &V.bias)) return rc;
+  return CTL_OK;
+}
+
+void conv_release(ctl_context* c, ConvLayer& V) {
+  dev_free(c, V.pts);
+  dev_free(c, V.bias);
+  V.pts = V.bias = nullptr;
+}
+
+// out = rescale(sum_{i<f} pt_i o rot_{i-h}(x) [+ bias]), h = (f-1)/2; the rotations share
+// one ModUp (hoisted) and each is bit-identical to ctl_rotate.
+int conv_apply(ctl_context* c, const ctl_keys* k, const ConvLayer& V, const u64* in, int nb, u64* out) {
+  const int lvl = (int)V.lvl;
+  const size_t cw = ct_words(c, lvl, nb);
+  DBuf rots(c, (size_t)V.f * cw), acc(c, cw);
+  if (!rots.p || !acc.p) {
+    set_error("conv1d: allocation failed");
+    return CTL_ENOMEM;
+  }
+  const int64_t h = ((int64_t)V.f - 1) / 2;
+  std::vector<int64_t> r;
+  for (uint32_t i = 0; i < V.f; i++) r.push_back((int64_t)i - h);
+  if (int rc = rotate_many(c, k, in, nb, lvl, r, rots.p)) return rc;
+  launch_pt_mac(c, rots.p, V.pts, (int)V.f, acc.p, nb, lvl);
+  c->op_ptmul += (uint64_t)V.f * nb;
+  c->op_add += (uint64_t)(V.f - 1) * nb;
+  if (V.bias) launch_add_plain(c, acc.p, V.bias, nb, lvl, (size_t)2 * lvl * c->N);
+  return rescale_into(c, acc.p, nb, lvl, out);
+}
+}  // namespace
+
+extern "C" int ctl_eval_mul(ctl_context* c, const ctl_keys* k, const ctl_ct* a, const ctl_ct* b, ctl_ct** out) {
+  if (!c || !k || !a || !b || !out) {
+    set_error("ctl_eval_mul: null argument");
+    return CTL_EINVAL;
+  }
+  *out = nullptr;
+  if (a->level != b->level || a->count != b->count) {
+    set_error("ctl_eval_mul: shape mismatch");
+    return CTL_ELEVEL;
+  }
+  if (a->level < 2) {
+    set_error("ctl_eval_mul: no level left");
+    return CTL_ELEVEL;
+  }
+  ctl_ct* o = new_ct(c, a->level - 1, a->count, a->scale * b->scale / (double)c->moduli[a->level - 1]);
+  if (!o) {
+    set_error("ctl_eval_mul: allocation failed");
+    return CTL_ENOMEM;
+  }
+  int rc = mul_into(c, k, a->d, b->d, (int)a->count, (int)a->level, o->d);
+  if (rc) {
+    ctl_ct_destroy(o);
+    return rc;
+  }
+  *out = o;
+  return CTL_OK;
+}
+
+static int affine_common(ctl_context* c, const ctl_ct* in, bool has_m, int64_t mul, int64_t add, double out_scale,
+                         ctl_ct** out) {
+  if (!c || !in || !out) {
+    set_error("constant operation: null argument");
+    return CTL_EINVAL;
+  }
+  *out = nullptr;
+  LimbConsts K;
+  if (int rc = limb_consts(c, (int)in->level, has_m, mul, add, K)) return rc;
+  ctl_ct* o = new_ct(c, in->level, in->count, out_scale);
+  if (!o) {
+    set_error("constant operation: allocation failed");
+    return CTL_ENOMEM;
+  }
+  const size_t LN = (size_t)in->level * c->N;
+  launch_affine(c, in->d, LN, nullptr, 0, o->d, LN, K, has_m, (int)(2 * in->count), (int)in->level);
+  *out = o;
+  return last_cuda("constant operation");
+}
+
+extern "C" int ctl_mul_const(ctl_context* c, const ctl_ct* in, int64_t cst, double c_scale, ctl_ct** out) {
+  if (!(c_scale > 0)) {
+    set_error("ctl_mul_const: invalid constant scale");
+    return CTL_EINVAL;
+  }
+  if (!in) {
+    set_error("ctl_mul_const: null argument");
+    return CTL_EINVAL;
+  }
+  int rc = affine_common(c, in, true, cst, 0, in->scale * c_scale, out);
+  if (!rc) c->op_ptmul += in->count;
+  return rc;
+}
+
+extern "C" int ctl_add_const(ctl_context* c, const ctl_ct* in, int64_t cst, ctl_ct** out) {
+  if (!in) {
+    set_error("ctl_add_const: null argument");
+    return CTL_EINVAL;
+  }
+  return affine_common(c, in, false, 0, cst, in->scale, out);
+}
+
+extern "C" int ctl_drop_level(ctl_context* c, const ctl_ct* in, uint32_t level, ctl_ct** out) {
+  if (!c || !in || !out) {
+    set_error("ctl_drop_level: null argument");
+    return CTL_EINVAL;
+  }
+  *out = nullptr;
+  if (level == 0 || level > in->level) {
+    set_error("ctl_drop_level: level %u not in [1, %u]", level, in->level);
+    return CTL_ELEVEL;
+  }
+  ctl_ct* o = new_ct(c, level, in->count, in->scale);
+  if (!o) {
+    set_error("ctl_drop_level: allocation failed");
+    return CTL_ENOMEM;
+  }
+  const size_t N = c->N;
+  cudaMemcpy2DAsync(o->d, (size_t)level * N * sizeof(u64), in->d, (size_t)in->level * N * sizeof(u64),
+                    (size_t)level * N * sizeof(u64), (size_t)2 * in->count, cudaMemcpyDeviceToDevice, c->stream);
+  *out = o;
+  return last_cuda("drop_level");
+}
+
+extern "C" int ctl_eval_poly3(ctl_context* c, const ctl_keys* k, const ctl_ct* in, const double* a, ctl_ct** out) {
+  if (!c || !k || !in || !a || !out) {
+    set_error("ctl_eval_poly3: null argument");
+    return CTL_EINVAL;
+  }
+  *out = nullptr;
+  i64 C[4];
+  double Sw;
+  if (int rc = poly3_consts(c, (int)in->level, in->scale, a, C, &Sw)) return rc;
+  ctl_ct* o = new_ct(c, in->level - 2, in->count, Sw);
+  if (!o) {
+    set_error("ctl_eval_poly3: allocation failed");
+    return CTL_ENOMEM;
+  }
+  int rc = poly3_into(c, k, in->d, (int)in->count, (int)in->level, in->scale, a, o->d, &Sw);
+  if (rc) {
+    ctl_ct_destroy(o);
+    return rc;
+  }
+  *out = o;
+  return CTL_OK;
+}
+
+extern "C" int ctl_eval_avgpool(ctl_context* c, const ctl_keys* k, const ctl_ct* in, uint32_t f, ctl_ct** out) {
+  if (!c || !k || !in || !out) {
+    set_error("ctl_eval_avgpool: null argument");
+    return CTL_EINVAL;
+  }
+  *out = nullptr;
+  if (in->level < 2) {
+    set_error("ctl_eval_avgpool: no level left");
+    return CTL_ELEVEL;
+  }
+  ctl_ct* o = new_ct(c, in->level - 1, in->count, in->scale);
+  if (!o) {
+    set_error("ctl_eval_avgpool: allocation failed");
+    return CTL_ENOMEM;
+  }
+  int rc = avgpool_into(c, k, in->d, (int)in->count, (int)in->level, f, o->d);
+  if (rc) {
+    ctl_ct_destroy(o);
+    return rc;
+  }
+  *out = o;
+  return CTL_OK;
+}
+
+static int conv_common(ctl_context* c, const ctl_keys* k, const ctl_ct* in, const double* w, const double* bias,
+                       const int64_t* pts, const int64_t* bias_c, uint32_t f, uint32_t n, uint32_t t, double pt_scale,
+                       ctl_ct** out) {
+  if (!c || !k || !in || !out) {
+    set_error("conv1d: null argument");
+    return CTL_EINVAL;
+  }
+  *out = nullptr;
+  ConvLayer V;
+  int rc = conv_prepare(c, V, w, bias, pts, bias_c, f, n, t, in->level, in->scale, pt_scale);
+  if (rc) {
+    conv_release(c, V);
+    return rc;
+  }
+  ctl_ct* o = new_ct(c, in->level - 1, in->count, V.out_scale);
+  if (!o) {
+    conv_release(c, V);
+    set_error("conv1d: allocation failed");
+    return CTL_ENOMEM;
+  }
+  rc = conv_apply(c, k, V, in->d, (int)in->count, o->d);
+  conv_release(c, V);
+  if (rc) {
+    ctl_ct_destroy(o);
+    return rc;
+  }
+  *out = o;
+  return CTL_OK;
+}
+
+extern "C" int ctl_eval_conv1d(ctl_context* c, const ctl_keys* k, const ctl_ct* in, const double* w, uint32_t f,
+                               uint32_t n, uint32_t t, const double* bias, ctl_ct** out) {
+  if (!w) {
+    set_error("ctl_eval_conv1d: null filter");
+    return CTL_EINVAL;
+  }
+  return conv_common(c, k, in, w, bias, nullptr, nullptr, f, n, t, 0.0, out);
+}
+
+extern "C" int ctl_eval_conv1d_coeffs(ctl_context* c, const ctl_keys* k, const ctl_ct* in, const int64_t* pts,
+                                      uint32_t f, const int64_t* bias, double pt_scale, ctl_ct** out) {
+  if (!pts || !(pt_scale > 0)) {
+    set_error("ctl_eval_conv1d_coeffs: invalid plaintexts");
+    return CTL_EINVAL;
+  }
+  return conv_common(c, k, in, nullptr, nullptr, pts, bias, f, 0, 0, pt_scale, out);
+}
+
 extern "C" int ctl_ntt_dev(ctl_context* c, const uint64_t* in, uint64_t* out, uint32_t n_polys, uint32_t limbs,
                            int inverse) {
   if (!c || !in || !out || limbs == 0 || limbs > c->L + c->K || n_polys == 0) {
@@ -1643,6 +2073,9 @@ extern "C" int ctl_ntt_dev(ctl_context* c, const uint64_t* in, uint64_t* out, ui
 struct LayerPlan {
   int kind = 0;
   DenseLayer dense;
+  ConvLayer conv;
+  double poly[4] = {0, 0, 0, 0};  // poly3: a0..a3
+  uint32_t pool_f = 0;            // avgpool: size f
   uint32_t rep_t = 0;
   uint32_t in_level = 0;
   double in_scale = 0, out_scale = 0;
@@ -1682,7 +2115,10 @@ extern "C" int ctl_model_create(ctl_context* c, const ctl_layer* layers, uint32_
   double sc = in_scale;
   std::vector<int32_t> rots;
   auto fail = [&](int rc) {
-    for (auto& L : M->layers) dense_release(c, L.dense);
+    for (auto& L : M->layers) {
+      dense_release(c, L.dense);
+      conv_release(c, L.conv);
+    }
     return rc;
   };
   for (uint32_t i = 0; i < n_layers; i++) {
@@ -1720,6 +2156,41 @@ extern "C" int ctl_model_create(ctl_context* c, const ctl_layer* layers, uint32_
       }
       P.rep_t = ly.rep_t;
       rots.push_back(-(int32_t)ly.rep_t);
+    } else if (ly.kind == CTL_LAYER_CONV1D) {
+      if (ly.m == 0 || (!ly.W && !ly.pt_coeffs)) {
+        set_error("ctl_model_create: conv1d layer %u needs a filter or coefficients", i);
+        return fail(CTL_EINVAL);
+      }
+      if (int rc = conv_prepare(c, P.conv, ly.W, ly.bias, ly.pt_coeffs, nullptr, ly.m, ly.n, ly.rep_t, lvl, sc,
+                                0.0)) {
+        M->layers.push_back(P);
+        return fail(rc);
+      }
+      M->bytes += (uint64_t)P.conv.f * lvl * c->N * 8;
+      const int32_t h = ((int32_t)ly.m - 1) / 2;
+      for (int32_t j = 0; j < (int32_t)ly.m; j++)
+        if (j != h) rots.push_back(j - h);
+      sc = P.conv.out_scale;
+      lvl--;
+    } else if (ly.kind == CTL_LAYER_POLY3) {
+      if (!ly.W) {
+        set_error("ctl_model_create: poly3 layer %u needs its four coefficients in W", i);
+        return fail(CTL_EINVAL);
+      }
+      i64 C[4];
+      double Sw;
+      if (int rc = poly3_consts(c, (int)lvl, sc, ly.W, C, &Sw)) return fail(rc);
+      for (int j = 0; j < 4; j++) P.poly[j] = ly.W[j];
+      sc = Sw;
+      lvl -= 2;
+    } else if (ly.kind == CTL_LAYER_AVGPOOL) {
+      if (ly.m == 0 || ly.m > c->N / 2 || lvl < 2) {
+        set_error("ctl_model_create: avgpool layer %u: invalid size or no level left", i);
+        return fail(lvl < 2 ? CTL_ELEVEL : CTL_EINVAL);
+      }
+      P.pool_f = ly.m;
+      for (uint32_t j = 1; j < ly.m; j++) rots.push_back(-(int32_t)j);
+      lvl--;
     } else {
       set_error("ctl_model_create: unknown layer kind %d", ly.kind);
       return fail(CTL_EINVAL);
@@ -1746,7 +2217,10 @@ extern "C" void ctl_model_destroy(ctl_model* M) {
     dev_free(gc, kv.second.out_buf);
     cudaStreamSynchronize(gc->stream);
   }
-  for (auto& L : M->layers) dense_release(M->ctx, L.dense);
+  for (auto& L : M->layers) {
+    dense_release(M->ctx, L.dense);
+    conv_release(M->ctx, L.conv);
+  }
   cudaStreamSynchronize(M->ctx->stream);
   delete M;
 }
@@ -1794,6 +2268,16 @@ static int model_run(ctl_context* c, const ctl_model* M, const ctl_keys* k, cons
       lvl--;
     } else if (P.kind == CTL_LAYER_SQUARE) {
       rc = square_into(c, k, cur, nb, (int)lvl, dst);
+      lvl--;
+    } else if (P.kind == CTL_LAYER_CONV1D) {
+      rc = conv_apply(c, k, P.conv, cur, nb, dst);
+      lvl--;
+    } else if (P.kind == CTL_LAYER_POLY3) {
+      double sw;
+      rc = poly3_into(c, k, cur, nb, (int)lvl, P.in_scale, P.poly, dst, &sw);
+      lvl -= 2;
+    } else if (P.kind == CTL_LAYER_AVGPOOL) {
+      rc = avgpool_into(c, k, cur, nb, (int)lvl, P.pool_f, dst);
       lvl--;
     } else {
       rc = rotate_many(c, k, cur, nb, (int)lvl, {-(int64_t)P.rep_t}, dst);

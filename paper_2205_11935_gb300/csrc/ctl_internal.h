@@ -182,6 +182,7 @@ struct ctl_context {
   int dense_mode = CTL_DENSE_COMPOSED;          // ctl_set_dense_mode
   int bsgs_chunk = 32, bsgs_karatsuba = 1;      // ctl_set_bsgs_shape (measured fastest)
   uint64_t ks_budget = 16ull << 30;              // ctl_set_keyswitch_budget
+  uint32_t windows = 1;                          // ctl_set_windows: prediction windows per ciphertext
   const ctl_context* parent = nullptr;  // clones share the parent's device tables
 };
 
@@ -321,5 +322,26 @@ void launch_bsgs_wino_diag(ctl_context* c, const u64* diag, size_t diag_stride, 
 // split product: on limbs whose prime has split width w > 0,
 // v -> (v >> w) << 32 | (v & (2^w - 1)).
 void launch_split_limbs(ctl_context* c, u64* data, int cnt, int limbs, int lvl);
+
+// Kernels of the other layers of the paper's network (kernels.cu).
+// Per-limb constants passed by value: m[i] a multiplier in Montgomery form
+// (m_plain * 2^64 mod q_i), a[i] an addend residue.  Levels above kMaxConstLimbs are
+// refused by the callers.
+constexpr int kMaxConstLimbs = 64;
+struct LimbConsts {
+  u64 m[kMaxConstLimbs];
+  u64 a[kMaxConstLimbs];
+};
+// (a, b) -> (a0 b0, a0 b1 + a1 b0, a1 b1) for nb ciphertext pairs; d [nb][3][lvl][N].
+void launch_tensor2(ctl_context* c, const u64* a, const u64* b, u64* d, int nb, int lvl);
+// out[pp] = in[pp] * m (if has_m) + add[pp] (if add non-null) + (pp even ? a : 0), for
+// n_polys polys (two per ciphertext, poly 0 first) spaced by s_in / s_add / s_out words.
+void launch_affine(ctl_context* c, const u64* in, size_t s_in, const u64* add, size_t s_add, u64* out, size_t s_out,
+                   const LimbConsts& K, bool has_m, int n_polys, int lvl);
+// out = (x + sum_{r < nr} rots[r]) * m, x and out [nb][2][lvl][N], rots [nr][nb][2][lvl][N].
+void launch_sum_scale(ctl_context* c, const u64* x, const u64* rots, int nr, u64* out, const LimbConsts& K, int nb,
+                      int lvl);
+// out = sum_{i < f} rots[i] o pts[i] (pts [f][lvl][N], Montgomery form), in increasing i.
+void launch_pt_mac(ctl_context* c, const u64* rots, const u64* pts, int f, u64* out, int nb, int lvl);
 
 }  // namespace ctl

@@ -844,4 +844,110 @@ void launch_bsgs_inner(ctl_context* c, const u64* baby, const u64* diag, size_t 
 #undef CTL_BSGS_CASE
 }
 
+// ---------------------------------------------------------------------------------
+// Kernels of the other layers of the paper's frozen network (Sec. 3.1: ReLU
+// approximation, average pooling, 1D convolution).  All are element-wise over the
+// NTT domain and bound by HBM traffic.
+// ---------------------------------------------------------------------------------
+// Tensor of two ciphertexts: (a0 b0, a0 b1 + a1 b0, a1 b1); d [nb][3][lvl][N].
+__global__ void k_tensor2(const u64* __restrict__ a, const u64* __restrict__ b, u64* __restrict__ d,
+                          const DPrime* __restrict__ pr, int logN, int lvl, size_t total) {
+  const size_t N = (size_t)1 << logN;
+  const size_t LN = (size_t)lvl * N;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t j = idx / LN, r = idx % LN;
+    const int i = (int)(r >> logN);
+    const DPrime P = pr[i];
+    const u64 a0 = a[j * 2 * LN + r], a1 = a[j * 2 * LN + LN + r];
+    const u64 b0m = mulmod_mont(b[j * 2 * LN + r], P.r2, P.q, P.qinv);       // b0 * R
+    const u64 b1m = mulmod_mont(b[j * 2 * LN + LN + r], P.r2, P.q, P.qinv);  // b1 * R
+    d[j * 3 * LN + r] = mulmod_mont(a0, b0m, P.q, P.qinv);
+    d[j * 3 * LN + LN + r] = addmod(mulmod_mont(a0, b1m, P.q, P.qinv), mulmod_mont(a1, b0m, P.q, P.qinv), P.q);
+    d[j * 3 * LN + 2 * LN + r] = mulmod_mont(a1, b1m, P.q, P.qinv);
+  }
+}
+void launch_tensor2(ctl_context* c, const u64* a, const u64* b, u64* d, int nb, int lvl) {
+  size_t total = (size_t)nb * lvl * c->N;
+  if (!total) return;
+  int g = elem_grid(c, total);
+  CTL_LAUNCH(KC_ELEM, 6.0 * total, g,
+             (k_tensor2<<<g, kThreads, 0, c->stream>>>(a, b, d, c->d_primes, (int)c->logN, lvl, total)));
+}
+
+// out[pp] = in[pp] * m_i (if has_m) + add[pp] (if add) + (pp even ? a_i : 0), for the
+// polys pp = 0..n_polys-1 (two per ciphertext), limb i -> prime i.
+__global__ void k_affine(const u64* in, size_t s_in, const u64* add, size_t s_add, u64* out, size_t s_out,
+                         const __grid_constant__ LimbConsts K, bool has_m, const DPrime* __restrict__ pr, int logN,
+                         int lvl, size_t total) {
+  const size_t N = (size_t)1 << logN;
+  const size_t LN = (size_t)lvl * N;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t pp = idx / LN, r = idx % LN;
+    const int i = (int)(r >> logN);
+    const u64 q = pr[i].q;
+    u64 v = in[pp * s_in + r];
+    if (has_m) v = mulmod_mont(v, K.m[i], q, pr[i].qinv);
+    if (add) v = addmod(v, add[pp * s_add + r], q);
+    if (!(pp & 1)) v = addmod(v, K.a[i], q);
+    out[pp * s_out + r] = v;
+  }
+}
+void launch_affine(ctl_context* c, const u64* in, size_t s_in, const u64* add, size_t s_add, u64* out, size_t s_out,
+                   const LimbConsts& K, bool has_m, int n_polys, int lvl) {
+  size_t total = (size_t)n_polys * lvl * c->N;
+  if (!total) return;
+  int g = elem_grid(c, total);
+  CTL_LAUNCH(KC_ELEM, has_m ? (double)total : 0.0, g,
+             (k_affine<<<g, kThreads, 0, c->stream>>>(in, s_in, add, s_add, out, s_out, K, has_m, c->d_primes,
+                                                     (int)c->logN, lvl, total)));
+}
+
+// out[j] = (x[j] + sum_{r < nr} rots[r][j]) * m_i over nb ciphertexts [nb][2][lvl][N];
+// rots [nr][nb][2][lvl][N].
+__global__ void k_sum_scale(const u64* __restrict__ x, const u64* __restrict__ rots, int nr, u64* __restrict__ out,
+                            const __grid_constant__ LimbConsts K, const DPrime* __restrict__ pr, int logN, int lvl,
+                            size_t total) {
+  const size_t N = (size_t)1 << logN;
+  const size_t LN = (size_t)lvl * N;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)((idx % LN) >> logN);
+    const u64 q = pr[i].q;
+    u64 s = x[idx];
+    for (int r = 0; r < nr; r++) s = addmod(s, rots[(size_t)r * total + idx], q);
+    out[idx] = mulmod_mont(s, K.m[i], q, pr[i].qinv);
+  }
+}
+void launch_sum_scale(ctl_context* c, const u64* x, const u64* rots, int nr, u64* out, const LimbConsts& K, int nb,
+                      int lvl) {
+  size_t total = (size_t)nb * 2 * lvl * c->N;
+  if (!total) return;
+  int g = elem_grid(c, total);
+  CTL_LAUNCH(KC_ELEM, (double)total, g,
+             (k_sum_scale<<<g, kThreads, 0, c->stream>>>(x, rots, nr, out, K, c->d_primes, (int)c->logN, lvl,
+                                                        total)));
+}
+
+// out[j] = sum_{i < f} rots[i][j] o pts[i] over nb ciphertexts [nb][2][lvl][N]; rots
+// [f][nb][2][lvl][N]; pts [f][lvl][N] in Montgomery form; sums in increasing i.
+__global__ void k_pt_mac(const u64* __restrict__ rots, const u64* __restrict__ pts, int f, u64* __restrict__ out,
+                         const DPrime* __restrict__ pr, int logN, int lvl, size_t total) {
+  const size_t N = (size_t)1 << logN;
+  const size_t LN = (size_t)lvl * N;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t r = idx % LN;
+    const int i = (int)(r >> logN);
+    const u64 q = pr[i].q, qinv = pr[i].qinv;
+    u64 s = mulmod_mont(rots[idx], pts[r], q, qinv);
+    for (int k = 1; k < f; k++) s = addmod(s, mulmod_mont(rots[(size_t)k * total + idx], pts[(size_t)k * LN + r], q, qinv), q);
+    out[idx] = s;
+  }
+}
+void launch_pt_mac(ctl_context* c, const u64* rots, const u64* pts, int f, u64* out, int nb, int lvl) {
+  size_t total = (size_t)nb * 2 * lvl * c->N;
+  if (!total) return;
+  int g = elem_grid(c, total);
+  CTL_LAUNCH(KC_ELEM, (double)f * total, g,
+             (k_pt_mac<<<g, kThreads, 0, c->stream>>>(rots, pts, f, out, c->d_primes, (int)c->logN, lvl, total)));
+}
+
 }  // namespace ctl

@@ -15,6 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libctl.so")
 
 CTL_LAYER_DENSE, CTL_LAYER_SQUARE, CTL_LAYER_REPLICATE = 1, 2, 3
+CTL_LAYER_CONV1D, CTL_LAYER_POLY3, CTL_LAYER_AVGPOOL = 4, 5, 6
 ERRORS = {-1: "EINVAL", -2: "ELEVEL", -3: "ESCALE", -4: "EKEY", -5: "ENOMEM", -6: "ECUDA", -7: "ETIMEOUT",
           -8: "EBUSY", -9: "ENOTSUP"}
 
@@ -54,6 +55,7 @@ SIGNATURES = {
     "ctl_get_ntt_shape": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "ctl_set_bsgs_shape": (C.c_int, [_vp, C.c_int, C.c_int]),
     "ctl_set_keyswitch_budget": (C.c_int, [_vp, C.c_uint64]),
+    "ctl_set_windows": (C.c_int, [_vp, C.c_uint32]),
     "ctl_autotune_ntt": (C.c_int, [_vp, C.c_uint32, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "ctl_synchronize": (C.c_int, [_vp]),
     "ctl_keygen": (C.c_int, [_vp, _i32p, C.c_uint32, C.c_uint64, _pp]),
@@ -82,6 +84,14 @@ SIGNATURES = {
     "ctl_replicate": (C.c_int, [_vp, _vp, _vp, C.c_uint32, _pp]),
     "ctl_add": (C.c_int, [_vp, _vp, _vp, _pp]),
     "ctl_mul_plain_coeffs": (C.c_int, [_vp, _vp, _i64p, C.c_double, _pp]),
+    "ctl_eval_mul": (C.c_int, [_vp, _vp, _vp, _vp, _pp]),
+    "ctl_mul_const": (C.c_int, [_vp, _vp, C.c_int64, C.c_double, _pp]),
+    "ctl_add_const": (C.c_int, [_vp, _vp, C.c_int64, _pp]),
+    "ctl_drop_level": (C.c_int, [_vp, _vp, C.c_uint32, _pp]),
+    "ctl_eval_poly3": (C.c_int, [_vp, _vp, _vp, _dp, _pp]),
+    "ctl_eval_avgpool": (C.c_int, [_vp, _vp, _vp, C.c_uint32, _pp]),
+    "ctl_eval_conv1d": (C.c_int, [_vp, _vp, _vp, _dp, C.c_uint32, C.c_uint32, C.c_uint32, _dp, _pp]),
+    "ctl_eval_conv1d_coeffs": (C.c_int, [_vp, _vp, _vp, _i64p, C.c_uint32, _i64p, C.c_double, _pp]),
     "ctl_ntt_dev": (C.c_int, [_vp, _vp, _vp, C.c_uint32, C.c_uint32, C.c_int]),
     "ctl_rescale_static_dev": (C.c_int, [_vp, _vp, _vp, C.c_uint32, C.c_uint32]),
     "ctl_rescale_static_capacity_words": (C.c_size_t, []),
@@ -180,6 +190,10 @@ class Context:
 
     def set_bsgs_shape(self, chunk=32, karatsuba=1):
         _check(lib().ctl_set_bsgs_shape(self.h, int(chunk), int(karatsuba)))
+
+    def set_windows(self, p):
+        """Prediction windows of 2t slots per ciphertext for layers created afterwards."""
+        _check(lib().ctl_set_windows(self.h, int(p)))
 
     def set_keyswitch_budget(self, nbytes):
         _check(lib().ctl_set_keyswitch_budget(self.h, int(nbytes)))
@@ -301,6 +315,38 @@ class Context:
         pt = np.ascontiguousarray(pt, dtype=np.int64)
         return self._op(lib().ctl_mul_plain_coeffs, self.h, ct.h, _p(pt, _i64p), pt_scale)
 
+    def mul(self, keys, a, b):
+        """HMult of two ciphertexts: tensor, relinearisation, rescale."""
+        return self._op(lib().ctl_eval_mul, self.h, keys.h, a.h, b.h)
+
+    def mul_const(self, ct, c, c_scale):
+        return self._op(lib().ctl_mul_const, self.h, ct.h, int(c), float(c_scale))
+
+    def add_const(self, ct, c):
+        return self._op(lib().ctl_add_const, self.h, ct.h, int(c))
+
+    def drop_level(self, ct, level):
+        return self._op(lib().ctl_drop_level, self.h, ct.h, level)
+
+    def poly3(self, keys, ct, a):
+        """a[3] z^3 + a[2] z^2 + a[1] z + a[0] (a = a0..a3) at depth 2."""
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        return self._op(lib().ctl_eval_poly3, self.h, keys.h, ct.h, _p(a, _dp))
+
+    def avgpool(self, keys, ct, f):
+        return self._op(lib().ctl_eval_avgpool, self.h, keys.h, ct.h, f)
+
+    def conv1d(self, keys, ct, w, n, t, bias=None):
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        bp = _p(np.ascontiguousarray(bias, dtype=np.float64), _dp) if bias is not None else None
+        return self._op(lib().ctl_eval_conv1d, self.h, keys.h, ct.h, _p(w, _dp), len(w), n, t, bp)
+
+    def conv1d_coeffs(self, keys, ct, pts, pt_scale, bias=None):
+        pts = np.ascontiguousarray(pts, dtype=np.int64)
+        bp = _p(np.ascontiguousarray(bias, dtype=np.int64), _i64p) if bias is not None else None
+        return self._op(lib().ctl_eval_conv1d_coeffs, self.h, keys.h, ct.h, _p(pts, _i64p), pts.shape[0], bp,
+                        pt_scale)
+
     def ntt_dev(self, in_ptr, out_ptr, n_polys, limbs, inverse=False):
         _check(lib().ctl_ntt_dev(self.h, C.c_void_p(in_ptr), C.c_void_p(out_ptr), n_polys, limbs, 1 if inverse else 0))
 
@@ -392,7 +438,8 @@ class Ciphertext:
 
 
 class Model:
-    """Frozen server layers: list of ("dense", W[, bias][, pt_coeffs]), ("square",), ("replicate", t)."""
+    """Frozen server layers: list of ("dense", W[, bias][, pt_coeffs]), ("square",), ("replicate", t),
+    ("conv1d", w, n, t[, bias][, pt_coeffs]), ("poly3", a0..a3), ("avgpool", f)."""
 
     def __init__(self, ctx, layers, in_level=None, in_scale=None):
         self.ctx = ctx
@@ -419,6 +466,30 @@ class Model:
             elif kind == "replicate":
                 arr[i].kind = CTL_LAYER_REPLICATE
                 arr[i].rep_t = ly[1]
+            elif kind == "conv1d":
+                w = np.ascontiguousarray(ly[1], dtype=np.float64)
+                self._keep.append(w)
+                arr[i].kind = CTL_LAYER_CONV1D
+                arr[i].m, arr[i].n, arr[i].rep_t = len(w), ly[2], ly[3]
+                arr[i].W = _p(w, _dp)
+                if len(ly) > 4 and ly[4] is not None:
+                    b = np.ascontiguousarray(ly[4], dtype=np.float64)
+                    self._keep.append(b)
+                    arr[i].bias = _p(b, _dp)
+                if len(ly) > 5 and ly[5] is not None:
+                    pc = np.ascontiguousarray(ly[5], dtype=np.int64)
+                    self._keep.append(pc)
+                    arr[i].pt_coeffs = _p(pc, _i64p)
+            elif kind == "poly3":
+                a = np.ascontiguousarray(ly[1], dtype=np.float64)
+                if a.shape != (4,):
+                    raise ValueError("poly3 takes the four coefficients a0..a3")
+                self._keep.append(a)
+                arr[i].kind = CTL_LAYER_POLY3
+                arr[i].W = _p(a, _dp)
+            elif kind == "avgpool":
+                arr[i].kind = CTL_LAYER_AVGPOOL
+                arr[i].m = ly[1]
             else:
                 raise ValueError(kind)
         h = C.c_void_p()

@@ -189,3 +189,35 @@ def test_paper_network_depth_6_matches_fp64(q_bits, p_bits, log_scale, tol):
     assert lv == [7, 6, 5, 3, 2, 1]  # conv 1, dense 1, ReLU 2, pool 1, dense 1
     y = dec(o, out, sc, m2)
     assert np.max(np.abs(y - netref.paper_net_fp64(x, w, W1, W2, a))) < tol
+
+
+def test_paper_predictions_per_ciphertext_windows():
+    """Sec. 3.1 "Multiple Predictions": p = floor(#slots / (2 #neurons)) inputs share one
+    ciphertext, each in its own window of 2t slots; every window's output equals the
+    FP64 network of its own input.  N = 512 (256 slots), n = 24 (t = 32): p = 4."""
+    N, n, f = 512, 24, 9
+    t = O.Oracle.bsgs_t(n, n)
+    p = (N // 2) // (2 * t)
+    assert p == 4
+    w, W1, W2, W2s = netref.paper_net_weights(n, f=f)
+    m2 = W2.shape[0]
+    o = ctx(N=N, q_bits=(60, 40, 40, 40, 40, 40, 40), p_bits=(60,), rots=paper_net_rotations(n, m2, f, t))
+    rng = np.random.default_rng(8)
+    xs = rng.uniform(-1, 1, (p, n))
+    slots = np.zeros(N // 2)
+    for k in range(p):
+        slots[2 * t * k:2 * t * (k + 1)] = netref.replicated_slots(xs[k], t, 2 * t)
+    a = netref.relu_coeffs()
+    h = enc(o, slots, 13)
+    sc = o.scale
+    h = o.conv1d(h, o.encode_conv(w, n, t, o.dense_scale(7, sc), windows=p))[0]
+    h = o.dense(h, o.encode_diagonals(W1, o.dense_scale(6, sc), windows=p))[0]
+    h = o.replicate(h, t)
+    h, sc = o.poly3(h, sc, a)
+    h = o.avgpool(h, 3)[0]
+    h = o.dense(h, o.encode_diagonals(W2s, o.dense_scale(2, sc), windows=p))[0]
+    y = dec(o, h, o.scale)
+    for k in range(p):
+        assert np.max(np.abs(y[2 * t * k:2 * t * k + m2] - netref.paper_net_fp64(xs[k], w, W1, W2, a))) < 1e-4
+    # windows = 1 reproduces the single-window encoding
+    assert np.array_equal(o.encode_diagonals(W1, 2.0 ** 30), o.encode_diagonals(W1, 2.0 ** 30, windows=1))
