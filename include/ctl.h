@@ -195,6 +195,29 @@ int ctl_ct_slice(const ctl_ct* batch, uint32_t i, ctl_ct** out);
 void ctl_ct_destroy(ctl_ct* ct);
 
 /* ---------------------------------------------------------------------------------
+ * Messages (Sec. 5.1: the client sends a ciphertext of log2(q) * N bits, the server
+ * answers with one of log2(q_0) * 2N bits).  Host only, no GPU needed: these work on
+ * coefficient-form arrays [2][level][N] as ctl_ct_export writes them and the primes of
+ * the chain (ctl_plan_primes / ctl_context_info).  A message is a 16-byte header
+ * ("CTL1", N, level, stored polys, flags), for seeded messages the 8-byte encryption
+ * seed, then every stored limb i packed LSB-first at bitlen(q_i) bits per residue, each
+ * limb padded to a byte.  seeded != 0 stores c0 only: valid for a fresh ctl_encrypt
+ * result, whose c1 is the uniform polynomial drawn from the seed, which ctl_deserialize
+ * draws again (the C->S message is then one ring element, as in Sec. 5.1).
+ * ctl_serialized_size: message bytes (0 for invalid arguments).
+ * ctl_serialize: writes the message to out[cap] and its size to *size (nullable).
+ *   Errors: CTL_EINVAL (cap too small, a residue >= its prime, bad arguments).
+ * ctl_deserialize: reads a message of exactly `size` bytes for ring degree N and primes
+ *   moduli[>= level] into coeffs[2][level][N] (cap words) and its level (<= max_level) to
+ *   *level.  Errors: CTL_EINVAL (malformed header, size, residue out of range).
+ * ------------------------------------------------------------------------------- */
+size_t ctl_serialized_size(uint32_t N, const uint64_t* moduli, uint32_t level, int seeded);
+int ctl_serialize(uint32_t N, const uint64_t* moduli, uint32_t level, const uint64_t* coeffs, int seeded,
+                  uint64_t seed, uint8_t* out, size_t cap, size_t* size);
+int ctl_deserialize(const uint8_t* in, size_t size, uint32_t N, const uint64_t* moduli, uint32_t max_level,
+                    uint64_t* coeffs, size_t cap, uint32_t* level);
+
+/* ---------------------------------------------------------------------------------
  * Homomorphic operations (Sec. 3.1).  Each accepts a batch (count >= 1) and returns a
  * new handle; the input is not modified.
  * ctl_rotate: left rotation of the slots by r (rot_r of Eq. bsgs).  Hybrid key

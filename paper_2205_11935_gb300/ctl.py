@@ -93,6 +93,10 @@ SIGNATURES = {
     "ctl_eval_conv1d": (C.c_int, [_vp, _vp, _vp, _dp, C.c_uint32, C.c_uint32, C.c_uint32, _dp, _pp]),
     "ctl_eval_conv1d_coeffs": (C.c_int, [_vp, _vp, _vp, _i64p, C.c_uint32, _i64p, C.c_double, _pp]),
     "ctl_ntt_dev": (C.c_int, [_vp, _vp, _vp, C.c_uint32, C.c_uint32, C.c_int]),
+    "ctl_serialized_size": (C.c_size_t, [C.c_uint32, _u64p, C.c_uint32, C.c_int]),
+    "ctl_serialize": (C.c_int, [C.c_uint32, _u64p, C.c_uint32, _u64p, C.c_int, C.c_uint64, C.POINTER(C.c_uint8),
+                                _sz, C.POINTER(C.c_size_t)]),
+    "ctl_deserialize": (C.c_int, [C.POINTER(C.c_uint8), _sz, C.c_uint32, _u64p, C.c_uint32, _u64p, _sz, _u32p]),
     "ctl_rescale_static_dev": (C.c_int, [_vp, _vp, _vp, C.c_uint32, C.c_uint32]),
     "ctl_rescale_static_capacity_words": (C.c_size_t, []),
     "ctl_model_create": (C.c_int, [_vp, C.POINTER(Layer), C.c_uint32, C.c_uint32, C.c_double, _pp]),
@@ -153,6 +157,32 @@ def plan_primes(N, bits):
     out = np.zeros(len(b), dtype=np.uint64)
     _check(lib().ctl_plan_primes(N, _p(b, _u32p), len(b), _p(out, _u64p)))
     return [int(x) for x in out]
+
+
+def serialize(N, moduli, coeffs, seed=None):
+    """Message bytes of a coefficient-form ciphertext [2][level][N]; with seed, the seeded
+    form (c0 and the seed; valid for a fresh encryption with that seed)."""
+    m = np.ascontiguousarray(moduli, dtype=np.uint64)
+    a = np.ascontiguousarray(coeffs, dtype=np.uint64)
+    level = a.shape[-2]
+    seeded = 0 if seed is None else 1
+    n = lib().ctl_serialized_size(N, _p(m, _u64p), level, seeded)
+    out = np.zeros(n, dtype=np.uint8)
+    size = C.c_size_t()
+    _check(lib().ctl_serialize(N, _p(m, _u64p), level, _p(a, _u64p), seeded, 0 if seed is None else int(seed),
+                               _p(out, C.POINTER(C.c_uint8)), n, C.byref(size)))
+    return out.tobytes()
+
+
+def deserialize(msg, N, moduli):
+    """Coefficient-form ciphertext [2][level][N] of a message."""
+    m = np.ascontiguousarray(moduli, dtype=np.uint64)
+    b = np.frombuffer(bytes(msg), dtype=np.uint8).copy()
+    out = np.zeros(2 * len(m) * N, dtype=np.uint64)
+    lvl = C.c_uint32()
+    _check(lib().ctl_deserialize(_p(b, C.POINTER(C.c_uint8)), len(b), N, _p(m, _u64p), len(m), _p(out, _u64p),
+                                 out.size, C.byref(lvl)))
+    return out[:2 * lvl.value * N].reshape(2, lvl.value, N)
 
 
 class Context:

@@ -1,0 +1,79 @@
+"""Host-side ciphertext messages (no GPU): round trips, the sizes Sec. 5.1 states
+(client -> server: log2(q) * N bits; server -> client: log2(q_0) * 2N bits) against the
+paper's Tab. 1, and the seeded form against the oracle's own encryption."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import ckks_oracle as O
+from paper_2205_11935_gb300 import ctl
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+PAPER = {"CryptoTL_p1": (8192, [34] + [25] * 6, [34]), "CryptoTL_p2": (16384, [60] + [50] * 6, [60])}
+
+
+def table1():
+    with open(os.path.join(GOLD, "paper_params.json")) as f:
+        return {p["name"]: p for p in json.load(f)["param_sets"]}
+
+
+def rand_ct(N, moduli, level, seed):
+    rng = np.random.default_rng(seed)
+    return np.stack([np.stack([rng.integers(0, q, N, dtype=np.uint64) for q in moduli[:level]]) for _ in range(2)])
+
+
+@pytest.mark.parametrize("name", list(PAPER))
+def test_round_trip_and_sizes_against_table1(name):
+    N, qb, pb = PAPER[name]
+    moduli = ctl.plan_primes(N, qb + pb)
+    L = len(qb)
+    ct = rand_ct(N, moduli, L, 1)
+    msg = ctl.serialize(N, moduli[:L], ct)
+    assert np.array_equal(ctl.deserialize(msg, N, moduli[:L]), ct)
+    tab = table1()[name]
+    bits = [int(q).bit_length() for q in moduli]
+    # server -> client: q_0 only after the six rescales, both polys (Sec. 5.1 formula)
+    out = rand_ct(N, moduli, 1, 2)
+    s2c = ctl.serialize(N, moduli[:1], out)
+    assert len(s2c) == 16 + bits[0] * 2 * N // 8
+    assert len(s2c) <= tab["s2c_kB"] * 1000
+    # client -> server: the seeded fresh ciphertext is one ring element; its size is at
+    # most log2(q) * N bits with q the whole modulus of Tab. 1 (data and special primes)
+    c2s = len(ctl.serialize(N, moduli[:L], ct, seed=7))
+    assert c2s == 16 + 8 + sum(bits[:L]) * N // 8
+    assert c2s <= tab["log2_q"] * N // 8 + 24 and c2s <= tab["c2s_kB"] * 1000
+    assert sum(bits) == tab["log2_q"]  # the chain's bit lengths add up to Tab. 1's log2 q
+
+
+def test_seeded_message_regenerates_the_oracles_c1():
+    N, qb, pb = 256, [60, 40, 40], [60]
+    o = O.Oracle(N, qb, pb, scale=2.0 ** 40)
+    o.keygen([], seed=3)
+    z = np.random.default_rng(3).uniform(-1, 1, N // 2)
+    ct = o.encrypt(o.encode(z), 1234)
+    msg = ctl.serialize(N, o.moduli[:3], ct, seed=1234)
+    back = ctl.deserialize(msg, N, o.moduli[:3])
+    assert np.array_equal(back, ct)
+    assert len(msg) < len(ctl.serialize(N, o.moduli[:3], ct))
+
+
+def test_malformed_messages_are_refused():
+    N = 64
+    moduli = ctl.plan_primes(N, [50, 40])
+    ct = rand_ct(N, moduli, 2, 5)
+    msg = bytearray(ctl.serialize(N, moduli, ct))
+    for bad in (bytes(msg[:-1]), b"XTL1" + bytes(msg[4:]), bytes(msg) + b"\0"):
+        with pytest.raises(ctl.CtlError):
+            ctl.deserialize(bad, N, moduli)
+    with pytest.raises(ctl.CtlError):
+        ctl.deserialize(bytes(msg), 2 * N, moduli)
+    # a residue at or above its prime is refused on both sides
+    big = ct.copy()
+    big[0, 0, 0] = moduli[0]
+    with pytest.raises(ctl.CtlError):
+        ctl.serialize(N, moduli, big)
+    # a message of a deeper level than the caller accepts
+    with pytest.raises(ctl.CtlError):
+        ctl.deserialize(bytes(msg), N, moduli[:1])
