@@ -448,7 +448,9 @@ def run_uneven(args, ctl):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=0,
+                    help="timed steps (default 5; 500 for single-query workloads, so that the clock sampler sees "
+                         "the timed region)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batched", choices=list(WORKLOADS) + ["serving", "uneven"])
@@ -484,6 +486,8 @@ def main():
     wl = dict(WORKLOADS[args.workload])
     if args.batch:
         wl["batch"] = args.batch
+    if not args.steps:
+        args.steps = 500 if wl["batch"] == 1 else 5
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
