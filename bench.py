@@ -445,6 +445,25 @@ def run_uneven(args, ctl):
             "per_ct_fwd_s": len(queries) / single, "speedup": single / grouped, "server_batches": st["batches"]}
 
 
+def max_over_ranks(x, dist):
+    """The slowest rank's time: every rank runs its own replica on its own GPU (the
+    queries are independent, so there is no data-path collective), and the job's time is
+    the maximum over ranks.  NCCL reduces a device tensor, gloo a host one."""
+    if not dist:
+        return x
+    import torch
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world, batch, steps, seconds):
+    """Whole-job forwards per second: world replicas of `batch` ciphertexts per step."""
+    return world * batch * steps / seconds
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -602,11 +621,8 @@ def main():
         kern = ctx.stats_kernels()
         timing_source = "CUDA events around every launch of eager forwards run after the graph-timed steps"
     ctx.stats_enable_timing(False)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * B * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(total_ms, dist)
+    value = replica_throughput(world, B, args.steps, total_ms / 1e3)
 
     # end to end through host buffers
     e2e = None
@@ -637,11 +653,9 @@ def main():
             e2e_step()
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t_start
-        if dist:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": world * B * args.steps / e2e_s, "unit": "forwards/s", "h2d_bytes_per_step": int(h2d),
+        e2e_s = max_over_ranks(e2e_s, dist)
+        e2e = {"value": replica_throughput(world, B, args.steps, e2e_s), "unit": "forwards/s",
+               "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(out_words * 8)}
 
     # the same workload with the dense layers in the lazy-ModDown form (a different, equally
