@@ -1286,16 +1286,17 @@ void launch_moddown_polys(ctl_context* c, const u64* acc, size_t acc_stride, int
 // ---------------------------------------------------------------------------------
 // Giant-step sums of ModDowns (see launch_giant_accum in ctl_internal.h).  A thread owns
 // coefficient k of (ciphertext b, poly t) for a group of up to LG data limbs and sweeps
-// the nr results: per result it reads the K special-limb values once and converts them
-// to every limb of its group.
+// the nr results, RPI at a time: per result it reads the K special-limb values once and
+// converts them to every limb of its group.
 // ---------------------------------------------------------------------------------
-template <int K, int LG>
-__global__ void __launch_bounds__(256) k_giant_accum(const u64* __restrict__ acc, int nr, int nb, int lvl, int E,
-                                                     int logN, const __grid_constant__ RotList rl,
-                                                     const u64* __restrict__ addend, size_t add_r, size_t add_b,
-                                                     u64* __restrict__ D, u64* __restrict__ C, u64* __restrict__ A,
-                                                     int first, const __grid_constant__ ConvTab tab,
-                                                     const DPrime* __restrict__ pr) {
+template <int K, int LG, int RPI>
+__global__ void __launch_bounds__(256, 4) k_giant_accum(const u64* __restrict__ acc, int nr, int nb, int lvl, int E,
+                                                        int logN, const __grid_constant__ RotList rl,
+                                                        const u64* __restrict__ addend, size_t add_r, size_t add_b,
+                                                        u64* __restrict__ D, u64* __restrict__ C,
+                                                        u64* __restrict__ A, int first,
+                                                        const __grid_constant__ ConvTab tab,
+                                                        const DPrime* __restrict__ pr) {
   const int N = 1 << logN;
   const int ngroups = (lvl + LG - 1) / LG;
   const size_t total = (size_t)nb * 2 * ngroups * N;
@@ -1349,16 +1350,16 @@ __global__ void __launch_bounds__(256) k_giant_accum(const u64* __restrict__ acc
         av[g] = with_a ? __ldg(ad + ((size_t)l << logN)) : 0;
       }
     };
-    // two rotations per iteration: all their loads in flight before the arithmetic
+    // RPI rotations per iteration: all their loads in flight before the arithmetic
     int r = 0;
-    for (; r + 1 < nr; r += 2) {
-      u64 s0[K], d0[LG], a0[LG], s1[K], d1[LG], a1[LG];
-      load_rot(r, s0, d0, a0);
-      load_rot(r + 1, s1, d1, a1);
-      add_rot(s0, d0, a0);
-      add_rot(s1, d1, a1);
+    for (; r + RPI - 1 < nr; r += RPI) {
+      u64 sv[RPI][K], dv[RPI][LG], av[RPI][LG];
+#pragma unroll
+      for (int u = 0; u < RPI; u++) load_rot(r + u, sv[u], dv[u], av[u]);
+#pragma unroll
+      for (int u = 0; u < RPI; u++) add_rot(sv[u], dv[u], av[u]);
     }
-    if (r < nr) {
+    for (; r < nr; r++) {
       u64 s0[K], d0[LG], a0[LG];
       load_rot(r, s0, d0, a0);
       add_rot(s0, d0, a0);
@@ -1380,7 +1381,11 @@ __global__ void __launch_bounds__(256) k_giant_accum(const u64* __restrict__ acc
 
 void launch_giant_accum(ctl_context* c, const u64* acc, int nr, int nb, int lvl, const RotList& rl,
                         const u64* addend, size_t add_r, size_t add_b, u64* D, u64* C, u64* A, bool first) {
-  constexpr int LG = 2;  // limbs per thread: more threads in flight per SM
+  // One limb per thread and two rotations' loads in flight, at 63 registers (four blocks of
+  // 256 per SM): the sums are bound by global-memory latency, so more resident warps beat
+  // fewer re-reads of the special limbs (which L2 serves); measured on the batched forward
+  // against two or four limbs per thread and three or four rotations per iteration.
+  constexpr int LG = 1, RPI = 2;
   const int ngroups = (lvl + LG - 1) / LG;
   const size_t total = (size_t)nb * 2 * ngroups * c->N;
   if (!total || nr <= 0) return;
@@ -1394,9 +1399,9 @@ void launch_giant_accum(ctl_context* c, const u64* acc, int nr, int nb, int lvl,
   switch (c->K) {
 #define CTL_GIANT_CASE(KK)                                                                                        \
   case KK:                                                                                                        \
-    k_giant_accum<KK, LG><<<grid, 256, 0, c->stream>>>(acc, nr, nb, lvl, E, (int)c->logN, rl, addend, add_r,      \
-                                                       add_b, D, C, A, first ? 1 : 0, c->moddown.conv,            \
-                                                       c->d_primes);                                              \
+    k_giant_accum<KK, LG, RPI><<<grid, 256, 0, c->stream>>>(acc, nr, nb, lvl, E, (int)c->logN, rl, addend,       \
+                                                            add_r, add_b, D, C, A, first ? 1 : 0,                 \
+                                                            c->moddown.conv, c->d_primes);                        \
     break;
     CTL_GIANT_CASE(1)
     CTL_GIANT_CASE(2)
