@@ -212,6 +212,13 @@ void ctl_ct_destroy(ctl_ct* ct);
  *   *level.  Errors: CTL_EINVAL (malformed header, size, residue out of range).
  * ------------------------------------------------------------------------------- */
 size_t ctl_serialized_size(uint32_t N, const uint64_t* moduli, uint32_t level, int seeded);
+/* Host only: slot values x[n] encoded at `scale` (any magnitude up to ~2^1000) straight to
+ * residues out[lvl][N] modulo moduli[0..lvl): round(m_k) mod q_i with m_k as ctl_encode
+ * defines it (half away from zero).  This is how dense and conv1d layers encode their
+ * biases, which join the products before the rescale at scale in_scale * pt_scale.
+ * Errors: CTL_EINVAL. */
+int ctl_encode_residues(uint32_t N, const uint64_t* moduli, uint32_t lvl, const double* x, size_t n, double scale,
+                        uint64_t* out);
 int ctl_serialize(uint32_t N, const uint64_t* moduli, uint32_t level, const uint64_t* coeffs, int seeded,
                   uint64_t seed, uint8_t* out, size_t cap, size_t* size);
 int ctl_deserialize(const uint8_t* in, size_t size, uint32_t N, const uint64_t* moduli, uint32_t max_level,

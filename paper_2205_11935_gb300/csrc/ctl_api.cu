@@ -1281,6 +1281,25 @@ int upload_plaintexts(ctl_context* c, const i64* coeffs, uint32_t cnt, uint32_t 
   return CTL_OK;
 }
 
+// Upload plaintext residues [lvl][N] (coefficient form, limb i modulo q_i) as NTT-form
+// residues: the plaintexts whose scale is too large for 64-bit coefficients.
+int upload_residues(ctl_context* c, const u64* res, uint32_t lvl, u64** out) {
+  u64* d = (u64*)dev_alloc(c, (size_t)lvl * c->N * sizeof(u64));
+  if (!d) {
+    set_error("plaintext upload: allocation failed");
+    return CTL_ENOMEM;
+  }
+  cudaMemcpyAsync(d, res, (size_t)lvl * c->N * sizeof(u64), cudaMemcpyHostToDevice, c->stream);
+  launch_ntt_fwd(c, d, (size_t)lvl * c->N, 1, 0, (int)lvl, (int)lvl);
+  int rc = cuda_check(cudaStreamSynchronize(c->stream), "plaintext upload");
+  if (rc) {
+    dev_free(c, d);
+    return rc;
+  }
+  *out = d;
+  return CTL_OK;
+}
+
 // Diagonals of W for Eq. (bsgs): diag_i[r] = W[r][(r+i) mod t] (zero padded),
 // diag'_i = rot_{-floor(i/t1)*t1}(diag_i), i.e. diag_i placed at slots [k*t1, k*t1 + t).
 // With c->windows = p > 1 (Sec. 3.1 "Multiple Predictions") the pattern of slots [0, 2t)
@@ -1347,21 +1366,20 @@ int dense_prepare(ctl_context* c, DenseLayer& D, const double* W, const double* 
     launch_bsgs_wino_diag(c, D.diag, (size_t)limbs * c->N, w.p, (int)D.t1, (int)D.t2, (int)limbs, (int)lvl);
     D.wino = w.release();
   }
-  std::vector<i64> benc;
-  const i64* bsrc = (const i64*)bias_in;
-  if (!bsrc && bias) {
+  if (bias_in) {
+    if (int rc = upload_plaintexts(c, (const i64*)bias_in, 1, lvl, lvl, false, &D.bias)) return rc;
+  } else if (bias) {
+    // the bias joins the products before the rescale, at their scale in_scale * pt_scale
+    // (far above 2^63): encoded straight to residues
     std::vector<double> v(c->N / 2, 0.0);
     for (uint32_t w = 0; w < c->windows; w++)
       for (uint32_t r = 0; r < m; r++) v[2 * D.t * w + r] = bias[r];
-    benc.resize(c->N);
-    if (!c->enc.encode(v.data(), v.size(), in_scale * D.pt_scale, benc.data())) {
+    std::vector<u64> res((size_t)lvl * c->N);
+    if (!c->enc.encode_rns(v.data(), v.size(), in_scale * D.pt_scale, c->moduli.data(), lvl, res.data())) {
       set_error("dense: bias encoding overflow");
       return CTL_EINVAL;
     }
-    bsrc = benc.data();
-  }
-  if (bsrc) {
-    if (int rc = upload_plaintexts(c, bsrc, 1, lvl, lvl, false, &D.bias)) return rc;
+    if (int rc = upload_residues(c, res.data(), lvl, &D.bias)) return rc;
   }
   return CTL_OK;
 }
@@ -1817,21 +1835,20 @@ int conv_prepare(ctl_context* c, ConvLayer& V, const double* w, const double* bi
     src = enc.data();
   }
   if (int rc = upload_plaintexts(c, src, f, lvl, lvl, true, &V.pts)) return rc;
-  std::vector<i64> benc;
-  const i64* bsrc = (const i64*)bias_in;
-  if (!bsrc && bias) {
+  if (bias_in) {
+    if (int rc = upload_plaintexts(c, (const i64*)bias_in, 1, lvl, lvl, false, &V.bias)) return rc;
+  } else if (bias) {
+    // added before the rescale, at the products' scale in_scale * pt_scale: residues
     std::vector<double> v(c->N / 2, 0.0);
     for (uint32_t w = 0; w < c->windows; w++)
       for (uint32_t s = 0; s < n; s++) v[2 * t * w + s] = v[2 * t * w + t + s] = bias[s];
-    benc.resize(c->N);
-    if (!c->enc.encode(v.data(), v.size(), in_scale * V.pt_scale, benc.data())) {
+    std::vector<u64> res((size_t)lvl * c->N);
+    if (!c->enc.encode_rns(v.data(), v.size(), in_scale * V.pt_scale, c->moduli.data(), lvl, res.data())) {
       set_error("conv1d: bias encoding overflow");
       return CTL_EINVAL;
     }
-    bsrc = benc.data();
+    if (int rc = upload_residues(c, res.data(), lvl, &V.bias)) return rc;
   }
-  if (bsrc)
-    if (int rc = upload_plaintexts(c, bsrc, 1, lvl, lvl, false, &V.bias)) return rc;
   return CTL_OK;
 }
 

@@ -121,6 +121,10 @@ struct Encoder {
   void init(uint32_t n);
   // m_k = round(scale * (2/N) * Re sum_j z_j zeta^(-5^j k)); returns false on overflow.
   bool encode(const double* z, size_t nz, double scale, i64* m) const;
+  // The same coefficients for any scale (up to 2^1000), as residues modulo the lvl primes
+  // moduli[0..lvl): out[i][k] = round(m_k) mod q_i, rounding half away from zero (a value
+  // of 2^53 or more is already an integer in FP64 and is reduced exactly).
+  bool encode_rns(const double* z, size_t nz, double scale, const u64* moduli, uint32_t lvl, u64* out) const;
   // z_j = Re( sum_k m_k zeta^(5^j k) ) / scale for j < nz.
   void decode(const double* m, size_t nz, double scale, double* z) const;
  private:

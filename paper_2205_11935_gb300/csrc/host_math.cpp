@@ -230,6 +230,37 @@ bool Encoder::encode(const double* z, size_t nz, double scale, i64* m) const {
   return ok;
 }
 
+bool Encoder::encode_rns(const double* z, size_t nz, double scale, const u64* moduli, uint32_t lvl,
+                         u64* out) const {
+  std::vector<double> re(N, 0.0), im(N, 0.0);
+  for (size_t j = 0; j < nz; j++) {
+    re[slot_pos[j]] = z[j];
+    re[conj_pos[j]] = z[j];
+  }
+  fft(re, im, true);
+  for (uint32_t k = 0; k < N; k++) {
+    const double v = (re[k] * zc[k] + im[k] * zs[k]) / (double)N * scale;
+    if (!std::isfinite(v) || std::fabs(v) > 1e300) return false;
+    const double r = std::fabs(v) < 4503599627370496.0 ? (double)std::llround(v) : v;  // integral from 2^52
+    const double a = std::fabs(r);
+    int e = 0;
+    const double mant = std::frexp(a, &e);  // a = mant * 2^e, mant in [0.5, 1)
+    u64 M = (u64)std::ldexp(mant, 53);      // a = M * 2^(e - 53), M < 2^53
+    e -= 53;
+    if (e < 0) {
+      M >>= -e;  // a is an integer, so the shifted-out bits are zero
+      e = 0;
+    }
+    for (uint32_t i = 0; i < lvl; i++) {
+      const u64 q = moduli[i];
+      u64 res = h_mulmod(M % q, h_powmod(2, (u64)e, q), q);
+      if (r < 0 && res) res = q - res;
+      out[(size_t)i * N + k] = res;
+    }
+  }
+  return true;
+}
+
 void Encoder::decode(const double* m, size_t nz, double scale, double* z) const {
   std::vector<double> re(N), im(N);
   for (uint32_t k = 0; k < N; k++) {

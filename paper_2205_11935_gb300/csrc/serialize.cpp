@@ -159,3 +159,21 @@ extern "C" int ctl_deserialize(const uint8_t* in, size_t size, uint32_t N, const
   if (level) *level = lvl;
   return CTL_OK;
 }
+
+// Host-only encoding straight to residues (the path a plaintext takes when its scale is
+// beyond 64-bit coefficients, such as a bias added before a rescale).
+extern "C" int ctl_encode_residues(uint32_t N, const uint64_t* moduli, uint32_t lvl, const double* x, size_t n,
+                                   double scale, uint64_t* out) {
+  if (!moduli || !out || (n && !x) || N < 16 || N > 16384 || (N & (N - 1)) || n > N / 2 || lvl == 0 ||
+      !(scale > 0)) {
+    set_error("ctl_encode_residues: invalid argument");
+    return CTL_EINVAL;
+  }
+  Encoder e;
+  e.init(N);
+  if (!e.encode_rns(x, n, scale, (const u64*)moduli, lvl, (u64*)out)) {
+    set_error("ctl_encode_residues: value out of range");
+    return CTL_EINVAL;
+  }
+  return CTL_OK;
+}

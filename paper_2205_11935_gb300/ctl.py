@@ -94,6 +94,7 @@ SIGNATURES = {
     "ctl_eval_conv1d_coeffs": (C.c_int, [_vp, _vp, _vp, _i64p, C.c_uint32, _i64p, C.c_double, _pp]),
     "ctl_ntt_dev": (C.c_int, [_vp, _vp, _vp, C.c_uint32, C.c_uint32, C.c_int]),
     "ctl_serialized_size": (C.c_size_t, [C.c_uint32, _u64p, C.c_uint32, C.c_int]),
+    "ctl_encode_residues": (C.c_int, [C.c_uint32, _u64p, C.c_uint32, _dp, _sz, C.c_double, _u64p]),
     "ctl_serialize": (C.c_int, [C.c_uint32, _u64p, C.c_uint32, _u64p, C.c_int, C.c_uint64, C.POINTER(C.c_uint8),
                                 _sz, C.POINTER(C.c_size_t)]),
     "ctl_deserialize": (C.c_int, [C.POINTER(C.c_uint8), _sz, C.c_uint32, _u64p, C.c_uint32, _u64p, _sz, _u32p]),
@@ -172,6 +173,15 @@ def serialize(N, moduli, coeffs, seed=None):
     _check(lib().ctl_serialize(N, _p(m, _u64p), level, _p(a, _u64p), seeded, 0 if seed is None else int(seed),
                                _p(out, C.POINTER(C.c_uint8)), n, C.byref(size)))
     return out.tobytes()
+
+
+def encode_residues(N, moduli, x, scale):
+    """Slot values encoded at any scale, as residues [len(moduli)][N] (host only)."""
+    m = np.ascontiguousarray(moduli, dtype=np.uint64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros((len(m), N), dtype=np.uint64)
+    _check(lib().ctl_encode_residues(N, _p(m, _u64p), len(m), _p(x, _dp), len(x), float(scale), _p(out, _u64p)))
+    return out
 
 
 def deserialize(msg, N, moduli):

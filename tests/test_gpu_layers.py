@@ -309,3 +309,51 @@ def test_paper_network_prediction_windows_bit_exact():
         ctl.Model(g, [("dense", W1)])
     model.close()
     model2.close()
+
+
+def test_biases_windows_and_lazy_dense_in_the_paper_stack():
+    """Biases of conv1d and dense layers (library encodings, replicated per window), the
+    lazy-ModDown dense form inside the paper's stack, and direct calls equal to the
+    model's layers: decoded within 1e-4 of FP64 per window."""
+    N, n, f = 512, 24, 9
+    qb, pb, scale = [60] + [40] * 6, [60], 2.0 ** 40
+    t = O.Oracle.bsgs_t(n, n)
+    p = (N // 2) // (2 * t)
+    w, W1, W2, W2s = netref.paper_net_weights(n, f=f)
+    m2 = W2.shape[0]
+    rng = np.random.default_rng(111)
+    bc, b1, b2 = rng.uniform(-0.2, 0.2, n), rng.uniform(-0.2, 0.2, n), rng.uniform(-0.2, 0.2, m2)
+    a = netref.relu_coeffs()
+
+    def ref(x):
+        h = netref.conv_same(x, w) + bc
+        z = W1 @ h + b1
+        r = netref.poly3(a, z)
+        return W2 @ netref.avgpool_valid(r, 3) + b2
+
+    xs = rng.uniform(-1, 1, (p, n))
+    slots = np.zeros(N // 2)
+    for j in range(p):
+        slots[2 * t * j:2 * t * (j + 1)] = netref.replicated_slots(xs[j], t, 2 * t)
+    for lazy in (False, True):
+        g = ctl.Context(N, qb, pb, dnum=7, scale=scale)
+        g.set_windows(p)
+        g.set_dense_mode(g.DENSE_LAZY_MODDOWN if lazy else g.DENSE_COMPOSED)
+        layers = [("conv1d", w, n, t, bc), ("dense", W1, b1), ("replicate", t), ("poly3", a), ("avgpool", 3),
+                  ("dense", W2s, b2)]
+        model = ctl.Model(g, layers)
+        k = g.keygen(model.rotations(), seed=3)
+        ct = g.encrypt(k, slots, 500)
+        out = model.forward(k, ct)
+        y = g.decrypt(k, out, N // 2)
+        for j in range(p):
+            assert np.max(np.abs(y[2 * t * j:2 * t * j + m2] - ref(xs[j]))) < TOL, (lazy, j)
+        # the same layers as direct calls give the same ciphertext
+        h = g.conv1d(k, ct, w, n, t, bias=bc)
+        h = g.dense(k, h, W1, bias=b1)
+        h = g.replicate(k, h, t)
+        h = g.poly3(k, h, a)
+        h = g.avgpool(k, h, 3)
+        h = g.dense(k, h, W2s, bias=b2)
+        assert np.array_equal(h.export(), out.export())
+        model.close()

@@ -77,3 +77,29 @@ def test_malformed_messages_are_refused():
     # a message of a deeper level than the caller accepts
     with pytest.raises(ctl.CtlError):
         ctl.deserialize(bytes(msg), N, moduli[:1])
+
+
+@pytest.mark.parametrize("log_scale", [30, 80, 100])
+def test_encode_residues_matches_the_oracle_encoding(log_scale):
+    """Residue encoding at scales beyond 64-bit coefficients (a bias before a rescale):
+    the CRT value of the residues, divided by 2^(s-30), is the oracle's 2^30 encoding
+    within one unit plus the FP64 rounding of the large product."""
+    from sympy.ntheory.modular import crt
+
+    N = 256
+    moduli = ctl.plan_primes(N, [60, 50, 50, 50])
+    o = O.Oracle(N, [60, 50, 50, 50], [60], scale=2.0 ** 30)
+    z = np.random.default_rng(4).uniform(-1, 1, N // 2)
+    res = ctl.encode_residues(N, moduli, z, 2.0 ** log_scale)
+    ref = o.encode(z, 2.0 ** 30)
+    Q = 1
+    for q in moduli:
+        Q *= q
+    shift = 2 ** (log_scale - 30)
+    for k in range(0, N, 7):
+        v = int(crt(moduli, [int(r[k]) for r in res])[0])
+        v = v - Q if v > Q // 2 else v
+        assert abs(v / shift - int(ref[k])) <= 1 + abs(int(ref[k])) * 2.0 ** -50
+    if log_scale == 30:  # within 64 bits: the same rounding as the 64-bit encoder, mod q
+        for i, q in enumerate(moduli):
+            assert np.array_equal(res[i], (ref.astype(object) % q).astype(np.uint64))
