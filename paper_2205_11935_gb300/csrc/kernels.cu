@@ -404,12 +404,11 @@ struct KeyRegs {
 
 // ND: the digit count when EXACT, else an upper bound of the run-time count nd_arg.
 template <int ND, bool EXACT>
-__global__ void __launch_bounds__(256) k_key_ip(const u64* __restrict__ ext, size_t ext_r,
-                                                const __grid_constant__ RotList rl, u64* __restrict__ acc,
-                                                const u64* __restrict__ add_c0, size_t add_b,
-                                                const u64* __restrict__ pmod, const u64* __restrict__ pmod_sh,
-                                                const DPrime* __restrict__ pr, int logN, int nb, int nd_arg, int E,
-                                                int lvl, int L, int LK) {
+__device__ __forceinline__ void key_ip_body(const u64* __restrict__ ext, size_t ext_r, const RotList& rl,
+                                            u64* __restrict__ acc, const u64* __restrict__ add_c0, size_t add_b,
+                                            const u64* __restrict__ pmod, const u64* __restrict__ pmod_sh,
+                                            const DPrime* __restrict__ pr, int logN, int nb, int nd_arg, int E,
+                                            int lvl, int L, int LK) {
   const int nd = EXACT ? ND : nd_arg;
   const size_t N = (size_t)1 << logN;
   const size_t EN = (size_t)E << logN;
@@ -476,6 +475,29 @@ __global__ void __launch_bounds__(256) k_key_ip(const u64* __restrict__ ext, siz
     o[EN] = r1;
   }
 }
+// Up to four digits the key product fits 80 registers and runs three blocks per SM
+// (measured faster than two blocks at 98 registers: it is issue-bound, and more resident
+// warps cover the dependent multiply-add chains); the larger digit counts keep their
+// registers (they would spill at 80).
+template <int ND, bool EXACT>
+__global__ void __launch_bounds__(256, 3) k_key_ip(const u64* __restrict__ ext, size_t ext_r,
+                                                   const __grid_constant__ RotList rl, u64* __restrict__ acc,
+                                                   const u64* __restrict__ add_c0, size_t add_b,
+                                                   const u64* __restrict__ pmod, const u64* __restrict__ pmod_sh,
+                                                   const DPrime* __restrict__ pr, int logN, int nb, int nd_arg,
+                                                   int E, int lvl, int L, int LK) {
+  key_ip_body<ND, EXACT>(ext, ext_r, rl, acc, add_c0, add_b, pmod, pmod_sh, pr, logN, nb, nd_arg, E, lvl, L, LK);
+}
+template <int ND, bool EXACT>
+__global__ void __launch_bounds__(256) k_key_ip_wide(const u64* __restrict__ ext, size_t ext_r,
+                                                     const __grid_constant__ RotList rl, u64* __restrict__ acc,
+                                                     const u64* __restrict__ add_c0, size_t add_b,
+                                                     const u64* __restrict__ pmod, const u64* __restrict__ pmod_sh,
+                                                     const DPrime* __restrict__ pr, int logN, int nb, int nd_arg,
+                                                     int E, int lvl, int L, int LK) {
+  key_ip_body<ND, EXACT>(ext, ext_r, rl, acc, add_c0, add_b, pmod, pmod_sh, pr, logN, nb, nd_arg, E, lvl, L, LK);
+}
+
 // g^-1 mod 2N for odd g (2N a power of two): Newton iteration on the 2-adic inverse.
 static u64 inv_mod_2n(u64 g, u64 two_n) {
   u64 x = g;  // correct to 3 bits for odd g
@@ -497,19 +519,19 @@ void launch_key_ip(ctl_context* c, const u64* ext, size_t ext_r, int nb, int lvl
   double work = 2.0 * nd * EN * nb * nrot;
   const u64* pm = c->moddown.pmod;
   const u64* pms = c->moddown.pmod_sh;
-#define CTL_KEYIP_CASE(NDV, EX)                                                                                \
+#define CTL_KEYIP_CASE(KERN, NDV, EX)                                                                          \
   CTL_LAUNCH(KC_KEYIP, work, grid,                                                                             \
-             (k_key_ip<NDV, EX><<<grid, 256, 0, c->stream>>>(ext, ext_r, rl, acc, add_c0, add_b, pm, pms,       \
-                                                             c->d_primes, (int)c->logN, nb, nd, E, lvl,        \
-                                                             (int)c->L, LK)))
+             (KERN<NDV, EX><<<grid, 256, 0, c->stream>>>(ext, ext_r, rl, acc, add_c0, add_b, pm, pms,           \
+                                                         c->d_primes, (int)c->logN, nb, nd, E, lvl, (int)c->L,  \
+                                                         LK)))
   switch (nd) {
-    case 1: CTL_KEYIP_CASE(1, true); break;
-    case 2: CTL_KEYIP_CASE(2, true); break;
-    case 3: CTL_KEYIP_CASE(3, true); break;
-    case 4: CTL_KEYIP_CASE(4, true); break;
+    case 1: CTL_KEYIP_CASE(k_key_ip, 1, true); break;
+    case 2: CTL_KEYIP_CASE(k_key_ip, 2, true); break;
+    case 3: CTL_KEYIP_CASE(k_key_ip, 3, true); break;
+    case 4: CTL_KEYIP_CASE(k_key_ip, 4, true); break;
     default:
-      if (nd <= 8) CTL_KEYIP_CASE(8, false);
-      else CTL_KEYIP_CASE(16, false);
+      if (nd <= 8) CTL_KEYIP_CASE(k_key_ip_wide, 8, false);
+      else CTL_KEYIP_CASE(k_key_ip_wide, 16, false);
   }
 #undef CTL_KEYIP_CASE
 }
