@@ -155,6 +155,16 @@ void ctl_keys_destroy(ctl_keys* keys);
  * [beta][2][n_q+n_p][N] coefficient-form residues into out (cap words).
  * Errors: CTL_EKEY (no such key), CTL_EINVAL (cap too small). */
 int ctl_keys_export(const ctl_keys* keys, uint64_t key_id, uint64_t* out, size_t cap);
+/* Evaluation keys received from a client (Fig. alg:cryptotl: the server holds the
+ * client's public evaluation keys, never its secret).  ctl_keys_create makes an empty key
+ * set with no secret: ctl_encrypt* and ctl_decrypt* on it fail with CTL_EKEY.
+ * ctl_keys_import adds (or replaces) key key_id (0 = relinearisation, an odd Galois
+ * element g < 2N = the key of X -> X^g) from the coefficient-form residues
+ * coeffs[beta][2][n_q+n_p][N] that ctl_keys_export writes (n_words must equal that
+ * size).  The import synchronises the context stream.  Errors: CTL_EINVAL (size, key id,
+ * a residue >= its prime), CTL_ENOMEM, CTL_ECUDA. */
+int ctl_keys_create(ctl_context* ctx, ctl_keys** out);
+int ctl_keys_import(ctl_keys* keys, uint64_t key_id, const uint64_t* coeffs, size_t n_words);
 /* Galois element 5^(r mod N/2) mod 2N of a left rotation by r. */
 uint64_t ctl_galois_element(const ctl_context* ctx, int64_t r);
 

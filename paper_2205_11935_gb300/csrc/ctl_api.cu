@@ -725,6 +725,61 @@ extern "C" void ctl_keys_destroy(ctl_keys* k) {
   delete k;
 }
 
+extern "C" int ctl_keys_create(ctl_context* c, ctl_keys** out) {
+  if (!c || !out) {
+    set_error("ctl_keys_create: null argument");
+    return CTL_EINVAL;
+  }
+  ctl_keys* k = new (std::nothrow) ctl_keys();
+  if (!k) {
+    set_error("ctl_keys_create: allocation failed");
+    return CTL_ENOMEM;
+  }
+  k->ctx = c;
+  *out = k;
+  return CTL_OK;
+}
+
+extern "C" int ctl_keys_import(ctl_keys* k, uint64_t key_id, const uint64_t* coeffs, size_t n_words) {
+  if (!k || !coeffs) {
+    set_error("ctl_keys_import: null argument");
+    return CTL_EINVAL;
+  }
+  ctl_context* c = k->ctx;
+  const uint32_t N = c->N, LK = c->L + c->K;
+  const size_t kw = (size_t)c->beta * 2 * LK * N;
+  if (n_words != kw) {
+    set_error("ctl_keys_import: %zu words given, a key has %zu", n_words, kw);
+    return CTL_EINVAL;
+  }
+  if (key_id != 0 && (!(key_id & 1) || key_id >= 2ull * N)) {
+    set_error("ctl_keys_import: key id %llu is neither 0 nor an odd Galois element below 2N",
+              (unsigned long long)key_id);
+    return CTL_EINVAL;
+  }
+  for (size_t j = 0; j < (size_t)c->beta * 2; j++)
+    for (uint32_t i = 0; i < LK; i++)
+      for (uint32_t x = 0; x < N; x++)
+        if (coeffs[(j * LK + i) * N + x] >= c->moduli[i]) {
+          set_error("ctl_keys_import: residue out of range (limb %u)", i);
+          return CTL_EINVAL;
+        }
+  DBuf key(c, kw);
+  CHECK_ALLOC(key);
+  cudaMemcpyAsync(key.p, coeffs, kw * sizeof(u64), cudaMemcpyHostToDevice, c->stream);
+  launch_ntt_fwd(c, key.p, (size_t)LK * N, (int)(2 * c->beta), 0, (int)LK, (int)c->L);
+  launch_to_mont(c, key.p, (int)(2 * c->beta), (int)LK, (int)c->L, (size_t)LK * N, true);
+  if (int rc = cuda_check(cudaStreamSynchronize(c->stream), "key import")) return rc;
+  auto it = k->evk.find(key_id);
+  if (it != k->evk.end()) {
+    dev_free(c, it->second);
+    k->key_bytes -= kw * sizeof(u64);
+  }
+  k->evk[key_id] = key.release();
+  k->key_bytes += kw * sizeof(u64);
+  return CTL_OK;
+}
+
 extern "C" int ctl_keys_export(const ctl_keys* k, uint64_t key_id, uint64_t* out, size_t cap) {
   if (!k || !out) {
     set_error("ctl_keys_export: null argument");
@@ -781,6 +836,10 @@ extern "C" int ctl_encrypt_coeffs(ctl_context* c, const ctl_keys* k, const int64
     return CTL_EINVAL;
   }
   *out = nullptr;
+  if (!k->d_s) {
+    set_error("ctl_encrypt_coeffs: this key set holds no secret key (imported evaluation keys)");
+    return CTL_EKEY;
+  }
   const uint32_t N = c->N, L = c->L;
   std::vector<u64> a((size_t)L * N);
   for (uint32_t i = 0; i < L; i++) {
@@ -836,6 +895,10 @@ extern "C" int ctl_decrypt_coeffs(ctl_context* c, const ctl_keys* k, const ctl_c
   if (!c || !k || !ct || !m) {
     set_error("ctl_decrypt_coeffs: null argument");
     return CTL_EINVAL;
+  }
+  if (!k->d_s) {
+    set_error("ctl_decrypt_coeffs: this key set holds no secret key (imported evaluation keys)");
+    return CTL_EKEY;
   }
   const uint32_t N = c->N, lvl = ct->level;
   DBuf t(c, (size_t)lvl * N);
@@ -1012,6 +1075,7 @@ int keyswitch(ctl_context* c, int nr, int nb, int lvl, const u64* x, size_t x_r,
   const int E = lvl + (int)c->K;
   const bool hoisted = (x_r == 0);
   const int n_in = hoisted ? nb : nr * nb;
+  NvtxRange range(giant ? "keyswitch (giant steps)" : hoisted ? "keyswitch (hoisted)" : "keyswitch");
   if (nr > CTL_MAX_ROT) {
     set_error("keyswitch: at most %d rotations per launch", CTL_MAX_ROT);
     return CTL_EINVAL;
@@ -2277,9 +2341,11 @@ static int model_run(ctl_context* c, const ctl_model* M, const ctl_keys* k, cons
   u64* bufs[2] = {a.p, b.p};
   int w = 0;
   uint32_t lvl = M->in_level;
+  static const char* kLayerName[] = {"?", "dense", "square", "replicate", "conv1d", "poly3", "avgpool"};
   for (const LayerPlan& P : M->layers) {
     u64* dst = bufs[w];
     int rc = CTL_OK;
+    NvtxRange range(P.kind >= 1 && P.kind <= 6 ? kLayerName[P.kind] : kLayerName[0]);
     if (P.kind == CTL_LAYER_DENSE) {
       rc = dense_apply(c, k, P.dense, cur, nb, dst);
       lvl--;

@@ -8,6 +8,7 @@
 #include <mutex>
 #include <atomic>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "ctl.h"
 
@@ -210,6 +211,14 @@ struct ctl_ct {
 
 namespace ctl {
 
+// NVTX range over a scope (one per model layer and per key switch), for profilers that
+// attach to the process (ncu --nvtx); without a tool the push and pop are no-ops.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 // ---------------------------------------------------------------------------------
 // Memory and error helpers (ctl_api.cu).
 // ---------------------------------------------------------------------------------

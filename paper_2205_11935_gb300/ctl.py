@@ -61,6 +61,8 @@ SIGNATURES = {
     "ctl_keygen": (C.c_int, [_vp, _i32p, C.c_uint32, C.c_uint64, _pp]),
     "ctl_keys_destroy": (None, [_vp]),
     "ctl_keys_export": (C.c_int, [_vp, C.c_uint64, _u64p, _sz]),
+    "ctl_keys_create": (C.c_int, [_vp, _pp]),
+    "ctl_keys_import": (C.c_int, [_vp, C.c_uint64, _u64p, _sz]),
     "ctl_galois_element": (C.c_uint64, [_vp, C.c_int64]),
     "ctl_encode": (C.c_int, [_vp, _dp, _sz, C.c_double, _i64p]),
     "ctl_decode": (C.c_int, [_vp, _dp, _sz, C.c_double, _dp]),
@@ -269,6 +271,12 @@ class Context:
         _check(lib().ctl_keygen(self.h, _p(r, _i32p), len(r), seed, C.byref(h)))
         return Keys(self, h)
 
+    def keys_create(self):
+        """An empty key set (no secret) for evaluation keys received from a client."""
+        h = C.c_void_p()
+        _check(lib().ctl_keys_create(self.h, C.byref(h)))
+        return Keys(self, h)
+
     def encode(self, x, scale=None):
         x = np.ascontiguousarray(x, dtype=np.float64)
         m = np.zeros(self.N, dtype=np.int64)
@@ -424,6 +432,10 @@ class Keys:
         out = np.zeros((c.beta, 2, c.L + c.K, c.N), dtype=np.uint64)
         _check(lib().ctl_keys_export(self.h, key_id, _p(out, _u64p), out.size))
         return out
+
+    def import_key(self, key_id, coeffs):
+        a = np.ascontiguousarray(coeffs, dtype=np.uint64)
+        _check(lib().ctl_keys_import(self.h, int(key_id), _p(a, _u64p), a.size))
 
     def close(self):
         # a handle outlives nothing: once its context is destroyed, the context took its
