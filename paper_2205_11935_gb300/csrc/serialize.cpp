@@ -92,12 +92,20 @@ extern "C" int ctl_serialize(uint32_t N, const uint64_t* moduli, uint32_t level,
     for (uint32_t i = 0; i < level; i++) {
       const uint32_t w = bitlen(moduli[i]);
       const uint64_t* src = coeffs + ((size_t)p * level + i) * N;
-      size_t bit = 0;
+      // LSB-first bit stream: residues enter a 128-bit window, whole bytes leave it
+      unsigned __int128 acc = 0;
+      uint32_t nbits = 0;
+      size_t o = pos;
       for (uint32_t k = 0; k < N; k++) {
-        const u64 v = src[k];
-        for (uint32_t b = 0; b < w; b++, bit++)
-          if ((v >> b) & 1) out[pos + bit / 8] |= (uint8_t)(1u << (bit % 8));
+        acc |= (unsigned __int128)src[k] << nbits;
+        nbits += w;
+        while (nbits >= 8) {
+          out[o++] = (uint8_t)acc;
+          acc >>= 8;
+          nbits -= 8;
+        }
       }
+      if (nbits) out[o] = (uint8_t)acc;
       pos += limb_bytes(moduli[i], N);
     }
   if (size) *size = need;
@@ -135,12 +143,19 @@ extern "C" int ctl_deserialize(const uint8_t* in, size_t size, uint32_t N, const
   for (uint32_t p = 0; p < np; p++)
     for (uint32_t i = 0; i < lvl; i++) {
       const uint32_t w = bitlen(moduli[i]);
+      const u64 mask = w == 64 ? ~0ull : (1ull << w) - 1;
       uint64_t* dst = coeffs + ((size_t)p * lvl + i) * N;
-      size_t bit = 0;
+      unsigned __int128 acc = 0;
+      uint32_t nbits = 0;
+      size_t o = pos;
       for (uint32_t k = 0; k < N; k++) {
-        u64 v = 0;
-        for (uint32_t b = 0; b < w; b++, bit++)
-          if ((in[pos + bit / 8] >> (bit % 8)) & 1) v |= 1ull << b;
+        while (nbits < w) {
+          acc |= (unsigned __int128)in[o++] << nbits;
+          nbits += 8;
+        }
+        const u64 v = (u64)acc & mask;
+        acc >>= w;
+        nbits -= w;
         if (v >= moduli[i]) {
           set_error("ctl_deserialize: residue out of range (poly %u, limb %u)", p, i);
           return CTL_EINVAL;
