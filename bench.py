@@ -634,25 +634,53 @@ def main():
         pinned_out = torch.empty(out_words, dtype=torch.int64).pin_memory()
         import ctypes as C
 
-        def e2e_step():
-            h = C.c_void_p()
-            ctl._check(ctl.lib().ctl_ct_import(ctx.h, C.cast(pinned_in.data_ptr(), ctl._u64p), B, len(wl["q"]),
-                                               scale, C.byref(h)))
-            ci = ctl.Ciphertext(ctx, h)
-            co = model.forward(keys, ci, graph=use_graph)
-            ctl._check(ctl.lib().ctl_ct_export(co.h, C.cast(pinned_out.data_ptr(), ctl._u64p), out_words))
-            ci.close()
-            co.close()
+        # two streams: step i+1's upload (H2D copy and transform, on a context clone's
+        # stream) and step i's download (D2H copy) overlap step i's forward; every step
+        # still uploads its inputs and reads its result back inside the timed region
+        io_stream = torch.cuda.Stream()
+        ctx_io = ctx.clone(io_stream.cuda_stream)
+        out_dev = [torch.empty(out_words, dtype=torch.int64, device="cuda") for _ in range(2)]
+        pinned_outs = [pinned_out, torch.empty(out_words, dtype=torch.int64).pin_memory()]
 
-        e2e_step()
+        def e2e_run(steps):
+            ci, ev_in, d2h = [None] * steps, [None] * steps, [None] * steps
+
+            def upload(i):
+                h = C.c_void_p()
+                ctl._check(ctl.lib().ctl_ct_import(ctx_io.h, C.cast(pinned_in.data_ptr(), ctl._u64p), B,
+                                                   len(wl["q"]), scale, C.byref(h)))
+                ci[i] = ctl.Ciphertext(ctx_io, h)
+                ev_in[i] = torch.cuda.Event()
+                ev_in[i].record(io_stream)
+
+            upload(0)
+            for i in range(steps):
+                stream.wait_event(ev_in[i])
+                co = model.forward(keys, ci[i], graph=use_graph)
+                if i + 1 < steps:
+                    upload(i + 1)
+                if i >= 2:
+                    stream.wait_event(d2h[i - 2])  # staging buffer i % 2 has been read back
+                ctl._check(ctl.lib().ctl_ct_export_dev(co.h, C.c_void_p(out_dev[i % 2].data_ptr()), out_words))
+                done = torch.cuda.Event()
+                done.record(stream)
+                io_stream.wait_event(done)
+                with torch.cuda.stream(io_stream):
+                    pinned_outs[i % 2].copy_(out_dev[i % 2], non_blocking=True)
+                d2h[i] = torch.cuda.Event()
+                d2h[i].record(io_stream)
+                co.close()
+                ci[i].close()  # freed on the upload stream, after the forward (waited above)
+            torch.cuda.synchronize()
+
+        e2e_run(1)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
         t_start = time.perf_counter()
-        for _ in range(args.steps):
-            e2e_step()
-        torch.cuda.synchronize()
+        e2e_run(args.steps)
         e2e_s = time.perf_counter() - t_start
+        ctx_io.close()
         e2e_s = max_over_ranks(e2e_s, dist)
         e2e = {"value": replica_throughput(world, B, args.steps, e2e_s), "unit": "forwards/s",
                "h2d_bytes_per_step": int(h2d),

@@ -86,7 +86,10 @@ void ctl_context_destroy(ctl_context* ctx);
 /* Writes the n_q + n_p primes (data chain then special primes) to moduli (nullable) and
  * the counts to the other (nullable) outputs. */
 int ctl_context_info(const ctl_context* ctx, uint64_t* moduli, uint32_t* n_q, uint32_t* n_p, uint32_t* alpha);
-/* Makes the context issue its work on `stream` (a cudaStream_t, NULL = library stream). */
+/* Makes the context issue its work on `stream` (a cudaStream_t owned by the caller, which
+ * must outlive the context's use of it; the library never destroys it), or, with NULL, on a
+ * new stream of the library's own.  Work already queued on the previous stream is finished
+ * first. */
 int ctl_set_stream(ctl_context* ctx, void* stream);
 int ctl_set_allocator(ctl_context* ctx, ctl_alloc_fn alloc_fn, ctl_free_fn free_fn, void* user);
 /* Blocks until the context stream is idle. */

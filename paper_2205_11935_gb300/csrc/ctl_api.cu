@@ -465,7 +465,14 @@ extern "C" int ctl_set_stream(ctl_context* c, void* stream) {
     return CTL_EINVAL;
   }
   if (stream) {
+    // the caller's stream: the library stops owning one (its own is finished and
+    // destroyed first, so earlier work stays ordered before later work)
+    if (c->own_stream) {
+      cudaStreamSynchronize(c->stream);
+      cudaStreamDestroy(c->stream);
+    }
     c->stream = (cudaStream_t)stream;
+    c->own_stream = false;
   } else {
     cudaStream_t s;
     if (int rc = cuda_check(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "stream")) return rc;

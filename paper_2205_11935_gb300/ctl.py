@@ -254,6 +254,19 @@ class Context:
     def set_stream(self, stream_ptr):
         _check(lib().ctl_set_stream(self.h, C.c_void_p(stream_ptr)))
 
+    def clone(self, stream_ptr=None):
+        """ctl_context_clone: same parameters and device tables, own stream (close the
+        clone before the original)."""
+        h = C.c_void_p()
+        _check(lib().ctl_context_clone(self.h, C.byref(h)))
+        c = object.__new__(Context)
+        c.h = h
+        c.N, c.L, c.K, c.scale = self.N, self.L, self.K, self.scale
+        c.moduli, c.alpha, c.beta = self.moduli, self.alpha, self.beta
+        if stream_ptr is not None:
+            c.set_stream(stream_ptr)
+        return c
+
     def synchronize(self):
         _check(lib().ctl_synchronize(self.h))
 
