@@ -357,3 +357,36 @@ def test_biases_windows_and_lazy_dense_in_the_paper_stack():
         h = g.dense(k, h, W2s, bias=b2)
         assert np.array_equal(h.export(), out.export())
         model.close()
+
+
+def test_layer_error_codes():
+    """Refusals of the new calls: each fails with its documented code and leaves the
+    context usable."""
+    P = pair("b4")
+    g, k = P.g, P.k
+    z, ct_o = P.fresh(112)
+    ct = g.ct_import(ct_o, P.scale)
+    low = g.drop_level(ct, 2)
+
+    def code(fn, *a):
+        with pytest.raises(ctl.CtlError) as e:
+            fn(*a)
+        return e.value.code
+
+    assert code(g.mul, k, ct, low) == -2                  # levels differ
+    assert code(g.poly3, k, low, [0, 1, 0, 0]) == -2      # depth 2 needs three primes
+    assert code(g.poly3, k, ct, [0, 0, 0, 1e30]) == -1    # a constant beyond 2^63
+    assert code(g.avgpool, k, ct, 0) == -1
+    assert code(g.avgpool, k, ct, P.N) == -1
+    assert code(g.conv1d, k, ct, [1.0, 2.0, 3.0], 40, 32) == -1   # n > t
+    assert code(g.conv1d, k, ct, [1.0], 8, P.N) == -1             # 2t beyond the slots
+    assert code(g.drop_level, ct, 0) == -2
+    assert code(g.mul_const, ct, 3, 0.0) == -1
+    assert code(g.avgpool, k, g.drop_level(ct, 1), 2) == -2       # no level left
+    assert code(g.rotate, k, ct, 9) == -4                          # no Galois key for 9
+    with pytest.raises(ctl.CtlError) as e:
+        ctl.Model(g, [("poly3", [0, 1, 0, 0])], in_level=2)
+    assert e.value.code == -2
+    # the context still works
+    out = g.poly3(k, ct, [0.1, 0.2, 0.3, 0.0])
+    assert out.info()[0] == ct_o.shape[1] - 2
