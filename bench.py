@@ -748,11 +748,16 @@ def main():
     basis = (f"{SM_COUNT} SMs x {IMAD_PER_CLK_SM} IMAD/clk x {MAX_SM_MHZ:.0f} MHz / " +
              (f"{SPLIT_MAC_IMAD:.0f} IMAD slots per split-half MAC" if dom in MAC_CLASSES
               else f"{SHOUP_IMAD} IMAD per Shoup modmul (measured)"))
+    # the unit rates behind the peak, measured on this GPU now (ctl_microbench_unit_rate)
+    ub = {name: ctl.microbench_unit_rate(kind) for kind, name in
+          enumerate(("shoup_modmul", "harvey_butterfly", "shoup_three_half", "split_mac"))}
+    ub["imad_slots_per_shoup_modmul"] = IMAD_PER_CLK_SM / ub["shoup_modmul"]
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved / 1e9, "peak": peak / 1e9,
                 "unit": unit, "frac": achieved / peak, "traffic": traffic, "peak_basis": basis,
                 "traffic_basis": ("ncu dram bytes per limb item of this kernel at batch 16, times the items of "
                                   "an average launch" if traffic is not None else None),
                 "avg_launch_ms": d["ms"] / max(d["launches"], 1), "classes": per_class,
+                "unit_rates_per_clk_sm": ub,
                 "timing": timing_source}
 
     cpu = None

@@ -444,6 +444,13 @@ int ctl_server_stats(ctl_server* srv, uint64_t* counts6, double* p50_ms, double*
 /* Stops the workers (queued requests are dropped) and releases the server. */
 void ctl_server_destroy(ctl_server* srv);
 
+/* Microbenchmark of the integer work units the roofline counts, on the current device:
+ * writes units per clock per SM (at the device's maximum SM clock) of kind 0 = 64-bit
+ * Shoup modular multiplication, 1 = Harvey butterfly, 2 = three-high-half Shoup product,
+ * 3 = split-half multiply-accumulate (four 32x32->64 multiply-adds).  Synchronous; tens of
+ * milliseconds.  Errors: CTL_EINVAL, CTL_ENOMEM, CTL_ECUDA. */
+int ctl_microbench_unit_rate(int kind, double* per_clk_sm);
+
 /* ---------------------------------------------------------------------------------
  * Statistics: kernel launches since the last reset, homomorphic operation counters
  * (rotations, plaintext products, additions, relinearisations, rescales), and, when

@@ -119,6 +119,7 @@ SIGNATURES = {
     "ctl_server_wait": (C.c_int, [_vp, C.c_uint64, C.c_uint32, _u64p, _sz, _dp]),
     "ctl_server_stats": (C.c_int, [_vp, _u64p, _dp, _dp]),
     "ctl_server_destroy": (None, [_vp]),
+    "ctl_microbench_unit_rate": (C.c_int, [C.c_int, _dp]),
     "ctl_stats_reset": (C.c_int, [_vp]),
     "ctl_stats_enable_timing": (C.c_int, [_vp, C.c_int]),
     "ctl_stats_launches": (C.c_uint64, [_vp]),
@@ -153,6 +154,14 @@ def _check(rc):
 
 def _p(a, t):
     return a.ctypes.data_as(t)
+
+
+def microbench_unit_rate(kind):
+    """Units per clock per SM of kind 0 = Shoup modmul, 1 = Harvey butterfly, 2 = three-high-half
+    Shoup product, 3 = split-half multiply-accumulate (ctl_microbench_unit_rate)."""
+    v = C.c_double()
+    _check(lib().ctl_microbench_unit_rate(int(kind), C.byref(v)))
+    return v.value
 
 
 def plan_primes(N, bits):
