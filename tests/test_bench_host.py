@@ -1,0 +1,48 @@
+"""Host-side pieces of bench.py (no GPU): its synthetic paper network and FP64 reference
+agree with the test suite's, the input layout holds one [x, x] window per prediction,
+and the CPU-baseline extrapolation counts the operations the paper states."""
+import os
+import sys
+
+import numpy as np
+
+from tests import netref
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_paper_network_and_reference_match_the_tests():
+    n = 768
+    layers, pw = bench.paper_layers_for(n)
+    w, W1, W2, W2s = netref.paper_net_weights(n)
+    assert np.array_equal(pw[0], w) and np.array_equal(pw[1], W1) and np.array_equal(pw[2], W2)
+    assert [ly[0] for ly in layers] == ["conv1d", "dense", "replicate", "poly3", "avgpool", "dense"]
+    assert np.array_equal(layers[5][1], W2s)
+    assert bench.RELU_APPROX == netref.relu_coeffs()
+    x = np.random.default_rng(3).uniform(-1, 1, n)
+    assert np.max(np.abs(bench.paper_fp64(pw, x) - netref.paper_net_fp64(x, w, W1, W2, netref.relu_coeffs()))) < 1e-12
+
+
+def test_input_windows_layout():
+    N, t0 = 8192, 1024
+    xs, slots = bench.inputs_for(N, [768], 3, t0, windows=2)
+    assert xs.shape == (3, 2, 768) and slots.shape == (3, N // 2)
+    for b in range(3):
+        for j in range(2):
+            base = 2 * t0 * j
+            assert np.array_equal(slots[b, base:base + 768], xs[b, j])
+            assert np.array_equal(slots[b, base + t0:base + t0 + 768], xs[b, j])
+            assert not slots[b, base + 768:base + t0].any()
+
+
+def test_operation_plan_follows_the_papers_counts():
+    # dense t x t by Eq. (bsgs): t1 + t2 - 2 rotations and t products; conv f = 9: 8
+    # rotations and 9 products; avgpool 3: 2 rotations; the paper's depth 6
+    plan = bench.op_plan(bench.WORKLOADS["paper_p1"])
+    rots = sum(p[0] for p in plan)
+    assert rots == 8 + 62 + 1 + 2 + 2 + 62  # conv, dense, replicate, ReLU (2 relins), pool, dense
+    assert [p[3] for p in plan] == [7, 6, 5, 5, 4, 3, 2]
+    plan = bench.op_plan(bench.WORKLOADS["batched"])
+    assert sum(p[1] for p in plan if p[1] >= 1) >= 1024 + 256 + 256
