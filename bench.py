@@ -526,7 +526,13 @@ def main():
 
     import __graft_entry__
 
-    __graft_entry__.build()
+    # one rank per node compiles (the object files are shared); the others wait for it
+    if local == 0:
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    if local != 0:
+        __graft_entry__.build()  # up to date by now: returns at once
     from paper_2205_11935_gb300 import ctl
 
     N, B = wl["N"], wl["batch"]
