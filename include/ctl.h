@@ -225,6 +225,19 @@ void ctl_ct_destroy(ctl_ct* ct);
  *   *level.  Errors: CTL_EINVAL (malformed header, size, residue out of range).
  * ------------------------------------------------------------------------------- */
 size_t ctl_serialized_size(uint32_t N, const uint64_t* moduli, uint32_t level, int seeded);
+/* Key-switching key messages (the evaluation keys a client sends; host only): a key
+ * [beta][2][limbs][N] in the coefficient form of ctl_keys_export (limbs = n_q + n_p, primes
+ * moduli[limbs], data then special) is packed like ciphertext limbs after a 20-byte header
+ * ("CTLK", N, limbs, beta, flags, key id).  seeded != 0 stores only the b part of every
+ * digit plus the key-generation seed: the a parts are the uniform polynomials of the
+ * streams (seed, key id, digit, limb), which ctl_deserialize_key draws again.  The
+ * message of a key made by ctl_keygen(..., seed) with that seed is half the size.
+ * Errors: CTL_EINVAL (capacity, parameters, a residue >= its prime, malformed message). */
+size_t ctl_key_message_size(uint32_t N, const uint64_t* moduli, uint32_t limbs, uint32_t beta, int seeded);
+int ctl_serialize_key(uint32_t N, const uint64_t* moduli, uint32_t limbs, uint32_t beta, uint64_t key_id,
+                      const uint64_t* coeffs, int seeded, uint64_t seed, uint8_t* out, size_t cap, size_t* size);
+int ctl_deserialize_key(const uint8_t* in, size_t size, uint32_t N, const uint64_t* moduli, uint32_t limbs,
+                        uint32_t beta, uint64_t* coeffs, size_t cap, uint64_t* key_id);
 /* Host only: slot values x[n] encoded at `scale` (any magnitude up to ~2^1000) straight to
  * residues out[lvl][N] modulo moduli[0..lvl): round(m_k) mod q_i with m_k as ctl_encode
  * defines it (half away from zero).  This is how dense and conv1d layers encode their

@@ -45,6 +45,51 @@ uint32_t get32(const uint8_t* p) {
   for (int i = 0; i < 4; i++) v |= (uint32_t)p[i] << (8 * i);
   return v;
 }
+
+// One limb of N residues, LSB-first at w bits each through a 128-bit window; out holds
+// limb_bytes(q, N) zeroed bytes.
+void pack_limb(const u64* src, uint32_t N, uint32_t w, uint8_t* out) {
+  unsigned __int128 acc = 0;
+  uint32_t nbits = 0;
+  size_t o = 0;
+  for (uint32_t k = 0; k < N; k++) {
+    acc |= (unsigned __int128)src[k] << nbits;
+    nbits += w;
+    while (nbits >= 8) {
+      out[o++] = (uint8_t)acc;
+      acc >>= 8;
+      nbits -= 8;
+    }
+  }
+  if (nbits) out[o] = (uint8_t)acc;
+}
+// The inverse; false if a residue is not below q.
+bool unpack_limb(const uint8_t* in, uint32_t N, uint32_t w, u64 q, u64* dst) {
+  const u64 mask = w == 64 ? ~0ull : (1ull << w) - 1;
+  unsigned __int128 acc = 0;
+  uint32_t nbits = 0;
+  size_t o = 0;
+  for (uint32_t k = 0; k < N; k++) {
+    while (nbits < w) {
+      acc |= (unsigned __int128)in[o++] << nbits;
+      nbits += 8;
+    }
+    const u64 v = (u64)acc & mask;
+    acc >>= w;
+    nbits -= w;
+    if (v >= q) return false;
+    dst[k] = v;
+  }
+  return true;
+}
+void put64(uint8_t* p, u64 v) {
+  for (int i = 0; i < 8; i++) p[i] = (uint8_t)(v >> (8 * i));
+}
+u64 get64(const uint8_t* p) {
+  u64 v = 0;
+  for (int i = 0; i < 8; i++) v |= (u64)p[i] << (8 * i);
+  return v;
+}
 }  // namespace
 
 extern "C" size_t ctl_serialized_size(uint32_t N, const uint64_t* moduli, uint32_t level, int seeded) {
@@ -90,22 +135,7 @@ extern "C" int ctl_serialize(uint32_t N, const uint64_t* moduli, uint32_t level,
   }
   for (uint32_t p = 0; p < np; p++)
     for (uint32_t i = 0; i < level; i++) {
-      const uint32_t w = bitlen(moduli[i]);
-      const uint64_t* src = coeffs + ((size_t)p * level + i) * N;
-      // LSB-first bit stream: residues enter a 128-bit window, whole bytes leave it
-      unsigned __int128 acc = 0;
-      uint32_t nbits = 0;
-      size_t o = pos;
-      for (uint32_t k = 0; k < N; k++) {
-        acc |= (unsigned __int128)src[k] << nbits;
-        nbits += w;
-        while (nbits >= 8) {
-          out[o++] = (uint8_t)acc;
-          acc >>= 8;
-          nbits -= 8;
-        }
-      }
-      if (nbits) out[o] = (uint8_t)acc;
+      pack_limb((const u64*)(coeffs + ((size_t)p * level + i) * N), N, bitlen(moduli[i]), out + pos);
       pos += limb_bytes(moduli[i], N);
     }
   if (size) *size = need;
@@ -142,25 +172,9 @@ extern "C" int ctl_deserialize(const uint8_t* in, size_t size, uint32_t N, const
   }
   for (uint32_t p = 0; p < np; p++)
     for (uint32_t i = 0; i < lvl; i++) {
-      const uint32_t w = bitlen(moduli[i]);
-      const u64 mask = w == 64 ? ~0ull : (1ull << w) - 1;
-      uint64_t* dst = coeffs + ((size_t)p * lvl + i) * N;
-      unsigned __int128 acc = 0;
-      uint32_t nbits = 0;
-      size_t o = pos;
-      for (uint32_t k = 0; k < N; k++) {
-        while (nbits < w) {
-          acc |= (unsigned __int128)in[o++] << nbits;
-          nbits += 8;
-        }
-        const u64 v = (u64)acc & mask;
-        acc >>= w;
-        nbits -= w;
-        if (v >= moduli[i]) {
-          set_error("ctl_deserialize: residue out of range (poly %u, limb %u)", p, i);
-          return CTL_EINVAL;
-        }
-        dst[k] = v;
+      if (!unpack_limb(in + pos, N, bitlen(moduli[i]), moduli[i], (u64*)(coeffs + ((size_t)p * lvl + i) * N))) {
+        set_error("ctl_deserialize: residue out of range (poly %u, limb %u)", p, i);
+        return CTL_EINVAL;
       }
       pos += limb_bytes(moduli[i], N);
     }
@@ -190,5 +204,115 @@ extern "C" int ctl_encode_residues(uint32_t N, const uint64_t* moduli, uint32_t 
     set_error("ctl_encode_residues: value out of range");
     return CTL_EINVAL;
   }
+  return CTL_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// Key-switching key messages (the evaluation keys a client sends to the server).  Format:
+//   bytes 0..3 'C' 'T' 'L' 'K', 4..7 N, 8..9 limbs (data then special primes), 10 digits
+//   (beta), 11 flags (bit 0: seeded), 12..19 key id, 20..27 key seed (seeded only), then
+//   per digit d the limbs of b_d and, unless seeded, of a_d, packed as ciphertext limbs.
+// A seeded message omits every a_d: it is the uniform polynomial of the key generation's
+// streams (seed, key id, digit, limb), drawn again on receipt.
+// ---------------------------------------------------------------------------------
+namespace {
+constexpr size_t kKeyHeader = 20;
+}
+
+extern "C" size_t ctl_key_message_size(uint32_t N, const uint64_t* moduli, uint32_t limbs, uint32_t beta,
+                                       int seeded) {
+  if (!valid(N, moduli, limbs) || beta == 0 || beta > 255) return 0;
+  size_t s = kKeyHeader + (seeded ? 8 : 0), per = 0;
+  for (uint32_t i = 0; i < limbs; i++) per += limb_bytes(moduli[i], N);
+  return s + (size_t)beta * (seeded ? 1 : 2) * per;
+}
+
+extern "C" int ctl_serialize_key(uint32_t N, const uint64_t* moduli, uint32_t limbs, uint32_t beta, uint64_t key_id,
+                                 const uint64_t* coeffs, int seeded, uint64_t seed, uint8_t* out, size_t cap,
+                                 size_t* size) {
+  const size_t need = ctl_key_message_size(N, moduli, limbs, beta, seeded);
+  if (!need || !coeffs || !out) {
+    set_error("ctl_serialize_key: invalid argument");
+    return CTL_EINVAL;
+  }
+  if (cap < need) {
+    set_error("ctl_serialize_key: %zu bytes needed, %zu given", need, cap);
+    return CTL_EINVAL;
+  }
+  for (size_t j = 0; j < (size_t)beta * 2; j++)
+    for (uint32_t i = 0; i < limbs; i++)
+      for (uint32_t k = 0; k < N; k++)
+        if (coeffs[(j * limbs + i) * N + k] >= moduli[i]) {
+          set_error("ctl_serialize_key: residue not reduced (limb %u)", i);
+          return CTL_EINVAL;
+        }
+  memset(out, 0, need);
+  out[0] = 'C';
+  out[1] = 'T';
+  out[2] = 'L';
+  out[3] = 'K';
+  put32(out + 4, N);
+  out[8] = (uint8_t)(limbs & 0xFF);
+  out[9] = (uint8_t)(limbs >> 8);
+  out[10] = (uint8_t)beta;
+  out[11] = seeded ? 1 : 0;
+  put64(out + 12, key_id);
+  size_t pos = kKeyHeader;
+  if (seeded) {
+    put64(out + pos, seed);
+    pos += 8;
+  }
+  for (uint32_t d = 0; d < beta; d++)
+    for (uint32_t p = 0; p < (seeded ? 1u : 2u); p++)
+      for (uint32_t i = 0; i < limbs; i++) {
+        pack_limb((const u64*)(coeffs + (((size_t)d * 2 + p) * limbs + i) * N), N, bitlen(moduli[i]), out + pos);
+        pos += limb_bytes(moduli[i], N);
+      }
+  if (size) *size = need;
+  return CTL_OK;
+}
+
+extern "C" int ctl_deserialize_key(const uint8_t* in, size_t size, uint32_t N, const uint64_t* moduli,
+                                   uint32_t limbs, uint32_t beta, uint64_t* coeffs, size_t cap,
+                                   uint64_t* key_id) {
+  if (!in || !moduli || !coeffs || size < kKeyHeader) {
+    set_error("ctl_deserialize_key: invalid argument");
+    return CTL_EINVAL;
+  }
+  const bool seeded = (in[11] & 1) != 0;
+  if (in[0] != 'C' || in[1] != 'T' || in[2] != 'L' || in[3] != 'K' || get32(in + 4) != N ||
+      ((uint32_t)in[8] | ((uint32_t)in[9] << 8)) != limbs || in[10] != beta || (in[11] & ~1u) ||
+      size != ctl_key_message_size(N, moduli, limbs, beta, seeded ? 1 : 0)) {
+    set_error("ctl_deserialize_key: not a key message for these parameters");
+    return CTL_EINVAL;
+  }
+  if (cap < (size_t)beta * 2 * limbs * N) {
+    set_error("ctl_deserialize_key: output needs %zu words", (size_t)beta * 2 * limbs * N);
+    return CTL_EINVAL;
+  }
+  const u64 kid = get64(in + 12);
+  size_t pos = kKeyHeader;
+  u64 seed = 0;
+  if (seeded) {
+    seed = get64(in + pos);
+    pos += 8;
+  }
+  for (uint32_t d = 0; d < beta; d++)
+    for (uint32_t p = 0; p < (seeded ? 1u : 2u); p++)
+      for (uint32_t i = 0; i < limbs; i++) {
+        if (!unpack_limb(in + pos, N, bitlen(moduli[i]), moduli[i],
+                         (u64*)(coeffs + (((size_t)d * 2 + p) * limbs + i) * N))) {
+          set_error("ctl_deserialize_key: residue out of range (digit %u, limb %u)", d, i);
+          return CTL_EINVAL;
+        }
+        pos += limb_bytes(moduli[i], N);
+      }
+  if (seeded)
+    for (uint32_t d = 0; d < beta; d++)
+      for (uint32_t i = 0; i < limbs; i++) {
+        SplitMixStream sa(seed, stream_id_key_a(kid, d, i));
+        draw_uniform(sa, moduli[i], N, (u64*)(coeffs + (((size_t)d * 2 + 1) * limbs + i) * N));
+      }
+  if (key_id) *key_id = kid;
   return CTL_OK;
 }

@@ -97,6 +97,11 @@ SIGNATURES = {
     "ctl_ntt_dev": (C.c_int, [_vp, _vp, _vp, C.c_uint32, C.c_uint32, C.c_int]),
     "ctl_serialized_size": (C.c_size_t, [C.c_uint32, _u64p, C.c_uint32, C.c_int]),
     "ctl_encode_residues": (C.c_int, [C.c_uint32, _u64p, C.c_uint32, _dp, _sz, C.c_double, _u64p]),
+    "ctl_key_message_size": (C.c_size_t, [C.c_uint32, _u64p, C.c_uint32, C.c_uint32, C.c_int]),
+    "ctl_serialize_key": (C.c_int, [C.c_uint32, _u64p, C.c_uint32, C.c_uint32, C.c_uint64, _u64p, C.c_int,
+                                    C.c_uint64, C.POINTER(C.c_uint8), _sz, C.POINTER(C.c_size_t)]),
+    "ctl_deserialize_key": (C.c_int, [C.POINTER(C.c_uint8), _sz, C.c_uint32, _u64p, C.c_uint32, C.c_uint32, _u64p,
+                                      _sz, _u64p]),
     "ctl_serialize": (C.c_int, [C.c_uint32, _u64p, C.c_uint32, _u64p, C.c_int, C.c_uint64, C.POINTER(C.c_uint8),
                                 _sz, C.POINTER(C.c_size_t)]),
     "ctl_deserialize": (C.c_int, [C.POINTER(C.c_uint8), _sz, C.c_uint32, _u64p, C.c_uint32, _u64p, _sz, _u32p]),
@@ -193,6 +198,31 @@ def encode_residues(N, moduli, x, scale):
     out = np.zeros((len(m), N), dtype=np.uint64)
     _check(lib().ctl_encode_residues(N, _p(m, _u64p), len(m), _p(x, _dp), len(x), float(scale), _p(out, _u64p)))
     return out
+
+
+def serialize_key(N, moduli, key_id, coeffs, seed=None):
+    """Message bytes of a key [beta][2][limbs][N] (coefficient form, as Keys.export returns);
+    with seed (the ctl_keygen seed), the seeded form that omits the a parts."""
+    m = np.ascontiguousarray(moduli, dtype=np.uint64)
+    a = np.ascontiguousarray(coeffs, dtype=np.uint64)
+    beta, _, limbs, _ = a.shape
+    seeded = 0 if seed is None else 1
+    n = lib().ctl_key_message_size(N, _p(m, _u64p), limbs, beta, seeded)
+    out = np.zeros(n, dtype=np.uint8)
+    _check(lib().ctl_serialize_key(N, _p(m, _u64p), limbs, beta, int(key_id), _p(a, _u64p), seeded,
+                                   0 if seed is None else int(seed), _p(out, C.POINTER(C.c_uint8)), n, None))
+    return out.tobytes()
+
+
+def deserialize_key(msg, N, moduli, beta):
+    """(key id, key [beta][2][limbs][N]) of a key message."""
+    m = np.ascontiguousarray(moduli, dtype=np.uint64)
+    b = np.frombuffer(bytes(msg), dtype=np.uint8).copy()
+    out = np.zeros((beta, 2, len(m), N), dtype=np.uint64)
+    kid = C.c_uint64()
+    _check(lib().ctl_deserialize_key(_p(b, C.POINTER(C.c_uint8)), len(b), N, _p(m, _u64p), len(m), beta,
+                                     _p(out, _u64p), out.size, C.byref(kid)))
+    return kid.value, out
 
 
 def deserialize(msg, N, moduli):

@@ -103,3 +103,53 @@ def test_encode_residues_matches_the_oracle_encoding(log_scale):
     if log_scale == 30:  # within 64 bits: the same rounding as the 64-bit encoder, mod q
         for i, q in enumerate(moduli):
             assert np.array_equal(res[i], (ref.astype(object) % q).astype(np.uint64))
+
+
+@pytest.mark.parametrize("seeded", [False, True])
+def test_key_messages_round_trip_and_seeded_form_regenerates_the_oracles_keys(seeded):
+    """The seeded key message carries only the b parts; the receiver draws the a parts
+    again from the key-generation streams.  Pinned against the oracle's own key
+    generation (an independent implementation of the generator and the stream ids)."""
+    N, qb, pb, dnum = 256, [45, 45, 45, 45], [60, 60], 2
+    o = O.Oracle(N, qb, pb, dnum=dnum, scale=2.0 ** 40)
+    o.keygen([1, -4], seed=11)
+    for r in (None, 1, -4):
+        kid = 0 if r is None else o.galois_element(r)
+        key = o.key_export(kid)
+        msg = ctl.serialize_key(N, o.moduli, kid, key, seed=11 if seeded else None)
+        got_id, back = ctl.deserialize_key(msg, N, o.moduli, o.beta)
+        assert got_id == kid and np.array_equal(back, key)
+    full = ctl.serialize_key(N, o.moduli, 0, o.key_export(0))
+    half = ctl.serialize_key(N, o.moduli, 0, o.key_export(0), seed=11)
+    assert len(half) - 8 - 20 == (len(full) - 20) // 2
+
+
+def test_key_message_sizes_for_the_batched_parameters():
+    # N = 16384, 8 x 45-bit + 2 x 60-bit primes, 4 digits: 4 x 2 x 983,040 bytes, or half seeded
+    N = 16384
+    moduli = ctl.plan_primes(N, [45] * 8 + [60, 60])
+    m = np.asarray(moduli, dtype=np.uint64)
+    import ctypes as C
+    size = ctl.lib().ctl_key_message_size(N, m.ctypes.data_as(C.POINTER(C.c_uint64)), 10, 4, 0)
+    seeded = ctl.lib().ctl_key_message_size(N, m.ctypes.data_as(C.POINTER(C.c_uint64)), 10, 4, 1)
+    per = (8 * 45 + 2 * 60) * N // 8
+    assert size == 20 + 8 * per and seeded == 28 + 4 * per
+
+
+def test_malformed_key_messages_are_refused():
+    N = 64
+    moduli = ctl.plan_primes(N, [50, 40, 60])
+    rng = np.random.default_rng(6)
+    key = np.stack([np.stack([np.stack([rng.integers(0, q, N, dtype=np.uint64) for q in moduli])
+                              for _ in range(2)]) for _ in range(2)])
+    msg = ctl.serialize_key(N, moduli, 5, key)
+    assert np.array_equal(ctl.deserialize_key(msg, N, moduli, 2)[1], key)
+    for bad in (msg[:-1], b"CTL1" + msg[4:], msg + b"\0"):
+        with pytest.raises(ctl.CtlError):
+            ctl.deserialize_key(bad, N, moduli, 2)
+    with pytest.raises(ctl.CtlError):
+        ctl.deserialize_key(msg, N, moduli, 3)  # another digit count
+    big = key.copy()
+    big[1, 0, 2, 7] = moduli[2]
+    with pytest.raises(ctl.CtlError):
+        ctl.serialize_key(N, moduli, 5, big)
