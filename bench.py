@@ -52,7 +52,7 @@ WORKLOADS = {
     "single8192": dict(N=8192, q=[60, 40, 40, 40], p=[60], dnum=4, batch=1, dims=[512, 128, 64],
                        desc="1 ciphertext, N=8192, q {60,40,40,40} + 60-bit p, scale 2^40; "
                             "dense 512->128, x^2, dense 128->64"),
-    "single4096": dict(N=4096, q=[50, 40, 40], p=[60], dnum=3, batch=1, dims=[64, 32],
+    "single4096": dict(N=4096, q=[50, 40, 40], p=[60], dnum=3, batch=1, dims=[64, 32], square_last=True,
                        desc="1 ciphertext, N=4096, q {50,40,40} + 60-bit p, scale 2^40; dense 64->32, x^2"),
     # the paper's own frozen network (Sec. 4.1) at its parameter sets (Tab. 1)
     "paper_p1": dict(N=8192, q=[34] + [25] * 6, p=[34], dnum=7, batch=1, dims=[768, 768, 766], net="paper",
@@ -218,7 +218,7 @@ def op_plan(wl):
         t1, t2 = split(t)
         plan.append((t1 + t2 - 2, t, 1, lvl))
         lvl -= 1
-        if i + 1 < len(dims) - 1 or wl is WORKLOADS["single4096"]:
+        if i + 1 < len(dims) - 1 or wl.get("square_last", False):
             plan.append((1, 1.5, 1, lvl))  # square: 3 products, relinearisation, rescale
             lvl -= 1
             if i + 1 < len(dims) - 1:
@@ -226,11 +226,62 @@ def op_plan(wl):
     return plan
 
 
-def cpu_oracle_sample(wl):
-    """Times the oracle on one rotation, one plaintext product and one rescale at the top
-    level of the workload's ring, and extrapolates a forward by its operation counts.
-    Returns (seconds per forward estimate, description, cores)."""
+def oracle_forward_seconds(wl):
+    """One whole forward of a dense / square / replicate network on the oracle (rings of
+    N <= 4096, where it takes seconds); key generation and the diagonals' encoding are
+    set-up and not timed.  Returns (seconds, max decoded error against FP64)."""
     from oracle import ckks_oracle as O
+
+    N, q = wl["N"], wl["q"]
+    square_last = wl.get("square_last", False)
+    layers, Ws = layers_for(wl["dims"], square_last)
+    o = O.Oracle(N, q, wl["p"], dnum=wl["dnum"], scale=2.0 ** 40)
+    rots = set()
+    for ly in layers:
+        if ly[0] == "dense":
+            rots |= set(O.Oracle.bsgs_rotations(*ly[1].shape))
+        elif ly[0] == "replicate":
+            rots.add(-ly[1])
+    o.keygen(sorted(rots), seed=3)
+    lvl, sc, plan = len(q), o.scale, []
+    for ly in layers:  # plaintexts at the level and scale each layer sees
+        if ly[0] == "dense":
+            plan.append(("dense", o.encode_diagonals(ly[1], o.dense_scale(lvl, sc))))
+            sc, lvl = o.scale, lvl - 1
+        elif ly[0] == "square":
+            plan.append(("square",))
+            sc, lvl = o.square_scale(lvl, sc), lvl - 1
+        else:
+            plan.append(ly)
+    t0 = bsgs_t(*Ws[0].shape)
+    xs, slots = inputs_for(N, wl["dims"], 1, t0)
+    h = o.encrypt(o.encode(slots[0]), 4)
+    start = time.perf_counter()
+    for step in plan:
+        if step[0] == "dense":
+            h = o.dense(h, step[1])[0]
+        elif step[0] == "square":
+            h = o.square(h)
+        else:
+            h = o.replicate(h, step[1])
+    secs = time.perf_counter() - start
+    y = o.decode(o.decrypt(h), wl["dims"][-1], sc)
+    return secs, float(np.max(np.abs(y - fp64_forward(Ws, xs[0, 0], square_last))))
+
+
+def cpu_oracle_sample(wl):
+    """The oracle's time per forward on the host cores: a whole forward for rings up to
+    N = 4096; otherwise one rotation, one plaintext product and one rescale at the top
+    level of the workload's ring, extrapolated by the forward's operation counts.
+    Returns (seconds per forward, description, cores, seconds spent)."""
+    from oracle import ckks_oracle as O
+
+    if wl["N"] <= 4096 and wl.get("net") != "paper":
+        t0 = time.perf_counter()
+        secs, err = oracle_forward_seconds(wl)
+        cores = os.cpu_count()
+        return secs, (f"one whole forward on the oracle ({cores} host threads), N={wl['N']}; decoded error "
+                      f"{err:.1e} against FP64"), cores, time.perf_counter() - t0
 
     N, q, p, dnum = wl["N"], wl["q"], wl["p"], wl["dnum"]
     o = O.Oracle(N, q, p, dnum=dnum, scale=wl.get("scale", 2.0 ** 40))
@@ -537,7 +588,7 @@ def main():
 
     N, B = wl["N"], wl["batch"]
     scale = wl.get("scale", 2.0 ** 40)
-    square_last = args.workload == "single4096"
+    square_last = wl.get("square_last", False)
     if wl.get("net") == "paper":
         layers, pw = paper_layers_for(wl["dims"][0])
         t0 = bsgs_t(wl["dims"][0], wl["dims"][0])

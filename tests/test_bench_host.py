@@ -46,3 +46,10 @@ def test_operation_plan_follows_the_papers_counts():
     assert [p[3] for p in plan] == [7, 6, 5, 5, 4, 3, 2]
     plan = bench.op_plan(bench.WORKLOADS["batched"])
     assert sum(p[1] for p in plan if p[1] >= 1) >= 1024 + 256 + 256
+
+
+def test_cpu_baseline_runs_a_whole_oracle_forward_on_small_rings():
+    wl = dict(bench.WORKLOADS["single4096"])
+    wl.update(N=256, dims=[16, 8])  # the same network shape (dense, then x^2), small enough for a unit test
+    secs, err = bench.oracle_forward_seconds(wl)
+    assert secs > 0 and err < 1e-4
