@@ -221,3 +221,22 @@ def test_paper_predictions_per_ciphertext_windows():
         assert np.max(np.abs(y[2 * t * k:2 * t * k + m2] - netref.paper_net_fp64(xs[k], w, W1, W2, a))) < 1e-4
     # windows = 1 reproduces the single-window encoding
     assert np.array_equal(o.encode_diagonals(W1, 2.0 ** 30), o.encode_diagonals(W1, 2.0 ** 30, windows=1))
+
+
+def test_degenerate_cases():
+    """Average pooling of size 1 is the identity at one level less (the constant q_last
+    at scale q_last, then an exact division); the zero polynomial gives zero; a 1-tap
+    convolution is a plaintext product."""
+    o = ctx()
+    rng = np.random.default_rng(20)
+    z = rng.uniform(-1, 1, 64)
+    ct = enc(o, z, 21)
+    out, cnt = o.avgpool(ct, 1)
+    assert cnt == [0, 1, 0]
+    assert np.array_equal(out, o.drop_level(ct, 3))
+    zero, sc = o.poly3(ct, o.scale, [0.0, 0.0, 0.0, 0.0])
+    assert np.max(np.abs(dec(o, zero, sc))) < 1e-6
+    pts = o.encode_conv([0.5], 10, 16, o.dense_scale(4))
+    c1, cnt = o.conv1d(ct, pts)
+    assert cnt == [0, 1, 0]
+    assert np.array_equal(c1, o.rescale(o.mul_plain(ct, pts[0])))
