@@ -262,12 +262,16 @@ int ctl_deserialize(const uint8_t* in, size_t size, uint32_t N, const uint64_t* 
  *   ciphertext products are the costliest operation, Sec. 5.1).  Scale becomes
  *   scale^2 / q_last.
  * ctl_eval_dense: y = W x for W (m x n, row-major FP64) by Eq. (bsgs): t = next power of
- *   two >= max(m, n) (zero padding), t1 = min(t, 2^ceil(log2(4t)/2)), t2 = t/t1; t1+t2-2
- *   rotations, t plaintext products, depth 1.  The input must hold [x, x] in slots
+ *   two >= max(m, n) (zero padding), t2 = t/t1; t1+t2-2 rotations, t plaintext products,
+ *   depth 1.  The split t1 depends on the dense mode (ctl_set_dense_mode):
+ *     CTL_DENSE_COMPOSED (default): t1 = 2^ceil(log2(t)/2);
+ *     CTL_DENSE_LAZY_MODDOWN:       t1 = min(t, 2^ceil(log2(4t)/2)).
+ *   Either way the layer needs the Galois keys of 1..t1-1 and k*t1 (k = 1..t2-1) for
+ *   that mode's t1 (ctl_model_rotations lists them).  The input must hold [x, x] in slots
  *   [0, 2t); the output holds y in slots [0, m) and zeros elsewhere.  The diagonals are
  *   encoded at scale q_last * Delta / scale_in, so the output carries Delta again.
- *   bias (nullable, m values) is added before the rescale.  Needs the Galois keys of
- *   1..t1-1 and k*t1 (k = 1..t2-1).  Errors: CTL_EINVAL (2t > N/2), CTL_EKEY, CTL_ELEVEL.
+ *   bias (nullable, m values) is added before the rescale.
+ *   Errors: CTL_EINVAL (2t > N/2), CTL_EKEY, CTL_ELEVEL.
  * ctl_eval_dense_coeffs: the same with the t diagonal plaintexts given as integer
  *   coefficients pts[t][N] (and bias as coefficients, nullable); the scale bookkeeping
  *   uses pt_scale.  Lets a caller inject exactly encoded plaintexts.

@@ -64,6 +64,28 @@ def test_sampling_distributions():
     assert abs(e.mean()) < 0.1 and abs(e.var() - 10.5) < 0.6  # centred binomial k=21: var 21/2
 
 
+def test_centred_binomial_is_k21_exactly():
+    # The error distribution is a difference of two sums of 21 fair bits: P(e = v) =
+    # C(42, 21 + v) / 2^42, variance 21/2.  At 2^18 samples the variance is known to about
+    # +-0.03 (one standard deviation), so k = 20 (variance 10) or k = 22 (11) fails the
+    # +-0.15 window; the chi-square statistic against the exact k = 21 law (43 cells, tail
+    # cells merged) rejects the neighbouring k as well.
+    from math import comb
+    e = np.concatenate([O.sample(11, 900 + s, 2, 0, 1 << 16) for s in range(4)])
+    n = len(e)
+    assert abs(e.var() - 10.5) < 0.15
+    pmf = {v: comb(42, 21 + v) / 2.0 ** 42 for v in range(-21, 22)}
+    cells = [v for v in range(-21, 22) if pmf[v] * n >= 5]
+    lo, hi = min(cells), max(cells)
+    obs = [np.sum(e <= lo)] + [np.sum(e == v) for v in range(lo + 1, hi)] + [np.sum(e >= hi)]
+    exp = [sum(pmf[v] for v in range(-21, lo + 1)) * n] + [pmf[v] * n for v in range(lo + 1, hi)] + \
+          [sum(pmf[v] for v in range(hi, 22)) * n]
+    chi2 = sum((o - x) ** 2 / x for o, x in zip(obs, exp))
+    # dof = cells - 1 (about 25); 80 is far in the tail of that chi-square law, while k = 20
+    # or k = 22 gives a statistic in the thousands at this sample size.
+    assert chi2 < 80, chi2
+
+
 # ----------------------------------------------------------------------------- primes
 @pytest.mark.parametrize("N,bits", [(4096, [50, 40, 40, 60]), (8192, [60, 40, 40, 40, 60]),
                                     (16384, [45] * 8 + [60, 60])])
@@ -282,6 +304,64 @@ def test_modup_invariants(dnum):
             assert (Y - a) % Qd == 0
             uu = (Y - a) // Qd
             assert 0 <= uu < len(dig) and uu == int(u[k])
+
+
+@pytest.mark.parametrize("dnum", [3, 2, 1])
+@pytest.mark.parametrize("pbits", [[60], [60, 58]])
+def test_modup_is_the_fast_conversion_elementwise(dnum, pbits):
+    # The fixed ModUp variant (fast base conversion, no correction): for digit d with primes
+    # q_j, q_hat_j = Q_d / q_j, every other prime p of Q_l u P receives
+    #   y mod p,  y = sum_j [a_j * q_hat_j^-1]_{q_j} * q_hat_j   (a Python integer),
+    # and the digit's own primes receive a_j unchanged.  An exact conversion (y = a) or
+    # any other correction differs from this on most coefficients.
+    o = O.Oracle(32, [50, 40, 40], pbits, dnum=dnum)
+    rng = np.random.default_rng(50 + dnum + 10 * len(pbits))
+    lvl = 3
+    poly = np.stack([rng.integers(0, q, o.N, dtype=np.uint64) for q in o.moduli[:lvl]])
+    basis = o.moduli[:lvl] + o.moduli[o.L:]
+    for d in range((lvl + o.alpha - 1) // o.alpha):
+        ext, _ = o.modup(poly, d)
+        dig = list(range(d * o.alpha, min((d + 1) * o.alpha, lvl)))
+        qs = [o.moduli[j] for j in dig]
+        Qd = 1
+        for q in qs:
+            Qd *= q
+        hats = [Qd // q for q in qs]
+        invs = [pow(h % q, -1, q) for h, q in zip(hats, qs)]
+        n_differ_from_exact = 0
+        for k in range(o.N):
+            y = sum(((int(poly[j, k]) * iv) % q) * h for j, q, h, iv in zip(dig, qs, hats, invs))
+            a = y % Qd  # the digit value itself (CRT), what an exact conversion would carry
+            for i, p in enumerate(basis):
+                want = int(poly[i, k]) if i in dig else y % p
+                assert int(ext[i, k]) == want, (d, i, k)
+            n_differ_from_exact += y != a
+        if len(dig) > 1:
+            assert n_differ_from_exact > 0  # the inputs exercise the u > 0 case
+
+
+@pytest.mark.parametrize("lvl", [3, 2])
+@pytest.mark.parametrize("pbits", [[60], [60, 58]])
+def test_moddown_is_the_fast_conversion_elementwise(pbits, lvl):
+    # The fixed ModDown variant (no rounding offset): with P = prod p_j, P_hat_j = P / p_j,
+    #   out_i = (c_i - sum_j [c_{p_j} * P_hat_j^-1]_{p_j} * P_hat_j) * P^-1  mod q_i.
+    # Adding floor(P/2) first (the rounding variant) changes about half of the outputs.
+    o = O.Oracle(32, [50, 40, 40], pbits)
+    rng = np.random.default_rng(60 + lvl + 10 * len(pbits))
+    ps = o.moduli[o.L:]
+    basis = o.moduli[:lvl] + ps
+    ext = np.stack([rng.integers(0, q, o.N, dtype=np.uint64) for q in basis])
+    out = o.moddown(ext)
+    P = 1
+    for p in ps:
+        P *= p
+    hats = [P // p for p in ps]
+    invs = [pow(h % p, -1, p) for h, p in zip(hats, ps)]
+    for k in range(o.N):
+        yP = sum(((int(ext[lvl + j, k]) * iv) % p) * h for j, (p, h, iv) in enumerate(zip(ps, hats, invs)))
+        for i in range(lvl):
+            q = o.moduli[i]
+            assert int(out[i, k]) == ((int(ext[i, k]) - yP) * pow(P % q, -1, q)) % q, (i, k)
 
 
 @pytest.mark.parametrize("pbits", [[60], [60, 58]])
