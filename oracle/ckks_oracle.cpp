@@ -931,6 +931,74 @@ int orc_dense_lazy(const orc_ctx* c, const orc_keys* k, const u64* ct, uint32_t 
   return orc_rescale(c, acc.data(), lvl, out);
 }
 
+// Rectangular diagonal form of a dense layer.  Sec. 3.1 ("Dense-Layer") pads a non-square
+// matrix with zeros to a square one; this reading pads only the short side.  For W (m x n,
+// row-major) with tm = pow2 >= m below tn = pow2 >= n, the tm diagonals of length tn are
+//   rd_i[r] = W[r mod tm][(r + i) mod tn]   (zero outside W),  r < tn,  i < tm,
+// so that z = sum_i rd_i o rot_i(x), on the [x, x] input layout over 2 tn slots, holds in
+// slot r < tn the partial sum over the columns (r + i) mod tn of row r mod tm, and
+// y[j] = sum_{k < tn/tm} z[j + k tm].  They are placed as in Eq. (bsgs):
+// rd'_i = rot_{-floor(i/t1) t1}(rd_i) with rd_i in slots [0, tn) and t1 = orc_bsgs_t1(tm).
+int orc_encode_diagonals_rect(const orc_ctx* c, const double* W, uint32_t m, uint32_t n, double scale, i64* pts) {
+  const uint32_t tm = orc_bsgs_t(m, 1), tn = orc_bsgs_t(n, 1), ns = c->N / 2;
+  if (tm >= tn || 2 * tn > ns) return -1;
+  const uint32_t t1 = orc_bsgs_t1(tm);
+  std::vector<double> v(ns);
+  for (uint32_t i = 0; i < tm; i++) {
+    std::fill(v.begin(), v.end(), 0.0);
+    const uint32_t sh = (i / t1) * t1;
+    for (uint32_t r = 0; r < tn; r++) {
+      const uint32_t row = r % tm, col = (r + i) % tn;
+      v[r + sh] = (row < m && col < n) ? W[(size_t)row * n + col] : 0.0;
+    }
+    int rc = orc_encode(c, v.data(), ns, scale, pts + (size_t)i * c->N);
+    if (rc) return rc;
+  }
+  return 0;
+}
+
+// Rectangular dense layer on the [x, x] layout over 2 tn slots, with the tm plaintexts of
+// orc_encode_diagonals_rect:
+//   z' = rescale( sum_k rot_{k t1}( sum_j rd'_{k t1 + j} o rot_j(ct) ) [+ bias] )
+// (the composed form of orc_dense over tm diagonals), then for fold >= 1 the sum over the
+// tn/tm blocks of z':
+//   S = z';  S = S + rot_s(S)  for s = tn/2, tn/4, ..., tm,
+// which leaves y[j] in slot j < tm, and for fold = 2 also  S = S + rot_{-tm}(z'),  which
+// puts y[j] in slot tm + j as well: the [y, y] layout a following layer of width tm
+// reads (the replicate of Sec. 3.1 "Multiple Predictions" taken into the fold).  Other
+// slots hold partial sums.  counters: rotations t1+t2-2 + log2(tn/tm) (+1), products tm,
+// additions tm-1 + log2(tn/tm) (+1).
+int orc_dense_rect(const orc_ctx* c, const orc_keys* k, const u64* ct, uint32_t lvl, const i64* pts, uint32_t tm,
+                   uint32_t tn, const i64* bias, int fold, u64* out, u64* counters) {
+  if (tm == 0 || tm >= tn || (tm & (tm - 1)) || (tn & (tn - 1)) || fold < 0 || fold > 2 || lvl < 2) return -1;
+  const uint32_t lo = lvl - 1;
+  const size_t csz = (size_t)2 * lo * c->N;
+  std::vector<u64> z(csz), r(csz);
+  u64 cnt[3] = {0, 0, 0};
+  int rc = orc_dense(c, k, ct, lvl, pts, tm, bias, z.data(), cnt);
+  if (rc) return rc;
+  std::vector<u64> S = z;
+  if (fold >= 1) {
+    for (uint32_t s = tn / 2; s >= tm; s /= 2) {
+      rc = orc_rotate(c, k, S.data(), lo, (int64_t)s, r.data());
+      if (rc) return rc;
+      orc_add(c, S.data(), r.data(), lo, S.data());
+      cnt[0]++;
+      cnt[2]++;
+    }
+    if (fold == 2) {
+      rc = orc_rotate(c, k, z.data(), lo, -(int64_t)tm, r.data());
+      if (rc) return rc;
+      orc_add(c, S.data(), r.data(), lo, S.data());
+      cnt[0]++;
+      cnt[2]++;
+    }
+  }
+  std::copy(S.begin(), S.end(), out);
+  if (counters) { counters[0] = cnt[0]; counters[1] = cnt[1]; counters[2] = cnt[2]; }
+  return 0;
+}
+
 // Replicate: y + rot_{-t}(y), which turns a vector held in slots [0, t) into [y, y].
 int orc_replicate(const orc_ctx* c, const orc_keys* k, const u64* ct, uint32_t lvl, uint32_t t, u64* out) {
   std::vector<u64> r((size_t)2 * lvl * c->N);

@@ -240,3 +240,67 @@ def test_degenerate_cases():
     c1, cnt = o.conv1d(ct, pts)
     assert cnt == [0, 1, 0]
     assert np.array_equal(c1, o.rescale(o.mul_plain(ct, pts[0])))
+
+
+def rect_model(W, x, tn, ns, fold):
+    """FP64 slot vector of the rectangular dense form (its definition written out): the
+    partial sums z[r] = sum_i rd_i[r] x~[r + i] over the tm diagonals of length tn, then the
+    fold S = z; S += rot_s(S) for s = tn/2 .. tm; (fold = 2) S += rot_{-tm}(z)."""
+    m, n = W.shape
+    tm = 1
+    while tm < m:
+        tm <<= 1
+    xt = np.zeros(ns)
+    xt[:n] = x
+    xt[tn:tn + n] = x
+    z = np.zeros(ns)
+    for r in range(tn):
+        for i in range(tm):
+            row, col = r % tm, (r + i) % tn
+            if row < m and col < n:
+                z[r] += W[row, col] * xt[r + i]
+    S = z.copy()
+    if fold >= 1:
+        s = tn // 2
+        while s >= tm:
+            S = S + np.roll(S, -s)  # rot_s moves slot r + s to slot r
+            s //= 2
+    if fold == 2:
+        S = S + np.roll(z, tm)
+    return z, S
+
+
+@pytest.mark.parametrize("m,n", [(4, 16), (3, 12), (8, 32), (2, 64)])
+@pytest.mark.parametrize("fold", [0, 1, 2])
+def test_dense_rect_matches_its_fp64_definition(m, n, fold):
+    # Rectangular diagonals (tm < tn): every slot of the decoded output against the FP64
+    # partial sums and fold of the definition; after the fold, W x sits in slots [0, m)
+    # (and [tm, tm + m) with fold = 2), as the dense layer of Sec. 3.1 computes.
+    rots = O.Oracle.rect_rotations(m, n, fold)
+    o = ctx(N=256, rots=rots)
+    rng = np.random.default_rng(m * 100 + n)
+    W = rng.normal(0, 1 / np.sqrt(n), (m, n))
+    x = rng.uniform(-1, 1, n)
+    tm, tn = O.Oracle.bsgs_t(m, 1), O.Oracle.bsgs_t(n, 1)
+    ct = enc(o, netref.replicated_slots(x, tn, o.N // 2), 12)
+    pts = o.encode_diagonals_rect(W, o.dense_scale(4))
+    assert pts.shape == (tm, o.N)
+    out, cnt = o.dense_rect(ct, pts, tn, fold=fold)
+    t1 = O.Oracle.bsgs_t1(tm)
+    folds = (tn // tm).bit_length() - 1 if fold >= 1 else 0
+    extra = folds + (1 if fold == 2 else 0)
+    assert cnt == [(t1 - 1) + (tm // t1 - 1) + extra, tm, tm - 1 + extra]
+    assert len(set(rots)) == (t1 - 1) + (tm // t1 - 1) + extra
+    y = dec(o, out, o.scale)
+    _, S = rect_model(W, x, tn, o.N // 2, fold)
+    assert np.max(np.abs(y - S)) < 1e-6
+    if fold >= 1:
+        assert np.max(np.abs(y[:m] - W @ x)) < 1e-6
+    if fold == 2:
+        assert np.max(np.abs(y[tm:tm + m] - W @ x)) < 1e-6
+
+
+def test_dense_rect_rejects_square_shapes():
+    o = ctx(N=256, rots=[1])
+    with pytest.raises(RuntimeError):
+        o.encode_diagonals_rect(np.ones((16, 16)), o.dense_scale(4))
