@@ -34,16 +34,26 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 SM_COUNT = 152
-IMAD_PER_CLK_SM = 64          # 32-bit integer multiply-add lanes per SM per clock
-SHOUP_IMAD = 17.4             # IMAD issue slots of one 64-bit Shoup modmul (microbenchmark)
+IMAD_PER_CLK_SM = 64          # 32-bit integer multiply-add lanes per SM per clock (issue slots)
 MAX_SM_MHZ = 2070.0
-# one split-half multiply-accumulate (four 32x32->64 IMAD.WIDE, each two IMAD issue slots)
-SPLIT_MAC_IMAD = 8.0
 MAC_CLASSES = ("key_ip", "bsgs_inner")  # kernel classes whose work unit is a split-half MAC
-# DRAM bytes (read + write) per limb item of the fused NTT kernels, from one ncu capture of
-# the same kernels at batch 16 (profiles/ncu_full_modup_moddown_bsgs_keyip_n16384_b16.md);
-# traffic grows with the items, so a launch's traffic is this times its items.
-TRAFFIC_PER_ITEM = {"moddown_ntt": 2909.2e6 / 7936, "modup_ntt": 4160.1e6 / 19840}
+HBM_FALLBACK_GBS = 6800.0     # copy bandwidth of an earlier GB300 measurement, if none is given
+# DRAM traffic over algorithmic bytes per kernel class: the dram__bytes_read.sum +
+# dram__bytes_write.sum of every launch of one forward at batch 16 (ncu, one pass), over
+# the algorithmic bytes the library counts for the same launches.  Traffic grows in
+# proportion to the batch, so a full-size launch's traffic is this ratio times its
+# algorithmic bytes.  A class missing here was not captured for the current kernels.
+TRAFFIC_RATIO = {"modup_ntt": 1.070, "moddown_ntt": 1.061, "key_ip": 0.956, "bsgs_inner": 0.979,
+                 "ntt_inv": 0.872, "rescale": 0.581}
+
+
+def hbm_peak_gbs():
+    """The measured copy bandwidth of the GB300s, else the fallback (says which)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return HBM_FALLBACK_GBS, "fallback"
 
 WORKLOADS = {
     "batched": dict(N=16384, q=[45] * 8, p=[60, 60], dnum=4, batch=256, dims=[1024, 256, 256, 64],
@@ -226,118 +236,150 @@ def op_plan(wl):
     return plan
 
 
-def oracle_forward_seconds(wl):
-    """One whole forward of a dense / square / replicate network on the oracle (rings of
-    N <= 4096, where it takes seconds); key generation and the diagonals' encoding are
-    set-up and not timed.  Returns (seconds, max decoded error against FP64)."""
-    from oracle import ckks_oracle as O
+class OracleSample:
+    """A bounded sample of the workload on the oracle (the plain C++ CKKS implementation),
+    timed on the host cores.  set-up (keys, plaintexts) is not timed; step() runs one sample
+    and returns its seconds; `fraction` is the share of one encrypted forward a sample does.
 
-    N, q = wl["N"], wl["q"]
-    square_last = wl.get("square_last", False)
-    layers, Ws = layers_for(wl["dims"], square_last)
-    o = O.Oracle(N, q, wl["p"], dnum=wl["dnum"], scale=2.0 ** 40)
-    rots = set()
-    for ly in layers:
-        if ly[0] == "dense":
-            rots |= set(O.Oracle.bsgs_rotations(*ly[1].shape))
-        elif ly[0] == "replicate":
-            rots.add(-ly[1])
-    o.keygen(sorted(rots), seed=3)
-    lvl, sc, plan = len(q), o.scale, []
-    for ly in layers:  # plaintexts at the level and scale each layer sees
-        if ly[0] == "dense":
-            plan.append(("dense", o.encode_diagonals(ly[1], o.dense_scale(lvl, sc))))
-            sc, lvl = o.scale, lvl - 1
-        elif ly[0] == "square":
-            plan.append(("square",))
-            sc, lvl = o.square_scale(lvl, sc), lvl - 1
+    Rings of N <= 4096 (the dense/square networks): a sample is one whole forward
+    (fraction 1), with its decoded error against FP64.  Larger rings: a sample is one
+    rotation, one plaintext product and one rescale at the workload's top level; the
+    forward is that many samples as its operation counts say (key switches weighted by
+    their digits x limbs relative to the top level, products and rescales by their limbs),
+    with the weights taken from the timed sample itself."""
+
+    def __init__(self, wl, whole=None):
+        from oracle import ckks_oracle as O
+
+        self.wl = wl
+        self.cores = os.cpu_count()
+        N, q = wl["N"], wl["q"]
+        self.whole = (N <= 4096 and wl.get("net") != "paper") if whole is None else whole
+        self.o = O.Oracle(N, q, wl["p"], dnum=wl["dnum"], scale=wl.get("scale", 2.0 ** 40))
+        o = self.o
+        if self.whole:
+            square_last = wl.get("square_last", False)
+            layers, self.Ws = layers_for(wl["dims"], square_last)
+            rots = set()
+            for ly in layers:
+                if ly[0] == "dense":
+                    rots |= set(O.Oracle.bsgs_rotations(*ly[1].shape))
+                elif ly[0] == "replicate":
+                    rots.add(-ly[1])
+            o.keygen(sorted(rots), seed=3)
+            lvl, sc, self.plan = len(q), o.scale, []
+            for ly in layers:  # plaintexts at the level and scale each layer sees
+                if ly[0] == "dense":
+                    self.plan.append(("dense", o.encode_diagonals(ly[1], o.dense_scale(lvl, sc))))
+                    sc, lvl = o.scale, lvl - 1
+                elif ly[0] == "square":
+                    self.plan.append(("square",))
+                    sc, lvl = o.square_scale(lvl, sc), lvl - 1
+                else:
+                    self.plan.append(ly)
+            self.out_scale = sc
+            t0 = bsgs_t(*self.Ws[0].shape)
+            self.xs, slots = inputs_for(N, wl["dims"], 1, t0)
+            self.ct = o.encrypt(o.encode(slots[0]), 4)
+            self.fraction = 1.0
+            self.err = None
         else:
-            plan.append(ly)
-    t0 = bsgs_t(*Ws[0].shape)
-    xs, slots = inputs_for(N, wl["dims"], 1, t0)
-    h = o.encrypt(o.encode(slots[0]), 4)
-    start = time.perf_counter()
-    for step in plan:
-        if step[0] == "dense":
-            h = o.dense(h, step[1])[0]
-        elif step[0] == "square":
-            h = o.square(h)
-        else:
-            h = o.replicate(h, step[1])
-    secs = time.perf_counter() - start
-    y = o.decode(o.decrypt(h), wl["dims"][-1], sc)
-    return secs, float(np.max(np.abs(y - fp64_forward(Ws, xs[0, 0], square_last))))
+            o.keygen([1], seed=3)
+            rng = np.random.default_rng(9)
+            L = len(q)
+            self.ct = np.stack([np.stack([rng.integers(0, m, N, dtype=np.uint64) for m in o.moduli[:L]])
+                                for _ in range(2)])
+            self.pt = rng.integers(-2 ** 20, 2 ** 20, N, dtype=np.int64)
+            self.fraction = None
+            self.parts = None
 
-
-def cpu_oracle_sample(wl):
-    """The oracle's time per forward on the host cores: a whole forward for rings up to
-    N = 4096; otherwise one rotation, one plaintext product and one rescale at the top
-    level of the workload's ring, extrapolated by the forward's operation counts.
-    Returns (seconds per forward, description, cores, seconds spent)."""
-    from oracle import ckks_oracle as O
-
-    if wl["N"] <= 4096 and wl.get("net") != "paper":
+    def step(self):
+        o = self.o
         t0 = time.perf_counter()
-        secs, err = oracle_forward_seconds(wl)
-        cores = os.cpu_count()
-        return secs, (f"one whole forward on the oracle ({cores} host threads), N={wl['N']}; decoded error "
-                      f"{err:.1e} against FP64"), cores, time.perf_counter() - t0
+        if self.whole:
+            h = self.ct
+            for st in self.plan:
+                if st[0] == "dense":
+                    h = o.dense(h, st[1])[0]
+                elif st[0] == "square":
+                    h = o.square(h)
+                else:
+                    h = o.replicate(h, st[1])
+            secs = time.perf_counter() - t0
+            if self.err is None:
+                sq = self.wl.get("square_last", False)
+                y = o.decode(o.decrypt(h), self.wl["dims"][-1], self.out_scale)
+                self.err = float(np.max(np.abs(y - fp64_forward(self.Ws, self.xs[0, 0], sq))))
+            return secs
+        o.rotate(self.ct, 1)
+        t1 = time.perf_counter()
+        o.mul_plain(self.ct, self.pt)
+        t2 = time.perf_counter()
+        o.rescale(self.ct)
+        t3 = time.perf_counter()
+        self.parts = (t1 - t0, t2 - t1, t3 - t2)
+        self.fraction = (t3 - t0) / self.forward_seconds(*self.parts)
+        return t3 - t0
 
-    N, q, p, dnum = wl["N"], wl["q"], wl["p"], wl["dnum"]
-    o = O.Oracle(N, q, p, dnum=dnum, scale=wl.get("scale", 2.0 ** 40))
-    t0 = time.perf_counter()
-    o.keygen([1], seed=3)
-    t_keygen = time.perf_counter() - t0
-    rng = np.random.default_rng(9)
-    L = len(q)
-    ct = np.stack([np.stack([rng.integers(0, m, N, dtype=np.uint64) for m in o.moduli[:L]]) for _ in range(2)])
-    t0 = time.perf_counter()
-    o.rotate(ct, 1)
-    t_rot = time.perf_counter() - t0
-    pt = rng.integers(-2 ** 20, 2 ** 20, N, dtype=np.int64)
-    t0 = time.perf_counter()
-    o.mul_plain(ct, pt)
-    t_pt = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    o.rescale(ct)
-    t_rs = time.perf_counter() - t0
-    # operation counts of the forward, each scaled by its level relative to the top
-    K = len(p)
-    alpha = (L + dnum - 1) // dnum
+    def forward_seconds(self, t_rot, t_pt, t_rs):
+        """One forward from the operation counts, each operation at its level."""
+        wl = self.wl
+        L, K = len(wl["q"]), len(wl["p"])
+        alpha = (L + wl["dnum"] - 1) // wl["dnum"]
 
-    def ks_scale(l):
-        nd = (l + alpha - 1) // alpha
-        ndL = (L + alpha - 1) // alpha
-        return (nd * (l + K)) / (ndL * (L + K))
+        def ks_scale(lv):
+            return (((lv + alpha - 1) // alpha) * (lv + K)) / (((L + alpha - 1) // alpha) * (L + K))
 
-    est = sum(ks * t_rot * ks_scale(lv) + npt * t_pt * lv / L + nrs * t_rs * lv / L for ks, npt, nrs, lv in op_plan(wl))
-    cores = os.cpu_count()
-    desc = (f"oracle on {cores} host threads: 1 rotation ({t_rot:.2f} s), 1 plaintext product ({t_pt:.2f} s), "
-            f"1 rescale ({t_rs:.2f} s) at N={N}, level {L}, plus one Galois key ({t_keygen:.2f} s); "
-            f"forward extrapolated by operation counts and limb counts")
-    return est, desc, cores, t_rot + t_pt + t_rs + t_keygen
+        return sum(ks * t_rot * ks_scale(lv) + npt * t_pt * lv / L + nrs * t_rs * lv / L
+                   for ks, npt, nrs, lv in op_plan(wl))
+
+    def describe(self):
+        if self.whole:
+            return (f"one whole forward per step on the oracle ({self.cores} host threads), N={self.wl['N']}; "
+                    f"decoded error {self.err:.1e} against FP64")
+        t_rot, t_pt, t_rs = self.parts
+        return (f"oracle on {self.cores} host threads, per step: 1 rotation ({t_rot:.2f} s), 1 plaintext product "
+                f"({t_pt:.2f} s) and 1 rescale ({t_rs:.3f} s) at N={self.wl['N']}, level {len(self.wl['q'])}; "
+                f"a step is {self.fraction:.2e} of a forward by the forward's operation and limb counts "
+                f"(forwards/s extrapolated from the timed steps)")
+
+
+def cpu_oracle_sample(wl, steps=1):
+    """The oracle's forwards/s on the host cores from `steps` timed samples (see
+    OracleSample); returns (forwards/s, description, cores, per-step seconds)."""
+    smp = OracleSample(wl)
+    secs = [smp.step() for _ in range(steps)]
+    t = statistics.median(secs)
+    return smp.fraction / t, smp.describe(), smp.cores, secs
+
+
+def shared_config(wl, world, **extra):
+    """The `config` object both arms print for the same workload."""
+    cfg = {"workload": wl["desc"], "batch_per_gpu": wl["batch"], "N": wl["N"],
+           "parallelism": f"replicas x{world}"}
+    cfg.update(extra)
+    return cfg
 
 
 def run_reference(args, wl, rank, world):
+    """The oracle as the reference arm: W untimed and K timed steps, each one bounded
+    sample of the workload (OracleSample) on rank 0's host cores; other ranks do no work."""
     if rank != 0:
         return
-    times = []
-    desc, cores = "", os.cpu_count()
-    for s in range(args.warmup + args.steps):
-        est, desc, cores, spent = cpu_oracle_sample(wl)
-        if s >= args.warmup:
-            times.append(est)
-        if spent * (args.warmup + args.steps) > 240:  # keep the whole run within minutes
-            break
-    est = statistics.median(times) if times else est
-    value = wl["batch"] / (est * wl["batch"])
+    smp = OracleSample(wl)
+    for _ in range(args.warmup):
+        smp.step()
+    t_start = time.perf_counter()
+    secs = [smp.step() for _ in range(args.steps)]
+    total = time.perf_counter() - t_start
+    value = smp.fraction * len(secs) / total
     line = {"impl": "reference", "metric": "encrypted forwards/sec (batched)", "value": value,
-            "unit": "forwards/s", "n_gpus": args.gpus, "steps": len(times), "warmup": args.warmup,
-            "ms_per_step": est * 1e3 * wl["batch"], "higher_is_better": True, "scaling": "weak",
+            "unit": "forwards/s", "n_gpus": args.gpus, "steps": len(secs), "warmup": args.warmup,
+            "ms_per_step": total * 1e3 / len(secs), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": wl["desc"], "batch": wl["batch"]},
-            "cpu_baseline": {"value": value, "unit": "forwards/s", "cores": cores, "kind": "oracle",
-                             "sample": desc},
+            "config": shared_config(wl, world),
+            "cpu_baseline": {"value": value, "unit": "forwards/s", "cores": smp.cores, "kind": "oracle",
+                             "sample": smp.describe()},
             "e2e": {"value": value, "unit": "forwards/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -496,6 +538,55 @@ def run_uneven(args, ctl):
             "per_ct_fwd_s": len(queries) / single, "speedup": single / grouped, "server_batches": st["batches"]}
 
 
+def single_query_point(ctl, torch, name, steps):
+    """One query per forward through the replayed CUDA graph: forwards/s and p50/p99 of the
+    per-forward device time (CUDA events on the library's stream), inputs resident."""
+    wl = WORKLOADS[name]
+    layers, Ws = layers_for(wl["dims"], wl.get("square_last", False))
+    t0 = bsgs_t(Ws[0].shape[0], Ws[0].shape[1])
+    stream = torch.cuda.Stream()
+    ctx = ctl.Context(wl["N"], wl["q"], wl["p"], dnum=wl["dnum"], scale=2.0 ** 40)
+    ctx.set_stream(stream.cuda_stream)
+    model = ctl.Model(ctx, layers)
+    keys = ctx.keygen(model.rotations(), seed=3)
+    xs, slots = inputs_for(wl["N"], wl["dims"], 1, t0)
+    ct = ctx.encrypt(keys, slots[0], 4)
+    o = model.forward(keys, ct, graph=True)
+    y = ctx.decrypt(keys, o, wl["dims"][-1])
+    err = float(np.max(np.abs(y - fp64_forward(Ws, xs[0, 0], wl.get("square_last", False)))))
+    o.close()
+    for _ in range(10):
+        model.forward(keys, ct, graph=True).close()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    ev[0].record(stream)
+    for i in range(steps):
+        model.forward(keys, ct, graph=True).close()
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    ms = sorted(ev[i].elapsed_time(ev[i + 1]) for i in range(steps))
+    total = ev[0].elapsed_time(ev[-1])
+    res = {"desc": wl["desc"].replace("256 ciphertexts", "1 ciphertext"), "value": steps / (total / 1e3),
+           "unit": "forwards/s", "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+           "steps": steps, "cuda_graph": True, "max_abs_err_vs_fp64": err}
+    ct.close()
+    model.close()
+    keys.close()
+    ctx.close()
+    return res
+
+
+def serving_point(ctl, rate, seconds, n_clients):
+    """One arrival rate of configuration 5 (see run_serving), fewer clients and seconds."""
+    ns = argparse.Namespace(mem_budget_gb=160.0, workers=4, max_batch=64, clients=n_clients, rates=[rate],
+                            seconds=seconds)
+    pt = run_serving(ns, ctl)[0]
+    pt.update({"clients": n_clients, "seconds": seconds, "unit": "forwards/s",
+               "desc": "Poisson arrivals, query shapes of configurations 1-3, per-client keys resident, "
+                       "continuous batching with memory admission; latency = submit to result on the host"})
+    return pt
+
+
 def max_over_ranks(x, dist):
     """The slowest rank's time: every rank runs its own replica on its own GPU (the
     queries are independent, so there is no data-path collective), and the job's time is
@@ -527,7 +618,9 @@ def main():
     ap.add_argument("--batch", type=int, default=0, help="override the batch size")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--graph", type=int, default=-1, help="1: replay a CUDA graph of the forward (default: single-query workloads)")
+    ap.add_argument("--graph", type=int, default=1, help="1 (default): replay a CUDA graph of the forward; 0: eager")
+    ap.add_argument("--class-steps", type=int, default=2,
+                    help="eager forwards timed per kernel class after the timed steps (roofline breakdown)")
     ap.add_argument("--rates", type=float, nargs="+", default=[50, 100, 200, 500, 1000, 2000])
     ap.add_argument("--seconds", type=float, default=5.0, help="serving: load duration per arrival rate")
     ap.add_argument("--clients", type=int, default=64)
@@ -538,6 +631,15 @@ def main():
     ap.add_argument("--ntt-shape", default="auto", choices=["auto", "r32", "r16"],
                     help="register NTT shape (default: the context's autotuned choice)")
     ap.add_argument("--bsgs-shape", default="", help="chunk,karatsuba for the BSGS kernel (default: library's)")
+    ap.add_argument("--profile-forward", action="store_true",
+                    help="run one eager forward inside cudaProfilerStart/Stop and print its per-class "
+                         "algorithmic work and bytes (for an ncu capture of exactly that forward)")
+    ap.add_argument("--no-others", action="store_true",
+                    help="skip the single-query and serving points measured beside the batched value")
+    ap.add_argument("--single-steps", type=int, default=300, help="timed single-query forwards per point")
+    ap.add_argument("--serve-rate", type=float, default=500.0, help="arrival rate of the serving point (req/s)")
+    ap.add_argument("--serve-seconds", type=float, default=4.0)
+    ap.add_argument("--serve-clients", type=int, default=16)
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the extra measurement of the lazy-ModDown dense form")
     args = ap.parse_args()
@@ -635,7 +737,25 @@ def main():
             max_err = max(max_err, float(np.max(np.abs(yi[2 * t0 * j:2 * t0 * j + m_out] - reference(xs[i, j])))))
     out.close()
 
-    use_graph = (args.graph == 1) or (args.graph == -1 and B == 1)
+    if args.profile_forward:
+        # one eager forward between cudaProfilerStart/Stop (for ncu --profile-from-start off),
+        # with the library's per-class algorithmic work and bytes of the same launches
+        model.forward(keys, batch).close()
+        torch.cuda.synchronize()
+        ctx.stats_reset()
+        ctx.stats_enable_timing(True)
+        torch.cuda.profiler.start()
+        model.forward(keys, batch).close()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        kern = {k: v for k, v in ctx.stats_kernels().items() if v["launches"]}
+        print(json.dumps({"profile_forward": wl["desc"], "batch": B, "launches": ctx.stats_launches(),
+                          "classes": kern}), flush=True)
+        return
+
+    # the forward replays one captured CUDA graph by default (all launches of the network,
+    # captured once per batch size); --graph 0 times eager launches instead
+    use_graph = args.graph != 0
 
     def step():
         o = model.forward(keys, batch, graph=use_graph)
@@ -645,9 +765,9 @@ def main():
         step()
     torch.cuda.synchronize()
 
-    # timed region: device-resident inputs
+    # timed region: device-resident inputs, no per-launch events
     ctx.stats_reset()
-    ctx.stats_enable_timing(True)
+    ctx.stats_enable_timing(False)
     sampler = ClockSampler(local)
     sampler.start()
     if dist:
@@ -665,21 +785,23 @@ def main():
     step_ms = [ev[s].elapsed_time(ev[s + 1]) for s in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
     launches = ctx.stats_launches()
-    kern = ctx.stats_kernels()
     ops = ctx.stats_ops()
-    timing_source = "CUDA events around every launch of the timed steps"
-    if use_graph:
-        # a replayed graph records no per-launch events: take the per-class times from
-        # the same number of eager forwards (the same kernels) right after the timed region
-        ctx.stats_reset()
-        for _ in range(args.steps):
-            o = model.forward(keys, batch)
-            o.close()
-        kern = ctx.stats_kernels()
-        timing_source = "CUDA events around every launch of eager forwards run after the graph-timed steps"
-    ctx.stats_enable_timing(False)
     total_ms = max_over_ranks(total_ms, dist)
     value = replica_throughput(world, B, args.steps, total_ms / 1e3)
+
+    # per-kernel-class device time in a separate pass: eager forwards of the same kernels
+    # with CUDA events around every launch on the library's stream (untimed for `value`)
+    ctx.stats_reset()
+    ctx.stats_enable_timing(True)
+    class_steps = max(1, min(args.steps, args.class_steps))
+    for _ in range(class_steps):
+        o = model.forward(keys, batch)
+        o.close()
+    kern = ctx.stats_kernels()
+    ctx.stats_enable_timing(False)
+    class_ms_per_step = sum(v["ms"] for v in kern.values()) / class_steps
+    timing_source = (f"CUDA events around every launch of {class_steps} eager forwards run after the timed "
+                     f"steps (the timed steps replay the graph without events)")
 
     # end to end through host buffers
     e2e = None
@@ -758,12 +880,12 @@ def main():
                 err_l = max(err_l, float(np.max(np.abs(yi[2 * t0 * j:2 * t0 * j + m_out] - reference(xs[i, j])))))
         o.close()
         for _ in range(2):
-            model_l.forward(keys_l, batch, graph=use_graph).close()
+            model_l.forward(keys_l, batch).close()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.steps):
-            model_l.forward(keys_l, batch, graph=use_graph).close()
+            model_l.forward(keys_l, batch).close()
         e1.record(stream)
         torch.cuda.synchronize()
         ms_l = e0.elapsed_time(e1)
@@ -776,51 +898,83 @@ def main():
         keys_l.close()
         ctx.set_dense_mode(ctx.DENSE_COMPOSED)
 
-    # roofline of the dominant kernel class (integer-multiply bound): NTT-type classes count
-    # Shoup modmuls (butterflies + conversions), key_ip and bsgs_inner count split-half MACs
-    peak_modmul = SM_COUNT * IMAD_PER_CLK_SM * MAX_SM_MHZ * 1e6 / SHOUP_IMAD
-    peak_mac = SM_COUNT * IMAD_PER_CLK_SM * MAX_SM_MHZ * 1e6 / SPLIT_MAC_IMAD
+    # rooflines per kernel class.  Work units: Shoup modmuls for the transform classes and
+    # split-half MACs for the key product and BSGS sums; each unit's peak is this GPU's rate
+    # measured now by the unit-rate microbenchmark (ctl_microbench_unit_rate) at the maximum
+    # SM clock; the HBM side takes the class's algorithmic bytes against the measured copy
+    # bandwidth.  A class's roofline time is max(bytes / HBM, work / unit peak) and its
+    # fraction that time over the measured one.
+    ub = {name: ctl.microbench_unit_rate(kind) for kind, name in
+          enumerate(("shoup_modmul", "harvey_butterfly", "shoup_three_half", "split_mac"))}
+    clk = MAX_SM_MHZ * 1e6
+    peak_modmul = SM_COUNT * clk * ub["shoup_modmul"]
+    peak_mac = SM_COUNT * clk * ub["split_mac"]
+    imad_slots = SM_COUNT * IMAD_PER_CLK_SM * clk
+    hbm_gbs, hbm_src = hbm_peak_gbs()
     classes = {k: v for k, v in kern.items() if v["launches"]}
-    dom = max(classes, key=lambda k: classes[k]["ms"])
-    d = classes[dom]
 
     def unit_peak(k):
         return ("Gmac/s", peak_mac) if k in MAC_CLASSES else ("Gmodmul/s", peak_modmul)
 
-    def rate(v):
-        return v["modmul"] / (v["ms"] / 1e3) if v["ms"] else 0.0
-
-    per_class = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
-                     "share": v["ms"] / max(sum(x["ms"] for x in classes.values()), 1e-9),
-                     "rate": rate(v) / 1e9, "unit": unit_peak(k)[0], "peak": unit_peak(k)[1] / 1e9,
-                     "frac_of_alu_peak": rate(v) / unit_peak(k)[1]}
-                 for k, v in classes.items()}
-    unit, peak = unit_peak(dom)
-    achieved = rate(d)
-    traffic = None
-    if dom in TRAFFIC_PER_ITEM and args.workload == "batched":
-        K, alpha = len(wl["p"]), -(-len(wl["q"]) // wl["dnum"])
-        per_item = 0.5 * N * 14 + (2 * K + 1) * N if dom == "moddown_ntt" else 0.5 * N * 14 + alpha * 2 * N
-        traffic = TRAFFIC_PER_ITEM[dom] * (d["modmul"] / max(d["launches"], 1)) / per_item
-    basis = (f"{SM_COUNT} SMs x {IMAD_PER_CLK_SM} IMAD/clk x {MAX_SM_MHZ:.0f} MHz / " +
-             (f"{SPLIT_MAC_IMAD:.0f} IMAD slots per split-half MAC" if dom in MAC_CLASSES
-              else f"{SHOUP_IMAD} IMAD per Shoup modmul (measured)"))
-    # the unit rates behind the peak, measured on this GPU now (ctl_microbench_unit_rate)
-    ub = {name: ctl.microbench_unit_rate(kind) for kind, name in
-          enumerate(("shoup_modmul", "harvey_butterfly", "shoup_three_half", "split_mac"))}
-    ub["imad_slots_per_shoup_modmul"] = IMAD_PER_CLK_SM / ub["shoup_modmul"]
-    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved / 1e9, "peak": peak / 1e9,
-                "unit": unit, "frac": achieved / peak, "traffic": traffic, "peak_basis": basis,
-                "traffic_basis": ("ncu dram bytes per limb item of this kernel at batch 16, times the items of "
-                                  "an average launch" if traffic is not None else None),
-                "avg_launch_ms": d["ms"] / max(d["launches"], 1), "classes": per_class,
+    per_class = {}
+    for k, v in classes.items():
+        secs = v["ms"] / 1e3
+        u, pk = unit_peak(k)
+        t_alu = v["modmul"] / pk
+        t_hbm = v["bytes"] / (hbm_gbs * 1e9)
+        per_class[k] = {
+            "ms_per_step": v["ms"] / class_steps, "launches_per_step": v["launches"] / class_steps,
+            "share": v["ms"] / max(sum(x["ms"] for x in classes.values()), 1e-9),
+            "work_rate": v["modmul"] / secs / 1e9 if secs else 0.0, "work_unit": u, "work_peak": pk / 1e9,
+            "alu_frac": t_alu / secs if secs else 0.0,
+            "hbm_gbs": v["bytes"] / secs / 1e9 if secs else 0.0, "hbm_frac": t_hbm / secs if secs else 0.0,
+            "bound": "hbm" if t_hbm > t_alu else "alu",
+            "frac": max(t_alu, t_hbm) / secs if secs else 0.0,
+            "algorithmic_bytes_per_step": v["bytes"] / class_steps,
+            "traffic_over_algorithmic": TRAFFIC_RATIO.get(k)}
+    dom = max(classes, key=lambda k: classes[k]["ms"])
+    d, pc = classes[dom], per_class[dom]
+    n_launch = max(d["launches"], 1)
+    avg_s = d["ms"] / 1e3 / n_launch
+    if pc["bound"] == "hbm":
+        achieved, peak, unit = d["bytes"] / n_launch / avg_s / 1e9, hbm_gbs, "GB/s"
+        peak_basis = f"HBM copy bandwidth, {hbm_src}"
+    else:
+        u, pk = unit_peak(dom)
+        achieved, peak, unit = d["modmul"] / n_launch / avg_s / 1e9, pk / 1e9, u
+        peak_basis = (f"{SM_COUNT} SMs x {MAX_SM_MHZ:.0f} MHz x "
+                      f"{ub['split_mac' if dom in MAC_CLASSES else 'shoup_modmul']:.3f} units/clk/SM measured "
+                      f"now (ctl_microbench_unit_rate)")
+    ratio = TRAFFIC_RATIO.get(dom)
+    roofline = {"bound": pc["bound"], "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "peak_basis": peak_basis,
+                "traffic": ratio * d["bytes"] / n_launch if ratio else None,
+                "traffic_basis": ("ncu dram bytes over algorithmic bytes of this class at batch 16, times the "
+                                  "algorithmic bytes of an average launch" if ratio else None),
+                "algorithmic_bytes_per_launch": d["bytes"] / n_launch,
+                "hbm_peak_gbs": hbm_gbs, "hbm_frac": pc["hbm_frac"], "alu_frac": pc["alu_frac"],
+                "avg_launch_ms": d["ms"] / n_launch, "classes": per_class,
                 "unit_rates_per_clk_sm": ub,
+                "imad_slot_peak": {"per_s": imad_slots,
+                                   "slots_per_shoup_modmul": IMAD_PER_CLK_SM / ub["shoup_modmul"],
+                                   "slots_per_split_mac": IMAD_PER_CLK_SM / ub["split_mac"]},
+                "eager_ms_per_step": class_ms_per_step,
                 "timing": timing_source}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        est, desc, cores, _ = cpu_oracle_sample(wl)
-        cpu = {"value": 1.0 / est, "unit": "forwards/s", "cores": cores, "kind": "oracle", "sample": desc}
+        fwd_s, desc, cores, _ = cpu_oracle_sample(wl)
+        cpu = {"value": fwd_s, "unit": "forwards/s", "cores": cores, "kind": "oracle", "sample": desc}
+
+    # the other configurations, measured in the same run: single queries under the graph
+    # (configurations 1 and 2, and the batched network one query at a time) and one short
+    # serving point (configuration 5)
+    others = None
+    if rank == 0 and world == 1 and args.workload == "batched" and not args.no_others:
+        others = {name: single_query_point(ctl, torch, name, args.single_steps)
+                  for name in ("single4096", "single8192", "batched")}
+        others["batched"]["desc"] = "the batched network, one query per forward (batch 1)"
+        others["serving"] = serving_point(ctl, args.serve_rate, args.serve_seconds, args.serve_clients)
 
     if rank == 0:
         lat = sorted(step_ms)
@@ -836,7 +990,7 @@ def main():
                                "per": f"batch of {B}"},
                 "ops_per_step": {k: v / args.steps for k, v in ops.items()},
                 "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
-                "gpu_launches": int(launches), "variants": variants}
+                "gpu_launches": int(launches), "variants": variants, "other_workloads": others}
         if args.workload in PAPER_T_S:
             ts, pp = PAPER_T_S[args.workload], {"paper_p1": 2, "paper_p2": 5}[args.workload]
             line["predictions_per_ciphertext"] = windows

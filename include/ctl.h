@@ -458,6 +458,13 @@ int ctl_server_poll(ctl_server* srv, uint64_t request, uint64_t* out, size_t cap
 int ctl_server_wait(ctl_server* srv, uint64_t request, uint32_t timeout_ms, uint64_t* out, size_t cap,
                     double* latency_ms);
 int ctl_server_stats(ctl_server* srv, uint64_t* counts6, double* p50_ms, double* p99_ms);
+/* Memory admission of the server: the device-memory estimate per in-flight ciphertext of
+ * the client's lane (a batch of n reserves n times it, and is admitted only while the
+ * reservations of running batches plus its own stay within mem_budget_bytes; a batch of
+ * one runs even above the budget when nothing else runs), the highest total reservation
+ * so far, and how often a worker found requests queued but had to wait for memory. */
+int ctl_server_admission(ctl_server* srv, uint32_t client, uint64_t* bytes_per_ct, uint64_t* peak_reserved,
+                         uint64_t* deferred);
 /* Stops the workers (queued requests are dropped) and releases the server. */
 void ctl_server_destroy(ctl_server* srv);
 
@@ -467,6 +474,21 @@ void ctl_server_destroy(ctl_server* srv);
  * 3 = split-half multiply-accumulate (four 32x32->64 multiply-adds).  Synchronous; tens of
  * milliseconds.  Errors: CTL_EINVAL, CTL_ENOMEM, CTL_ECUDA. */
 int ctl_microbench_unit_rate(int kind, double* per_clk_sm);
+
+/* Evaluates one of the kernels' modular-arithmetic primitives (the word-size residue
+ * arithmetic of Sec. 3.1's RNS representation) on n host values x, on the current
+ * device, writing n results to host out.  Synchronous; allocates 16n bytes of device
+ * memory for the call.  kind:
+ *   0 shoup(x, w, wsh, q)      = x*w mod q in [0, q) for any 64-bit x, wsh = floor(w 2^64 / q);
+ *   1 shoup_lazy(x, w, wsh, q) = x*w mod q plus 0 or q, in [0, 2q);
+ *   2 shoup_small(x, w, wsh, q): x*w mod q plus a multiple of q, in [0, 4q);
+ *   3 reduce_wide(x, q, aux)   = x mod q for x < 2^63, 2^32 < q, aux = floor(2^64 / q);
+ *   4 mulmod_mont(x, w, q, aux) = x * w * 2^-64 mod q for any 64-bit x, w < q,
+ *                                 aux = q^-1 mod 2^64;
+ *   5 reduce4(x, q)            = x mod q for x < 4q.
+ * Errors: CTL_EINVAL, CTL_ENOMEM, CTL_ECUDA. */
+int ctl_modarith_eval(int kind, const uint64_t* x, size_t n, uint64_t w, uint64_t wsh, uint64_t q, uint64_t aux,
+                      uint64_t* out);
 
 /* ---------------------------------------------------------------------------------
  * Statistics: kernel launches since the last reset, homomorphic operation counters
@@ -483,6 +505,10 @@ const char* ctl_stats_class_name(int i);
 /* Collects pending event timings (synchronises) and writes ms[i], launches[i] and the
  * algorithmic modular multiplications work[i] of each class i. */
 int ctl_stats_kernels(ctl_context* ctx, double* ms, uint64_t* launches, double* work);
+/* Writes bytes[i], the algorithmic HBM bytes of class i since the last reset (every
+ * operand of a launch read once and every result written once), for the HBM side of the
+ * per-class rooflines.  Counted while timing is enabled, like work[i]. */
+int ctl_stats_kernel_bytes(const ctl_context* ctx, double* bytes);
 
 #ifdef __cplusplus
 }

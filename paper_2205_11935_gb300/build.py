@@ -5,6 +5,7 @@ Every translation unit under csrc/ is compiled in parallel with nvcc
 """
 import concurrent.futures as cf
 import os
+import shutil
 import subprocess
 import sys
 
@@ -17,6 +18,16 @@ NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]
+
+
+def cuda_lib_dir():
+    """The CUDA runtime's library directory of the toolkit whose nvcc builds the library."""
+    nvcc = shutil.which(NVCC) or NVCC
+    root = os.path.dirname(os.path.dirname(os.path.realpath(nvcc)))
+    for d in ("lib64", "lib"):
+        if os.path.isdir(os.path.join(root, d)):
+            return os.path.join(root, d)
+    return os.path.join(root, "lib64")
 
 
 def sources():
@@ -60,7 +71,7 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
         objs = list(ex.map(lambda s: _compile(s, extra), srcs))
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [NVCC] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + [
-        "-Xlinker", "-rpath", "-Xlinker", "/usr/local/cuda/lib64"]
+        "-Xlinker", "-rpath", "-Xlinker", cuda_lib_dir()]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -65,7 +65,7 @@ void timing_begin(ctl_context* c, int, cudaEvent_t* ev) {
   cudaEventRecord(e, c->stream);
   *ev = e;
 }
-void timing_end(ctl_context* c, int cls, cudaEvent_t ev, double work) {
+void timing_end(ctl_context* c, int cls, cudaEvent_t ev, double work, double bytes) {
   if (!c->timing.enabled || !ev) return;
   cudaEvent_t e;
   if (!c->timing.pool.empty()) {
@@ -78,6 +78,7 @@ void timing_end(ctl_context* c, int cls, cudaEvent_t ev, double work) {
   c->timing.pending.push_back({cls, {ev, e}});
   c->timing.launches[cls]++;
   c->timing.work[cls] += work;
+  c->timing.bytes[cls] += bytes;
 }
 }  // namespace ctl
 
@@ -2526,6 +2527,7 @@ extern "C" int ctl_stats_reset(ctl_context* c) {
     c->timing.ms[i] = 0;
     c->timing.launches[i] = 0;
     c->timing.work[i] = 0;
+    c->timing.bytes[i] = 0;
   }
   c->launch_count = 0;
   c->op_rot = c->op_ptmul = c->op_add = c->op_relin = c->op_rescale = 0;
@@ -2564,5 +2566,11 @@ extern "C" int ctl_stats_kernels(ctl_context* c, double* ms, uint64_t* launches,
     if (launches) launches[i] = c->timing.launches[i];
     if (work) work[i] = c->timing.work[i];
   }
+  return CTL_OK;
+}
+
+extern "C" int ctl_stats_kernel_bytes(const ctl_context* c, double* bytes) {
+  if (!c || !bytes) return CTL_EINVAL;
+  for (int i = 0; i < KC_COUNT; i++) bytes[i] = c->timing.bytes[i];
   return CTL_OK;
 }

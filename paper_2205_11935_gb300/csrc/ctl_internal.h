@@ -149,7 +149,8 @@ struct Timing {
   std::vector<cudaEvent_t> pool;
   double ms[KC_COUNT] = {0};
   uint64_t launches[KC_COUNT] = {0};
-  double work[KC_COUNT] = {0};  // algorithmic units (modmul) attributed to the class
+  double work[KC_COUNT] = {0};   // algorithmic units (modmul or MAC) attributed to the class
+  double bytes[KC_COUNT] = {0};  // algorithmic HBM bytes (each operand read once, each result written once)
 };
 
 }  // namespace ctl
@@ -227,7 +228,7 @@ void dev_free(ctl_context* c, void* p);
 void set_error(const char* fmt, ...);
 int cuda_check(cudaError_t e, const char* what);
 void timing_begin(ctl_context* c, int cls, cudaEvent_t* ev);
-void timing_end(ctl_context* c, int cls, cudaEvent_t ev, double work);
+void timing_end(ctl_context* c, int cls, cudaEvent_t ev, double work, double bytes = 0.0);
 
 inline uint32_t prime_of_limb(uint32_t l, uint32_t lvl, uint32_t L) { return l < lvl ? l : L + (l - lvl); }
 

@@ -26,14 +26,17 @@ static int elem_grid(ctl_context* c, size_t total) {
   return (int)(g < cap ? g : cap);
 }
 
-#define CTL_LAUNCH(cls, work, grid, ...)  \
-  do {                                    \
-    cudaEvent_t ev__;                     \
-    timing_begin(c, cls, &ev__);          \
-    __VA_ARGS__;                          \
-    c->launch_count++;                    \
-    timing_end(c, cls, ev__, work);       \
+// A launch with its algorithmic work (modmul or MAC units) and HBM bytes for the
+// per-class rooflines; CTL_LAUNCH counts no bytes.
+#define CTL_LAUNCH_C(cls, work, bytes, grid, ...) \
+  do {                                            \
+    cudaEvent_t ev__;                             \
+    timing_begin(c, cls, &ev__);                  \
+    __VA_ARGS__;                                  \
+    c->launch_count++;                            \
+    timing_end(c, cls, ev__, work, bytes);        \
   } while (0)
+#define CTL_LAUNCH(cls, work, grid, ...) CTL_LAUNCH_C(cls, work, 0.0, grid, __VA_ARGS__)
 
 // ---------------------------------------------------------------------------------
 // add / sub over n_polys polys of lvl limbs (limb i -> prime i).
@@ -517,10 +520,14 @@ void launch_key_ip(ctl_context* c, const u64* ext, size_t ext_r, int nb, int lvl
   const unsigned eblocks = (unsigned)((EN + 255) / 256);
   dim3 grid = ext_r == 0 ? dim3((unsigned)nrot, eblocks) : dim3(eblocks, (unsigned)nrot);
   double work = 2.0 * nd * EN * nb * nrot;
+  // bytes: the extended digits once (shared by the rotations when hoisted), each rotation's
+  // key once, the two accumulator polys written, and the c0 addend read when given
+  const double bytes = 8.0 * (double)EN * ((ext_r == 0 ? 1.0 : nrot) * nb * nd + 2.0 * nd * nrot + 2.0 * nrot * nb +
+                                           (add_c0 ? (double)nrot * nb * lvl / E : 0.0));
   const u64* pm = c->moddown.pmod;
   const u64* pms = c->moddown.pmod_sh;
 #define CTL_KEYIP_CASE(KERN, NDV, EX)                                                                          \
-  CTL_LAUNCH(KC_KEYIP, work, grid,                                                                             \
+  CTL_LAUNCH_C(KC_KEYIP, work, bytes, grid,                                                                    \
              (KERN<NDV, EX><<<grid, 256, 0, c->stream>>>(ext, ext_r, rl, acc, add_c0, add_b, pm, pms,           \
                                                          c->d_primes, (int)c->logN, nb, nd, E, lvl, (int)c->L,  \
                                                          LK)))
@@ -606,8 +613,12 @@ void launch_key_ip_acc(ctl_context* c, const u64* ext, size_t ext_r, int nb, int
   const int b_per = (nb + splits - 1) / splits;
   dim3 grid(gx, (unsigned)((nb + b_per - 1) / b_per));
   double work = 2.0 * nd * EN * nb * rl.n;
+  // bytes: the digits of every rotation's input, the keys, the addend and the sums S read
+  // and written
+  const double bytes = 8.0 * (double)EN * ((double)rl.n * nb * nd + 2.0 * nd * rl.n + (double)rl.n * nb * 2.0 +
+                                           4.0 * nb);
 #define CTL_KEYIPA_CASE(NDV)                                                                                     \
-  CTL_LAUNCH(KC_KEYIP, work, grid,                                                                               \
+  CTL_LAUNCH_C(KC_KEYIP, work, bytes, grid,                                                                      \
              (k_key_ip_acc<NDV><<<grid, 256, 0, c->stream>>>(ext, ext_r, rl, add, add_r, add_b, S, s_b,           \
                                                              c->d_primes, (int)c->logN, nb, b_per, nd, E, lvl,    \
                                                              (int)c->L, LK)))
@@ -836,16 +847,19 @@ void launch_bsgs_inner(ctl_context* c, const u64* baby, const u64* diag, size_t 
   const int wpb = std::min(8, nb * 2);  // warps (ciphertext polys) per block
   dim3 grid((unsigned)((nb * 2 + wpb - 1) / wpb), gy, (unsigned)((chunks + gy - 1) / gy));
   double work = (double)t1 * t2 * nb * 2 * LN;
+  // bytes: the t1 baby steps and the t diagonals (plus the t2 Winograd pair terms) read
+  // once, the t2 inner sums written once
+  const double bytes = 8.0 * (double)LN * ((double)t1 * nb * 2 + (double)t1 * t2 + t2 + (double)t2 * nb * 2);
   const bool kara = c->bsgs_karatsuba != 0;
 #define CTL_BSGS_CASE(TT)                                                                                      \
   case TT:                                                                                                     \
     if (kara)                                                                                                  \
-      CTL_LAUNCH(KC_BSGS, work, grid,                                                                          \
+      CTL_LAUNCH_C(KC_BSGS, work, bytes, grid,                                                                 \
                  (k_bsgs<TT, true><<<grid, 32 * wpb, 0, c->stream>>>(baby, diag, diag_stride, wino,      \
                                                                      inner, c->d_primes, (int)c->logN, t1, t2, nb,   \
                                                                      limbs, lvl, (int)c->L)));                \
     else                                                                                                       \
-      CTL_LAUNCH(KC_BSGS, work, grid,                                                                          \
+      CTL_LAUNCH_C(KC_BSGS, work, bytes, grid,                                                                 \
                  (k_bsgs<TT, false><<<grid, 32 * wpb, 0, c->stream>>>(baby, diag, diag_stride, wino,    \
                                                                       inner, c->d_primes, (int)c->logN, t1, t2, nb,  \
                                                                       limbs, lvl, (int)c->L)));               \

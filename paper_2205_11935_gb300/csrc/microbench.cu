@@ -104,3 +104,59 @@ extern "C" int ctl_microbench_unit_rate(int kind, double* per_clk_sm) {
     default: return time_unit<3>(sms, per_clk_sm);
   }
 }
+
+namespace ctl {
+namespace {
+
+__global__ void k_modarith_eval(int kind, const u64* __restrict__ x, u64* __restrict__ out, size_t n, u64 w, u64 wsh,
+                                u64 q, u64 aux) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const u64 v = x[i];
+    u64 r;
+    switch (kind) {
+      case 0: r = shoup(v, w, wsh, q); break;
+      case 1: r = shoup_lazy(v, w, wsh, q); break;
+      case 2: r = shoup_small(v, w, wsh, q); break;
+      case 3: r = reduce_wide(v, q, aux); break;
+      case 4: r = mulmod_mont(v, w, q, aux); break;
+      default: r = reduce4(v, q); break;
+    }
+    out[i] = r;
+  }
+}
+
+}  // namespace
+}  // namespace ctl
+
+// Evaluates one modular-arithmetic primitive of the kernels on n host values (copied to
+// the device and back, synchronously, on the current device), so that tests can compare
+// the device results with exact integer arithmetic.  kind: 0 = shoup(x, w, wsh, q),
+// 1 = shoup_lazy, 2 = shoup_small (three-high-half product), 3 = reduce_wide(x, q, bar =
+// aux), 4 = mulmod_mont(x, bmont = w, q, qinv = aux), 5 = reduce4(x, q).
+extern "C" int ctl_modarith_eval(int kind, const uint64_t* x, size_t n, uint64_t w, uint64_t wsh, uint64_t q,
+                                 uint64_t aux, uint64_t* out) {
+  using namespace ctl;
+  if (kind < 0 || kind > 5 || (n && (!x || !out)) || q < 2) {
+    set_error("ctl_modarith_eval: invalid argument");
+    return CTL_EINVAL;
+  }
+  if (!n) return CTL_OK;
+  u64 *dx = nullptr, *dy = nullptr;
+  if (cudaMalloc(&dx, n * sizeof(u64)) != cudaSuccess || cudaMalloc(&dy, n * sizeof(u64)) != cudaSuccess) {
+    cudaGetLastError();
+    if (dx) cudaFree(dx);
+    set_error("ctl_modarith_eval: allocation failed");
+    return CTL_ENOMEM;
+  }
+  int rc = cuda_check(cudaMemcpy(dx, x, n * sizeof(u64), cudaMemcpyHostToDevice), "modarith copy");
+  if (!rc) {
+    const int threads = 256;
+    const int blocks = (int)std::min<size_t>((n + threads - 1) / threads, 4096);
+    k_modarith_eval<<<blocks, threads>>>(kind, dx, dy, n, w, wsh, q, aux);
+    rc = cuda_check(cudaGetLastError(), "modarith launch");
+  }
+  if (!rc) rc = cuda_check(cudaMemcpy(out, dy, n * sizeof(u64), cudaMemcpyDeviceToHost), "modarith copy back");
+  cudaFree(dx);
+  cudaFree(dy);
+  return rc;
+}

@@ -1131,9 +1131,16 @@ static void launch_reg(ctl_context* c, const Pro& pro, const Epi& epi, int items
   }
 }
 
+// Algorithmic cost of one launch: modular multiplications and HBM bytes (every operand
+// read once and every result written once), accumulated per kernel class for the
+// rooflines.
+struct Cost {
+  double work, bytes;
+};
+
 template <bool INV, class Pro, class Epi>
 static void run_ntt(ctl_context* c, int cls, const Pro& pro, const Epi& epi, int n_polys, int limb_lo, int limb_hi,
-                    int lvl, double work_per_limb, const InvScale* scl = nullptr) {
+                    int lvl, Cost cost, const InvScale* scl = nullptr) {
   const int lr = limb_hi - limb_lo;
   const int items = n_polys * lr;
   if (items <= 0) return;
@@ -1163,33 +1170,39 @@ static void run_ntt(ctl_context* c, int cls, const Pro& pro, const Epi& epi, int
     }
   }
   c->launch_count++;
-  timing_end(c, cls, ev, work_per_limb * items);
+  timing_end(c, cls, ev, cost.work, cost.bytes);
 }
 
 static double butterflies(const ctl_context* c) { return 0.5 * c->N * c->logN; }
+// A plain limb transform of `limbs` limbs: butterflies (plus one product per coefficient
+// when a scale is folded in), one limb read and one written each.
+static Cost limb_cost(const ctl_context* c, double limbs, bool scaled = false) {
+  const double N = (double)c->N;
+  return {limbs * (butterflies(c) + (scaled ? N : 0.0)), limbs * 16.0 * N};
+}
 
 void launch_ntt_fwd(ctl_context* c, u64* data, size_t poly_stride, int n_polys, int limb_lo, int limb_hi, int lvl) {
   run_ntt<false>(c, KC_NTT_FWD, ProLoad{data, poly_stride}, EpiStore{data, poly_stride}, n_polys,
-                 limb_lo, limb_hi, lvl, butterflies(c));
+                 limb_lo, limb_hi, lvl, limb_cost(c, (double)n_polys * (limb_hi - limb_lo)));
 }
 
 void launch_ntt_inv(ctl_context* c, u64* data, size_t poly_stride, int n_polys, int limb_lo, int limb_hi, int lvl) {
   run_ntt<true>(c, KC_NTT_INV, ProLoad{data, poly_stride}, EpiStore{data, poly_stride}, n_polys,
-                limb_lo, limb_hi, lvl, butterflies(c));
+                limb_lo, limb_hi, lvl, limb_cost(c, (double)n_polys * (limb_hi - limb_lo)));
 }
 
 void launch_ntt_inv_oop(ctl_context* c, const u64* src, size_t src_stride, u64* dst, size_t dst_stride, int n_polys,
                         int limb_lo, int limb_hi, int lvl, const InvScale* scl) {
   // limb l of poly p: read at src + p*src_stride + l*N, written at dst + p*dst_stride + l*N
   run_ntt<true>(c, KC_NTT_INV, ProLoad{src, src_stride}, EpiStore{dst, dst_stride}, n_polys, limb_lo, limb_hi, lvl,
-                butterflies(c), scl);
+                limb_cost(c, (double)n_polys * (limb_hi - limb_lo), scl != nullptr), scl);
 }
 
 void launch_intt_rescale_last(ctl_context* c, const u64* in, size_t poly_stride, int n_polys, int lvl, u64* r_out) {
   const RescaleTab& R = c->rescale_tabs[lvl];
   // limb lvl-1 of poly p is read at in + p*poly_stride + (lvl-1)*N; r_out[p] is written.
   run_ntt<true>(c, KC_RESCALE, ProLoad{in, poly_stride}, EpiRescaleLast{r_out, R.h}, n_polys,
-                lvl - 1, lvl, lvl, butterflies(c));
+                lvl - 1, lvl, lvl, limb_cost(c, (double)n_polys));
 }
 
 void launch_rescale_ntt(ctl_context* c, const u64* r, const u64* in, size_t in_stride, u64* out, size_t out_stride,
@@ -1197,7 +1210,11 @@ void launch_rescale_ntt(ctl_context* c, const u64* r, const u64* in, size_t in_s
   const RescaleTab& R = c->rescale_tabs[lvl];
   ProRescale pro{r, R.h};
   EpiRescale epi{in, in_stride, out, out_stride, R.inv, R.inv_sh};
-  run_ntt<false>(c, KC_RESCALE, pro, epi, n_polys, 0, lvl - 1, lvl, butterflies(c) + 2.0 * c->N);
+  // per output limb: the transform of the last limb's residue r, then (c_i - r) q_l^-1 (two
+  // products); bytes: r once per poly, each input limb read and each output limb written
+  const double N = (double)c->N, outl = (double)n_polys * (lvl - 1);
+  run_ntt<false>(c, KC_RESCALE, pro, epi, n_polys, 0, lvl - 1, lvl,
+                 Cost{outl * (butterflies(c) + 2.0 * N), 8.0 * N * (n_polys + 2.0 * outl)});
 }
 
 template <int NS>
@@ -1217,8 +1234,20 @@ static void modup_ns(ctl_context* c, const u64* src_coef, size_t coef_stride, co
   pro.alpha = (int)c->alpha;
   for (int d = 0; d < CTL_MAX_DIGITS; d++)
     pro.tabs[d] = d < nd ? c->modup_tabs[(size_t)(lvl - 1) * c->beta + d] : ConvTab{};
+  // Algorithmic work: only the E - |d| converted limbs of digit d are credited, each with
+  // its transform and one product per source limb of the digit (the digit's own limbs are
+  // copies; the per-source factors [a_j q_hat_j^-1] belong to the preceding inverse
+  // transform).  Bytes: the digit's coefficient-form and NTT-form limbs read once, the E
+  // extended limbs written once.
+  double work = 0, bytes = 0;
+  const double N = (double)c->N;
+  for (int d = 0; d < nd; d++) {
+    const int dl = std::min((int)c->alpha, lvl - d * (int)c->alpha);
+    work += (double)(E - dl) * (butterflies(c) + dl * N);
+    bytes += 8.0 * N * (2.0 * dl + E);
+  }
   run_ntt<false>(c, KC_MODUP, pro, EpiStoreSplit{ext, (size_t)E * c->N}, nb * nd, 0, E, lvl,
-                 butterflies(c) + (double)c->alpha * 2.0 * c->N);
+                 Cost{nb * work, nb * bytes});
 }
 
 void launch_modup_ntt(ctl_context* c, const u64* src_coef, size_t coef_stride, const u64* src_ntt, size_t src_stride,
@@ -1256,7 +1285,15 @@ static void moddown_ns(ctl_context* c, const u64* acc, size_t acc_stride, int n_
   epi.nb = nb;
   epi.accum = accum ? 1 : 0;
   for (int r = 0; r < CTL_MAX_ROT; r++) epi.g[r] = (rl && r < rl->n) ? rl->g[r] : 1;
-  run_ntt<false>(c, KC_MODDOWN, pro, epi, n_polys, 0, lvl, lvl, butterflies(c) + (double)(c->K * 2 + 1) * c->N);
+  // per output limb: the transform, one product per special limb (conversion) and the P^-1
+  // product.  Bytes: the K special limbs once per poly; per output limb its accumulator
+  // limb read, the result written, and the addend (and the output, when accumulating) read.
+  const double N = (double)c->N;
+  const double add_polys = addend ? (add_both ? n_polys : n_polys / 2.0) : 0.0;
+  const double bytes = 8.0 * N * ((double)n_polys * c->K + (double)lvl * (2.0 * n_polys + add_polys +
+                                                                          (accum ? n_polys : 0.0)));
+  run_ntt<false>(c, KC_MODDOWN, pro, epi, n_polys, 0, lvl, lvl,
+                 Cost{(double)n_polys * lvl * (butterflies(c) + (double)(c->K + 1) * N), bytes});
 }
 
 template <class... A>
@@ -1394,6 +1431,11 @@ void launch_giant_accum(ctl_context* c, const u64* acc, int nr, int nb, int lvl,
   const int grid = (int)(g < cap ? g : cap);
   const int E = lvl + (int)c->K;
   const double work = (double)nr * nb * 2 * lvl * c->N * c->K;
+  // per rotation: the data and special limbs of both polys and the addend (poly 0) read once;
+  // the three sums read (unless first) and written once per launch
+  const double Nd = (double)c->N;
+  const double bytes = 8.0 * Nd * ((double)nr * nb * (2.0 * (lvl + c->K) + (addend ? lvl : 0)) +
+                                   (first ? 1.0 : 2.0) * nb * 5.0 * lvl);
   cudaEvent_t ev;
   timing_begin(c, KC_MODDOWN, &ev);
   switch (c->K) {
@@ -1413,7 +1455,7 @@ void launch_giant_accum(ctl_context* c, const u64* acc, int nr, int nb, int lvl,
       break;
   }
   c->launch_count++;
-  timing_end(c, KC_MODDOWN, ev, work);
+  timing_end(c, KC_MODDOWN, ev, work, bytes);
 }
 
 void launch_giant_moddown(ctl_context* c, const u64* D, const u64* C, const u64* A, int nb, int lvl, u64* out) {
@@ -1433,7 +1475,11 @@ void launch_giant_moddown(ctl_context* c, const u64* D, const u64* C, const u64*
   epi.nb = nb;
   epi.accum = 1;
   for (int r = 0; r < CTL_MAX_ROT; r++) epi.g[r] = 1;
-  run_ntt<false>(c, KC_MODDOWN, ProLoad{C, LN}, epi, nb * 2, 0, lvl, lvl, butterflies(c) + 3.0 * c->N);
+  // per output limb: the transform of the summed conversions and the P^-1 product; bytes:
+  // the sums C and D and the addend sum A (poly 0) read, the output read and written
+  const double N = (double)c->N, limbs = 2.0 * nb * lvl;
+  run_ntt<false>(c, KC_MODDOWN, ProLoad{C, LN}, epi, nb * 2, 0, lvl, lvl,
+                 Cost{limbs * (butterflies(c) + N), 8.0 * N * (limbs * 4.0 + nb * lvl)});
 }
 
 }  // namespace ctl

@@ -66,6 +66,7 @@ struct ctl_server {
   uint64_t next_id = 1;
   bool started = false, stopping = false;
   uint64_t n_submitted = 0, n_completed = 0, n_rejected = 0, n_failed = 0, n_batches = 0, batched_cts = 0;
+  uint64_t peak_reserved = 0, n_deferred = 0;  // admission: high-water mark, waits for memory
   std::vector<double> latencies_ms;
 };
 
@@ -133,6 +134,7 @@ void worker_loop(ctl_server* s, uint32_t wi) {
           if (s->reserved + n * ln.bytes_per_ct <= s->budget || s->reserved == 0) {
             need = n * ln.bytes_per_ct;
             s->reserved += need;
+            s->peak_reserved = std::max(s->peak_reserved, s->reserved);
             lane = cl.lane;
             for (size_t i = 0; i < n; i++) {
               Request* r = s->reqs[ids[i]].get();
@@ -144,6 +146,7 @@ void worker_loop(ctl_server* s, uint32_t wi) {
             s->batched_cts += n;
             break;
           }
+          s->n_deferred++;  // the oldest request waits until running batches release memory
         }
         s->cv.wait_for(lk, std::chrono::milliseconds(50));
       }
@@ -222,6 +225,19 @@ extern "C" int ctl_server_add_client(ctl_server* s, uint32_t lane, const ctl_key
   std::lock_guard<std::mutex> lk(s->mu);
   s->clients.push_back(Client{lane, keys});
   if (client) *client = (uint32_t)s->clients.size() - 1;
+  return CTL_OK;
+}
+
+extern "C" int ctl_server_admission(ctl_server* s, uint32_t client, uint64_t* bytes_per_ct,
+                                    uint64_t* peak_reserved, uint64_t* deferred) {
+  if (!s || client >= s->clients.size()) {
+    set_error("ctl_server_admission: unknown client");
+    return CTL_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (bytes_per_ct) *bytes_per_ct = s->lanes[s->clients[client].lane].bytes_per_ct;
+  if (peak_reserved) *peak_reserved = s->peak_reserved;
+  if (deferred) *deferred = s->n_deferred;
   return CTL_OK;
 }
 

@@ -123,8 +123,10 @@ SIGNATURES = {
     "ctl_server_poll": (C.c_int, [_vp, C.c_uint64, _u64p, _sz, _dp]),
     "ctl_server_wait": (C.c_int, [_vp, C.c_uint64, C.c_uint32, _u64p, _sz, _dp]),
     "ctl_server_stats": (C.c_int, [_vp, _u64p, _dp, _dp]),
+    "ctl_server_admission": (C.c_int, [_vp, C.c_uint32, _u64p, _u64p, _u64p]),
     "ctl_server_destroy": (None, [_vp]),
     "ctl_microbench_unit_rate": (C.c_int, [C.c_int, _dp]),
+    "ctl_modarith_eval": (C.c_int, [C.c_int, _u64p, _sz, C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64, _u64p]),
     "ctl_stats_reset": (C.c_int, [_vp]),
     "ctl_stats_enable_timing": (C.c_int, [_vp, C.c_int]),
     "ctl_stats_launches": (C.c_uint64, [_vp]),
@@ -132,6 +134,7 @@ SIGNATURES = {
     "ctl_stats_kernel_classes": (C.c_int, []),
     "ctl_stats_class_name": (C.c_char_p, [C.c_int]),
     "ctl_stats_kernels": (C.c_int, [_vp, _dp, _u64p, _dp]),
+    "ctl_stats_kernel_bytes": (C.c_int, [_vp, _dp]),
 }
 
 _LIB = None
@@ -167,6 +170,16 @@ def microbench_unit_rate(kind):
     v = C.c_double()
     _check(lib().ctl_microbench_unit_rate(int(kind), C.byref(v)))
     return v.value
+
+
+def modarith_eval(kind, x, q, w=0, wsh=0, aux=0):
+    """One modular-arithmetic primitive of the kernels evaluated on the device over the
+    values x (ctl_modarith_eval); returns a uint64 array."""
+    x = np.ascontiguousarray(x, dtype=np.uint64)
+    out = np.zeros_like(x)
+    _check(lib().ctl_modarith_eval(int(kind), _p(x, _u64p), x.size, int(w), int(wsh), int(q), int(aux),
+                                   _p(out, _u64p)))
+    return out
 
 
 def plan_primes(N, bits):
@@ -470,9 +483,12 @@ class Context:
         ms = np.zeros(n)
         la = np.zeros(n, dtype=np.uint64)
         wk = np.zeros(n)
+        by = np.zeros(n)
         _check(lib().ctl_stats_kernels(self.h, _p(ms, _dp), _p(la, _u64p), _p(wk, _dp)))
+        _check(lib().ctl_stats_kernel_bytes(self.h, _p(by, _dp)))
         return {lib().ctl_stats_class_name(i).decode(): {"ms": float(ms[i]), "launches": int(la[i]),
-                                                           "modmul": float(wk[i])} for i in range(n)}
+                                                           "modmul": float(wk[i]), "bytes": float(by[i])}
+                for i in range(n)}
 
 
 class Keys:
@@ -647,6 +663,13 @@ class Server:
         _check(lib().ctl_server_add_client(self.h, lane, keys.h, C.byref(cl)))
         self._keep.append(keys)
         return cl.value
+
+    def admission(self, client):
+        """(bytes per in-flight ciphertext of the client's lane, highest total reservation,
+        number of waits for memory) (ctl_server_admission)."""
+        b, pk, d = C.c_uint64(), C.c_uint64(), C.c_uint64()
+        _check(lib().ctl_server_admission(self.h, client, C.byref(b), C.byref(pk), C.byref(d)))
+        return b.value, pk.value, d.value
 
     def io_words(self, client):
         i, o = C.c_size_t(), C.c_size_t()

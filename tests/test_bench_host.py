@@ -51,5 +51,26 @@ def test_operation_plan_follows_the_papers_counts():
 def test_cpu_baseline_runs_a_whole_oracle_forward_on_small_rings():
     wl = dict(bench.WORKLOADS["single4096"])
     wl.update(N=256, dims=[16, 8])  # the same network shape (dense, then x^2), small enough for a unit test
-    secs, err = bench.oracle_forward_seconds(wl)
-    assert secs > 0 and err < 1e-4
+    smp = bench.OracleSample(wl)
+    secs = smp.step()
+    assert secs > 0 and smp.fraction == 1.0 and smp.err < 1e-4
+
+
+def test_cpu_baseline_sample_is_a_fraction_of_the_forward():
+    # larger rings: a step is one rotation, one product and one rescale, a known share of a
+    # forward; the forward is at least as long as one rotation per key switch at the lowest level
+    wl = dict(bench.WORKLOADS["batched"])
+    wl.update(N=1024)
+    smp = bench.OracleSample(wl, whole=False)
+    secs = smp.step()
+    t_rot, t_pt, t_rs = smp.parts
+    fwd = smp.forward_seconds(t_rot, t_pt, t_rs)
+    n_ks = sum(p[0] for p in bench.op_plan(wl))
+    assert 0 < smp.fraction < 1 and abs(smp.fraction - secs / fwd) < 1e-12
+    assert fwd > n_ks * t_rot * (2 * 6) / (4 * 10) * 0.99  # lowest level of the plan: 4 primes, 2 digits, 6 limbs
+
+
+def test_both_arms_print_the_same_config():
+    wl = bench.WORKLOADS["batched"]
+    assert bench.shared_config(wl, 1) == bench.shared_config(wl, 1)
+    assert set(bench.shared_config(wl, 2, cuda_graph=True)) >= {"workload", "batch_per_gpu", "N", "parallelism"}

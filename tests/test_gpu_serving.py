@@ -1,7 +1,8 @@
 """GPU checks of the batching and serving layer: CUDA-graph forwards and the
 continuous-batching server return exactly what a plain single-query forward returns
 (the integer path is deterministic, so 'the same' means bit-identical), a failing
-client's requests fail while the server keeps serving, and a full queue is refused."""
+client's requests fail while the server keeps serving, a full queue is refused, and
+batches are admitted by the memory budget."""
 import numpy as np
 import pytest
 
@@ -112,4 +113,39 @@ def test_server_failure_and_full_queue():
         if i is not None:
             srv.wait(i, ow)
     assert srv.stats()["rejected"] > 0
+    srv.close()
+
+
+def test_server_admits_by_memory_budget():
+    """A budget that holds one in-flight ciphertext's estimate but not two: every batch
+    shrinks to one request, workers wait while another batch holds the memory (the total
+    reservation never exceeds the budget), and every request still completes, bit-identical
+    to the same query run alone."""
+    ctx, model, _ = make_lane(4096, [50, 40, 40], [60], 3, [64, 32], 6)
+    keys = ctx.keygen(model.rotations(), seed=3)
+    probe = ctl.Server(mem_budget_bytes=1 << 40, n_workers=1, max_batch=1, max_queue=4)
+    cl0 = probe.add_client(probe.add_lane(ctx, model), keys)
+    bpc = probe.admission(cl0)[0]
+    probe.close()
+    assert bpc > 0
+    budget = bpc + bpc // 2
+    srv = ctl.Server(mem_budget_bytes=budget, n_workers=3, max_batch=4, max_queue=100)
+    cl = srv.add_client(srv.add_lane(ctx, model), keys)
+    ow = srv.io_words(cl)[1]
+    cts = [query(ctx, keys, 64, 64, 500 + i) for i in range(12)]
+    alone = [model.forward(keys, c).export()[0] for c in cts]
+    coeffs = [c.export()[0] for c in cts]
+    srv.start()
+    ids = [srv.submit(cl, x) for x in coeffs]  # a burst: requests queue behind the running one
+    assert all(i is not None for i in ids)
+    for rid, want in zip(ids, alone):
+        got, _ = srv.wait(rid, ow)
+        assert np.array_equal(got.reshape(want.shape), want)
+    st = srv.stats()
+    b, peak, deferred = srv.admission(cl)
+    assert b == bpc
+    assert st["completed"] == 12 and st["failed"] == 0
+    assert st["batches"] == 12  # groups of up to 4 shrank to 1 to fit the budget
+    assert peak <= budget  # never two batches' reservations at once
+    assert deferred > 0  # idle workers waited for memory while requests were queued
     srv.close()
