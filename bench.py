@@ -56,7 +56,7 @@ def hbm_peak_gbs():
         return HBM_FALLBACK_GBS, "fallback"
 
 WORKLOADS = {
-    "batched": dict(N=16384, q=[45] * 8, p=[60, 60], dnum=4, batch=256, dims=[1024, 256, 256, 64],
+    "batched": dict(N=16384, q=[45] * 8, p=[60, 60], dnum=4, batch=256, dims=[1024, 256, 256, 64], dense_form="rect",
                     desc="256 ciphertexts, N=16384, 8x45-bit q + 2x60-bit p, dnum=4, scale 2^40; "
                          "dense 1024->256, x^2, dense 256->256, x^2, dense 256->64"),
     "single8192": dict(N=8192, q=[60, 40, 40, 40], p=[60], dnum=4, batch=1, dims=[512, 128, 64],
@@ -223,15 +223,27 @@ def op_plan(wl):
         plan.append((t1 + t2 - 2, t, 1, lvl))                     # dense
         return plan
     dims = wl["dims"]
+    rect = wl.get("dense_form") == "rect"
     for i in range(len(dims) - 1):
-        t = bsgs_t(dims[i + 1], dims[i])
-        t1, t2 = split(t)
-        plan.append((t1 + t2 - 2, t, 1, lvl))
+        tm, tn = bsgs_t(dims[i + 1], 1), bsgs_t(dims[i], 1)
+        last = i + 1 == len(dims) - 1
+        if rect and tm < tn:
+            # rectangular form: Eq. (bsgs) over tm diagonals, then the fold after the rescale
+            # (log2(tn/tm) rotations, one more when it also forms the next layer's [y, y])
+            t1, t2 = split(tm)
+            fuse = not last and bsgs_t(dims[i + 2], dims[i + 1]) == tm
+            plan.append((t1 + t2 - 2, tm, 1, lvl))
+            plan.append(((tn // tm).bit_length() - 1 + (1 if fuse else 0), 0, 0, lvl - 1))
+        else:
+            t = bsgs_t(dims[i + 1], dims[i])
+            t1, t2 = split(t)
+            plan.append((t1 + t2 - 2, t, 1, lvl))
+            fuse = False
         lvl -= 1
-        if i + 1 < len(dims) - 1 or wl.get("square_last", False):
+        if not last or wl.get("square_last", False):
             plan.append((1, 1.5, 1, lvl))  # square: 3 products, relinearisation, rescale
             lvl -= 1
-            if i + 1 < len(dims) - 1:
+            if not last and not fuse:
                 plan.append((1, 0, 0, lvl))  # replicate
     return plan
 
@@ -260,23 +272,35 @@ class OracleSample:
         if self.whole:
             square_last = wl.get("square_last", False)
             layers, self.Ws = layers_for(wl["dims"], square_last)
-            rots = set()
+            rect = wl.get("dense_form") == "rect"
+            rots, skip = set(), set()
             for ly in layers:
-                if ly[0] == "dense":
-                    rots |= set(O.Oracle.bsgs_rotations(*ly[1].shape))
-                elif ly[0] == "replicate":
+                if ly[0] == "replicate":
                     rots.add(-ly[1])
-            o.keygen(sorted(rots), seed=3)
             lvl, sc, self.plan = len(q), o.scale, []
-            for ly in layers:  # plaintexts at the level and scale each layer sees
+            for i, ly in enumerate(layers):  # plaintexts at the level and scale each layer sees
+                if i in skip:
+                    continue
                 if ly[0] == "dense":
-                    self.plan.append(("dense", o.encode_diagonals(ly[1], o.dense_scale(lvl, sc))))
+                    m, n = ly[1].shape
+                    tm, tn = bsgs_t(m, 1), bsgs_t(n, 1)
+                    if rect and tm < tn:  # the rectangular form, as the library's CTL_DENSE_RECT
+                        j = i + 1 + (1 if i + 1 < len(layers) and layers[i + 1][0] == "square" else 0)
+                        fold = 2 if j < len(layers) and layers[j] == ("replicate", tm) else 1
+                        if fold == 2:
+                            skip.add(j)
+                        rots |= set(O.Oracle.rect_rotations(m, n, fold))
+                        self.plan.append(("rect", o.encode_diagonals_rect(ly[1], o.dense_scale(lvl, sc)), tn, fold))
+                    else:
+                        rots |= set(O.Oracle.bsgs_rotations(m, n))
+                        self.plan.append(("dense", o.encode_diagonals(ly[1], o.dense_scale(lvl, sc))))
                     sc, lvl = o.scale, lvl - 1
                 elif ly[0] == "square":
                     self.plan.append(("square",))
                     sc, lvl = o.square_scale(lvl, sc), lvl - 1
                 else:
                     self.plan.append(ly)
+            o.keygen(sorted(rots), seed=3)
             self.out_scale = sc
             t0 = bsgs_t(*self.Ws[0].shape)
             self.xs, slots = inputs_for(N, wl["dims"], 1, t0)
@@ -301,6 +325,8 @@ class OracleSample:
             for st in self.plan:
                 if st[0] == "dense":
                     h = o.dense(h, st[1])[0]
+                elif st[0] == "rect":
+                    h = o.dense_rect(h, st[1], st[2], fold=st[3])[0]
                 elif st[0] == "square":
                     h = o.square(h)
                 else:
@@ -356,7 +382,8 @@ def cpu_oracle_sample(wl, steps=1):
 def shared_config(wl, world, **extra):
     """The `config` object both arms print for the same workload."""
     cfg = {"workload": wl["desc"], "batch_per_gpu": wl["batch"], "N": wl["N"],
-           "parallelism": f"replicas x{world}"}
+           "parallelism": f"replicas x{world}", "dense_form": wl.get("dense_form", "square"),
+           "l2": "inputs larger than L2 (working set of tens of GB per step)"}
     cfg.update(extra)
     return cfg
 
@@ -547,6 +574,8 @@ def single_query_point(ctl, torch, name, steps):
     stream = torch.cuda.Stream()
     ctx = ctl.Context(wl["N"], wl["q"], wl["p"], dnum=wl["dnum"], scale=2.0 ** 40)
     ctx.set_stream(stream.cuda_stream)
+    if wl.get("dense_form") == "rect":
+        ctx.set_dense_mode(ctx.DENSE_RECT)
     model = ctl.Model(ctx, layers)
     keys = ctx.keygen(model.rotations(), seed=3)
     xs, slots = inputs_for(wl["N"], wl["dims"], 1, t0)
@@ -634,6 +663,9 @@ def main():
     ap.add_argument("--profile-forward", action="store_true",
                     help="run one eager forward inside cudaProfilerStart/Stop and print its per-class "
                          "algorithmic work and bytes (for an ncu capture of exactly that forward)")
+    ap.add_argument("--dense-form", default="", choices=["", "rect", "square"],
+                    help="rect: shrinking dense layers in the rectangular form (default for the dense/x^2 "
+                         "networks); square: every layer padded to a square t x t matrix")
     ap.add_argument("--no-others", action="store_true",
                     help="skip the single-query and serving points measured beside the batched value")
     ap.add_argument("--single-steps", type=int, default=300, help="timed single-query forwards per point")
@@ -658,6 +690,8 @@ def main():
     wl = dict(WORKLOADS[args.workload])
     if args.batch:
         wl["batch"] = args.batch
+    if args.dense_form:
+        wl["dense_form"] = args.dense_form
     if not args.steps:
         args.steps = 500 if wl["batch"] == 1 else 5
 
@@ -709,6 +743,10 @@ def main():
     # Sec. 3.1 "Multiple Predictions": the paper's network packs p = floor(#slots / 2t)
     # inputs per ciphertext (one window of 2t slots each)
     windows = (N // 2) // (2 * t0) if wl.get("net") == "paper" else 1
+    dense_form = args.dense_form or wl.get("dense_form", "square")
+    wl["dense_form"] = dense_form
+    if dense_form == "rect":  # shrinking dense layers take the rectangular form
+        ctx.set_dense_mode(ctx.DENSE_RECT)
     ctx.set_windows(windows)
     if args.ntt_shape != "auto":
         sh = ctx.NTT_R16 if args.ntt_shape == "r16" else ctx.NTT_R32
@@ -869,34 +907,47 @@ def main():
     # valid ciphertext; its own BSGS split and Galois keys): reported beside, not as, the value
     variants = None
     if not args.no_variants and world == 1:
-        ctx.set_dense_mode(ctx.DENSE_LAZY_MODDOWN)
-        model_l = ctl.Model(ctx, layers)
-        keys_l = ctx.keygen(model_l.rotations(), seed=3)  # same secret (same seed)
-        o = model_l.forward(keys_l, batch)
-        err_l = 0.0
-        for i in check_idx:
-            yi = ctx.decrypt(keys_l, o.slice(i), 2 * t0 * (windows - 1) + m_out)
-            for j in range(windows):
-                err_l = max(err_l, float(np.max(np.abs(yi[2 * t0 * j:2 * t0 * j + m_out] - reference(xs[i, j])))))
-        o.close()
-        for _ in range(2):
-            model_l.forward(keys_l, batch).close()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            model_l.forward(keys_l, batch).close()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms_l = e0.elapsed_time(e1)
-        variants = {"lazy_moddown": {
-            "value": B * args.steps / (ms_l / 1e3), "unit": "forwards/s", "ms_per_step": ms_l / args.steps,
-            "max_abs_err_vs_fp64": err_l, "rotations_per_forward": len(model_l.rotations()),
-            "desc": "ctl_set_dense_mode(CTL_DENSE_LAZY_MODDOWN): rotations kept in the extended basis, "
-                    "ModDown once per giant step and once per layer, t1 = min(t, 2^ceil(log2(4t)/2))"}}
-        model_l.close()
-        keys_l.close()
-        ctx.set_dense_mode(ctx.DENSE_COMPOSED)
+        # the same workload with the dense layers in the other forms (different, equally valid
+        # ciphertexts with their own Galois keys): reported beside, not as, the value
+        forms = {"square_padding": (ctx.DENSE_COMPOSED,
+                                    "ctl_set_dense_mode(CTL_DENSE_COMPOSED): every dense layer padded to a square "
+                                    "t x t matrix, t = 2^ceil(log2 max(m, n)), t1 = 2^ceil(log2(t)/2)"),
+                 "lazy_moddown": (ctx.DENSE_LAZY_MODDOWN,
+                                  "ctl_set_dense_mode(CTL_DENSE_LAZY_MODDOWN): square padding, rotations kept in the "
+                                  "extended basis, ModDown once per giant step and once per layer, "
+                                  "t1 = min(t, 2^ceil(log2(4t)/2))")}
+        if dense_form != "rect":
+            forms["rectangular"] = (ctx.DENSE_RECT, "ctl_set_dense_mode(CTL_DENSE_RECT)")
+            del forms["square_padding"]
+        variants = {}
+        for name, (mode, desc) in forms.items():
+            ctx.set_dense_mode(mode)
+            model_l = ctl.Model(ctx, layers)
+            keys_l = ctx.keygen(model_l.rotations(), seed=3)  # same secret (same seed)
+            o = model_l.forward(keys_l, batch)
+            err_l = 0.0
+            for i in check_idx:
+                yi = ctx.decrypt(keys_l, o.slice(i), 2 * t0 * (windows - 1) + m_out)
+                for j in range(windows):
+                    err_l = max(err_l, float(np.max(np.abs(yi[2 * t0 * j:2 * t0 * j + m_out] - reference(xs[i, j])))))
+            o.close()
+            for _ in range(2):
+                model_l.forward(keys_l, batch).close()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                model_l.forward(keys_l, batch).close()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_l = e0.elapsed_time(e1)
+            variants[name] = {
+                "value": B * args.steps / (ms_l / 1e3), "unit": "forwards/s", "ms_per_step": ms_l / args.steps,
+                "max_abs_err_vs_fp64": err_l, "rotation_keys": len(model_l.rotations()), "cuda_graph": False,
+                "desc": desc}
+            model_l.close()
+            keys_l.close()
+        ctx.set_dense_mode(ctx.DENSE_RECT if dense_form == "rect" else ctx.DENSE_COMPOSED)
 
     # rooflines per kernel class.  Work units: Shoup modmuls for the transform classes and
     # split-half MACs for the key product and BSGS sums; each unit's peak is this GPU's rate
@@ -982,10 +1033,8 @@ def main():
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
                 "data": "synthetic",
-                "config": {"workload": wl["desc"], "batch_per_gpu": B, "N": N, "parallelism": f"replicas x{world}",
-                           "cuda_graph": bool(use_graph), "ntt_shape": ntt_shape,
-                           "l2": "inputs larger than L2 (working set of tens of GB per step)",
-                           "max_abs_err_vs_fp64": max_err},
+                "config": shared_config(wl, world),
+                "run": {"cuda_graph": bool(use_graph), "ntt_shape": ntt_shape, "max_abs_err_vs_fp64": max_err},
                 "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                                "per": f"batch of {B}"},
                 "ops_per_step": {k: v / args.steps for k, v in ops.items()},

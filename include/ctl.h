@@ -102,6 +102,12 @@ int ctl_synchronize(ctl_context* ctx);
  *     giant step (on c1) and once at the end; t1 = min(t, 2^ceil(log2(4t)/2)).  A
  *     different ciphertext of the same values (lower noise), not bit-identical to the
  *     default; needs the Galois keys of its own split.
+ *   CTL_DENSE_RECT: the composed form, except that a layer whose padded output side
+ *     tm = 2^ceil(log2 m) is below its input side tn = 2^ceil(log2 n) takes the
+ *     rectangular form of ctl_eval_dense_rect (tm diagonals instead of tn, plus a
+ *     log2(tn/tm)-rotation fold).  In a model, when such a layer is followed by
+ *     [square,] replicate(tm), the fold also forms the [y, y] layout (fold 2) and that
+ *     replicate is not run again.  Layers with tm >= tn are as in the composed form.
  * The paper fixes neither choice (Sec. 3.1 only fixes t = t1 * t2 and the hoisting).  A
  * model keeps the mode it was created with.  Errors: CTL_EINVAL (unknown mode). */
 /* Register-resident NTT shapes for N = 4096 .. 16384 (other N use one shared-memory
@@ -143,6 +149,7 @@ int ctl_set_keyswitch_budget(ctl_context* ctx, uint64_t bytes);
 int ctl_set_windows(ctl_context* ctx, uint32_t p);
 #define CTL_DENSE_COMPOSED 0
 #define CTL_DENSE_LAZY_MODDOWN 1
+#define CTL_DENSE_RECT 2
 int ctl_set_dense_mode(ctl_context* ctx, int mode);
 
 /* ---------------------------------------------------------------------------------
@@ -286,6 +293,26 @@ int ctl_eval_dense(ctl_context* ctx, const ctl_keys* keys, const ctl_ct* in, con
 int ctl_eval_dense_coeffs(ctl_context* ctx, const ctl_keys* keys, const ctl_ct* in, const int64_t* pts, uint32_t t,
                           const int64_t* bias, double pt_scale, ctl_ct** out);
 int ctl_replicate(ctl_context* ctx, const ctl_keys* keys, const ctl_ct* in, uint32_t t, ctl_ct** out);
+/* Rectangular form of a dense layer (Sec. 3.1 "Dense-Layer" pads a non-square matrix with
+ * zeros; this form pads only the short side).  For W (m x n) with tm = 2^ceil(log2 m)
+ * below tn = 2^ceil(log2 n), on the [x, x] layout over 2 tn slots:
+ *   rd_i[r] = W[r mod tm][(r + i) mod tn], r < tn, i < tm (zero outside W);
+ *   z' = rescale( sum_k rot_{k t1}( sum_j rd'_{k t1 + j} o rot_j(x) ) [+ bias] ),
+ *        rd'_i = rot_{-floor(i/t1) t1}(rd_i), t1 = 2^ceil(log2(tm)/2), t2 = tm / t1;
+ *   fold >= 1: S = z'; S = S + rot_s(S) for s = tn/2, tn/4, ..., tm  -> y in slots [0, m);
+ *   fold == 2: S = S + rot_{-tm}(z')                                  -> y also in [tm, tm + m).
+ * Other slots of the output hold partial sums (not zeros).  Work: tm plaintext products
+ * and t1 + t2 - 2 + log2(tn/tm) (+1) rotations, against tn products and about 2 sqrt(tn)
+ * rotations for the square padding.  Needs the Galois keys of 1..t1-1, k*t1, the fold
+ * shifts tn/2 .. tm and (fold 2) -tm.  bias (m values) is added before the rescale.
+ * Errors: CTL_EINVAL (tm >= tn, 2 tn > N/2, windows > 1, the lazy-ModDown mode), CTL_EKEY,
+ * CTL_ELEVEL.
+ * ctl_eval_dense_rect_coeffs: the same with the tm plaintexts given as integer
+ * coefficients pts[tm][N] (and bias as coefficients, nullable) at pt_scale. */
+int ctl_eval_dense_rect(ctl_context* ctx, const ctl_keys* keys, const ctl_ct* in, const double* W, uint32_t m,
+                        uint32_t n, const double* bias, int fold, ctl_ct** out);
+int ctl_eval_dense_rect_coeffs(ctl_context* ctx, const ctl_keys* keys, const ctl_ct* in, const int64_t* pts,
+                               uint32_t tm, uint32_t tn, const int64_t* bias, double pt_scale, int fold, ctl_ct** out);
 int ctl_add(ctl_context* ctx, const ctl_ct* a, const ctl_ct* b, ctl_ct** out);
 int ctl_mul_plain_coeffs(ctl_context* ctx, const ctl_ct* in, const int64_t* pt, double pt_scale, ctl_ct** out);
 

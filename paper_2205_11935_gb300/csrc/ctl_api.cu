@@ -497,7 +497,7 @@ extern "C" int ctl_set_allocator(ctl_context* c, ctl_alloc_fn a, ctl_free_fn f, 
 }
 
 extern "C" int ctl_set_dense_mode(ctl_context* c, int mode) {
-  if (!c || (mode != CTL_DENSE_COMPOSED && mode != CTL_DENSE_LAZY_MODDOWN)) {
+  if (!c || (mode != CTL_DENSE_COMPOSED && mode != CTL_DENSE_LAZY_MODDOWN && mode != CTL_DENSE_RECT)) {
     set_error("ctl_set_dense_mode: invalid argument");
     return CTL_EINVAL;
   }
@@ -1303,6 +1303,11 @@ extern "C" int ctl_add(ctl_context* c, const ctl_ct* a, const ctl_ct* b, ctl_ct*
 struct DenseLayer {
   uint32_t m = 0, n = 0, t = 0, t1 = 0, t2 = 0, lvl = 0;
   bool lazy = false;     // lazy-ModDown form (CTL_DENSE_LAZY_MODDOWN) instead of composed rotations
+  // rectangular form (CTL_DENSE_RECT, t = tm < tn): t diagonals of length tn, then the fold
+  // over the tn/t blocks after the rescale (fold 1), and the [y, y] layout at stride t (fold 2)
+  bool rect = false;
+  uint32_t tn = 0;
+  int fold = 0;
   double pt_scale = 0, in_scale = 0, out_scale = 0;
   u64* diag = nullptr;   // [t][limbs][N] NTT + Montgomery form (split); limbs = lvl (+K if lazy)
   u64* wino = nullptr;   // [t2][limbs][N] diagonal pair terms of the Winograd inner sums
@@ -1397,12 +1402,51 @@ int encode_diagonals(ctl_context* c, const double* W, uint32_t m, uint32_t n, ui
   return CTL_OK;
 }
 
+// Rectangular diagonals of W (m x n, tm = pow2 >= m below tn = pow2 >= n):
+// rd_i[r] = W[r mod tm][(r + i) mod tn] for r < tn, i < tm, placed as rd'_i =
+// rot_{-floor(i/t1) t1}(rd_i) with rd_i in slots [0, tn); pts [tm][N].
+int encode_diagonals_rect(ctl_context* c, const double* W, uint32_t m, uint32_t n, uint32_t tm, uint32_t tn,
+                          uint32_t t1, double scale, std::vector<i64>& pts) {
+  const uint32_t ns = c->N / 2;
+  pts.assign((size_t)tm * c->N, 0);
+  std::vector<double> v(ns);
+  for (uint32_t i = 0; i < tm; i++) {
+    std::fill(v.begin(), v.end(), 0.0);
+    const uint32_t sh = (i / t1) * t1;
+    for (uint32_t r = 0; r < tn; r++) {
+      const uint32_t row = r % tm, col = (r + i) % tn;
+      v[r + sh] = (row < m && col < n) ? W[(size_t)row * n + col] : 0.0;
+    }
+    if (!c->enc.encode(v.data(), ns, scale, &pts[(size_t)i * c->N])) {
+      set_error("dense: diagonal encoding overflow");
+      return CTL_EINVAL;
+    }
+  }
+  return CTL_OK;
+}
+
+// The rectangular form's shape: tm < tn, both powers of two, one window, 2 tn <= N/2.
+struct RectSpec {
+  uint32_t tn = 0;
+  int fold = 0;
+};
+
 int dense_prepare(ctl_context* c, DenseLayer& D, const double* W, const double* bias, const int64_t* pts_in,
                   const int64_t* bias_in, uint32_t m, uint32_t n, uint32_t t_given, uint32_t lvl, double in_scale,
-                  double pt_scale) {
+                  double pt_scale, const RectSpec* rs = nullptr) {
   D.m = m;
   D.n = n;
-  D.t = pts_in ? t_given : bsgs_t(m, n);
+  D.t = pts_in ? t_given : (rs ? bsgs_t(m, 1) : bsgs_t(m, n));
+  D.rect = rs != nullptr;
+  if (rs) {
+    D.tn = rs->tn;
+    D.fold = rs->fold;
+    if (c->dense_mode == CTL_DENSE_LAZY_MODDOWN || c->windows != 1 || D.t >= D.tn || (D.tn & (D.tn - 1)) ||
+        2 * D.tn > c->N / 2 || rs->fold < 0 || rs->fold > 2) {
+      set_error("dense (rectangular): needs tm < tn (powers of two), 2 tn <= N/2, one window, the composed form");
+      return CTL_EINVAL;
+    }
+  }
   D.lazy = c->dense_mode == CTL_DENSE_LAZY_MODDOWN;
   D.t1 = bsgs_t1(D.t, D.lazy);
   D.t2 = D.t / D.t1;
@@ -1423,7 +1467,9 @@ int dense_prepare(ctl_context* c, DenseLayer& D, const double* W, const double* 
   std::vector<i64> enc;
   const i64* src = (const i64*)pts_in;
   if (!src) {
-    if (int rc = encode_diagonals(c, W, m, n, D.t1, D.pt_scale, enc)) return rc;
+    if (int rc = D.rect ? encode_diagonals_rect(c, W, m, n, D.t, D.tn, D.t1, D.pt_scale, enc)
+                        : encode_diagonals(c, W, m, n, D.t1, D.pt_scale, enc))
+      return rc;
     src = enc.data();
   }
   const uint32_t limbs = D.lazy ? lvl + c->K : lvl;
@@ -1560,6 +1606,31 @@ int dense_apply_lazy(ctl_context* c, const ctl_keys* k, const DenseLayer& D, con
   return rescale_into(c, acc.p, nb, (int)lvl, out);
 }
 
+// The fold of the rectangular form on the rescaled partial sums z' (level lv, batch nb,
+// in place in S = z'):  S = S + rot_s(S) for s = tn/2, tn/4, ..., tm, leaving y in slots
+// [0, tm); with fold 2 also S = S + rot_{-tm}(z'), the [y, y] layout at stride tm.  The
+// first fold rotation and rot_{-tm}(z') rotate the same ciphertext and share one ModUp.
+int rect_fold(ctl_context* c, const ctl_keys* k, const DenseLayer& D, u64* S, int nb, int lv) {
+  const size_t LN = (size_t)lv * c->N, bw = (size_t)nb * 2 * LN;
+  std::vector<int64_t> first = {(int64_t)(D.tn / 2)};
+  if (D.fold == 2) first.push_back(-(int64_t)D.t);
+  DBuf tmp(c, bw * first.size());
+  CHECK_ALLOC(tmp);
+  if (int rc = rotate_many(c, k, S, nb, lv, first, tmp.p)) return rc;
+  launch_add(c, S, tmp.p, S, nb * 2, lv, LN, LN, LN);
+  c->op_add += nb;
+  for (uint32_t sh = D.tn / 4; sh >= D.t; sh /= 2) {
+    if (int rc = rotate_many(c, k, S, nb, lv, {(int64_t)sh}, tmp.p)) return rc;
+    launch_add(c, S, tmp.p, S, nb * 2, lv, LN, LN, LN);
+    c->op_add += nb;
+  }
+  if (D.fold == 2) {
+    launch_add(c, S, tmp.p + bw, S, nb * 2, lv, LN, LN, LN);
+    c->op_add += nb;
+  }
+  return last_cuda("dense fold");
+}
+
 // Dense layer by Eq. (bsgs) as the composition of whole rotations, batch nb:
 //   out = rescale( sum_k rot_{k t1}( sum_j diag'_{k t1 + j} o rot_j(in) ) [+ bias] ),
 // the baby steps sharing one ModUp (hoisted), each rotation ending with its ModDown.
@@ -1617,7 +1688,9 @@ int dense_apply_composed(ctl_context* c, const ctl_keys* k, const DenseLayer& D,
     launch_giant_moddown(c, gD.p, gC.p, gA.p, nb, (int)lvl, acc);
   }
   if (D.bias) launch_add_plain(c, acc, D.bias, nb, (int)lvl, ctw);
-  return rescale_into(c, acc, nb, (int)lvl, out);
+  int rc = rescale_into(c, acc, nb, (int)lvl, out);
+  if (rc || !D.rect || D.fold == 0) return rc;
+  return rect_fold(c, k, D, out, nb, (int)lvl - 1);
 }
 
 int dense_apply(ctl_context* c, const ctl_keys* k, const DenseLayer& D, const u64* in, int nb, u64* out) {
@@ -1628,14 +1701,14 @@ int dense_apply(ctl_context* c, const ctl_keys* k, const DenseLayer& D, const u6
 
 static int dense_common(ctl_context* c, const ctl_keys* k, const ctl_ct* in, const double* W, const double* bias,
                         const int64_t* pts, const int64_t* bias_c, uint32_t m, uint32_t n, uint32_t t, double pt_scale,
-                        ctl_ct** out) {
+                        ctl_ct** out, const RectSpec* rs = nullptr) {
   if (!c || !k || !in || !out) {
     set_error("dense: null argument");
     return CTL_EINVAL;
   }
   *out = nullptr;
   DenseLayer D;
-  int rc = dense_prepare(c, D, W, bias, pts, bias_c, m, n, t, in->level, in->scale, pt_scale);
+  int rc = dense_prepare(c, D, W, bias, pts, bias_c, m, n, t, in->level, in->scale, pt_scale, rs);
   if (rc) {
     dense_release(c, D);
     return rc;
@@ -1662,7 +1735,34 @@ extern "C" int ctl_eval_dense(ctl_context* c, const ctl_keys* k, const ctl_ct* i
     set_error("ctl_eval_dense: invalid weights");
     return CTL_EINVAL;
   }
+  // CTL_DENSE_RECT: the rectangular form (fold 1) when the padded output side is shorter
+  const uint32_t tm = bsgs_t(m, 1), tn = bsgs_t(n, 1);
+  if (c && c->dense_mode == CTL_DENSE_RECT && tm < tn && c->windows == 1) {
+    RectSpec rs{tn, 1};
+    return dense_common(c, k, in, W, bias, nullptr, nullptr, m, n, 0, 0.0, out, &rs);
+  }
   return dense_common(c, k, in, W, bias, nullptr, nullptr, m, n, 0, 0.0, out);
+}
+
+extern "C" int ctl_eval_dense_rect(ctl_context* c, const ctl_keys* k, const ctl_ct* in, const double* W, uint32_t m,
+                                   uint32_t n, const double* bias, int fold, ctl_ct** out) {
+  if (!W || m == 0 || n == 0) {
+    set_error("ctl_eval_dense_rect: invalid weights");
+    return CTL_EINVAL;
+  }
+  RectSpec rs{bsgs_t(n, 1), fold};
+  return dense_common(c, k, in, W, bias, nullptr, nullptr, m, n, 0, 0.0, out, &rs);
+}
+
+extern "C" int ctl_eval_dense_rect_coeffs(ctl_context* c, const ctl_keys* k, const ctl_ct* in, const int64_t* pts,
+                                          uint32_t tm, uint32_t tn, const int64_t* bias, double pt_scale, int fold,
+                                          ctl_ct** out) {
+  if (!pts || tm == 0 || (tm & (tm - 1)) || !(pt_scale > 0)) {
+    set_error("ctl_eval_dense_rect_coeffs: invalid plaintexts");
+    return CTL_EINVAL;
+  }
+  RectSpec rs{tn, fold};
+  return dense_common(c, k, in, nullptr, nullptr, pts, bias, tm, tn, tm, pt_scale, out, &rs);
 }
 
 extern "C" int ctl_eval_dense_coeffs(ctl_context* c, const ctl_keys* k, const ctl_ct* in, const int64_t* pts,
@@ -2166,6 +2266,7 @@ struct LayerPlan {
   double poly[4] = {0, 0, 0, 0};  // poly3: a0..a3
   uint32_t pool_f = 0;            // avgpool: size f
   uint32_t rep_t = 0;
+  bool skip = false;              // a replicate already done by the preceding rectangular fold
   uint32_t in_level = 0;
   double in_scale = 0, out_scale = 0;
 };
@@ -2210,25 +2311,53 @@ extern "C" int ctl_model_create(ctl_context* c, const ctl_layer* layers, uint32_
     }
     return rc;
   };
+  std::vector<bool> skip(n_layers, false);
   for (uint32_t i = 0; i < n_layers; i++) {
     const ctl_layer& ly = layers[i];
     LayerPlan P;
     P.kind = ly.kind;
     P.in_level = lvl;
     P.in_scale = sc;
+    if (skip[i]) {  // the replicate the preceding rectangular dense layer's fold produced
+      P.skip = true;
+      P.rep_t = ly.rep_t;
+      P.out_scale = sc;
+      M->layers.push_back(P);
+      continue;
+    }
     if (ly.kind == CTL_LAYER_DENSE) {
       if (ly.m == 0 || ly.n == 0 || (!ly.W && !ly.pt_coeffs)) {
         set_error("ctl_model_create: dense layer %u needs W or coefficients", i);
         return fail(CTL_EINVAL);
       }
-      const uint32_t t = bsgs_t(ly.m, ly.n);
-      if (int rc = dense_prepare(c, P.dense, ly.W, ly.bias, ly.pt_coeffs, nullptr, ly.m, ly.n, t, lvl, sc, 0.0)) {
+      // CTL_DENSE_RECT: a layer whose padded output side tm is below its input side tn
+      // takes the rectangular form; when the next layers are [square,] replicate(tm), the
+      // fold also forms the [y, y] layout and that replicate is not run again
+      const uint32_t tm = bsgs_t(ly.m, 1), tn = bsgs_t(ly.n, 1);
+      RectSpec rs{tn, 1};
+      // (injected coefficients are then the tm rectangular diagonals)
+      const bool rect = c->dense_mode == CTL_DENSE_RECT && tm < tn && c->windows == 1;
+      if (rect) {
+        uint32_t j = i + 1;
+        if (j < n_layers && layers[j].kind == CTL_LAYER_SQUARE) j++;
+        if (j < n_layers && layers[j].kind == CTL_LAYER_REPLICATE && layers[j].rep_t == tm) {
+          rs.fold = 2;
+          skip[j] = true;
+        }
+      }
+      const uint32_t t = rect ? tm : bsgs_t(ly.m, ly.n);
+      if (int rc = dense_prepare(c, P.dense, ly.W, ly.bias, ly.pt_coeffs, nullptr, ly.m, ly.n, t, lvl, sc, 0.0,
+                                 rect ? &rs : nullptr)) {
         M->layers.push_back(P);
         return fail(rc);
       }
       M->bytes += (uint64_t)(P.dense.t + P.dense.t2) * (P.dense.lazy ? lvl + c->K : lvl) * c->N * 8;
       for (uint32_t j = 1; j < P.dense.t1; j++) rots.push_back((int32_t)j);
       for (uint32_t k = 1; k < P.dense.t2; k++) rots.push_back((int32_t)(k * P.dense.t1));
+      if (P.dense.rect) {
+        for (uint32_t sh = P.dense.tn / 2; sh >= P.dense.t; sh /= 2) rots.push_back((int32_t)sh);
+        if (P.dense.fold == 2) rots.push_back(-(int32_t)P.dense.t);
+      }
       sc = P.dense.out_scale;
       lvl--;
     } else if (ly.kind == CTL_LAYER_SQUARE) {
@@ -2351,6 +2480,7 @@ static int model_run(ctl_context* c, const ctl_model* M, const ctl_keys* k, cons
   uint32_t lvl = M->in_level;
   static const char* kLayerName[] = {"?", "dense", "square", "replicate", "conv1d", "poly3", "avgpool"};
   for (const LayerPlan& P : M->layers) {
+    if (P.skip) continue;
     u64* dst = bufs[w];
     int rc = CTL_OK;
     NvtxRange range(P.kind >= 1 && P.kind <= 6 ? kLayerName[P.kind] : kLayerName[0]);

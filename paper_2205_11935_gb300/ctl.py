@@ -83,6 +83,9 @@ SIGNATURES = {
     "ctl_eval_square": (C.c_int, [_vp, _vp, _vp, _pp]),
     "ctl_eval_dense": (C.c_int, [_vp, _vp, _vp, _dp, C.c_uint32, C.c_uint32, _dp, _pp]),
     "ctl_eval_dense_coeffs": (C.c_int, [_vp, _vp, _vp, _i64p, C.c_uint32, _i64p, C.c_double, _pp]),
+    "ctl_eval_dense_rect": (C.c_int, [_vp, _vp, _vp, _dp, C.c_uint32, C.c_uint32, _dp, C.c_int, _pp]),
+    "ctl_eval_dense_rect_coeffs": (C.c_int, [_vp, _vp, _vp, _i64p, C.c_uint32, C.c_uint32, _i64p, C.c_double,
+                                             C.c_int, _pp]),
     "ctl_replicate": (C.c_int, [_vp, _vp, _vp, C.c_uint32, _pp]),
     "ctl_add": (C.c_int, [_vp, _vp, _vp, _pp]),
     "ctl_mul_plain_coeffs": (C.c_int, [_vp, _vp, _i64p, C.c_double, _pp]),
@@ -270,9 +273,11 @@ class Context:
 
     DENSE_COMPOSED = 0
     DENSE_LAZY_MODDOWN = 1
+    DENSE_RECT = 2
 
     def set_dense_mode(self, mode):
-        """Dense layers created afterwards: DENSE_COMPOSED (default) or DENSE_LAZY_MODDOWN."""
+        """Dense layers created afterwards: DENSE_COMPOSED (default), DENSE_LAZY_MODDOWN or
+        DENSE_RECT (rectangular form for layers whose output side is the shorter)."""
         _check(lib().ctl_set_dense_mode(self.h, int(mode)))
 
     NTT_R32 = 0
@@ -420,6 +425,18 @@ class Context:
 
     def replicate(self, keys, ct, t):
         return self._op(lib().ctl_replicate, self.h, keys.h, ct.h, t)
+
+    def dense_rect(self, keys, ct, W, bias=None, fold=2):
+        W = np.ascontiguousarray(W, dtype=np.float64)
+        m, n = W.shape
+        bp = _p(np.ascontiguousarray(bias, dtype=np.float64), _dp) if bias is not None else None
+        return self._op(lib().ctl_eval_dense_rect, self.h, keys.h, ct.h, _p(W, _dp), m, n, bp, int(fold))
+
+    def dense_rect_coeffs(self, keys, ct, pts, tn, pt_scale, bias=None, fold=2):
+        pts = np.ascontiguousarray(pts, dtype=np.int64)
+        bp = _p(np.ascontiguousarray(bias, dtype=np.int64), _i64p) if bias is not None else None
+        return self._op(lib().ctl_eval_dense_rect_coeffs, self.h, keys.h, ct.h, _p(pts, _i64p), pts.shape[0], int(tn),
+                        bp, pt_scale, int(fold))
 
     def add(self, a, b):
         return self._op(lib().ctl_add, self.h, a.h, b.h)

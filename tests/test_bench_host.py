@@ -44,8 +44,15 @@ def test_operation_plan_follows_the_papers_counts():
     rots = sum(p[0] for p in plan)
     assert rots == 8 + 62 + 1 + 2 + 2 + 62  # conv, dense, replicate, ReLU (2 relins), pool, dense
     assert [p[3] for p in plan] == [7, 6, 5, 5, 4, 3, 2]
+    # the batched network in the rectangular form: 1024->256 (t1 = t2 = 16, fold of 2 rotations
+    # plus the [y, y] one), x^2, 256->256 (30 + replicate), x^2, 256->64 (t1 = t2 = 8, fold 2)
     plan = bench.op_plan(bench.WORKLOADS["batched"])
-    assert sum(p[1] for p in plan if p[1] >= 1) >= 1024 + 256 + 256
+    assert sum(p[0] for p in plan) == (30 + 3) + 1 + (30 + 1) + 1 + (14 + 2)
+    assert sum(p[1] for p in plan) == 256 + 1.5 + 256 + 1.5 + 64
+    sq = dict(bench.WORKLOADS["batched"], dense_form="square")
+    plan = bench.op_plan(sq)
+    assert sum(p[0] for p in plan) == 62 + 1 + 1 + 30 + 1 + 1 + 30
+    assert sum(p[1] for p in plan) == 1024 + 1.5 + 256 + 1.5 + 256
 
 
 def test_cpu_baseline_runs_a_whole_oracle_forward_on_small_rings():

@@ -198,3 +198,28 @@ def _cached_dense(o, ct, pts):
     if key not in _DENSE_EXP:
         _DENSE_EXP[key] = o.dense(ct, pts)[0]
     return _DENSE_EXP[key]
+
+
+def test_dense_rect_full_size_bit_exact():
+    """The rectangular form at N = 16384 with the batched workload's primes: a 16 x 64 layer
+    (tm = 16, tn = 64: 6 BSGS rotations, a fold of two and the [y, y] rotation), bit-exact
+    against the oracle alone and as member 2 of a batch of 3."""
+    m, n = 16, 64
+    rots = O.Oracle.rect_rotations(m, n, 2)
+    o, g, k = _full_pair(rots)
+    N = 16384
+    rng = np.random.default_rng(1664)
+    W = rng.normal(0, 1 / np.sqrt(n), (m, n))
+    cts = []
+    for i in range(3):
+        x = rng.uniform(-1, 1, n)
+        slots = np.zeros(N // 2)
+        slots[:n] = x
+        slots[n:2 * n] = x
+        cts.append(o.encrypt(o.encode(slots), 800 + i))
+    sc = o.dense_scale(8)
+    pts = o.encode_diagonals_rect(W, sc)
+    exp = o.dense_rect(cts[2], pts, n, fold=2)[0]
+    assert np.array_equal(g.dense_rect_coeffs(k, g.ct_import(cts[2], 2.0 ** 40), pts, n, sc, fold=2).export()[0], exp)
+    out = g.dense_rect_coeffs(k, g.ct_import(np.stack(cts), 2.0 ** 40), pts, n, sc, fold=2).export()
+    assert np.array_equal(out[2], exp)

@@ -557,3 +557,143 @@ def test_full_size_networks_properties(name, N, qb, pb, dnum, dims, B):
         assert np.array_equal(model.forward(k, cts[i]).export()[0], got[i])
     assert np.array_equal(model.forward(k, batch, graph=True).export(), got)
     assert np.array_equal(model.forward(k, batch).export(), got)
+
+
+# ----------------------------------------------------------------------------- rectangular form
+def rect_case(P, m, n, seed):
+    rng = np.random.default_rng(seed)
+    tn = O.Oracle.bsgs_t(n, 1)
+    W = rng.normal(0, 1 / np.sqrt(n), (m, n))
+    x = rng.uniform(-1, 1, n)
+    slots = np.zeros(P.N // 2)
+    slots[:n] = x
+    slots[tn:tn + n] = x
+    _, ct_o = P.fresh(seed, z=slots)
+    return W, x, tn, ct_o
+
+
+@pytest.mark.parametrize("fold", [0, 1, 2])
+@pytest.mark.parametrize("name,m,n", [("a1", 4, 16), ("a2", 8, 64), ("a2", 3, 40), ("c2", 32, 128), ("c2", 1, 64)])
+def test_dense_rect_bit_exact_and_fp64(name, m, n, fold):
+    """The rectangular form (tm < tn) against the oracle's, bit-exact, with its operation
+    counts; the library's own encoding decodes to W x in slots [0, m) (and [tm, tm + m)
+    with fold 2)."""
+    P = pair(name)
+    rots = sorted(set(O.Oracle.rect_rotations(m, n, fold)))
+    o = O.Oracle(P.N, *PARAMS[name][1:3], dnum=PARAMS[name][3], scale=2.0 ** 40)
+    o.keygen(rots, seed=3)
+    g = P.g
+    k = g.keygen(rots, seed=3)
+    W, x, tn, ct_o = rect_case(P, m, n, 170 + m)
+    tm = O.Oracle.bsgs_t(m, 1)
+    sc = o.dense_scale(ct_o.shape[1])
+    pts = o.encode_diagonals_rect(W, sc)
+    exp, cnt = o.dense_rect(ct_o, pts, tn, fold=fold)
+    ct = g.ct_import(ct_o, 2.0 ** 40)
+    g.stats_reset()
+    out = g.dense_rect_coeffs(k, ct, pts, tn, sc, fold=fold)
+    ops = g.stats_ops()
+    assert np.array_equal(out.export()[0], exp)
+    assert ops["rotations"] == cnt[0] and ops["ptmul"] == cnt[1] and ops["add"] == cnt[2]
+    if fold:
+        y = g.decrypt(k, g.dense_rect(k, ct, W, fold=fold), P.N // 2)
+        assert np.max(np.abs(y[:m] - W @ x)) < TOL
+        if fold == 2:
+            assert np.max(np.abs(y[tm:tm + m] - W @ x)) < TOL
+    k.close()
+
+
+def test_dense_rect_arguments():
+    P = pair("a2")
+    W = np.ones((16, 16))
+    ct = P.g.ct_import(P.fresh(5)[1], 2.0 ** 40)
+    with pytest.raises(ctl.CtlError):
+        P.g.dense_rect(P.k, ct, W)  # tm = tn: not rectangular
+    with pytest.raises(ctl.CtlError):
+        P.g.dense_rect(P.k, ct, np.ones((4, 128)))  # 2 tn > N/2
+
+
+def oracle_forward_rect(o, ct, layers):
+    """The oracle's forward under the rectangular mode: a dense layer with tm < tn takes
+    the rectangular form, with fold 2 (and the next replicate(tm) not run) when
+    [square,] replicate(tm) follows it."""
+    sc, skip = o.scale, set()
+    for i, ly in enumerate(layers):
+        lvl = ct.shape[1]
+        if i in skip:
+            continue
+        if ly[0] == "dense":
+            m, n = ly[1].shape
+            tm, tn = O.Oracle.bsgs_t(m, 1), O.Oracle.bsgs_t(n, 1)
+            if tm < tn:
+                j = i + 1
+                if j < len(layers) and layers[j][0] == "square":
+                    j += 1
+                fold = 1
+                if j < len(layers) and layers[j][0] == "replicate" and layers[j][1] == tm:
+                    fold = 2
+                    skip.add(j)
+                pts = o.encode_diagonals_rect(ly[1], o.dense_scale(lvl, sc))
+                ct = o.dense_rect(ct, pts, tn, fold=fold)[0]
+            else:
+                ct = o.dense(ct, o.encode_diagonals(ly[1], o.dense_scale(lvl, sc)))[0]
+            sc = o.scale
+        elif ly[0] == "square":
+            ct = o.square(ct)
+            sc = o.square_scale(lvl, sc)
+        else:
+            ct = o.replicate(ct, ly[1])
+    return ct, sc
+
+
+def inject_rect(o, layers):
+    out, sc, lvl = [], o.scale, o.L
+    for ly in layers:
+        if ly[0] == "dense":
+            m, n = ly[1].shape
+            rect = O.Oracle.bsgs_t(m, 1) < O.Oracle.bsgs_t(n, 1)
+            pts = (o.encode_diagonals_rect(ly[1], o.dense_scale(lvl, sc)) if rect
+                   else o.encode_diagonals(ly[1], o.dense_scale(lvl, sc)))
+            out.append(("dense", ly[1], None, pts))
+            sc = o.scale
+            lvl -= 1
+        elif ly[0] == "square":
+            out.append(ly)
+            sc = o.square_scale(lvl, sc)
+            lvl -= 1
+        else:
+            out.append(ly)
+    return out
+
+
+@pytest.mark.parametrize("N,qb,pb,dnum,dims", [
+    (256, [60, 40, 40, 40], [60], 4, [16, 8, 4]),
+    (512, [45, 45, 45, 45, 45, 45], [60, 60], 3, [64, 16, 16, 4]),
+])
+def test_network_rect_bit_exact_and_fp64(N, qb, pb, dnum, dims):
+    """A model under CTL_DENSE_RECT (the batched network's shape: shrinking layers take the
+    rectangular form, the first one's fold forms the next layer's [y, y]) against the
+    oracle's composition of the same layers, bit-exact, and FP64 within the tolerance."""
+    layers, slots, ref = network_case(N, qb, pb, dnum, dims)
+    t0 = O.Oracle.bsgs_t(dims[0], 1)
+    slots = np.zeros(N // 2)
+    x = network_case(N, qb, pb, dnum, dims)[1][:dims[0]]
+    slots[:dims[0]] = x
+    slots[t0:t0 + dims[0]] = x
+    g = ctl.Context(N, qb, pb, dnum=dnum, scale=2.0 ** 40)
+    g.set_dense_mode(g.DENSE_RECT)
+    o = O.Oracle(N, qb, pb, dnum=dnum, scale=2.0 ** 40)
+    model = ctl.Model(g, inject_rect(o, layers))
+    rots = model.rotations()
+    o.keygen(rots, seed=3)
+    k = g.keygen(rots, seed=3)
+    ct_o = o.encrypt(o.encode(slots), 4)
+    exp, sc = oracle_forward_rect(o, ct_o, layers)
+    out = model.forward(k, g.ct_import(ct_o, 2.0 ** 40))
+    assert np.array_equal(out.export()[0], exp)
+    assert np.array_equal(model.forward(k, g.ct_import(ct_o, 2.0 ** 40), graph=True).export()[0], exp)
+    y = g.decrypt(k, out, len(ref))
+    assert np.max(np.abs(y - ref)) < TOL
+    model2 = ctl.Model(g, layers)  # the library's own encoding
+    y2 = g.decrypt(k, model2.forward(k, g.encrypt(k, slots, 4)), len(ref))
+    assert np.max(np.abs(y2 - ref)) < TOL
