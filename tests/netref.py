@@ -73,3 +73,30 @@ def replicated_slots(x, t, n_slots):
     s[:len(x)] = x
     s[t:t + len(x)] = x
     return s
+
+
+def keyswitch_slot_sigma(N, digit_bits, p_bits, log_scale, var_e=10.5):
+    """Standard deviation of one slot's decoded error after one hybrid key switch of a
+    ciphertext at scale 2^log_scale.  The key product adds sum_d ModUp_d(c1) * e_d: each
+    coefficient of ModUp_d is uniform below q_d (second moment q_d^2 / 3), each error
+    coefficient has variance var_e (centred binomial k = 21: 21/2), and a negacyclic
+    product sums N such terms, so a coefficient's variance is N var_e sum_d q_d^2 / 3 before
+    ModDown divides it by P.  A slot is a sum of N coefficients times unit-modulus roots,
+    so its real part has sqrt(N/2) times the coefficient's deviation; decoding divides by
+    the scale.  (The ModDown rounding and the encryption noise are far smaller at the
+    parameter sets used here.)"""
+    P2 = float(2 ** (2 * sum(p_bits)))
+    s = sum(float(2 ** (2 * b)) for b in digit_bits) / P2
+    coef_sd = (N * var_e * s / 3.0) ** 0.5
+    return coef_sd * (N / 2) ** 0.5 / 2.0 ** log_scale
+
+
+def keyswitch_error_bound(N, digit_bits, p_bits, log_scale, n_ks, n_outputs, k=None):
+    """Max-abs bound over n_outputs slots for an output that accumulates n_ks independent
+    key-switch errors at the input scale (unit-norm weight rows carry each through): a
+    Gaussian tail at k standard deviations, k = sqrt(2 ln(n_outputs)) + 2 by default."""
+    import math
+
+    if k is None:
+        k = math.sqrt(2.0 * math.log(max(n_outputs, 2))) + 2.0
+    return k * math.sqrt(n_ks) * keyswitch_slot_sigma(N, digit_bits, p_bits, log_scale)

@@ -304,3 +304,19 @@ def test_dense_rect_rejects_square_shapes():
     o = ctx(N=256, rots=[1])
     with pytest.raises(RuntimeError):
         o.encode_diagonals_rect(np.ones((16, 16)), o.dense_scale(4))
+
+
+def test_keyswitch_noise_matches_its_derivation():
+    # The CryptoTL_p1 tolerances rest on netref.keyswitch_slot_sigma: the decoded error
+    # that one key switch adds at scale 2^25 (N = 256, the paper's p1 prime sizes).  The
+    # measured deviation of rot_1's slot errors must agree with it within a factor of 2.
+    o = ctx(N=256, q_bits=[34] + [25] * 6, p_bits=[34], rots=[1], dnum=7, scale=2.0 ** 25)
+    sd = netref.keyswitch_slot_sigma(256, [34] + [25] * 6, [34], 25)
+    errs = []
+    rng = np.random.default_rng(25)
+    for t in range(4):
+        z = rng.uniform(-1, 1, 128)
+        ct = enc(o, z, 40 + t)
+        errs.append(dec(o, o.rotate(ct, 1), 2.0 ** 25) - np.roll(z, -1))
+    got = float(np.std(np.concatenate(errs)))
+    assert 0.5 * sd < got < 2.0 * sd, (got, sd)
