@@ -605,6 +605,41 @@ def single_query_point(ctl, torch, name, steps):
     return res
 
 
+def client_round_trip_point(ctl, torch, ctx, model, keys, slots, m_out, steps):
+    """The whole protocol for a batch, client side on the device too: the slot vectors
+    copied from pinned host memory, encoded and encrypted on the GPU (ctl_encrypt_dev), the
+    forward (graph), decrypted and decoded on the GPU (ctl_decrypt_dev), and the outputs
+    copied back to pinned host memory, every step."""
+    B, nz = slots.shape
+    host_in = torch.from_numpy(np.ascontiguousarray(slots)).pin_memory()
+    host_out = torch.empty((B, m_out), dtype=torch.float64).pin_memory()
+    z_dev = torch.empty((B, nz), dtype=torch.float64, device="cuda")
+    y_dev = torch.empty((B, m_out), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def one(step):
+        z_dev.copy_(host_in, non_blocking=True)
+        stream.synchronize()
+        ct = ctx.encrypt_dev(keys, z_dev.data_ptr(), nz, B, [1000003 * step + b for b in range(B)])
+        out = model.forward(keys, ct, graph=True)
+        ctx.decrypt_dev(keys, out, m_out, y_dev.data_ptr())
+        ctx.synchronize()
+        host_out.copy_(y_dev, non_blocking=True)
+        torch.cuda.synchronize()
+        ct.close()
+        out.close()
+
+    one(0)
+    t0 = time.perf_counter()
+    for s in range(steps):
+        one(s + 1)
+    secs = time.perf_counter() - t0
+    return {"value": B * steps / secs, "unit": "forwards/s", "steps": steps, "batch": B,
+            "h2d_bytes_per_step": int(host_in.numel() * 8), "d2h_bytes_per_step": int(host_out.numel() * 8),
+            "desc": "host FP64 slots -> device encode + encrypt (ctl_encrypt_dev) -> forward (graph) -> device "
+                    "decrypt + decode (ctl_decrypt_dev) -> host FP64 outputs, every step (wall clock)"}
+
+
 def serving_point(ctl, rate, seconds, n_clients):
     """One arrival rate of configuration 5 (see run_serving), fewer clients and seconds."""
     ns = argparse.Namespace(mem_budget_gb=160.0, workers=4, max_batch=64, clients=n_clients, rates=[rate],
@@ -1026,6 +1061,7 @@ def main():
                   for name in ("single4096", "single8192", "batched")}
         others["batched"]["desc"] = "the batched network, one query per forward (batch 1)"
         others["serving"] = serving_point(ctl, args.serve_rate, args.serve_seconds, args.serve_clients)
+        others["client_round_trip"] = client_round_trip_point(ctl, torch, ctx, model, keys, slots, m_out, 3)
 
     if rank == 0:
         lat = sorted(step_ms)

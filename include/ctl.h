@@ -108,6 +108,8 @@ int ctl_synchronize(ctl_context* ctx);
  *     log2(tn/tm)-rotation fold).  In a model, when such a layer is followed by
  *     [square,] replicate(tm), the fold also forms the [y, y] layout (fold 2) and that
  *     replicate is not run again.  Layers with tm >= tn are as in the composed form.
+ *   CTL_DENSE_RECT_LAZY: as CTL_DENSE_RECT with Eq. (bsgs) of every layer (rectangular or
+ *     not) in the lazy-ModDown form and its split; the fold is the same.
  * The paper fixes neither choice (Sec. 3.1 only fixes t = t1 * t2 and the hoisting).  A
  * model keeps the mode it was created with.  Errors: CTL_EINVAL (unknown mode). */
 /* Register-resident NTT shapes for N = 4096 .. 16384 (other N use one shared-memory
@@ -150,6 +152,7 @@ int ctl_set_windows(ctl_context* ctx, uint32_t p);
 #define CTL_DENSE_COMPOSED 0
 #define CTL_DENSE_LAZY_MODDOWN 1
 #define CTL_DENSE_RECT 2
+#define CTL_DENSE_RECT_LAZY 3
 int ctl_set_dense_mode(ctl_context* ctx, int mode);
 
 /* ---------------------------------------------------------------------------------
@@ -184,9 +187,11 @@ uint64_t ctl_galois_element(const ctl_context* ctx, int64_t r);
  *   (host FP64 canonical embedding, round half away from zero).
  * ctl_encrypt: encodes x at the nominal scale and encrypts at the top level with the
  *   secret key: ct = (-a*s + m + e, a), a and e drawn from streams of `seed`.
- * ctl_encrypt_coeffs: the same from given integer coefficients m[N].
+ * ctl_encrypt_coeffs: the same from given integer coefficients m[N] (for N <= 16384 the
+ *   randomness is drawn on the device, as ctl_encrypt_coeffs_dev does).
  * ctl_decrypt: decrypts and decodes the first n slots into y[n] (synchronises).
- * ctl_decrypt_coeffs: the centred coefficients of c0 + c1*s as doubles, m[N].
+ * ctl_decrypt_coeffs: the centred coefficients of c0 + c1*s as doubles, m[N] (the CRT runs
+ *   on the device for N <= 16384).
  * ------------------------------------------------------------------------------- */
 int ctl_encode(ctl_context* ctx, const double* x, size_t n, double scale, int64_t* m);
 int ctl_decode(ctl_context* ctx, const double* m, size_t n, double scale, double* y);
@@ -194,6 +199,34 @@ int ctl_encrypt(ctl_context* ctx, const ctl_keys* keys, const double* x, size_t 
 int ctl_encrypt_coeffs(ctl_context* ctx, const ctl_keys* keys, const int64_t* m, uint64_t seed, ctl_ct** out);
 int ctl_decrypt(ctl_context* ctx, const ctl_keys* keys, const ctl_ct* ct, double* y, size_t n);
 int ctl_decrypt_coeffs(ctl_context* ctx, const ctl_keys* keys, const ctl_ct* ct, double* m);
+
+/* Client side on the device, for batches of queries (N <= 16384; CTL_EINVAL otherwise).
+ * All pointers named *_dev are device memory owned by the caller; seeds is a host array.
+ * ctl_encode_dev: count slot vectors z_dev[count][nz] -> integer coefficients
+ *   m_dev[count][N] at `scale`: the canonical embedding of Sec. 3.1 computed as one
+ *   length-N/2 FP64 FFT per vector (slot j at zeta^(5^j), zeta = exp(i pi / N)), rounded
+ *   half away from zero.  Agrees with ctl_encode within one unit per coefficient (two FP64
+ *   evaluation orders).  Synchronises; CTL_EINVAL if a coefficient leaves +-4e18.
+ * ctl_decode_dev: m_dev[count][N] (doubles) -> z_dev[count][nz], the real parts of the
+ *   slots divided by scale.  Asynchronous on the context stream.
+ * ctl_encrypt_coeffs_dev: encrypts m_dev[count][N] at the top level, ciphertext b with
+ *   seeds[b]: the uniform a and the centred binomial e are drawn on the device from the
+ *   same counter-based streams as ctl_encrypt_coeffs, so each ciphertext equals
+ *   ctl_encrypt_coeffs(m_b, seeds[b]) bit for bit.  Synchronises.
+ * ctl_encrypt_dev: ctl_encode_dev at the nominal scale, then ctl_encrypt_coeffs_dev.
+ * ctl_decrypt_coeffs_dev: the centred coefficients of c0 + c1*s of every ciphertext of ct
+ *   as doubles, m_dev[count][N] (Garner's mixed radix on the device).  Asynchronous.
+ * ctl_decrypt_dev: ctl_decrypt_coeffs_dev, then ctl_decode_dev at ct's scale into
+ *   z_dev[count][nz].  Asynchronous.
+ * Errors: CTL_EINVAL, CTL_EKEY (a key set without the secret), CTL_ENOMEM, CTL_ECUDA. */
+int ctl_encode_dev(ctl_context* ctx, const double* z_dev, size_t nz, uint32_t count, double scale, int64_t* m_dev);
+int ctl_decode_dev(ctl_context* ctx, const double* m_dev, uint32_t count, size_t nz, double scale, double* z_dev);
+int ctl_encrypt_coeffs_dev(ctl_context* ctx, const ctl_keys* keys, const int64_t* m_dev, uint32_t count,
+                           const uint64_t* seeds, ctl_ct** out);
+int ctl_encrypt_dev(ctl_context* ctx, const ctl_keys* keys, const double* z_dev, size_t nz, uint32_t count,
+                    const uint64_t* seeds, ctl_ct** out);
+int ctl_decrypt_coeffs_dev(ctl_context* ctx, const ctl_keys* keys, const ctl_ct* ct, double* m_dev);
+int ctl_decrypt_dev(ctl_context* ctx, const ctl_keys* keys, const ctl_ct* ct, size_t nz, double* z_dev);
 
 /* ---------------------------------------------------------------------------------
  * Ciphertext handles.  ctl_ct_import copies count ciphertexts [count][2][level][N]
@@ -305,8 +338,9 @@ int ctl_replicate(ctl_context* ctx, const ctl_keys* keys, const ctl_ct* in, uint
  * and t1 + t2 - 2 + log2(tn/tm) (+1) rotations, against tn products and about 2 sqrt(tn)
  * rotations for the square padding.  Needs the Galois keys of 1..t1-1, k*t1, the fold
  * shifts tn/2 .. tm and (fold 2) -tm.  bias (m values) is added before the rescale.
- * Errors: CTL_EINVAL (tm >= tn, 2 tn > N/2, windows > 1, the lazy-ModDown mode), CTL_EKEY,
- * CTL_ELEVEL.
+ * In the lazy-ModDown modes the sums of Eq. (bsgs) take that form and its split t1 =
+ * min(tm, 2^ceil(log2(4 tm)/2)); the fold is the same.
+ * Errors: CTL_EINVAL (tm >= tn, 2 tn > N/2, windows > 1), CTL_EKEY, CTL_ELEVEL.
  * ctl_eval_dense_rect_coeffs: the same with the tm plaintexts given as integer
  * coefficients pts[tm][N] (and bias as coefficients, nullable) at pt_scale. */
 int ctl_eval_dense_rect(ctl_context* ctx, const ctl_keys* keys, const ctl_ct* in, const double* W, uint32_t m,

@@ -939,10 +939,12 @@ int orc_dense_lazy(const orc_ctx* c, const orc_keys* k, const u64* ct, uint32_t 
 // slot r < tn the partial sum over the columns (r + i) mod tn of row r mod tm, and
 // y[j] = sum_{k < tn/tm} z[j + k tm].  They are placed as in Eq. (bsgs):
 // rd'_i = rot_{-floor(i/t1) t1}(rd_i) with rd_i in slots [0, tn) and t1 = orc_bsgs_t1(tm).
-int orc_encode_diagonals_rect(const orc_ctx* c, const double* W, uint32_t m, uint32_t n, double scale, i64* pts) {
+// lazy = 1 places them for the lazy-ModDown form's split t1 = orc_bsgs_t1_lazy(tm).
+int orc_encode_diagonals_rect_ex(const orc_ctx* c, const double* W, uint32_t m, uint32_t n, double scale, int lazy,
+                                 i64* pts) {
   const uint32_t tm = orc_bsgs_t(m, 1), tn = orc_bsgs_t(n, 1), ns = c->N / 2;
   if (tm >= tn || 2 * tn > ns) return -1;
-  const uint32_t t1 = orc_bsgs_t1(tm);
+  const uint32_t t1 = lazy ? orc_bsgs_t1_lazy(tm) : orc_bsgs_t1(tm);
   std::vector<double> v(ns);
   for (uint32_t i = 0; i < tm; i++) {
     std::fill(v.begin(), v.end(), 0.0);
@@ -956,6 +958,9 @@ int orc_encode_diagonals_rect(const orc_ctx* c, const double* W, uint32_t m, uin
   }
   return 0;
 }
+int orc_encode_diagonals_rect(const orc_ctx* c, const double* W, uint32_t m, uint32_t n, double scale, i64* pts) {
+  return orc_encode_diagonals_rect_ex(c, W, m, n, scale, 0, pts);
+}
 
 // Rectangular dense layer on the [x, x] layout over 2 tn slots, with the tm plaintexts of
 // orc_encode_diagonals_rect:
@@ -968,14 +973,17 @@ int orc_encode_diagonals_rect(const orc_ctx* c, const double* W, uint32_t m, uin
 // reads (the replicate of Sec. 3.1 "Multiple Predictions" taken into the fold).  Other
 // slots hold partial sums.  counters: rotations t1+t2-2 + log2(tn/tm) (+1), products tm,
 // additions tm-1 + log2(tn/tm) (+1).
-int orc_dense_rect(const orc_ctx* c, const orc_keys* k, const u64* ct, uint32_t lvl, const i64* pts, uint32_t tm,
-                   uint32_t tn, const i64* bias, int fold, u64* out, u64* counters) {
+// With lazy = 1, z' is the lazy-ModDown form of Eq. (bsgs) over the tm diagonals
+// (orc_dense_lazy, diagonals placed for its split) and the fold is the same.
+int orc_dense_rect_ex(const orc_ctx* c, const orc_keys* k, const u64* ct, uint32_t lvl, const i64* pts, uint32_t tm,
+                      uint32_t tn, const i64* bias, int fold, int lazy, u64* out, u64* counters) {
   if (tm == 0 || tm >= tn || (tm & (tm - 1)) || (tn & (tn - 1)) || fold < 0 || fold > 2 || lvl < 2) return -1;
   const uint32_t lo = lvl - 1;
   const size_t csz = (size_t)2 * lo * c->N;
   std::vector<u64> z(csz), r(csz);
   u64 cnt[3] = {0, 0, 0};
-  int rc = orc_dense(c, k, ct, lvl, pts, tm, bias, z.data(), cnt);
+  int rc = lazy ? orc_dense_lazy(c, k, ct, lvl, pts, tm, bias, z.data(), cnt)
+                : orc_dense(c, k, ct, lvl, pts, tm, bias, z.data(), cnt);
   if (rc) return rc;
   std::vector<u64> S = z;
   if (fold >= 1) {
@@ -997,6 +1005,10 @@ int orc_dense_rect(const orc_ctx* c, const orc_keys* k, const u64* ct, uint32_t 
   std::copy(S.begin(), S.end(), out);
   if (counters) { counters[0] = cnt[0]; counters[1] = cnt[1]; counters[2] = cnt[2]; }
   return 0;
+}
+int orc_dense_rect(const orc_ctx* c, const orc_keys* k, const u64* ct, uint32_t lvl, const i64* pts, uint32_t tm,
+                   uint32_t tn, const i64* bias, int fold, u64* out, u64* counters) {
+  return orc_dense_rect_ex(c, k, ct, lvl, pts, tm, tn, bias, fold, 0, out, counters);
 }
 
 // Replicate: y + rot_{-t}(y), which turns a vector held in slots [0, t) into [y, y].

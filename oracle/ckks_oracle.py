@@ -71,6 +71,10 @@ def _lib():
             "orc_dense_lazy": (C.c_int, [vp, vp, _u64p, C.c_uint32, _i64p, C.c_uint32, _i64p, _u64p, _u64p]),
             "orc_replicate": (C.c_int, [vp, vp, _u64p, C.c_uint32, C.c_uint32, _u64p]),
             "orc_encode_diagonals_rect": (C.c_int, [vp, _dp, C.c_uint32, C.c_uint32, C.c_double, _i64p]),
+            "orc_encode_diagonals_rect_ex": (C.c_int, [vp, _dp, C.c_uint32, C.c_uint32, C.c_double, C.c_int,
+                                                       _i64p]),
+            "orc_dense_rect_ex": (C.c_int, [vp, vp, _u64p, C.c_uint32, _i64p, C.c_uint32, C.c_uint32, _i64p, C.c_int,
+                                            C.c_int, _u64p, _u64p]),
             "orc_dense_rect": (C.c_int, [vp, vp, _u64p, C.c_uint32, _i64p, C.c_uint32, C.c_uint32, _i64p, C.c_int,
                                          _u64p, _u64p]),
             "orc_tensor": (C.c_int, [vp, _u64p, _u64p, C.c_uint32, _u64p]),
@@ -329,34 +333,36 @@ class Oracle:
                 _p(out, _u64p), _p(cnt, _u64p)), "dense")
         return out, [int(x) for x in cnt]
 
-    def encode_diagonals_rect(self, W, scale):
+    def encode_diagonals_rect(self, W, scale, lazy=False):
         """The tm rectangular diagonals of a dense layer m x n with tm < tn (powers of two
-        >= m and >= n), placed as in Eq. (bsgs) with t1 = bsgs_t1(tm)."""
+        >= m and >= n), placed as in Eq. (bsgs) with t1 = bsgs_t1(tm, lazy)."""
         W = np.ascontiguousarray(W, dtype=np.float64)
         m, n = W.shape
         tm = self.bsgs_t(m, 1)
         out = np.zeros((tm, self.N), dtype=np.int64)
-        _chk(self.lib.orc_encode_diagonals_rect(self.h, _p(W, _dp), m, n, scale, _p(out, _i64p)), "encode_rect")
+        _chk(self.lib.orc_encode_diagonals_rect_ex(self.h, _p(W, _dp), m, n, scale, int(lazy), _p(out, _i64p)),
+             "encode_rect")
         return out
 
-    def dense_rect(self, ct, pts, tn, bias=None, fold=2):
-        """Rectangular dense layer: the composed Eq. (bsgs) over the tm = len(pts) diagonals,
-        the rescale, then fold = 1: the sum over the tn/tm blocks (y in slots [0, tm)),
-        fold = 2: and the [y, y] layout at block stride tm; fold = 0: no fold."""
+    def dense_rect(self, ct, pts, tn, bias=None, fold=2, lazy=False):
+        """Rectangular dense layer: Eq. (bsgs) over the tm = len(pts) diagonals (composed, or
+        the lazy-ModDown form with lazy=True), the rescale, then fold = 1: the sum over the
+        tn/tm blocks (y in slots [0, tm)), fold = 2: and the [y, y] layout at block stride
+        tm; fold = 0: no fold."""
         ct = _u64(ct); pts = _i64(pts); lvl = ct.shape[1]
         out = np.zeros((2, lvl - 1, self.N), dtype=np.uint64)
         cnt = np.zeros(3, dtype=np.uint64)
         bp = _p(_i64(bias), _i64p) if bias is not None else None
-        _chk(self.lib.orc_dense_rect(self.h, self.keys, _p(ct, _u64p), lvl, _p(pts, _i64p), pts.shape[0], tn, bp,
-                                     fold, _p(out, _u64p), _p(cnt, _u64p)), "dense_rect")
+        _chk(self.lib.orc_dense_rect_ex(self.h, self.keys, _p(ct, _u64p), lvl, _p(pts, _i64p), pts.shape[0], tn, bp,
+                                        fold, int(lazy), _p(out, _u64p), _p(cnt, _u64p)), "dense_rect")
         return out, [int(x) for x in cnt]
 
     @classmethod
-    def rect_rotations(cls, m, n, fold=2):
+    def rect_rotations(cls, m, n, fold=2, lazy=False):
         """Galois rotations of the rectangular form: the Eq. (bsgs) split of tm, the fold
         shifts tn/2 .. tm and, fold = 2, -tm."""
         tm, tn = cls.bsgs_t(m, 1), cls.bsgs_t(n, 1)
-        t1 = cls.bsgs_t1(tm)
+        t1 = cls.bsgs_t1(tm, lazy)
         rots = list(range(1, t1)) + [k * t1 for k in range(1, tm // t1)]
         if fold >= 1:
             s = tn // 2

@@ -84,24 +84,6 @@ void timing_end(ctl_context* c, int cls, cudaEvent_t ev, double work, double byt
 
 namespace {
 
-// Device buffer released (stream-ordered) at scope exit.
-struct DBuf {
-  ctl_context* c = nullptr;
-  u64* p = nullptr;
-  DBuf() = default;
-  DBuf(ctl_context* cc, size_t words) : c(cc) { p = (u64*)dev_alloc(cc, words * sizeof(u64)); }
-  ~DBuf() {
-    if (p) dev_free(c, p);
-  }
-  DBuf(const DBuf&) = delete;
-  DBuf& operator=(const DBuf&) = delete;
-  u64* release() {
-    u64* r = p;
-    p = nullptr;
-    return r;
-  }
-};
-
 #define CHECK_ARG(cond, msg)      \
   do {                            \
     if (!(cond)) {                \
@@ -109,19 +91,11 @@ struct DBuf {
       return CTL_EINVAL;          \
     }                             \
   } while (0)
-#define CHECK_ALLOC(buf)                                 \
-  do {                                                   \
-    if (!(buf).p) {                                      \
-      set_error("device allocation failed");             \
-      return CTL_ENOMEM;                                 \
-    }                                                    \
-  } while (0)
 
-int last_cuda(const char* what) { return cuda_check(cudaGetLastError(), what); }
 
-size_t ct_words(const ctl_context* c, uint32_t lvl, uint32_t count) { return (size_t)count * 2 * lvl * c->N; }
+}  // namespace
 
-ctl_ct* new_ct(ctl_context* c, uint32_t lvl, uint32_t count, double scale) {
+ctl_ct* ctl::new_ct(ctl_context* c, uint32_t lvl, uint32_t count, double scale) {
   ctl_ct* ct = new (std::nothrow) ctl_ct();
   if (!ct) return nullptr;
   ct->ctx = c;
@@ -136,6 +110,8 @@ ctl_ct* new_ct(ctl_context* c, uint32_t lvl, uint32_t count, double scale) {
   }
   return ct;
 }
+
+namespace {
 
 // Scale agreement up to FP64 rounding of the bookkeeping.
 bool same_scale(double a, double b) { return std::fabs(a - b) <= 1e-9 * std::max(std::fabs(a), std::fabs(b)); }
@@ -374,6 +350,7 @@ extern "C" int ctl_context_create(ctl_context** out, uint32_t N, const uint32_t*
   }
   c->enc.init(N);
   if ((rc = build_tables(c.get()))) return rc;
+  if ((rc = client_tables_create(c.get()))) return rc;
   if ((rc = ctl_autotune_ntt(c.get(), 0, nullptr, nullptr)) && rc != CTL_ENOMEM) return rc;
   *out = c.release();
   return CTL_OK;
@@ -388,6 +365,7 @@ extern "C" void ctl_context_destroy(ctl_context* c) {
   }
   for (auto e : c->timing.pool) cudaEventDestroy(e);
   if (!c->parent) {  // clones share the parent's tables
+    client_tables_destroy(c);
     cudaFree(c->d_primes);
     cudaFree(c->d_tw2);
     cudaFree(c->d_tables);
@@ -430,6 +408,7 @@ extern "C" int ctl_context_clone(const ctl_context* c, ctl_context** out) {
   k->moddown = c->moddown;
   k->d_md_scale = c->d_md_scale;
   k->d_mu_scale = c->d_mu_scale;
+  k->client = c->client;
   k->h_primes = c->h_primes;
   k->enc = c->enc;
   k->dense_mode = c->dense_mode;
@@ -497,7 +476,7 @@ extern "C" int ctl_set_allocator(ctl_context* c, ctl_alloc_fn a, ctl_free_fn f, 
 }
 
 extern "C" int ctl_set_dense_mode(ctl_context* c, int mode) {
-  if (!c || (mode != CTL_DENSE_COMPOSED && mode != CTL_DENSE_LAZY_MODDOWN && mode != CTL_DENSE_RECT)) {
+  if (!c || mode < CTL_DENSE_COMPOSED || mode > CTL_DENSE_RECT_LAZY) {
     set_error("ctl_set_dense_mode: invalid argument");
     return CTL_EINVAL;
   }
@@ -849,6 +828,12 @@ extern "C" int ctl_encrypt_coeffs(ctl_context* c, const ctl_keys* k, const int64
     return CTL_EKEY;
   }
   const uint32_t N = c->N, L = c->L;
+  if (c->client) {  // the device sampler (client.cu): the same streams, drawn on the GPU
+    DBuf md(c, N);
+    CHECK_ALLOC(md);
+    cudaMemcpyAsync(md.p, m, N * sizeof(u64), cudaMemcpyHostToDevice, c->stream);
+    return encrypt_coeffs_dev(c, k, (const i64*)md.p, 1, (const u64*)&seed, out);
+  }
   std::vector<u64> a((size_t)L * N);
   for (uint32_t i = 0; i < L; i++) {
     SplitMixStream sa(seed, stream_id_enc_a(i));
@@ -909,6 +894,13 @@ extern "C" int ctl_decrypt_coeffs(ctl_context* c, const ctl_keys* k, const ctl_c
     return CTL_EKEY;
   }
   const uint32_t N = c->N, lvl = ct->level;
+  if (c->client) {  // the centred CRT on the device (client.cu); ct's first ciphertext
+    DBuf md(c, (size_t)ct->count * N);
+    CHECK_ALLOC(md);
+    if (int rc = decrypt_coeffs_dev(c, k, ct, (double*)md.p)) return rc;
+    cudaMemcpyAsync(m, md.p, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    return cuda_check(cudaStreamSynchronize(c->stream), "decrypt");
+  }
   DBuf t(c, (size_t)lvl * N);
   CHECK_ALLOC(t);
   launch_decrypt_mul(c, ct->d, k->d_s, t.p, 1, (int)lvl);
@@ -1441,13 +1433,13 @@ int dense_prepare(ctl_context* c, DenseLayer& D, const double* W, const double* 
   if (rs) {
     D.tn = rs->tn;
     D.fold = rs->fold;
-    if (c->dense_mode == CTL_DENSE_LAZY_MODDOWN || c->windows != 1 || D.t >= D.tn || (D.tn & (D.tn - 1)) ||
-        2 * D.tn > c->N / 2 || rs->fold < 0 || rs->fold > 2) {
-      set_error("dense (rectangular): needs tm < tn (powers of two), 2 tn <= N/2, one window, the composed form");
+    if (c->windows != 1 || D.t >= D.tn || (D.tn & (D.tn - 1)) || 2 * D.tn > c->N / 2 || rs->fold < 0 ||
+        rs->fold > 2) {
+      set_error("dense (rectangular): needs tm < tn (powers of two), 2 tn <= N/2 and one window");
       return CTL_EINVAL;
     }
   }
-  D.lazy = c->dense_mode == CTL_DENSE_LAZY_MODDOWN;
+  D.lazy = c->dense_mode == CTL_DENSE_LAZY_MODDOWN || c->dense_mode == CTL_DENSE_RECT_LAZY;
   D.t1 = bsgs_t1(D.t, D.lazy);
   D.t2 = D.t / D.t1;
   D.lvl = lvl;
@@ -1540,6 +1532,8 @@ int rot_list(ctl_context* c, const ctl_keys* k, int64_t r0, int64_t step, int n,
 //   S = inner[0] + sum_{k >= 1} (sigma_{k t1}(inner[k].0) + ip'_k.0, ip'_k.1),
 //       ip'_k = key product of ModDown(inner[k].1) for rot_{k t1},
 //   out = rescale( ModDown(S) [+ bias] ),  batch nb.
+int rect_fold(ctl_context* c, const ctl_keys* k, const DenseLayer& D, u64* S, int nb, int lv);
+
 int dense_apply_lazy(ctl_context* c, const ctl_keys* k, const DenseLayer& D, const u64* in, int nb, u64* out) {
   const uint32_t N = c->N, lvl = D.lvl, t1 = D.t1, t2 = D.t2;
   const int E = (int)lvl + (int)c->K;
@@ -1603,7 +1597,9 @@ int dense_apply_lazy(ctl_context* c, const ctl_keys* k, const DenseLayer& D, con
   launch_ntt_inv_oop(c, inner.p, EN, inner.p, EN, 2 * nb, (int)lvl, E, (int)lvl, c->d_md_scale);
   launch_moddown_polys(c, inner.p, EN, 2 * nb, (int)lvl, acc.p, LN);
   if (D.bias) launch_add_plain(c, acc.p, D.bias, nb, (int)lvl, ctw);
-  return rescale_into(c, acc.p, nb, (int)lvl, out);
+  int rc = rescale_into(c, acc.p, nb, (int)lvl, out);
+  if (rc || !D.rect || D.fold == 0) return rc;
+  return rect_fold(c, k, D, out, nb, (int)lvl - 1);
 }
 
 // The fold of the rectangular form on the rescaled partial sums z' (level lv, batch nb,
@@ -1737,7 +1733,7 @@ extern "C" int ctl_eval_dense(ctl_context* c, const ctl_keys* k, const ctl_ct* i
   }
   // CTL_DENSE_RECT: the rectangular form (fold 1) when the padded output side is shorter
   const uint32_t tm = bsgs_t(m, 1), tn = bsgs_t(n, 1);
-  if (c && c->dense_mode == CTL_DENSE_RECT && tm < tn && c->windows == 1) {
+  if (c && (c->dense_mode == CTL_DENSE_RECT || c->dense_mode == CTL_DENSE_RECT_LAZY) && tm < tn && c->windows == 1) {
     RectSpec rs{tn, 1};
     return dense_common(c, k, in, W, bias, nullptr, nullptr, m, n, 0, 0.0, out, &rs);
   }
@@ -2336,7 +2332,8 @@ extern "C" int ctl_model_create(ctl_context* c, const ctl_layer* layers, uint32_
       const uint32_t tm = bsgs_t(ly.m, 1), tn = bsgs_t(ly.n, 1);
       RectSpec rs{tn, 1};
       // (injected coefficients are then the tm rectangular diagonals)
-      const bool rect = c->dense_mode == CTL_DENSE_RECT && tm < tn && c->windows == 1;
+      const bool rect = (c->dense_mode == CTL_DENSE_RECT || c->dense_mode == CTL_DENSE_RECT_LAZY) && tm < tn &&
+                        c->windows == 1;
       if (rect) {
         uint32_t j = i + 1;
         if (j < n_layers && layers[j].kind == CTL_LAYER_SQUARE) j++;

@@ -158,6 +158,10 @@ struct Timing {
 // ---------------------------------------------------------------------------------
 // Opaque handles of the C-ABI.
 // ---------------------------------------------------------------------------------
+namespace ctl {
+struct ClientTabs;
+}  // namespace ctl
+
 struct ctl_context {
   uint32_t N = 0, logN = 0, L = 0, K = 0, alpha = 1, beta = 1;
   double scale = 0;
@@ -190,7 +194,12 @@ struct ctl_context {
   uint64_t ks_budget = 16ull << 30;              // ctl_set_keyswitch_budget
   uint32_t windows = 1;                          // ctl_set_windows: prediction windows per ciphertext
   const ctl_context* parent = nullptr;  // clones share the parent's device tables
+  ctl::ClientTabs* client = nullptr;    // GPU encoder / sampler / CRT tables (client.cu)
 };
+
+namespace ctl {
+inline size_t ct_words(const ctl_context* c, uint32_t lvl, uint32_t count) { return (size_t)count * 2 * lvl * c->N; }
+}  // namespace ctl
 
 struct ctl_keys {
   ctl_context* ctx = nullptr;
@@ -225,8 +234,47 @@ struct NvtxRange {
 // ---------------------------------------------------------------------------------
 void* dev_alloc(ctl_context* c, size_t bytes);
 void dev_free(ctl_context* c, void* p);
+
+// Device buffer of `words` 64-bit words from the context's allocator, released
+// (stream-ordered) at scope exit.
+struct DBuf {
+  ctl_context* c = nullptr;
+  u64* p = nullptr;
+  DBuf() = default;
+  DBuf(ctl_context* cc, size_t words) : c(cc) { p = (u64*)dev_alloc(cc, words * sizeof(u64)); }
+  ~DBuf() {
+    if (p) dev_free(c, p);
+  }
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  u64* release() {
+    u64* r = p;
+    p = nullptr;
+    return r;
+  }
+};
+#define CHECK_ALLOC(buf)                     \
+  do {                                       \
+    if (!(buf).p) {                          \
+      set_error("device allocation failed"); \
+      return CTL_ENOMEM;                     \
+    }                                        \
+  } while (0)
+// A new ciphertext handle [count][2][lvl][N] at `scale` (null when allocation fails).
+ctl_ct* new_ct(ctl_context* c, uint32_t lvl, uint32_t count, double scale);
+inline size_t ct_words(const ctl_context* c, uint32_t lvl, uint32_t count);
+// The client tables (client.cu): created with the context for N <= 16384.
+struct ClientTabs;
+int client_tables_create(ctl_context* c);
+void client_tables_destroy(ctl_context* c);
+// Batch encryption of integer plaintexts m [count][N] (device) with the device sampler, and
+// decryption to centred coefficient values [count][N] (device doubles) (client.cu).
+int encrypt_coeffs_dev(ctl_context* c, const ctl_keys* k, const i64* m_dev, uint32_t count, const u64* seeds,
+                       ctl_ct** out);
+int decrypt_coeffs_dev(ctl_context* c, const ctl_keys* k, const ctl_ct* ct, double* m_dev);
 void set_error(const char* fmt, ...);
 int cuda_check(cudaError_t e, const char* what);
+inline int last_cuda(const char* what) { return cuda_check(cudaGetLastError(), what); }
 void timing_begin(ctl_context* c, int cls, cudaEvent_t* ev);
 void timing_end(ctl_context* c, int cls, cudaEvent_t ev, double work, double bytes = 0.0);
 

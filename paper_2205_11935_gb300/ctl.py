@@ -129,6 +129,12 @@ SIGNATURES = {
     "ctl_server_admission": (C.c_int, [_vp, C.c_uint32, _u64p, _u64p, _u64p]),
     "ctl_server_destroy": (None, [_vp]),
     "ctl_microbench_unit_rate": (C.c_int, [C.c_int, _dp]),
+    "ctl_encode_dev": (C.c_int, [_vp, _vp, _sz, C.c_uint32, C.c_double, _vp]),
+    "ctl_decode_dev": (C.c_int, [_vp, _vp, C.c_uint32, _sz, C.c_double, _vp]),
+    "ctl_encrypt_coeffs_dev": (C.c_int, [_vp, _vp, _vp, C.c_uint32, _u64p, _pp]),
+    "ctl_encrypt_dev": (C.c_int, [_vp, _vp, _vp, _sz, C.c_uint32, _u64p, _pp]),
+    "ctl_decrypt_coeffs_dev": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "ctl_decrypt_dev": (C.c_int, [_vp, _vp, _vp, _sz, _vp]),
     "ctl_modarith_eval": (C.c_int, [C.c_int, _u64p, _sz, C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64, _u64p]),
     "ctl_stats_reset": (C.c_int, [_vp]),
     "ctl_stats_enable_timing": (C.c_int, [_vp, C.c_int]),
@@ -274,6 +280,7 @@ class Context:
     DENSE_COMPOSED = 0
     DENSE_LAZY_MODDOWN = 1
     DENSE_RECT = 2
+    DENSE_RECT_LAZY = 3
 
     def set_dense_mode(self, mode):
         """Dense layers created afterwards: DENSE_COMPOSED (default), DENSE_LAZY_MODDOWN or
@@ -380,6 +387,33 @@ class Context:
         m = np.zeros(self.N, dtype=np.float64)
         _check(lib().ctl_decrypt_coeffs(self.h, keys.h, ct.h, _p(m, _dp)))
         return m
+
+    # --- the client side on the device (pointers are device addresses, e.g. data_ptr()) ---
+    def encode_dev(self, z_ptr, nz, count, m_ptr, scale=None):
+        _check(lib().ctl_encode_dev(self.h, C.c_void_p(z_ptr), nz, count, self.scale if scale is None else scale,
+                                    C.c_void_p(m_ptr)))
+
+    def decode_dev(self, m_ptr, count, nz, z_ptr, scale=None):
+        _check(lib().ctl_decode_dev(self.h, C.c_void_p(m_ptr), count, nz, self.scale if scale is None else scale,
+                                    C.c_void_p(z_ptr)))
+
+    def encrypt_coeffs_dev(self, keys, m_ptr, count, seeds):
+        sd = np.ascontiguousarray(seeds, dtype=np.uint64)
+        h = C.c_void_p()
+        _check(lib().ctl_encrypt_coeffs_dev(self.h, keys.h, C.c_void_p(m_ptr), count, _p(sd, _u64p), C.byref(h)))
+        return Ciphertext(self, h)
+
+    def encrypt_dev(self, keys, z_ptr, nz, count, seeds):
+        sd = np.ascontiguousarray(seeds, dtype=np.uint64)
+        h = C.c_void_p()
+        _check(lib().ctl_encrypt_dev(self.h, keys.h, C.c_void_p(z_ptr), nz, count, _p(sd, _u64p), C.byref(h)))
+        return Ciphertext(self, h)
+
+    def decrypt_coeffs_dev(self, keys, ct, m_ptr):
+        _check(lib().ctl_decrypt_coeffs_dev(self.h, keys.h, ct.h, C.c_void_p(m_ptr)))
+
+    def decrypt_dev(self, keys, ct, nz, z_ptr):
+        _check(lib().ctl_decrypt_dev(self.h, keys.h, ct.h, nz, C.c_void_p(z_ptr)))
 
     def ct_import(self, coeffs, scale):
         a = np.ascontiguousarray(coeffs, dtype=np.uint64)

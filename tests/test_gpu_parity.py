@@ -572,14 +572,15 @@ def rect_case(P, m, n, seed):
     return W, x, tn, ct_o
 
 
+@pytest.mark.parametrize("lazy", [False, True])
 @pytest.mark.parametrize("fold", [0, 1, 2])
 @pytest.mark.parametrize("name,m,n", [("a1", 4, 16), ("a2", 8, 64), ("a2", 3, 40), ("c2", 32, 128), ("c2", 1, 64)])
-def test_dense_rect_bit_exact_and_fp64(name, m, n, fold):
+def test_dense_rect_bit_exact_and_fp64(name, m, n, fold, lazy):
     """The rectangular form (tm < tn) against the oracle's, bit-exact, with its operation
-    counts; the library's own encoding decodes to W x in slots [0, m) (and [tm, tm + m)
-    with fold 2)."""
+    counts, in the composed and the lazy-ModDown forms; the library's own encoding decodes
+    to W x in slots [0, m) (and [tm, tm + m) with fold 2)."""
     P = pair(name)
-    rots = sorted(set(O.Oracle.rect_rotations(m, n, fold)))
+    rots = sorted(set(O.Oracle.rect_rotations(m, n, fold, lazy)))
     o = O.Oracle(P.N, *PARAMS[name][1:3], dnum=PARAMS[name][3], scale=2.0 ** 40)
     o.keygen(rots, seed=3)
     g = P.g
@@ -587,19 +588,23 @@ def test_dense_rect_bit_exact_and_fp64(name, m, n, fold):
     W, x, tn, ct_o = rect_case(P, m, n, 170 + m)
     tm = O.Oracle.bsgs_t(m, 1)
     sc = o.dense_scale(ct_o.shape[1])
-    pts = o.encode_diagonals_rect(W, sc)
-    exp, cnt = o.dense_rect(ct_o, pts, tn, fold=fold)
+    pts = o.encode_diagonals_rect(W, sc, lazy)
+    exp, cnt = o.dense_rect(ct_o, pts, tn, fold=fold, lazy=lazy)
     ct = g.ct_import(ct_o, 2.0 ** 40)
-    g.stats_reset()
-    out = g.dense_rect_coeffs(k, ct, pts, tn, sc, fold=fold)
-    ops = g.stats_ops()
-    assert np.array_equal(out.export()[0], exp)
-    assert ops["rotations"] == cnt[0] and ops["ptmul"] == cnt[1] and ops["add"] == cnt[2]
-    if fold:
-        y = g.decrypt(k, g.dense_rect(k, ct, W, fold=fold), P.N // 2)
-        assert np.max(np.abs(y[:m] - W @ x)) < TOL
-        if fold == 2:
-            assert np.max(np.abs(y[tm:tm + m] - W @ x)) < TOL
+    g.set_dense_mode(g.DENSE_RECT_LAZY if lazy else g.DENSE_RECT)
+    try:
+        g.stats_reset()
+        out = g.dense_rect_coeffs(k, ct, pts, tn, sc, fold=fold)
+        ops = g.stats_ops()
+        assert np.array_equal(out.export()[0], exp)
+        assert ops["rotations"] == cnt[0] and ops["ptmul"] == cnt[1] and ops["add"] == cnt[2]
+        if fold:
+            y = g.decrypt(k, g.dense_rect(k, ct, W, fold=fold), P.N // 2)
+            assert np.max(np.abs(y[:m] - W @ x)) < TOL
+            if fold == 2:
+                assert np.max(np.abs(y[tm:tm + m] - W @ x)) < TOL
+    finally:
+        g.set_dense_mode(g.DENSE_COMPOSED)
     k.close()
 
 
@@ -613,10 +618,10 @@ def test_dense_rect_arguments():
         P.g.dense_rect(P.k, ct, np.ones((4, 128)))  # 2 tn > N/2
 
 
-def oracle_forward_rect(o, ct, layers):
+def oracle_forward_rect(o, ct, layers, lazy=False):
     """The oracle's forward under the rectangular mode: a dense layer with tm < tn takes
     the rectangular form, with fold 2 (and the next replicate(tm) not run) when
-    [square,] replicate(tm) follows it."""
+    [square,] replicate(tm) follows it; lazy: every Eq. (bsgs) in the lazy-ModDown form."""
     sc, skip = o.scale, set()
     for i, ly in enumerate(layers):
         lvl = ct.shape[1]
@@ -633,10 +638,10 @@ def oracle_forward_rect(o, ct, layers):
                 if j < len(layers) and layers[j][0] == "replicate" and layers[j][1] == tm:
                     fold = 2
                     skip.add(j)
-                pts = o.encode_diagonals_rect(ly[1], o.dense_scale(lvl, sc))
-                ct = o.dense_rect(ct, pts, tn, fold=fold)[0]
+                pts = o.encode_diagonals_rect(ly[1], o.dense_scale(lvl, sc), lazy)
+                ct = o.dense_rect(ct, pts, tn, fold=fold, lazy=lazy)[0]
             else:
-                ct = o.dense(ct, o.encode_diagonals(ly[1], o.dense_scale(lvl, sc)))[0]
+                ct = o.dense(ct, o.encode_diagonals(ly[1], o.dense_scale(lvl, sc), lazy), lazy=lazy)[0]
             sc = o.scale
         elif ly[0] == "square":
             ct = o.square(ct)
@@ -646,14 +651,14 @@ def oracle_forward_rect(o, ct, layers):
     return ct, sc
 
 
-def inject_rect(o, layers):
+def inject_rect(o, layers, lazy=False):
     out, sc, lvl = [], o.scale, o.L
     for ly in layers:
         if ly[0] == "dense":
             m, n = ly[1].shape
             rect = O.Oracle.bsgs_t(m, 1) < O.Oracle.bsgs_t(n, 1)
-            pts = (o.encode_diagonals_rect(ly[1], o.dense_scale(lvl, sc)) if rect
-                   else o.encode_diagonals(ly[1], o.dense_scale(lvl, sc)))
+            pts = (o.encode_diagonals_rect(ly[1], o.dense_scale(lvl, sc), lazy) if rect
+                   else o.encode_diagonals(ly[1], o.dense_scale(lvl, sc), lazy))
             out.append(("dense", ly[1], None, pts))
             sc = o.scale
             lvl -= 1
@@ -666,11 +671,12 @@ def inject_rect(o, layers):
     return out
 
 
+@pytest.mark.parametrize("lazy", [False, True])
 @pytest.mark.parametrize("N,qb,pb,dnum,dims", [
     (256, [60, 40, 40, 40], [60], 4, [16, 8, 4]),
     (512, [45, 45, 45, 45, 45, 45], [60, 60], 3, [64, 16, 16, 4]),
 ])
-def test_network_rect_bit_exact_and_fp64(N, qb, pb, dnum, dims):
+def test_network_rect_bit_exact_and_fp64(N, qb, pb, dnum, dims, lazy):
     """A model under CTL_DENSE_RECT (the batched network's shape: shrinking layers take the
     rectangular form, the first one's fold forms the next layer's [y, y]) against the
     oracle's composition of the same layers, bit-exact, and FP64 within the tolerance."""
@@ -681,14 +687,14 @@ def test_network_rect_bit_exact_and_fp64(N, qb, pb, dnum, dims):
     slots[:dims[0]] = x
     slots[t0:t0 + dims[0]] = x
     g = ctl.Context(N, qb, pb, dnum=dnum, scale=2.0 ** 40)
-    g.set_dense_mode(g.DENSE_RECT)
+    g.set_dense_mode(g.DENSE_RECT_LAZY if lazy else g.DENSE_RECT)
     o = O.Oracle(N, qb, pb, dnum=dnum, scale=2.0 ** 40)
-    model = ctl.Model(g, inject_rect(o, layers))
+    model = ctl.Model(g, inject_rect(o, layers, lazy))
     rots = model.rotations()
     o.keygen(rots, seed=3)
     k = g.keygen(rots, seed=3)
     ct_o = o.encrypt(o.encode(slots), 4)
-    exp, sc = oracle_forward_rect(o, ct_o, layers)
+    exp, sc = oracle_forward_rect(o, ct_o, layers, lazy)
     out = model.forward(k, g.ct_import(ct_o, 2.0 ** 40))
     assert np.array_equal(out.export()[0], exp)
     assert np.array_equal(model.forward(k, g.ct_import(ct_o, 2.0 ** 40), graph=True).export()[0], exp)

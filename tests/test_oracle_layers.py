@@ -270,23 +270,25 @@ def rect_model(W, x, tn, ns, fold):
     return z, S
 
 
+@pytest.mark.parametrize("lazy", [False, True])
 @pytest.mark.parametrize("m,n", [(4, 16), (3, 12), (8, 32), (2, 64)])
 @pytest.mark.parametrize("fold", [0, 1, 2])
-def test_dense_rect_matches_its_fp64_definition(m, n, fold):
+def test_dense_rect_matches_its_fp64_definition(m, n, fold, lazy):
     # Rectangular diagonals (tm < tn): every slot of the decoded output against the FP64
     # partial sums and fold of the definition; after the fold, W x sits in slots [0, m)
-    # (and [tm, tm + m) with fold = 2), as the dense layer of Sec. 3.1 computes.
-    rots = O.Oracle.rect_rotations(m, n, fold)
+    # (and [tm, tm + m) with fold = 2), as the dense layer of Sec. 3.1 computes.  lazy:
+    # the BSGS part in the lazy-ModDown form (its own split), the same fold.
+    rots = O.Oracle.rect_rotations(m, n, fold, lazy)
     o = ctx(N=256, rots=rots)
     rng = np.random.default_rng(m * 100 + n)
     W = rng.normal(0, 1 / np.sqrt(n), (m, n))
     x = rng.uniform(-1, 1, n)
     tm, tn = O.Oracle.bsgs_t(m, 1), O.Oracle.bsgs_t(n, 1)
     ct = enc(o, netref.replicated_slots(x, tn, o.N // 2), 12)
-    pts = o.encode_diagonals_rect(W, o.dense_scale(4))
+    pts = o.encode_diagonals_rect(W, o.dense_scale(4), lazy)
     assert pts.shape == (tm, o.N)
-    out, cnt = o.dense_rect(ct, pts, tn, fold=fold)
-    t1 = O.Oracle.bsgs_t1(tm)
+    out, cnt = o.dense_rect(ct, pts, tn, fold=fold, lazy=lazy)
+    t1 = O.Oracle.bsgs_t1(tm, lazy)
     folds = (tn // tm).bit_length() - 1 if fold >= 1 else 0
     extra = folds + (1 if fold == 2 else 0)
     assert cnt == [(t1 - 1) + (tm // t1 - 1) + extra, tm, tm - 1 + extra]
