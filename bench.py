@@ -56,7 +56,8 @@ def hbm_peak_gbs():
         return HBM_FALLBACK_GBS, "fallback"
 
 WORKLOADS = {
-    "batched": dict(N=16384, q=[45] * 8, p=[60, 60], dnum=4, batch=256, dims=[1024, 256, 256, 64], dense_form="rect",
+    "batched": dict(N=16384, q=[45] * 8, p=[60, 60], dnum=4, batch=256, dims=[1024, 256, 256, 64],
+                    dense_form="rect_lazy",
                     desc="256 ciphertexts, N=16384, 8x45-bit q + 2x60-bit p, dnum=4, scale 2^40; "
                          "dense 1024->256, x^2, dense 256->256, x^2, dense 256->64"),
     "single8192": dict(N=8192, q=[60, 40, 40, 40], p=[60], dnum=4, batch=1, dims=[512, 128, 64],
@@ -78,6 +79,21 @@ WORKLOADS = {
 PAPER_T_S = {"paper_p1": 1.08, "paper_p2": 2.56}
 # ReLU approximation of Sec. 3.1 (a3 z^3 + a2 z^2 + a1 z + a0), as a0..a3
 RELU_APPROX = [0.49383, 0.59259, 0.092593, -0.0061728]
+
+
+# dense-layer forms (ctl_set_dense_mode): square padding or the rectangular form for shrinking
+# layers, each with Eq. (bsgs) composed of whole rotations or in the lazy-ModDown form
+DENSE_FORMS = {"square": "DENSE_COMPOSED", "lazy": "DENSE_LAZY_MODDOWN", "rect": "DENSE_RECT",
+               "rect_lazy": "DENSE_RECT_LAZY"}
+DENSE_FORM_DESC = {
+    "square": "ctl_set_dense_mode(CTL_DENSE_COMPOSED): every dense layer padded to a square t x t matrix, "
+              "t = 2^ceil(log2 max(m, n)), t1 = 2^ceil(log2(t)/2), whole rotations",
+    "lazy": "ctl_set_dense_mode(CTL_DENSE_LAZY_MODDOWN): square padding, rotations kept in the extended basis, "
+            "ModDown once per giant step and once per layer, t1 = min(t, 2^ceil(log2(4t)/2))",
+    "rect": "ctl_set_dense_mode(CTL_DENSE_RECT): shrinking layers with tm diagonals of length tn and a "
+            "log2(tn/tm)-rotation fold, whole rotations",
+    "rect_lazy": "ctl_set_dense_mode(CTL_DENSE_RECT_LAZY): the rectangular form for shrinking layers, every "
+                 "Eq. (bsgs) in the lazy-ModDown form and its split"}
 
 
 def bsgs_t(m, n):
@@ -207,9 +223,15 @@ def op_plan(wl):
     L = len(wl["q"])
     plan, lvl = [], L
 
+    form = wl.get("dense_form", "square")
+    lazy = form in ("lazy", "rect_lazy")
+
     def split(t):
         lg = t.bit_length() - 1
-        t1 = 1 << ((lg + 1) // 2)  # the default (composed-rotation) split, 2^ceil(log2(t)/2)
+        if lazy:  # the lazy-ModDown form's split, min(t, 2^ceil(log2(4t)/2))
+            t1 = min(t, 1 << ((lg + 3) // 2))
+        else:  # the composed form's split, 2^ceil(log2(t)/2)
+            t1 = 1 << ((lg + 1) // 2)
         return t1, t // t1
 
     if wl.get("net") == "paper":
@@ -223,7 +245,7 @@ def op_plan(wl):
         plan.append((t1 + t2 - 2, t, 1, lvl))                     # dense
         return plan
     dims = wl["dims"]
-    rect = wl.get("dense_form") == "rect"
+    rect = form in ("rect", "rect_lazy")
     for i in range(len(dims) - 1):
         tm, tn = bsgs_t(dims[i + 1], 1), bsgs_t(dims[i], 1)
         last = i + 1 == len(dims) - 1
@@ -272,7 +294,8 @@ class OracleSample:
         if self.whole:
             square_last = wl.get("square_last", False)
             layers, self.Ws = layers_for(wl["dims"], square_last)
-            rect = wl.get("dense_form") == "rect"
+            form = wl.get("dense_form", "square")
+            rect, lazy = form in ("rect", "rect_lazy"), form in ("lazy", "rect_lazy")
             rots, skip = set(), set()
             for ly in layers:
                 if ly[0] == "replicate":
@@ -289,11 +312,12 @@ class OracleSample:
                         fold = 2 if j < len(layers) and layers[j] == ("replicate", tm) else 1
                         if fold == 2:
                             skip.add(j)
-                        rots |= set(O.Oracle.rect_rotations(m, n, fold))
-                        self.plan.append(("rect", o.encode_diagonals_rect(ly[1], o.dense_scale(lvl, sc)), tn, fold))
+                        rots |= set(O.Oracle.rect_rotations(m, n, fold, lazy))
+                        self.plan.append(("rect", o.encode_diagonals_rect(ly[1], o.dense_scale(lvl, sc), lazy), tn,
+                                          fold))
                     else:
-                        rots |= set(O.Oracle.bsgs_rotations(m, n))
-                        self.plan.append(("dense", o.encode_diagonals(ly[1], o.dense_scale(lvl, sc))))
+                        rots |= set(O.Oracle.bsgs_rotations(m, n, lazy))
+                        self.plan.append(("dense", o.encode_diagonals(ly[1], o.dense_scale(lvl, sc), lazy)))
                     sc, lvl = o.scale, lvl - 1
                 elif ly[0] == "square":
                     self.plan.append(("square",))
@@ -301,6 +325,7 @@ class OracleSample:
                 else:
                     self.plan.append(ly)
             o.keygen(sorted(rots), seed=3)
+            self.lazy = lazy
             self.out_scale = sc
             t0 = bsgs_t(*self.Ws[0].shape)
             self.xs, slots = inputs_for(N, wl["dims"], 1, t0)
@@ -324,9 +349,9 @@ class OracleSample:
             h = self.ct
             for st in self.plan:
                 if st[0] == "dense":
-                    h = o.dense(h, st[1])[0]
+                    h = o.dense(h, st[1], lazy=self.lazy)[0]
                 elif st[0] == "rect":
-                    h = o.dense_rect(h, st[1], st[2], fold=st[3])[0]
+                    h = o.dense_rect(h, st[1], st[2], fold=st[3], lazy=self.lazy)[0]
                 elif st[0] == "square":
                     h = o.square(h)
                 else:
@@ -574,8 +599,7 @@ def single_query_point(ctl, torch, name, steps):
     stream = torch.cuda.Stream()
     ctx = ctl.Context(wl["N"], wl["q"], wl["p"], dnum=wl["dnum"], scale=2.0 ** 40)
     ctx.set_stream(stream.cuda_stream)
-    if wl.get("dense_form") == "rect":
-        ctx.set_dense_mode(ctx.DENSE_RECT)
+    ctx.set_dense_mode(getattr(ctx, DENSE_FORMS[wl.get("dense_form", "square")]))
     model = ctl.Model(ctx, layers)
     keys = ctx.keygen(model.rotations(), seed=3)
     xs, slots = inputs_for(wl["N"], wl["dims"], 1, t0)
@@ -698,9 +722,9 @@ def main():
     ap.add_argument("--profile-forward", action="store_true",
                     help="run one eager forward inside cudaProfilerStart/Stop and print its per-class "
                          "algorithmic work and bytes (for an ncu capture of exactly that forward)")
-    ap.add_argument("--dense-form", default="", choices=["", "rect", "square"],
-                    help="rect: shrinking dense layers in the rectangular form (default for the dense/x^2 "
-                         "networks); square: every layer padded to a square t x t matrix")
+    ap.add_argument("--dense-form", default="", choices=[""] + list(DENSE_FORMS),
+                    help="square / lazy / rect / rect_lazy (ctl_set_dense_mode); default: the workload's "
+                         "(rect_lazy for the batched network, square otherwise)")
     ap.add_argument("--no-others", action="store_true",
                     help="skip the single-query and serving points measured beside the batched value")
     ap.add_argument("--single-steps", type=int, default=300, help="timed single-query forwards per point")
@@ -780,8 +804,7 @@ def main():
     windows = (N // 2) // (2 * t0) if wl.get("net") == "paper" else 1
     dense_form = args.dense_form or wl.get("dense_form", "square")
     wl["dense_form"] = dense_form
-    if dense_form == "rect":  # shrinking dense layers take the rectangular form
-        ctx.set_dense_mode(ctx.DENSE_RECT)
+    ctx.set_dense_mode(getattr(ctx, DENSE_FORMS[dense_form]))
     ctx.set_windows(windows)
     if args.ntt_shape != "auto":
         sh = ctx.NTT_R16 if args.ntt_shape == "r16" else ctx.NTT_R32
@@ -944,16 +967,8 @@ def main():
     if not args.no_variants and world == 1:
         # the same workload with the dense layers in the other forms (different, equally valid
         # ciphertexts with their own Galois keys): reported beside, not as, the value
-        forms = {"square_padding": (ctx.DENSE_COMPOSED,
-                                    "ctl_set_dense_mode(CTL_DENSE_COMPOSED): every dense layer padded to a square "
-                                    "t x t matrix, t = 2^ceil(log2 max(m, n)), t1 = 2^ceil(log2(t)/2)"),
-                 "lazy_moddown": (ctx.DENSE_LAZY_MODDOWN,
-                                  "ctl_set_dense_mode(CTL_DENSE_LAZY_MODDOWN): square padding, rotations kept in the "
-                                  "extended basis, ModDown once per giant step and once per layer, "
-                                  "t1 = min(t, 2^ceil(log2(4t)/2))")}
-        if dense_form != "rect":
-            forms["rectangular"] = (ctx.DENSE_RECT, "ctl_set_dense_mode(CTL_DENSE_RECT)")
-            del forms["square_padding"]
+        forms = {name: (getattr(ctx, DENSE_FORMS[name]), DENSE_FORM_DESC[name]) for name in DENSE_FORMS
+                 if name != dense_form}
         variants = {}
         for name, (mode, desc) in forms.items():
             ctx.set_dense_mode(mode)
@@ -982,7 +997,7 @@ def main():
                 "desc": desc}
             model_l.close()
             keys_l.close()
-        ctx.set_dense_mode(ctx.DENSE_RECT if dense_form == "rect" else ctx.DENSE_COMPOSED)
+        ctx.set_dense_mode(getattr(ctx, DENSE_FORMS[dense_form]))
 
     # rooflines per kernel class.  Work units: Shoup modmuls for the transform classes and
     # split-half MACs for the key product and BSGS sums; each unit's peak is this GPU's rate

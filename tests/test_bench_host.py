@@ -46,9 +46,13 @@ def test_operation_plan_follows_the_papers_counts():
     assert [p[3] for p in plan] == [7, 6, 5, 5, 4, 3, 2]
     # the batched network in the rectangular form: 1024->256 (t1 = t2 = 16, fold of 2 rotations
     # plus the [y, y] one), x^2, 256->256 (30 + replicate), x^2, 256->64 (t1 = t2 = 8, fold 2)
-    plan = bench.op_plan(bench.WORKLOADS["batched"])
+    plan = bench.op_plan(dict(bench.WORKLOADS["batched"], dense_form="rect"))
     assert sum(p[0] for p in plan) == (30 + 3) + 1 + (30 + 1) + 1 + (14 + 2)
     assert sum(p[1] for p in plan) == 256 + 1.5 + 256 + 1.5 + 64
+    # the lazy-ModDown split: t1 = 32, t2 = 8 for t = 256; t1 = 16, t2 = 4 for t = 64
+    plan = bench.op_plan(bench.WORKLOADS["batched"])
+    assert bench.WORKLOADS["batched"]["dense_form"] == "rect_lazy"
+    assert sum(p[0] for p in plan) == (38 + 3) + 1 + (38 + 1) + 1 + (18 + 2)
     sq = dict(bench.WORKLOADS["batched"], dense_form="square")
     plan = bench.op_plan(sq)
     assert sum(p[0] for p in plan) == 62 + 1 + 1 + 30 + 1 + 1 + 30

@@ -223,3 +223,30 @@ def test_dense_rect_full_size_bit_exact():
     assert np.array_equal(g.dense_rect_coeffs(k, g.ct_import(cts[2], 2.0 ** 40), pts, n, sc, fold=2).export()[0], exp)
     out = g.dense_rect_coeffs(k, g.ct_import(np.stack(cts), 2.0 ** 40), pts, n, sc, fold=2).export()
     assert np.array_equal(out[2], exp)
+
+
+def test_dense_rect_lazy_full_size_bit_exact():
+    """The batched benchmark's dense form (rectangular, lazy-ModDown sums) at N = 16384: a
+    16 x 64 layer with fold 2 bit-exact against the oracle, as member 0 of a batch of 2."""
+    m, n = 16, 64
+    rots = O.Oracle.rect_rotations(m, n, 2, lazy=True)
+    o, g, k = _full_pair(rots)
+    N = 16384
+    rng = np.random.default_rng(1665)
+    W = rng.normal(0, 1 / np.sqrt(n), (m, n))
+    cts = []
+    for i in range(2):
+        x = rng.uniform(-1, 1, n)
+        slots = np.zeros(N // 2)
+        slots[:n] = x
+        slots[n:2 * n] = x
+        cts.append(o.encrypt(o.encode(slots), 900 + i))
+    sc = o.dense_scale(8)
+    pts = o.encode_diagonals_rect(W, sc, lazy=True)
+    exp = o.dense_rect(cts[0], pts, n, fold=2, lazy=True)[0]
+    g.set_dense_mode(g.DENSE_RECT_LAZY)
+    try:
+        out = g.dense_rect_coeffs(k, g.ct_import(np.stack(cts), 2.0 ** 40), pts, n, sc, fold=2).export()
+    finally:
+        g.set_dense_mode(g.DENSE_COMPOSED)
+    assert np.array_equal(out[0], exp)

@@ -519,15 +519,17 @@ def _fp64_forward(Ws, x, square_last):
     return h
 
 
-@pytest.mark.parametrize("name,N,qb,pb,dnum,dims,B", [
-    ("cfg2", 8192, [60, 40, 40, 40], [60], 4, [512, 128, 64], 2),
-    ("cfg3", 16384, [45] * 8, [60, 60], 4, [1024, 256, 256, 64], 8),
+@pytest.mark.parametrize("name,N,qb,pb,dnum,dims,B,mode", [
+    ("cfg2", 8192, [60, 40, 40, 40], [60], 4, [512, 128, 64], 2, 0),
+    ("cfg3", 16384, [45] * 8, [60, 60], 4, [1024, 256, 256, 64], 8, 0),
+    ("cfg3", 16384, [45] * 8, [60, 60], 4, [1024, 256, 256, 64], 8, 3),
 ])
-def test_full_size_networks_properties(name, N, qb, pb, dnum, dims, B):
+def test_full_size_networks_properties(name, N, qb, pb, dnum, dims, B, mode):
     """The single-query (N = 8192) and batched (N = 16384) networks at their full sizes,
-    in the launch configuration bench.py times: every decoded output within 1e-4 of the
-    FP64 network, each ciphertext of the batch bit-identical to its forward alone, the
-    CUDA-graph replay bit-identical to the eager forward, and two runs identical."""
+    in the launch configuration bench.py times (mode 3: CTL_DENSE_RECT_LAZY, the batched
+    benchmark's form): every decoded output within 1e-4 of the FP64 network, each
+    ciphertext of the batch bit-identical to its forward alone, the CUDA-graph replay
+    bit-identical to the eager forward, and two runs identical."""
     rng = np.random.default_rng(1)
     Ws = [rng.normal(0, 1 / np.sqrt(dims[i]), (dims[i + 1], dims[i])) for i in range(len(dims) - 1)]
     layers = []
@@ -537,6 +539,7 @@ def test_full_size_networks_properties(name, N, qb, pb, dnum, dims, B):
             layers += [("square",), ("replicate", O.Oracle.bsgs_t(*Ws[i + 1].shape))]
     t0 = O.Oracle.bsgs_t(*Ws[0].shape)
     g = ctl.Context(N, qb, pb, dnum=dnum, scale=2.0 ** 40)
+    g.set_dense_mode(mode)
     model = ctl.Model(g, layers)
     k = g.keygen(model.rotations(), seed=3)
     xs, cts = [], []
