@@ -39,12 +39,13 @@ MAX_SM_MHZ = 2070.0
 MAC_CLASSES = ("key_ip", "bsgs_inner")  # kernel classes whose work unit is a split-half MAC
 HBM_FALLBACK_GBS = 6800.0     # copy bandwidth of an earlier GB300 measurement, if none is given
 # DRAM traffic over algorithmic bytes per kernel class: the dram__bytes_read.sum +
-# dram__bytes_write.sum of every launch of one forward at batch 16 (ncu, one pass), over
-# the algorithmic bytes the library counts for the same launches.  Traffic grows in
-# proportion to the batch, so a full-size launch's traffic is this ratio times its
-# algorithmic bytes.  A class missing here was not captured for the current kernels.
-TRAFFIC_RATIO = {"modup_ntt": 1.070, "moddown_ntt": 1.061, "key_ip": 0.956, "bsgs_inner": 0.979,
-                 "ntt_inv": 0.872, "rescale": 0.581}
+# dram__bytes_write.sum of every launch of one forward of the batched network in its
+# benchmark form (CTL_DENSE_RECT_LAZY) at batch 16, over the algorithmic bytes the library
+# counts for the same launches.  A full-size launch's traffic is taken as this ratio times
+# its algorithmic bytes; ratios below 1 are L2 hits at batch 16, so this is a lower
+# estimate at batch 256.  A class missing here was not captured for the current kernels.
+TRAFFIC_RATIO = {"modup_ntt": 0.827, "moddown_ntt": 0.775, "key_ip": 0.780, "bsgs_inner": 0.987,
+                 "ntt_inv": 0.634, "rescale": 0.581}
 
 
 def hbm_peak_gbs():
@@ -526,6 +527,7 @@ def run_uneven(args, ctl):
             p = [60] if Nn == 8192 else [60, 60]
             dnum = len(q) if Nn == 8192 else (len(q) + 1) // 2
             ctx = ctl.Context(Nn, q, p, dnum=dnum, scale=2.0 ** 40)
+            ctx.set_dense_mode(getattr(ctx, DENSE_FORMS[args.dense_form or "rect_lazy"]))
             shapes[(Nn, d)] = {"ctx": ctx, "models": {}}
     queries = [((int(rng.choice([8192, 16384])), int(rng.integers(2, 7))), int(rng.choice([128, 256, 512, 1024])))
                for _ in range(args.queries)]
