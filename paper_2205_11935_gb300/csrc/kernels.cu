@@ -387,6 +387,21 @@ struct KeyRegs {
       }
       r0 = split_redc(a00, am - a00 - a11, a11, P.q, P.qinv);
       r1 = split_redc(c00, cm - c00 - c11, c11, P.q, P.qinv);
+    } else if constexpr (ND <= 8) {
+      // at most 8 products below q^2 < 2^124: the 128-bit sums cannot overflow and their
+      // high words stay below 2^63, reduced once before REDC (same residue as reducing
+      // after every product)
+      u64 lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
+#pragma unroll
+      for (int d = 0; d < ND; d++) {
+        if (d < nd) {
+          const u64 x = xv[d];
+          mac(lo0, hi0, x, k0[d]);
+          mac(lo1, hi1, x, k1[d]);
+        }
+      }
+      r0 = redc(reduce_wide(hi0, P.q, P.bar), lo0, P.q, P.qinv);
+      r1 = redc(reduce_wide(hi1, P.q, P.bar), lo1, P.q, P.qinv);
     } else {
       u64 lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
 #pragma unroll
@@ -791,6 +806,13 @@ __global__ void __launch_bounds__(256) k_bsgs(const u64* __restrict__ baby, cons
       // S = a11 * 2^(2W) + m * 2^W + a00 (W = kSplitW); m < 2^62
       res = split_redc(a00, m, a11, P.q, P.qinv);
       if constexpr (kWino) res = submod(submod(res, Y, P.q), ek, P.q);
+    } else if (P.q < (1ull << 61)) {
+      // at most 32 products below q^2 < 2^122: no overflow, the high word stays below 2^63
+      // and is reduced once before REDC (the same residue as reducing after every product)
+      u64 lo = 0, hi = 0;
+#pragma unroll
+      for (int j = 0; j < T1; j++) mac(lo, hi, x[j], D[j][lane]);
+      res = redc(reduce_wide(hi, P.q, P.bar), lo, P.q, P.qinv);
     } else {
       u64 lo = 0, hi = 0;
 #pragma unroll
