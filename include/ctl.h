@@ -54,6 +54,7 @@ typedef struct ctl_keys ctl_keys;
 typedef struct ctl_ct ctl_ct;
 typedef struct ctl_model ctl_model;
 typedef struct ctl_server ctl_server;
+typedef struct ctl_multi ctl_multi;
 
 /* Device allocator hooks: alloc(bytes, stream, user) returns device memory ordered on
  * `stream`; free(ptr, stream, user) releases it.  NULL hooks select the library's
@@ -481,6 +482,25 @@ int ctl_model_forward(ctl_context* ctx, const ctl_model* model, const ctl_keys* 
  * ctl_model_destroy. */
 int ctl_model_forward_graph(ctl_context* ctx, const ctl_model* model, const ctl_keys* keys, const ctl_ct* in,
                             ctl_ct** out);
+/* Several groups of queries in one launch (configuration 4's uneven batch: mixed ring
+ * degrees, depths and layer shapes; each query is one ClassifyHE call of Fig. alg:cryptotl).
+ * Group i has its own context ctxs[i] (ring, primes, stream), model models[i], keys keys[i]
+ * and a batch of counts[i] ciphertexts.  ctl_multi_create runs each group once eagerly on
+ * zero inputs, then captures all groups' forwards as branches of ONE CUDA graph: the first
+ * context's stream forks to every group's stream, each branch is that group's whole layer
+ * sequence, and the branches join back; groups on distinct streams (e.g. context clones,
+ * one per group) run concurrently when the graph is replayed.  ctl_multi_forward takes one
+ * input batch per group (matching count, level and scale), launches the graph once on
+ * ctxs[0]'s stream and returns one output per group; every group's stream is ordered after
+ * that work.  Each output equals ctl_model_forward of its group alone, bit for bit.  The
+ * contexts, models and keys must outlive the handle; ctl_multi_destroy releases the graph
+ * and its staging buffers.  Needs the library's own allocator.  Errors: CTL_EINVAL,
+ * CTL_ENOMEM, CTL_ECUDA (and the errors of the groups' forwards at creation). */
+int ctl_multi_create(uint32_t n, ctl_context* const* ctxs, const ctl_model* const* models, const ctl_keys* const* keys,
+                     const uint32_t* counts, ctl_multi** out);
+int ctl_multi_forward(ctl_multi* multi, const ctl_ct* const* in, ctl_ct** out);
+void ctl_multi_destroy(ctl_multi* multi);
+
 /* Output level and scale of the model. */
 int ctl_model_info(const ctl_model* model, uint32_t* out_level, double* out_scale, uint64_t* bytes);
 

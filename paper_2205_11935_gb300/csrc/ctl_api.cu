@@ -9,6 +9,8 @@
 #include <tuple>
 #include <mutex>
 #include <new>
+#include <array>
+
 #include "ctl_internal.h"
 #include "modarith.cuh"
 
@@ -2638,6 +2640,192 @@ extern "C" int ctl_model_forward_graph(ctl_context* c, const ctl_model* M, const
   *out = o;
   return CTL_OK;
 }
+
+// =====================================================================================
+// Several groups of ciphertexts (each with its own context, model and keys: mixed ring
+// degrees, levels and layer shapes) as one CUDA graph
+// =====================================================================================
+struct ctl_multi {
+  std::vector<ctl_context*> ctx;
+  std::vector<const ctl_model*> model;
+  std::vector<const ctl_keys*> keys;
+  std::vector<uint32_t> count;
+  std::vector<u64*> in_buf, out_buf;
+  cudaGraphExec_t exec = nullptr;
+  uint64_t kernels = 0;
+};
+
+static void multi_release(ctl_multi* m) {
+  if (!m) return;
+  if (m->exec) {
+    cudaStreamSynchronize(m->ctx[0]->stream);
+    cudaGraphExecDestroy(m->exec);
+  }
+  for (size_t i = 0; i < m->ctx.size(); i++) {
+    if (i < m->in_buf.size()) dev_free(m->ctx[i], m->in_buf[i]);
+    if (i < m->out_buf.size()) dev_free(m->ctx[i], m->out_buf[i]);
+    cudaStreamSynchronize(m->ctx[i]->stream);
+  }
+  delete m;
+}
+
+// Captures the n groups' forwards as branches of one graph: the first context's stream
+// forks to every group's stream (an event), each group's layer sequence is captured on its
+// own stream (stream-ordered temporaries become graph memory nodes), and the branches join
+// back.  Groups on distinct streams (e.g. context clones) run concurrently when replayed.
+extern "C" int ctl_multi_create(uint32_t n, ctl_context* const* ctxs, const ctl_model* const* models,
+                                const ctl_keys* const* keys, const uint32_t* counts, ctl_multi** out) {
+  if (!n || !ctxs || !models || !keys || !counts || !out) {
+    set_error("ctl_multi_create: invalid argument");
+    return CTL_EINVAL;
+  }
+  *out = nullptr;
+  std::unique_ptr<ctl_multi> m(new ctl_multi());
+  for (uint32_t i = 0; i < n; i++) {
+    ctl_context* c = ctxs[i];
+    const ctl_model* M = models[i];
+    if (!c || !M || !keys[i] || !counts[i] || c->alloc_fn || c->N != M->ctx->N || c->moduli != M->ctx->moduli ||
+        c->device != ctxs[0]->device) {
+      set_error("ctl_multi_create: group %u: null handle, zero count, a caller allocator, a model of other "
+                "parameters or another device", i);
+      return CTL_EINVAL;
+    }
+    m->ctx.push_back(c);
+    m->model.push_back(M);
+    m->keys.push_back(keys[i]);
+    m->count.push_back(counts[i]);
+  }
+  for (uint32_t i = 0; i < n; i++) {
+    ctl_context* c = ctxs[i];
+    const ctl_model* M = models[i];
+    u64* a = (u64*)dev_alloc(c, ct_words(c, M->in_level, counts[i]) * sizeof(u64));
+    u64* b = (u64*)dev_alloc(c, ct_words(c, M->out_level, counts[i]) * sizeof(u64));
+    m->in_buf.push_back(a);
+    m->out_buf.push_back(b);
+    if (!a || !b) {
+      set_error("ctl_multi_create: allocation failed");
+      multi_release(m.release());
+      return CTL_ENOMEM;
+    }
+    cudaMemsetAsync(a, 0, ct_words(c, M->in_level, counts[i]) * sizeof(u64), c->stream);
+    // one eager run per group settles every launch configuration before the capture
+    int rc = model_run(c, M, keys[i], a, (int)counts[i], b);
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(c->stream), "multi warm-up");
+    if (rc) {
+      multi_release(m.release());
+      return rc;
+    }
+  }
+  std::vector<bool> timing(n);
+  std::vector<uint64_t> l0(n);
+  std::vector<std::array<uint64_t, 5>> o0(n);
+  for (uint32_t i = 0; i < n; i++) {
+    ctl_context* c = ctxs[i];
+    timing[i] = c->timing.enabled;
+    c->timing.enabled = false;
+    l0[i] = c->launch_count.load();
+    o0[i] = {c->op_rot, c->op_ptmul, c->op_add, c->op_relin, c->op_rescale};
+  }
+  cudaStream_t s0 = ctxs[0]->stream;
+  std::vector<cudaEvent_t> ev(n + 1, nullptr);
+  for (auto& e : ev) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+  cudaGraph_t graph = nullptr;
+  int rc = cuda_check(cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal), "begin capture");
+  if (!rc) {
+    int rr = CTL_OK;
+    cudaEventRecord(ev[n], s0);
+    for (uint32_t i = 0; i < n && !rr; i++) {
+      ctl_context* c = ctxs[i];
+      if (c->stream != s0) cudaStreamWaitEvent(c->stream, ev[n], 0);
+      rr = model_run(c, models[i], keys[i], m->in_buf[i], (int)counts[i], m->out_buf[i]);
+      if (c->stream != s0) {
+        cudaEventRecord(ev[i], c->stream);
+        cudaStreamWaitEvent(s0, ev[i], 0);
+      }
+    }
+    const int re = cuda_check(cudaStreamEndCapture(s0, &graph), "end capture");
+    rc = rr ? rr : re;
+  }
+  if (!rc) rc = cuda_check(cudaGraphInstantiate(&m->exec, graph, 0), "graph instantiate");
+  if (graph) cudaGraphDestroy(graph);
+  for (auto& e : ev) cudaEventDestroy(e);
+  for (uint32_t i = 0; i < n; i++) {
+    ctl_context* c = ctxs[i];
+    c->timing.enabled = timing[i];
+    m->kernels += c->launch_count.load() - l0[i];
+    c->launch_count = l0[i];
+    c->op_rot = o0[i][0];
+    c->op_ptmul = o0[i][1];
+    c->op_add = o0[i][2];
+    c->op_relin = o0[i][3];
+    c->op_rescale = o0[i][4];
+  }
+  if (rc) {
+    cudaGetLastError();
+    multi_release(m.release());
+    return rc;
+  }
+  *out = m.release();
+  return CTL_OK;
+}
+
+// One graph launch for all groups: inputs copied into the staging buffers, the graph
+// replayed on the first context's stream, outputs copied out; every group's context
+// stream then waits for that work, so later calls on the outputs are ordered after it.
+extern "C" int ctl_multi_forward(ctl_multi* m, const ctl_ct* const* in, ctl_ct** out) {
+  if (!m || !in || !out) {
+    set_error("ctl_multi_forward: null argument");
+    return CTL_EINVAL;
+  }
+  const size_t n = m->ctx.size();
+  for (size_t i = 0; i < n; i++) {
+    out[i] = nullptr;
+    const ctl_model* M = m->model[i];
+    if (!in[i] || in[i]->count != m->count[i] || in[i]->level != M->in_level ||
+        !same_scale(in[i]->scale, M->in_scale) || in[i]->ctx->N != m->ctx[i]->N) {
+      set_error("ctl_multi_forward: input %zu does not match its group (count, level, scale or ring)", i);
+      return CTL_EINVAL;
+    }
+  }
+  cudaStream_t s0 = m->ctx[0]->stream;
+  cudaEvent_t e;
+  cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+  for (size_t i = 0; i < n; i++) {  // inputs made on the group's stream come first
+    if (m->ctx[i]->stream != s0) {
+      cudaEventRecord(e, m->ctx[i]->stream);
+      cudaStreamWaitEvent(s0, e, 0);
+    }
+    cudaMemcpyAsync(m->in_buf[i], in[i]->d, in[i]->bytes, cudaMemcpyDeviceToDevice, s0);
+  }
+  int rc = cuda_check(cudaGraphLaunch(m->exec, s0), "graph launch");
+  for (size_t i = 0; i < n && !rc; i++) {
+    ctl_context* c = m->ctx[i];
+    ctl_ct* o = new_ct(c, m->model[i]->out_level, m->count[i], m->model[i]->out_scale);
+    if (!o) {
+      set_error("ctl_multi_forward: allocation failed");
+      rc = CTL_ENOMEM;
+      break;
+    }
+    cudaMemcpyAsync(o->d, m->out_buf[i], o->bytes, cudaMemcpyDeviceToDevice, s0);
+    out[i] = o;
+  }
+  cudaEventRecord(e, s0);
+  for (size_t i = 0; i < n; i++)
+    if (m->ctx[i]->stream != s0) cudaStreamWaitEvent(m->ctx[i]->stream, e, 0);
+  cudaEventDestroy(e);
+  if (!rc) rc = last_cuda("multi forward");
+  if (rc) {
+    for (size_t i = 0; i < n; i++) {
+      if (out[i]) ctl_ct_destroy(out[i]);
+      out[i] = nullptr;
+    }
+    return rc;
+  }
+  m->ctx[0]->launch_count += m->kernels;
+  return CTL_OK;
+}
+
+extern "C" void ctl_multi_destroy(ctl_multi* m) { multi_release(m); }
 
 // =====================================================================================
 // Statistics

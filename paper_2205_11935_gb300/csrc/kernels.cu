@@ -628,9 +628,9 @@ void launch_key_ip_acc(ctl_context* c, const u64* ext, size_t ext_r, int nb, int
   const int b_per = (nb + splits - 1) / splits;
   dim3 grid(gx, (unsigned)((nb + b_per - 1) / b_per));
   double work = 2.0 * nd * EN * nb * rl.n;
-  // bytes: the digits of every rotation's input, the keys, the addend and the sums S read
-  // and written
-  const double bytes = 8.0 * (double)EN * ((double)rl.n * nb * nd + 2.0 * nd * rl.n + (double)rl.n * nb * 2.0 +
+  // bytes: the digits of every rotation's input, the keys, the poly-0 addend of every
+  // rotation, and the sums S (two polys) read and written once
+  const double bytes = 8.0 * (double)EN * ((double)rl.n * nb * nd + 2.0 * nd * rl.n + (double)rl.n * nb +
                                            4.0 * nb);
 #define CTL_KEYIPA_CASE(NDV)                                                                                     \
   CTL_LAUNCH_C(KC_KEYIP, work, bytes, grid,                                                                      \

@@ -116,6 +116,9 @@ SIGNATURES = {
     "ctl_model_forward": (C.c_int, [_vp, _vp, _vp, _vp, _pp]),
     "ctl_model_forward_graph": (C.c_int, [_vp, _vp, _vp, _vp, _pp]),
     "ctl_model_info": (C.c_int, [_vp, _u32p, _dp, _u64p]),
+    "ctl_multi_create": (C.c_int, [C.c_uint32, _pp, _pp, _pp, _u32p, _pp]),
+    "ctl_multi_forward": (C.c_int, [_vp, _pp, _pp]),
+    "ctl_multi_destroy": (None, [_vp]),
     "ctl_context_clone": (C.c_int, [_vp, _pp]),
     "ctl_server_create": (C.c_int, [_pp, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32]),
     "ctl_server_add_lane": (C.c_int, [_vp, _vp, _vp, _u32p]),
@@ -692,6 +695,35 @@ class Model:
         if getattr(self, "h", None) and getattr(self.ctx, "h", None):
             lib().ctl_model_destroy(self.h)
         self.h = None
+
+
+class Multi:
+    """Groups of (context, model, keys, batch size) forwarded by one CUDA graph launch
+    (ctl_multi_*); outputs are bit-identical to each group's own forward."""
+
+    def __init__(self, groups):
+        n = len(groups)
+        self.groups = list(groups)
+        ctxs = (C.c_void_p * n)(*[g[0].h for g in groups])
+        models = (C.c_void_p * n)(*[g[1].h for g in groups])
+        keys = (C.c_void_p * n)(*[g[2].h for g in groups])
+        counts = np.ascontiguousarray([g[3] for g in groups], dtype=np.uint32)
+        h = C.c_void_p()
+        _check(lib().ctl_multi_create(n, C.cast(ctxs, _pp), C.cast(models, _pp), C.cast(keys, _pp),
+                                      _p(counts, _u32p), C.byref(h)))
+        self.h = h
+
+    def forward(self, cts):
+        n = len(self.groups)
+        ins = (C.c_void_p * n)(*[c.h for c in cts])
+        outs = (C.c_void_p * n)()
+        _check(lib().ctl_multi_forward(self.h, C.cast(ins, _pp), C.cast(outs, _pp)))
+        return [Ciphertext(self.groups[i][0], C.c_void_p(outs[i])) for i in range(n)]
+
+    def close(self):
+        if self.h:
+            lib().ctl_multi_destroy(self.h)
+            self.h = None
 
 
 class Server:

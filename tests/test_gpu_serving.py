@@ -149,3 +149,45 @@ def test_server_admits_by_memory_budget():
     assert peak <= budget  # never two batches' reservations at once
     assert deferred > 0  # idle workers waited for memory while requests were queued
     srv.close()
+
+
+def test_multi_graph_equals_each_groups_forward():
+    """Configuration 4's one-launch form: three groups with different ring degrees, depths,
+    dense forms and batch sizes captured as branches of one CUDA graph; every output equals
+    its group's own forward bit for bit, on two calls with different inputs, and a second
+    context clone per group runs its branch on its own stream."""
+    specs = [  # (N, q, p, dnum, dims, dense mode, batch)
+        (8192, [60, 40, 40], [60], 3, [256, 64], 0, 2),
+        (16384, [60, 40, 40, 40, 40], [60, 60], 3, [512, 128, 64], 3, 3),
+        (8192, [60, 40, 40, 40, 40], [60], 5, [128, 128, 128], 2, 1),
+    ]
+    groups, made = [], []
+    for gi, (N, qb, pb, dnum, dims, mode, B) in enumerate(specs):
+        rng = np.random.default_rng(gi)
+        Ws = [rng.normal(0, 1 / np.sqrt(dims[i]), (dims[i + 1], dims[i])) for i in range(len(dims) - 1)]
+        layers = []
+        for i, W in enumerate(Ws):
+            layers.append(("dense", W))
+            layers.append(("square",))
+            if i + 1 < len(Ws):
+                layers.append(("replicate", bsgs_t(*Ws[i + 1].shape)))
+        ctx = ctl.Context(N, qb, pb, dnum=dnum, scale=2.0 ** 40)
+        ctx.set_dense_mode(mode)
+        model = ctl.Model(ctx, layers)
+        keys = ctx.keygen(model.rotations(), seed=10 + gi)
+        clone = ctx.clone()
+        groups.append((clone, model, keys, B))
+        made.append((ctx, model, keys, dims, B, bsgs_t(Ws[0].shape[0], Ws[0].shape[1])))
+    multi = ctl.Multi(groups)
+    for call in range(2):
+        ins, exp = [], []
+        for gi, (ctx, model, keys, dims, B, t0) in enumerate(made):
+            batch = ctx.concat([query(ctx, keys, dims[0], t0, 100 * call + 10 * gi + b) for b in range(B)])
+            ins.append(batch)
+            exp.append(model.forward(keys, batch).export())
+        outs = multi.forward(ins)
+        for gi in range(len(made)):
+            assert np.array_equal(outs[gi].export(), exp[gi]), f"call {call}, group {gi}"
+    multi.close()
+    for clone, _, _, _ in groups:
+        clone.close()
