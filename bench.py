@@ -1106,8 +1106,9 @@ def main():
         cpu = {"value": fwd_s, "unit": "forwards/s", "cores": cores, "kind": "oracle", "sample": desc}
 
     # the other configurations, measured in the same run: single queries under the graph
-    # (configurations 1 and 2, and the batched network one query at a time) and one short
-    # serving point (configuration 5)
+    # (configurations 1 and 2, and the batched network one query at a time), one short
+    # serving point (configuration 5), the client round trip and the uneven batch
+    # (configuration 4)
     others = None
     if rank == 0 and world == 1 and args.workload == "batched" and not args.no_others:
         others = {name: single_query_point(ctl, torch, name, args.single_steps)
@@ -1115,6 +1116,11 @@ def main():
         others["batched"]["desc"] = "the batched network, one query per forward (batch 1)"
         others["serving"] = serving_point(ctl, args.serve_rate, args.serve_seconds, args.serve_clients)
         others["client_round_trip"] = client_round_trip_point(ctl, torch, ctx, model, keys, slots, m_out, 3)
+        un = run_uneven(argparse.Namespace(queries=1024, workers=4, max_batch=64, mem_budget_gb=160.0,
+                                           dense_form=""), ctl)
+        un.update({"unit": "forwards/s", "desc": "configuration 4: 1024 queries, N in {8192, 16384}, depth 2-6, "
+                   "input 128-1024, each shape group a branch of one CUDA graph (ctl_multi_forward)"})
+        others["uneven"] = un
 
     if rank == 0:
         lat = sorted(step_ms)
