@@ -706,3 +706,62 @@ def test_network_rect_bit_exact_and_fp64(N, qb, pb, dnum, dims, lazy):
     model2 = ctl.Model(g, layers)  # the library's own encoding
     y2 = g.decrypt(k, model2.forward(k, g.encrypt(k, slots, 4)), len(ref))
     assert np.max(np.abs(y2 - ref)) < TOL
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_dense_random_shapes_all_forms_bit_exact(seed):
+    """Random layer shapes (square, shrinking, growing, non-powers of two) in each dense form,
+    bit-exact against the oracle's function for that form: composed (Eq. bsgs with square
+    padding), lazy-ModDown, and, for shrinking layers, the rectangular form composed and
+    lazy with a random fold."""
+    rng = np.random.default_rng(900 + seed)
+    name = ["a2", "c2"][seed % 2]
+    P = pair(name)
+    half = P.N // 2
+    lim = half // 2
+    m = int(rng.integers(1, lim + 1))
+    n = int(rng.integers(1, lim + 1))
+    tm, tn = O.Oracle.bsgs_t(m, 1), O.Oracle.bsgs_t(n, 1)
+    t = O.Oracle.bsgs_t(m, n)
+    W = rng.normal(0, 1 / np.sqrt(n), (m, n))
+    x = rng.uniform(-1, 1, n)
+    slots = np.zeros(half)
+    slots[:n] = x
+    slots[t:t + n] = x
+    _, ct_o = P.fresh(950 + seed, z=slots)
+    lvl = ct_o.shape[1]
+    o = O.Oracle(P.N, *PARAMS[name][1:3], dnum=PARAMS[name][3], scale=2.0 ** 40)
+    g = P.g
+    forms = [("composed", False, None), ("lazy", True, None)]
+    if tm < tn:
+        forms += [("rect", False, int(rng.integers(0, 3))), ("rect_lazy", True, int(rng.integers(0, 3)))]
+    for form, lazy, fold in forms:
+        if fold is None:
+            rots = O.Oracle.bsgs_rotations(m, n, lazy)
+        else:
+            rots = O.Oracle.rect_rotations(m, n, fold, lazy)
+        rots = sorted(set(rots))
+        o.keygen(rots, seed=3)
+        k = g.keygen(rots, seed=3)
+        sc = o.dense_scale(lvl)
+        ct = g.ct_import(ct_o, 2.0 ** 40)
+        try:
+            if fold is None:
+                g.set_dense_mode(g.DENSE_LAZY_MODDOWN if lazy else g.DENSE_COMPOSED)
+                pts = o.encode_diagonals(W, sc, lazy)
+                exp = o.dense(ct_o, pts, lazy=lazy)[0]
+                got = g.dense_coeffs(k, ct, pts, sc).export()[0]
+            else:
+                g.set_dense_mode(g.DENSE_RECT_LAZY if lazy else g.DENSE_RECT)
+                pts = o.encode_diagonals_rect(W, sc, lazy)
+                # the rectangular input layout: [x, x] at stride tn
+                s2 = np.zeros(half)
+                s2[:n] = x
+                s2[tn:tn + n] = x
+                ct2_o = o.encrypt(o.encode(s2), 970 + seed)
+                exp = o.dense_rect(ct2_o, pts, tn, fold=fold, lazy=lazy)[0]
+                got = g.dense_rect_coeffs(k, g.ct_import(ct2_o, 2.0 ** 40), pts, tn, sc, fold=fold).export()[0]
+            assert np.array_equal(got, exp), (form, m, n, fold)
+        finally:
+            g.set_dense_mode(g.DENSE_COMPOSED)
+        k.close()
