@@ -188,11 +188,11 @@ uint64_t ctl_galois_element(const ctl_context* ctx, int64_t r);
  *   (host FP64 canonical embedding, round half away from zero).
  * ctl_encrypt: encodes x at the nominal scale and encrypts at the top level with the
  *   secret key: ct = (-a*s + m + e, a), a and e drawn from streams of `seed`.
- * ctl_encrypt_coeffs: the same from given integer coefficients m[N] (for N <= 16384 the
- *   randomness is drawn on the device, as ctl_encrypt_coeffs_dev does).
+ * ctl_encrypt_coeffs: the same from given integer coefficients m[N] (where the device client
+ *   path applies, the randomness is drawn on the device, as ctl_encrypt_coeffs_dev does).
  * ctl_decrypt: decrypts and decodes the first n slots into y[n] (synchronises).
  * ctl_decrypt_coeffs: the centred coefficients of c0 + c1*s as doubles, m[N] (the CRT runs
- *   on the device for N <= 16384).
+ *   on the device where the device client path applies).
  * ------------------------------------------------------------------------------- */
 int ctl_encode(ctl_context* ctx, const double* x, size_t n, double scale, int64_t* m);
 int ctl_decode(ctl_context* ctx, const double* m, size_t n, double scale, double* y);
@@ -201,7 +201,8 @@ int ctl_encrypt_coeffs(ctl_context* ctx, const ctl_keys* keys, const int64_t* m,
 int ctl_decrypt(ctl_context* ctx, const ctl_keys* keys, const ctl_ct* ct, double* y, size_t n);
 int ctl_decrypt_coeffs(ctl_context* ctx, const ctl_keys* keys, const ctl_ct* ct, double* m);
 
-/* Client side on the device, for batches of queries (N <= 16384; CTL_EINVAL otherwise).
+/* Client side on the device, for batches of queries (N <= 16384 and at most 16 data primes;
+ * CTL_EINVAL otherwise).
  * All pointers named *_dev are device memory owned by the caller; seeds is a host array.
  * ctl_encode_dev: count slot vectors z_dev[count][nz] -> integer coefficients
  *   m_dev[count][N] at `scale`: the canonical embedding of Sec. 3.1 computed as one

@@ -251,7 +251,8 @@ __global__ void k_crt_centred(const u64* __restrict__ res, int lvl, int logN, si
 namespace ctl {
 
 int client_tables_create(ctl_context* c) {
-  if (c->logN > kMaxClientLogN || c->logN < 2) return CTL_OK;  // the host encoder covers other rings
+  // the host paths cover other rings and chains longer than the CRT kernel's 16 primes
+  if (c->logN > kMaxClientLogN || c->logN < 2 || c->L > 16) return CTL_OK;
   const uint32_t N = c->N, M = N / 2, L = c->L;
   std::vector<double2> tw(M / 2), twist(M);
   for (uint32_t k = 0; k < M / 2; k++) tw[k] = make_double2(c->enc.cs[2 * k], c->enc.sn[2 * k]);
@@ -324,7 +325,7 @@ namespace {
 
 int need_client(const ctl_context* c, const char* who) {
   if (!c->client) {
-    set_error("%s: the GPU client transforms need 4 <= N <= 16384", who);
+    set_error("%s: the GPU client transforms need 4 <= N <= 16384 and at most 16 data primes", who);
     return CTL_EINVAL;
   }
   return CTL_OK;

@@ -765,3 +765,35 @@ def test_dense_random_shapes_all_forms_bit_exact(seed):
         finally:
             g.set_dense_mode(g.DENSE_COMPOSED)
         k.close()
+
+
+@pytest.mark.parametrize("lazy", [False, True])
+def test_dense_rect_with_bias(lazy):
+    """The rectangular form with a bias (added before the rescale, so the fold carries it
+    into both halves of the [y, y] layout): bit-exact against the oracle with an injected
+    integer bias, and W x + b within the tolerance with the library's own encodings."""
+    P = pair("c2")
+    m, n = 24, 100
+    rots = sorted(set(O.Oracle.rect_rotations(m, n, 2, lazy)))
+    o = O.Oracle(P.N, *PARAMS["c2"][1:3], dnum=PARAMS["c2"][3], scale=2.0 ** 40)
+    o.keygen(rots, seed=3)
+    g = P.g
+    k = g.keygen(rots, seed=3)
+    W, x, tn, ct_o = rect_case(P, m, n, 333)
+    tm = O.Oracle.bsgs_t(m, 1)
+    sc = o.dense_scale(ct_o.shape[1])
+    pts = o.encode_diagonals_rect(W, sc, lazy)
+    bias_c = np.random.default_rng(4).integers(-2 ** 40, 2 ** 40, P.N, dtype=np.int64)
+    exp = o.dense_rect(ct_o, pts, tn, bias=bias_c, fold=2, lazy=lazy)[0]
+    ct = g.ct_import(ct_o, 2.0 ** 40)
+    g.set_dense_mode(g.DENSE_RECT_LAZY if lazy else g.DENSE_RECT)
+    try:
+        got = g.dense_rect_coeffs(k, ct, pts, tn, sc, bias=bias_c, fold=2).export()[0]
+        assert np.array_equal(got, exp)
+        b = np.random.default_rng(5).uniform(-0.5, 0.5, m)
+        y = g.decrypt(k, g.dense_rect(k, ct, W, bias=b, fold=2), P.N // 2)
+        assert np.max(np.abs(y[:m] - (W @ x + b))) < TOL
+        assert np.max(np.abs(y[tm:tm + m] - (W @ x + b))) < TOL
+    finally:
+        g.set_dense_mode(g.DENSE_COMPOSED)
+    k.close()

@@ -188,6 +188,11 @@ def test_multi_graph_equals_each_groups_forward():
         outs = multi.forward(ins)
         for gi in range(len(made)):
             assert np.array_equal(outs[gi].export(), exp[gi]), f"call {call}, group {gi}"
+    # an input that does not match its group (batch size) is refused, nothing launched
+    ctx0, _, keys0, dims0, B0, t00 = made[0]
+    wrong = ctx0.concat([query(ctx0, keys0, dims0[0], t00, 7 + b) for b in range(B0 + 1)])
+    with pytest.raises(ctl.CtlError):
+        multi.forward([wrong] + ins[1:])
     multi.close()
     for clone, _, _, _ in groups:
         clone.close()
