@@ -908,6 +908,60 @@ struct Pass16 {
   }
 };
 
+// The last pass (stages S0 .. LOGN-1, sub-transforms of R = 2^LOGR consecutive elements)
+// with warp w owning the 512 consecutive elements 512w .. 512w+511 and lane j its
+// sub-transforms 512w/R + 32i + j (i < 16/R): consecutive lanes take consecutive
+// sub-transforms (coalesced twiddles, conflict-free padded addresses), and the pass
+// before it (stages 8..11, blocks of N/256 elements shared by N/4096 threads) wrote the
+// warp's 512 elements from the same warp, so a warp barrier orders the exchange.
+template <int LOGN, int S0, int LOGR>
+struct PassLast16 {
+  static_assert(S0 + LOGR == LOGN, "the last pass ends at stage LOGN");
+  static constexpr int R = 1 << LOGR, NS = 16 / R, UW = 512 / R;
+  __device__ __forceinline__ static int sub(int t, int i) { return (t >> 5) * UW + 32 * i + (t & 31); }
+  __device__ __forceinline__ static void load(u64* x, const u64* smem, int t) {
+#pragma unroll
+    for (int i = 0; i < NS; i++) {
+      const u64* s = smem + pidx(sub(t, i) * R);
+#pragma unroll
+      for (int k = 0; k < R; k++) x[i * R + k] = s[k];
+    }
+  }
+  __device__ __forceinline__ static void store(const u64* x, u64* smem, int t) {
+#pragma unroll
+    for (int i = 0; i < NS; i++) {
+      u64* s = smem + pidx(sub(t, i) * R);
+#pragma unroll
+      for (int k = 0; k < R; k++) s[k] = x[i * R + k];
+    }
+  }
+  template <bool SMALL>
+  __device__ __forceinline__ static void fwd(u64* x, int t, const ulonglong2* W, u64 q) {
+#pragma unroll
+    for (int i = 0; i < NS; i++) fwd_regs<S0, LOGR, SMALL>(x + i * R, sub(t, i), W, q);
+  }
+  template <bool SMALL>
+  __device__ __forceinline__ static void inv(u64* x, int t, const ulonglong2* W, u64 q, const InvLast& P) {
+#pragma unroll
+    for (int i = 0; i < NS; i++) inv_regs<S0, LOGR, InvLast, SMALL, LOGN>(x + i * R, sub(t, i), W, q, P);
+  }
+};
+
+// Barrier of the aligned group of G threads that exchange data between the second and
+// third passes (G = N / 256: the threads of one block of N/16 elements at stage 4).  A
+// warp barrier when the group fits a warp; otherwise named barriers 1..8 over groups of
+// max(G, T/8) threads (T = N/16 threads; barrier 0 is the block's).
+template <int LOGN>
+__device__ __forceinline__ void pass12_sync(int t) {
+  constexpr int N = 1 << LOGN, T = N / 16, G0 = N / 256, G = G0 > T / 8 ? G0 : T / 8;
+  if constexpr (G0 <= 32) {
+    __syncwarp();
+  } else {
+    static_assert(T / G <= 8 && G % 32 == 0, "at most 8 named groups of whole warps");
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + t / G), "n"(G) : "memory");
+  }
+}
+
 // Forward passes and the epilogue of one item (16 elements per thread).
 template <int LOGN, bool SMALL, class Epi>
 __device__ __forceinline__ void fwd16_body(u64* x, u64* smem, int t, const ulonglong2* __restrict__ W, u64 q,
@@ -915,23 +969,30 @@ __device__ __forceinline__ void fwd16_body(u64* x, u64* smem, int t, const ulong
   constexpr int N = 1 << LOGN, T = N / 16, R3 = LOGN - 12;
   typedef Pass16<LOGN, 0, 4> P0;
   typedef Pass16<LOGN, 4, 4> P1;
-  typedef Pass16<LOGN, 8, 4> P2;
-  typedef Pass16<LOGN, 12, (R3 > 0 ? R3 : 1)> P3;
+  // Exchanges: all threads after the first pass, groups of N/256 threads after the second,
+  // a warp after the third; the epilogue reads element t + T*k, so all threads again.
   P0::template fwd<SMALL>(x, t, W, q);
   P0::store(x, smem, t);
   __syncthreads();
   P1::load(x, smem, t);
   P1::template fwd<SMALL>(x, t, W, q);
   P1::store(x, smem, t);
-  __syncthreads();
-  P2::load(x, smem, t);
-  P2::template fwd<SMALL>(x, t, W, q);
-  P2::store(x, smem, t);
+  pass12_sync<LOGN>(t);
   if constexpr (R3 > 0) {
-    __syncthreads();
+    typedef Pass16<LOGN, 8, 4> P2;
+    typedef PassLast16<LOGN, 12, R3> P3;
+    P2::load(x, smem, t);
+    P2::template fwd<SMALL>(x, t, W, q);
+    P2::store(x, smem, t);
+    __syncwarp();
     P3::load(x, smem, t);
     P3::template fwd<SMALL>(x, t, W, q);
     P3::store(x, smem, t);
+  } else {  // N = 4096: the third pass is the last
+    typedef PassLast16<LOGN, 8, 4> P2;
+    P2::load(x, smem, t);
+    P2::template fwd<SMALL>(x, t, W, q);
+    P2::store(x, smem, t);
   }
   __syncthreads();
   typename Epi::State es;
@@ -991,7 +1052,9 @@ k_nttf_r16(const __grid_constant__ Pro pro, const __grid_constant__ Epi epi, con
       fwd16_body<LOGN, true>(x, smem, t, W, q, epi, p, l, pi, primes);
     else
       fwd16_body<LOGN, false>(x, smem, t, W, q, epi, p, l, pi, primes);
-    __syncthreads();
+    // No barrier before the next item: from the epilogue up to the next item's first
+    // barrier a thread reads and writes only its own slots (elements t + T*k), and every
+    // other thread's reads of them ended before the barrier that precedes the epilogue.
   }
 }
 
@@ -1003,18 +1066,25 @@ __device__ __forceinline__ void inv16_body(u64* x, u64* smem, int t, const ulong
   constexpr int N = 1 << LOGN, T = N / 16, R3 = LOGN - 12;
   typedef Pass16<LOGN, 0, 4> P0;
   typedef Pass16<LOGN, 4, 4> P1;
-  typedef Pass16<LOGN, 8, 4> P2;
-  typedef Pass16<LOGN, 12, (R3 > 0 ? R3 : 1)> P3;
+  // Exchanges (the caller's barrier precedes the first pass): a warp after the first pass,
+  // groups of N/256 threads before the second to last, all threads before the last.
   if constexpr (R3 > 0) {
+    typedef PassLast16<LOGN, 12, R3> P3;
+    typedef Pass16<LOGN, 8, 4> P2;
     P3::load(x, smem, t);
     P3::template inv<SMALL>(x, t, W, q, P);
     P3::store(x, smem, t);
-    __syncthreads();
+    __syncwarp();
+    P2::load(x, smem, t);
+    P2::template inv<SMALL>(x, t, W, q, P);
+    P2::store(x, smem, t);
+  } else {  // N = 4096: the first pass is stages 11..8
+    typedef PassLast16<LOGN, 8, 4> P2;
+    P2::load(x, smem, t);
+    P2::template inv<SMALL>(x, t, W, q, P);
+    P2::store(x, smem, t);
   }
-  P2::load(x, smem, t);
-  P2::template inv<SMALL>(x, t, W, q, P);
-  P2::store(x, smem, t);
-  __syncthreads();
+  pass12_sync<LOGN>(t);
   P1::load(x, smem, t);
   P1::template inv<SMALL>(x, t, W, q, P);
   P1::store(x, smem, t);
@@ -1069,7 +1139,8 @@ k_ntti_r16(const __grid_constant__ Pro pro, const __grid_constant__ Epi epi, con
       inv16_body<LOGN, true>(x, smem, t, W, q, P, epi, p, l, pi, primes);
     else
       inv16_body<LOGN, false>(x, smem, t, W, q, P, epi, p, l, pi, primes);
-    __syncthreads();
+    // No barrier before the next item: after the last barrier of the transform a thread
+    // reads only its own slots (elements t + T*k), the ones its next prologue writes.
   }
 }
 
