@@ -44,8 +44,8 @@ HBM_FALLBACK_GBS = 6800.0     # copy bandwidth of an earlier GB300 measurement, 
 # counts for the same launches.  A full-size launch's traffic is taken as this ratio times
 # its algorithmic bytes; ratios below 1 are L2 hits at batch 16, so this is a lower
 # estimate at batch 256.  A class missing here was not captured for the current kernels.
-TRAFFIC_RATIO = {"modup_ntt": 0.828, "moddown_ntt": 0.775, "key_ip": 0.815, "bsgs_inner": 0.987,
-                 "ntt_inv": 0.634, "rescale": 0.581}
+TRAFFIC_RATIO = {"modup_ntt": 0.833, "moddown_ntt": 0.759, "key_ip": 0.802, "bsgs_inner": 0.987,
+                 "ntt_inv": 0.631, "rescale": 0.571}
 
 
 def hbm_peak_gbs():
