@@ -1559,7 +1559,8 @@ int dense_apply_lazy(ctl_context* c, const ctl_keys* k, const DenseLayer& D, con
       const int n = (int)std::min<uint32_t>(t1 - j0, CTL_MAX_ROT);
       RotList rl;
       if (int rc = rot_list(c, k, j0, 1, n, rl)) return rc;
-      launch_key_ip(c, ext.p, 0, nb, (int)lvl, rl, baby.p + (size_t)j0 * xw, in, ctw);
+      // addend: P * c0 of each input, poly 0 of baby step 0 (stride 2 E N per input)
+      launch_key_ip(c, ext.p, 0, nb, (int)lvl, rl, baby.p + (size_t)j0 * xw, baby.p, 2 * EN);
     }
     c->op_rot += (uint64_t)(t1 - 1) * nb;
   }

@@ -302,11 +302,12 @@ void launch_modup_ntt(ctl_context* c, const u64* src_coef, size_t coef_stride, c
 // Key inner products with automorphism: for rotation r (g[r], key[r]) and batch b:
 //   acc[r][b][t][i][k] = sum_d ext_r[b][d][i][perm_g(k)] * key_r[d][t][prime(i)][k],
 // ext_r = ext + r * ext_r_stride (0 when the ModUp is shared by all rotations).
-// With add_c0 set, output poly t = 0 on the data limbs also gets (P mod q_i) * sigma_g(c0)
-// with c0 of input b at add_c0 + b*add_b (NTT form, level lvl): the baby step of a
-// rotation kept in the extended basis.
+// With add_pc0 set, output poly t = 0 on the data limbs also gets sigma_g(P * c0), with the
+// data limbs of P * c0 for input b at add_pc0 + b*add_b (NTT form, [lvl][N], residues in
+// [0, q_i), as launch_scale_to_ext writes them): the baby step of a rotation kept in the
+// extended basis.
 void launch_key_ip(ctl_context* c, const u64* ext, size_t ext_r_stride, int nb, int lvl, const RotList& rl, u64* acc,
-                   const u64* add_c0 = nullptr, size_t add_b = 0);
+                   const u64* add_pc0 = nullptr, size_t add_b = 0);
 // Key inner products of nr = rl.n rotations summed into S in the extended basis:
 //   S[b][0] += sum_r ( ip_r[b][0] + sigma_{g_r}(add[r][b]) ),  S[b][1] += sum_r ip_r[b][1],
 // ext_r = ext + r*ext_r_stride ([nb][nd][E][N] each), add[r][b] = add + r*add_r + b*add_b

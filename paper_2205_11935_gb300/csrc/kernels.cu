@@ -423,8 +423,7 @@ struct KeyRegs {
 // ND: the digit count when EXACT, else an upper bound of the run-time count nd_arg.
 template <int ND, bool EXACT>
 __device__ __forceinline__ void key_ip_body(const u64* __restrict__ ext, size_t ext_r, const RotList& rl,
-                                            u64* __restrict__ acc, const u64* __restrict__ add_c0, size_t add_b,
-                                            const u64* __restrict__ pmod, const u64* __restrict__ pmod_sh,
+                                            u64* __restrict__ acc, const u64* __restrict__ add_pc0, size_t add_b,
                                             const DPrime* __restrict__ pr, int logN, int nb, int nd_arg, int E,
                                             int lvl, int L, int LK) {
   const int nd = EXACT ? ND : nd_arg;
@@ -448,10 +447,10 @@ __device__ __forceinline__ void key_ip_body(const u64* __restrict__ ext, size_t 
   const uint32_t ks = (g == 1 || src_major) ? e : auto_src_k(e, g, logN);
   KeyRegs<ND> kr;
   kr.load(rl.key[r], nd, pi, LK, N, k, sp);
-  // baby step in the extended basis: + (P mod q_i) * sigma_g(c0) on the data limbs
-  const bool with_c0 = add_c0 != nullptr && i < lvl;
-  const u64 pm = with_c0 ? __ldg(pmod + i) : 0, pms = with_c0 ? __ldg(pmod_sh + i) : 0;
-  const u64* c0 = with_c0 ? add_c0 + ((size_t)i << logN) + ks : nullptr;
+  // baby step in the extended basis: + sigma_g(P * c0) on the data limbs (the product taken
+  // once per layer, not once per rotation)
+  const bool with_c0 = add_pc0 != nullptr && i < lvl;
+  const u64* c0 = with_c0 ? add_pc0 + ((size_t)i << logN) + ks : nullptr;
   // running pointers (ciphertext b: digits at ex + d*EN, outputs at o and o + EN): the
   // loop advances them by constant strides instead of recomputing 64-bit offsets
   const u64* ex = ext + (size_t)r * ext_r + ((size_t)i << logN) + ks;
@@ -474,8 +473,8 @@ __device__ __forceinline__ void key_ip_body(const u64* __restrict__ ext, size_t 
     kr.ip(xa, nd, sp, P, r0, r1);
     kr.ip(xb, nd, sp, P, s0, s1);
     if (with_c0) {
-      r0 = addmod(r0, shoup(ca, pm, pms, P.q), P.q);
-      s0 = addmod(s0, shoup(cb, pm, pms, P.q), P.q);
+      r0 = addmod(r0, ca, P.q);
+      s0 = addmod(s0, cb, P.q);
     }
     o[0] = r0;
     o[EN] = r1;
@@ -488,7 +487,7 @@ __device__ __forceinline__ void key_ip_body(const u64* __restrict__ ext, size_t 
     KeyRegs<ND>::fetch(ex, EN, nd, xa);
     u64 r0, r1;
     kr.ip(xa, nd, sp, P, r0, r1);
-    if (with_c0) r0 = addmod(r0, shoup(c0[0], pm, pms, P.q), P.q);
+    if (with_c0) r0 = addmod(r0, c0[0], P.q);
     o[0] = r0;
     o[EN] = r1;
   }
@@ -500,20 +499,18 @@ __device__ __forceinline__ void key_ip_body(const u64* __restrict__ ext, size_t 
 template <int ND, bool EXACT>
 __global__ void __launch_bounds__(256, 3) k_key_ip(const u64* __restrict__ ext, size_t ext_r,
                                                    const __grid_constant__ RotList rl, u64* __restrict__ acc,
-                                                   const u64* __restrict__ add_c0, size_t add_b,
-                                                   const u64* __restrict__ pmod, const u64* __restrict__ pmod_sh,
+                                                   const u64* __restrict__ add_pc0, size_t add_b,
                                                    const DPrime* __restrict__ pr, int logN, int nb, int nd_arg,
                                                    int E, int lvl, int L, int LK) {
-  key_ip_body<ND, EXACT>(ext, ext_r, rl, acc, add_c0, add_b, pmod, pmod_sh, pr, logN, nb, nd_arg, E, lvl, L, LK);
+  key_ip_body<ND, EXACT>(ext, ext_r, rl, acc, add_pc0, add_b, pr, logN, nb, nd_arg, E, lvl, L, LK);
 }
 template <int ND, bool EXACT>
 __global__ void __launch_bounds__(256) k_key_ip_wide(const u64* __restrict__ ext, size_t ext_r,
                                                      const __grid_constant__ RotList rl, u64* __restrict__ acc,
-                                                     const u64* __restrict__ add_c0, size_t add_b,
-                                                     const u64* __restrict__ pmod, const u64* __restrict__ pmod_sh,
+                                                     const u64* __restrict__ add_pc0, size_t add_b,
                                                      const DPrime* __restrict__ pr, int logN, int nb, int nd_arg,
                                                      int E, int lvl, int L, int LK) {
-  key_ip_body<ND, EXACT>(ext, ext_r, rl, acc, add_c0, add_b, pmod, pmod_sh, pr, logN, nb, nd_arg, E, lvl, L, LK);
+  key_ip_body<ND, EXACT>(ext, ext_r, rl, acc, add_pc0, add_b, pr, logN, nb, nd_arg, E, lvl, L, LK);
 }
 
 // g^-1 mod 2N for odd g (2N a power of two): Newton iteration on the 2-adic inverse.
@@ -524,7 +521,7 @@ static u64 inv_mod_2n(u64 g, u64 two_n) {
 }
 
 void launch_key_ip(ctl_context* c, const u64* ext, size_t ext_r, int nb, int lvl, const RotList& rl_in, u64* acc,
-                   const u64* add_c0, size_t add_b) {
+                   const u64* add_pc0, size_t add_b) {
   RotList rl = rl_in;
   for (int r = 0; r < rl.n; r++) rl.ginv[r] = inv_mod_2n(rl.g[r], 2ull * c->N);
   const int nrot = rl.n;
@@ -536,16 +533,13 @@ void launch_key_ip(ctl_context* c, const u64* ext, size_t ext_r, int nb, int lvl
   dim3 grid = ext_r == 0 ? dim3((unsigned)nrot, eblocks) : dim3(eblocks, (unsigned)nrot);
   double work = 2.0 * nd * EN * nb * nrot;
   // bytes: the extended digits once (shared by the rotations when hoisted), each rotation's
-  // key once, the two accumulator polys written, and the c0 addend read when given
+  // key once, the two accumulator polys written, and the P * c0 addend read when given
   const double bytes = 8.0 * (double)EN * ((ext_r == 0 ? 1.0 : nrot) * nb * nd + 2.0 * nd * nrot + 2.0 * nrot * nb +
-                                           (add_c0 ? (double)nrot * nb * lvl / E : 0.0));
-  const u64* pm = c->moddown.pmod;
-  const u64* pms = c->moddown.pmod_sh;
+                                           (add_pc0 ? (double)nrot * nb * lvl / E : 0.0));
 #define CTL_KEYIP_CASE(KERN, NDV, EX)                                                                          \
   CTL_LAUNCH_C(KC_KEYIP, work, bytes, grid,                                                                    \
-             (KERN<NDV, EX><<<grid, 256, 0, c->stream>>>(ext, ext_r, rl, acc, add_c0, add_b, pm, pms,           \
-                                                         c->d_primes, (int)c->logN, nb, nd, E, lvl, (int)c->L,  \
-                                                         LK)))
+             (KERN<NDV, EX><<<grid, 256, 0, c->stream>>>(ext, ext_r, rl, acc, add_pc0, add_b, c->d_primes,      \
+                                                         (int)c->logN, nb, nd, E, lvl, (int)c->L, LK)))
   switch (nd) {
     case 1: CTL_KEYIP_CASE(k_key_ip, 1, true); break;
     case 2: CTL_KEYIP_CASE(k_key_ip, 2, true); break;
