@@ -309,7 +309,10 @@ int ctl_deserialize(const uint8_t* in, size_t size, uint32_t N, const uint64_t* 
  *     CTL_DENSE_COMPOSED (default): t1 = 2^ceil(log2(t)/2);
  *     CTL_DENSE_LAZY_MODDOWN:       t1 = min(t, 2^ceil(log2(4t)/2)).
  *   Either way the layer needs the Galois keys of 1..t1-1 and k*t1 (k = 1..t2-1) for
- *   that mode's t1 (ctl_model_rotations lists them).  The input must hold [x, x] in slots
+ *   that mode's t1 (ctl_model_rotations lists them).  In CTL_DENSE_RECT and
+ *   CTL_DENSE_RECT_LAZY a layer with 2^ceil(log2 m) < 2^ceil(log2 n) is evaluated as
+ *   ctl_eval_dense_rect with fold 1 (its keys and output layout are that call's); other
+ *   layers as in CTL_DENSE_COMPOSED and CTL_DENSE_LAZY_MODDOWN respectively.  The input must hold [x, x] in slots
  *   [0, 2t); the output holds y in slots [0, m) and zeros elsewhere.  The diagonals are
  *   encoded at scale q_last * Delta / scale_in, so the output carries Delta again.
  *   bias (nullable, m values) is added before the rescale.
