@@ -1130,6 +1130,11 @@ def main():
         others = {name: single_query_point(ctl, torch, name, args.single_steps)
                   for name in ("single4096", "single8192", "batched")}
         others["batched"]["desc"] = "the batched network, one query per forward (batch 1)"
+        if not args.no_cpu_baseline:  # the oracle on the host cores for configurations 1 and 2
+            for name in ("single4096", "single8192"):
+                fwd_s, desc, cores, _ = cpu_oracle_sample(WORKLOADS[name])
+                others[name]["cpu_baseline"] = {"value": fwd_s, "unit": "forwards/s", "cores": cores,
+                                                "kind": "oracle", "sample": desc}
         others["serving"] = serving_point(ctl, args.serve_rate, args.serve_seconds, args.serve_clients)
         others["client_round_trip"] = client_round_trip_point(ctl, torch, ctx, model, keys, slots, m_out, 3)
         un = run_uneven(argparse.Namespace(queries=1024, workers=4, max_batch=64, mem_budget_gb=160.0,
