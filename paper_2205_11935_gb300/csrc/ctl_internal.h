@@ -281,7 +281,7 @@ void timing_end(ctl_context* c, int cls, cudaEvent_t ev, double work, double byt
 inline uint32_t prime_of_limb(uint32_t l, uint32_t lvl, uint32_t L) { return l < lvl ? l : L + (l - lvl); }
 
 // ---------------------------------------------------------------------------------
-// Kernel launchers (ntt.cu, kernels.cu).  All operate on the context stream.
+// Kernel launchers (ntt.cu, ntt_modup.cu, ntt_moddown.cu, ntt_giant.cu, kernels.cu).  All operate on the context stream.
 // Layout conventions: a "poly" is [limbs][N]; polys are spaced by poly_stride words.
 // A limb l of a poly of a level-lvl object maps to prime prime_of_limb(l, lvl, L).
 // ---------------------------------------------------------------------------------
