@@ -92,6 +92,39 @@ def test_ntt_matches_definition(N, shape):
     g.close()
 
 
+@pytest.mark.parametrize("N", [4096, 8192])
+def test_ntt_many_limbs_per_block(N):
+    """Thousands of limbs at N = 4096 and 8192, several per CTA (the 16-element kernels go on
+    to a CTA's next limb without a block-wide barrier): both register shapes give the same
+    transform of every limb, the inverse returns the input, and sampled limbs, among them the
+    last, equal the oracle's direct evaluation."""
+    o = O.Oracle(N, [50, 40, 61], [60])
+    g = ctl.Context(N, [50, 40, 61], [60])
+    limbs, polys = 3, (1200 if N == 4096 else 600)
+    rng = np.random.default_rng(N + 7)
+    a = np.empty((polys, limbs, N), dtype=np.uint64)
+    for i in range(limbs):
+        a[:, i] = rng.integers(0, o.moduli[i], (polys, N), dtype=np.uint64)
+    a[-1, 1, :5] = np.uint64(o.moduli[1] - 1)  # edge values in the last limb of a CTA's run
+    x = to_dev(a)
+    fwd = {}
+    for shape in (0, 1):
+        g.set_ntt_shape(shape, shape)
+        y = torch.empty_like(x)
+        z = torch.empty_like(x)
+        torch.cuda.synchronize()
+        g.ntt_dev(x.data_ptr(), y.data_ptr(), polys, limbs)
+        g.ntt_dev(y.data_ptr(), z.data_ptr(), polys, limbs, inverse=True)
+        g.synchronize()
+        assert torch.equal(z, x), f"shape {shape}: inverse of forward"
+        fwd[shape] = y
+    assert torch.equal(fwd[0], fwd[1])
+    for p, i in ((polys - 1, 1), (polys // 2, 0), (1, 2)):
+        got = from_dev(fwd[1][p, i].contiguous(), (N,))
+        assert np.array_equal(got, o.ntt_direct(i, a[p, i])), f"poly {p}, limb {i}"
+    g.close()
+
+
 @pytest.mark.parametrize("shape", [0, 1])
 def test_ntt_16384_convolution_and_batch(shape):
     """N = 16384 (the batched workload's ring): NTT-domain product equals the schoolbook
