@@ -481,9 +481,13 @@ int ctl_model_forward(ctl_context* ctx, const ctl_model* model, const ctl_keys* 
  * sequence (kernels, stream-ordered temporary allocations, copies) into a graph with
  * fixed staging buffers; later calls copy the input into the staging buffer, replay the
  * graph and copy the result out, with one launch instead of several hundred.  Calls
- * for the same (ctx, model) must not overlap.  Needs the library's own allocator
- * (CTL_ENOTSUP after ctl_set_allocator).  Graph memory is released by
- * ctl_model_destroy. */
+ * for the same (ctx, model) must not overlap.  A batch of 64 ciphertexts or more is
+ * captured as two halves on concurrent branches of the graph, the second half on the
+ * stream of a context clone that the graph keeps (same result: the ciphertexts of a batch
+ * are independent; the halves' launches overlap on the device, and their temporaries are
+ * live at the same time).  Needs the library's own allocator (CTL_ENOTSUP after
+ * ctl_set_allocator).  Graph memory and the clone are released by ctl_model_destroy,
+ * which must come before ctl_context_destroy of ctx. */
 int ctl_model_forward_graph(ctl_context* ctx, const ctl_model* model, const ctl_keys* keys, const ctl_ct* in,
                             ctl_ct** out);
 /* Several groups of queries in one launch (configuration 4's uneven batch: mixed ring

@@ -2271,10 +2271,14 @@ struct LayerPlan {
 };
 // A captured forward: the whole layer sequence of a model for one (context, keys, batch
 // size), reading a fixed staging input and writing a fixed staging output.
+// Batches from this size on are captured as two concurrent halves (ctl_model_forward_graph).
+static constexpr uint32_t kGraphSplitMin = 64;
 struct GraphEntry {
   cudaGraphExec_t exec = nullptr;
   ctl::u64* in_buf = nullptr;
   ctl::u64* out_buf = nullptr;
+  ctl_context* twin = nullptr;  // clone whose stream runs the second half of a split batch
+  uint32_t nb1 = 0;             // ciphertexts in the first half (all of them if not split)
   uint64_t kernels = 0;
   uint64_t ops[5] = {0, 0, 0, 0, 0};
 };
@@ -2434,6 +2438,7 @@ extern "C" void ctl_model_destroy(ctl_model* M) {
     dev_free(gc, kv.second.in_buf);
     dev_free(gc, kv.second.out_buf);
     cudaStreamSynchronize(gc->stream);
+    if (kv.second.twin) ctl_context_destroy(kv.second.twin);
   }
   for (auto& L : M->layers) {
     dense_release(M->ctx, L.dense);
@@ -2579,31 +2584,73 @@ extern "C" int ctl_model_forward_graph(ctl_context* c, const ctl_model* M, const
       return CTL_ENOMEM;
     }
     cudaMemsetAsync(G.in_buf, 0, ct_words(c, M->in_level, nb) * sizeof(u64), c->stream);
-    // one eager run settles every launch configuration before capture
-    int rc = model_run(c, M, k, G.in_buf, (int)nb, G.out_buf);
-    if (!rc) rc = cuda_check(cudaStreamSynchronize(c->stream), "graph warm-up");
-    if (rc) {
+    // A batch of kGraphSplitMin ciphertexts or more is captured as two halves on concurrent
+    // branches, the second on a clone's stream: the ciphertexts are independent, so the
+    // result is the same, and each launch's last wave overlaps the other half's work.
+    G.nb1 = nb >= kGraphSplitMin ? nb / 2 : nb;
+    const uint32_t nb2 = nb - G.nb1;
+    u64* in2 = G.in_buf + ct_words(c, M->in_level, G.nb1);
+    u64* out2 = G.out_buf + ct_words(c, M->out_level, G.nb1);
+    auto release = [&]() {
+      cudaStreamSynchronize(c->stream);
+      if (G.twin) ctl_context_destroy(G.twin);
       dev_free(c, G.in_buf);
       dev_free(c, G.out_buf);
+    };
+    int rc = CTL_OK;
+    if (nb2) {
+      rc = ctl_context_clone(c, &G.twin);
+      if (!rc) rc = cuda_check(cudaStreamSynchronize(c->stream), "graph staging");
+    }
+    // one eager run (per half) settles every launch configuration before capture
+    if (!rc) rc = model_run(c, M, k, G.in_buf, (int)G.nb1, G.out_buf);
+    if (!rc && nb2) rc = model_run(G.twin, M, k, in2, (int)nb2, out2);
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(c->stream), "graph warm-up");
+    if (!rc && nb2) rc = cuda_check(cudaStreamSynchronize(G.twin->stream), "graph warm-up");
+    if (rc) {
+      release();
       return rc;
     }
     const bool timing = c->timing.enabled;
     c->timing.enabled = false;
-    const uint64_t l0 = c->launch_count.load();
+    const uint64_t l0 = c->launch_count.load(), t0 = nb2 ? G.twin->launch_count.load() : 0;
     const uint64_t o0[5] = {c->op_rot, c->op_ptmul, c->op_add, c->op_relin, c->op_rescale};
+    ctl_context* tw = nb2 ? G.twin : c;  // the second half's counters (c's own when not split)
+    const uint64_t p0[5] = {tw->op_rot, tw->op_ptmul, tw->op_add, tw->op_relin, tw->op_rescale};
     cudaGraph_t graph = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    if (nb2) {
+      cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+      cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+    }
     rc = cuda_check(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
     if (!rc) {
-      const int rr = model_run(c, M, k, G.in_buf, (int)nb, G.out_buf);
+      if (nb2) {
+        cudaEventRecord(fork, c->stream);
+        cudaStreamWaitEvent(G.twin->stream, fork, 0);
+      }
+      int rr = model_run(c, M, k, G.in_buf, (int)G.nb1, G.out_buf);
+      if (nb2) {
+        if (!rr) rr = model_run(G.twin, M, k, in2, (int)nb2, out2);
+        cudaEventRecord(join, G.twin->stream);
+        cudaStreamWaitEvent(c->stream, join, 0);
+      }
       const int re = cuda_check(cudaStreamEndCapture(c->stream, &graph), "end capture");
       rc = rr ? rr : re;
     }
     if (!rc) rc = cuda_check(cudaGraphInstantiate(&G.exec, graph, 0), "graph instantiate");
     if (graph) cudaGraphDestroy(graph);
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
     c->timing.enabled = timing;
     G.kernels = c->launch_count.load() - l0;
     const uint64_t o1[5] = {c->op_rot, c->op_ptmul, c->op_add, c->op_relin, c->op_rescale};
     for (int i = 0; i < 5; i++) G.ops[i] = o1[i] - o0[i];
+    if (nb2) {  // the second half's launches and operations, counted by its clone
+      const uint64_t p1[5] = {tw->op_rot, tw->op_ptmul, tw->op_add, tw->op_relin, tw->op_rescale};
+      for (int i = 0; i < 5; i++) G.ops[i] += p1[i] - p0[i];
+      G.kernels += tw->launch_count.load() - t0;
+    }
     c->launch_count = l0;
     c->op_rot = o0[0];
     c->op_ptmul = o0[1];
@@ -2612,8 +2659,7 @@ extern "C" int ctl_model_forward_graph(ctl_context* c, const ctl_model* M, const
     c->op_rescale = o0[4];
     if (rc) {
       cudaGetLastError();
-      dev_free(c, G.in_buf);
-      dev_free(c, G.out_buf);
+      release();
       return rc;
     }
     it = Mm->graphs.emplace(key, G).first;

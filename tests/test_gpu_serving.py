@@ -45,17 +45,24 @@ def query(ctx, keys, n_in, t0, seed):
 
 
 @pytest.mark.parametrize("N,qb,pb,dnum,dims,B", [(4096, [50, 40, 40], [60], 3, [64, 32], 1),
-                                                 (8192, [60, 40, 40, 40], [60], 4, [128, 64, 32], 3)])
+                                                 (8192, [60, 40, 40, 40], [60], 4, [128, 64, 32], 3),
+                                                 (4096, [50, 40, 40], [60], 3, [64, 32], 67)])
 def test_graph_forward_equals_eager(N, qb, pb, dnum, dims, B):
+    """The graph forward equals the eager one bit for bit, and each replay counts the same
+    operations; B = 67 takes the capture as two concurrent halves (33 + 34 ciphertexts)."""
     ctx, model, _ = make_lane(N, qb, pb, dnum, dims, 1)
     keys = ctx.keygen(model.rotations(), seed=3)
     t0 = bsgs_t(dims[1], dims[0])
     batch = ctx.concat([query(ctx, keys, dims[0], t0, 10 + i) for i in range(B)])
-    eager = model.forward(keys, batch).export()
     ctx.stats_reset()
-    for _ in range(3):  # first call captures, later calls replay
+    eager = model.forward(keys, batch).export()
+    ops = ctx.stats_ops()
+    for i in range(3):  # first call captures, later calls replay
+        ctx.stats_reset()
         g = model.forward(keys, batch, graph=True).export()
         assert np.array_equal(g, eager)
+        if i:
+            assert ctx.stats_ops() == ops
     assert ctx.stats_launches() > 0 and ctx.stats_ops()["rotations"] > 0
 
 
