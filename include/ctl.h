@@ -481,7 +481,7 @@ int ctl_model_forward(ctl_context* ctx, const ctl_model* model, const ctl_keys* 
  * sequence (kernels, stream-ordered temporary allocations, copies) into a graph with
  * fixed staging buffers; later calls copy the input into the staging buffer, replay the
  * graph and copy the result out, with one launch instead of several hundred.  Calls
- * for the same (ctx, model) must not overlap.  A batch of 64 ciphertexts or more is
+ * for the same (ctx, model) must not overlap.  A batch of 8 ciphertexts or more is
  * captured as two halves on concurrent branches of the graph, the second half on the
  * stream of a context clone that the graph keeps (same result: the ciphertexts of a batch
  * are independent; the halves' launches overlap on the device, and their temporaries are
